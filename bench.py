@@ -1,0 +1,349 @@
+#!/usr/bin/env python
+"""Throughput of one time step of the GEA pressure-based Euler solver
+(Girfoglio, Quaini & Rozza, arXiv 2303.10499, Section 3) on GB300.
+
+A step is one pass of the whole hot path: continuity predictor, implicit
+momentum and enthalpy predictors, EOS update and the PISO correctors with
+their multigrid-preconditioned CG pressure solves, on the smooth rising
+bubble (640 x 320 cells, dt = 0.05 s, FP64) unless --workload says otherwise.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line. value = cell-steps/s summed over ranks (each rank runs
+an independent replica: the solver runs on one GPU), timed with CUDA events
+on the solver's stream, L2 flushed (256 MB write) between timed steps.
+--impl reference times the FP64 CPU oracle on this machine's host cores.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "cell-steps/sec and pressure-solve ms/step vs plain FP64 GPU at matched error"
+UNIT = "cell-steps/s"
+
+# Algorithmic traffic and arithmetic per cell of one launch: FP64 words read
+# once plus written once, and FP64 operations (add, mul, div, sqrt each 1;
+# an FMA counts 2). Coarse-level multigrid kernels are per cell of the level
+# they run on. Derivations are in the design notes.
+KERNEL_MODEL = {
+    "pred_setup": (12, 46),
+    "mom_jacobi": (10, 112),
+    "enth_rhs": (13, 84),
+    "enth_jacobi": (7, 56),
+    "eos_coef": (14, 52),
+    "mg_coarsen": (4, 3),
+    "H": (9, 112),
+    "helm_rhs": (15, 68),
+    "mg_down": (6.25, 17),
+    "mg_coarse": (7, 13),
+    "mg_up": (7.25, 24),
+    "mg_single": (6, 24),
+    "cg_p": (3, 2),
+    "cg_spmv": (5, 12),
+    "cg_update": (6, 6),
+    "correct": (16, 66),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="bubble640x320")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="target CPU time of the oracle baseline sample")
+    return ap.parse_args()
+
+
+def peaks():
+    p = {"hbm_gbs": 6800.0, "fp64_tflops": 1.25, "src": "fallback"}
+    try:
+        m = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        p["hbm_gbs"] = float(m["hbm_gbs"])
+        p["src"] = "measured"
+    except Exception:
+        pass
+    return p
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(parts)
+            except Exception:
+                pass
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if "Active" in r[5 + j]
+                          and "Not" not in r[5 + j]})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    try:
+        t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        src = open(os.path.join(ROOT, "paper_2303_10499_gb300", "csrc", "gea_kernels.cu"), "rb").read()
+        if t.get("kernels_sha256") != hashlib.sha256(src).hexdigest():
+            return None
+        return t.get("per_launch_bytes", {}).get(kernel)
+    except Exception:
+        return None
+
+
+def roofline(prof, pk):
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    name, d = dom
+    words, flops = KERNEL_MODEL.get(name, (0, 0))
+    cells_per_launch = d["cells"] / d["launches"]
+    t = d["ms"] / d["launches"] * 1e-3
+    gbs = words * 8 * cells_per_launch / t / 1e9
+    tfl = flops * cells_per_launch / t / 1e12
+    t_hbm = words * 8 * cells_per_launch / (pk["hbm_gbs"] * 1e9)
+    t_alu = flops * cells_per_launch / (pk["fp64_tflops"] * 1e12)
+    total = sum(v["ms"] for v in prof.values())
+    share = {k: round(v["ms"] / total, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
+    if t_alu >= t_hbm:
+        out = {"bound": "alu", "achieved": tfl, "peak": pk["fp64_tflops"], "unit": "TFLOP/s",
+               "frac": tfl / pk["fp64_tflops"],
+               "peak_source": "FP64 nominal 1.25 TFLOP/s (GB300, no FP64 entry in the measured peaks)"}
+    else:
+        out = {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+               "frac": gbs / pk["hbm_gbs"], "peak_source": f"{pk['src']} hbm_gbs"}
+    out.update({"kernel": name, "launches_per_step": d["launches"],
+                "avg_launch_ms": d["ms"] / d["launches"],
+                "algorithmic_bytes_per_launch": words * 8 * cells_per_launch,
+                "algorithmic_flops_per_launch": flops * cells_per_launch,
+                "hbm_gbs_achieved": gbs, "fp64_tflops_achieved": tfl,
+                "traffic": traffic_for(name), "kernel_share_of_step": share,
+                "timing": "CUDA events around each launch of one eager step on the solver stream"})
+    return out
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_2303_10499_gb300 import build as B
+    from paper_2303_10499_gb300 import gea
+    from paper_2303_10499_gb300 import workloads as W
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or not os.path.exists(B.LIB):
+        B.build()
+    if world > 1:
+        torch.distributed.barrier()
+    wl = W.get(args.workload)
+    cells = wl.grid.cells
+    stream = torch.cuda.current_stream()
+    s = gea.Solver(wl.grid, wl.const, stream=stream)
+    dev = {k: torch.from_numpy(v).cuda() for k, v in wl.fields.items()}
+    s.set_conservative(dev)
+    for _ in range(args.warmup):
+        s.step_async(1)
+    s.sync()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    l0 = s.stats()["launches"]
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    clk = ClockSampler(local)
+    clk.start()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for e0, e1 in evs:
+        flush.zero_()
+        e0.record(stream)
+        s.step_async(1)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = clk.stop()
+    s.sync()
+    st = s.stats()
+    launches = st["launches"] - l0
+    ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+    tot_s = sum(ms) / 1e3
+    if world > 1:
+        t = torch.tensor([tot_s], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_s = float(t.item())
+    value = world * cells * args.steps / tot_s
+
+    # pressure-solve time per step (events inside the step graph)
+    pms = []
+    for _ in range(5):
+        s.step(1)
+        pms.append(s.pressure_ms())
+    prof = s.profile_step()
+    pk = peaks()
+    roof = roofline(prof, pk)
+
+    # end to end through the C ABI with host buffers: H2D of the full state,
+    # one step, D2H of the full state, every step
+    nx, nz = wl.grid.nx, wl.grid.nz
+    host = s.get_full()
+    pin = {k: torch.from_numpy(v).pin_memory().numpy() for k, v in host.items()}
+    out = {k: torch.empty(v.shape, dtype=torch.float64).pin_memory().numpy() for k, v in host.items()}
+    nbytes = sum(v.nbytes for v in pin.values())
+    ne = max(3, min(args.steps, 20))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ne):
+        s.set_full(pin)
+        s.step(1)
+        s.get_full(out)
+    t_e2e = time.perf_counter() - t0
+    e2e = {"value": world * cells * ne / t_e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": nbytes,
+           "path": "gea_set_state(FULL, host) + gea_step(1) + gea_get_state(FULL, host)"}
+
+    res = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": statistics.mean(ms), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "grid": [nx, nz], "cells": cells,
+                   "domain_m": [wl.grid.lx, wl.grid.lz], "dt": wl.const.dt,
+                   "n_corr": wl.const.n_corr, "jac_rtol": wl.const.jac_rtol,
+                   "cg_rtol": wl.const.cg_rtol, "mg_levels": st["mg_levels"],
+                   "l2": "flushed between timed steps (256 MB write, untimed)",
+                   "parallelism": f"replicas x{world}"},
+        "pressure_solve_ms_per_step": statistics.mean(pms),
+        "cg_iters_last_step": st["cg_iters"], "jacobi_sweeps_last_step": [st["jac_u"], st["jac_h"]],
+        "ms_per_step_min": min(ms), "ms_per_step_median": statistics.median(ms),
+        "gpu_launches": int(launches) * world, "clocks": clocks, "e2e": e2e, "roofline": roof,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+
+
+def cpu_baseline(wl, seconds):
+    """The FP64 CPU oracle as it stands, single-threaded, on a bounded sample
+    of the same workload (consecutive steps from t = 0)."""
+    import oracle
+    o = oracle.Oracle(wl.grid, wl.const)
+    st = o.derive(wl.fields)
+    t0 = time.perf_counter()
+    o.step(st, 1)
+    t1 = time.perf_counter() - t0
+    n = max(1, min(200, int(seconds / max(t1, 1e-6)) - 1))
+    t0 = time.perf_counter()
+    o.step(st, n)
+    dt = time.perf_counter() - t0
+    return {"value": wl.grid.cells * n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"steps 2..{n + 1} of {wl.name} from t=0 ({n} steps, {dt:.1f} s)"}
+
+
+def run_reference(args):
+    world, rank, local = dist_env()
+    if rank != 0:
+        return
+    from paper_2303_10499_gb300 import workloads as W
+    import oracle
+    wl = W.get(args.workload)
+    o = oracle.Oracle(wl.grid, wl.const)
+    st = o.derive(wl.fields)
+    for _ in range(args.warmup):
+        o.step(st, 1)
+    ms = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        o.step(st, 1)
+        ms.append((time.perf_counter() - t0) * 1e3)
+    value = wl.grid.cells * args.steps / (sum(ms) / 1e3)
+    res = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(ms),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "grid": [wl.grid.nx, wl.grid.nz], "cells": wl.grid.cells,
+                   "dt": wl.const.dt, "parallelism": "single host thread"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} consecutive steps of {wl.name} after "
+                                   f"{args.warmup} warm-up steps"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(res), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,199 @@
+/*
+ * gea.h -- C ABI of the GB300 (sm_103a) library that advances the dry
+ * compressible Euler equations with the pressure-based finite-volume scheme
+ * of Girfoglio, Quaini & Rozza, "GEA: a new finite volume-based open source
+ * code for the numerical simulation of atmospheric and ocean flows"
+ * (arXiv 2303.10499).
+ *
+ * One time step is the three-step split of Section 3 on a uniform Cartesian
+ * x-z grid with free-slip walls (Section 4):
+ *   Step 1  continuity predictor (eq. e1_d), implicit momentum predictor
+ *           (eq. step2_sd, first line) and K^{n+1/3} (eq. step1_3sd);
+ *   Step 2  implicit enthalpy equation (eq. step3_sd), temperature update
+ *           (eq. step3_2sd) and rho^{n+2/3} (eq. step3_3sd);
+ *   Step 3  PISO correctors: momentum corrector (eq. step2_sd, second line)
+ *           and the compressible pressure equation (eq. p_prime_sd) in its
+ *           Helmholtz form, solved by multigrid-preconditioned conjugate
+ *           gradients, then p, K and rho^{n+1} (eq. step4_4sd).
+ * Every stage runs in this library's CUDA kernels on one GPU, in FP64.
+ *
+ * Conventions
+ *  - Cell fields are nz rows of nx values, x fastest (row-major, index
+ *    k*nx + i for cell (i,k) centred at ((i+1/2) dx, (k+1/2) dz)).
+ *  - phix holds the mass fluxes phi_j = (rho u)_j . A_j (kg/s per unit depth)
+ *    through the nx+1 x-faces of each row: nz rows of nx+1 values, face f
+ *    between cells f-1 and f; phiz holds the z-face fluxes: nz+1 rows of nx
+ *    values, face f between rows f-1 and f. Wall faces carry zero.
+ *  - Pressure split p = p' - rho g z with g > 0 and z up (the force in the
+ *    momentum equation is grad p' - g z grad rho).
+ *  - All calls are ordered on the context's stream (gea_set_stream). Calls
+ *    that take host buffers return after the copies are complete.
+ *  - Functions return GEA_OK (0) or one of the GEA_ERR_* codes;
+ *    gea_last_error() gives a message for the last failure on a context.
+ *  - One context must not be used from two host threads at once. Contexts
+ *    are independent; the library keeps no global mutable state.
+ */
+#ifndef GEA_H
+#define GEA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    GEA_OK = 0,
+    GEA_ERR_INVAL = 1,      /* bad argument: sizes, constants, null pointers */
+    GEA_ERR_NOMEM = 2,      /* device allocation failed */
+    GEA_ERR_CUDA = 3,       /* a CUDA runtime call failed */
+    GEA_ERR_NOCONV = 4,     /* a linear solve reached its iteration cap */
+    GEA_ERR_NONFINITE = 5,  /* NaN or Inf in a residual norm */
+    GEA_ERR_STATE = 6       /* no state has been set yet */
+};
+
+enum { GEA_STATE_CONSERVATIVE = 0, GEA_STATE_FULL = 1 };
+enum { GEA_MEM_HOST = 0, GEA_MEM_DEVICE = 1 };
+
+/* Uniform Cartesian grid: nx * nz cells on [0, lx] x [0, lz] (metres).
+ * nx, nz >= 4. */
+typedef struct gea_grid {
+    int32_t nx, nz;
+    double lx, lz;
+} gea_grid;
+
+/* Physical constants (SI) and solver settings.
+ *  R, cp     gas constant and heat capacity at constant pressure (eq. p,
+ *            eq. K_h); cv = cp - R.
+ *  g         gravitational acceleration, > 0 (0 allowed: no gravity).
+ *  p0        reference pressure of the potential temperature (Remark 2).
+ *  mu, Pr    constant artificial (dynamic) viscosity and Prandtl number of
+ *            Remark 1, eqs. (mom_LES), (ent_LES).
+ *  dt        time step (BDF1).
+ *  n_corr    number of PISO correctors (Section 3), 1..4.
+ *  jac_rtol, jac_maxit   Jacobi iteration for the implicit momentum and
+ *            enthalpy predictors: stops after the sweep whose residual met
+ *            ||r||_2 <= jac_rtol ||b||_2.
+ *  cg_rtol, cg_maxit     conjugate gradients for the pressure equation:
+ *            stops when ||r||_2 <= cg_rtol ||b||_2 (recursive residual).
+ *  mg_min_cells  the multigrid preconditioner coarsens (by 2 in x and z,
+ *            while both sizes are even) until a level has at most this many
+ *            cells; 0 selects the default (4096). 1 disables coarsening.
+ *  flags     reserved, pass 0. */
+typedef struct gea_constants {
+    double R, cp, g, p0, mu, Pr, dt;
+    int32_t n_corr;
+    double jac_rtol;
+    int32_t jac_maxit;
+    double cg_rtol;
+    int32_t cg_maxit;
+    int32_t mg_min_cells;
+    int32_t flags;
+} gea_constants;
+
+/* A view of caller-owned buffers (host or device, per mem). The library
+ * copies from/to them; it never keeps the pointers.
+ *  CONSERVATIVE: rho, rhou, rhow, rhoe (rho e = rho (cv T + |u|^2/2 + g z)).
+ *  FULL: rho, u, w, T, h, p, pp (= p'), pold (= p^{n-1}), phix, phiz -- the
+ *        complete state carried between steps; a FULL get followed by a FULL
+ *        set continues bit for bit as if the run had not been interrupted. */
+typedef struct gea_state_view {
+    int32_t kind;
+    int32_t mem;
+    double *rho, *rhou, *rhow, *rhoe;
+    double *u, *w, *T, *h, *p, *pp, *pold, *phix, *phiz;
+} gea_state_view;
+
+/* Counters of the last completed step. */
+typedef struct gea_stats {
+    int64_t steps_done;        /* steps completed since the last set_state */
+    int32_t jac_u, jac_h;      /* Jacobi sweeps: momentum (u and w together), enthalpy */
+    int32_t cg_iters[4];       /* CG iterations per PISO corrector */
+    double cg_relres[4];       /* final ||r|| / ||b|| per corrector */
+    int32_t status;            /* GEA_OK or the first device-side error */
+    int32_t mg_levels;         /* multigrid levels in use */
+    int64_t launches;          /* kernel launches since the last set_state */
+} gea_stats;
+
+typedef struct gea_ctx gea_ctx;
+
+/* Create a context for one grid and constant set on the current CUDA device:
+ * validates the arguments and allocates every device buffer (state, scratch,
+ * multigrid hierarchy). The context owns them; gea_destroy frees them.
+ * Errors: GEA_ERR_INVAL (sizes < 4, non-positive R, cp > R, dt, lengths,
+ * n_corr outside 1..4, non-positive tolerances or caps), GEA_ERR_NOMEM,
+ * GEA_ERR_CUDA. */
+int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out);
+
+/* Order all later work of ctx on this cudaStream_t (NULL: the legacy default
+ * stream). */
+int gea_set_stream(gea_ctx *ctx, void *stream);
+
+/* Load a state. CONSERVATIVE derives the rest on the device: u = (rho u)/rho,
+ * T = (e - K - g z)/cv, p = rho R T (eq. p), h = cp T (eq. K_h),
+ * p' = p + rho g z, p^{n-1} = p, and phi on interior faces the average of the
+ * two cells' normal momentum times the face area (Section 3).
+ * Errors: GEA_ERR_INVAL (null pointers, rho <= 0 or T <= 0 anywhere). */
+int gea_set_state(gea_ctx *ctx, const gea_state_view *v);
+
+/* Advance n >= 0 steps (Section 3, Steps 1-3). Returns after the launches
+ * are enqueued and the status of the finished steps has been read back,
+ * i.e. it synchronises the stream once at the end. On GEA_ERR_NOCONV or
+ * GEA_ERR_NONFINITE the state stays at the last completed step. */
+int gea_step(gea_ctx *ctx, int32_t n);
+
+/* Enqueue n steps without waiting; gea_sync reports their status. */
+int gea_step_async(gea_ctx *ctx, int32_t n);
+int gea_sync(gea_ctx *ctx);
+
+/* Copy the state out (kind/mem as in set_state). Synchronises. */
+int gea_get_state(gea_ctx *ctx, gea_state_view *out);
+
+/* Diagnostics (Remark 2): theta' = T (p0/p)^(R/cp) - theta_bar(z) per cell
+ * into theta_prime (host, nz*nx, may be NULL), given the background
+ * theta_bar (host, nz values); mass = sum rho V and energy = sum rho e V
+ * (may be NULL). Computed on the device. */
+int gea_get_diag(gea_ctx *ctx, const double *theta_bar, double *theta_prime,
+                 double *mass, double *energy);
+
+/* Counters of the last completed step. */
+int gea_get_stats(gea_ctx *ctx, gea_stats *s);
+
+/* Intermediate fields of the last step, copied to host (nz*nx doubles, or
+ * face arrays as in phix/phiz for GEA_FIELD_DX/DZ):
+ *  RHO1 = rho^{n+1/3}; U1, W1 = u^{n+1/3}; H1 = h^{n+1}; RHO2 = rho^{n+2/3};
+ *  HX, HZ = H(u) and B = pressure right-hand side of the last corrector;
+ *  DX, DZ = face coefficients D_f = dt rho2_f / rho1_f. */
+enum {
+    GEA_FIELD_RHO1 = 0, GEA_FIELD_U1 = 1, GEA_FIELD_W1 = 2, GEA_FIELD_H1 = 3,
+    GEA_FIELD_RHO2 = 4, GEA_FIELD_HX = 5, GEA_FIELD_HZ = 6, GEA_FIELD_B = 7,
+    GEA_FIELD_DX = 8, GEA_FIELD_DZ = 9
+};
+int gea_get_field(gea_ctx *ctx, int32_t which, double *host);
+
+/* Event-timed duration (ms) of the pressure solves (all correctors) of the
+ * last step launched by gea_step/gea_step_async, or -1 if unavailable. */
+double gea_last_pressure_ms(gea_ctx *ctx);
+
+/* Per-kernel timing of one step. */
+typedef struct gea_kernel_time {
+    char name[40];     /* kernel (stage) name */
+    int32_t launches;  /* launches in the step */
+    int64_t cells;     /* grid cells covered, summed over the launches */
+    double ms;         /* summed CUDA-event durations of the launches */
+} gea_kernel_time;
+
+/* Advance one step with the same kernels as gea_step, launched one by one
+ * (no graph) with a CUDA event pair around each launch on the context's
+ * stream, the solver loops checked from the host. Writes up to max_entries
+ * per-kernel totals to out and their number to *n_entries. Synchronises. */
+int gea_profile_step(gea_ctx *ctx, gea_kernel_time *out, int32_t max_entries,
+                     int32_t *n_entries);
+
+const char *gea_last_error(const gea_ctx *ctx);
+void gea_destroy(gea_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GEA_H */

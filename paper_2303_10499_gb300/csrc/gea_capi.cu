@@ -1,0 +1,646 @@
+// gea_capi.cu -- context, CUDA-graph step driver and the C ABI declared in
+// include/gea.h.
+//
+// A context owns one device allocation that holds two copies of the state
+// (the step reads one and writes the other, so a failed step leaves the last
+// completed state intact), the per-step scratch, the multigrid hierarchy and
+// the device scalars. One time step is one CUDA graph: the iterations of the
+// Jacobi and conjugate-gradient solves run as conditional WHILE nodes whose
+// bodies end in a one-thread control kernel, so a step needs no host
+// round trip. Two graphs (state 0 -> 1 and state 1 -> 0) are built on the
+// first step.
+#include "gea_internal.cuh"
+#include "../../include/gea.h"
+
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+using namespace gea;
+
+struct gea_ctx {
+    Geom G;
+    Phys F;
+    gea_constants C;
+    int device = 0;
+    cudaStream_t stream = nullptr;        // user stream (launches)
+    cudaStream_t cap = nullptr;           // private stream used for graph capture
+    cudaStream_t cap2 = nullptr;          // private stream used for loop bodies
+    char *mem = nullptr;
+    size_t mem_bytes = 0;
+    State S[2];
+    double *rho1, *jd, *bu, *bw, *ua, *wa, *ub, *wb, *bh, *ha, *hb, *rho2, *Dx, *Dz, *Hx, *Hz,
+        *b, *p, *q;
+    double *stage;                         // staging for conservative set/get (4 fields)
+    double *thbar;                         // nz values
+    double *thout;                         // theta' output
+    std::vector<Level> L;
+    Scal *sc = nullptr;
+    double *partials = nullptr;
+    cudaGraph_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    cudaEvent_t ev[8];
+    int nev = 0;
+    bool have_state = false;
+    int base = 0;                         // state slot loaded by the last set_state
+    long long steps_at_sync = 0;          // device steps_done at the last sync
+    char err[256] = {0};
+};
+
+namespace {
+
+int fail(gea_ctx *c, int code, const char *fmt, ...)
+{
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof(c->err), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+#define CK(call)                                                                           \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(ctx, GEA_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                               \
+    } while (0)
+
+size_t round_up(size_t x, size_t m) { return (x + m - 1) / m * m; }
+
+Geom make_geom(int nx, int nz, double lx, double lz)
+{
+    Geom G;
+    G.nx = nx;
+    G.nz = nz;
+    G.P = (int)round_up((size_t)nx + 1, 32);
+    G.dx = lx / nx;
+    G.dz = lz / nz;
+    G.idx = 1.0 / G.dx;
+    G.idz = 1.0 / G.dz;
+    G.iV = 1.0 / (G.dx * G.dz);
+    return G;
+}
+
+// bytes of one pitched array with `rows` rows
+size_t arr_bytes(const Geom &G, int rows) { return round_up((size_t)G.P * rows * sizeof(double), 256); }
+
+StepArgs step_args(gea_ctx *c, int from)
+{
+    StepArgs a;
+    a.G = c->G;
+    a.F = c->F;
+    a.S = c->S[from];
+    a.N = c->S[from ^ 1];
+    a.rho1 = c->rho1; a.jd = c->jd; a.bu = c->bu; a.bw = c->bw;
+    a.ua = c->ua; a.wa = c->wa; a.ub = c->ub; a.wb = c->wb;
+    a.bh = c->bh; a.ha = c->ha; a.hb = c->hb;
+    a.rho2 = c->rho2; a.Dx = c->Dx; a.Dz = c->Dz; a.Hx = c->Hx; a.Hz = c->Hz; a.b = c->b;
+    a.p = c->p; a.q = c->q;
+    a.sc = c->sc;
+    a.partials = c->partials;
+    a.jac_rtol2 = c->C.jac_rtol * c->C.jac_rtol;
+    a.cg_rtol2 = c->C.cg_rtol * c->C.cg_rtol;
+    return a;
+}
+
+constexpr int kCoarseSweeps = 4;
+constexpr double kOmega = 0.8;
+
+// Append a WHILE conditional node to the graph being captured on `s`; its
+// body is captured from body(body_stream, handle, true).
+template <class Body>
+int capture_while(gea_ctx *ctx, cudaStream_t s, Body body)
+{
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g;
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *edges = nullptr;
+    size_t ndeps = 0;
+    CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, &edges, &ndeps));
+    if (cs != cudaStreamCaptureStatusActive) return fail(ctx, GEA_ERR_CUDA, "capture not active");
+    cudaGraphConditionalHandle h;
+    CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams prm = {cudaGraphNodeTypeConditional};
+    prm.conditional.handle = h;
+    prm.conditional.type = cudaGraphCondTypeWhile;
+    prm.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, g, deps, edges, ndeps, &prm));
+    cudaGraph_t bodyg = prm.conditional.phGraph_out[0];
+    CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    CK(cudaStreamBeginCaptureToGraph(ctx->cap2, bodyg, nullptr, nullptr, 0,
+                                     cudaStreamCaptureModeThreadLocal));
+    body(ctx->cap2, h, true);
+    cudaGraph_t out = nullptr;
+    CK(cudaStreamEndCapture(ctx->cap2, &out));
+    return GEA_OK;
+}
+
+// Run a loop body eagerly on `s` until its control kernel reports that the
+// loop is finished (converged, failed or at its trip cap).
+template <class Body>
+int eager_while(gea_ctx *ctx, cudaStream_t s, int which, int maxtrips, Body body)
+{
+    for (int t = 0; t < maxtrips + 1; ++t) {
+        body(s, (cudaGraphConditionalHandle)0, false);
+        Scal h;
+        CK(cudaMemcpyAsync(&h, ctx->sc, sizeof(Scal), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (h.done[which] || h.status || h.trips[which] >= maxtrips) break;
+    }
+    return GEA_OK;
+}
+
+// The kernel sequence of one time step reading state `from` and writing
+// state `from ^ 1` (Section 3: Step 1, Step 2, then n_corr PISO correctors).
+// graph = true: enqueue into the capture running on s (loops become WHILE
+// nodes); graph = false: launch eagerly with host-checked loops, every launch
+// bracketed by tr.
+int record_step(gea_ctx *ctx, int from, cudaStream_t s, bool graph, Tracer *tr)
+{
+    StepArgs a = step_args(ctx, from);
+    Level *L = ctx->L.data();
+    const int nlev = (int)ctx->L.size();
+    const int jtrips = (ctx->C.jac_maxit + 1) / 2;
+    int fixed = 0;
+    int rc = GEA_OK;
+    auto loop = [&](int which, int maxtrips, auto body) {
+        return graph ? capture_while(ctx, s, body) : eager_while(ctx, s, which, maxtrips, body);
+    };
+
+    launch_step_begin(ctx->sc, s, tr); ++fixed;
+    // Step 1: continuity predictor and implicit momentum predictor
+    launch_pred_setup(a, s, tr); ++fixed;
+    rc = loop(LOOP_MOM, jtrips, [&](cudaStream_t bs, cudaGraphConditionalHandle h, bool g) {
+        launch_mom_jacobi(a, a.ua, a.wa, a.ub, a.wb, bs, tr);
+        launch_mom_jacobi(a, a.ub, a.wb, a.ua, a.wa, bs, tr);
+        launch_loop_ctl(a.sc, h, g, LOOP_MOM, jtrips, 3, bs, tr);
+    });
+    if (rc) return rc;
+    // Step 2: enthalpy, temperature, rho^{n+2/3}
+    launch_enth_rhs(a, s, tr); ++fixed;
+    rc = loop(LOOP_ENTH, jtrips, [&](cudaStream_t bs, cudaGraphConditionalHandle h, bool g) {
+        launch_enth_jacobi(a, a.ha, a.hb, bs, tr);
+        launch_enth_jacobi(a, a.hb, a.ha, bs, tr);
+        launch_loop_ctl(a.sc, h, g, LOOP_ENTH, jtrips, 3, bs, tr);
+    });
+    if (rc) return rc;
+    launch_eos_coef(a, L[0], s, tr); ++fixed;
+    for (int l = 0; l + 1 < nlev; ++l) { launch_mg_coarsen(L[l], L[l + 1], s, tr); ++fixed; }
+    // Step 3: PISO correctors
+    const int body_cg = (nlev == 1 ? 1 : 2 * (nlev - 1) + kCoarseSweeps) + 3 + 1;
+    for (int c = 0; c < ctx->C.n_corr; ++c) {
+        const double *U = c == 0 ? a.ua : a.N.u;
+        const double *W = c == 0 ? a.wa : a.N.w;
+        launch_H(a, U, W, s, tr); ++fixed;
+        CK(cudaEventRecord(ctx->ev[2 * c], s));
+        launch_helm_rhs(a, L[0], c == 0 ? a.S.pp : a.N.pp, a.N.pp, c, s, tr); ++fixed;
+        rc = loop(LOOP_CG, ctx->C.cg_maxit, [&](cudaStream_t bs, cudaGraphConditionalHandle h, bool g) {
+            launch_vcycle(a, L, nlev, kCoarseSweeps, kOmega, bs, tr);
+            launch_cg_iter_tail(a, L[0], a.N.pp, bs, tr);
+            launch_loop_ctl(a.sc, h, g, LOOP_CG, ctx->C.cg_maxit, body_cg, bs, tr);
+        });
+        if (rc) return rc;
+        CK(cudaEventRecord(ctx->ev[2 * c + 1], s));
+        launch_correct(a, s, tr); ++fixed;
+    }
+    ++fixed;
+    launch_step_end(ctx->sc, fixed, s, tr);
+    return GEA_OK;
+}
+
+int build_graph(gea_ctx *ctx, int from)
+{
+    cudaStream_t s = ctx->cap;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    int rc = record_step(ctx, from, s, true, nullptr);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(ctx, GEA_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+    ctx->graph[from] = g;
+    CK(cudaGraphInstantiate(&ctx->exec[from], g, 0));
+    return GEA_OK;
+}
+
+int ensure_graphs(gea_ctx *ctx)
+{
+    for (int f = 0; f < 2; ++f)
+        if (!ctx->exec[f]) {
+            int rc = build_graph(ctx, f);
+            if (rc) return rc;
+        }
+    return GEA_OK;
+}
+
+// Records an event pair around every launch of an eager step.
+struct EventTracer : Tracer {
+    struct Rec {
+        const char *name;
+        long long cells;
+        cudaEvent_t e0, e1;
+    };
+    std::vector<Rec> recs;
+    void begin(const char *name, long long cells, cudaStream_t st) override
+    {
+        Rec r{name, cells, nullptr, nullptr};
+        cudaEventCreate(&r.e0);
+        cudaEventCreate(&r.e1);
+        cudaEventRecord(r.e0, st);
+        recs.push_back(r);
+    }
+    void end(cudaStream_t st) override { cudaEventRecord(recs.back().e1, st); }
+    ~EventTracer() override
+    {
+        for (auto &r : recs) {
+            cudaEventDestroy(r.e0);
+            cudaEventDestroy(r.e1);
+        }
+    }
+};
+
+int read_scal(gea_ctx *ctx, Scal *h)
+{
+    CK(cudaMemcpyAsync(h, ctx->sc, sizeof(Scal), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return GEA_OK;
+}
+
+int current_slot(gea_ctx *ctx, const Scal &h)
+{
+    return (int)((ctx->base + h.steps_done) & 1);
+}
+
+// Pitched copy of a dense nz x ncols host/device array to/from device.
+int copy_in(gea_ctx *ctx, double *dst, const double *src, int ncols, int rows)
+{
+    CK(cudaMemcpy2DAsync(dst, (size_t)ctx->G.P * sizeof(double), src, (size_t)ncols * sizeof(double),
+                         (size_t)ncols * sizeof(double), rows, cudaMemcpyDefault, ctx->stream));
+    return GEA_OK;
+}
+int copy_out(gea_ctx *ctx, double *dst, const double *src, int ncols, int rows)
+{
+    CK(cudaMemcpy2DAsync(dst, (size_t)ncols * sizeof(double), src, (size_t)ctx->G.P * sizeof(double),
+                         (size_t)ncols * sizeof(double), rows, cudaMemcpyDefault, ctx->stream));
+    return GEA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
+{
+    gea_ctx *ctx = nullptr;
+    if (!grid || !c || !out) return GEA_ERR_INVAL;
+    *out = nullptr;
+    if (grid->nx < 4 || grid->nz < 4 || !(grid->lx > 0) || !(grid->lz > 0)) return GEA_ERR_INVAL;
+    if ((long long)grid->nx * grid->nz > (1LL << 31) / 2) return GEA_ERR_INVAL;
+    if (!(c->R > 0) || !(c->cp > c->R) || !(c->g >= 0) || !(c->p0 > 0) || !(c->mu >= 0) ||
+        !(c->Pr > 0) || !(c->dt > 0) || c->n_corr < 1 || c->n_corr > 4 || !(c->jac_rtol > 0) ||
+        c->jac_maxit < 1 || !(c->cg_rtol > 0) || c->cg_maxit < 1 || c->mg_min_cells < 0)
+        return GEA_ERR_INVAL;
+
+    ctx = new gea_ctx();
+    ctx->C = *c;
+    if (ctx->C.mg_min_cells == 0) ctx->C.mg_min_cells = 4096;
+    ctx->G = make_geom(grid->nx, grid->nz, grid->lx, grid->lz);
+    ctx->F.R = c->R; ctx->F.cp = c->cp; ctx->F.g = c->g; ctx->F.p0 = c->p0;
+    ctx->F.mu = c->mu; ctx->F.nuh = c->mu / c->Pr; ctx->F.dt = c->dt; ctx->F.idt = 1.0 / c->dt;
+    if (cudaGetDevice(&ctx->device) != cudaSuccess) {
+        delete ctx;
+        return GEA_ERR_CUDA;
+    }
+
+    // multigrid levels: halve while both sizes are even and the level is
+    // larger than mg_min_cells
+    std::vector<Geom> lg;
+    lg.push_back(ctx->G);
+    while (true) {
+        const Geom &f = lg.back();
+        if (f.nx % 2 || f.nz % 2 || f.nx < 8 || f.nz < 8) break;
+        if ((long long)f.nx * f.nz <= ctx->C.mg_min_cells) break;
+        lg.push_back(make_geom(f.nx / 2, f.nz / 2, f.nx * f.dx, f.nz * f.dz));
+    }
+
+    // one allocation for everything
+    const Geom &G = ctx->G;
+    const size_t cell = arr_bytes(G, G.nz), fz = arr_bytes(G, G.nz + 1);
+    size_t total = 0;
+    total += 2 * (9 * cell + fz);                  // two states (phiz has nz+1 rows)
+    total += 19 * cell + 2 * fz;                   // scratch (Dz has nz+1 rows) + stage
+    total += 4 * cell;                             // staging for conservative fields
+    total += 2 * cell + round_up(G.nz * sizeof(double), 256);   // theta_bar, theta'
+    for (const Geom &g : lg) total += 6 * arr_bytes(g, g.nz) + arr_bytes(g, g.nz + 1);
+    const size_t nb = (size_t)max_blocks(G);
+    total += round_up(4 * nb * sizeof(double), 256);
+    total += round_up(sizeof(Scal), 256);
+    ctx->mem_bytes = total;
+    if (cudaMalloc(&ctx->mem, total) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return GEA_ERR_NOMEM;
+    }
+    cudaMemset(ctx->mem, 0, total);
+    char *ptr = ctx->mem;
+    auto take = [&](size_t bytes) { double *r = (double *)ptr; ptr += bytes; return r; };
+    for (int s = 0; s < 2; ++s) {
+        State &S = ctx->S[s];
+        S.rho = take(cell); S.u = take(cell); S.w = take(cell); S.T = take(cell); S.h = take(cell);
+        S.p = take(cell); S.pp = take(cell); S.pold = take(cell); S.phix = take(cell); S.phiz = take(fz);
+    }
+    ctx->rho1 = take(cell); ctx->jd = take(cell); ctx->bu = take(cell); ctx->bw = take(cell);
+    ctx->ua = take(cell); ctx->wa = take(cell); ctx->ub = take(cell); ctx->wb = take(cell);
+    ctx->bh = take(cell); ctx->ha = take(cell); ctx->hb = take(cell); ctx->rho2 = take(cell);
+    ctx->Dx = take(cell); ctx->Dz = take(fz); ctx->Hx = take(cell); ctx->Hz = take(cell);
+    ctx->b = take(cell); ctx->p = take(cell); ctx->q = take(cell);
+    ctx->stage = take(4 * cell);
+    ctx->thout = take(cell);
+    ctx->thbar = take(round_up(G.nz * sizeof(double), 256));
+    for (const Geom &g : lg) {
+        Level l;
+        l.G = g;
+        const size_t lc = arr_bytes(g, g.nz), lf = arr_bytes(g, g.nz + 1);
+        l.c = take(lc); l.ax = take(lc); l.az = take(lf); l.dinv = take(lc);
+        l.r = take(lc); l.e = take(lc); l.e2 = take(lc);
+        ctx->L.push_back(l);
+    }
+    ctx->partials = take(round_up(4 * nb * sizeof(double), 256));
+    ctx->sc = (Scal *)take(round_up(sizeof(Scal), 256));
+    if ((size_t)(ptr - ctx->mem) > total) {
+        gea_destroy(ctx);
+        return GEA_ERR_NOMEM;
+    }
+    for (int e = 0; e < 8; ++e) cudaEventCreate(&ctx->ev[e]);
+    ctx->nev = 8;
+    if (cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->cap2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess) {
+        gea_destroy(ctx);
+        return GEA_ERR_CUDA;
+    }
+    *out = ctx;
+    return GEA_OK;
+}
+
+int gea_set_stream(gea_ctx *ctx, void *stream)
+{
+    if (!ctx) return GEA_ERR_INVAL;
+    ctx->stream = (cudaStream_t)stream;
+    return GEA_OK;
+}
+
+int gea_set_state(gea_ctx *ctx, const gea_state_view *v)
+{
+    if (!ctx || !v) return GEA_ERR_INVAL;
+    const Geom &G = ctx->G;
+    const int nx = G.nx, nz = G.nz;
+    if (!v->rho) return fail(ctx, GEA_ERR_INVAL, "rho is null");
+    // reset the device scalars: status, counters, step count
+    CK(cudaMemsetAsync(ctx->sc, 0, sizeof(Scal), ctx->stream));
+    State &S = ctx->S[0];
+    if (v->kind == GEA_STATE_CONSERVATIVE) {
+        if (!v->rhou || !v->rhow || !v->rhoe) return fail(ctx, GEA_ERR_INVAL, "null conservative field");
+        const size_t cellw = arr_bytes(G, nz) / sizeof(double);
+        double *st = ctx->stage;
+        int rc;
+        if ((rc = copy_in(ctx, st, v->rho, nx, nz)) || (rc = copy_in(ctx, st + cellw, v->rhou, nx, nz)) ||
+            (rc = copy_in(ctx, st + 2 * cellw, v->rhow, nx, nz)) ||
+            (rc = copy_in(ctx, st + 3 * cellw, v->rhoe, nx, nz)))
+            return rc;
+        launch_derive(G, ctx->F, st, st + cellw, st + 2 * cellw, st + 3 * cellw, S, ctx->sc, ctx->stream);
+        CK(cudaGetLastError());
+    } else if (v->kind == GEA_STATE_FULL) {
+        const double *src[10] = {v->rho, v->u, v->w, v->T, v->h, v->p, v->pp, v->pold, v->phix, v->phiz};
+        double *dst[10] = {S.rho, S.u, S.w, S.T, S.h, S.p, S.pp, S.pold, S.phix, S.phiz};
+        for (int f = 0; f < 10; ++f) {
+            if (!src[f]) return fail(ctx, GEA_ERR_INVAL, "null field %d", f);
+            const int cols = f == 8 ? nx + 1 : nx, rows = f == 9 ? nz + 1 : nz;
+            int rc = copy_in(ctx, dst[f], src[f], cols, rows);
+            if (rc) return rc;
+        }
+    } else {
+        return fail(ctx, GEA_ERR_INVAL, "unknown state kind %d", v->kind);
+    }
+    Scal h;
+    int rc = read_scal(ctx, &h);
+    if (rc) return rc;
+    if (h.bad_cells) {
+        ctx->have_state = false;
+        return fail(ctx, GEA_ERR_INVAL, "%d cells with rho <= 0 or T <= 0", h.bad_cells);
+    }
+    ctx->base = 0;
+    ctx->steps_at_sync = 0;
+    ctx->have_state = true;
+    return GEA_OK;
+}
+
+int gea_step_async(gea_ctx *ctx, int32_t n)
+{
+    if (!ctx || n < 0) return GEA_ERR_INVAL;
+    if (!ctx->have_state) return fail(ctx, GEA_ERR_STATE, "no state set");
+    int rc = ensure_graphs(ctx);
+    if (rc) return rc;
+    // the slot holding the newest state is base + steps launched so far;
+    // launches alternate the two graphs
+    for (int s = 0; s < n; ++s) {
+        const int from = (int)((ctx->base + ctx->steps_at_sync) & 1);
+        CK(cudaGraphLaunch(ctx->exec[from], ctx->stream));
+        ctx->steps_at_sync += 1;
+    }
+    return GEA_OK;
+}
+
+int gea_sync(gea_ctx *ctx)
+{
+    if (!ctx) return GEA_ERR_INVAL;
+    Scal h;
+    int rc = read_scal(ctx, &h);
+    if (rc) return rc;
+    // steps that did not complete (after a device-side error) did not move
+    // the state
+    ctx->steps_at_sync = h.steps_done;
+    if (h.last_status == GEA_ERR_NOCONV) return fail(ctx, GEA_ERR_NOCONV, "a linear solve reached its iteration cap");
+    if (h.last_status == GEA_ERR_NONFINITE) return fail(ctx, GEA_ERR_NONFINITE, "non-finite residual");
+    if (h.last_status) return fail(ctx, h.last_status, "device status %d", h.last_status);
+    return GEA_OK;
+}
+
+int gea_step(gea_ctx *ctx, int32_t n)
+{
+    int rc = gea_step_async(ctx, n);
+    if (rc) return rc;
+    return gea_sync(ctx);
+}
+
+int gea_get_state(gea_ctx *ctx, gea_state_view *v)
+{
+    if (!ctx || !v) return GEA_ERR_INVAL;
+    if (!ctx->have_state) return fail(ctx, GEA_ERR_STATE, "no state set");
+    Scal h;
+    int rc = read_scal(ctx, &h);
+    if (rc) return rc;
+    const Geom &G = ctx->G;
+    const int nx = G.nx, nz = G.nz;
+    const State &S = ctx->S[current_slot(ctx, h)];
+    if (v->kind == GEA_STATE_FULL) {
+        double *dst[10] = {v->rho, v->u, v->w, v->T, v->h, v->p, v->pp, v->pold, v->phix, v->phiz};
+        const double *src[10] = {S.rho, S.u, S.w, S.T, S.h, S.p, S.pp, S.pold, S.phix, S.phiz};
+        for (int f = 0; f < 10; ++f) {
+            if (!dst[f]) continue;
+            const int cols = f == 8 ? nx + 1 : nx, rows = f == 9 ? nz + 1 : nz;
+            if ((rc = copy_out(ctx, dst[f], src[f], cols, rows))) return rc;
+        }
+    } else if (v->kind == GEA_STATE_CONSERVATIVE) {
+        return fail(ctx, GEA_ERR_INVAL, "conservative get is computed by the caller from FULL");
+    } else {
+        return fail(ctx, GEA_ERR_INVAL, "unknown state kind %d", v->kind);
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return GEA_OK;
+}
+
+int gea_get_diag(gea_ctx *ctx, const double *theta_bar, double *theta_prime, double *mass,
+                 double *energy)
+{
+    if (!ctx) return GEA_ERR_INVAL;
+    if (!ctx->have_state) return fail(ctx, GEA_ERR_STATE, "no state set");
+    Scal h;
+    int rc = read_scal(ctx, &h);
+    if (rc) return rc;
+    const Geom &G = ctx->G;
+    if (theta_prime && !theta_bar) return fail(ctx, GEA_ERR_INVAL, "theta_prime needs theta_bar");
+    if (theta_bar)
+        CK(cudaMemcpyAsync(ctx->thbar, theta_bar, G.nz * sizeof(double), cudaMemcpyDefault, ctx->stream));
+    launch_diag(G, ctx->F, ctx->S[current_slot(ctx, h)], ctx->thbar, theta_prime ? ctx->thout : nullptr,
+                ctx->sc, ctx->partials, ctx->stream);
+    CK(cudaGetLastError());
+    if (theta_prime && (rc = copy_out(ctx, theta_prime, ctx->thout, G.nx, G.nz))) return rc;
+    if ((rc = read_scal(ctx, &h))) return rc;
+    if (mass) *mass = h.mass;
+    if (energy) *energy = h.energy;
+    return GEA_OK;
+}
+
+int gea_get_stats(gea_ctx *ctx, gea_stats *s)
+{
+    if (!ctx || !s) return GEA_ERR_INVAL;
+    Scal h;
+    int rc = read_scal(ctx, &h);
+    if (rc) return rc;
+    memset(s, 0, sizeof(*s));
+    s->steps_done = h.steps_done;
+    s->jac_u = h.last_sweeps[0];
+    s->jac_h = h.last_sweeps[1];
+    for (int c = 0; c < 4; ++c) {
+        s->cg_iters[c] = h.last_cg_iters[c];
+        s->cg_relres[c] = h.last_cg_relres[c];
+    }
+    s->status = h.last_status;
+    s->mg_levels = (int)ctx->L.size();
+    s->launches = h.launches;
+    return GEA_OK;
+}
+
+int gea_get_field(gea_ctx *ctx, int32_t which, double *host)
+{
+    if (!ctx || !host) return GEA_ERR_INVAL;
+    const Geom &G = ctx->G;
+    const double *src = nullptr;
+    int cols = G.nx, rows = G.nz;
+    switch (which) {
+    case GEA_FIELD_RHO1: src = ctx->rho1; break;
+    case GEA_FIELD_U1: src = ctx->ua; break;
+    case GEA_FIELD_W1: src = ctx->wa; break;
+    case GEA_FIELD_H1: src = ctx->ha; break;
+    case GEA_FIELD_RHO2: src = ctx->rho2; break;
+    case GEA_FIELD_HX: src = ctx->Hx; break;
+    case GEA_FIELD_HZ: src = ctx->Hz; break;
+    case GEA_FIELD_B: src = ctx->b; break;
+    case GEA_FIELD_DX: src = ctx->Dx; cols = G.nx + 1; break;
+    case GEA_FIELD_DZ: src = ctx->Dz; rows = G.nz + 1; break;
+    default: return fail(ctx, GEA_ERR_INVAL, "unknown field %d", which);
+    }
+    int rc = copy_out(ctx, host, src, cols, rows);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return GEA_OK;
+}
+
+double gea_last_pressure_ms(gea_ctx *ctx)
+{
+    if (!ctx || !ctx->exec[0]) return -1.0;
+    double tot = 0.0;
+    for (int c = 0; c < ctx->C.n_corr; ++c) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ctx->ev[2 * c], ctx->ev[2 * c + 1]) != cudaSuccess) {
+            cudaGetLastError();
+            return -1.0;
+        }
+        tot += ms;
+    }
+    return tot;
+}
+
+int gea_profile_step(gea_ctx *ctx, gea_kernel_time *out, int32_t max_entries, int32_t *n_entries)
+{
+    if (!ctx || (!out && max_entries > 0) || !n_entries) return GEA_ERR_INVAL;
+    if (!ctx->have_state) return fail(ctx, GEA_ERR_STATE, "no state set");
+    Scal h;
+    int rc = read_scal(ctx, &h);
+    if (rc) return rc;
+    if (h.status) return fail(ctx, h.status, "device status %d", h.status);
+    const int from = current_slot(ctx, h);
+    EventTracer tr;
+    rc = record_step(ctx, from, ctx->stream, false, &tr);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(ctx->stream));
+    std::vector<gea_kernel_time> agg;
+    for (auto &r : tr.recs) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, r.e0, r.e1));
+        size_t j = 0;
+        for (; j < agg.size(); ++j)
+            if (!strcmp(agg[j].name, r.name)) break;
+        if (j == agg.size()) {
+            gea_kernel_time k;
+            memset(&k, 0, sizeof(k));
+            snprintf(k.name, sizeof(k.name), "%s", r.name);
+            agg.push_back(k);
+        }
+        agg[j].launches += 1;
+        agg[j].cells += r.cells;
+        agg[j].ms += ms;
+    }
+    *n_entries = (int32_t)agg.size();
+    for (size_t j = 0; j < agg.size() && (int32_t)j < max_entries; ++j) out[j] = agg[j];
+    ctx->steps_at_sync += 1;
+    return gea_sync(ctx);
+}
+
+const char *gea_last_error(const gea_ctx *ctx) { return ctx ? ctx->err : "null context"; }
+
+void gea_destroy(gea_ctx *ctx)
+{
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    for (int f = 0; f < 2; ++f) {
+        if (ctx->exec[f]) cudaGraphExecDestroy(ctx->exec[f]);
+        if (ctx->graph[f]) cudaGraphDestroy(ctx->graph[f]);
+    }
+    for (int e = 0; e < ctx->nev; ++e) cudaEventDestroy(ctx->ev[e]);
+    if (ctx->cap) cudaStreamDestroy(ctx->cap);
+    if (ctx->cap2) cudaStreamDestroy(ctx->cap2);
+    if (ctx->mem) cudaFree(ctx->mem);
+    delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,270 @@
+// gea_internal.cuh -- device-side data layout and stencil helpers of the GEA
+// time step (Girfoglio, Quaini & Rozza, arXiv 2303.10499, Section 3).
+//
+// Layout in HBM: every field is row-major with one row per grid row k and a
+// row pitch P (doubles) that is a multiple of 32 and >= nx+1, so rows start
+// on 256-byte boundaries. Cell fields use columns 0..nx-1 of rows 0..nz-1;
+// x-face arrays use columns 0..nx (face f between cells f-1 and f) of rows
+// 0..nz-1; z-face arrays use columns 0..nx-1 of rows 0..nz (face f between
+// rows f-1 and f). Wall faces are stored and hold zero.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gea {
+
+constexpr int BX = 32;          // threads per block along x (one warp per row)
+constexpr int BZ = 8;           // rows per block
+constexpr int NTHREADS = BX * BZ;
+
+enum Bc { BC_EVEN = 0, BC_U = 1, BC_W = 2, BC_H = 3 };
+
+struct Geom {
+    int nx, nz, P;              // cells in x and z, row pitch in doubles
+    double dx, dz, idx, idz, iV; // spacings, their inverses, 1/(dx dz)
+};
+
+struct Phys {
+    double R, cp, g, p0, mu, nuh, dt, idt;   // nuh = mu / Pr
+};
+
+// Persistent state of one time level (Section 3's solution tuple plus the
+// face mass fluxes phi and p^{n-1}).
+struct State {
+    double *rho, *u, *w, *T, *h, *p, *pp, *pold, *phix, *phiz;
+};
+
+// One multigrid level of the Helmholtz operator
+//   (A x)_i = c_i x_i + sum_f a_f (x_i - x_N).
+struct Level {
+    Geom G;
+    double *c, *ax, *az, *dinv;  // reaction term, x/z face coefficients, 1/diag
+    double *r, *e, *e2;          // residual, pre-smoothed correction, post-smoothed
+};
+
+// Loop bookkeeping slots.
+enum { LOOP_MOM = 0, LOOP_ENTH = 1, LOOP_CG = 2, NLOOPS = 3 };
+
+// Device-resident scalars of one context.
+struct Scal {
+    double bn2[3];              // ||b_u||^2, ||b_w||^2, ||b_h||^2
+    double b2, r2, rz, rz_old, pq, alpha, beta;
+    int done[NLOOPS];           // convergence flag of the running loop
+    int trips[NLOOPS];          // trips of the running loop
+    int sweeps[2];              // Jacobi sweeps of this step (momentum, enthalpy)
+    int cg_it;                  // CG iterations of the running solve
+    int corr;                   // running corrector
+    int cg_iters[4];
+    double cg_relres[4];
+    int status;                 // first device-side error of the running step
+    int bad_cells;              // set_state validation
+    long long steps_done;
+    // last completed step (copied by the end-of-step kernel)
+    int last_sweeps[2];
+    int last_cg_iters[4];
+    double last_cg_relres[4];
+    int last_status;
+    double mass, energy;        // diagnostics
+    long long launches;         // kernel launches of completed and running steps
+    unsigned counters[32];      // reduction arrival counters, one per kernel kind
+};
+
+// Optional per-launch hook (profiled eager steps only; never during graph
+// capture): begin/end bracket every kernel launch on stream st.
+struct Tracer {
+    virtual void begin(const char *name, long long cells, cudaStream_t st) = 0;
+    virtual void end(cudaStream_t st) = 0;
+    virtual ~Tracer() {}
+};
+
+enum {
+    CNT_PRED = 0, CNT_MOM = 1, CNT_ENTH_RHS = 2, CNT_ENTH = 3, CNT_HELM = 4,
+    CNT_RZ = 5, CNT_PQ = 6, CNT_UPD = 7, CNT_DIAG = 8
+};
+
+// Everything one time step's kernels need: the state read (S) and written
+// (N), per-step scratch and the device scalars.
+struct StepArgs {
+    Geom G;
+    Phys F;
+    State S, N;
+    double *rho1, *jd, *bu, *bw, *ua, *wa, *ub, *wb;   // Step 1
+    double *bh, *ha, *hb;                               // Step 2
+    double *rho2, *Dx, *Dz, *Hx, *Hz, *b;               // Step 3
+    double *p, *q;                                      // CG direction and A p
+    Scal *sc;
+    double *partials;
+    double jac_rtol2, cg_rtol2;
+};
+
+__device__ __forceinline__ int cidx(const Geom &G, int i, int k) { return k * G.P + i; }
+
+// Cell value at (i,k), i in [-1, nx] and k in [-1, nz]; outside the box the
+// one-layer ghost of the wall condition: wall-normal velocity odd (zero on
+// the wall), tangential velocity and scalars even (zero gradient), h with
+// dh/dz = -g on the bottom and top walls.
+template <int BC>
+__device__ __forceinline__ double ldc(const Geom &G, const Phys &F, const double *__restrict__ X,
+                                      int i, int k)
+{
+    if (i < 0) {
+        double v = X[k * G.P];
+        return BC == BC_U ? -v : v;
+    }
+    if (i >= G.nx) {
+        double v = X[k * G.P + G.nx - 1];
+        return BC == BC_U ? -v : v;
+    }
+    if (k < 0) {
+        double v = X[i];
+        if (BC == BC_W) return -v;
+        if (BC == BC_H) return v + F.g * G.dz;
+        return v;
+    }
+    if (k >= G.nz) {
+        double v = X[(G.nz - 1) * G.P + i];
+        if (BC == BC_W) return -v;
+        if (BC == BC_H) return v - F.g * G.dz;
+        return v;
+    }
+    return X[k * G.P + i];
+}
+
+// Fourth-order face value between cells a and b = a+1 from a-1, a, b, b+1
+// (the finite-volume reconstruction weights (-1, 7, 7, -1)/12).
+__device__ __forceinline__ double interp4(double xm, double xa, double xb, double xp)
+{
+    return (-xm + 7.0 * xa + 7.0 * xb - xp) * (1.0 / 12.0);
+}
+
+// Convective term (1/V) sum_j phi_j X_j of cell (i,k); wall faces carry no flux.
+template <int BC>
+__device__ __forceinline__ double convection(const Geom &G, const Phys &F,
+                                             const double *__restrict__ phix,
+                                             const double *__restrict__ phiz,
+                                             const double *__restrict__ X, int i, int k)
+{
+    double s = 0.0;
+    if (i + 1 < G.nx)
+        s += phix[k * G.P + i + 1] *
+             interp4(ldc<BC>(G, F, X, i - 1, k), ldc<BC>(G, F, X, i, k),
+                     ldc<BC>(G, F, X, i + 1, k), ldc<BC>(G, F, X, i + 2, k));
+    if (i > 0)
+        s -= phix[k * G.P + i] *
+             interp4(ldc<BC>(G, F, X, i - 2, k), ldc<BC>(G, F, X, i - 1, k),
+                     ldc<BC>(G, F, X, i, k), ldc<BC>(G, F, X, i + 1, k));
+    if (k + 1 < G.nz)
+        s += phiz[(k + 1) * G.P + i] *
+             interp4(ldc<BC>(G, F, X, i, k - 1), ldc<BC>(G, F, X, i, k),
+                     ldc<BC>(G, F, X, i, k + 1), ldc<BC>(G, F, X, i, k + 2));
+    if (k > 0)
+        s -= phiz[k * G.P + i] *
+             interp4(ldc<BC>(G, F, X, i, k - 2), ldc<BC>(G, F, X, i, k - 1),
+                     ldc<BC>(G, F, X, i, k), ldc<BC>(G, F, X, i, k + 1));
+    return s * G.iV;
+}
+
+// Diffusive face sum (1/V) sum_j (grad X)_j . A_j with compact face-normal
+// gradients; wall faces through the ghost layer.
+template <int BC>
+__device__ __forceinline__ double laplacian(const Geom &G, const Phys &F,
+                                            const double *__restrict__ X, int i, int k)
+{
+    double xc = X[k * G.P + i];
+    double sx = (ldc<BC>(G, F, X, i + 1, k) - xc) + (ldc<BC>(G, F, X, i - 1, k) - xc);
+    double sz = (ldc<BC>(G, F, X, i, k + 1) - xc) + (ldc<BC>(G, F, X, i, k - 1) - xc);
+    return sx * G.idx * G.idx + sz * G.idz * G.idz;
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Deterministic grid-wide sum of NV values per thread. Each block writes its
+// partial sums; the block that arrives last adds the partials in a fixed
+// order and returns true in its thread 0 with the totals in tot[]. Every
+// thread of every block must call it (no early return before it).
+template <int NV>
+__device__ bool grid_sum(const double (&v)[NV], double *partials, unsigned *counter,
+                         double (&tot)[NV])
+{
+    __shared__ double sh[NV][NTHREADS / 32];
+    __shared__ int am_last;
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int nthr = blockDim.x * blockDim.y;
+    const int lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
+    const int bid = blockIdx.x + blockIdx.y * gridDim.x;
+    const int nb = gridDim.x * gridDim.y;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        double s = warp_sum(v[j]);
+        if (lane == 0) sh[j][wid] = s;
+    }
+    __syncthreads();
+    if (tid == 0) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            double s = 0.0;
+            for (int q = 0; q < nw; ++q) s += sh[j][q];
+            partials[(size_t)j * nb + bid] = s;
+        }
+        __threadfence();
+        unsigned t = atomicAdd(counter, 1u);
+        am_last = (t == (unsigned)nb - 1u);
+    }
+    __syncthreads();
+    if (!am_last) return false;
+    __threadfence();
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        double s = 0.0;
+        for (int b = tid; b < nb; b += nthr) s += __ldcg(&partials[(size_t)j * nb + b]);
+        s = warp_sum(s);
+        __syncthreads();
+        if (lane == 0) sh[j][wid] = s;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int q = 0; q < nw; ++q) t += sh[j][q];
+            tot[j] = t;
+        }
+    }
+    if (tid == 0) *counter = 0u;
+    return tid == 0;
+}
+
+// ---- host-side launchers (gea_kernels.cu); tr may be null ----
+void launch_derive(const Geom &G, const Phys &F, const double *rho, const double *rhou,
+                   const double *rhow, const double *rhoe, const State &S, Scal *sc,
+                   cudaStream_t st);
+void launch_pred_setup(const StepArgs &a, cudaStream_t st, Tracer *tr);
+void launch_mom_jacobi(const StepArgs &a, const double *uin, const double *win, double *uout,
+                       double *wout, cudaStream_t st, Tracer *tr);
+void launch_enth_rhs(const StepArgs &a, cudaStream_t st, Tracer *tr);
+void launch_enth_jacobi(const StepArgs &a, const double *hin, double *hout, cudaStream_t st,
+                        Tracer *tr);
+void launch_eos_coef(const StepArgs &a, const Level &L0, cudaStream_t st, Tracer *tr);
+void launch_mg_coarsen(const Level &f, const Level &c, cudaStream_t st, Tracer *tr);
+void launch_H(const StepArgs &a, const double *U, const double *W, cudaStream_t st, Tracer *tr);
+void launch_helm_rhs(const StepArgs &a, const Level &L0, const double *xin, double *xout,
+                     int corr, cudaStream_t st, Tracer *tr);
+// returns the number of kernels launched
+int launch_vcycle(const StepArgs &a, Level *levels, int nlev, int ncoarse, double omega,
+                  cudaStream_t st, Tracer *tr);
+int launch_cg_iter_tail(const StepArgs &a, const Level &L0, double *x, cudaStream_t st,
+                        Tracer *tr);
+void launch_correct(const StepArgs &a, cudaStream_t st, Tracer *tr);
+// graph: set the WHILE condition through h; otherwise bookkeeping only
+void launch_loop_ctl(Scal *sc, cudaGraphConditionalHandle h, bool graph, int which,
+                     int maxtrips, int body_launches, cudaStream_t st, Tracer *tr);
+void launch_step_begin(Scal *sc, cudaStream_t st, Tracer *tr);
+void launch_step_end(Scal *sc, int fixed_launches, cudaStream_t st, Tracer *tr);
+void launch_diag(const Geom &G, const Phys &F, const State &S, const double *theta_bar,
+                 double *theta_out, Scal *sc, double *partials, cudaStream_t st);
+int max_blocks(const Geom &G);
+
+}  // namespace gea

@@ -1,0 +1,234 @@
+"""Thin ctypes binding of the CUDA library (include/gea.h).
+
+Argument marshalling only: every step of the time step runs in the
+library's kernels. There is no fallback: if the shared library is missing,
+or no CUDA device is present, the calls raise.
+
+Arrays are float64 with the layouts of include/gea.h: cell fields (nz, nx),
+phix (nz, nx+1), phiz (nz+1, nx). Host arrays are numpy arrays; device
+arrays may be torch CUDA tensors (their data pointers are passed through).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Dict, Optional
+
+import numpy as np
+
+from .build import LIB
+
+GEA_OK, GEA_ERR_INVAL, GEA_ERR_NOMEM, GEA_ERR_CUDA, GEA_ERR_NOCONV, GEA_ERR_NONFINITE, \
+    GEA_ERR_STATE = range(7)
+STATE_CONSERVATIVE, STATE_FULL = 0, 1
+MEM_HOST, MEM_DEVICE = 0, 1
+FIELDS = {"rho1": 0, "u1": 1, "w1": 2, "h1": 3, "rho2": 4, "Hx": 5, "Hz": 6, "b": 7,
+          "Dx": 8, "Dz": 9}
+FULL_FIELDS = ("rho", "u", "w", "T", "h", "p", "pp", "pold", "phix", "phiz")
+
+
+class GeaError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"gea error {code}: {msg}")
+        self.code = code
+
+
+class _Grid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("nz", C.c_int32), ("lx", C.c_double), ("lz", C.c_double)]
+
+
+class _Const(C.Structure):
+    _fields_ = [("R", C.c_double), ("cp", C.c_double), ("g", C.c_double), ("p0", C.c_double),
+                ("mu", C.c_double), ("Pr", C.c_double), ("dt", C.c_double),
+                ("n_corr", C.c_int32), ("jac_rtol", C.c_double), ("jac_maxit", C.c_int32),
+                ("cg_rtol", C.c_double), ("cg_maxit", C.c_int32),
+                ("mg_min_cells", C.c_int32), ("flags", C.c_int32)]
+
+
+class _View(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("mem", C.c_int32)] + [
+        (n, C.c_void_p) for n in ("rho", "rhou", "rhow", "rhoe", "u", "w", "T", "h", "p", "pp",
+                                  "pold", "phix", "phiz")]
+
+
+class _Stats(C.Structure):
+    _fields_ = [("steps_done", C.c_int64), ("jac_u", C.c_int32), ("jac_h", C.c_int32),
+                ("cg_iters", C.c_int32 * 4), ("cg_relres", C.c_double * 4),
+                ("status", C.c_int32), ("mg_levels", C.c_int32), ("launches", C.c_int64)]
+
+
+class _KTime(C.Structure):
+    _fields_ = [("name", C.c_char * 40), ("launches", C.c_int32), ("cells", C.c_int64),
+                ("ms", C.c_double)]
+
+
+_lib = None
+
+
+def library() -> C.CDLL:
+    """Load libgea.so (built by paper_2303_10499_gb300.build.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"CUDA library {LIB} is not built; call "
+                               "paper_2303_10499_gb300.build.build() first")
+        lib = C.CDLL(LIB)
+        P = C.c_void_p
+        lib.gea_create.argtypes = [C.POINTER(_Grid), C.POINTER(_Const), C.POINTER(P)]
+        lib.gea_set_stream.argtypes = [P, P]
+        lib.gea_set_state.argtypes = [P, C.POINTER(_View)]
+        lib.gea_step.argtypes = [P, C.c_int32]
+        lib.gea_step_async.argtypes = [P, C.c_int32]
+        lib.gea_sync.argtypes = [P]
+        lib.gea_get_state.argtypes = [P, C.POINTER(_View)]
+        lib.gea_get_diag.argtypes = [P, P, P, P, P]
+        lib.gea_get_stats.argtypes = [P, C.POINTER(_Stats)]
+        lib.gea_get_field.argtypes = [P, C.c_int32, P]
+        lib.gea_last_pressure_ms.argtypes = [P]
+        lib.gea_last_pressure_ms.restype = C.c_double
+        lib.gea_profile_step.argtypes = [P, C.POINTER(_KTime), C.c_int32, C.POINTER(C.c_int32)]
+        lib.gea_last_error.argtypes = [P]
+        lib.gea_last_error.restype = C.c_char_p
+        lib.gea_destroy.argtypes = [P]
+        lib.gea_destroy.restype = None
+        _lib = lib
+    return _lib
+
+
+def _addr(a) -> int:
+    """Data pointer of a float64 numpy array or torch tensor (contiguous)."""
+    if isinstance(a, np.ndarray):
+        assert a.dtype == np.float64 and a.flags.c_contiguous, "need C-contiguous float64"
+        return a.ctypes.data
+    assert a.dtype.__str__() == "torch.float64" and a.is_contiguous(), "need contiguous float64"
+    return a.data_ptr()
+
+
+def _is_device(a) -> bool:
+    return not isinstance(a, np.ndarray) and getattr(a, "is_cuda", False)
+
+
+class Solver:
+    """One context of the library: a grid, its constants and device state."""
+
+    def __init__(self, grid, const, mg_min_cells: int = 0, stream=None):
+        self.lib = library()
+        self.grid, self.const = grid, const
+        g = _Grid(grid.nx, grid.nz, grid.lx, grid.lz)
+        c = _Const(const.R, const.cp, const.g, const.p0, const.mu, const.Pr, const.dt,
+                   const.n_corr, const.jac_rtol, const.jac_maxit, const.cg_rtol, const.cg_maxit,
+                   mg_min_cells, 0)
+        h = C.c_void_p()
+        rc = self.lib.gea_create(C.byref(g), C.byref(c), C.byref(h))
+        if rc != GEA_OK:
+            raise GeaError(rc, "gea_create failed")
+        self.h = h
+        if stream is not None:
+            self.set_stream(stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gea_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc: int):
+        if rc != GEA_OK:
+            msg = self.lib.gea_last_error(self.h)
+            raise GeaError(rc, msg.decode() if msg else "")
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, a raw cudaStream_t integer or None."""
+        s = getattr(stream, "cuda_stream", stream)
+        self._check(self.lib.gea_set_stream(self.h, C.c_void_p(s or 0)))
+
+    # -- state -------------------------------------------------------------
+    def set_conservative(self, fields: Dict):
+        v = _View()
+        v.kind = STATE_CONSERVATIVE
+        v.mem = MEM_DEVICE if _is_device(fields["rho"]) else MEM_HOST
+        for k in ("rho", "rhou", "rhow", "rhoe"):
+            setattr(v, k, _addr(fields[k]))
+        self._check(self.lib.gea_set_state(self.h, C.byref(v)))
+
+    def set_full(self, state: Dict):
+        v = _View()
+        v.kind = STATE_FULL
+        v.mem = MEM_DEVICE if _is_device(state["rho"]) else MEM_HOST
+        for k in FULL_FIELDS:
+            setattr(v, k, _addr(state[k]))
+        self._check(self.lib.gea_set_state(self.h, C.byref(v)))
+
+    def get_full(self, out: Optional[Dict] = None) -> Dict[str, np.ndarray]:
+        nx, nz = self.grid.nx, self.grid.nz
+        if out is None:
+            out = {k: np.empty((nz, nx)) for k in FULL_FIELDS}
+            out["phix"] = np.empty((nz, nx + 1))
+            out["phiz"] = np.empty((nz + 1, nx))
+        v = _View()
+        v.kind = STATE_FULL
+        v.mem = MEM_DEVICE if _is_device(out["rho"]) else MEM_HOST
+        for k in FULL_FIELDS:
+            setattr(v, k, _addr(out[k]))
+        self._check(self.lib.gea_get_state(self.h, C.byref(v)))
+        return out
+
+    def get_conservative(self) -> Dict[str, np.ndarray]:
+        s = self.get_full()
+        z = (np.arange(self.grid.nz) + 0.5)[:, None] * self.grid.dz
+        cv = self.const.cp - self.const.R
+        rho, u, w, T = s["rho"], s["u"], s["w"], s["T"]
+        return {"rho": rho, "rhou": rho * u, "rhow": rho * w,
+                "rhoe": rho * (cv * T + 0.5 * (u * u + w * w) + self.const.g * z)}
+
+    # -- stepping ----------------------------------------------------------
+    def step(self, n: int = 1):
+        self._check(self.lib.gea_step(self.h, int(n)))
+
+    def step_async(self, n: int = 1):
+        self._check(self.lib.gea_step_async(self.h, int(n)))
+
+    def sync(self):
+        self._check(self.lib.gea_sync(self.h))
+
+    # -- diagnostics -------------------------------------------------------
+    def diagnostics(self, theta_bar: np.ndarray):
+        tb = np.ascontiguousarray(theta_bar, dtype=np.float64)
+        th = np.empty((self.grid.nz, self.grid.nx))
+        m = C.c_double()
+        e = C.c_double()
+        self._check(self.lib.gea_get_diag(self.h, tb.ctypes.data, th.ctypes.data,
+                                          C.addressof(m), C.addressof(e)))
+        return th, m.value, e.value
+
+    def stats(self) -> Dict:
+        s = _Stats()
+        self._check(self.lib.gea_get_stats(self.h, C.byref(s)))
+        n = self.const.n_corr
+        return {"steps_done": s.steps_done, "jac_u": s.jac_u, "jac_h": s.jac_h,
+                "cg_iters": list(s.cg_iters)[:n], "cg_relres": list(s.cg_relres)[:n],
+                "status": s.status, "mg_levels": s.mg_levels, "launches": s.launches}
+
+    def field(self, name: str) -> np.ndarray:
+        nx, nz = self.grid.nx, self.grid.nz
+        shape = {"Dx": (nz, nx + 1), "Dz": (nz + 1, nx)}.get(name, (nz, nx))
+        out = np.empty(shape)
+        self._check(self.lib.gea_get_field(self.h, FIELDS[name], out.ctypes.data))
+        return out
+
+    def pressure_ms(self) -> float:
+        return float(self.lib.gea_last_pressure_ms(self.h))
+
+    def profile_step(self) -> Dict[str, Dict]:
+        """Advance one step with every kernel launch timed by CUDA events on
+        the context's stream; returns {kernel: {launches, cells, ms}}."""
+        buf = (_KTime * 64)()
+        n = C.c_int32()
+        self._check(self.lib.gea_profile_step(self.h, buf, 64, C.byref(n)))
+        return {buf[i].name.decode(): {"launches": buf[i].launches, "cells": buf[i].cells,
+                                       "ms": buf[i].ms} for i in range(min(n.value, 64))}

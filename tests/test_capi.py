@@ -1,0 +1,63 @@
+"""The C-ABI library builds for sm_103a and exports every entry point that
+include/gea.h declares (no GPU needed: nothing is called)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "gea.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gea_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for s in ("gea_create", "gea_set_state", "gea_step", "gea_get_state", "gea_destroy"):
+        assert s in syms
+
+
+def test_library_builds_and_exports_every_symbol():
+    from paper_2303_10499_gb300 import build as B
+    path = B.build()
+    lib = ctypes.CDLL(path)
+    missing = [s for s in declared_symbols() if not hasattr(lib, s)]
+    assert not missing, missing
+
+
+def test_binding_struct_sizes_match_header():
+    """The ctypes structs mirror the C structs (checked with the host C
+    compiler against include/gea.h)."""
+    import subprocess
+    import tempfile
+    from paper_2303_10499_gb300 import gea
+    code = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "gea.h"
+int main(void){printf("%zu %zu %zu %zu\n", sizeof(gea_grid), sizeof(gea_constants),
+ sizeof(gea_state_view), sizeof(gea_stats)); return 0;}
+'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "s.c")
+        open(c, "w").write(code)
+        exe = os.path.join(d, "s")
+        subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
+        sizes = [int(x) for x in subprocess.check_output([exe]).split()]
+    assert sizes == [ctypes.sizeof(gea._Grid), ctypes.sizeof(gea._Const),
+                     ctypes.sizeof(gea._View), ctypes.sizeof(gea._Stats)]
+
+
+def test_binding_fails_loudly_without_a_gpu():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    from paper_2303_10499_gb300 import gea
+    from paper_2303_10499_gb300 import workloads as W
+    wl = W.get("bubble160x80")
+    with pytest.raises(gea.GeaError):
+        gea.Solver(wl.grid, wl.const)

@@ -1,0 +1,233 @@
+"""Parity of the CUDA library (through its C ABI) with the FP64 CPU oracle.
+
+Tolerances. Every solve is driven to round-off, so the two sides differ by
+rounding order only. The velocity fields carry round-off noise of the
+near-hydrostatic state (p' ~ 1e5 Pa resolved to ~1e-11 Pa), measured on the
+oracle by perturbing the initial density by one ulp: relative L2 changes of
+6e-12 (160x80) and 1.1e-11 (640x320) in rho u after 100 steps. The bar is
+1e-10 relative L2 per field after 100 steps. In short runs the horizontal
+velocity is still tiny (1e-4 m/s after three steps) and its round-off noise
+is ~1e-10 of itself, so there velocity components, momenta and face fluxes
+are measured against the norm of their vector; stage fields after one step
+are compared element by element against the largest value of the field or
+of its vector.
+"""
+import numpy as np
+import pytest
+
+from paper_2303_10499_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gea():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required")
+    from paper_2303_10499_gb300 import build as B
+    B.build()
+    from paper_2303_10499_gb300 import gea as G
+    return G
+
+
+def rel_l2(a, b):
+    n = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (n if n > 0 else 1.0)
+
+
+def run_both(gea, oracle_mod, wl, steps, **solver_kw):
+    o = oracle_mod.Oracle(wl.grid, wl.const)
+    so = o.derive(wl.fields)
+    o.step(so, steps)
+    s = gea.Solver(wl.grid, wl.const, **solver_kw)
+    s.set_conservative(wl.fields)
+    s.step(steps)
+    return so, s
+
+
+def compare_state(gea_state, so, tol, const, grid, fields=None, vector_norm=False):
+    """Relative L2 error per field. vector_norm: velocity components,
+    momenta and face fluxes are measured against the norm of their vector
+    (for short runs in which one component is still at round-off level)."""
+    out = {}
+    cv = const.cp - const.R
+    co = so.conservative(const.g, cv, grid.dz)
+    z = (np.arange(grid.nz) + 0.5)[:, None] * grid.dz
+    gs = gea_state
+    cg = {"rho": gs["rho"], "rhou": gs["rho"] * gs["u"], "rhow": gs["rho"] * gs["w"],
+          "rhoe": gs["rho"] * (cv * gs["T"] + 0.5 * (gs["u"] ** 2 + gs["w"] ** 2) + const.g * z)}
+    vec = {}
+    if vector_norm:
+        m = np.hypot(np.linalg.norm(co["rhou"]), np.linalg.norm(co["rhow"]))
+        f = np.hypot(np.linalg.norm(so["phix"]), np.linalg.norm(so["phiz"]))
+        vec = {"rhou": m, "rhow": m, "phix": f, "phiz": f}
+    for k in ("rho", "rhou", "rhow", "rhoe"):
+        out[k] = np.linalg.norm(cg[k] - co[k]) / vec[k] if k in vec else rel_l2(cg[k], co[k])
+    for k in fields or ("T", "h", "p", "pp", "pold", "phix", "phiz"):
+        out[k] = np.linalg.norm(gs[k] - so[k]) / vec[k] if k in vec else rel_l2(gs[k], so[k])
+    bad = {k: v for k, v in out.items() if not v <= tol}
+    assert not bad, (bad, out)
+    return out
+
+
+def test_stage_parity_one_step(gea, oracle_mod):
+    wl = W.get("bubble160x80")
+    wl.const.n_corr = 1
+    o = oracle_mod.Oracle(wl.grid, wl.const)
+    so = o.derive(wl.fields)
+    st_o, d = o.step(so, 1, dump=True)
+    s = gea.Solver(wl.grid, wl.const)
+    s.set_conservative(wl.fields)
+    s.step(1)
+    # element-wise, relative to the field's (or its vector's) largest value
+    scale = {"u1": "w1", "Hx": "Hz"}
+    for name, tol in (("rho1", 1e-14), ("u1", 1e-11), ("w1", 1e-11), ("h1", 1e-14),
+                      ("rho2", 1e-14), ("Dx", 1e-13), ("Dz", 1e-13), ("Hx", 1e-11),
+                      ("Hz", 1e-11), ("b", 1e-14)):
+        g = s.field(name)
+        ref = d[name]
+        sc = max(np.abs(ref).max(), np.abs(d[scale.get(name, name)]).max(), 1e-300)
+        err = np.abs(g - ref).max() / sc
+        assert err <= tol, (name, err)
+    compare_state(s.get_full(), so, 1e-11, wl.const, wl.grid, vector_norm=True)
+    st = s.stats()
+    assert st["status"] == 0 and st["steps_done"] == 1
+    assert st["cg_relres"][0] <= wl.const.cg_rtol
+
+
+@pytest.mark.parametrize("name", ["bubble160x80", "bubble640x320"])
+def test_parity_100_steps(gea, oracle_mod, name):
+    wl = W.get(name)
+    so, s = run_both(gea, oracle_mod, wl, 100)
+    errs = compare_state(s.get_full(), so, 1e-10, wl.const, wl.grid)
+    th_g, m_g, e_g = s.diagnostics(wl.theta_bar)
+    th_o, m_o, e_o = oracle_mod.Oracle(wl.grid, wl.const).diagnostics(so, wl.theta_bar)
+    assert np.abs(th_g - th_o).max() < 1e-9
+    assert abs(m_g - m_o) / m_o < 1e-13 and abs(e_g - e_o) / e_o < 1e-13
+    print(name, errs, s.stats())
+
+
+@pytest.mark.parametrize("nx,nz,ncorr", [(37, 23, 2), (50, 34, 2), (4, 4, 1), (66, 130, 3),
+                                          (128, 96, 2)])
+def test_parity_ragged_sizes(gea, oracle_mod, nx, nz, ncorr):
+    """Sizes that are not multiples of the 32 x 8 tile, odd sizes (a
+    single multigrid level), the smallest grid, and several corrector
+    counts, on a moving stratified state."""
+    grid = W.Grid(nx, nz, 40.0 * nx, 30.0 * nz)
+    c = W.Constants(dt=0.2, n_corr=ncorr, mu=1.5)
+    wl = W.random_flow(grid, c, seed=nx * 1000 + nz, uamp=3.0, thamp=2.0)
+    so, s = run_both(gea, oracle_mod, wl, 20)
+    compare_state(s.get_full(), so, 1e-10, c, grid)
+
+
+@pytest.mark.parametrize("kw", [dict(g=0.0), dict(mu=0.0), dict(Pr=0.7, mu=3.0)])
+def test_parity_constants(gea, oracle_mod, kw):
+    grid = W.Grid(48, 40, 2400.0, 2000.0)
+    c = W.Constants(dt=0.1, **kw)
+    wl = W.random_flow(grid, c, seed=11, uamp=2.0)
+    so, s = run_both(gea, oracle_mod, wl, 20)
+    compare_state(s.get_full(), so, 1e-10, c, grid)
+
+
+def test_rest_atmosphere_on_gpu(gea):
+    wl = W.rest_atmosphere(W.Grid(160, 80, 20000.0, 10000.0), W.Constants(dt=0.1))
+    s = gea.Solver(wl.grid, wl.const)
+    s.set_conservative(wl.fields)
+    s.step(100)
+    st = s.get_full()
+    assert np.abs(st["u"]).max() < 1e-10 and np.abs(st["w"]).max() < 1e-10
+    th, _, _ = s.diagnostics(wl.theta_bar)
+    assert np.abs(th).max() < 1e-10
+
+
+def test_checkpoint_roundtrip_bitwise(gea):
+    """FULL get + set continues bit for bit."""
+    wl = W.get("bubble160x80")
+    a = gea.Solver(wl.grid, wl.const)
+    a.set_conservative(wl.fields)
+    a.step(7)
+    ck = a.get_full()
+    a.step(5)
+    ref = a.get_full()
+    b = gea.Solver(wl.grid, wl.const)
+    b.set_full(ck)
+    b.step(5)
+    got = b.get_full()
+    for k in ref:
+        assert np.array_equal(got[k], ref[k]), k
+
+
+def test_deterministic(gea):
+    wl = W.get("bubble160x80")
+    out = []
+    for _ in range(2):
+        s = gea.Solver(wl.grid, wl.const)
+        s.set_conservative(wl.fields)
+        s.step(10)
+        out.append(s.get_full())
+    for k in out[0]:
+        assert np.array_equal(out[0][k], out[1][k]), k
+
+
+def test_noconv_keeps_last_state(gea):
+    """A pressure solve that hits its iteration cap reports GEA_ERR_NOCONV
+    and leaves the last completed state in place."""
+    wl = W.get("bubble160x80")
+    wl.const.cg_maxit = 1
+    s = gea.Solver(wl.grid, wl.const)
+    s.set_conservative(wl.fields)
+    before = s.get_full()
+    with pytest.raises(gea.GeaError) as ei:
+        s.step(3)
+    assert ei.value.code == gea.GEA_ERR_NOCONV
+    after = s.get_full()
+    for k in before:
+        assert np.array_equal(before[k], after[k]), k
+
+
+def test_set_state_rejects_bad_input(gea):
+    wl = W.get("bubble160x80")
+    s = gea.Solver(wl.grid, wl.const)
+    f = {k: v.copy() for k, v in wl.fields.items()}
+    f["rho"][3, 4] = -1.0
+    with pytest.raises(gea.GeaError) as ei:
+        s.set_conservative(f)
+    assert ei.value.code == gea.GEA_ERR_INVAL
+    with pytest.raises(gea.GeaError):
+        s.step(1)
+
+
+def test_device_tensors_in_and_out(gea):
+    import torch
+    wl = W.get("bubble160x80")
+    dev = {k: torch.from_numpy(v).cuda() for k, v in wl.fields.items()}
+    s = gea.Solver(wl.grid, wl.const, stream=torch.cuda.current_stream())
+    s.set_conservative(dev)
+    s.step(2)
+    host = s.get_full()
+    nx, nz = wl.grid.nx, wl.grid.nz
+    out = {k: torch.empty((nz, nx), dtype=torch.float64, device="cuda") for k in host}
+    out["phix"] = torch.empty((nz, nx + 1), dtype=torch.float64, device="cuda")
+    out["phiz"] = torch.empty((nz + 1, nx), dtype=torch.float64, device="cuda")
+    s.get_full(out)
+    torch.cuda.synchronize()
+    for k in host:
+        assert np.array_equal(out[k].cpu().numpy(), host[k]), k
+
+
+def test_full_size_one_step(gea, oracle_mod):
+    """4096 x 2048 (larger than L2 at FP64): one step against the oracle,
+    plus mass conservation and mirror symmetry of the GPU state."""
+    wl = W.get("bubble4096x2048")
+    so, s = run_both(gea, oracle_mod, wl, 1)
+    g = s.get_full()
+    compare_state(g, so, 1e-10, wl.const, wl.grid, vector_norm=True)
+    _, m1, _ = s.diagnostics(wl.theta_bar)
+    s2 = gea.Solver(wl.grid, wl.const)
+    s2.set_conservative(wl.fields)
+    _, m0, _ = s2.diagnostics(wl.theta_bar)
+    assert abs(m1 - m0) / m0 < 1e-13
+    u, w = g["u"], g["w"]
+    assert np.abs(u + u[:, ::-1]).max() <= 1e-9 * np.abs(u).max()
+    assert np.abs(w - w[:, ::-1]).max() <= 1e-9 * np.abs(w).max()
