@@ -36,22 +36,21 @@ UNIT = "cell-steps/s"
 # an FMA counts 2). Coarse-level multigrid kernels are per cell of the level
 # they run on. Derivations are in the design notes.
 KERNEL_MODEL = {
-    "pred_setup": (12, 46),
-    "mom_jacobi": (10, 112),
-    "enth_rhs": (13, 84),
-    "enth_jacobi": (7, 56),
-    "eos_coef": (14, 52),
-    "mg_coarsen": (4, 3),
-    "H": (9, 112),
-    "helm_rhs": (15, 68),
-    "mg_down": (6.25, 17),
-    "mg_coarse": (7, 13),
-    "mg_up": (7.25, 24),
-    "mg_single": (6, 24),
-    "cg_p": (3, 2),
-    "cg_spmv": (5, 12),
+    "pred_setup": (22, 66),
+    "mom_jacobi": (16, 44),
+    "enth_rhs": (13, 41),
+    "enth_jacobi": (13, 22),
+    "eos_coef": (16, 33),
+    "mg_coarsen": (17, 18),
+    "H": (17, 44),
+    "helm_rhs": (15, 51),
+    "mg_down": (5.25, 11.5),
+    "mg_coarse": (7, 6.5),
+    "mg_up": (7.25, 15),
+    "mg_single": (6, 15),
+    "cg_pspmv": (7, 13.5),
     "cg_update": (6, 6),
-    "correct": (16, 66),
+    "correct": (16, 38),
 }
 
 

@@ -76,9 +76,12 @@ typedef struct gea_grid {
  *            ||r||_2 <= jac_rtol ||b||_2.
  *  cg_rtol, cg_maxit     conjugate gradients for the pressure equation:
  *            stops when ||r||_2 <= cg_rtol ||b||_2 (recursive residual).
- *  mg_min_cells  the multigrid preconditioner coarsens (by 2 in x and z,
- *            while both sizes are even) until a level has at most this many
- *            cells; 0 selects the default (4096). 1 disables coarsening.
+ *  mg_min_cells  the multigrid preconditioner coarsens by 2 in x and z
+ *            while both sizes are even and >= 8. 0 (default): until the
+ *            estimated Laplacian-to-diagonal ratio of the pressure operator,
+ *            2 dt^2 R T (1/dx^2 + 1/dz^2) at T = 300 K, is below 0.3 (the
+ *            coarse levels are then nearly diagonal). > 0: until a level has
+ *            at most this many cells (a value >= nx*nz gives one level).
  *  flags     reserved, pass 0. */
 typedef struct gea_constants {
     double R, cp, g, p0, mu, Pr, dt;

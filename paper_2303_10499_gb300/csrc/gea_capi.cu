@@ -31,8 +31,9 @@ struct gea_ctx {
     char *mem = nullptr;
     size_t mem_bytes = 0;
     State S[2];
-    double *rho1, *jd, *bu, *bw, *ua, *wa, *ub, *wb, *bh, *ha, *hb, *rho2, *Dx, *Dz, *Hx, *Hz,
-        *b, *p, *q;
+    Stencil9 T;
+    double *rho1, *dinvu, *dinvh, *bu, *bw, *ua, *wa, *ub, *wb, *bh, *ha, *hb, *rho2, *psi, *Dx,
+        *Dz, *Hx, *Hz, *b, *p0, *p1, *q;
     double *stage;                         // staging for conservative set/get (4 fields)
     double *thbar;                         // nz values
     double *thout;                         // theta' output
@@ -96,11 +97,12 @@ StepArgs step_args(gea_ctx *c, int from)
     a.F = c->F;
     a.S = c->S[from];
     a.N = c->S[from ^ 1];
-    a.rho1 = c->rho1; a.jd = c->jd; a.bu = c->bu; a.bw = c->bw;
+    a.T = c->T;
+    a.rho1 = c->rho1; a.dinvu = c->dinvu; a.dinvh = c->dinvh; a.bu = c->bu; a.bw = c->bw;
     a.ua = c->ua; a.wa = c->wa; a.ub = c->ub; a.wb = c->wb;
     a.bh = c->bh; a.ha = c->ha; a.hb = c->hb;
-    a.rho2 = c->rho2; a.Dx = c->Dx; a.Dz = c->Dz; a.Hx = c->Hx; a.Hz = c->Hz; a.b = c->b;
-    a.p = c->p; a.q = c->q;
+    a.rho2 = c->rho2; a.psi = c->psi; a.Dx = c->Dx; a.Dz = c->Dz; a.Hx = c->Hx; a.Hz = c->Hz;
+    a.b = c->b; a.p0 = c->p0; a.p1 = c->p1; a.q = c->q;
     a.sc = c->sc;
     a.partials = c->partials;
     a.jac_rtol2 = c->C.jac_rtol * c->C.jac_rtol;
@@ -108,8 +110,14 @@ StepArgs step_args(gea_ctx *c, int from)
     return a;
 }
 
-constexpr int kCoarseSweeps = 4;
-constexpr double kOmega = 0.8;
+constexpr int kCoarseSweeps = 2;   // damped Jacobi sweeps on the coarsest level (even)
+constexpr double kOmega = 0.8;     // smoother weight
+// The multigrid hierarchy stops once the Laplacian part of the Helmholtz
+// operator is small against its diagonal psi/dt: with D ~ dt and psi ~ 1/(RT),
+// sum_f a_f / c ~ 2 dt^2 R T (1/dx^2 + 1/dz^2), and every coarsening divides
+// it by 4. Coarsening continues while the ratio exceeds this bound.
+constexpr double kCoarsestRatio = 0.3;
+constexpr double kRefT = 300.0;    // reference temperature of that estimate (K)
 
 // Append a WHILE conditional node to the graph being captured on `s`; its
 // body is captured from body(body_stream, handle, true).
@@ -191,22 +199,26 @@ int record_step(gea_ctx *ctx, int from, cudaStream_t s, bool graph, Tracer *tr)
     });
     if (rc) return rc;
     launch_eos_coef(a, L[0], s, tr); ++fixed;
-    for (int l = 0; l + 1 < nlev; ++l) { launch_mg_coarsen(L[l], L[l + 1], s, tr); ++fixed; }
+    for (int l = 0; l + 1 < nlev; ++l) { launch_mg_coarsen(L[l], L[l + 1], kOmega, s, tr); ++fixed; }
     // Step 3: PISO correctors
-    const int body_cg = (nlev == 1 ? 1 : 2 * (nlev - 1) + kCoarseSweeps) + 3 + 1;
+    const int body_cg = (nlev == 1 ? 1 : 2 * (nlev - 1) + kCoarseSweeps) + 2 + 1;
     for (int c = 0; c < ctx->C.n_corr; ++c) {
         const double *U = c == 0 ? a.ua : a.N.u;
         const double *W = c == 0 ? a.wa : a.N.w;
         launch_H(a, U, W, s, tr); ++fixed;
-        CK(cudaEventRecord(ctx->ev[2 * c], s));
+        // inside a capture an event record becomes a timing node only when
+        // recorded as external
+        CK(graph ? cudaEventRecordWithFlags(ctx->ev[2 * c], s, cudaEventRecordExternal)
+                 : cudaEventRecord(ctx->ev[2 * c], s));
         launch_helm_rhs(a, L[0], c == 0 ? a.S.pp : a.N.pp, a.N.pp, c, s, tr); ++fixed;
         rc = loop(LOOP_CG, ctx->C.cg_maxit, [&](cudaStream_t bs, cudaGraphConditionalHandle h, bool g) {
-            launch_vcycle(a, L, nlev, kCoarseSweeps, kOmega, bs, tr);
+            launch_vcycle(a, L, nlev, kCoarseSweeps, bs, tr);
             launch_cg_iter_tail(a, L[0], a.N.pp, bs, tr);
             launch_loop_ctl(a.sc, h, g, LOOP_CG, ctx->C.cg_maxit, body_cg, bs, tr);
         });
         if (rc) return rc;
-        CK(cudaEventRecord(ctx->ev[2 * c + 1], s));
+        CK(graph ? cudaEventRecordWithFlags(ctx->ev[2 * c + 1], s, cudaEventRecordExternal)
+                 : cudaEventRecord(ctx->ev[2 * c + 1], s));
         launch_correct(a, s, tr); ++fixed;
     }
     ++fixed;
@@ -311,24 +323,28 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
 
     ctx = new gea_ctx();
     ctx->C = *c;
-    if (ctx->C.mg_min_cells == 0) ctx->C.mg_min_cells = 4096;
     ctx->G = make_geom(grid->nx, grid->nz, grid->lx, grid->lz);
     ctx->F.R = c->R; ctx->F.cp = c->cp; ctx->F.g = c->g; ctx->F.p0 = c->p0;
     ctx->F.mu = c->mu; ctx->F.nuh = c->mu / c->Pr; ctx->F.dt = c->dt; ctx->F.idt = 1.0 / c->dt;
+    ctx->F.omega = kOmega;
     if (cudaGetDevice(&ctx->device) != cudaSuccess) {
         delete ctx;
         return GEA_ERR_CUDA;
     }
 
-    // multigrid levels: halve while both sizes are even and the level is
-    // larger than mg_min_cells
+    // multigrid levels: halve while both sizes are even, the level is larger
+    // than mg_min_cells (if given) and the estimated Laplacian-to-diagonal
+    // ratio of the Helmholtz operator exceeds kCoarsestRatio
     std::vector<Geom> lg;
     lg.push_back(ctx->G);
+    double ratio = 2.0 * c->dt * c->dt * c->R * kRefT * (ctx->G.idx * ctx->G.idx + ctx->G.idz * ctx->G.idz);
     while (true) {
         const Geom &f = lg.back();
         if (f.nx % 2 || f.nz % 2 || f.nx < 8 || f.nz < 8) break;
-        if ((long long)f.nx * f.nz <= ctx->C.mg_min_cells) break;
+        if (c->mg_min_cells > 0 && (long long)f.nx * f.nz <= c->mg_min_cells) break;
+        if (c->mg_min_cells == 0 && ratio <= kCoarsestRatio) break;
         lg.push_back(make_geom(f.nx / 2, f.nz / 2, f.nx * f.dx, f.nz * f.dz));
+        ratio *= 0.25;
     }
 
     // one allocation for everything
@@ -336,10 +352,10 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
     const size_t cell = arr_bytes(G, G.nz), fz = arr_bytes(G, G.nz + 1);
     size_t total = 0;
     total += 2 * (9 * cell + fz);                  // two states (phiz has nz+1 rows)
-    total += 19 * cell + 2 * fz;                   // scratch (Dz has nz+1 rows) + stage
+    total += 33 * cell + 2 * fz;                   // scratch (Dz has nz+1 rows)
     total += 4 * cell;                             // staging for conservative fields
     total += 2 * cell + round_up(G.nz * sizeof(double), 256);   // theta_bar, theta'
-    for (const Geom &g : lg) total += 6 * arr_bytes(g, g.nz) + arr_bytes(g, g.nz + 1);
+    for (const Geom &g : lg) total += 7 * arr_bytes(g, g.nz) + arr_bytes(g, g.nz + 1);
     const size_t nb = (size_t)max_blocks(G);
     total += round_up(4 * nb * sizeof(double), 256);
     total += round_up(sizeof(Scal), 256);
@@ -357,11 +373,16 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
         S.rho = take(cell); S.u = take(cell); S.w = take(cell); S.T = take(cell); S.h = take(cell);
         S.p = take(cell); S.pp = take(cell); S.pold = take(cell); S.phix = take(cell); S.phiz = take(fz);
     }
-    ctx->rho1 = take(cell); ctx->jd = take(cell); ctx->bu = take(cell); ctx->bw = take(cell);
+    Stencil9 &T = ctx->T;
+    T.cC = take(cell); T.cE1 = take(cell); T.cE2 = take(cell); T.cW1 = take(cell); T.cW2 = take(cell);
+    T.cN1 = take(cell); T.cN2 = take(cell); T.cS1 = take(cell); T.cS2 = take(cell);
+    ctx->rho1 = take(cell); ctx->dinvu = take(cell); ctx->dinvh = take(cell);
+    ctx->bu = take(cell); ctx->bw = take(cell);
     ctx->ua = take(cell); ctx->wa = take(cell); ctx->ub = take(cell); ctx->wb = take(cell);
     ctx->bh = take(cell); ctx->ha = take(cell); ctx->hb = take(cell); ctx->rho2 = take(cell);
-    ctx->Dx = take(cell); ctx->Dz = take(fz); ctx->Hx = take(cell); ctx->Hz = take(cell);
-    ctx->b = take(cell); ctx->p = take(cell); ctx->q = take(cell);
+    ctx->psi = take(cell); ctx->Dx = take(cell); ctx->Dz = take(fz); ctx->Hx = take(cell);
+    ctx->Hz = take(cell); ctx->b = take(cell); ctx->p0 = take(cell); ctx->p1 = take(cell);
+    ctx->q = take(cell);
     ctx->stage = take(4 * cell);
     ctx->thout = take(cell);
     ctx->thbar = take(round_up(G.nz * sizeof(double), 256));
@@ -369,7 +390,7 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
         Level l;
         l.G = g;
         const size_t lc = arr_bytes(g, g.nz), lf = arr_bytes(g, g.nz + 1);
-        l.c = take(lc); l.ax = take(lc); l.az = take(lf); l.dinv = take(lc);
+        l.c = take(lc); l.d = take(lc); l.wd = take(lc); l.ax = take(lc); l.az = take(lf);
         l.r = take(lc); l.e = take(lc); l.e2 = take(lc);
         ctx->L.push_back(l);
     }

@@ -27,6 +27,7 @@ struct Geom {
 
 struct Phys {
     double R, cp, g, p0, mu, nuh, dt, idt;   // nuh = mu / Pr
+    double omega;                            // damped-Jacobi weight of the smoother
 };
 
 // Persistent state of one time level (Section 3's solution tuple plus the
@@ -36,11 +37,20 @@ struct State {
 };
 
 // One multigrid level of the Helmholtz operator
-//   (A x)_i = c_i x_i + sum_f a_f (x_i - x_N).
+//   (A x)_i = c_i x_i + sum_f a_f (x_i - x_N) = d_i x_i - sum_f a_f x_N,
+// d_i = c_i + sum_f a_f, kept as d and wd = omega / d.
 struct Level {
     Geom G;
-    double *c, *ax, *az, *dinv;  // reaction term, x/z face coefficients, 1/diag
-    double *r, *e, *e2;          // residual, pre-smoothed correction, post-smoothed
+    double *c, *d, *wd, *ax, *az;  // reaction, diagonal, omega/diagonal, face coefficients
+    double *r, *e, *e2;            // residual, pre-smoothed correction, post-smoothed
+};
+
+// The implicit transport operator of Steps 1-2,
+//   T(X)_i = (rho1/dt) X_i + C(X)_i - mu L(X)_i,
+// assembled once per step as a 9-point cross stencil (offsets 0, +-1, +-2 in x
+// and z) on the ghost-extended field.
+struct Stencil9 {
+    double *cC, *cE1, *cE2, *cW1, *cW2, *cN1, *cN2, *cS1, *cS2;
 };
 
 // Loop bookkeeping slots.
@@ -89,10 +99,11 @@ struct StepArgs {
     Geom G;
     Phys F;
     State S, N;
-    double *rho1, *jd, *bu, *bw, *ua, *wa, *ub, *wb;   // Step 1
-    double *bh, *ha, *hb;                               // Step 2
-    double *rho2, *Dx, *Dz, *Hx, *Hz, *b;               // Step 3
-    double *p, *q;                                      // CG direction and A p
+    Stencil9 T;                                          // transport operator (with mu)
+    double *rho1, *dinvu, *dinvh, *bu, *bw, *ua, *wa, *ub, *wb;   // Step 1
+    double *bh, *ha, *hb;                                // Step 2
+    double *rho2, *psi, *Dx, *Dz, *Hx, *Hz, *b;          // Step 3
+    double *p0, *p1, *q;                                 // CG directions (ping-pong) and A p
     Scal *sc;
     double *partials;
     double jac_rtol2, cg_rtol2;
@@ -248,13 +259,13 @@ void launch_enth_rhs(const StepArgs &a, cudaStream_t st, Tracer *tr);
 void launch_enth_jacobi(const StepArgs &a, const double *hin, double *hout, cudaStream_t st,
                         Tracer *tr);
 void launch_eos_coef(const StepArgs &a, const Level &L0, cudaStream_t st, Tracer *tr);
-void launch_mg_coarsen(const Level &f, const Level &c, cudaStream_t st, Tracer *tr);
+void launch_mg_coarsen(const Level &f, const Level &c, double omega, cudaStream_t st, Tracer *tr);
 void launch_H(const StepArgs &a, const double *U, const double *W, cudaStream_t st, Tracer *tr);
 void launch_helm_rhs(const StepArgs &a, const Level &L0, const double *xin, double *xout,
                      int corr, cudaStream_t st, Tracer *tr);
 // returns the number of kernels launched
-int launch_vcycle(const StepArgs &a, Level *levels, int nlev, int ncoarse, double omega,
-                  cudaStream_t st, Tracer *tr);
+int launch_vcycle(const StepArgs &a, Level *levels, int nlev, int ncoarse, cudaStream_t st,
+                  Tracer *tr);
 int launch_cg_iter_tail(const StepArgs &a, const Level &L0, double *x, cudaStream_t st,
                         Tracer *tr);
 void launch_correct(const StepArgs &a, cudaStream_t st, Tracer *tr);

