@@ -193,6 +193,33 @@ typedef struct gea_kernel_time {
 int gea_profile_step(gea_ctx *ctx, gea_kernel_time *out, int32_t max_entries,
                      int32_t *n_entries);
 
+/* Total mass sum rho V and total energy sum rho (cv T + |u|^2/2 + g z) V of a
+ * caller-owned state, computed without allocating any device memory. The
+ * paper has no counterpart: this entry point serves callers that cannot
+ * allocate device memory (their memory is owned by a framework's caching
+ * allocator or a fixed arena, or they must not call cudaMalloc, which can
+ * synchronise the device or fail at run time). It needs no context.
+ *
+ * rho, u, w, T: device arrays, nz rows of nx values (x fastest, no padding).
+ * out: device array of 2 doubles, receives {mass, energy}. cp, R, g as in
+ * gea_constants; lx, lz the domain size. Enqueued on `stream` (a
+ * cudaStream_t; NULL for the legacy default stream); it does not wait.
+ *
+ * Scratch: the reduction's per-block partial sums and its arrival counter
+ * live in a fixed 1 MiB file-scope device array that every GPU that loads
+ * the library keeps until the process exits. Its device address is looked
+ * up on the first call on each device (cudaGetSymbolAddress, with that
+ * device current); make that first call before any stream capture. Every
+ * call shares the array: the counter is cleared at the start of each call,
+ * and calls whose kernels overlap on the GPU (on different streams or
+ * threads) race on it -- order them on one stream.
+ * Errors: GEA_ERR_INVAL for null pointers, non-positive sizes, or more than
+ * GEA_NOALLOC_MAX_CELLS cells; GEA_ERR_CUDA if a CUDA call fails. */
+#define GEA_NOALLOC_MAX_CELLS 16777216
+int gea_mass_energy_noalloc(int32_t nx, int32_t nz, double lx, double lz, double cp, double R,
+                            double g, const double *rho, const double *u, const double *w,
+                            const double *T, double *out, void *stream);
+
 const char *gea_last_error(const gea_ctx *ctx);
 void gea_destroy(gea_ctx *ctx);
 
