@@ -62,6 +62,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="bubble640x320")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--graph", action="store_true",
+                    help="step through the CUDA graph of per-phase kernels instead of the "
+                         "persistent cooperative kernel")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle baseline sample")
     return ap.parse_args()
@@ -199,7 +202,7 @@ def run_ours(args):
     wl = W.get(args.workload)
     cells = wl.grid.cells
     stream = torch.cuda.current_stream()
-    s = gea.Solver(wl.grid, wl.const, stream=stream)
+    s = gea.Solver(wl.grid, wl.const, stream=stream, graph=args.graph)
     dev = {k: torch.from_numpy(v).cuda() for k, v in wl.fields.items()}
     s.set_conservative(dev)
     for _ in range(args.warmup):
@@ -272,6 +275,7 @@ def run_ours(args):
                    "n_corr": wl.const.n_corr, "jac_rtol": wl.const.jac_rtol,
                    "cg_rtol": wl.const.cg_rtol, "mg_levels": st["mg_levels"],
                    "l2": "flushed between timed steps (256 MB write, untimed)",
+                   "driver": "cuda-graph" if args.graph else "persistent-cooperative-kernel",
                    "parallelism": f"replicas x{world}"},
         "pressure_solve_ms_per_step": statistics.mean(pms),
         "cg_iters_last_step": st["cg_iters"], "jacobi_sweeps_last_step": [st["jac_u"], st["jac_h"]],

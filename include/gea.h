@@ -49,10 +49,12 @@ enum {
     GEA_ERR_CUDA = 3,       /* a CUDA runtime call failed */
     GEA_ERR_NOCONV = 4,     /* a linear solve reached its iteration cap */
     GEA_ERR_NONFINITE = 5,  /* NaN or Inf in a residual norm */
-    GEA_ERR_STATE = 6       /* no state has been set yet */
+    GEA_ERR_STATE = 6,      /* no state has been set yet */
+    GEA_ERR_TIMEOUT = 7     /* a device-side wait gave up (never expected) */
 };
 
 enum { GEA_STATE_CONSERVATIVE = 0, GEA_STATE_FULL = 1 };
+enum { GEA_FLAG_GRAPH = 1 };
 enum { GEA_MEM_HOST = 0, GEA_MEM_DEVICE = 1 };
 
 /* Uniform Cartesian grid: nx * nz cells on [0, lx] x [0, lz] (metres).
@@ -82,7 +84,10 @@ typedef struct gea_grid {
  *            2 dt^2 R T (1/dx^2 + 1/dz^2) at T = 300 K, is below 0.3 (the
  *            coarse levels are then nearly diagonal). > 0: until a level has
  *            at most this many cells (a value >= nx*nz gives one level).
- *  flags     reserved, pass 0. */
+ *  flags     GEA_FLAG_GRAPH: run steps as a CUDA graph of per-phase kernels
+ *            instead of the default persistent cooperative kernel (the
+ *            graph path is also used when a cooperative launch of the grid
+ *            is not possible). Other bits must be 0. */
 typedef struct gea_constants {
     double R, cp, g, p0, mu, Pr, dt;
     int32_t n_corr;
@@ -141,8 +146,11 @@ int gea_set_state(gea_ctx *ctx, const gea_state_view *v);
 
 /* Advance n >= 0 steps (Section 3, Steps 1-3). Returns after the launches
  * are enqueued and the status of the finished steps has been read back,
- * i.e. it synchronises the stream once at the end. On GEA_ERR_NOCONV or
- * GEA_ERR_NONFINITE the state stays at the last completed step. */
+ * i.e. it synchronises the stream once at the end. On GEA_ERR_NOCONV,
+ * GEA_ERR_NONFINITE or GEA_ERR_TIMEOUT the state stays at the last completed
+ * step. By default all n steps run in one cooperative kernel launch whose
+ * blocks stay resident (grid barriers between phases, solver loops on the
+ * device); with GEA_FLAG_GRAPH each step is one CUDA graph launch. */
 int gea_step(gea_ctx *ctx, int32_t n);
 
 /* Enqueue n steps without waiting; gea_sync reports their status. */

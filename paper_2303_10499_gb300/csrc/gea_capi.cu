@@ -46,6 +46,7 @@ struct gea_ctx {
     int nev = 0;
     bool have_state = false;
     int base = 0;                         // state slot loaded by the last set_state
+    int pers_blocks = 0;                  // persistent-kernel grid (0: graph path only)
     long long steps_at_sync = 0;          // device steps_done at the last sync
     char err[256] = {0};
 };
@@ -318,7 +319,8 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
     if ((long long)grid->nx * grid->nz > (1LL << 31) / 2) return GEA_ERR_INVAL;
     if (!(c->R > 0) || !(c->cp > c->R) || !(c->g >= 0) || !(c->p0 > 0) || !(c->mu >= 0) ||
         !(c->Pr > 0) || !(c->dt > 0) || c->n_corr < 1 || c->n_corr > 4 || !(c->jac_rtol > 0) ||
-        c->jac_maxit < 1 || !(c->cg_rtol > 0) || c->cg_maxit < 1 || c->mg_min_cells < 0)
+        c->jac_maxit < 1 || !(c->cg_rtol > 0) || c->cg_maxit < 1 || c->mg_min_cells < 0 ||
+        (c->flags & ~GEA_FLAG_GRAPH))
         return GEA_ERR_INVAL;
 
     ctx = new gea_ctx();
@@ -343,6 +345,7 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
         if (f.nx % 2 || f.nz % 2 || f.nx < 8 || f.nz < 8) break;
         if (c->mg_min_cells > 0 && (long long)f.nx * f.nz <= c->mg_min_cells) break;
         if (c->mg_min_cells == 0 && ratio <= kCoarsestRatio) break;
+        if ((int)lg.size() >= kMaxLevels) break;
         lg.push_back(make_geom(f.nx / 2, f.nz / 2, f.nx * f.dx, f.nz * f.dz));
         ratio *= 0.25;
     }
@@ -402,6 +405,11 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
     }
     for (int e = 0; e < 8; ++e) cudaEventCreate(&ctx->ev[e]);
     ctx->nev = 8;
+    if (!(c->flags & GEA_FLAG_GRAPH)) {
+        const int pmax = persistent_max_blocks();
+        ctx->pers_blocks = pmax < (int)nb ? pmax : (int)nb;
+        cudaGetLastError();
+    }
     if (cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&ctx->cap2, cudaStreamNonBlocking) != cudaSuccess ||
         cudaDeviceSynchronize() != cudaSuccess) {
@@ -468,6 +476,16 @@ int gea_step_async(gea_ctx *ctx, int32_t n)
 {
     if (!ctx || n < 0) return GEA_ERR_INVAL;
     if (!ctx->have_state) return fail(ctx, GEA_ERR_STATE, "no state set");
+    if (n == 0) return GEA_OK;
+    if (ctx->pers_blocks > 0) {
+        StepArgs a[2] = {step_args(ctx, 0), step_args(ctx, 1)};
+        const int first = (int)((ctx->base + ctx->steps_at_sync) & 1);
+        CK(launch_persistent(a, ctx->L.data(), (int)ctx->L.size(), kCoarseSweeps, ctx->C.n_corr,
+                             ctx->C.jac_maxit, ctx->C.cg_maxit, first, n, ctx->pers_blocks,
+                             ctx->stream));
+        ctx->steps_at_sync += n;
+        return GEA_OK;
+    }
     int rc = ensure_graphs(ctx);
     if (rc) return rc;
     // the slot holding the newest state is base + steps launched so far;
@@ -575,13 +593,16 @@ int gea_get_field(gea_ctx *ctx, int32_t which, double *host)
 {
     if (!ctx || !host) return GEA_ERR_INVAL;
     const Geom &G = ctx->G;
+    Scal h;
+    if (int rc0 = read_scal(ctx, &h)) return rc0;
+    const bool slot_u1 = h.u1_slot != 0, slot_h1 = h.h1_slot != 0;
     const double *src = nullptr;
     int cols = G.nx, rows = G.nz;
     switch (which) {
     case GEA_FIELD_RHO1: src = ctx->rho1; break;
-    case GEA_FIELD_U1: src = ctx->ua; break;
-    case GEA_FIELD_W1: src = ctx->wa; break;
-    case GEA_FIELD_H1: src = ctx->ha; break;
+    case GEA_FIELD_U1: src = slot_u1 ? ctx->ub : ctx->ua; break;
+    case GEA_FIELD_W1: src = slot_u1 ? ctx->wb : ctx->wa; break;
+    case GEA_FIELD_H1: src = slot_h1 ? ctx->hb : ctx->ha; break;
     case GEA_FIELD_RHO2: src = ctx->rho2; break;
     case GEA_FIELD_HX: src = ctx->Hx; break;
     case GEA_FIELD_HZ: src = ctx->Hz; break;
@@ -598,7 +619,13 @@ int gea_get_field(gea_ctx *ctx, int32_t which, double *host)
 
 double gea_last_pressure_ms(gea_ctx *ctx)
 {
-    if (!ctx || !ctx->exec[0]) return -1.0;
+    if (!ctx) return -1.0;
+    if (ctx->pers_blocks > 0) {
+        Scal h;
+        if (read_scal(ctx, &h)) return -1.0;
+        return (double)h.press_ns * 1e-6;
+    }
+    if (!ctx->exec[0]) return -1.0;
     double tot = 0.0;
     for (int c = 0; c < ctx->C.n_corr; ++c) {
         float ms = 0.f;

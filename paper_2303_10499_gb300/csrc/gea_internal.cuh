@@ -12,11 +12,14 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/gea.h"
+
 namespace gea {
 
 constexpr int BX = 32;          // threads per block along x (one warp per row)
 constexpr int BZ = 8;           // rows per block
 constexpr int NTHREADS = BX * BZ;
+constexpr int kMaxLevels = 16;  // multigrid levels (grids up to 2^16 cells a side)
 
 enum Bc { BC_EVEN = 0, BC_U = 1, BC_W = 2, BC_H = 3 };
 
@@ -78,6 +81,10 @@ struct Scal {
     double mass, energy;        // diagnostics
     long long launches;         // kernel launches of completed and running steps
     unsigned counters[32];      // reduction arrival counters, one per kernel kind
+    // persistent step kernel: grid barrier and per-step results
+    unsigned bar_count, bar_gen;
+    int u1_slot, h1_slot;       // 1 if u^{n+1/3} / h^{n+1} ended in the b buffers
+    unsigned long long press_ns; // globaltimer nanoseconds of the pressure solves, last step
 };
 
 // Optional per-launch hook (profiled eager steps only; never during graph
@@ -142,52 +149,6 @@ __device__ __forceinline__ double ldc(const Geom &G, const Phys &F, const double
     return X[k * G.P + i];
 }
 
-// Fourth-order face value between cells a and b = a+1 from a-1, a, b, b+1
-// (the finite-volume reconstruction weights (-1, 7, 7, -1)/12).
-__device__ __forceinline__ double interp4(double xm, double xa, double xb, double xp)
-{
-    return (-xm + 7.0 * xa + 7.0 * xb - xp) * (1.0 / 12.0);
-}
-
-// Convective term (1/V) sum_j phi_j X_j of cell (i,k); wall faces carry no flux.
-template <int BC>
-__device__ __forceinline__ double convection(const Geom &G, const Phys &F,
-                                             const double *__restrict__ phix,
-                                             const double *__restrict__ phiz,
-                                             const double *__restrict__ X, int i, int k)
-{
-    double s = 0.0;
-    if (i + 1 < G.nx)
-        s += phix[k * G.P + i + 1] *
-             interp4(ldc<BC>(G, F, X, i - 1, k), ldc<BC>(G, F, X, i, k),
-                     ldc<BC>(G, F, X, i + 1, k), ldc<BC>(G, F, X, i + 2, k));
-    if (i > 0)
-        s -= phix[k * G.P + i] *
-             interp4(ldc<BC>(G, F, X, i - 2, k), ldc<BC>(G, F, X, i - 1, k),
-                     ldc<BC>(G, F, X, i, k), ldc<BC>(G, F, X, i + 1, k));
-    if (k + 1 < G.nz)
-        s += phiz[(k + 1) * G.P + i] *
-             interp4(ldc<BC>(G, F, X, i, k - 1), ldc<BC>(G, F, X, i, k),
-                     ldc<BC>(G, F, X, i, k + 1), ldc<BC>(G, F, X, i, k + 2));
-    if (k > 0)
-        s -= phiz[k * G.P + i] *
-             interp4(ldc<BC>(G, F, X, i, k - 2), ldc<BC>(G, F, X, i, k - 1),
-                     ldc<BC>(G, F, X, i, k), ldc<BC>(G, F, X, i, k + 1));
-    return s * G.iV;
-}
-
-// Diffusive face sum (1/V) sum_j (grad X)_j . A_j with compact face-normal
-// gradients; wall faces through the ghost layer.
-template <int BC>
-__device__ __forceinline__ double laplacian(const Geom &G, const Phys &F,
-                                            const double *__restrict__ X, int i, int k)
-{
-    double xc = X[k * G.P + i];
-    double sx = (ldc<BC>(G, F, X, i + 1, k) - xc) + (ldc<BC>(G, F, X, i - 1, k) - xc);
-    double sz = (ldc<BC>(G, F, X, i, k + 1) - xc) + (ldc<BC>(G, F, X, i, k - 1) - xc);
-    return sx * G.idx * G.idx + sz * G.idz * G.idz;
-}
-
 __device__ __forceinline__ double warp_sum(double v)
 {
 #pragma unroll
@@ -195,55 +156,61 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-// Deterministic grid-wide sum of NV values per thread. Each block writes its
-// partial sums; the block that arrives last adds the partials in a fixed
-// order and returns true in its thread 0 with the totals in tot[]. Every
-// thread of every block must call it (no early return before it).
+// Block totals of NV per-thread values, valid in thread 0. The values pass
+// through shared memory (red: NV * NTHREADS doubles) and one warp adds them,
+// 8 per lane and then a shuffle tree: about 1.5 FP64 additions per value per
+// thread instead of 5 for a full-block shuffle tree (FP64 issue is the
+// scarce resource on this GPU).
 template <int NV>
-__device__ bool grid_sum(const double (&v)[NV], double *partials, unsigned *counter,
-                         double (&tot)[NV])
+__device__ __forceinline__ void block_sum(const double (&v)[NV], double *red, double (&out)[NV])
 {
-    __shared__ double sh[NV][NTHREADS / 32];
-    __shared__ int am_last;
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    const int nthr = blockDim.x * blockDim.y;
-    const int lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
-    const int bid = blockIdx.x + blockIdx.y * gridDim.x;
-    const int nb = gridDim.x * gridDim.y;
 #pragma unroll
-    for (int j = 0; j < NV; ++j) {
-        double s = warp_sum(v[j]);
-        if (lane == 0) sh[j][wid] = s;
-    }
+    for (int j = 0; j < NV; ++j) red[j * NTHREADS + tid] = v[j];
     __syncthreads();
-    if (tid == 0) {
+    if (tid < 32) {
 #pragma unroll
         for (int j = 0; j < NV; ++j) {
-            double s = 0.0;
-            for (int q = 0; q < nw; ++q) s += sh[j][q];
-            partials[(size_t)j * nb + bid] = s;
+            double s = red[j * NTHREADS + tid];
+#pragma unroll
+            for (int q = 1; q < NTHREADS / 32; ++q) s += red[j * NTHREADS + tid + 32 * q];
+            s = warp_sum(s);
+            if (tid == 0) out[j] = s;
         }
+    }
+    __syncthreads();
+}
+
+// Deterministic grid-wide sum of NV values per thread (one launch). Each
+// block writes its totals; the block that arrives last adds the partials in
+// a fixed order and returns true in its thread 0 with the totals in tot[].
+// Every thread of every block must call it.
+template <int NV>
+__device__ bool grid_sum(const double (&v)[NV], double *red, double *partials, unsigned *counter,
+                         double (&tot)[NV])
+{
+    __shared__ int am_last;
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int bid = blockIdx.x + blockIdx.y * gridDim.x;
+    const int nb = gridDim.x * gridDim.y;
+    double bt[NV];
+    block_sum<NV>(v, red, bt);
+    if (tid == 0) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) partials[(size_t)j * nb + bid] = bt[j];
         __threadfence();
-        unsigned t = atomicAdd(counter, 1u);
-        am_last = (t == (unsigned)nb - 1u);
+        am_last = atomicAdd(counter, 1u) == (unsigned)nb - 1u;
     }
     __syncthreads();
     if (!am_last) return false;
     __threadfence();
+    double s[NV];
 #pragma unroll
     for (int j = 0; j < NV; ++j) {
-        double s = 0.0;
-        for (int b = tid; b < nb; b += nthr) s += __ldcg(&partials[(size_t)j * nb + b]);
-        s = warp_sum(s);
-        __syncthreads();
-        if (lane == 0) sh[j][wid] = s;
-        __syncthreads();
-        if (tid == 0) {
-            double t = 0.0;
-            for (int q = 0; q < nw; ++q) t += sh[j][q];
-            tot[j] = t;
-        }
+        s[j] = 0.0;
+        for (int b = tid; b < nb; b += NTHREADS) s[j] += __ldcg(&partials[(size_t)j * nb + b]);
     }
+    block_sum<NV>(s, red, tot);
     if (tid == 0) *counter = 0u;
     return tid == 0;
 }
@@ -277,5 +244,10 @@ void launch_step_end(Scal *sc, int fixed_launches, cudaStream_t st, Tracer *tr);
 void launch_diag(const Geom &G, const Phys &F, const State &S, const double *theta_bar,
                  double *theta_out, Scal *sc, double *partials, cudaStream_t st);
 int max_blocks(const Geom &G);
+// persistent cooperative step kernel (gea_persistent.cu)
+int persistent_max_blocks();
+cudaError_t launch_persistent(const StepArgs a[2], const Level *L, int nlev, int ncoarse, int n_corr,
+                              int jac_maxit, int cg_maxit, int first_slot, int nsteps, int blocks,
+                              cudaStream_t st);
 
 }  // namespace gea

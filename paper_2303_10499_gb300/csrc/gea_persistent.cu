@@ -1,0 +1,348 @@
+// gea_persistent.cu -- n time steps of the GEA pressure-based Euler solver
+// (Girfoglio, Quaini & Rozza, arXiv 2303.10499, Section 3) as one cooperative
+// kernel.
+//
+// On grids of up to a few hundred thousand cells a step is a chain of ~90
+// short phases, and launching each as its own kernel leaves the GPU waiting
+// on launch latency. Here the blocks stay resident for the whole step: each
+// phase is a block-stride loop over tiles running the tile functions of
+// gea_tiles.cuh, phases are separated by a grid barrier, and every residual
+// norm or CG dot product is folded into the barrier (the last block to
+// arrive adds the block partials in a fixed order and publishes the result
+// before releasing the others). The Jacobi and CG loops run inside the
+// kernel; every block takes the same decisions because it reads the same
+// published scalars.
+//
+// The barrier waits spin on an acquire load with an iteration cap; a block
+// that gives up sets GEA_ERR_TIMEOUT in the context status, and every block
+// leaves the step at its next phase boundary when the status is set, so the
+// kernel always ends.
+#include "gea_internal.cuh"
+#include "gea_tiles.cuh"
+
+namespace gea {
+
+namespace {
+
+using namespace tiles;
+
+constexpr unsigned long long kSpinLimit = 1ull << 25;   // x ~64 ns: a few seconds
+
+struct PersistArgs {
+    StepArgs a[2];          // a[s] reads state slot s and writes slot s ^ 1
+    Level L[kMaxLevels];
+    int nlev, ncoarse, nsteps, first_slot, n_corr, jac_maxit, cg_maxit;
+};
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int rdi(const int *p) { return __ldcg(p); }
+__device__ __forceinline__ double rdd(const double *p) { return __ldcg(p); }
+
+__device__ __forceinline__ unsigned long long globaltimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ int tid_of() { return threadIdx.x + threadIdx.y * BX; }
+
+// Arrive and wait. The last block to arrive runs last() (all its threads)
+// and then releases the others.
+template <class Last>
+__device__ __forceinline__ void barrier_with(Scal *sc, Last last)
+{
+    __shared__ int am_last;
+    __shared__ unsigned gen0;
+    const int tid = tid_of();
+    // every thread of the block has finished its writes of this phase before
+    // thread 0 arrives (its fence then publishes them, cumulatively)
+    __syncthreads();
+    if (tid == 0) {
+        gen0 = ld_acquire(&sc->bar_gen);
+        __threadfence();
+        am_last = atomicAdd(&sc->bar_count, 1u) == gridDim.x - 1u;
+    }
+    __syncthreads();
+    if (am_last) {
+        __threadfence();
+        last();
+        if (tid == 0) {
+            sc->bar_count = 0u;
+            __threadfence();
+            atomicAdd(&sc->bar_gen, 1u);
+        }
+    } else if (tid == 0) {
+        unsigned long long spins = 0;
+        while (ld_acquire(&sc->bar_gen) == gen0) {
+            if (++spins > kSpinLimit) {
+                atomicCAS(&sc->status, 0, GEA_ERR_TIMEOUT);
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void gbar(Scal *sc)
+{
+    barrier_with(sc, [] {});
+}
+
+// Barrier with a deterministic grid-wide sum of NV per-thread values; fin(tot)
+// runs in one thread of the last block before the release.
+template <int NV, class Fin>
+__device__ __forceinline__ void rbar(const double (&v)[NV], double *red, Scal *sc, double *partials,
+                                     Fin fin)
+{
+    const int tid = tid_of();
+    const int nb = gridDim.x;
+    double bt[NV];
+    block_sum<NV>(v, red, bt);
+    if (tid == 0) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) partials[(size_t)j * nb + blockIdx.x] = bt[j];
+    }
+    barrier_with(sc, [&] {
+        double s[NV], tot[NV];
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            s[j] = 0.0;
+            for (int b = tid; b < nb; b += NTHREADS) s[j] += __ldcg(&partials[(size_t)j * nb + b]);
+        }
+        block_sum<NV>(s, red, tot);
+        if (tid == 0) fin(tot);
+    });
+}
+
+template <class F>
+__device__ __forceinline__ void for_tiles(const Geom &G, F f)
+{
+    const int tx = (G.nx + BX - 1) / BX, tz = (G.nz + BZ - 1) / BZ;
+    const int nt = tx * tz;
+    for (int t = blockIdx.x; t < nt; t += gridDim.x) f(t % tx, t / tx);
+}
+
+__device__ __forceinline__ bool stop(const Scal *sc) { return rdi(&sc->status) != 0; }
+
+// One time step reading a.S and writing a.N. Returns false if the step did
+// not complete (a device error is set).
+__device__ bool run_step(const PersistArgs &P, const StepArgs &a, double *sm, double *red)
+{
+    Scal *sc = a.sc;
+    const Geom &G = a.G;
+    const Level *L = P.L;
+    const int nlev = P.nlev;
+
+    // ---- Step 1: continuity predictor, transport operator, momentum RHS ----
+    {
+        double acc[2] = {0.0, 0.0};
+        for_tiles(G, [&](int bx, int bz) { ph_pred(a, bx, bz, acc); });
+        rbar<2>(acc, red, sc, a.partials, [&](const double (&t)[2]) {
+            fin_pred(sc, t);
+            for (int c = 0; c < 4; ++c) { sc->cg_iters[c] = 0; sc->cg_relres[c] = 0.0; }
+            sc->sweeps[1] = 0;
+            sc->press_ns = 0ull;
+        });
+    }
+    if (stop(sc)) return false;
+    // implicit momentum predictor: Jacobi until the sweep whose residual met
+    // the tolerance
+    const double *uin = a.ua, *win = a.wa;
+    double *uout = a.ub, *wout = a.wb;
+    for (;;) {
+        double acc[2] = {0.0, 0.0};
+        for_tiles(G, [&](int bx, int bz) { ph_mom(a, uin, win, uout, wout, sm, bx, bz, acc); });
+        rbar<2>(acc, red, sc, a.partials, [&](const double (&t)[2]) {
+            fin_mom(sc, t, a.jac_rtol2);
+            if (!sc->done[LOOP_MOM] && !sc->status && sc->sweeps[0] >= P.jac_maxit) sc->status = GEA_ERR_NOCONV;
+        });
+        const double *tu = uin, *tw = win;
+        uin = uout; win = wout;
+        uout = const_cast<double *>(tu); wout = const_cast<double *>(tw);
+        if (stop(sc) || rdi(&sc->done[LOOP_MOM])) break;
+    }
+    if (stop(sc)) return false;
+    const double *u1 = uin, *w1 = win;
+
+    // ---- Step 2: enthalpy, temperature, rho^{n+2/3} ----
+    {
+        double acc[1] = {0.0};
+        for_tiles(G, [&](int bx, int bz) { ph_enth_rhs(a, u1, w1, a.ha, sm, bx, bz, acc); });
+        rbar<1>(acc, red, sc, a.partials, [&](const double (&t)[1]) { fin_enth_rhs(sc, t); });
+    }
+    if (stop(sc)) return false;
+    const double *hin = a.ha;
+    double *hout = a.hb;
+    for (;;) {
+        double acc[1] = {0.0};
+        for_tiles(G, [&](int bx, int bz) { ph_enth(a, hin, hout, sm, bx, bz, acc); });
+        rbar<1>(acc, red, sc, a.partials, [&](const double (&t)[1]) {
+            fin_enth(sc, t, a.jac_rtol2);
+            if (!sc->done[LOOP_ENTH] && !sc->status && sc->sweeps[1] >= P.jac_maxit) sc->status = GEA_ERR_NOCONV;
+        });
+        const double *t = hin;
+        hin = hout;
+        hout = const_cast<double *>(t);
+        if (stop(sc) || rdi(&sc->done[LOOP_ENTH])) break;
+    }
+    if (stop(sc)) return false;
+    const double *h1 = hin;
+    for_tiles(G, [&](int bx, int bz) { ph_eos(a, L[0], h1, sm, bx, bz); });
+    gbar(sc);
+    for (int l = 0; l + 1 < nlev; ++l) {
+        for_tiles(L[l + 1].G, [&](int bx, int bz) { ph_coarsen(L[l], L[l + 1], a.F.omega, bx, bz); });
+        gbar(sc);
+    }
+    if (stop(sc)) return false;
+    if (blockIdx.x == 0 && tid_of() == 0) {
+        sc->u1_slot = (u1 == a.ub);
+        sc->h1_slot = (h1 == a.hb);
+    }
+
+    // ---- Step 3: PISO correctors ----
+    for (int c = 0; c < P.n_corr; ++c) {
+        const double *U = c == 0 ? u1 : a.N.u;
+        const double *W = c == 0 ? w1 : a.N.w;
+        for_tiles(G, [&](int bx, int bz) { ph_H(a, U, W, sm, bx, bz); });
+        gbar(sc);
+        unsigned long long t0 = 0;
+        if (blockIdx.x == 0 && tid_of() == 0) t0 = globaltimer();
+        {
+            double acc[2] = {0.0, 0.0};
+            const double *xin = c == 0 ? a.S.pp : a.N.pp;
+            for_tiles(G, [&](int bx, int bz) { ph_helm_rhs(a, L[0], xin, a.N.pp, sm, bx, bz, acc); });
+            rbar<2>(acc, red, sc, a.partials, [&](const double (&t)[2]) { fin_helm(sc, t, a.cg_rtol2, c); });
+        }
+        while (!stop(sc) && !rdi(&sc->done[LOOP_CG])) {
+            // z = M^-1 r: one V(1,1)-cycle
+            if (nlev == 1) {
+                double acc[1] = {0.0};
+                for_tiles(G, [&](int bx, int bz) { ph_mg_single(L[0], L[0].e2, sm, bx, bz, acc); });
+                rbar<1>(acc, red, sc, a.partials, [&](const double (&t)[1]) { fin_rz(sc, t); });
+            } else {
+                for (int l = 0; l + 1 < nlev; ++l) {
+                    for_tiles(L[l].G, [&](int bx, int bz) { ph_mg_down(L[l], L[l + 1], a.F.omega, sm, bx, bz); });
+                    gbar(sc);
+                }
+                const Level &C = L[nlev - 1];
+                for (int s = 0; s < P.ncoarse; ++s) {
+                    double *out = ((P.ncoarse - 1 - s) % 2 == 0) ? C.e2 : C.e;
+                    const double *in = (out == C.e2) ? C.e : C.e2;
+                    for_tiles(C.G, [&](int bx, int bz) { ph_mg_coarse(C, in, out, s == 0, sm, bx, bz); });
+                    gbar(sc);
+                }
+                for (int l = nlev - 2; l >= 0; --l) {
+                    double acc[1] = {0.0};
+                    for_tiles(L[l].G, [&](int bx, int bz) {
+                        ph_mg_up(L[l], L[l + 1].e2, L[l + 1].G.P, L[l].e2, sm, bx, bz, acc);
+                    });
+                    if (l > 0) gbar(sc);
+                    else rbar<1>(acc, red, sc, a.partials, [&](const double (&t)[1]) { fin_rz(sc, t); });
+                }
+            }
+            // p = z + beta p, q = A p; then x, r
+            const int it = rdi(&sc->cg_it);
+            const double *pold = (it & 1) ? a.p1 : a.p0;
+            double *pnew = (it & 1) ? a.p0 : a.p1;
+            {
+                const double beta = rdd(&sc->beta);
+                double acc[1] = {0.0};
+                for_tiles(G, [&](int bx, int bz) { ph_pspmv(a, L[0], pold, pnew, beta, sm, bx, bz, acc); });
+                rbar<1>(acc, red, sc, a.partials, [&](const double (&t)[1]) { fin_pq(sc, t); });
+            }
+            {
+                const double alpha = rdd(&sc->alpha);
+                double acc[1] = {0.0};
+                for_tiles(G, [&](int bx, int bz) { ph_update(a, L[0], a.N.pp, pnew, alpha, bx, bz, acc); });
+                rbar<1>(acc, red, sc, a.partials, [&](const double (&t)[1]) {
+                    fin_update(sc, t, a.cg_rtol2);
+                    if (!sc->done[LOOP_CG] && !sc->status && sc->cg_it >= P.cg_maxit) sc->status = GEA_ERR_NOCONV;
+                });
+            }
+        }
+        if (stop(sc)) return false;
+        if (blockIdx.x == 0 && tid_of() == 0) sc->press_ns += globaltimer() - t0;
+        for_tiles(G, [&](int bx, int bz) { ph_correct(a, sm, bx, bz); });
+        if (c + 1 < P.n_corr) gbar(sc);
+    }
+    // end of step: publish the step's counters
+    barrier_with(sc, [&] {
+        if (tid_of() == 0 && !sc->status) {
+            sc->steps_done += 1;
+            sc->last_sweeps[0] = sc->sweeps[0];
+            sc->last_sweeps[1] = sc->sweeps[1];
+            for (int c = 0; c < 4; ++c) {
+                sc->last_cg_iters[c] = sc->cg_iters[c];
+                sc->last_cg_relres[c] = sc->cg_relres[c];
+            }
+            sc->last_status = 0;
+        }
+    });
+    return !stop(sc);
+}
+
+__global__ void __launch_bounds__(NTHREADS, 3) k_persistent(PersistArgs P)
+{
+    extern __shared__ double dsm[];
+    double *sm = dsm;
+    double *red = dsm + kTileSmem;
+    // a failed earlier launch may have left the barrier mid-count; the error
+    // is sticky until the next set_state, which clears it
+    if (rdi(&P.a[0].sc->status)) return;
+    if (blockIdx.x == 0 && tid_of() == 0) P.a[0].sc->launches += 1;
+    for (int s = 0; s < P.nsteps; ++s) {
+        const int slot = (P.first_slot + s) & 1;
+        if (!run_step(P, P.a[slot], sm, red)) break;
+    }
+    Scal *sc = P.a[0].sc;
+    if (blockIdx.x == 0 && tid_of() == 0 && sc->status) sc->last_status = sc->status;
+}
+
+constexpr size_t kPersistSmem = (size_t)(kTileSmem + 2 * NTHREADS) * sizeof(double);
+
+}  // namespace
+
+int persistent_max_blocks()
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kPersistSmem) != cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent, NTHREADS, kPersistSmem) !=
+        cudaSuccess)
+        return 0;
+    return per_sm * sms;
+}
+
+cudaError_t launch_persistent(const StepArgs a[2], const Level *L, int nlev, int ncoarse, int n_corr,
+                              int jac_maxit, int cg_maxit, int first_slot, int nsteps, int blocks,
+                              cudaStream_t st)
+{
+    PersistArgs P;
+    P.a[0] = a[0];
+    P.a[1] = a[1];
+    for (int l = 0; l < nlev && l < kMaxLevels; ++l) P.L[l] = L[l];
+    P.nlev = nlev;
+    P.ncoarse = ncoarse;
+    P.nsteps = nsteps;
+    P.first_slot = first_slot;
+    P.n_corr = n_corr;
+    P.jac_maxit = jac_maxit;
+    P.cg_maxit = cg_maxit;
+    void *args[] = {&P};
+    return cudaLaunchCooperativeKernel((const void *)k_persistent, dim3(blocks), dim3(BX, BZ), args,
+                                       kPersistSmem, st);
+}
+
+}  // namespace gea

@@ -1,0 +1,759 @@
+// gea_tiles.cuh -- the phases of one time step of the GEA pressure-based
+// Euler solver (Girfoglio, Quaini & Rozza, arXiv 2303.10499, Section 3) as
+// tile-level device functions. A tile is BX x BZ cells, one per thread of a
+// BX x BZ block; (bx, bz) are the tile's coordinates. Both the per-phase
+// kernels (gea_kernels.cu) and the persistent step kernel
+// (gea_persistent.cu) run these functions; the persistent kernel walks the
+// tiles of a phase in a block-stride loop and separates phases with grid
+// barriers.
+//
+// GB300 executes FP64 at 1/64 of its FP32 rate (two FP64 lanes per SM per
+// clock, about 1.2 TFLOP/s) while HBM delivers about 6.8 TB/s, so every phase
+// is FP64-issue-bound. The functions execute as few FP64 instructions as
+// possible and spend loads, integer and shared-memory work instead:
+//  - neighbour values come from a shared-memory tile with a halo, wall ghosts
+//    filled while loading, so the arithmetic has no boundary branches;
+//  - the implicit transport operator of Steps 1-2 is assembled once per step
+//    as a 9-point stencil; a Jacobi sweep and H(u) are 9 FMAs per component;
+//  - the Helmholtz operator is kept as d x - sum a x_N with omega/d stored;
+//    values needed at neighbours are computed once per tile cell;
+//  - divisions are done once per step into stored reciprocals.
+// Global reads go through L2 (ld.global.cg): within one persistent launch a
+// buffer is rewritten by other blocks between phases, and L1 is not coherent
+// across SMs.
+//
+// Shared memory: each function takes `sm`, a block-wide scratch area of at
+// least kTileSmem doubles, and ends with a __syncthreads() so the next tile
+// can reuse it. Reduction contributions are added to the caller's per-thread
+// accumulators.
+#pragma once
+
+#include "gea_internal.cuh"
+
+namespace gea {
+namespace tiles {
+
+template <int H>
+using Tile = double[BZ + 2 * H][BX + 2 * H];
+
+constexpr int kT1 = (BZ + 2) * (BX + 2);   // doubles of a halo-1 tile
+constexpr int kT2 = (BZ + 4) * (BX + 4);   // doubles of a halo-2 tile
+constexpr int kTileSmem = 4 * kT1;         // the largest phase footprint
+
+template <int H>
+__device__ __forceinline__ Tile<H> &tile_at(double *sm, int slot)
+{
+    return *reinterpret_cast<Tile<H> *>(sm + slot * (BZ + 2 * H) * (BX + 2 * H));
+}
+
+__device__ __forceinline__ double ld(const double *p) { return __ldcg(p); }
+
+__device__ __forceinline__ bool cell_of(const Geom &G, int bx, int bz, int &i, int &k)
+{
+    i = bx * BX + threadIdx.x;
+    k = bz * BZ + threadIdx.y;
+    return i < G.nx && k < G.nz;
+}
+
+// Cell value at (i,k) just outside the box: the one-layer wall ghost of rule
+// BC (wall-normal velocity odd, tangential velocity and scalars even, h with
+// dh/dz = -g at the horizontal walls).
+template <int BC>
+__device__ __forceinline__ double ghost(const Geom &G, const Phys &F, const double *X, int i, int k)
+{
+    if (i < 0) {
+        const double v = ld(&X[k * G.P]);
+        return BC == BC_U ? -v : v;
+    }
+    if (i >= G.nx) {
+        const double v = ld(&X[k * G.P + G.nx - 1]);
+        return BC == BC_U ? -v : v;
+    }
+    if (k < 0) {
+        const double v = ld(&X[i]);
+        if (BC == BC_W) return -v;
+        if (BC == BC_H) return v + F.g * G.dz;
+        return v;
+    }
+    const double v = ld(&X[(G.nz - 1) * G.P + i]);
+    if (BC == BC_W) return -v;
+    if (BC == BC_H) return v - F.g * G.dz;
+    return v;
+}
+
+// Fill the (BZ+2H) x (BX+2H) tile of X around tile (bx, bz): cells inside the
+// box, the one-layer wall ghosts of rule BC, zero elsewhere (deeper ghosts and
+// corners only ever meet zero coefficients).
+template <int BC, int H>
+__device__ __forceinline__ void load_tile(Tile<H> &s, const Geom &G, const Phys &F,
+                                          const double *X, int bx, int bz)
+{
+    const int i0 = bx * BX - H, k0 = bz * BZ - H;
+    const int tid = threadIdx.x + threadIdx.y * BX;
+    constexpr int W = BX + 2 * H, NE = (BZ + 2 * H) * (BX + 2 * H);
+    for (int e = tid; e < NE; e += NTHREADS) {
+        const int tk = e / W, ti = e - tk * W;
+        const int i = i0 + ti, k = k0 + tk;
+        const bool xin = i >= 0 && i < G.nx, zin = k >= 0 && k < G.nz;
+        double v = 0.0;
+        if (xin && zin) v = ld(&X[k * G.P + i]);
+        else if (zin && (i == -1 || i == G.nx)) v = ghost<BC>(G, F, X, i, k);
+        else if (xin && (k == -1 || k == G.nz)) v = ghost<BC>(G, F, X, i, k);
+        s[tk][ti] = v;
+    }
+}
+
+// Same for a field given by f(q, i, k) at cell (i, k), index q (zero outside
+// the box).
+template <int H, class Fn>
+__device__ __forceinline__ void load_tile_fn(Tile<H> &s, const Geom &G, int bx, int bz, Fn f)
+{
+    const int i0 = bx * BX - H, k0 = bz * BZ - H;
+    const int tid = threadIdx.x + threadIdx.y * BX;
+    constexpr int W = BX + 2 * H, NE = (BZ + 2 * H) * (BX + 2 * H);
+    for (int e = tid; e < NE; e += NTHREADS) {
+        const int tk = e / W, ti = e - tk * W;
+        const int i = i0 + ti, k = k0 + tk;
+        s[tk][ti] = (i >= 0 && i < G.nx && k >= 0 && k < G.nz) ? f(k * G.P + i, i, k) : 0.0;
+    }
+}
+
+// 9-point cross stencil sum_o c_o X_o at tile position (y, x).
+template <int H>
+__device__ __forceinline__ double apply9(const Stencil9 &T, int q, const Tile<H> &s, int y, int x)
+{
+    double acc = ld(&T.cC[q]) * s[y][x];
+    acc = fma(ld(&T.cE1[q]), s[y][x + 1], acc);
+    acc = fma(ld(&T.cW1[q]), s[y][x - 1], acc);
+    acc = fma(ld(&T.cN1[q]), s[y + 1][x], acc);
+    acc = fma(ld(&T.cS1[q]), s[y - 1][x], acc);
+    acc = fma(ld(&T.cE2[q]), s[y][x + 2], acc);
+    acc = fma(ld(&T.cW2[q]), s[y][x - 2], acc);
+    acc = fma(ld(&T.cN2[q]), s[y + 2][x], acc);
+    acc = fma(ld(&T.cS2[q]), s[y - 2][x], acc);
+    return acc;
+}
+
+// 5-point Laplacian (X_E + X_W - 2 X_C)/dx^2 + (X_N + X_S - 2 X_C)/dz^2.
+template <int H>
+__device__ __forceinline__ double lap5(const Geom &G, const Tile<H> &s, int y, int x)
+{
+    const double c2 = 2.0 * s[y][x];
+    return (s[y][x + 1] + s[y][x - 1] - c2) * (G.idx * G.idx) +
+           (s[y + 1][x] + s[y - 1][x] - c2) * (G.idz * G.idz);
+}
+
+// A x = d x - sum a x_N at tile position (y, x) of cell (i, k) (zero tile
+// entries and zero wall coefficients beyond the box).
+template <int H>
+__device__ __forceinline__ double helm_tile(const Level &L, int q, int i, int k, const Tile<H> &s,
+                                            int y, int x)
+{
+    const Geom &G = L.G;
+    double t = ld(&L.d[q]) * s[y][x];
+    t = fma(-ld(&L.ax[k * G.P + i]), s[y][x - 1], t);
+    t = fma(-ld(&L.ax[k * G.P + i + 1]), s[y][x + 1], t);
+    t = fma(-ld(&L.az[k * G.P + i]), s[y - 1][x], t);
+    t = fma(-ld(&L.az[(k + 1) * G.P + i]), s[y + 1][x], t);
+    return t;
+}
+
+// ---------------------------------------------------------------------------
+// Step 1 (eq. e1_d and eq. step2_sd, first line)
+// ---------------------------------------------------------------------------
+
+// rho^{n+1/3} = rho^n - dt sum_j phi_j / V; the transport operator
+//   T(X) = (rho1/dt) X + C(X) - mu L(X)
+// as a 9-point stencil: the east face contributes f_e (-X_W1 + 7 X_C + 7 X_E1
+// - X_E2) with f_e = phi_e / (12 V), the west face -f_w (-X_W2 + 7 X_W1 + 7 X_C
+// - X_E1), likewise in z, and -mu L adds 2 mu (1/dx^2 + 1/dz^2) at the centre
+// and -mu/dx^2, -mu/dz^2 at the nearest neighbours; the Jacobi reciprocals of
+// the momentum (mu) and enthalpy (mu/Pr) diagonals; b = rho^n u^n / dt - G_cell^n
+// with G_cell the average of the two face forces grad p'^n - g z grad rho^n
+// per direction (zero on wall faces); the initial guess u^n.
+// acc += (b_u^2, b_w^2).
+__device__ __forceinline__ void ph_pred(const StepArgs &a, int bx, int bz, double (&acc)[2])
+{
+    const Geom &G = a.G;
+    const Phys &F = a.F;
+    int i, k;
+    if (!cell_of(G, bx, bz, i, k)) return;
+    const int q = cidx(G, i, k);
+    const State &S = a.S;
+    const double pw = ld(&S.phix[q]), pe = ld(&S.phix[q + 1]), ps = ld(&S.phiz[q]), pn = ld(&S.phiz[q + G.P]);
+    const double div = (pe - pw + pn - ps) * G.iV;
+    const double rq = ld(&S.rho[q]);
+    const double rho1 = rq - F.dt * div;
+    const double s12 = G.iV * (1.0 / 12.0);
+    const double fe = pe * s12, fw = pw * s12, fn = pn * s12, fs = ps * s12;
+    const double mx = F.mu * G.idx * G.idx, mz = F.mu * G.idz * G.idz;
+    const double cC = rho1 * F.idt + (7.0 / 12.0) * div + 2.0 * (mx + mz);
+    a.T.cC[q] = cC;
+    a.T.cE1[q] = fma(7.0, fe, fw) - mx;
+    a.T.cW1[q] = -fma(7.0, fw, fe) - mx;
+    a.T.cE2[q] = -fe;
+    a.T.cW2[q] = fw;
+    a.T.cN1[q] = fma(7.0, fn, fs) - mz;
+    a.T.cS1[q] = -fma(7.0, fs, fn) - mz;
+    a.T.cN2[q] = -fn;
+    a.T.cS2[q] = fs;
+    a.dinvu[q] = 1.0 / cC;
+    a.dinvh[q] = 1.0 / (cC + 2.0 * (F.nuh - F.mu) * (G.idx * G.idx + G.idz * G.idz));
+    const double z = (k + 0.5) * G.dz;
+    const double pq = ld(&S.pp[q]);
+    double gxw = 0.0, gxe = 0.0, gzs = 0.0, gzn = 0.0;
+    if (i > 0) gxw = (pq - ld(&S.pp[q - 1])) * G.idx - F.g * z * (rq - ld(&S.rho[q - 1])) * G.idx;
+    if (i + 1 < G.nx) gxe = (ld(&S.pp[q + 1]) - pq) * G.idx - F.g * z * (ld(&S.rho[q + 1]) - rq) * G.idx;
+    if (k > 0)
+        gzs = (pq - ld(&S.pp[q - G.P])) * G.idz - F.g * (k * G.dz) * (rq - ld(&S.rho[q - G.P])) * G.idz;
+    if (k + 1 < G.nz)
+        gzn = (ld(&S.pp[q + G.P]) - pq) * G.idz - F.g * ((k + 1) * G.dz) * (ld(&S.rho[q + G.P]) - rq) * G.idz;
+    const double u = ld(&S.u[q]), w = ld(&S.w[q]);
+    const double bu = rq * u * F.idt - 0.5 * (gxw + gxe);
+    const double bw = rq * w * F.idt - 0.5 * (gzs + gzn);
+    a.rho1[q] = rho1;
+    a.bu[q] = bu;
+    a.bw[q] = bw;
+    a.ua[q] = u;
+    a.wa[q] = w;
+    acc[0] = fma(bu, bu, acc[0]);
+    acc[1] = fma(bw, bw, acc[1]);
+}
+
+// One Jacobi sweep of T(X) = b for X = u (odd in x) and X = w (odd in z):
+// r = b - T(X), X <- X + r / T_CC. acc += (r_u^2, r_w^2).
+__device__ __forceinline__ void ph_mom(const StepArgs &a, const double *uin, const double *win,
+                                       double *uout, double *wout, double *sm, int bx, int bz,
+                                       double (&acc)[2])
+{
+    const Geom &G = a.G;
+    const Phys &F = a.F;
+    Tile<2> &su = tile_at<2>(sm, 0), &sw = tile_at<2>(sm, 1);
+    load_tile<BC_U, 2>(su, G, F, uin, bx, bz);
+    load_tile<BC_W, 2>(sw, G, F, win, bx, bz);
+    __syncthreads();
+    int i, k;
+    if (cell_of(G, bx, bz, i, k)) {
+        const int q = cidx(G, i, k);
+        const int y = threadIdx.y + 2, x = threadIdx.x + 2;
+        const double di = ld(&a.dinvu[q]);
+        const double ru = ld(&a.bu[q]) - apply9<2>(a.T, q, su, y, x);
+        const double rw = ld(&a.bw[q]) - apply9<2>(a.T, q, sw, y, x);
+        uout[q] = fma(ru, di, su[y][x]);
+        wout[q] = fma(rw, di, sw[y][x]);
+        acc[0] = fma(ru, ru, acc[0]);
+        acc[1] = fma(rw, rw, acc[1]);
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Step 2 (eq. step3_sd, step3_2sd, step3_3sd)
+// ---------------------------------------------------------------------------
+
+// Right-hand side of the enthalpy equation:
+//   (rho^n h^n + rho^n K^n - p^{n-1})/dt - rho1 K1/dt - C(K1) + p^n/dt - rho1 g w1
+// with K1 = |u^{n+1/3}|^2/2 (eq. step1_3sd); initial guess h^n (into h0).
+// acc += b_h^2.
+__device__ __forceinline__ void ph_enth_rhs(const StepArgs &a, const double *u1, const double *w1,
+                                            double *h0, double *sm, int bx, int bz, double (&acc)[1])
+{
+    const Geom &G = a.G;
+    const Phys &F = a.F;
+    Tile<2> &su = tile_at<2>(sm, 0), &sw = tile_at<2>(sm, 1);
+    load_tile<BC_U, 2>(su, G, F, u1, bx, bz);
+    load_tile<BC_W, 2>(sw, G, F, w1, bx, bz);
+    __syncthreads();
+    // K1 in place of u (ghost velocities give the mirrored cell's K); w1 at
+    // the cell centre is kept aside first
+    const double w1c = sw[threadIdx.y + 2][threadIdx.x + 2];
+    {
+        const int tid = threadIdx.x + threadIdx.y * BX;
+        for (int e = tid; e < kT2; e += NTHREADS) {
+            const int tk = e / (BX + 4), ti = e - tk * (BX + 4);
+            su[tk][ti] = 0.5 * (su[tk][ti] * su[tk][ti] + sw[tk][ti] * sw[tk][ti]);
+        }
+    }
+    __syncthreads();
+    int i, k;
+    if (cell_of(G, bx, bz, i, k)) {
+        const int q = cidx(G, i, k);
+        const State &S = a.S;
+        const int y = threadIdx.y + 2, x = threadIdx.x + 2;
+        const Tile<2> &K = su;
+        // convective sum of K1 with the four-point face values (wall faces
+        // carry phi = 0)
+        double c = ld(&S.phix[q + 1]) * (7.0 * (K[y][x] + K[y][x + 1]) - (K[y][x - 1] + K[y][x + 2]));
+        c -= ld(&S.phix[q]) * (7.0 * (K[y][x - 1] + K[y][x]) - (K[y][x - 2] + K[y][x + 1]));
+        c += ld(&S.phiz[q + G.P]) * (7.0 * (K[y][x] + K[y + 1][x]) - (K[y - 1][x] + K[y + 2][x]));
+        c -= ld(&S.phiz[q]) * (7.0 * (K[y - 1][x] + K[y][x]) - (K[y - 2][x] + K[y + 1][x]));
+        c *= G.iV * (1.0 / 12.0);
+        const double rq = ld(&S.rho[q]), u = ld(&S.u[q]), w = ld(&S.w[q]), h = ld(&S.h[q]);
+        const double Kn = 0.5 * (u * u + w * w);
+        const double rho1 = ld(&a.rho1[q]);
+        const double be = (rq * h + rq * Kn - ld(&S.pold[q])) * F.idt;
+        const double bh = be - rho1 * K[y][x] * F.idt - c + ld(&S.p[q]) * F.idt - rho1 * F.g * w1c;
+        a.bh[q] = bh;
+        h0[q] = h;
+        acc[0] = fma(bh, bh, acc[0]);
+    }
+    __syncthreads();
+}
+
+// One Jacobi sweep of (rho1/dt) h + C(h) - (mu/Pr) L(h) = b_h (dh/dz = -g on
+// the horizontal walls): the momentum stencil plus (mu - mu/Pr) L(h).
+// acc += r^2.
+__device__ __forceinline__ void ph_enth(const StepArgs &a, const double *hin, double *hout,
+                                        double *sm, int bx, int bz, double (&acc)[1])
+{
+    const Geom &G = a.G;
+    const Phys &F = a.F;
+    Tile<2> &sh = tile_at<2>(sm, 0);
+    load_tile<BC_H, 2>(sh, G, F, hin, bx, bz);
+    __syncthreads();
+    int i, k;
+    if (cell_of(G, bx, bz, i, k)) {
+        const int q = cidx(G, i, k);
+        const int y = threadIdx.y + 2, x = threadIdx.x + 2;
+        double t = apply9<2>(a.T, q, sh, y, x);
+        if (F.nuh != F.mu) t = fma(F.mu - F.nuh, lap5<2>(G, sh, y, x), t);
+        const double r = ld(&a.bh[q]) - t;
+        hout[q] = fma(r, ld(&a.dinvh[q]), sh[y][x]);
+        acc[0] = fma(r, r, acc[0]);
+    }
+    __syncthreads();
+}
+
+// T^{n+1} = T^n + (h^{n+1} - h^n)/cp; psi = 1/(R T^{n+1}); rho^{n+2/3} = p^n/(R T^{n+1})
+// (eq. step3_3sd); face coefficients D_f = dt rho2_f / rho1_f (linear face
+// averages); the fine Helmholtz operator c = psi/dt, a_f = D_f |A_f|/(V Delta_f),
+// d = c + sum a_f and omega/d. h1 holds h^{n+1}.
+__device__ __forceinline__ void ph_eos(const StepArgs &a, const Level &L, const double *h1,
+                                       double *sm, int bx, int bz)
+{
+    const Geom &G = a.G;
+    const Phys &F = a.F;
+    Tile<1> &s2 = tile_at<1>(sm, 0), &s1 = tile_at<1>(sm, 1);
+    double(*fx)[BX + 1] = reinterpret_cast<double(*)[BX + 1]>(sm + 2 * kT1);
+    double(*fz)[BX] = reinterpret_cast<double(*)[BX]>(sm + 2 * kT1 + BZ * (BX + 1));
+    const State &S = a.S;
+    const double icp = 1.0 / F.cp;
+    load_tile_fn<1>(s2, G, bx, bz, [&](int q, int, int) {
+        const double T1 = fma(ld(&h1[q]) - ld(&S.h[q]), icp, ld(&S.T[q]));
+        return ld(&S.p[q]) / (F.R * T1);
+    });
+    load_tile_fn<1>(s1, G, bx, bz, [&](int q, int, int) { return ld(&a.rho1[q]); });
+    __syncthreads();
+    int i, k;
+    const bool in = cell_of(G, bx, bz, i, k);
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int y = ty + 1, x = tx + 1;
+    const double ix2 = G.idx * G.idx, iz2 = G.idz * G.idz;
+    auto dface = [&](int ya, int xa, int yb, int xb) {
+        return F.dt * (0.5 * (s2[ya][xa] + s2[yb][xb])) / (0.5 * (s1[ya][xa] + s1[yb][xb]));
+    };
+    if (in) {
+        fx[ty][tx] = i > 0 ? dface(y, x - 1, y, x) : 0.0;
+        fz[ty][tx] = k > 0 ? dface(y - 1, x, y, x) : 0.0;
+        if (tx == BX - 1 || i == G.nx - 1) fx[ty][tx + 1] = i + 1 < G.nx ? dface(y, x, y, x + 1) : 0.0;
+        if (ty == BZ - 1 || k == G.nz - 1) fz[ty + 1][tx] = k + 1 < G.nz ? dface(y, x, y + 1, x) : 0.0;
+    }
+    __syncthreads();
+    if (in) {
+        const int q = cidx(G, i, k);
+        const double h1q = ld(&h1[q]);
+        const double T1 = fma(h1q - ld(&S.h[q]), icp, ld(&S.T[q]));
+        const double psi = 1.0 / (F.R * T1);
+        a.N.T[q] = T1;
+        a.N.h[q] = h1q;
+        a.rho2[q] = s2[y][x];
+        a.psi[q] = psi;
+        const double Dw = fx[ty][tx], De = fx[ty][tx + 1], Ds = fz[ty][tx], Dn = fz[ty + 1][tx];
+        a.Dx[k * G.P + i] = Dw;
+        a.Dz[k * G.P + i] = Ds;
+        L.ax[k * G.P + i] = Dw * ix2;
+        L.az[k * G.P + i] = Ds * iz2;
+        if (i == G.nx - 1) { a.Dx[k * G.P + G.nx] = 0.0; L.ax[k * G.P + G.nx] = 0.0; }
+        if (k == G.nz - 1) { a.Dz[G.nz * G.P + i] = 0.0; L.az[G.nz * G.P + i] = 0.0; }
+        const double c = psi * F.idt;
+        const double d = c + (Dw + De) * ix2 + (Ds + Dn) * iz2;
+        L.c[q] = c;
+        L.d[q] = d;
+        L.wd[q] = F.omega / d;
+    }
+    __syncthreads();
+}
+
+// Galerkin coarsening with piecewise-constant transfer: the coarse reaction
+// term averages the four fine ones, a coarse face coefficient is a quarter
+// of the sum of its two fine faces. (bx, bz) is a tile of the coarse level.
+__device__ __forceinline__ void ph_coarsen(const Level &f, const Level &c, double omega, int bx, int bz)
+{
+    const Geom &G = c.G;
+    int I, K;
+    if (!cell_of(G, bx, bz, I, K)) return;
+    const int Pf = f.G.P;
+    const int q00 = (2 * K) * Pf + 2 * I;
+    const int Q = cidx(G, I, K);
+    const double cc = 0.25 * (ld(&f.c[q00]) + ld(&f.c[q00 + 1]) + ld(&f.c[q00 + Pf]) + ld(&f.c[q00 + Pf + 1]));
+    const double aw = 0.25 * (ld(&f.ax[q00]) + ld(&f.ax[q00 + Pf]));
+    const double ae = 0.25 * (ld(&f.ax[q00 + 2]) + ld(&f.ax[q00 + Pf + 2]));
+    const double as = 0.25 * (ld(&f.az[q00]) + ld(&f.az[q00 + 1]));
+    const double an = 0.25 * (ld(&f.az[q00 + 2 * Pf]) + ld(&f.az[q00 + 2 * Pf + 1]));
+    c.c[Q] = cc;
+    c.ax[K * G.P + I] = aw;
+    c.az[K * G.P + I] = as;
+    if (I == G.nx - 1) c.ax[K * G.P + G.nx] = ae;
+    if (K == G.nz - 1) c.az[G.nz * G.P + I] = an;
+    const double d = cc + aw + ae + as + an;
+    c.d[Q] = d;
+    c.wd[Q] = omega / d;
+}
+
+// ---------------------------------------------------------------------------
+// Step 3: PISO corrector (eq. step2_sd second line, eq. p_prime_sd, step4_4sd)
+// ---------------------------------------------------------------------------
+
+// H(u) = rho^n u^n/dt - C(u) + mu L(u) = rho^n u^n/dt + (rho1/dt) u - T(u) at the
+// newest velocity.
+__device__ __forceinline__ void ph_H(const StepArgs &a, const double *U, const double *W, double *sm,
+                                     int bx, int bz)
+{
+    const Geom &G = a.G;
+    const Phys &F = a.F;
+    Tile<2> &su = tile_at<2>(sm, 0), &sw = tile_at<2>(sm, 1);
+    load_tile<BC_U, 2>(su, G, F, U, bx, bz);
+    load_tile<BC_W, 2>(sw, G, F, W, bx, bz);
+    __syncthreads();
+    int i, k;
+    if (cell_of(G, bx, bz, i, k)) {
+        const int q = cidx(G, i, k);
+        const int y = threadIdx.y + 2, x = threadIdx.x + 2;
+        const State &S = a.S;
+        const double rdt = ld(&S.rho[q]) * F.idt, r1dt = ld(&a.rho1[q]) * F.idt;
+        a.Hx[q] = fma(r1dt, su[y][x], fma(rdt, ld(&S.u[q]), -apply9<2>(a.T, q, su, y, x)));
+        a.Hz[q] = fma(r1dt, sw[y][x], fma(rdt, ld(&S.w[q]), -apply9<2>(a.T, q, sw, y, x)));
+    }
+    __syncthreads();
+}
+
+// Right-hand side of the pressure equation,
+//   b_i = (rho^n_i + psi_i rho2_i g z_i)/dt
+//         - (1/V) sum_f D_f |A_f| [H_f . n + g z_f (rho2_N - rho2_i)/Delta_f],
+// the initial residual r = b - A x (x = xin, copied to xout) and p0 = 0.
+// acc += (b^2, r^2).
+__device__ __forceinline__ void ph_helm_rhs(const StepArgs &a, const Level &L, const double *xin,
+                                            double *xout, double *sm, int bx, int bz,
+                                            double (&acc)[2])
+{
+    const Geom &G = a.G;
+    const Phys &F = a.F;
+    Tile<1> &sx = tile_at<1>(sm, 0), &s2 = tile_at<1>(sm, 1), &shx = tile_at<1>(sm, 2),
+            &shz = tile_at<1>(sm, 3);
+    load_tile_fn<1>(sx, G, bx, bz, [&](int q, int, int) { return ld(&xin[q]); });
+    load_tile_fn<1>(s2, G, bx, bz, [&](int q, int, int) { return ld(&a.rho2[q]); });
+    load_tile_fn<1>(shx, G, bx, bz, [&](int q, int, int) { return ld(&a.Hx[q]); });
+    load_tile_fn<1>(shz, G, bx, bz, [&](int q, int, int) { return ld(&a.Hz[q]); });
+    __syncthreads();
+    int i, k;
+    if (cell_of(G, bx, bz, i, k)) {
+        const int q = cidx(G, i, k);
+        const int y = threadIdx.y + 1, x = threadIdx.x + 1;
+        const double z = (k + 0.5) * G.dz;
+        const double r2q = s2[y][x];
+        const double Dw = ld(&a.Dx[k * G.P + i]), De = ld(&a.Dx[k * G.P + i + 1]);
+        const double Ds = ld(&a.Dz[k * G.P + i]), Dn = ld(&a.Dz[(k + 1) * G.P + i]);
+        // wall faces have D = 0 and zero tile entries beyond the box
+        double flux = De * G.dz * (0.5 * (shx[y][x] + shx[y][x + 1]) + F.g * z * (s2[y][x + 1] - r2q) * G.idx);
+        flux += Dw * G.dz * (-0.5 * (shx[y][x] + shx[y][x - 1]) + F.g * z * (s2[y][x - 1] - r2q) * G.idx);
+        flux += Dn * G.dx *
+                (0.5 * (shz[y][x] + shz[y + 1][x]) + F.g * ((k + 1) * G.dz) * (s2[y + 1][x] - r2q) * G.idz);
+        flux += Ds * G.dx *
+                (-0.5 * (shz[y][x] + shz[y - 1][x]) + F.g * (k * G.dz) * (s2[y - 1][x] - r2q) * G.idz);
+        const double b = (ld(&a.S.rho[q]) + ld(&a.psi[q]) * r2q * F.g * z) * F.idt - flux * G.iV;
+        const double r = b - helm_tile<1>(L, q, i, k, sx, y, x);
+        a.b[q] = b;
+        L.r[q] = r;
+        xout[q] = sx[y][x];
+        a.p0[q] = 0.0;
+        acc[0] = fma(b, b, acc[0]);
+        acc[1] = fma(r, r, acc[1]);
+    }
+    __syncthreads();
+}
+
+// ---- V-cycle ----
+
+// Restriction step of a level: pre-smooth with one damped Jacobi sweep from
+// zero, e = (omega/d) r, and restrict the new residual r - A e (= (1-omega) r +
+// sum a e_N) by averaging the four fine cells of each coarse cell. (bx, bz)
+// is a tile of the fine level, whose sizes are even.
+__device__ __forceinline__ void ph_mg_down(const Level &f, const Level &c, double omega, double *sm,
+                                           int bx, int bz)
+{
+    const Geom &G = f.G;
+    Tile<1> &se = tile_at<1>(sm, 0);
+    double(*sres)[BX] = reinterpret_cast<double(*)[BX]>(sm + kT1);
+    load_tile_fn<1>(se, G, bx, bz, [&](int q, int, int) { return ld(&f.wd[q]) * ld(&f.r[q]); });
+    __syncthreads();
+    int i, k;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    if (cell_of(G, bx, bz, i, k)) {
+        const int q = cidx(G, i, k);
+        const int y = ty + 1, x = tx + 1;
+        double t = (1.0 - omega) * ld(&f.r[q]);
+        t = fma(ld(&f.ax[k * G.P + i]), se[y][x - 1], t);
+        t = fma(ld(&f.ax[k * G.P + i + 1]), se[y][x + 1], t);
+        t = fma(ld(&f.az[k * G.P + i]), se[y - 1][x], t);
+        t = fma(ld(&f.az[(k + 1) * G.P + i]), se[y + 1][x], t);
+        f.e[q] = se[y][x];
+        sres[ty][tx] = t;
+    }
+    __syncthreads();
+    // one thread per coarse cell: all four of its fine cells are inside the
+    // box or all outside
+    if (tx < BX / 2 && ty < BZ / 2) {
+        const int I = bx * (BX / 2) + tx, K = bz * (BZ / 2) + ty;
+        if (I < c.G.nx && K < c.G.nz)
+            c.r[cidx(c.G, I, K)] = 0.25 * ((sres[2 * ty][2 * tx] + sres[2 * ty][2 * tx + 1]) +
+                                           (sres[2 * ty + 1][2 * tx] + sres[2 * ty + 1][2 * tx + 1]));
+    }
+    __syncthreads();
+}
+
+// Coarsest level: one damped Jacobi sweep (first = starts from zero).
+__device__ __forceinline__ void ph_mg_coarse(const Level &L, const double *ein, double *eout, int first,
+                                             double *sm, int bx, int bz)
+{
+    const Geom &G = L.G;
+    int i, k;
+    if (first) {
+        if (cell_of(G, bx, bz, i, k)) {
+            const int q = cidx(G, i, k);
+            eout[q] = ld(&L.wd[q]) * ld(&L.r[q]);
+        }
+        return;
+    }
+    Tile<1> &se = tile_at<1>(sm, 0);
+    load_tile_fn<1>(se, G, bx, bz, [&](int q, int, int) { return ld(&ein[q]); });
+    __syncthreads();
+    if (cell_of(G, bx, bz, i, k)) {
+        const int q = cidx(G, i, k);
+        const int y = threadIdx.y + 1, x = threadIdx.x + 1;
+        eout[q] = fma(ld(&L.wd[q]), ld(&L.r[q]) - helm_tile<1>(L, q, i, k, se, y, x), se[y][x]);
+    }
+    __syncthreads();
+}
+
+// Prolongation step of a level: e' = e + P e_c (piecewise constant), then one
+// damped Jacobi post-smoothing sweep e'' = e' + (omega/d)(r - A e'). At the
+// finest level the result is z = M^-1 r; acc += r.z.
+__device__ __forceinline__ void ph_mg_up(const Level &f, const double *ec, int Pc, double *out,
+                                         double *sm, int bx, int bz, double (&acc)[1])
+{
+    const Geom &G = f.G;
+    Tile<1> &se = tile_at<1>(sm, 0);
+    load_tile_fn<1>(se, G, bx, bz, [&](int q, int ii, int kk) {
+        return ld(&f.e[q]) + ld(&ec[(kk >> 1) * Pc + (ii >> 1)]);
+    });
+    __syncthreads();
+    int i, k;
+    if (cell_of(G, bx, bz, i, k)) {
+        const int q = cidx(G, i, k);
+        const int y = threadIdx.y + 1, x = threadIdx.x + 1;
+        const double rq = ld(&f.r[q]);
+        const double z = fma(ld(&f.wd[q]), rq - helm_tile<1>(f, q, i, k, se, y, x), se[y][x]);
+        out[q] = z;
+        acc[0] = fma(rq, z, acc[0]);
+    }
+    __syncthreads();
+}
+
+// Single-level preconditioner: two damped Jacobi sweeps from zero,
+// z = e + (omega/d)(r - A e) with e = (omega/d) r; acc += r.z.
+__device__ __forceinline__ void ph_mg_single(const Level &f, double *out, double *sm, int bx, int bz,
+                                             double (&acc)[1])
+{
+    const Geom &G = f.G;
+    Tile<1> &se = tile_at<1>(sm, 0);
+    load_tile_fn<1>(se, G, bx, bz, [&](int q, int, int) { return ld(&f.wd[q]) * ld(&f.r[q]); });
+    __syncthreads();
+    int i, k;
+    if (cell_of(G, bx, bz, i, k)) {
+        const int q = cidx(G, i, k);
+        const int y = threadIdx.y + 1, x = threadIdx.x + 1;
+        const double rq = ld(&f.r[q]);
+        const double z = fma(ld(&f.wd[q]), rq - helm_tile<1>(f, q, i, k, se, y, x), se[y][x]);
+        out[q] = z;
+        acc[0] = fma(rq, z, acc[0]);
+    }
+    __syncthreads();
+}
+
+// ---- CG vector steps ----
+
+// p_new = z + beta p_old (computed once per tile cell) and q = A p_new;
+// acc += p.q.
+__device__ __forceinline__ void ph_pspmv(const StepArgs &a, const Level &L, const double *pold,
+                                         double *pnew, double beta, double *sm, int bx, int bz,
+                                         double (&acc)[1])
+{
+    const Geom &G = a.G;
+    const double *z = L.e2;
+    Tile<1> &sp = tile_at<1>(sm, 0);
+    load_tile_fn<1>(sp, G, bx, bz, [&](int q, int, int) { return fma(beta, ld(&pold[q]), ld(&z[q])); });
+    __syncthreads();
+    int i, k;
+    if (cell_of(G, bx, bz, i, k)) {
+        const int q = cidx(G, i, k);
+        const int y = threadIdx.y + 1, x = threadIdx.x + 1;
+        const double pq = sp[y][x];
+        const double Ap = helm_tile<1>(L, q, i, k, sp, y, x);
+        pnew[q] = pq;
+        a.q[q] = Ap;
+        acc[0] = fma(pq, Ap, acc[0]);
+    }
+    __syncthreads();
+}
+
+// x += alpha p, r -= alpha q; acc += r^2.
+__device__ __forceinline__ void ph_update(const StepArgs &a, const Level &L, double *x, const double *p,
+                                          double alpha, int bx, int bz, double (&acc)[1])
+{
+    int i, k;
+    if (!cell_of(a.G, bx, bz, i, k)) return;
+    const int q = cidx(a.G, i, k);
+    x[q] = fma(alpha, ld(&p[q]), ld(&x[q]));
+    const double r = fma(-alpha, ld(&a.q[q]), ld(&L.r[q]));
+    L.r[q] = r;
+    acc[0] = fma(r, r, acc[0]);
+}
+
+// Flux and velocity correction: F_f = D_f (H_f - G_f) with
+// G_f = (p'_b - p'_a)/Delta - g z_f (rho2_b - rho2_a)/Delta; u = (dt/rho1)(H - G_cell);
+// p = p' - rho2 g z; rho = p / (R T^{n+1}) = p psi; phi = F |A|; p^{n-1} <- p^n.
+__device__ __forceinline__ void ph_correct(const StepArgs &a, double *sm, int bx, int bz)
+{
+    const Geom &G = a.G;
+    const Phys &F = a.F;
+    Tile<1> &sx = tile_at<1>(sm, 0), &s2 = tile_at<1>(sm, 1);
+    double(*gx)[BX + 1] = reinterpret_cast<double(*)[BX + 1]>(sm + 2 * kT1);
+    double(*gz)[BX] = reinterpret_cast<double(*)[BX]>(sm + 2 * kT1 + BZ * (BX + 1));
+    const State &N = a.N;
+    load_tile_fn<1>(sx, G, bx, bz, [&](int q, int, int) { return ld(&N.pp[q]); });
+    load_tile_fn<1>(s2, G, bx, bz, [&](int q, int, int) { return ld(&a.rho2[q]); });
+    __syncthreads();
+    int i, k;
+    const bool in = cell_of(G, bx, bz, i, k);
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int y = ty + 1, x = tx + 1;
+    const double z = (k + 0.5) * G.dz;
+    auto gxf = [&](int xa) {   // x-face between tile columns xa and xa+1 of row y
+        return (sx[y][xa + 1] - sx[y][xa]) * G.idx - F.g * z * (s2[y][xa + 1] - s2[y][xa]) * G.idx;
+    };
+    auto gzf = [&](int ya, int kf) {   // z-face between tile rows ya and ya+1, face index kf
+        return (sx[ya + 1][x] - sx[ya][x]) * G.idz - F.g * (kf * G.dz) * (s2[ya + 1][x] - s2[ya][x]) * G.idz;
+    };
+    if (in) {
+        gx[ty][tx] = i > 0 ? gxf(x - 1) : 0.0;
+        gz[ty][tx] = k > 0 ? gzf(y - 1, k) : 0.0;
+        if (tx == BX - 1 || i == G.nx - 1) gx[ty][tx + 1] = i + 1 < G.nx ? gxf(x) : 0.0;
+        if (ty == BZ - 1 || k == G.nz - 1) gz[ty + 1][tx] = k + 1 < G.nz ? gzf(y, k + 1) : 0.0;
+    }
+    __syncthreads();
+    if (in) {
+        const int q = cidx(G, i, k);
+        const double hxq = ld(&a.Hx[q]), hzq = ld(&a.Hz[q]);
+        const double gxw = gx[ty][tx], gxe = gx[ty][tx + 1], gzs = gz[ty][tx], gzn = gz[ty + 1][tx];
+        const double Fw = i > 0 ? ld(&a.Dx[k * G.P + i]) * (0.5 * (ld(&a.Hx[q - 1]) + hxq) - gxw) : 0.0;
+        const double Fs = k > 0 ? ld(&a.Dz[k * G.P + i]) * (0.5 * (ld(&a.Hz[q - G.P]) + hzq) - gzs) : 0.0;
+        N.phix[k * G.P + i] = Fw * G.dz;
+        N.phiz[k * G.P + i] = Fs * G.dx;
+        if (i == G.nx - 1) N.phix[k * G.P + G.nx] = 0.0;
+        if (k == G.nz - 1) N.phiz[G.nz * G.P + i] = 0.0;
+        const double dtr1 = F.dt / ld(&a.rho1[q]);
+        N.u[q] = dtr1 * (hxq - 0.5 * (gxw + gxe));
+        N.w[q] = dtr1 * (hzq - 0.5 * (gzs + gzn));
+        const double pn = fma(-s2[y][x] * F.g, z, sx[y][x]);
+        N.p[q] = pn;
+        N.rho[q] = pn * ld(&a.psi[q]);
+        N.pold[q] = ld(&a.S.p[q]);
+    }
+    __syncthreads();
+}
+
+// ---- what the block that completes a reduction does with the totals ----
+
+__device__ __forceinline__ void fin_pred(Scal *sc, const double (&t)[2])
+{
+    sc->bn2[0] = t[0];
+    sc->bn2[1] = t[1];
+    sc->done[LOOP_MOM] = 0;
+    sc->trips[LOOP_MOM] = 0;
+    sc->sweeps[0] = 0;
+}
+
+__device__ __forceinline__ void fin_mom(Scal *sc, const double (&t)[2], double tol2)
+{
+    sc->sweeps[0] += 1;
+    if (!isfinite(t[0]) || !isfinite(t[1])) sc->status = 5;
+    else if (t[0] <= tol2 * sc->bn2[0] && t[1] <= tol2 * sc->bn2[1]) sc->done[LOOP_MOM] = 1;
+}
+
+__device__ __forceinline__ void fin_enth_rhs(Scal *sc, const double (&t)[1])
+{
+    sc->bn2[2] = t[0];
+    sc->done[LOOP_ENTH] = 0;
+    sc->trips[LOOP_ENTH] = 0;
+    sc->sweeps[1] = 0;
+}
+
+__device__ __forceinline__ void fin_enth(Scal *sc, const double (&t)[1], double tol2)
+{
+    sc->sweeps[1] += 1;
+    if (!isfinite(t[0])) sc->status = 5;
+    else if (t[0] <= tol2 * sc->bn2[2]) sc->done[LOOP_ENTH] = 1;
+}
+
+__device__ __forceinline__ void fin_helm(Scal *sc, const double (&t)[2], double tol2, int corr)
+{
+    sc->b2 = t[0];
+    sc->r2 = t[1];
+    sc->cg_it = 0;
+    sc->corr = corr;
+    sc->trips[LOOP_CG] = 0;
+    sc->rz = 0.0;
+    sc->beta = 0.0;
+    sc->done[LOOP_CG] = t[1] <= tol2 * t[0];
+    sc->cg_iters[corr] = 0;
+    sc->cg_relres[corr] = t[0] > 0.0 ? sqrt(t[1] / t[0]) : 0.0;
+    if (!isfinite(t[0]) || !isfinite(t[1])) sc->status = 5;
+}
+
+__device__ __forceinline__ void fin_rz(Scal *sc, const double (&t)[1])
+{
+    sc->beta = (sc->cg_it == 0 || sc->rz == 0.0) ? 0.0 : t[0] / sc->rz;
+    sc->rz = t[0];
+}
+
+__device__ __forceinline__ void fin_pq(Scal *sc, const double (&t)[1])
+{
+    sc->pq = t[0];
+    sc->alpha = t[0] != 0.0 ? sc->rz / t[0] : 0.0;
+    if (!isfinite(t[0])) sc->status = 5;
+}
+
+__device__ __forceinline__ void fin_update(Scal *sc, const double (&t)[1], double tol2)
+{
+    const int it = sc->cg_it + 1;
+    sc->cg_it = it;
+    sc->r2 = t[0];
+    const int c = sc->corr;
+    sc->cg_iters[c] = it;
+    sc->cg_relres[c] = sc->b2 > 0.0 ? sqrt(t[0] / sc->b2) : 0.0;
+    if (!isfinite(t[0])) sc->status = 5;
+    else if (t[0] <= tol2 * sc->b2) sc->done[LOOP_CG] = 1;
+}
+
+}  // namespace tiles
+}  // namespace gea

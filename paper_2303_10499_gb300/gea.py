@@ -111,13 +111,15 @@ def _is_device(a) -> bool:
 class Solver:
     """One context of the library: a grid, its constants and device state."""
 
-    def __init__(self, grid, const, mg_min_cells: int = 0, stream=None):
+    def __init__(self, grid, const, mg_min_cells: int = 0, stream=None, graph: bool = False):
+        """graph=True runs each step as a CUDA graph of per-phase kernels
+        instead of the persistent cooperative kernel (GEA_FLAG_GRAPH)."""
         self.lib = library()
         self.grid, self.const = grid, const
         g = _Grid(grid.nx, grid.nz, grid.lx, grid.lz)
         c = _Const(const.R, const.cp, const.g, const.p0, const.mu, const.Pr, const.dt,
                    const.n_corr, const.jac_rtol, const.jac_maxit, const.cg_rtol, const.cg_maxit,
-                   mg_min_cells, 0)
+                   mg_min_cells, 1 if graph else 0)
         h = C.c_void_p()
         rc = self.lib.gea_create(C.byref(g), C.byref(c), C.byref(h))
         if rc != GEA_OK:
