@@ -50,6 +50,8 @@ KERNEL_MODEL = {
     "mg_single": (6, 15),
     "cg_pspmv": (7, 13.5),
     "cg_update": (6, 6),
+    "cg_update_single": (11, 22),
+    "cg_update_down": (10.25, 18),
     "correct": (16, 38),
 }
 
@@ -63,8 +65,8 @@ def parse():
     ap.add_argument("--workload", default="bubble640x320")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--graph", action="store_true",
-                    help="step through the CUDA graph of per-phase kernels instead of the "
-                         "persistent cooperative kernel")
+                    help="always step through the CUDA graph of per-phase kernels (default: the "
+                         "library picks the persistent kernel on small grids)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle baseline sample")
     return ap.parse_args()
@@ -141,45 +143,75 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def traffic_for(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source (else None)."""
+def kernels_sha256():
+    """Hash of the CUDA sources (any change invalidates recorded counters)."""
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2303_10499_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(f.encode())
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()
+
+
+def traffic_for(kernel, workload):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu
+    summary (profiles/traffic.json), if it was taken on the current CUDA
+    sources (else None)."""
     try:
         t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-        src = open(os.path.join(ROOT, "paper_2303_10499_gb300", "csrc", "gea_kernels.cu"), "rb").read()
-        if t.get("kernels_sha256") != hashlib.sha256(src).hexdigest():
+        if t.get("kernels_sha256") != kernels_sha256():
             return None
-        return t.get("per_launch_bytes", {}).get(kernel)
+        return t.get("per_launch_bytes", {}).get(workload, {}).get(kernel)
     except Exception:
         return None
 
 
-def roofline(prof, pk):
-    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
-    name, d = dom
-    words, flops = KERNEL_MODEL.get(name, (0, 0))
-    cells_per_launch = d["cells"] / d["launches"]
-    t = d["ms"] / d["launches"] * 1e-3
-    gbs = words * 8 * cells_per_launch / t / 1e9
-    tfl = flops * cells_per_launch / t / 1e12
-    t_hbm = words * 8 * cells_per_launch / (pk["hbm_gbs"] * 1e9)
-    t_alu = flops * cells_per_launch / (pk["fp64_tflops"] * 1e12)
+def step_model(prof):
+    """Algorithmic FP64 words and operations of one step: the per-cell model
+    of each phase times the cells its launches covered in the profiled step
+    (the same iteration counts as a timed step, up to the state's drift)."""
+    words = sum(KERNEL_MODEL.get(k, (0, 0))[0] * v["cells"] for k, v in prof.items())
+    flops = sum(KERNEL_MODEL.get(k, (0, 0))[1] * v["cells"] for k, v in prof.items())
+    return words * 8.0, flops
+
+
+def roofline(prof, pk, ms_per_step, persistent, workload):
     total = sum(v["ms"] for v in prof.values())
     share = {k: round(v["ms"] / total, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
-    if t_alu >= t_hbm:
+    step_bytes, step_flops = step_model(prof)
+    if persistent:
+        # the timed region runs one kernel, the persistent step kernel, once
+        # per step: its duration is the event-timed step
+        name, launches, per_launch_ms = "k_persistent (whole step)", 1, ms_per_step
+        bytes_l, flops_l = step_bytes, step_flops
+    else:
+        name, d = max(prof.items(), key=lambda kv: kv[1]["ms"])
+        words, flops = KERNEL_MODEL.get(name, (0, 0))
+        launches = d["launches"]
+        per_launch_ms = d["ms"] / d["launches"]
+        cells = d["cells"] / d["launches"]
+        bytes_l, flops_l = words * 8 * cells, flops * cells
+    t = per_launch_ms * 1e-3
+    gbs = bytes_l / t / 1e9
+    tfl = flops_l / t / 1e12
+    if flops_l / (pk["fp64_tflops"] * 1e12) >= bytes_l / (pk["hbm_gbs"] * 1e9):
         out = {"bound": "alu", "achieved": tfl, "peak": pk["fp64_tflops"], "unit": "TFLOP/s",
                "frac": tfl / pk["fp64_tflops"],
-               "peak_source": "FP64 nominal 1.25 TFLOP/s (GB300, no FP64 entry in the measured peaks)"}
+               "peak_source": "FP64 nominal 1.25 TFLOP/s of GB300 (152 SMs x 2 FP64 FMA lanes x "
+                              "2 flops x ~2.06 GHz; 1.20 measured by an FMA-chain probe); "
+                              "the measured peaks file has no FP64 entry"}
     else:
         out = {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
                "frac": gbs / pk["hbm_gbs"], "peak_source": f"{pk['src']} hbm_gbs"}
-    out.update({"kernel": name, "launches_per_step": d["launches"],
-                "avg_launch_ms": d["ms"] / d["launches"],
-                "algorithmic_bytes_per_launch": words * 8 * cells_per_launch,
-                "algorithmic_flops_per_launch": flops * cells_per_launch,
+    out.update({"kernel": name, "launches_per_step": launches, "avg_launch_ms": per_launch_ms,
+                "algorithmic_bytes_per_launch": bytes_l, "algorithmic_flops_per_launch": flops_l,
                 "hbm_gbs_achieved": gbs, "fp64_tflops_achieved": tfl,
-                "traffic": traffic_for(name), "kernel_share_of_step": share,
-                "timing": "CUDA events around each launch of one eager step on the solver stream"})
+                "traffic": traffic_for(name.split()[0], workload),
+                "phase_share_of_eager_step": share,
+                "timing": ("CUDA events around each timed step on the solver stream"
+                           if persistent else
+                           "CUDA events around each launch of one eager step on the solver stream")})
     return out
 
 
@@ -245,7 +277,7 @@ def run_ours(args):
         pms.append(s.pressure_ms())
     prof = s.profile_step()
     pk = peaks()
-    roof = roofline(prof, pk)
+    roof = roofline(prof, pk, statistics.mean(ms), st["driver"] == "persistent", wl.name)
 
     # end to end through the C ABI with host buffers: H2D of the full state,
     # one step, D2H of the full state, every step
@@ -275,7 +307,7 @@ def run_ours(args):
                    "n_corr": wl.const.n_corr, "jac_rtol": wl.const.jac_rtol,
                    "cg_rtol": wl.const.cg_rtol, "mg_levels": st["mg_levels"],
                    "l2": "flushed between timed steps (256 MB write, untimed)",
-                   "driver": "cuda-graph" if args.graph else "persistent-cooperative-kernel",
+                   "driver": st["driver"],
                    "parallelism": f"replicas x{world}"},
         "pressure_solve_ms_per_step": statistics.mean(pms),
         "cg_iters_last_step": st["cg_iters"], "jacobi_sweeps_last_step": [st["jac_u"], st["jac_h"]],

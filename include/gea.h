@@ -84,10 +84,11 @@ typedef struct gea_grid {
  *            2 dt^2 R T (1/dx^2 + 1/dz^2) at T = 300 K, is below 0.3 (the
  *            coarse levels are then nearly diagonal). > 0: until a level has
  *            at most this many cells (a value >= nx*nz gives one level).
- *  flags     GEA_FLAG_GRAPH: run steps as a CUDA graph of per-phase kernels
- *            instead of the default persistent cooperative kernel (the
- *            graph path is also used when a cooperative launch of the grid
- *            is not possible). Other bits must be 0. */
+ *  flags     GEA_FLAG_GRAPH: always run steps as a CUDA graph of per-phase
+ *            kernels. By default the library picks the persistent
+ *            cooperative kernel when the grid has at most 4 tiles (32 x 8
+ *            cells) per block that fits on the GPU at once, where a phase is
+ *            latency-bound, and the graph otherwise. Other bits must be 0. */
 typedef struct gea_constants {
     double R, cp, g, p0, mu, Pr, dt;
     int32_t n_corr;
@@ -121,6 +122,8 @@ typedef struct gea_stats {
     int32_t status;            /* GEA_OK or the first device-side error */
     int32_t mg_levels;         /* multigrid levels in use */
     int64_t launches;          /* kernel launches since the last set_state */
+    int32_t driver;            /* 1: persistent cooperative kernel, 0: CUDA graph */
+    int32_t reserved;
 } gea_stats;
 
 typedef struct gea_ctx gea_ctx;
@@ -148,9 +151,10 @@ int gea_set_state(gea_ctx *ctx, const gea_state_view *v);
  * are enqueued and the status of the finished steps has been read back,
  * i.e. it synchronises the stream once at the end. On GEA_ERR_NOCONV,
  * GEA_ERR_NONFINITE or GEA_ERR_TIMEOUT the state stays at the last completed
- * step. By default all n steps run in one cooperative kernel launch whose
- * blocks stay resident (grid barriers between phases, solver loops on the
- * device); with GEA_FLAG_GRAPH each step is one CUDA graph launch. */
+ * step. With the persistent driver all n steps run in one cooperative kernel
+ * launch whose blocks stay resident (grid barriers between phases, solver
+ * loops on the device); with the graph driver each step is one CUDA graph
+ * launch (see gea_constants.flags). */
 int gea_step(gea_ctx *ctx, int32_t n);
 
 /* Enqueue n steps without waiting; gea_sync reports their status. */

@@ -117,8 +117,9 @@ constexpr double kOmega = 0.8;     // smoother weight
 // operator is small against its diagonal psi/dt: with D ~ dt and psi ~ 1/(RT),
 // sum_f a_f / c ~ 2 dt^2 R T (1/dx^2 + 1/dz^2), and every coarsening divides
 // it by 4. Coarsening continues while the ratio exceeds this bound.
-constexpr double kCoarsestRatio = 0.3;
+constexpr double kCoarsestRatio = 1.0;
 constexpr double kRefT = 300.0;    // reference temperature of that estimate (K)
+constexpr int kPersistTilesPerBlock = 4;
 
 // Append a WHILE conditional node to the graph being captured on `s`; its
 // body is captured from body(body_stream, handle, true).
@@ -202,7 +203,7 @@ int record_step(gea_ctx *ctx, int from, cudaStream_t s, bool graph, Tracer *tr)
     launch_eos_coef(a, L[0], s, tr); ++fixed;
     for (int l = 0; l + 1 < nlev; ++l) { launch_mg_coarsen(L[l], L[l + 1], kOmega, s, tr); ++fixed; }
     // Step 3: PISO correctors
-    const int body_cg = (nlev == 1 ? 1 : 2 * (nlev - 1) + kCoarseSweeps) + 2 + 1;
+    const int body_cg = (nlev == 1 ? 2 : 2 + (nlev - 2) + kCoarseSweeps + (nlev - 1)) + 1;
     for (int c = 0; c < ctx->C.n_corr; ++c) {
         const double *U = c == 0 ? a.ua : a.N.u;
         const double *W = c == 0 ? a.wa : a.N.w;
@@ -212,9 +213,9 @@ int record_step(gea_ctx *ctx, int from, cudaStream_t s, bool graph, Tracer *tr)
         CK(graph ? cudaEventRecordWithFlags(ctx->ev[2 * c], s, cudaEventRecordExternal)
                  : cudaEventRecord(ctx->ev[2 * c], s));
         launch_helm_rhs(a, L[0], c == 0 ? a.S.pp : a.N.pp, a.N.pp, c, s, tr); ++fixed;
+        fixed += launch_vcycle(a, L, nlev, kCoarseSweeps, s, tr);   // z = M^-1 r_0
         rc = loop(LOOP_CG, ctx->C.cg_maxit, [&](cudaStream_t bs, cudaGraphConditionalHandle h, bool g) {
-            launch_vcycle(a, L, nlev, kCoarseSweeps, bs, tr);
-            launch_cg_iter_tail(a, L[0], a.N.pp, bs, tr);
+            launch_cg_iter(a, L, nlev, kCoarseSweeps, a.N.pp, bs, tr);
             launch_loop_ctl(a.sc, h, g, LOOP_CG, ctx->C.cg_maxit, body_cg, bs, tr);
         });
         if (rc) return rc;
@@ -358,7 +359,7 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
     total += 33 * cell + 2 * fz;                   // scratch (Dz has nz+1 rows)
     total += 4 * cell;                             // staging for conservative fields
     total += 2 * cell + round_up(G.nz * sizeof(double), 256);   // theta_bar, theta'
-    for (const Geom &g : lg) total += 7 * arr_bytes(g, g.nz) + arr_bytes(g, g.nz + 1);
+    for (const Geom &g : lg) total += 8 * arr_bytes(g, g.nz) + arr_bytes(g, g.nz + 1);
     const size_t nb = (size_t)max_blocks(G);
     total += round_up(4 * nb * sizeof(double), 256);
     total += round_up(sizeof(Scal), 256);
@@ -394,7 +395,7 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
         l.G = g;
         const size_t lc = arr_bytes(g, g.nz), lf = arr_bytes(g, g.nz + 1);
         l.c = take(lc); l.d = take(lc); l.wd = take(lc); l.ax = take(lc); l.az = take(lf);
-        l.r = take(lc); l.e = take(lc); l.e2 = take(lc);
+        l.r = take(lc); l.e = take(lc); l.e2 = take(lc); l.r_alt = take(lc);
         ctx->L.push_back(l);
     }
     ctx->partials = take(round_up(4 * nb * sizeof(double), 256));
@@ -405,10 +406,14 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
     }
     for (int e = 0; e < 8; ++e) cudaEventCreate(&ctx->ev[e]);
     ctx->nev = 8;
+    // step driver: the persistent kernel pays off while a phase is a few
+    // tiles per resident block (its phases are latency-bound); on larger
+    // grids the per-phase kernels keep more blocks resident per SM
     if (!(c->flags & GEA_FLAG_GRAPH)) {
         const int pmax = persistent_max_blocks();
-        ctx->pers_blocks = pmax < (int)nb ? pmax : (int)nb;
         cudaGetLastError();
+        if (pmax > 0 && (long long)nb <= (long long)kPersistTilesPerBlock * pmax)
+            ctx->pers_blocks = pmax < (int)nb ? pmax : (int)nb;
     }
     if (cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&ctx->cap2, cudaStreamNonBlocking) != cudaSuccess ||
@@ -586,6 +591,7 @@ int gea_get_stats(gea_ctx *ctx, gea_stats *s)
     s->status = h.last_status;
     s->mg_levels = (int)ctx->L.size();
     s->launches = h.launches;
+    s->driver = ctx->pers_blocks > 0 ? 1 : 0;
     return GEA_OK;
 }
 

@@ -46,7 +46,15 @@ struct Level {
     Geom G;
     double *c, *d, *wd, *ax, *az;  // reaction, diagonal, omega/diagonal, face coefficients
     double *r, *e, *e2;            // residual, pre-smoothed correction, post-smoothed
+    double *r_alt;                 // finest level: second residual buffer (CG iterations
+                                   // alternate r and r_alt; the update reads one, writes the other)
 };
+
+// Finest-level residual after `it` CG updates.
+__host__ __device__ __forceinline__ double *res_of(const Level &L, int it)
+{
+    return (it & 1) ? L.r_alt : L.r;
+}
 
 // The implicit transport operator of Steps 1-2,
 //   T(X)_i = (rho1/dt) X_i + C(X)_i - mu L(X)_i,
@@ -233,8 +241,8 @@ void launch_helm_rhs(const StepArgs &a, const Level &L0, const double *xin, doub
 // returns the number of kernels launched
 int launch_vcycle(const StepArgs &a, Level *levels, int nlev, int ncoarse, cudaStream_t st,
                   Tracer *tr);
-int launch_cg_iter_tail(const StepArgs &a, const Level &L0, double *x, cudaStream_t st,
-                        Tracer *tr);
+int launch_cg_iter(const StepArgs &a, Level *levels, int nlev, int ncoarse, double *x,
+                   cudaStream_t st, Tracer *tr);
 void launch_correct(const StepArgs &a, cudaStream_t st, Tracer *tr);
 // graph: set the WHILE condition through h; otherwise bookkeeping only
 void launch_loop_ctl(Scal *sc, cudaGraphConditionalHandle h, bool graph, int which,

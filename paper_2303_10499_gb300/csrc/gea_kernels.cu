@@ -150,7 +150,9 @@ __global__ void k_mg_up(Level f, const double *ec, int Pc, double *out, int fine
     __shared__ double sm[kT1];
     __shared__ double red[NTHREADS];
     double acc[1] = {0.0}, tot[1];
-    ph_mg_up(f, ec, Pc, out, sm, blockIdx.x, blockIdx.y, acc);
+    // the finest level's residual alternates between two buffers
+    const double *res = finest ? res_of(f, a.sc->cg_it) : f.r;
+    ph_mg_up(f, res, ec, Pc, out, sm, blockIdx.x, blockIdx.y, acc);
     if (!finest) return;
     if (grid_sum<1>(acc, red, a.partials, &a.sc->counters[CNT_RZ], tot)) fin_rz(a.sc, tot);
 }
@@ -190,6 +192,38 @@ __global__ void k_cg_update(StepArgs a, Level L, double *x)
     const double *p = (it & 1) ? a.p0 : a.p1;
     double acc[1] = {0.0}, tot[1];
     ph_update(a, L, x, p, sc->alpha, blockIdx.x, blockIdx.y, acc);
+    if (grid_sum<1>(acc, red, a.partials, &sc->counters[CNT_UPD], tot)) fin_update(sc, tot, a.cg_rtol2);
+}
+
+__global__ void k_cg_update_single(StepArgs a, Level L, double *x)
+{
+    Scal *sc = a.sc;
+    if (loop_over(sc, LOOP_CG)) return;
+    __shared__ double sm[2 * kT1];
+    __shared__ double red[2 * NTHREADS];
+    const int it = sc->cg_it;
+    const double *p = (it & 1) ? a.p0 : a.p1;
+    double acc[2] = {0.0, 0.0}, tot[2];
+    ph_update_single(a, L, res_of(L, it), res_of(L, it + 1), x, p, sc->alpha, sm, blockIdx.x,
+                     blockIdx.y, acc);
+    if (grid_sum<2>(acc, red, a.partials, &sc->counters[CNT_UPD], tot)) {
+        const double t0[1] = {tot[0]}, t1[1] = {tot[1]};
+        fin_update(sc, t0, a.cg_rtol2);
+        fin_rz(sc, t1);
+    }
+}
+
+__global__ void k_cg_update_down(StepArgs a, Level f, Level c, double *x)
+{
+    Scal *sc = a.sc;
+    if (loop_over(sc, LOOP_CG)) return;
+    __shared__ double sm[2 * kT1 + BZ * BX];
+    __shared__ double red[NTHREADS];
+    const int it = sc->cg_it;
+    const double *p = (it & 1) ? a.p0 : a.p1;
+    double acc[1] = {0.0}, tot[1];
+    ph_update_down(a, f, c, res_of(f, it), res_of(f, it + 1), x, p, sc->alpha, a.F.omega, sm,
+                   blockIdx.x, blockIdx.y, acc);
     if (grid_sum<1>(acc, red, a.partials, &sc->counters[CNT_UPD], tot)) fin_update(sc, tot, a.cg_rtol2);
 }
 
@@ -363,11 +397,45 @@ int launch_vcycle(const StepArgs &a, Level *L, int nlev, int ncoarse, cudaStream
     return n;
 }
 
-int launch_cg_iter_tail(const StepArgs &a, const Level &L0, double *x, cudaStream_t st, Tracer *tr)
+// V-cycle levels below the finest: restriction steps of levels 1..nlev-2,
+// the coarsest sweeps and the prolongation steps down to the finest (which
+// yields z and r.z). Returns the number of kernels launched.
+static int launch_vcycle_rest(const StepArgs &a, Level *L, int nlev, int ncoarse, cudaStream_t st,
+                              Tracer *tr)
 {
-    TRACED(tr, "cg_pspmv", ncell(a.G), (k_cg_pspmv<<<grid_of(a.G), kBlock, 0, st>>>(a, L0)));
-    TRACED(tr, "cg_update", ncell(a.G), (k_cg_update<<<grid_of(a.G), kBlock, 0, st>>>(a, L0, x)));
-    return 2;
+    int n = 0;
+    for (int l = 1; l + 1 < nlev; ++l, ++n)
+        TRACED(tr, "mg_down", ncell(L[l].G),
+               (k_mg_down<<<grid_of(L[l].G), kBlock, 0, st>>>(L[l], L[l + 1], a.F.omega, a.sc)));
+    Level &C = L[nlev - 1];
+    for (int s = 0; s < ncoarse; ++s, ++n) {
+        double *out = ((ncoarse - 1 - s) % 2 == 0) ? C.e2 : C.e;
+        const double *in = (out == C.e2) ? C.e : C.e2;
+        TRACED(tr, "mg_coarse", ncell(C.G),
+               (k_mg_coarse_sweep<<<grid_of(C.G), kBlock, 0, st>>>(C, in, out, s == 0, a.sc)));
+    }
+    for (int l = nlev - 2; l >= 0; --l, ++n)
+        TRACED(tr, "mg_up", ncell(L[l].G),
+               (k_mg_up<<<grid_of(L[l].G), kBlock, 0, st>>>(L[l], L[l + 1].e2, L[l + 1].G.P, L[l].e2,
+                                                             l == 0, a)));
+    return n;
+}
+
+// One CG iteration after the first preconditioning: p = z + beta p and q = A p;
+// x, r updated together with the first step of the next V-cycle; the rest of
+// the V-cycle. Returns the number of kernels launched.
+int launch_cg_iter(const StepArgs &a, Level *L, int nlev, int ncoarse, double *x, cudaStream_t st,
+                   Tracer *tr)
+{
+    TRACED(tr, "cg_pspmv", ncell(a.G), (k_cg_pspmv<<<grid_of(a.G), kBlock, 0, st>>>(a, L[0])));
+    if (nlev == 1) {
+        TRACED(tr, "cg_update_single", ncell(a.G),
+               (k_cg_update_single<<<grid_of(a.G), kBlock, 0, st>>>(a, L[0], x)));
+        return 2;
+    }
+    TRACED(tr, "cg_update_down", ncell(a.G),
+           (k_cg_update_down<<<grid_of(a.G), kBlock, 0, st>>>(a, L[0], L[1], x)));
+    return 2 + launch_vcycle_rest(a, L, nlev, ncoarse, st, tr);
 }
 
 void launch_correct(const StepArgs &a, cudaStream_t st, Tracer *tr)

@@ -222,34 +222,41 @@ __device__ bool run_step(const PersistArgs &P, const StepArgs &a, double *sm, do
             for_tiles(G, [&](int bx, int bz) { ph_helm_rhs(a, L[0], xin, a.N.pp, sm, bx, bz, acc); });
             rbar<2>(acc, red, sc, a.partials, [&](const double (&t)[2]) { fin_helm(sc, t, a.cg_rtol2, c); });
         }
-        while (!stop(sc) && !rdi(&sc->done[LOOP_CG])) {
-            // z = M^-1 r: one V(1,1)-cycle
+        // z = M^-1 r_0 (one V(1,1)-cycle), then the iterations
+        auto vcycle_levels = [&](int lfirst) {
+            for (int l = lfirst; l + 1 < nlev; ++l) {
+                for_tiles(L[l].G, [&](int bx, int bz) { ph_mg_down(L[l], L[l + 1], a.F.omega, sm, bx, bz); });
+                gbar(sc);
+            }
+            const Level &C = L[nlev - 1];
+            for (int s = 0; s < P.ncoarse; ++s) {
+                double *out = ((P.ncoarse - 1 - s) % 2 == 0) ? C.e2 : C.e;
+                const double *in = (out == C.e2) ? C.e : C.e2;
+                for_tiles(C.G, [&](int bx, int bz) { ph_mg_coarse(C, in, out, s == 0, sm, bx, bz); });
+                gbar(sc);
+            }
+            const double *res0 = res_of(L[0], rdi(&sc->cg_it));
+            for (int l = nlev - 2; l >= 0; --l) {
+                double acc[1] = {0.0};
+                const double *res = l == 0 ? res0 : L[l].r;
+                for_tiles(L[l].G, [&](int bx, int bz) {
+                    ph_mg_up(L[l], res, L[l + 1].e2, L[l + 1].G.P, L[l].e2, sm, bx, bz, acc);
+                });
+                if (l > 0) gbar(sc);
+                else rbar<1>(acc, red, sc, a.partials, [&](const double (&t)[1]) { fin_rz(sc, t); });
+            }
+        };
+        if (!stop(sc) && !rdi(&sc->done[LOOP_CG])) {
             if (nlev == 1) {
                 double acc[1] = {0.0};
                 for_tiles(G, [&](int bx, int bz) { ph_mg_single(L[0], L[0].e2, sm, bx, bz, acc); });
                 rbar<1>(acc, red, sc, a.partials, [&](const double (&t)[1]) { fin_rz(sc, t); });
             } else {
-                for (int l = 0; l + 1 < nlev; ++l) {
-                    for_tiles(L[l].G, [&](int bx, int bz) { ph_mg_down(L[l], L[l + 1], a.F.omega, sm, bx, bz); });
-                    gbar(sc);
-                }
-                const Level &C = L[nlev - 1];
-                for (int s = 0; s < P.ncoarse; ++s) {
-                    double *out = ((P.ncoarse - 1 - s) % 2 == 0) ? C.e2 : C.e;
-                    const double *in = (out == C.e2) ? C.e : C.e2;
-                    for_tiles(C.G, [&](int bx, int bz) { ph_mg_coarse(C, in, out, s == 0, sm, bx, bz); });
-                    gbar(sc);
-                }
-                for (int l = nlev - 2; l >= 0; --l) {
-                    double acc[1] = {0.0};
-                    for_tiles(L[l].G, [&](int bx, int bz) {
-                        ph_mg_up(L[l], L[l + 1].e2, L[l + 1].G.P, L[l].e2, sm, bx, bz, acc);
-                    });
-                    if (l > 0) gbar(sc);
-                    else rbar<1>(acc, red, sc, a.partials, [&](const double (&t)[1]) { fin_rz(sc, t); });
-                }
+                vcycle_levels(0);
             }
-            // p = z + beta p, q = A p; then x, r
+        }
+        while (!stop(sc) && !rdi(&sc->done[LOOP_CG])) {
+            // p = z + beta p, q = A p
             const int it = rdi(&sc->cg_it);
             const double *pold = (it & 1) ? a.p1 : a.p0;
             double *pnew = (it & 1) ? a.p0 : a.p1;
@@ -259,14 +266,34 @@ __device__ bool run_step(const PersistArgs &P, const StepArgs &a, double *sm, do
                 for_tiles(G, [&](int bx, int bz) { ph_pspmv(a, L[0], pold, pnew, beta, sm, bx, bz, acc); });
                 rbar<1>(acc, red, sc, a.partials, [&](const double (&t)[1]) { fin_pq(sc, t); });
             }
-            {
-                const double alpha = rdd(&sc->alpha);
+            // x += alpha p, r -= alpha q, with the first step of the next V-cycle
+            const double alpha = rdd(&sc->alpha);
+            auto cap = [&] {
+                if (!sc->done[LOOP_CG] && !sc->status && sc->cg_it >= P.cg_maxit) sc->status = GEA_ERR_NOCONV;
+            };
+            if (nlev == 1) {
+                double acc[2] = {0.0, 0.0};
+                for_tiles(G, [&](int bx, int bz) {
+                    ph_update_single(a, L[0], res_of(L[0], it), res_of(L[0], it + 1), a.N.pp, pnew, alpha,
+                                     sm, bx, bz, acc);
+                });
+                rbar<2>(acc, red, sc, a.partials, [&](const double (&t)[2]) {
+                    const double t0[1] = {t[0]}, t1[1] = {t[1]};
+                    fin_update(sc, t0, a.cg_rtol2);
+                    fin_rz(sc, t1);
+                    cap();
+                });
+            } else {
                 double acc[1] = {0.0};
-                for_tiles(G, [&](int bx, int bz) { ph_update(a, L[0], a.N.pp, pnew, alpha, bx, bz, acc); });
+                for_tiles(G, [&](int bx, int bz) {
+                    ph_update_down(a, L[0], L[1], res_of(L[0], it), res_of(L[0], it + 1), a.N.pp, pnew,
+                                   alpha, a.F.omega, sm, bx, bz, acc);
+                });
                 rbar<1>(acc, red, sc, a.partials, [&](const double (&t)[1]) {
                     fin_update(sc, t, a.cg_rtol2);
-                    if (!sc->done[LOOP_CG] && !sc->status && sc->cg_it >= P.cg_maxit) sc->status = GEA_ERR_NOCONV;
+                    cap();
                 });
+                if (!stop(sc) && !rdi(&sc->done[LOOP_CG])) vcycle_levels(1);
             }
         }
         if (stop(sc)) return false;

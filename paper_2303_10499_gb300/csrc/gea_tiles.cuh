@@ -548,8 +548,8 @@ __device__ __forceinline__ void ph_mg_coarse(const Level &L, const double *ein, 
 // Prolongation step of a level: e' = e + P e_c (piecewise constant), then one
 // damped Jacobi post-smoothing sweep e'' = e' + (omega/d)(r - A e'). At the
 // finest level the result is z = M^-1 r; acc += r.z.
-__device__ __forceinline__ void ph_mg_up(const Level &f, const double *ec, int Pc, double *out,
-                                         double *sm, int bx, int bz, double (&acc)[1])
+__device__ __forceinline__ void ph_mg_up(const Level &f, const double *res, const double *ec, int Pc,
+                                         double *out, double *sm, int bx, int bz, double (&acc)[1])
 {
     const Geom &G = f.G;
     Tile<1> &se = tile_at<1>(sm, 0);
@@ -561,7 +561,7 @@ __device__ __forceinline__ void ph_mg_up(const Level &f, const double *ec, int P
     if (cell_of(G, bx, bz, i, k)) {
         const int q = cidx(G, i, k);
         const int y = threadIdx.y + 1, x = threadIdx.x + 1;
-        const double rq = ld(&f.r[q]);
+        const double rq = ld(&res[q]);
         const double z = fma(ld(&f.wd[q]), rq - helm_tile<1>(f, q, i, k, se, y, x), se[y][x]);
         out[q] = z;
         acc[0] = fma(rq, z, acc[0]);
@@ -627,6 +627,99 @@ __device__ __forceinline__ void ph_update(const StepArgs &a, const Level &L, dou
     const double r = fma(-alpha, ld(&a.q[q]), ld(&L.r[q]));
     L.r[q] = r;
     acc[0] = fma(r, r, acc[0]);
+}
+
+// x += alpha p and r -= alpha q, fused with the first step of the next
+// V-cycle on the new residual (a CG iteration then needs one grid-wide
+// synchronisation less): the new residual and e = (omega/d) r_new are formed
+// on the tile and its halo from the old r and q in one pass.
+__device__ __forceinline__ void update_tiles(const StepArgs &a, const Level &L, const double *rin,
+                                             double alpha, Tile<1> &sr, Tile<1> &se, int bx, int bz)
+{
+    const Geom &G = L.G;
+    const int i0 = bx * BX - 1, k0 = bz * BZ - 1;
+    const int tid = threadIdx.x + threadIdx.y * BX;
+    constexpr int W = BX + 2, NE = (BZ + 2) * (BX + 2);
+    for (int e = tid; e < NE; e += NTHREADS) {
+        const int tk = e / W, ti = e - tk * W;
+        const int i = i0 + ti, k = k0 + tk;
+        double rn = 0.0, ev = 0.0;
+        if (i >= 0 && i < G.nx && k >= 0 && k < G.nz) {
+            const int q = k * G.P + i;
+            rn = fma(-alpha, ld(&a.q[q]), ld(&rin[q]));
+            ev = ld(&L.wd[q]) * rn;
+        }
+        sr[tk][ti] = rn;
+        se[tk][ti] = ev;
+    }
+}
+
+// The residual is read from rin (halo included) and written to rout: other
+// blocks still read the old residual while this one writes the new.
+// Single-level preconditioner: then z = e + (omega/d)(r_new - A e);
+// acc += (r_new^2, r_new . z).
+__device__ __forceinline__ void ph_update_single(const StepArgs &a, const Level &L, const double *rin,
+                                                 double *rout, double *x, const double *p,
+                                                 double alpha, double *sm, int bx, int bz,
+                                                 double (&acc)[2])
+{
+    const Geom &G = L.G;
+    Tile<1> &sr = tile_at<1>(sm, 0), &se = tile_at<1>(sm, 1);
+    update_tiles(a, L, rin, alpha, sr, se, bx, bz);
+    __syncthreads();
+    int i, k;
+    if (cell_of(G, bx, bz, i, k)) {
+        const int q = cidx(G, i, k);
+        const int y = threadIdx.y + 1, xx = threadIdx.x + 1;
+        const double rn = sr[y][xx];
+        x[q] = fma(alpha, ld(&p[q]), ld(&x[q]));
+        rout[q] = rn;
+        const double z = fma(ld(&L.wd[q]), rn - helm_tile<1>(L, q, i, k, se, y, xx), se[y][xx]);
+        L.e2[q] = z;
+        acc[0] = fma(rn, rn, acc[0]);
+        acc[1] = fma(rn, z, acc[1]);
+    }
+    __syncthreads();
+}
+
+// Multigrid preconditioner: then the restriction step of the finest level
+// (pre-smoothed e and the averaged residual (1-omega) r_new + sum a e_N into
+// the next level); acc += r_new^2.
+__device__ __forceinline__ void ph_update_down(const StepArgs &a, const Level &f, const Level &c,
+                                               const double *rin, double *rout, double *x,
+                                               const double *p, double alpha, double omega,
+                                               double *sm, int bx, int bz, double (&acc)[1])
+{
+    const Geom &G = f.G;
+    Tile<1> &sr = tile_at<1>(sm, 0), &se = tile_at<1>(sm, 1);
+    double(*sres)[BX] = reinterpret_cast<double(*)[BX]>(sm + 2 * kT1);
+    update_tiles(a, f, rin, alpha, sr, se, bx, bz);
+    __syncthreads();
+    int i, k;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    if (cell_of(G, bx, bz, i, k)) {
+        const int q = cidx(G, i, k);
+        const int y = ty + 1, xx = tx + 1;
+        const double rn = sr[y][xx];
+        x[q] = fma(alpha, ld(&p[q]), ld(&x[q]));
+        rout[q] = rn;
+        double t = (1.0 - omega) * rn;
+        t = fma(ld(&f.ax[k * G.P + i]), se[y][xx - 1], t);
+        t = fma(ld(&f.ax[k * G.P + i + 1]), se[y][xx + 1], t);
+        t = fma(ld(&f.az[k * G.P + i]), se[y - 1][xx], t);
+        t = fma(ld(&f.az[(k + 1) * G.P + i]), se[y + 1][xx], t);
+        f.e[q] = se[y][xx];
+        sres[ty][tx] = t;
+        acc[0] = fma(rn, rn, acc[0]);
+    }
+    __syncthreads();
+    if (tx < BX / 2 && ty < BZ / 2) {
+        const int I = bx * (BX / 2) + tx, K = bz * (BZ / 2) + ty;
+        if (I < c.G.nx && K < c.G.nz)
+            c.r[cidx(c.G, I, K)] = 0.25 * ((sres[2 * ty][2 * tx] + sres[2 * ty][2 * tx + 1]) +
+                                           (sres[2 * ty + 1][2 * tx] + sres[2 * ty + 1][2 * tx + 1]));
+    }
+    __syncthreads();
 }
 
 // Flux and velocity correction: F_f = D_f (H_f - G_f) with

@@ -54,7 +54,8 @@ class _View(C.Structure):
 class _Stats(C.Structure):
     _fields_ = [("steps_done", C.c_int64), ("jac_u", C.c_int32), ("jac_h", C.c_int32),
                 ("cg_iters", C.c_int32 * 4), ("cg_relres", C.c_double * 4),
-                ("status", C.c_int32), ("mg_levels", C.c_int32), ("launches", C.c_int64)]
+                ("status", C.c_int32), ("mg_levels", C.c_int32), ("launches", C.c_int64),
+                ("driver", C.c_int32), ("reserved", C.c_int32)]
 
 
 class _KTime(C.Structure):
@@ -214,7 +215,8 @@ class Solver:
         n = self.const.n_corr
         return {"steps_done": s.steps_done, "jac_u": s.jac_u, "jac_h": s.jac_h,
                 "cg_iters": list(s.cg_iters)[:n], "cg_relres": list(s.cg_relres)[:n],
-                "status": s.status, "mg_levels": s.mg_levels, "launches": s.launches}
+                "status": s.status, "mg_levels": s.mg_levels, "launches": s.launches,
+                "driver": "persistent" if s.driver == 1 else "graph"}
 
     def field(self, name: str) -> np.ndarray:
         nx, nz = self.grid.nx, self.grid.nz

@@ -257,6 +257,7 @@ def test_persistent_and_graph_paths_agree(gea):
         s = gea.Solver(wl.grid, wl.const, graph=graph)
         s.set_conservative(wl.fields)
         s.step(20)
+        assert s.stats()["driver"] == ("graph" if graph else "persistent")
         out.append(s.get_full())
     for k in ("rho", "T", "pp"):
         assert np.abs(out[0][k] - out[1][k]).max() <= 1e-13 * np.abs(out[1][k]).max(), k
