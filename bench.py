@@ -31,28 +31,44 @@ if ROOT not in sys.path:
 METRIC = "cell-steps/sec and pressure-solve ms/step vs plain FP64 GPU at matched error"
 UNIT = "cell-steps/s"
 
-# Algorithmic traffic and arithmetic per cell of one launch: FP64 words read
-# once plus written once, and FP64 operations (add, mul, div, sqrt each 1;
-# an FMA counts 2). Coarse-level multigrid kernels are per cell of the level
-# they run on. Derivations are in the design notes.
+# Algorithmic traffic and arithmetic per cell of one launch: 8-byte words read
+# once plus written once (an FP32 value is half a word), and operations (add,
+# mul, div, sqrt each 1; an FMA counts 2) in the precision named last.
+# Coarse-level multigrid kernels are per cell of the level they run on.
+# Derivations are in the design notes. The mx_ kernels are the
+# mixed-precision step.
 KERNEL_MODEL = {
-    "pred_setup": (22, 66),
-    "mom_jacobi": (16, 44),
-    "enth_rhs": (13, 41),
-    "enth_jacobi": (13, 22),
-    "eos_coef": (16, 33),
-    "mg_coarsen": (17, 18),
-    "H": (17, 44),
-    "helm_rhs": (15, 51),
-    "mg_down": (5.25, 11.5),
-    "mg_coarse": (7, 6.5),
-    "mg_up": (7.25, 15),
-    "mg_single": (6, 15),
-    "cg_pspmv": (7, 13.5),
-    "cg_update": (6, 6),
-    "cg_update_single": (11, 22),
-    "cg_update_down": (10.25, 18),
-    "correct": (16, 38),
+    "pred_setup": (22, 66, "f64"),
+    "mom_jacobi": (16, 44, "f64"),
+    "enth_rhs": (13, 41, "f64"),
+    "enth_jacobi": (13, 22, "f64"),
+    "eos_coef": (16, 33, "f64"),
+    "mg_coarsen": (17, 18, "f64"),
+    "H": (17, 44, "f64"),
+    "helm_rhs": (15, 51, "f64"),
+    "mg_down": (5.25, 11.5, "f64"),
+    "mg_coarse": (7, 6.5, "f64"),
+    "mg_up": (7.25, 15, "f64"),
+    "mg_single": (6, 15, "f64"),
+    "cg_pspmv": (7, 13.5, "f64"),
+    "cg_update_single": (11, 22, "f64"),
+    "cg_update_down": (10.25, 18, "f64"),
+    "correct": (16, 38, "f64"),
+    "mx_pred": (23.5, 104, "f64"),
+    "mx_mom": (8, 46, "f32"),
+    "mx_enth_rhs": (23.5, 70, "f64"),
+    "mx_enth": (6.5, 31, "f32"),
+    "mx_eos": (18, 33, "f64"),
+    "mx_coarsen": (8.5, 18, "f32"),
+    "mx_helm_rhs": (14.5, 51, "f64"),
+    "mx_mg_down": (2.625, 11.5, "f32"),
+    "mx_mg_coarse": (3.5, 6.5, "f32"),
+    "mx_mg_up": (3.625, 15, "f32"),
+    "mx_mg_single": (3, 15, "f32"),
+    "mx_pspmv": (3.5, 13.5, "f32"),
+    "mx_update_single": (5.5, 22, "f32"),
+    "mx_update_down": (5.125, 18, "f32"),
+    "mx_p_apply": (2.5, 1, "f64"),
 }
 
 
@@ -67,13 +83,18 @@ def parse():
     ap.add_argument("--graph", action="store_true",
                     help="always step through the CUDA graph of per-phase kernels (default: the "
                          "library picks the persistent kernel on small grids)")
+    ap.add_argument("--mixed", action="store_true",
+                    help="time the mixed-precision step (FP32 inner solves) on the main line; by "
+                         "default it is timed beside the FP64 step under 'mixed_precision'")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle baseline sample")
     return ap.parse_args()
 
 
 def peaks():
-    p = {"hbm_gbs": 6800.0, "fp64_tflops": 1.25, "src": "fallback"}
+    # FP64 and FP32 issue rates are nominal (the measured peaks file has
+    # neither): 152 SMs x (2 FP64 | 128 FP32) FMA lanes x 2 flops x 2.07 GHz
+    p = {"hbm_gbs": 6800.0, "fp64_tflops": 1.25, "fp32_tflops": 80.5, "src": "fallback"}
     try:
         m = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
         p["hbm_gbs"] = float(m["hbm_gbs"])
@@ -171,8 +192,8 @@ def step_model(prof):
     """Algorithmic FP64 words and operations of one step: the per-cell model
     of each phase times the cells its launches covered in the profiled step
     (the same iteration counts as a timed step, up to the state's drift)."""
-    words = sum(KERNEL_MODEL.get(k, (0, 0))[0] * v["cells"] for k, v in prof.items())
-    flops = sum(KERNEL_MODEL.get(k, (0, 0))[1] * v["cells"] for k, v in prof.items())
+    words = sum(KERNEL_MODEL.get(k, (0, 0, ""))[0] * v["cells"] for k, v in prof.items())
+    flops = sum(KERNEL_MODEL.get(k, (0, 0, ""))[1] * v["cells"] for k, v in prof.items())
     return words * 8.0, flops
 
 
@@ -180,6 +201,7 @@ def roofline(prof, pk, ms_per_step, persistent, workload):
     total = sum(v["ms"] for v in prof.values())
     share = {k: round(v["ms"] / total, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
     step_bytes, step_flops = step_model(prof)
+    prec = "f64"
     if persistent:
         # the timed region runs one kernel, the persistent step kernel, once
         # per step: its duration is the event-timed step
@@ -187,7 +209,7 @@ def roofline(prof, pk, ms_per_step, persistent, workload):
         bytes_l, flops_l = step_bytes, step_flops
     else:
         name, d = max(prof.items(), key=lambda kv: kv[1]["ms"])
-        words, flops = KERNEL_MODEL.get(name, (0, 0))
+        words, flops, prec = KERNEL_MODEL.get(name, (0, 0, "f64"))
         launches = d["launches"]
         per_launch_ms = d["ms"] / d["launches"]
         cells = d["cells"] / d["launches"]
@@ -195,12 +217,15 @@ def roofline(prof, pk, ms_per_step, persistent, workload):
     t = per_launch_ms * 1e-3
     gbs = bytes_l / t / 1e9
     tfl = flops_l / t / 1e12
-    if flops_l / (pk["fp64_tflops"] * 1e12) >= bytes_l / (pk["hbm_gbs"] * 1e9):
-        out = {"bound": "alu", "achieved": tfl, "peak": pk["fp64_tflops"], "unit": "TFLOP/s",
-               "frac": tfl / pk["fp64_tflops"],
-               "peak_source": "FP64 nominal 1.25 TFLOP/s of GB300 (152 SMs x 2 FP64 FMA lanes x "
-                              "2 flops x ~2.06 GHz; 1.20 measured by an FMA-chain probe); "
-                              "the measured peaks file has no FP64 entry"}
+    alu = pk["fp64_tflops"] if prec == "f64" else pk["fp32_tflops"]
+    if flops_l / (alu * 1e12) >= bytes_l / (pk["hbm_gbs"] * 1e9):
+        out = {"bound": "alu", "achieved": tfl, "peak": alu, "unit": "TFLOP/s",
+               "frac": tfl / alu,
+               "peak_source": ("FP64 nominal 1.25 TFLOP/s of GB300 (152 SMs x 2 FP64 FMA lanes x "
+                               "2 flops x ~2.06 GHz; 1.20 measured by an FMA-chain probe)"
+                               if prec == "f64" else
+                               "FP32 nominal 80.5 TFLOP/s (152 SMs x 128 FP32 lanes x 2 x 2.07 GHz)")
+                              + "; the measured peaks file has no entry for this precision"}
     else:
         out = {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
                "frac": gbs / pk["hbm_gbs"], "peak_source": f"{pk['src']} hbm_gbs"}
@@ -215,8 +240,69 @@ def roofline(prof, pk, ms_per_step, persistent, workload):
     return out
 
 
-def run_ours(args):
+def timed_steps(s, stream, flush, steps, warmup, world, local):
+    """warmup untimed steps, then `steps` steps each bracketed by CUDA events
+    on the solver stream, L2 flushed before each. Returns per-step ms, the
+    launches counted by the library and the sampled clocks."""
+    import torch
+    for _ in range(warmup):
+        s.step_async(1)
+    s.sync()
+    l0 = s.stats()["launches"]
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    clk = ClockSampler(local)
+    clk.start()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for e0, e1 in evs:
+        flush.zero_()
+        e0.record(stream)
+        s.step_async(1)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = clk.stop()
+    s.sync()
+    launches = s.stats()["launches"] - l0
+    return [e0.elapsed_time(e1) for e0, e1 in evs], launches, clocks
+
+
+def pressure_ms(s):
+    """Pressure-solve time per step (events around the solves inside the step)."""
+    pms = []
+    for _ in range(5):
+        s.step(1)
+        pms.append(s.pressure_ms())
+    return statistics.mean(pms)
+
+
+def matched_error(gea, wl, steps):
+    """The mixed-precision step against the FP64 step, both on this GPU from
+    the initial state: max |theta'| difference (K) and relative L2 of the
+    conservative fields (momenta against the momentum vector) after `steps`
+    steps."""
     import numpy as np
+    out = []
+    for mixed in (False, True):
+        s = gea.Solver(wl.grid, wl.const, mixed=mixed)
+        s.set_conservative(wl.fields)
+        s.step(steps)
+        th, _, _ = s.diagnostics(wl.theta_bar)
+        out.append((s.get_conservative(), th))
+        s.close()
+    (c64, th64), (c32, th32) = out
+    m = np.hypot(np.linalg.norm(c64["rhou"]), np.linalg.norm(c64["rhow"]))
+    rel = {k: float(np.linalg.norm(c32[k] - c64[k]) / np.linalg.norm(c64[k])) for k in ("rho", "rhoe")}
+    rel.update({k: float(np.linalg.norm(c32[k] - c64[k]) / m) for k in ("rhou", "rhow")})
+    return {"steps": steps, "max_abs_dtheta_K": float(np.abs(th32 - th64).max()),
+            "rel_l2": rel, "against": "FP64 GPU step (equal to the FP64 oracle to <= 1e-10 rel. L2)"}
+
+
+def run_ours(args):
     import torch
     from paper_2303_10499_gb300 import build as B
     from paper_2303_10499_gb300 import gea
@@ -234,35 +320,12 @@ def run_ours(args):
     wl = W.get(args.workload)
     cells = wl.grid.cells
     stream = torch.cuda.current_stream()
-    s = gea.Solver(wl.grid, wl.const, stream=stream, graph=args.graph)
+    s = gea.Solver(wl.grid, wl.const, stream=stream, graph=args.graph, mixed=args.mixed)
     dev = {k: torch.from_numpy(v).cuda() for k, v in wl.fields.items()}
     s.set_conservative(dev)
-    for _ in range(args.warmup):
-        s.step_async(1)
-    s.sync()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-    l0 = s.stats()["launches"]
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    clk = ClockSampler(local)
-    clk.start()
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    for e0, e1 in evs:
-        flush.zero_()
-        e0.record(stream)
-        s.step_async(1)
-        e1.record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    clocks = clk.stop()
-    s.sync()
+    ms, launches, clocks = timed_steps(s, stream, flush, args.steps, args.warmup, world, local)
     st = s.stats()
-    launches = st["launches"] - l0
-    ms = [e0.elapsed_time(e1) for e0, e1 in evs]
     tot_s = sum(ms) / 1e3
     if world > 1:
         t = torch.tensor([tot_s], device="cuda", dtype=torch.float64)
@@ -270,11 +333,7 @@ def run_ours(args):
         tot_s = float(t.item())
     value = world * cells * args.steps / tot_s
 
-    # pressure-solve time per step (events inside the step graph)
-    pms = []
-    for _ in range(5):
-        s.step(1)
-        pms.append(s.pressure_ms())
+    pms = pressure_ms(s)
     prof = s.profile_step()
     pk = peaks()
     roof = roofline(prof, pk, statistics.mean(ms), st["driver"] == "persistent", wl.name)
@@ -297,11 +356,13 @@ def run_ours(args):
     e2e = {"value": world * cells * ne / t_e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes,
            "d2h_bytes_per_step": nbytes,
            "path": "gea_set_state(FULL, host) + gea_step(1) + gea_get_state(FULL, host)"}
+    s.close()
 
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": statistics.mean(ms), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if args.mixed else "f64",
+        "data": "synthetic",
         "config": {"workload": wl.name, "grid": [nx, nz], "cells": cells,
                    "domain_m": [wl.grid.lx, wl.grid.lz], "dt": wl.const.dt,
                    "n_corr": wl.const.n_corr, "jac_rtol": wl.const.jac_rtol,
@@ -309,11 +370,36 @@ def run_ours(args):
                    "l2": "flushed between timed steps (256 MB write, untimed)",
                    "driver": st["driver"],
                    "parallelism": f"replicas x{world}"},
-        "pressure_solve_ms_per_step": statistics.mean(pms),
+        "pressure_solve_ms_per_step": pms,
         "cg_iters_last_step": st["cg_iters"], "jacobi_sweeps_last_step": [st["jac_u"], st["jac_h"]],
         "ms_per_step_min": min(ms), "ms_per_step_median": statistics.median(ms),
         "gpu_launches": int(launches) * world, "clocks": clocks, "e2e": e2e, "roofline": roof,
     }
+    if not args.mixed:
+        # the mixed-precision step timed the same way, with its error against
+        # the FP64 step at 100 steps
+        sm = gea.Solver(wl.grid, wl.const, stream=stream, mixed=True)
+        sm.set_conservative(dev)
+        ms_m, launches_m, clocks_m = timed_steps(sm, stream, flush, args.steps, args.warmup, world,
+                                                 local)
+        st_m = sm.stats()
+        tot_m = sum(ms_m) / 1e3
+        if world > 1:
+            t = torch.tensor([tot_m], device="cuda", dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            tot_m = float(t.item())
+        pms_m = pressure_ms(sm)
+        sm.close()
+        value_m = world * cells * args.steps / tot_m
+        res["mixed_precision"] = {
+            "value": value_m, "unit": UNIT, "ms_per_step": statistics.mean(ms_m),
+            "pressure_solve_ms_per_step": pms_m, "speedup_vs_fp64": value_m / value,
+            "pressure_speedup_vs_fp64": pms / pms_m if pms_m > 0 else None,
+            "cg_iters_last_step": st_m["cg_iters"],
+            "jacobi_sweeps_last_step": [st_m["jac_u"], st_m["jac_h"]],
+            "gpu_launches": int(launches_m) * world, "clocks": clocks_m, "driver": st_m["driver"],
+            "error_vs_fp64": matched_error(gea, wl, 100) if rank == 0 else None,
+        }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
     if world > 1:

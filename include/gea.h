@@ -54,7 +54,7 @@ enum {
 };
 
 enum { GEA_STATE_CONSERVATIVE = 0, GEA_STATE_FULL = 1 };
-enum { GEA_FLAG_GRAPH = 1 };
+enum { GEA_FLAG_GRAPH = 1, GEA_FLAG_MIXED = 2 };
 enum { GEA_MEM_HOST = 0, GEA_MEM_DEVICE = 1 };
 
 /* Uniform Cartesian grid: nx * nz cells on [0, lx] x [0, lz] (metres).
@@ -81,14 +81,26 @@ typedef struct gea_grid {
  *  mg_min_cells  the multigrid preconditioner coarsens by 2 in x and z
  *            while both sizes are even and >= 8. 0 (default): until the
  *            estimated Laplacian-to-diagonal ratio of the pressure operator,
- *            2 dt^2 R T (1/dx^2 + 1/dz^2) at T = 300 K, is below 0.3 (the
+ *            2 dt^2 R T (1/dx^2 + 1/dz^2) at T = 300 K, is at most 1 (the
  *            coarse levels are then nearly diagonal). > 0: until a level has
  *            at most this many cells (a value >= nx*nz gives one level).
  *  flags     GEA_FLAG_GRAPH: always run steps as a CUDA graph of per-phase
  *            kernels. By default the library picks the persistent
  *            cooperative kernel when the grid has at most 4 tiles (32 x 8
  *            cells) per block that fits on the GPU at once, where a phase is
- *            latency-bound, and the graph otherwise. Other bits must be 0. */
+ *            latency-bound, and the graph otherwise.
+ *            GEA_FLAG_MIXED: mixed-precision step (CUDA graph driver). The
+ *            state, the hydrostatic split p' = p + rho g z, the face forces,
+ *            every right-hand side and H(u) stay FP64; each of the three
+ *            linear solves becomes one defect correction: an FP64 residual
+ *            r0 = b - A x_old, an FP32 solve A dx = r0 (Jacobi, or multigrid
+ *            CG for the pressure) to ||r|| <= mp_rtol ||r0||, and the FP64
+ *            update x = x_old + dx. The pressure solve is skipped when
+ *            ||r0|| <= cg_rtol ||b||. jac_maxit and cg_maxit cap the FP32
+ *            iterations; gea_stats.cg_relres is then relative to ||r0||.
+ *            Other bits must be 0.
+ *  mp_rtol   relative tolerance of the FP32 solves (GEA_FLAG_MIXED only);
+ *            0 selects 1e-5, otherwise 1e-7 <= mp_rtol < 1. */
 typedef struct gea_constants {
     double R, cp, g, p0, mu, Pr, dt;
     int32_t n_corr;
@@ -98,6 +110,7 @@ typedef struct gea_constants {
     int32_t cg_maxit;
     int32_t mg_min_cells;
     int32_t flags;
+    double mp_rtol;
 } gea_constants;
 
 /* A view of caller-owned buffers (host or device, per mem). The library
@@ -122,7 +135,8 @@ typedef struct gea_stats {
     int32_t status;            /* GEA_OK or the first device-side error */
     int32_t mg_levels;         /* multigrid levels in use */
     int64_t launches;          /* kernel launches since the last set_state */
-    int32_t driver;            /* 1: persistent cooperative kernel, 0: CUDA graph */
+    int32_t driver;            /* 0: CUDA graph, 1: persistent cooperative kernel,
+                                  2: mixed-precision CUDA graph */
     int32_t reserved;
 } gea_stats;
 

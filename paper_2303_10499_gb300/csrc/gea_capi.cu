@@ -37,7 +37,10 @@ struct gea_ctx {
     double *stage;                         // staging for conservative set/get (4 fields)
     double *thbar;                         // nz values
     double *thout;                         // theta' output
-    std::vector<Level> L;
+    std::vector<Level> L;                 // FP64 hierarchy (mixed precision: the finest level only)
+    bool mixed = false;                   // GEA_FLAG_MIXED
+    MixedArgs mx{};                       // FP32 buffers of the mixed-precision step
+    std::vector<LevelF> Lf;               // FP32 hierarchy of the mixed-precision step
     Scal *sc = nullptr;
     double *partials = nullptr;
     cudaGraph_t graph[2] = {nullptr, nullptr};
@@ -90,6 +93,7 @@ Geom make_geom(int nx, int nz, double lx, double lz)
 
 // bytes of one pitched array with `rows` rows
 size_t arr_bytes(const Geom &G, int rows) { return round_up((size_t)G.P * rows * sizeof(double), 256); }
+size_t arr_bytes_f(const Geom &G, int rows) { return round_up((size_t)G.P * rows * sizeof(float), 256); }
 
 StepArgs step_args(gea_ctx *c, int from)
 {
@@ -120,6 +124,7 @@ constexpr double kOmega = 0.8;     // smoother weight
 constexpr double kCoarsestRatio = 1.0;
 constexpr double kRefT = 300.0;    // reference temperature of that estimate (K)
 constexpr int kPersistTilesPerBlock = 4;
+constexpr double kMixedRtol = 1e-5;  // default tolerance of the FP32 solves (relative to ||r0||)
 
 // Append a WHILE conditional node to the graph being captured on `s`; its
 // body is captured from body(body_stream, handle, true).
@@ -187,16 +192,16 @@ int record_step(gea_ctx *ctx, int from, cudaStream_t s, bool graph, Tracer *tr)
     // Step 1: continuity predictor and implicit momentum predictor
     launch_pred_setup(a, s, tr); ++fixed;
     rc = loop(LOOP_MOM, jtrips, [&](cudaStream_t bs, cudaGraphConditionalHandle h, bool g) {
-        launch_mom_jacobi(a, a.ua, a.wa, a.ub, a.wb, bs, tr);
-        launch_mom_jacobi(a, a.ub, a.wb, a.ua, a.wa, bs, tr);
+        launch_mom_jacobi(a, a.ua, a.wa, a.ub, a.wb, 0, bs, tr);
+        launch_mom_jacobi(a, a.ub, a.wb, a.ua, a.wa, 1, bs, tr);
         launch_loop_ctl(a.sc, h, g, LOOP_MOM, jtrips, 3, bs, tr);
     });
     if (rc) return rc;
     // Step 2: enthalpy, temperature, rho^{n+2/3}
     launch_enth_rhs(a, s, tr); ++fixed;
     rc = loop(LOOP_ENTH, jtrips, [&](cudaStream_t bs, cudaGraphConditionalHandle h, bool g) {
-        launch_enth_jacobi(a, a.ha, a.hb, bs, tr);
-        launch_enth_jacobi(a, a.hb, a.ha, bs, tr);
+        launch_enth_jacobi(a, a.ha, a.hb, 0, bs, tr);
+        launch_enth_jacobi(a, a.hb, a.ha, 1, bs, tr);
         launch_loop_ctl(a.sc, h, g, LOOP_ENTH, jtrips, 3, bs, tr);
     });
     if (rc) return rc;
@@ -228,11 +233,76 @@ int record_step(gea_ctx *ctx, int from, cudaStream_t s, bool graph, Tracer *tr)
     return GEA_OK;
 }
 
+// The mixed-precision step: the same phases, with the three linear solves
+// done as FP64 residual + FP32 solve for the increment + FP64 update. The
+// increments du, dw (Step 1) and dh (Step 2) run their Jacobi sweeps in
+// pairs that end in du[0], dw[0], dh[0]; the pressure increment accumulates
+// in mx.x and is added to p' before the correction.
+int record_step_mixed(gea_ctx *ctx, int from, cudaStream_t s, bool graph, Tracer *tr)
+{
+    StepArgs a = step_args(ctx, from);
+    const MixedArgs &m = ctx->mx;
+    Level &L0 = ctx->L[0];
+    LevelF *Lf = ctx->Lf.data();
+    const int nlev = (int)ctx->Lf.size();
+    const int jtrips = (ctx->C.jac_maxit + 1) / 2;
+    int fixed = 0;
+    int rc = GEA_OK;
+    auto loop = [&](int which, int maxtrips, auto body) {
+        return graph ? capture_while(ctx, s, body) : eager_while(ctx, s, which, maxtrips, body);
+    };
+
+    launch_step_begin(ctx->sc, s, tr); ++fixed;
+    launch_mx_pred(a, m, s, tr); ++fixed;
+    rc = loop(LOOP_MOM, jtrips, [&](cudaStream_t bs, cudaGraphConditionalHandle h, bool g) {
+        launch_mx_mom(a, m, m.du[0], m.dw[0], m.du[1], m.dw[1], 0, bs, tr);
+        launch_mx_mom(a, m, m.du[1], m.dw[1], m.du[0], m.dw[0], 1, bs, tr);
+        launch_loop_ctl(a.sc, h, g, LOOP_MOM, jtrips, 3, bs, tr);
+    });
+    if (rc) return rc;
+    launch_mx_enth_rhs(a, m, s, tr); ++fixed;
+    rc = loop(LOOP_ENTH, jtrips, [&](cudaStream_t bs, cudaGraphConditionalHandle h, bool g) {
+        launch_mx_enth(a, m, m.dh[0], m.dh[1], 0, bs, tr);
+        launch_mx_enth(a, m, m.dh[1], m.dh[0], 1, bs, tr);
+        launch_loop_ctl(a.sc, h, g, LOOP_ENTH, jtrips, 3, bs, tr);
+    });
+    if (rc) return rc;
+    launch_mx_eos(a, L0, Lf[0], m.dh[0], s, tr); ++fixed;
+    for (int l = 0; l + 1 < nlev; ++l) { launch_mx_coarsen(Lf[l], Lf[l + 1], kOmega, s, tr); ++fixed; }
+    const int body_cg = (nlev == 1 ? 2 : 2 + (nlev - 2) + kCoarseSweeps + (nlev - 1)) + 1;
+    for (int c = 0; c < ctx->C.n_corr; ++c) {
+        const double *U = c == 0 ? a.ua : a.N.u;
+        const double *W = c == 0 ? a.wa : a.N.w;
+        launch_H(a, U, W, s, tr); ++fixed;
+        CK(graph ? cudaEventRecordWithFlags(ctx->ev[2 * c], s, cudaEventRecordExternal)
+                 : cudaEventRecord(ctx->ev[2 * c], s));
+        launch_mx_helm_rhs(a, L0, Lf[0], m, c == 0 ? a.S.pp : a.N.pp, a.N.pp, c, s, tr); ++fixed;
+        fixed += launch_mx_vcycle(a, Lf, nlev, kCoarseSweeps, s, tr);
+        rc = loop(LOOP_CG, ctx->C.cg_maxit, [&](cudaStream_t bs, cudaGraphConditionalHandle h, bool g) {
+            launch_mx_cg_iter(a, m, Lf, nlev, kCoarseSweeps, bs, tr);
+            launch_loop_ctl(a.sc, h, g, LOOP_CG, ctx->C.cg_maxit, body_cg, bs, tr);
+        });
+        if (rc) return rc;
+        launch_mx_p_apply(a, m, s, tr); ++fixed;
+        CK(graph ? cudaEventRecordWithFlags(ctx->ev[2 * c + 1], s, cudaEventRecordExternal)
+                 : cudaEventRecord(ctx->ev[2 * c + 1], s));
+        launch_correct(a, s, tr); ++fixed;
+    }
+    ++fixed;
+    launch_step_end(ctx->sc, fixed, s, tr);
+    return GEA_OK;
+}
+
+int record_any(gea_ctx *ctx, int from, cudaStream_t s, bool graph, Tracer *tr)
+{
+    return ctx->mixed ? record_step_mixed(ctx, from, s, graph, tr) : record_step(ctx, from, s, graph, tr);
+}
+
 int build_graph(gea_ctx *ctx, int from)
 {
     cudaStream_t s = ctx->cap;
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    int rc = record_step(ctx, from, s, true, nullptr);
+    int rc = record_any(ctx, from, s, true, nullptr);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(s, &g);
     if (rc) {
@@ -321,7 +391,9 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
     if (!(c->R > 0) || !(c->cp > c->R) || !(c->g >= 0) || !(c->p0 > 0) || !(c->mu >= 0) ||
         !(c->Pr > 0) || !(c->dt > 0) || c->n_corr < 1 || c->n_corr > 4 || !(c->jac_rtol > 0) ||
         c->jac_maxit < 1 || !(c->cg_rtol > 0) || c->cg_maxit < 1 || c->mg_min_cells < 0 ||
-        (c->flags & ~GEA_FLAG_GRAPH))
+        (c->flags & ~(GEA_FLAG_GRAPH | GEA_FLAG_MIXED)))
+        return GEA_ERR_INVAL;
+    if ((c->flags & GEA_FLAG_MIXED) && c->mp_rtol != 0.0 && !(c->mp_rtol >= 1e-7 && c->mp_rtol < 1.0))
         return GEA_ERR_INVAL;
 
     ctx = new gea_ctx();
@@ -330,6 +402,7 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
     ctx->F.R = c->R; ctx->F.cp = c->cp; ctx->F.g = c->g; ctx->F.p0 = c->p0;
     ctx->F.mu = c->mu; ctx->F.nuh = c->mu / c->Pr; ctx->F.dt = c->dt; ctx->F.idt = 1.0 / c->dt;
     ctx->F.omega = kOmega;
+    ctx->mixed = (c->flags & GEA_FLAG_MIXED) != 0;
     if (cudaGetDevice(&ctx->device) != cudaSuccess) {
         delete ctx;
         return GEA_ERR_CUDA;
@@ -359,7 +432,14 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
     total += 33 * cell + 2 * fz;                   // scratch (Dz has nz+1 rows)
     total += 4 * cell;                             // staging for conservative fields
     total += 2 * cell + round_up(G.nz * sizeof(double), 256);   // theta_bar, theta'
-    for (const Geom &g : lg) total += 8 * arr_bytes(g, g.nz) + arr_bytes(g, g.nz + 1);
+    // FP64 levels (mixed precision: the finest only, for the FP64 residual)
+    const size_t nlev64 = ctx->mixed ? 1 : lg.size();
+    for (size_t l = 0; l < nlev64; ++l) total += 8 * arr_bytes(lg[l], lg[l].nz) + arr_bytes(lg[l], lg[l].nz + 1);
+    const size_t cellf = arr_bytes_f(G, G.nz);
+    if (ctx->mixed) {
+        total += 24 * cellf;                                        // MixedArgs
+        for (const Geom &g : lg) total += 8 * arr_bytes_f(g, g.nz) + arr_bytes_f(g, g.nz + 1);
+    }
     const size_t nb = (size_t)max_blocks(G);
     total += round_up(4 * nb * sizeof(double), 256);
     total += round_up(sizeof(Scal), 256);
@@ -390,13 +470,36 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
     ctx->stage = take(4 * cell);
     ctx->thout = take(cell);
     ctx->thbar = take(round_up(G.nz * sizeof(double), 256));
-    for (const Geom &g : lg) {
+    for (size_t lv = 0; lv < nlev64; ++lv) {
+        const Geom &g = lg[lv];
         Level l;
         l.G = g;
         const size_t lc = arr_bytes(g, g.nz), lf = arr_bytes(g, g.nz + 1);
         l.c = take(lc); l.d = take(lc); l.wd = take(lc); l.ax = take(lc); l.az = take(lf);
         l.r = take(lc); l.e = take(lc); l.e2 = take(lc); l.r_alt = take(lc);
         ctx->L.push_back(l);
+    }
+    if (ctx->mixed) {
+        auto takef = [&](size_t bytes) { return (float *)take(bytes); };
+        MixedArgs &m = ctx->mx;
+        Stencil9F &T32 = m.T;
+        T32.cC = takef(cellf); T32.cE1 = takef(cellf); T32.cE2 = takef(cellf); T32.cW1 = takef(cellf);
+        T32.cW2 = takef(cellf); T32.cN1 = takef(cellf); T32.cN2 = takef(cellf); T32.cS1 = takef(cellf);
+        T32.cS2 = takef(cellf);
+        m.dinvu = takef(cellf); m.dinvh = takef(cellf);
+        m.r0u = takef(cellf); m.r0w = takef(cellf); m.r0h = takef(cellf);
+        for (int j = 0; j < 2; ++j) { m.du[j] = takef(cellf); m.dw[j] = takef(cellf); m.dh[j] = takef(cellf); }
+        m.x = takef(cellf); m.p0 = takef(cellf); m.p1 = takef(cellf); m.q = takef(cellf);
+        const double rt = c->mp_rtol != 0.0 ? c->mp_rtol : kMixedRtol;
+        m.tol2 = rt * rt;
+        for (const Geom &g : lg) {
+            LevelF l;
+            l.G = g;
+            const size_t lc = arr_bytes_f(g, g.nz), lf = arr_bytes_f(g, g.nz + 1);
+            l.c = takef(lc); l.d = takef(lc); l.wd = takef(lc); l.ax = takef(lc); l.az = takef(lf);
+            l.r = takef(lc); l.e = takef(lc); l.e2 = takef(lc); l.r_alt = takef(lc);
+            ctx->Lf.push_back(l);
+        }
     }
     ctx->partials = take(round_up(4 * nb * sizeof(double), 256));
     ctx->sc = (Scal *)take(round_up(sizeof(Scal), 256));
@@ -409,7 +512,7 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
     // step driver: the persistent kernel pays off while a phase is a few
     // tiles per resident block (its phases are latency-bound); on larger
     // grids the per-phase kernels keep more blocks resident per SM
-    if (!(c->flags & GEA_FLAG_GRAPH)) {
+    if (!(c->flags & (GEA_FLAG_GRAPH | GEA_FLAG_MIXED))) {
         const int pmax = persistent_max_blocks();
         cudaGetLastError();
         if (pmax > 0 && (long long)nb <= (long long)kPersistTilesPerBlock * pmax)
@@ -589,9 +692,9 @@ int gea_get_stats(gea_ctx *ctx, gea_stats *s)
         s->cg_relres[c] = h.last_cg_relres[c];
     }
     s->status = h.last_status;
-    s->mg_levels = (int)ctx->L.size();
+    s->mg_levels = ctx->mixed ? (int)ctx->Lf.size() : (int)ctx->L.size();
     s->launches = h.launches;
-    s->driver = ctx->pers_blocks > 0 ? 1 : 0;
+    s->driver = ctx->mixed ? 2 : ctx->pers_blocks > 0 ? 1 : 0;
     return GEA_OK;
 }
 
@@ -608,7 +711,10 @@ int gea_get_field(gea_ctx *ctx, int32_t which, double *host)
     case GEA_FIELD_RHO1: src = ctx->rho1; break;
     case GEA_FIELD_U1: src = slot_u1 ? ctx->ub : ctx->ua; break;
     case GEA_FIELD_W1: src = slot_u1 ? ctx->wb : ctx->wa; break;
-    case GEA_FIELD_H1: src = slot_h1 ? ctx->hb : ctx->ha; break;
+    case GEA_FIELD_H1:
+        // mixed precision: h^{n+1} = h^n + dh goes straight into the new state
+        src = ctx->mixed ? ctx->S[current_slot(ctx, h)].h : slot_h1 ? ctx->hb : ctx->ha;
+        break;
     case GEA_FIELD_RHO2: src = ctx->rho2; break;
     case GEA_FIELD_HX: src = ctx->Hx; break;
     case GEA_FIELD_HZ: src = ctx->Hz; break;
@@ -654,7 +760,7 @@ int gea_profile_step(gea_ctx *ctx, gea_kernel_time *out, int32_t max_entries, in
     if (h.status) return fail(ctx, h.status, "device status %d", h.status);
     const int from = current_slot(ctx, h);
     EventTracer tr;
-    rc = record_step(ctx, from, ctx->stream, false, &tr);
+    rc = record_any(ctx, from, ctx->stream, false, &tr);
     if (rc) return rc;
     CK(cudaStreamSynchronize(ctx->stream));
     std::vector<gea_kernel_time> agg;

@@ -42,16 +42,22 @@ struct State {
 // One multigrid level of the Helmholtz operator
 //   (A x)_i = c_i x_i + sum_f a_f (x_i - x_N) = d_i x_i - sum_f a_f x_N,
 // d_i = c_i + sum_f a_f, kept as d and wd = omega / d.
-struct Level {
+// R is the value type: double on the FP64 path, float for the inner solves
+// of the mixed-precision path.
+template <class R>
+struct LevelT {
     Geom G;
-    double *c, *d, *wd, *ax, *az;  // reaction, diagonal, omega/diagonal, face coefficients
-    double *r, *e, *e2;            // residual, pre-smoothed correction, post-smoothed
-    double *r_alt;                 // finest level: second residual buffer (CG iterations
-                                   // alternate r and r_alt; the update reads one, writes the other)
+    R *c, *d, *wd, *ax, *az;  // reaction, diagonal, omega/diagonal, face coefficients
+    R *r, *e, *e2;            // residual, pre-smoothed correction, post-smoothed
+    R *r_alt;                 // finest level: second residual buffer (CG iterations
+                              // alternate r and r_alt; the update reads one, writes the other)
 };
+using Level = LevelT<double>;
+using LevelF = LevelT<float>;
 
 // Finest-level residual after `it` CG updates.
-__host__ __device__ __forceinline__ double *res_of(const Level &L, int it)
+template <class R>
+__host__ __device__ __forceinline__ R *res_of(const LevelT<R> &L, int it)
 {
     return (it & 1) ? L.r_alt : L.r;
 }
@@ -60,8 +66,23 @@ __host__ __device__ __forceinline__ double *res_of(const Level &L, int it)
 //   T(X)_i = (rho1/dt) X_i + C(X)_i - mu L(X)_i,
 // assembled once per step as a 9-point cross stencil (offsets 0, +-1, +-2 in x
 // and z) on the ghost-extended field.
-struct Stencil9 {
-    double *cC, *cE1, *cE2, *cW1, *cW2, *cN1, *cN2, *cS1, *cS2;
+template <class R>
+struct Stencil9T {
+    R *cC, *cE1, *cE2, *cW1, *cW2, *cN1, *cN2, *cS1, *cS2;
+};
+using Stencil9 = Stencil9T<double>;
+using Stencil9F = Stencil9T<float>;
+
+// Buffers of the mixed-precision path: FP32 copies of the operators and the
+// increments its inner solves iterate on (u, w, h and p' each get an FP64
+// residual, an FP32 solve for the increment, and an FP64 update).
+struct MixedArgs {
+    Stencil9F T;                   // transport operator (with mu)
+    float *dinvu, *dinvh;          // Jacobi reciprocals
+    float *r0u, *r0w, *r0h;        // FP64 residuals of the predictors, rounded to FP32
+    float *du[2], *dw[2], *dh[2];  // increments (Jacobi ping-pong)
+    float *x, *p0, *p1, *q;        // pressure increment, CG directions, A p
+    double tol2;                   // inner tolerance^2, relative to the initial residual
 };
 
 // Loop bookkeeping slots.
@@ -157,7 +178,8 @@ __device__ __forceinline__ double ldc(const Geom &G, const Phys &F, const double
     return X[k * G.P + i];
 }
 
-__device__ __forceinline__ double warp_sum(double v)
+template <class T>
+__device__ __forceinline__ T warp_sum(T v)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -169,8 +191,8 @@ __device__ __forceinline__ double warp_sum(double v)
 // 8 per lane and then a shuffle tree: about 1.5 FP64 additions per value per
 // thread instead of 5 for a full-block shuffle tree (FP64 issue is the
 // scarce resource on this GPU).
-template <int NV>
-__device__ __forceinline__ void block_sum(const double (&v)[NV], double *red, double (&out)[NV])
+template <int NV, class T = double>
+__device__ __forceinline__ void block_sum(const T (&v)[NV], T *red, T (&out)[NV])
 {
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
 #pragma unroll
@@ -179,7 +201,7 @@ __device__ __forceinline__ void block_sum(const double (&v)[NV], double *red, do
     if (tid < 32) {
 #pragma unroll
         for (int j = 0; j < NV; ++j) {
-            double s = red[j * NTHREADS + tid];
+            T s = red[j * NTHREADS + tid];
 #pragma unroll
             for (int q = 1; q < NTHREADS / 32; ++q) s += red[j * NTHREADS + tid + 32 * q];
             s = warp_sum(s);
@@ -193,19 +215,22 @@ __device__ __forceinline__ void block_sum(const double (&v)[NV], double *red, do
 // block writes its totals; the block that arrives last adds the partials in
 // a fixed order and returns true in its thread 0 with the totals in tot[].
 // Every thread of every block must call it.
-template <int NV>
-__device__ bool grid_sum(const double (&v)[NV], double *red, double *partials, unsigned *counter,
+// T is the type of the per-thread values and of the block sums (FP32 for the
+// inner solves of the mixed-precision path); block partials and the grid
+// total are FP64. red holds NV * NTHREADS doubles.
+template <int NV, class T = double>
+__device__ bool grid_sum(const T (&v)[NV], double *red, double *partials, unsigned *counter,
                          double (&tot)[NV])
 {
     __shared__ int am_last;
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     const int bid = blockIdx.x + blockIdx.y * gridDim.x;
     const int nb = gridDim.x * gridDim.y;
-    double bt[NV];
-    block_sum<NV>(v, red, bt);
+    T bt[NV];
+    block_sum<NV, T>(v, reinterpret_cast<T *>(red), bt);
     if (tid == 0) {
 #pragma unroll
-        for (int j = 0; j < NV; ++j) partials[(size_t)j * nb + bid] = bt[j];
+        for (int j = 0; j < NV; ++j) partials[(size_t)j * nb + bid] = (double)bt[j];
         __threadfence();
         am_last = atomicAdd(counter, 1u) == (unsigned)nb - 1u;
     }
@@ -228,11 +253,12 @@ void launch_derive(const Geom &G, const Phys &F, const double *rho, const double
                    const double *rhow, const double *rhoe, const State &S, Scal *sc,
                    cudaStream_t st);
 void launch_pred_setup(const StepArgs &a, cudaStream_t st, Tracer *tr);
+// second = 1: the second sweep of a pair (copies instead once converged)
 void launch_mom_jacobi(const StepArgs &a, const double *uin, const double *win, double *uout,
-                       double *wout, cudaStream_t st, Tracer *tr);
+                       double *wout, int second, cudaStream_t st, Tracer *tr);
 void launch_enth_rhs(const StepArgs &a, cudaStream_t st, Tracer *tr);
-void launch_enth_jacobi(const StepArgs &a, const double *hin, double *hout, cudaStream_t st,
-                        Tracer *tr);
+void launch_enth_jacobi(const StepArgs &a, const double *hin, double *hout, int second,
+                        cudaStream_t st, Tracer *tr);
 void launch_eos_coef(const StepArgs &a, const Level &L0, cudaStream_t st, Tracer *tr);
 void launch_mg_coarsen(const Level &f, const Level &c, double omega, cudaStream_t st, Tracer *tr);
 void launch_H(const StepArgs &a, const double *U, const double *W, cudaStream_t st, Tracer *tr);
@@ -252,6 +278,22 @@ void launch_step_end(Scal *sc, int fixed_launches, cudaStream_t st, Tracer *tr);
 void launch_diag(const Geom &G, const Phys &F, const State &S, const double *theta_bar,
                  double *theta_out, Scal *sc, double *partials, cudaStream_t st);
 int max_blocks(const Geom &G);
+// mixed-precision step (gea_mixed.cu)
+void launch_mx_pred(const StepArgs &a, const MixedArgs &m, cudaStream_t st, Tracer *tr);
+void launch_mx_mom(const StepArgs &a, const MixedArgs &m, const float *ui, const float *wi, float *uo,
+                   float *wo, int second, cudaStream_t st, Tracer *tr);
+void launch_mx_enth_rhs(const StepArgs &a, const MixedArgs &m, cudaStream_t st, Tracer *tr);
+void launch_mx_enth(const StepArgs &a, const MixedArgs &m, const float *hi, float *ho, int second,
+                    cudaStream_t st, Tracer *tr);
+void launch_mx_eos(const StepArgs &a, const Level &L0, const LevelF &L32, const float *dh, cudaStream_t st,
+                   Tracer *tr);
+void launch_mx_coarsen(const LevelF &f, const LevelF &c, double omega, cudaStream_t st, Tracer *tr);
+void launch_mx_helm_rhs(const StepArgs &a, const Level &L0, const LevelF &L32, const MixedArgs &m,
+                        const double *xin, double *xout, int corr, cudaStream_t st, Tracer *tr);
+int launch_mx_vcycle(const StepArgs &a, LevelF *L, int nlev, int ncoarse, cudaStream_t st, Tracer *tr);
+int launch_mx_cg_iter(const StepArgs &a, const MixedArgs &m, LevelF *L, int nlev, int ncoarse,
+                      cudaStream_t st, Tracer *tr);
+void launch_mx_p_apply(const StepArgs &a, const MixedArgs &m, cudaStream_t st, Tracer *tr);
 // persistent cooperative step kernel (gea_persistent.cu)
 int persistent_max_blocks();
 cudaError_t launch_persistent(const StepArgs a[2], const Level *L, int nlev, int ncoarse, int n_corr,

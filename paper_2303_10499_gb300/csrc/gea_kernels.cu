@@ -65,10 +65,18 @@ __global__ void k_pred_setup(StepArgs a)
     if (grid_sum<2>(acc, red, a.partials, &a.sc->counters[CNT_PRED], tot)) fin_pred(a.sc, tot);
 }
 
+// Sweeps run in pairs (X_a -> X_b -> X_a) so that the loop ends in X_a. The
+// second sweep of a pair whose first sweep met the tolerance copies X_b back
+// instead: the iteration stops after that sweep.
 __global__ void k_mom_jacobi(StepArgs a, const double *uin, const double *win, double *uout,
-                             double *wout)
+                             double *wout, int second)
 {
     if (a.sc->status) return;
+    if (second && a.sc->done[LOOP_MOM]) {
+        ph_copy(a.G, uin, uout, blockIdx.x, blockIdx.y);
+        ph_copy(a.G, win, wout, blockIdx.x, blockIdx.y);
+        return;
+    }
     __shared__ double sm[2 * kT2];
     __shared__ double red[2 * NTHREADS];
     double acc[2] = {0.0, 0.0}, tot[2];
@@ -88,9 +96,13 @@ __global__ void k_enth_rhs(StepArgs a)
     if (grid_sum<1>(acc, red, a.partials, &a.sc->counters[CNT_ENTH_RHS], tot)) fin_enth_rhs(a.sc, tot);
 }
 
-__global__ void k_enth_jacobi(StepArgs a, const double *hin, double *hout)
+__global__ void k_enth_jacobi(StepArgs a, const double *hin, double *hout, int second)
 {
     if (a.sc->status) return;
+    if (second && a.sc->done[LOOP_ENTH]) {
+        ph_copy(a.G, hin, hout, blockIdx.x, blockIdx.y);
+        return;
+    }
     __shared__ double sm[kT2];
     __shared__ double red[NTHREADS];
     double acc[1] = {0.0}, tot[1];
@@ -179,20 +191,8 @@ __global__ void k_cg_pspmv(StepArgs a, Level L)
     const double *pold = (it & 1) ? a.p1 : a.p0;
     double *pnew = (it & 1) ? a.p0 : a.p1;
     double acc[1] = {0.0}, tot[1];
-    ph_pspmv(a, L, pold, pnew, sc->beta, sm, blockIdx.x, blockIdx.y, acc);
+    ph_pspmv<double>(L, pold, pnew, a.q, sc->beta, sm, blockIdx.x, blockIdx.y, acc);
     if (grid_sum<1>(acc, red, a.partials, &sc->counters[CNT_PQ], tot)) fin_pq(sc, tot);
-}
-
-__global__ void k_cg_update(StepArgs a, Level L, double *x)
-{
-    Scal *sc = a.sc;
-    if (loop_over(sc, LOOP_CG)) return;
-    __shared__ double red[NTHREADS];
-    const int it = sc->cg_it;
-    const double *p = (it & 1) ? a.p0 : a.p1;
-    double acc[1] = {0.0}, tot[1];
-    ph_update(a, L, x, p, sc->alpha, blockIdx.x, blockIdx.y, acc);
-    if (grid_sum<1>(acc, red, a.partials, &sc->counters[CNT_UPD], tot)) fin_update(sc, tot, a.cg_rtol2);
 }
 
 __global__ void k_cg_update_single(StepArgs a, Level L, double *x)
@@ -204,8 +204,8 @@ __global__ void k_cg_update_single(StepArgs a, Level L, double *x)
     const int it = sc->cg_it;
     const double *p = (it & 1) ? a.p0 : a.p1;
     double acc[2] = {0.0, 0.0}, tot[2];
-    ph_update_single(a, L, res_of(L, it), res_of(L, it + 1), x, p, sc->alpha, sm, blockIdx.x,
-                     blockIdx.y, acc);
+    ph_update_single<double>(L, a.q, res_of(L, it), res_of(L, it + 1), x, p, sc->alpha, sm, blockIdx.x,
+                             blockIdx.y, acc);
     if (grid_sum<2>(acc, red, a.partials, &sc->counters[CNT_UPD], tot)) {
         const double t0[1] = {tot[0]}, t1[1] = {tot[1]};
         fin_update(sc, t0, a.cg_rtol2);
@@ -222,8 +222,8 @@ __global__ void k_cg_update_down(StepArgs a, Level f, Level c, double *x)
     const int it = sc->cg_it;
     const double *p = (it & 1) ? a.p0 : a.p1;
     double acc[1] = {0.0}, tot[1];
-    ph_update_down(a, f, c, res_of(f, it), res_of(f, it + 1), x, p, sc->alpha, a.F.omega, sm,
-                   blockIdx.x, blockIdx.y, acc);
+    ph_update_down<double>(f, c, a.q, res_of(f, it), res_of(f, it + 1), x, p, sc->alpha, a.F.omega, sm,
+                           blockIdx.x, blockIdx.y, acc);
     if (grid_sum<1>(acc, red, a.partials, &sc->counters[CNT_UPD], tot)) fin_update(sc, tot, a.cg_rtol2);
 }
 
@@ -329,10 +329,10 @@ void launch_pred_setup(const StepArgs &a, cudaStream_t st, Tracer *tr)
 }
 
 void launch_mom_jacobi(const StepArgs &a, const double *uin, const double *win, double *uout,
-                       double *wout, cudaStream_t st, Tracer *tr)
+                       double *wout, int second, cudaStream_t st, Tracer *tr)
 {
     TRACED(tr, "mom_jacobi", ncell(a.G),
-           (k_mom_jacobi<<<grid_of(a.G), kBlock, 0, st>>>(a, uin, win, uout, wout)));
+           (k_mom_jacobi<<<grid_of(a.G), kBlock, 0, st>>>(a, uin, win, uout, wout, second)));
 }
 
 void launch_enth_rhs(const StepArgs &a, cudaStream_t st, Tracer *tr)
@@ -340,11 +340,11 @@ void launch_enth_rhs(const StepArgs &a, cudaStream_t st, Tracer *tr)
     TRACED(tr, "enth_rhs", ncell(a.G), (k_enth_rhs<<<grid_of(a.G), kBlock, 0, st>>>(a)));
 }
 
-void launch_enth_jacobi(const StepArgs &a, const double *hin, double *hout, cudaStream_t st,
-                        Tracer *tr)
+void launch_enth_jacobi(const StepArgs &a, const double *hin, double *hout, int second,
+                        cudaStream_t st, Tracer *tr)
 {
     TRACED(tr, "enth_jacobi", ncell(a.G),
-           (k_enth_jacobi<<<grid_of(a.G), kBlock, 0, st>>>(a, hin, hout)));
+           (k_enth_jacobi<<<grid_of(a.G), kBlock, 0, st>>>(a, hin, hout, second)));
 }
 
 void launch_eos_coef(const StepArgs &a, const Level &L0, cudaStream_t st, Tracer *tr)

@@ -263,7 +263,7 @@ __device__ bool run_step(const PersistArgs &P, const StepArgs &a, double *sm, do
             {
                 const double beta = rdd(&sc->beta);
                 double acc[1] = {0.0};
-                for_tiles(G, [&](int bx, int bz) { ph_pspmv(a, L[0], pold, pnew, beta, sm, bx, bz, acc); });
+                for_tiles(G, [&](int bx, int bz) { ph_pspmv<double>(L[0], pold, pnew, a.q, beta, sm, bx, bz, acc); });
                 rbar<1>(acc, red, sc, a.partials, [&](const double (&t)[1]) { fin_pq(sc, t); });
             }
             // x += alpha p, r -= alpha q, with the first step of the next V-cycle
@@ -274,8 +274,8 @@ __device__ bool run_step(const PersistArgs &P, const StepArgs &a, double *sm, do
             if (nlev == 1) {
                 double acc[2] = {0.0, 0.0};
                 for_tiles(G, [&](int bx, int bz) {
-                    ph_update_single(a, L[0], res_of(L[0], it), res_of(L[0], it + 1), a.N.pp, pnew, alpha,
-                                     sm, bx, bz, acc);
+                    ph_update_single<double>(L[0], a.q, res_of(L[0], it), res_of(L[0], it + 1), a.N.pp,
+                                             pnew, alpha, sm, bx, bz, acc);
                 });
                 rbar<2>(acc, red, sc, a.partials, [&](const double (&t)[2]) {
                     const double t0[1] = {t[0]}, t1[1] = {t[1]};
@@ -286,8 +286,8 @@ __device__ bool run_step(const PersistArgs &P, const StepArgs &a, double *sm, do
             } else {
                 double acc[1] = {0.0};
                 for_tiles(G, [&](int bx, int bz) {
-                    ph_update_down(a, L[0], L[1], res_of(L[0], it), res_of(L[0], it + 1), a.N.pp, pnew,
-                                   alpha, a.F.omega, sm, bx, bz, acc);
+                    ph_update_down<double>(L[0], L[1], a.q, res_of(L[0], it), res_of(L[0], it + 1), a.N.pp,
+                                           pnew, alpha, a.F.omega, sm, bx, bz, acc);
                 });
                 rbar<1>(acc, red, sc, a.partials, [&](const double (&t)[1]) {
                     fin_update(sc, t, a.cg_rtol2);

@@ -33,20 +33,21 @@
 namespace gea {
 namespace tiles {
 
-template <int H>
-using Tile = double[BZ + 2 * H][BX + 2 * H];
+template <int H, class R = double>
+using Tile = R[BZ + 2 * H][BX + 2 * H];
 
 constexpr int kT1 = (BZ + 2) * (BX + 2);   // doubles of a halo-1 tile
 constexpr int kT2 = (BZ + 4) * (BX + 4);   // doubles of a halo-2 tile
 constexpr int kTileSmem = 4 * kT1;         // the largest phase footprint
 
-template <int H>
-__device__ __forceinline__ Tile<H> &tile_at(double *sm, int slot)
+template <int H, class R = double>
+__device__ __forceinline__ Tile<H, R> &tile_at(double *sm, int slot)
 {
-    return *reinterpret_cast<Tile<H> *>(sm + slot * (BZ + 2 * H) * (BX + 2 * H));
+    return *reinterpret_cast<Tile<H, R> *>(reinterpret_cast<R *>(sm) + slot * (BZ + 2 * H) * (BX + 2 * H));
 }
 
 __device__ __forceinline__ double ld(const double *p) { return __ldcg(p); }
+__device__ __forceinline__ float ld(const float *p) { return __ldcg(p); }
 
 __device__ __forceinline__ bool cell_of(const Geom &G, int bx, int bz, int &i, int &k)
 {
@@ -58,35 +59,55 @@ __device__ __forceinline__ bool cell_of(const Geom &G, int bx, int bz, int &i, i
 // Cell value at (i,k) just outside the box: the one-layer wall ghost of rule
 // BC (wall-normal velocity odd, tangential velocity and scalars even, h with
 // dh/dz = -g at the horizontal walls).
-template <int BC>
-__device__ __forceinline__ double ghost(const Geom &G, const Phys &F, const double *X, int i, int k)
+template <int BC, class R>
+__device__ __forceinline__ R ghost(const Geom &G, const Phys &F, const R *X, int i, int k)
 {
     if (i < 0) {
-        const double v = ld(&X[k * G.P]);
+        const R v = ld(&X[k * G.P]);
         return BC == BC_U ? -v : v;
     }
     if (i >= G.nx) {
-        const double v = ld(&X[k * G.P + G.nx - 1]);
+        const R v = ld(&X[k * G.P + G.nx - 1]);
         return BC == BC_U ? -v : v;
     }
     if (k < 0) {
-        const double v = ld(&X[i]);
+        const R v = ld(&X[i]);
         if (BC == BC_W) return -v;
-        if (BC == BC_H) return v + F.g * G.dz;
+        if (BC == BC_H) return v + (R)(F.g * G.dz);
         return v;
     }
-    const double v = ld(&X[(G.nz - 1) * G.P + i]);
+    const R v = ld(&X[(G.nz - 1) * G.P + i]);
     if (BC == BC_W) return -v;
-    if (BC == BC_H) return v - F.g * G.dz;
+    if (BC == BC_H) return v - (R)(F.g * G.dz);
     return v;
 }
 
 // Fill the (BZ+2H) x (BX+2H) tile of X around tile (bx, bz): cells inside the
 // box, the one-layer wall ghosts of rule BC, zero elsewhere (deeper ghosts and
 // corners only ever meet zero coefficients).
+template <int BC, int H, class R>
+__device__ __forceinline__ void load_tile(Tile<H, R> &s, const Geom &G, const Phys &F, const R *X,
+                                          int bx, int bz)
+{
+    const int i0 = bx * BX - H, k0 = bz * BZ - H;
+    const int tid = threadIdx.x + threadIdx.y * BX;
+    constexpr int W = BX + 2 * H, NE = (BZ + 2 * H) * (BX + 2 * H);
+    for (int e = tid; e < NE; e += NTHREADS) {
+        const int tk = e / W, ti = e - tk * W;
+        const int i = i0 + ti, k = k0 + tk;
+        const bool xin = i >= 0 && i < G.nx, zin = k >= 0 && k < G.nz;
+        R v = 0;
+        if (xin && zin) v = ld(&X[k * G.P + i]);
+        else if (zin && (i == -1 || i == G.nx)) v = ghost<BC>(G, F, X, i, k);
+        else if (xin && (k == -1 || k == G.nz)) v = ghost<BC>(G, F, X, i, k);
+        s[tk][ti] = v;
+    }
+}
+
+// Tile of X + Y (FP64 field plus FP32 increment with the same wall rule).
 template <int BC, int H>
-__device__ __forceinline__ void load_tile(Tile<H> &s, const Geom &G, const Phys &F,
-                                          const double *X, int bx, int bz)
+__device__ __forceinline__ void load_tile_sum(Tile<H> &s, const Geom &G, const Phys &F, const double *X,
+                                              const float *Y, int bx, int bz)
 {
     const int i0 = bx * BX - H, k0 = bz * BZ - H;
     const int tid = threadIdx.x + threadIdx.y * BX;
@@ -96,17 +117,17 @@ __device__ __forceinline__ void load_tile(Tile<H> &s, const Geom &G, const Phys 
         const int i = i0 + ti, k = k0 + tk;
         const bool xin = i >= 0 && i < G.nx, zin = k >= 0 && k < G.nz;
         double v = 0.0;
-        if (xin && zin) v = ld(&X[k * G.P + i]);
-        else if (zin && (i == -1 || i == G.nx)) v = ghost<BC>(G, F, X, i, k);
-        else if (xin && (k == -1 || k == G.nz)) v = ghost<BC>(G, F, X, i, k);
+        if (xin && zin) v = ld(&X[k * G.P + i]) + (double)ld(&Y[k * G.P + i]);
+        else if ((zin && (i == -1 || i == G.nx)) || (xin && (k == -1 || k == G.nz)))
+            v = ghost<BC>(G, F, X, i, k) + (double)ghost<BC == BC_H ? BC_EVEN : BC>(G, F, Y, i, k);
         s[tk][ti] = v;
     }
 }
 
 // Same for a field given by f(q, i, k) at cell (i, k), index q (zero outside
 // the box).
-template <int H, class Fn>
-__device__ __forceinline__ void load_tile_fn(Tile<H> &s, const Geom &G, int bx, int bz, Fn f)
+template <int H, class R, class Fn>
+__device__ __forceinline__ void load_tile_fn(Tile<H, R> &s, const Geom &G, int bx, int bz, Fn f)
 {
     const int i0 = bx * BX - H, k0 = bz * BZ - H;
     const int tid = threadIdx.x + threadIdx.y * BX;
@@ -114,15 +135,23 @@ __device__ __forceinline__ void load_tile_fn(Tile<H> &s, const Geom &G, int bx, 
     for (int e = tid; e < NE; e += NTHREADS) {
         const int tk = e / W, ti = e - tk * W;
         const int i = i0 + ti, k = k0 + tk;
-        s[tk][ti] = (i >= 0 && i < G.nx && k >= 0 && k < G.nz) ? f(k * G.P + i, i, k) : 0.0;
+        s[tk][ti] = (i >= 0 && i < G.nx && k >= 0 && k < G.nz) ? (R)f(k * G.P + i, i, k) : (R)0;
     }
 }
 
-// 9-point cross stencil sum_o c_o X_o at tile position (y, x).
-template <int H>
-__device__ __forceinline__ double apply9(const Stencil9 &T, int q, const Tile<H> &s, int y, int x)
+// Y = X on the tile's cells.
+template <class R>
+__device__ __forceinline__ void ph_copy(const Geom &G, const R *X, R *Y, int bx, int bz)
 {
-    double acc = ld(&T.cC[q]) * s[y][x];
+    int i, k;
+    if (cell_of(G, bx, bz, i, k)) Y[cidx(G, i, k)] = ld(&X[cidx(G, i, k)]);
+}
+
+// 9-point cross stencil sum_o c_o X_o at tile position (y, x).
+template <int H, class R>
+__device__ __forceinline__ R apply9(const Stencil9T<R> &T, int q, const Tile<H, R> &s, int y, int x)
+{
+    R acc = ld(&T.cC[q]) * s[y][x];
     acc = fma(ld(&T.cE1[q]), s[y][x + 1], acc);
     acc = fma(ld(&T.cW1[q]), s[y][x - 1], acc);
     acc = fma(ld(&T.cN1[q]), s[y + 1][x], acc);
@@ -135,22 +164,22 @@ __device__ __forceinline__ double apply9(const Stencil9 &T, int q, const Tile<H>
 }
 
 // 5-point Laplacian (X_E + X_W - 2 X_C)/dx^2 + (X_N + X_S - 2 X_C)/dz^2.
-template <int H>
-__device__ __forceinline__ double lap5(const Geom &G, const Tile<H> &s, int y, int x)
+template <int H, class R>
+__device__ __forceinline__ R lap5(const Geom &G, const Tile<H, R> &s, int y, int x)
 {
-    const double c2 = 2.0 * s[y][x];
-    return (s[y][x + 1] + s[y][x - 1] - c2) * (G.idx * G.idx) +
-           (s[y + 1][x] + s[y - 1][x] - c2) * (G.idz * G.idz);
+    const R c2 = (R)2 * s[y][x];
+    return (s[y][x + 1] + s[y][x - 1] - c2) * (R)(G.idx * G.idx) +
+           (s[y + 1][x] + s[y - 1][x] - c2) * (R)(G.idz * G.idz);
 }
 
 // A x = d x - sum a x_N at tile position (y, x) of cell (i, k) (zero tile
 // entries and zero wall coefficients beyond the box).
-template <int H>
-__device__ __forceinline__ double helm_tile(const Level &L, int q, int i, int k, const Tile<H> &s,
-                                            int y, int x)
+template <int H, class R>
+__device__ __forceinline__ R helm_tile(const LevelT<R> &L, int q, int i, int k, const Tile<H, R> &s,
+                                       int y, int x)
 {
     const Geom &G = L.G;
-    double t = ld(&L.d[q]) * s[y][x];
+    R t = ld(&L.d[q]) * s[y][x];
     t = fma(-ld(&L.ax[k * G.P + i]), s[y][x - 1], t);
     t = fma(-ld(&L.ax[k * G.P + i + 1]), s[y][x + 1], t);
     t = fma(-ld(&L.az[k * G.P + i]), s[y - 1][x], t);
@@ -172,79 +201,174 @@ __device__ __forceinline__ double helm_tile(const Level &L, int q, int i, int k,
 // with G_cell the average of the two face forces grad p'^n - g z grad rho^n
 // per direction (zero on wall faces); the initial guess u^n.
 // acc += (b_u^2, b_w^2).
-__device__ __forceinline__ void ph_pred(const StepArgs &a, int bx, int bz, double (&acc)[2])
+//
+// MX (mixed-precision path): instead of b, the reciprocals and the initial
+// guess, the FP64 residuals r0 = b - T(u^n) of both components, FP32 copies
+// of the operator, the reciprocals and r0, and the first FP32 Jacobi sweep
+// from zero, du = r0 / T_CC; acc += (r0_u^2, r0_w^2).
+template <bool MX>
+__device__ __forceinline__ void ph_pred_t(const StepArgs &a, const MixedArgs &m, double *sm, int bx,
+                                          int bz, double (&acc)[2])
 {
     const Geom &G = a.G;
     const Phys &F = a.F;
-    int i, k;
-    if (!cell_of(G, bx, bz, i, k)) return;
-    const int q = cidx(G, i, k);
     const State &S = a.S;
-    const double pw = ld(&S.phix[q]), pe = ld(&S.phix[q + 1]), ps = ld(&S.phiz[q]), pn = ld(&S.phiz[q + G.P]);
-    const double div = (pe - pw + pn - ps) * G.iV;
-    const double rq = ld(&S.rho[q]);
-    const double rho1 = rq - F.dt * div;
-    const double s12 = G.iV * (1.0 / 12.0);
-    const double fe = pe * s12, fw = pw * s12, fn = pn * s12, fs = ps * s12;
-    const double mx = F.mu * G.idx * G.idx, mz = F.mu * G.idz * G.idz;
-    const double cC = rho1 * F.idt + (7.0 / 12.0) * div + 2.0 * (mx + mz);
-    a.T.cC[q] = cC;
-    a.T.cE1[q] = fma(7.0, fe, fw) - mx;
-    a.T.cW1[q] = -fma(7.0, fw, fe) - mx;
-    a.T.cE2[q] = -fe;
-    a.T.cW2[q] = fw;
-    a.T.cN1[q] = fma(7.0, fn, fs) - mz;
-    a.T.cS1[q] = -fma(7.0, fs, fn) - mz;
-    a.T.cN2[q] = -fn;
-    a.T.cS2[q] = fs;
-    a.dinvu[q] = 1.0 / cC;
-    a.dinvh[q] = 1.0 / (cC + 2.0 * (F.nuh - F.mu) * (G.idx * G.idx + G.idz * G.idz));
-    const double z = (k + 0.5) * G.dz;
-    const double pq = ld(&S.pp[q]);
-    double gxw = 0.0, gxe = 0.0, gzs = 0.0, gzn = 0.0;
-    if (i > 0) gxw = (pq - ld(&S.pp[q - 1])) * G.idx - F.g * z * (rq - ld(&S.rho[q - 1])) * G.idx;
-    if (i + 1 < G.nx) gxe = (ld(&S.pp[q + 1]) - pq) * G.idx - F.g * z * (ld(&S.rho[q + 1]) - rq) * G.idx;
-    if (k > 0)
-        gzs = (pq - ld(&S.pp[q - G.P])) * G.idz - F.g * (k * G.dz) * (rq - ld(&S.rho[q - G.P])) * G.idz;
-    if (k + 1 < G.nz)
-        gzn = (ld(&S.pp[q + G.P]) - pq) * G.idz - F.g * ((k + 1) * G.dz) * (ld(&S.rho[q + G.P]) - rq) * G.idz;
-    const double u = ld(&S.u[q]), w = ld(&S.w[q]);
-    const double bu = rq * u * F.idt - 0.5 * (gxw + gxe);
-    const double bw = rq * w * F.idt - 0.5 * (gzs + gzn);
-    a.rho1[q] = rho1;
-    a.bu[q] = bu;
-    a.bw[q] = bw;
-    a.ua[q] = u;
-    a.wa[q] = w;
-    acc[0] = fma(bu, bu, acc[0]);
-    acc[1] = fma(bw, bw, acc[1]);
+    if (MX) {
+        load_tile<BC_U, 2>(tile_at<2>(sm, 0), G, F, S.u, bx, bz);
+        load_tile<BC_W, 2>(tile_at<2>(sm, 1), G, F, S.w, bx, bz);
+        __syncthreads();
+    }
+    int i, k;
+    if (cell_of(G, bx, bz, i, k)) {
+        const int q = cidx(G, i, k);
+        const double pw = ld(&S.phix[q]), pe = ld(&S.phix[q + 1]), ps = ld(&S.phiz[q]), pn = ld(&S.phiz[q + G.P]);
+        const double div = (pe - pw + pn - ps) * G.iV;
+        const double rq = ld(&S.rho[q]);
+        const double rho1 = rq - F.dt * div;
+        const double s12 = G.iV * (1.0 / 12.0);
+        const double fe = pe * s12, fw = pw * s12, fn = pn * s12, fs = ps * s12;
+        const double mx = F.mu * G.idx * G.idx, mz = F.mu * G.idz * G.idz;
+        const double cC = rho1 * F.idt + (7.0 / 12.0) * div + 2.0 * (mx + mz);
+        const double cE1 = fma(7.0, fe, fw) - mx, cW1 = -fma(7.0, fw, fe) - mx;
+        const double cN1 = fma(7.0, fn, fs) - mz, cS1 = -fma(7.0, fs, fn) - mz;
+        const double cE2 = -fe, cW2 = fw, cN2 = -fn, cS2 = fs;
+        a.T.cC[q] = cC;
+        a.T.cE1[q] = cE1;
+        a.T.cW1[q] = cW1;
+        a.T.cE2[q] = cE2;
+        a.T.cW2[q] = cW2;
+        a.T.cN1[q] = cN1;
+        a.T.cS1[q] = cS1;
+        a.T.cN2[q] = cN2;
+        a.T.cS2[q] = cS2;
+        const double diu = 1.0 / cC;
+        const double dih = 1.0 / (cC + 2.0 * (F.nuh - F.mu) * (G.idx * G.idx + G.idz * G.idz));
+        if (!MX) {
+            a.dinvu[q] = diu;
+            a.dinvh[q] = dih;
+        }
+        const double z = (k + 0.5) * G.dz;
+        const double pq = ld(&S.pp[q]);
+        double gxw = 0.0, gxe = 0.0, gzs = 0.0, gzn = 0.0;
+        if (i > 0) gxw = (pq - ld(&S.pp[q - 1])) * G.idx - F.g * z * (rq - ld(&S.rho[q - 1])) * G.idx;
+        if (i + 1 < G.nx) gxe = (ld(&S.pp[q + 1]) - pq) * G.idx - F.g * z * (ld(&S.rho[q + 1]) - rq) * G.idx;
+        if (k > 0)
+            gzs = (pq - ld(&S.pp[q - G.P])) * G.idz - F.g * (k * G.dz) * (rq - ld(&S.rho[q - G.P])) * G.idz;
+        if (k + 1 < G.nz)
+            gzn = (ld(&S.pp[q + G.P]) - pq) * G.idz - F.g * ((k + 1) * G.dz) * (ld(&S.rho[q + G.P]) - rq) * G.idz;
+        const double u = ld(&S.u[q]), w = ld(&S.w[q]);
+        const double bu = rq * u * F.idt - 0.5 * (gxw + gxe);
+        const double bw = rq * w * F.idt - 0.5 * (gzs + gzn);
+        a.rho1[q] = rho1;
+        if (!MX) {
+            a.bu[q] = bu;
+            a.bw[q] = bw;
+            a.ua[q] = u;
+            a.wa[q] = w;
+            acc[0] = fma(bu, bu, acc[0]);
+            acc[1] = fma(bw, bw, acc[1]);
+        } else {
+            const int y = threadIdx.y + 2, x = threadIdx.x + 2;
+            auto t9 = [&](const Tile<2> &t) {
+                double v = cC * t[y][x];
+                v = fma(cE1, t[y][x + 1], v);
+                v = fma(cW1, t[y][x - 1], v);
+                v = fma(cN1, t[y + 1][x], v);
+                v = fma(cS1, t[y - 1][x], v);
+                v = fma(cE2, t[y][x + 2], v);
+                v = fma(cW2, t[y][x - 2], v);
+                v = fma(cN2, t[y + 2][x], v);
+                v = fma(cS2, t[y - 2][x], v);
+                return v;
+            };
+            const double r0u = bu - t9(tile_at<2>(sm, 0)), r0w = bw - t9(tile_at<2>(sm, 1));
+            m.T.cC[q] = (float)cC;
+            m.T.cE1[q] = (float)cE1;
+            m.T.cW1[q] = (float)cW1;
+            m.T.cE2[q] = (float)cE2;
+            m.T.cW2[q] = (float)cW2;
+            m.T.cN1[q] = (float)cN1;
+            m.T.cS1[q] = (float)cS1;
+            m.T.cN2[q] = (float)cN2;
+            m.T.cS2[q] = (float)cS2;
+            const float fdiu = (float)diu;
+            m.dinvu[q] = fdiu;
+            m.dinvh[q] = (float)dih;
+            const float fru = (float)r0u, frw = (float)r0w;
+            m.r0u[q] = fru;
+            m.r0w[q] = frw;
+            m.du[0][q] = fru * fdiu;
+            m.dw[0][q] = frw * fdiu;
+            acc[0] = fma(r0u, r0u, acc[0]);
+            acc[1] = fma(r0w, r0w, acc[1]);
+        }
+    }
+    if (MX) __syncthreads();
 }
 
-// One Jacobi sweep of T(X) = b for X = u (odd in x) and X = w (odd in z):
-// r = b - T(X), X <- X + r / T_CC. acc += (r_u^2, r_w^2).
-__device__ __forceinline__ void ph_mom(const StepArgs &a, const double *uin, const double *win,
-                                       double *uout, double *wout, double *sm, int bx, int bz,
-                                       double (&acc)[2])
+__device__ __forceinline__ void ph_pred(const StepArgs &a, int bx, int bz, double (&acc)[2])
 {
-    const Geom &G = a.G;
-    const Phys &F = a.F;
-    Tile<2> &su = tile_at<2>(sm, 0), &sw = tile_at<2>(sm, 1);
-    load_tile<BC_U, 2>(su, G, F, uin, bx, bz);
-    load_tile<BC_W, 2>(sw, G, F, win, bx, bz);
+    ph_pred_t<false>(a, MixedArgs{}, nullptr, bx, bz, acc);
+}
+
+// One Jacobi sweep of T(X) = b for two fields with wall rules BCA, BCB:
+// r = b - T(X), X <- X + r / T_CC. acc += (r_a^2, r_b^2).
+template <class R, int BCA, int BCB>
+__device__ __forceinline__ void ph_sweep2(const Geom &G, const Phys &F, const Stencil9T<R> &T,
+                                          const R *dinv, const R *ba, const R *bb, const R *xa,
+                                          const R *xb, R *ya, R *yb, double *sm, int bx, int bz,
+                                          R (&acc)[2])
+{
+    Tile<2, R> &sa = tile_at<2, R>(sm, 0), &sb = tile_at<2, R>(sm, 1);
+    load_tile<BCA, 2, R>(sa, G, F, xa, bx, bz);
+    load_tile<BCB, 2, R>(sb, G, F, xb, bx, bz);
     __syncthreads();
     int i, k;
     if (cell_of(G, bx, bz, i, k)) {
         const int q = cidx(G, i, k);
         const int y = threadIdx.y + 2, x = threadIdx.x + 2;
-        const double di = ld(&a.dinvu[q]);
-        const double ru = ld(&a.bu[q]) - apply9<2>(a.T, q, su, y, x);
-        const double rw = ld(&a.bw[q]) - apply9<2>(a.T, q, sw, y, x);
-        uout[q] = fma(ru, di, su[y][x]);
-        wout[q] = fma(rw, di, sw[y][x]);
-        acc[0] = fma(ru, ru, acc[0]);
-        acc[1] = fma(rw, rw, acc[1]);
+        const R di = ld(&dinv[q]);
+        const R ra = ld(&ba[q]) - apply9<2, R>(T, q, sa, y, x);
+        const R rb = ld(&bb[q]) - apply9<2, R>(T, q, sb, y, x);
+        ya[q] = fma(ra, di, sa[y][x]);
+        yb[q] = fma(rb, di, sb[y][x]);
+        acc[0] = fma(ra, ra, acc[0]);
+        acc[1] = fma(rb, rb, acc[1]);
     }
     __syncthreads();
+}
+
+// One Jacobi sweep of T(X) + lc L(X) = b for one field with wall rule BC
+// (lc = mu - mu/Pr turns the momentum stencil into the enthalpy one).
+// acc += r^2.
+template <class R, int BC>
+__device__ __forceinline__ void ph_sweep1(const Geom &G, const Phys &F, const Stencil9T<R> &T,
+                                          const R *dinv, const R *bv, R lc, const R *xin, R *xout,
+                                          double *sm, int bx, int bz, R (&acc)[1])
+{
+    Tile<2, R> &sh = tile_at<2, R>(sm, 0);
+    load_tile<BC, 2, R>(sh, G, F, xin, bx, bz);
+    __syncthreads();
+    int i, k;
+    if (cell_of(G, bx, bz, i, k)) {
+        const int q = cidx(G, i, k);
+        const int y = threadIdx.y + 2, x = threadIdx.x + 2;
+        R t = apply9<2, R>(T, q, sh, y, x);
+        if (lc != (R)0) t = fma(lc, lap5<2, R>(G, sh, y, x), t);
+        const R r = ld(&bv[q]) - t;
+        xout[q] = fma(r, ld(&dinv[q]), sh[y][x]);
+        acc[0] = fma(r, r, acc[0]);
+    }
+    __syncthreads();
+}
+
+// Momentum predictor sweep: u odd in x, w odd in z.
+__device__ __forceinline__ void ph_mom(const StepArgs &a, const double *uin, const double *win,
+                                       double *uout, double *wout, double *sm, int bx, int bz,
+                                       double (&acc)[2])
+{
+    ph_sweep2<double, BC_U, BC_W>(a.G, a.F, a.T, a.dinvu, a.bu, a.bw, uin, win, uout, wout, sm, bx,
+                                  bz, acc);
 }
 
 // ---------------------------------------------------------------------------
@@ -255,18 +379,31 @@ __device__ __forceinline__ void ph_mom(const StepArgs &a, const double *uin, con
 //   (rho^n h^n + rho^n K^n - p^{n-1})/dt - rho1 K1/dt - C(K1) + p^n/dt - rho1 g w1
 // with K1 = |u^{n+1/3}|^2/2 (eq. step1_3sd); initial guess h^n (into h0).
 // acc += b_h^2.
-__device__ __forceinline__ void ph_enth_rhs(const StepArgs &a, const double *u1, const double *w1,
-                                            double *h0, double *sm, int bx, int bz, double (&acc)[1])
+// MX: u^{n+1/3} = u^n + du (written to ua, wa), and instead of b_h and h0 the
+// FP64 residual r0 = b_h - T_h(h^n) (h^n with its wall rule), its FP32 copy
+// and the first FP32 sweep dh = r0 / T_h,CC; acc += r0^2 instead.
+template <bool MX>
+__device__ __forceinline__ void ph_enth_rhs_t(const StepArgs &a, const MixedArgs &m, const double *u1,
+                                              const double *w1, double *h0, double *sm, int bx,
+                                              int bz, double (&acc)[1])
 {
     const Geom &G = a.G;
     const Phys &F = a.F;
+    const State &S = a.S;
     Tile<2> &su = tile_at<2>(sm, 0), &sw = tile_at<2>(sm, 1);
-    load_tile<BC_U, 2>(su, G, F, u1, bx, bz);
-    load_tile<BC_W, 2>(sw, G, F, w1, bx, bz);
+    if (MX) {
+        load_tile_sum<BC_U, 2>(su, G, F, S.u, m.du[0], bx, bz);
+        load_tile_sum<BC_W, 2>(sw, G, F, S.w, m.dw[0], bx, bz);
+        load_tile<BC_H, 2>(tile_at<2>(sm, 2), G, F, S.h, bx, bz);
+    } else {
+        load_tile<BC_U, 2>(su, G, F, u1, bx, bz);
+        load_tile<BC_W, 2>(sw, G, F, w1, bx, bz);
+    }
     __syncthreads();
-    // K1 in place of u (ghost velocities give the mirrored cell's K); w1 at
-    // the cell centre is kept aside first
-    const double w1c = sw[threadIdx.y + 2][threadIdx.x + 2];
+    // K1 in place of u (ghost velocities give the mirrored cell's K); u1 and
+    // w1 at the cell centre are kept aside first
+    const double u1c = su[threadIdx.y + 2][threadIdx.x + 2], w1c = sw[threadIdx.y + 2][threadIdx.x + 2];
+    __syncthreads();
     {
         const int tid = threadIdx.x + threadIdx.y * BX;
         for (int e = tid; e < kT2; e += NTHREADS) {
@@ -278,7 +415,6 @@ __device__ __forceinline__ void ph_enth_rhs(const StepArgs &a, const double *u1,
     int i, k;
     if (cell_of(G, bx, bz, i, k)) {
         const int q = cidx(G, i, k);
-        const State &S = a.S;
         const int y = threadIdx.y + 2, x = threadIdx.x + 2;
         const Tile<2> &K = su;
         // convective sum of K1 with the four-point face values (wall faces
@@ -293,11 +429,30 @@ __device__ __forceinline__ void ph_enth_rhs(const StepArgs &a, const double *u1,
         const double rho1 = ld(&a.rho1[q]);
         const double be = (rq * h + rq * Kn - ld(&S.pold[q])) * F.idt;
         const double bh = be - rho1 * K[y][x] * F.idt - c + ld(&S.p[q]) * F.idt - rho1 * F.g * w1c;
-        a.bh[q] = bh;
-        h0[q] = h;
-        acc[0] = fma(bh, bh, acc[0]);
+        if (!MX) {
+            a.bh[q] = bh;
+            h0[q] = h;
+            acc[0] = fma(bh, bh, acc[0]);
+        } else {
+            a.ua[q] = u1c;
+            a.wa[q] = w1c;
+            const Tile<2> &sh = tile_at<2>(sm, 2);
+            double t = apply9<2>(a.T, q, sh, y, x);
+            if (F.nuh != F.mu) t = fma(F.mu - F.nuh, lap5<2>(G, sh, y, x), t);
+            const double r0 = bh - t;
+            const float fr = (float)r0;
+            m.r0h[q] = fr;
+            m.dh[0][q] = fr * ld(&m.dinvh[q]);
+            acc[0] = fma(r0, r0, acc[0]);
+        }
     }
     __syncthreads();
+}
+
+__device__ __forceinline__ void ph_enth_rhs(const StepArgs &a, const double *u1, const double *w1,
+                                            double *h0, double *sm, int bx, int bz, double (&acc)[1])
+{
+    ph_enth_rhs_t<false>(a, MixedArgs{}, u1, w1, h0, sm, bx, bz, acc);
 }
 
 // One Jacobi sweep of (rho1/dt) h + C(h) - (mu/Pr) L(h) = b_h (dh/dz = -g on
@@ -306,30 +461,17 @@ __device__ __forceinline__ void ph_enth_rhs(const StepArgs &a, const double *u1,
 __device__ __forceinline__ void ph_enth(const StepArgs &a, const double *hin, double *hout,
                                         double *sm, int bx, int bz, double (&acc)[1])
 {
-    const Geom &G = a.G;
-    const Phys &F = a.F;
-    Tile<2> &sh = tile_at<2>(sm, 0);
-    load_tile<BC_H, 2>(sh, G, F, hin, bx, bz);
-    __syncthreads();
-    int i, k;
-    if (cell_of(G, bx, bz, i, k)) {
-        const int q = cidx(G, i, k);
-        const int y = threadIdx.y + 2, x = threadIdx.x + 2;
-        double t = apply9<2>(a.T, q, sh, y, x);
-        if (F.nuh != F.mu) t = fma(F.mu - F.nuh, lap5<2>(G, sh, y, x), t);
-        const double r = ld(&a.bh[q]) - t;
-        hout[q] = fma(r, ld(&a.dinvh[q]), sh[y][x]);
-        acc[0] = fma(r, r, acc[0]);
-    }
-    __syncthreads();
+    ph_sweep1<double, BC_H>(a.G, a.F, a.T, a.dinvh, a.bh, a.F.mu - a.F.nuh, hin, hout, sm, bx, bz, acc);
 }
 
 // T^{n+1} = T^n + (h^{n+1} - h^n)/cp; psi = 1/(R T^{n+1}); rho^{n+2/3} = p^n/(R T^{n+1})
 // (eq. step3_3sd); face coefficients D_f = dt rho2_f / rho1_f (linear face
 // averages); the fine Helmholtz operator c = psi/dt, a_f = D_f |A_f|/(V Delta_f),
 // d = c + sum a_f and omega/d. h1 holds h^{n+1}.
-__device__ __forceinline__ void ph_eos(const StepArgs &a, const Level &L, const double *h1,
-                                       double *sm, int bx, int bz)
+// MX: h^{n+1} = h^n + dh, and FP32 copies of the fine operator into L32.
+template <bool MX>
+__device__ __forceinline__ void ph_eos_t(const StepArgs &a, const Level &L, const LevelF &L32,
+                                         const double *h1, const float *dh, double *sm, int bx, int bz)
 {
     const Geom &G = a.G;
     const Phys &F = a.F;
@@ -338,8 +480,9 @@ __device__ __forceinline__ void ph_eos(const StepArgs &a, const Level &L, const 
     double(*fz)[BX] = reinterpret_cast<double(*)[BX]>(sm + 2 * kT1 + BZ * (BX + 1));
     const State &S = a.S;
     const double icp = 1.0 / F.cp;
+    auto h1_of = [&](int q) { return MX ? ld(&S.h[q]) + (double)ld(&dh[q]) : ld(&h1[q]); };
     load_tile_fn<1>(s2, G, bx, bz, [&](int q, int, int) {
-        const double T1 = fma(ld(&h1[q]) - ld(&S.h[q]), icp, ld(&S.T[q]));
+        const double T1 = fma(h1_of(q) - ld(&S.h[q]), icp, ld(&S.T[q]));
         return ld(&S.p[q]) / (F.R * T1);
     });
     load_tile_fn<1>(s1, G, bx, bz, [&](int q, int, int) { return ld(&a.rho1[q]); });
@@ -361,7 +504,7 @@ __device__ __forceinline__ void ph_eos(const StepArgs &a, const Level &L, const 
     __syncthreads();
     if (in) {
         const int q = cidx(G, i, k);
-        const double h1q = ld(&h1[q]);
+        const double h1q = h1_of(q);
         const double T1 = fma(h1q - ld(&S.h[q]), icp, ld(&S.T[q]));
         const double psi = 1.0 / (F.R * T1);
         a.N.T[q] = T1;
@@ -380,14 +523,31 @@ __device__ __forceinline__ void ph_eos(const StepArgs &a, const Level &L, const 
         L.c[q] = c;
         L.d[q] = d;
         L.wd[q] = F.omega / d;
+        if (MX) {
+            L32.c[q] = (float)c;
+            L32.d[q] = (float)d;
+            L32.wd[q] = (float)(F.omega / d);
+            L32.ax[k * G.P + i] = (float)(Dw * ix2);
+            L32.az[k * G.P + i] = (float)(Ds * iz2);
+            if (i == G.nx - 1) L32.ax[k * G.P + G.nx] = 0.0f;
+            if (k == G.nz - 1) L32.az[G.nz * G.P + i] = 0.0f;
+        }
     }
     __syncthreads();
+}
+
+__device__ __forceinline__ void ph_eos(const StepArgs &a, const Level &L, const double *h1,
+                                       double *sm, int bx, int bz)
+{
+    ph_eos_t<false>(a, L, LevelF{}, h1, nullptr, sm, bx, bz);
 }
 
 // Galerkin coarsening with piecewise-constant transfer: the coarse reaction
 // term averages the four fine ones, a coarse face coefficient is a quarter
 // of the sum of its two fine faces. (bx, bz) is a tile of the coarse level.
-__device__ __forceinline__ void ph_coarsen(const Level &f, const Level &c, double omega, int bx, int bz)
+template <class R>
+__device__ __forceinline__ void ph_coarsen(const LevelT<R> &f, const LevelT<R> &c, double omega, int bx,
+                                           int bz)
 {
     const Geom &G = c.G;
     int I, K;
@@ -395,19 +555,20 @@ __device__ __forceinline__ void ph_coarsen(const Level &f, const Level &c, doubl
     const int Pf = f.G.P;
     const int q00 = (2 * K) * Pf + 2 * I;
     const int Q = cidx(G, I, K);
-    const double cc = 0.25 * (ld(&f.c[q00]) + ld(&f.c[q00 + 1]) + ld(&f.c[q00 + Pf]) + ld(&f.c[q00 + Pf + 1]));
-    const double aw = 0.25 * (ld(&f.ax[q00]) + ld(&f.ax[q00 + Pf]));
-    const double ae = 0.25 * (ld(&f.ax[q00 + 2]) + ld(&f.ax[q00 + Pf + 2]));
-    const double as = 0.25 * (ld(&f.az[q00]) + ld(&f.az[q00 + 1]));
-    const double an = 0.25 * (ld(&f.az[q00 + 2 * Pf]) + ld(&f.az[q00 + 2 * Pf + 1]));
+    const R q4 = (R)0.25;
+    const R cc = q4 * (ld(&f.c[q00]) + ld(&f.c[q00 + 1]) + ld(&f.c[q00 + Pf]) + ld(&f.c[q00 + Pf + 1]));
+    const R aw = q4 * (ld(&f.ax[q00]) + ld(&f.ax[q00 + Pf]));
+    const R ae = q4 * (ld(&f.ax[q00 + 2]) + ld(&f.ax[q00 + Pf + 2]));
+    const R as = q4 * (ld(&f.az[q00]) + ld(&f.az[q00 + 1]));
+    const R an = q4 * (ld(&f.az[q00 + 2 * Pf]) + ld(&f.az[q00 + 2 * Pf + 1]));
     c.c[Q] = cc;
     c.ax[K * G.P + I] = aw;
     c.az[K * G.P + I] = as;
     if (I == G.nx - 1) c.ax[K * G.P + G.nx] = ae;
     if (K == G.nz - 1) c.az[G.nz * G.P + I] = an;
-    const double d = cc + aw + ae + as + an;
+    const R d = cc + aw + ae + as + an;
     c.d[Q] = d;
-    c.wd[Q] = omega / d;
+    c.wd[Q] = (R)omega / d;
 }
 
 // ---------------------------------------------------------------------------
@@ -442,9 +603,12 @@ __device__ __forceinline__ void ph_H(const StepArgs &a, const double *U, const d
 //         - (1/V) sum_f D_f |A_f| [H_f . n + g z_f (rho2_N - rho2_i)/Delta_f],
 // the initial residual r = b - A x (x = xin, copied to xout) and p0 = 0.
 // acc += (b^2, r^2).
-__device__ __forceinline__ void ph_helm_rhs(const StepArgs &a, const Level &L, const double *xin,
-                                            double *xout, double *sm, int bx, int bz,
-                                            double (&acc)[2])
+// MX: r0 rounded to FP32 into L32.r (instead of L.r), and a zero pressure
+// increment and first CG direction of the FP32 solve.
+template <bool MX>
+__device__ __forceinline__ void ph_helm_rhs_t(const StepArgs &a, const Level &L, const LevelF &L32,
+                                              const MixedArgs &m, const double *xin, double *xout,
+                                              double *sm, int bx, int bz, double (&acc)[2])
 {
     const Geom &G = a.G;
     const Phys &F = a.F;
@@ -473,13 +637,35 @@ __device__ __forceinline__ void ph_helm_rhs(const StepArgs &a, const Level &L, c
         const double b = (ld(&a.S.rho[q]) + ld(&a.psi[q]) * r2q * F.g * z) * F.idt - flux * G.iV;
         const double r = b - helm_tile<1>(L, q, i, k, sx, y, x);
         a.b[q] = b;
-        L.r[q] = r;
         xout[q] = sx[y][x];
-        a.p0[q] = 0.0;
+        if (!MX) {
+            L.r[q] = r;
+            a.p0[q] = 0.0;
+        } else {
+            L32.r[q] = (float)r;
+            m.x[q] = 0.0f;
+            m.p0[q] = 0.0f;
+        }
         acc[0] = fma(b, b, acc[0]);
         acc[1] = fma(r, r, acc[1]);
     }
     __syncthreads();
+}
+
+__device__ __forceinline__ void ph_helm_rhs(const StepArgs &a, const Level &L, const double *xin,
+                                            double *xout, double *sm, int bx, int bz,
+                                            double (&acc)[2])
+{
+    ph_helm_rhs_t<false>(a, L, LevelF{}, MixedArgs{}, xin, xout, sm, bx, bz, acc);
+}
+
+// p' <- p' + dp (mixed-precision path: the FP32 solve's increment).
+__device__ __forceinline__ void ph_p_apply(const StepArgs &a, const MixedArgs &m, int bx, int bz)
+{
+    int i, k;
+    if (!cell_of(a.G, bx, bz, i, k)) return;
+    const int q = cidx(a.G, i, k);
+    a.N.pp[q] = ld(&a.N.pp[q]) + (double)ld(&m.x[q]);
 }
 
 // ---- V-cycle ----
@@ -488,20 +674,21 @@ __device__ __forceinline__ void ph_helm_rhs(const StepArgs &a, const Level &L, c
 // zero, e = (omega/d) r, and restrict the new residual r - A e (= (1-omega) r +
 // sum a e_N) by averaging the four fine cells of each coarse cell. (bx, bz)
 // is a tile of the fine level, whose sizes are even.
-__device__ __forceinline__ void ph_mg_down(const Level &f, const Level &c, double omega, double *sm,
-                                           int bx, int bz)
+template <class R>
+__device__ __forceinline__ void ph_mg_down(const LevelT<R> &f, const LevelT<R> &c, double omega,
+                                           double *sm, int bx, int bz)
 {
     const Geom &G = f.G;
-    Tile<1> &se = tile_at<1>(sm, 0);
-    double(*sres)[BX] = reinterpret_cast<double(*)[BX]>(sm + kT1);
-    load_tile_fn<1>(se, G, bx, bz, [&](int q, int, int) { return ld(&f.wd[q]) * ld(&f.r[q]); });
+    Tile<1, R> &se = tile_at<1, R>(sm, 0);
+    R(*sres)[BX] = reinterpret_cast<R(*)[BX]>(reinterpret_cast<R *>(sm) + kT1);
+    load_tile_fn<1, R>(se, G, bx, bz, [&](int q, int, int) { return ld(&f.wd[q]) * ld(&f.r[q]); });
     __syncthreads();
     int i, k;
     const int tx = threadIdx.x, ty = threadIdx.y;
     if (cell_of(G, bx, bz, i, k)) {
         const int q = cidx(G, i, k);
         const int y = ty + 1, x = tx + 1;
-        double t = (1.0 - omega) * ld(&f.r[q]);
+        R t = (R)(1.0 - omega) * ld(&f.r[q]);
         t = fma(ld(&f.ax[k * G.P + i]), se[y][x - 1], t);
         t = fma(ld(&f.ax[k * G.P + i + 1]), se[y][x + 1], t);
         t = fma(ld(&f.az[k * G.P + i]), se[y - 1][x], t);
@@ -515,14 +702,15 @@ __device__ __forceinline__ void ph_mg_down(const Level &f, const Level &c, doubl
     if (tx < BX / 2 && ty < BZ / 2) {
         const int I = bx * (BX / 2) + tx, K = bz * (BZ / 2) + ty;
         if (I < c.G.nx && K < c.G.nz)
-            c.r[cidx(c.G, I, K)] = 0.25 * ((sres[2 * ty][2 * tx] + sres[2 * ty][2 * tx + 1]) +
-                                           (sres[2 * ty + 1][2 * tx] + sres[2 * ty + 1][2 * tx + 1]));
+            c.r[cidx(c.G, I, K)] = (R)0.25 * ((sres[2 * ty][2 * tx] + sres[2 * ty][2 * tx + 1]) +
+                                              (sres[2 * ty + 1][2 * tx] + sres[2 * ty + 1][2 * tx + 1]));
     }
     __syncthreads();
 }
 
 // Coarsest level: one damped Jacobi sweep (first = starts from zero).
-__device__ __forceinline__ void ph_mg_coarse(const Level &L, const double *ein, double *eout, int first,
+template <class R>
+__device__ __forceinline__ void ph_mg_coarse(const LevelT<R> &L, const R *ein, R *eout, int first,
                                              double *sm, int bx, int bz)
 {
     const Geom &G = L.G;
@@ -534,13 +722,13 @@ __device__ __forceinline__ void ph_mg_coarse(const Level &L, const double *ein, 
         }
         return;
     }
-    Tile<1> &se = tile_at<1>(sm, 0);
-    load_tile_fn<1>(se, G, bx, bz, [&](int q, int, int) { return ld(&ein[q]); });
+    Tile<1, R> &se = tile_at<1, R>(sm, 0);
+    load_tile_fn<1, R>(se, G, bx, bz, [&](int q, int, int) { return ld(&ein[q]); });
     __syncthreads();
     if (cell_of(G, bx, bz, i, k)) {
         const int q = cidx(G, i, k);
         const int y = threadIdx.y + 1, x = threadIdx.x + 1;
-        eout[q] = fma(ld(&L.wd[q]), ld(&L.r[q]) - helm_tile<1>(L, q, i, k, se, y, x), se[y][x]);
+        eout[q] = fma(ld(&L.wd[q]), ld(&L.r[q]) - helm_tile<1, R>(L, q, i, k, se, y, x), se[y][x]);
     }
     __syncthreads();
 }
@@ -548,12 +736,13 @@ __device__ __forceinline__ void ph_mg_coarse(const Level &L, const double *ein, 
 // Prolongation step of a level: e' = e + P e_c (piecewise constant), then one
 // damped Jacobi post-smoothing sweep e'' = e' + (omega/d)(r - A e'). At the
 // finest level the result is z = M^-1 r; acc += r.z.
-__device__ __forceinline__ void ph_mg_up(const Level &f, const double *res, const double *ec, int Pc,
-                                         double *out, double *sm, int bx, int bz, double (&acc)[1])
+template <class R>
+__device__ __forceinline__ void ph_mg_up(const LevelT<R> &f, const R *res, const R *ec, int Pc, R *out,
+                                         double *sm, int bx, int bz, R (&acc)[1])
 {
     const Geom &G = f.G;
-    Tile<1> &se = tile_at<1>(sm, 0);
-    load_tile_fn<1>(se, G, bx, bz, [&](int q, int ii, int kk) {
+    Tile<1, R> &se = tile_at<1, R>(sm, 0);
+    load_tile_fn<1, R>(se, G, bx, bz, [&](int q, int ii, int kk) {
         return ld(&f.e[q]) + ld(&ec[(kk >> 1) * Pc + (ii >> 1)]);
     });
     __syncthreads();
@@ -561,8 +750,8 @@ __device__ __forceinline__ void ph_mg_up(const Level &f, const double *res, cons
     if (cell_of(G, bx, bz, i, k)) {
         const int q = cidx(G, i, k);
         const int y = threadIdx.y + 1, x = threadIdx.x + 1;
-        const double rq = ld(&res[q]);
-        const double z = fma(ld(&f.wd[q]), rq - helm_tile<1>(f, q, i, k, se, y, x), se[y][x]);
+        const R rq = ld(&res[q]);
+        const R z = fma(ld(&f.wd[q]), rq - helm_tile<1, R>(f, q, i, k, se, y, x), se[y][x]);
         out[q] = z;
         acc[0] = fma(rq, z, acc[0]);
     }
@@ -571,19 +760,20 @@ __device__ __forceinline__ void ph_mg_up(const Level &f, const double *res, cons
 
 // Single-level preconditioner: two damped Jacobi sweeps from zero,
 // z = e + (omega/d)(r - A e) with e = (omega/d) r; acc += r.z.
-__device__ __forceinline__ void ph_mg_single(const Level &f, double *out, double *sm, int bx, int bz,
-                                             double (&acc)[1])
+template <class R>
+__device__ __forceinline__ void ph_mg_single(const LevelT<R> &f, R *out, double *sm, int bx, int bz,
+                                             R (&acc)[1])
 {
     const Geom &G = f.G;
-    Tile<1> &se = tile_at<1>(sm, 0);
-    load_tile_fn<1>(se, G, bx, bz, [&](int q, int, int) { return ld(&f.wd[q]) * ld(&f.r[q]); });
+    Tile<1, R> &se = tile_at<1, R>(sm, 0);
+    load_tile_fn<1, R>(se, G, bx, bz, [&](int q, int, int) { return ld(&f.wd[q]) * ld(&f.r[q]); });
     __syncthreads();
     int i, k;
     if (cell_of(G, bx, bz, i, k)) {
         const int q = cidx(G, i, k);
         const int y = threadIdx.y + 1, x = threadIdx.x + 1;
-        const double rq = ld(&f.r[q]);
-        const double z = fma(ld(&f.wd[q]), rq - helm_tile<1>(f, q, i, k, se, y, x), se[y][x]);
+        const R rq = ld(&f.r[q]);
+        const R z = fma(ld(&f.wd[q]), rq - helm_tile<1, R>(f, q, i, k, se, y, x), se[y][x]);
         out[q] = z;
         acc[0] = fma(rq, z, acc[0]);
     }
@@ -594,47 +784,36 @@ __device__ __forceinline__ void ph_mg_single(const Level &f, double *out, double
 
 // p_new = z + beta p_old (computed once per tile cell) and q = A p_new;
 // acc += p.q.
-__device__ __forceinline__ void ph_pspmv(const StepArgs &a, const Level &L, const double *pold,
-                                         double *pnew, double beta, double *sm, int bx, int bz,
-                                         double (&acc)[1])
+template <class R>
+__device__ __forceinline__ void ph_pspmv(const LevelT<R> &L, const R *pold, R *pnew, R *qv, double beta,
+                                         double *sm, int bx, int bz, R (&acc)[1])
 {
-    const Geom &G = a.G;
-    const double *z = L.e2;
-    Tile<1> &sp = tile_at<1>(sm, 0);
-    load_tile_fn<1>(sp, G, bx, bz, [&](int q, int, int) { return fma(beta, ld(&pold[q]), ld(&z[q])); });
+    const Geom &G = L.G;
+    const R *z = L.e2;
+    const R b = (R)beta;
+    Tile<1, R> &sp = tile_at<1, R>(sm, 0);
+    load_tile_fn<1, R>(sp, G, bx, bz, [&](int q, int, int) { return fma(b, ld(&pold[q]), ld(&z[q])); });
     __syncthreads();
     int i, k;
     if (cell_of(G, bx, bz, i, k)) {
         const int q = cidx(G, i, k);
         const int y = threadIdx.y + 1, x = threadIdx.x + 1;
-        const double pq = sp[y][x];
-        const double Ap = helm_tile<1>(L, q, i, k, sp, y, x);
+        const R pq = sp[y][x];
+        const R Ap = helm_tile<1, R>(L, q, i, k, sp, y, x);
         pnew[q] = pq;
-        a.q[q] = Ap;
+        qv[q] = Ap;
         acc[0] = fma(pq, Ap, acc[0]);
     }
     __syncthreads();
-}
-
-// x += alpha p, r -= alpha q; acc += r^2.
-__device__ __forceinline__ void ph_update(const StepArgs &a, const Level &L, double *x, const double *p,
-                                          double alpha, int bx, int bz, double (&acc)[1])
-{
-    int i, k;
-    if (!cell_of(a.G, bx, bz, i, k)) return;
-    const int q = cidx(a.G, i, k);
-    x[q] = fma(alpha, ld(&p[q]), ld(&x[q]));
-    const double r = fma(-alpha, ld(&a.q[q]), ld(&L.r[q]));
-    L.r[q] = r;
-    acc[0] = fma(r, r, acc[0]);
 }
 
 // x += alpha p and r -= alpha q, fused with the first step of the next
 // V-cycle on the new residual (a CG iteration then needs one grid-wide
 // synchronisation less): the new residual and e = (omega/d) r_new are formed
 // on the tile and its halo from the old r and q in one pass.
-__device__ __forceinline__ void update_tiles(const StepArgs &a, const Level &L, const double *rin,
-                                             double alpha, Tile<1> &sr, Tile<1> &se, int bx, int bz)
+template <class R>
+__device__ __forceinline__ void update_tiles(const LevelT<R> &L, const R *qv, const R *rin, R alpha,
+                                             Tile<1, R> &sr, Tile<1, R> &se, int bx, int bz)
 {
     const Geom &G = L.G;
     const int i0 = bx * BX - 1, k0 = bz * BZ - 1;
@@ -643,10 +822,10 @@ __device__ __forceinline__ void update_tiles(const StepArgs &a, const Level &L, 
     for (int e = tid; e < NE; e += NTHREADS) {
         const int tk = e / W, ti = e - tk * W;
         const int i = i0 + ti, k = k0 + tk;
-        double rn = 0.0, ev = 0.0;
+        R rn = 0, ev = 0;
         if (i >= 0 && i < G.nx && k >= 0 && k < G.nz) {
             const int q = k * G.P + i;
-            rn = fma(-alpha, ld(&a.q[q]), ld(&rin[q]));
+            rn = fma(-alpha, ld(&qv[q]), ld(&rin[q]));
             ev = ld(&L.wd[q]) * rn;
         }
         sr[tk][ti] = rn;
@@ -658,23 +837,24 @@ __device__ __forceinline__ void update_tiles(const StepArgs &a, const Level &L, 
 // blocks still read the old residual while this one writes the new.
 // Single-level preconditioner: then z = e + (omega/d)(r_new - A e);
 // acc += (r_new^2, r_new . z).
-__device__ __forceinline__ void ph_update_single(const StepArgs &a, const Level &L, const double *rin,
-                                                 double *rout, double *x, const double *p,
-                                                 double alpha, double *sm, int bx, int bz,
-                                                 double (&acc)[2])
+template <class R>
+__device__ __forceinline__ void ph_update_single(const LevelT<R> &L, const R *qv, const R *rin, R *rout,
+                                                 R *x, const R *p, double alpha_d, double *sm, int bx,
+                                                 int bz, R (&acc)[2])
 {
     const Geom &G = L.G;
-    Tile<1> &sr = tile_at<1>(sm, 0), &se = tile_at<1>(sm, 1);
-    update_tiles(a, L, rin, alpha, sr, se, bx, bz);
+    const R alpha = (R)alpha_d;
+    Tile<1, R> &sr = tile_at<1, R>(sm, 0), &se = tile_at<1, R>(sm, 1);
+    update_tiles<R>(L, qv, rin, alpha, sr, se, bx, bz);
     __syncthreads();
     int i, k;
     if (cell_of(G, bx, bz, i, k)) {
         const int q = cidx(G, i, k);
         const int y = threadIdx.y + 1, xx = threadIdx.x + 1;
-        const double rn = sr[y][xx];
+        const R rn = sr[y][xx];
         x[q] = fma(alpha, ld(&p[q]), ld(&x[q]));
         rout[q] = rn;
-        const double z = fma(ld(&L.wd[q]), rn - helm_tile<1>(L, q, i, k, se, y, xx), se[y][xx]);
+        const R z = fma(ld(&L.wd[q]), rn - helm_tile<1, R>(L, q, i, k, se, y, xx), se[y][xx]);
         L.e2[q] = z;
         acc[0] = fma(rn, rn, acc[0]);
         acc[1] = fma(rn, z, acc[1]);
@@ -685,25 +865,26 @@ __device__ __forceinline__ void ph_update_single(const StepArgs &a, const Level 
 // Multigrid preconditioner: then the restriction step of the finest level
 // (pre-smoothed e and the averaged residual (1-omega) r_new + sum a e_N into
 // the next level); acc += r_new^2.
-__device__ __forceinline__ void ph_update_down(const StepArgs &a, const Level &f, const Level &c,
-                                               const double *rin, double *rout, double *x,
-                                               const double *p, double alpha, double omega,
-                                               double *sm, int bx, int bz, double (&acc)[1])
+template <class R>
+__device__ __forceinline__ void ph_update_down(const LevelT<R> &f, const LevelT<R> &c, const R *qv,
+                                               const R *rin, R *rout, R *x, const R *p, double alpha_d,
+                                               double omega, double *sm, int bx, int bz, R (&acc)[1])
 {
     const Geom &G = f.G;
-    Tile<1> &sr = tile_at<1>(sm, 0), &se = tile_at<1>(sm, 1);
-    double(*sres)[BX] = reinterpret_cast<double(*)[BX]>(sm + 2 * kT1);
-    update_tiles(a, f, rin, alpha, sr, se, bx, bz);
+    const R alpha = (R)alpha_d;
+    Tile<1, R> &sr = tile_at<1, R>(sm, 0), &se = tile_at<1, R>(sm, 1);
+    R(*sres)[BX] = reinterpret_cast<R(*)[BX]>(reinterpret_cast<R *>(sm) + 2 * kT1);
+    update_tiles<R>(f, qv, rin, alpha, sr, se, bx, bz);
     __syncthreads();
     int i, k;
     const int tx = threadIdx.x, ty = threadIdx.y;
     if (cell_of(G, bx, bz, i, k)) {
         const int q = cidx(G, i, k);
         const int y = ty + 1, xx = tx + 1;
-        const double rn = sr[y][xx];
+        const R rn = sr[y][xx];
         x[q] = fma(alpha, ld(&p[q]), ld(&x[q]));
         rout[q] = rn;
-        double t = (1.0 - omega) * rn;
+        R t = (R)(1.0 - omega) * rn;
         t = fma(ld(&f.ax[k * G.P + i]), se[y][xx - 1], t);
         t = fma(ld(&f.ax[k * G.P + i + 1]), se[y][xx + 1], t);
         t = fma(ld(&f.az[k * G.P + i]), se[y - 1][xx], t);
@@ -716,8 +897,8 @@ __device__ __forceinline__ void ph_update_down(const StepArgs &a, const Level &f
     if (tx < BX / 2 && ty < BZ / 2) {
         const int I = bx * (BX / 2) + tx, K = bz * (BZ / 2) + ty;
         if (I < c.G.nx && K < c.G.nz)
-            c.r[cidx(c.G, I, K)] = 0.25 * ((sres[2 * ty][2 * tx] + sres[2 * ty][2 * tx + 1]) +
-                                           (sres[2 * ty + 1][2 * tx] + sres[2 * ty + 1][2 * tx + 1]));
+            c.r[cidx(c.G, I, K)] = (R)0.25 * ((sres[2 * ty][2 * tx] + sres[2 * ty][2 * tx + 1]) +
+                                              (sres[2 * ty + 1][2 * tx] + sres[2 * ty + 1][2 * tx + 1]));
     }
     __syncthreads();
 }
@@ -821,6 +1002,24 @@ __device__ __forceinline__ void fin_helm(Scal *sc, const double (&t)[2], double 
     sc->cg_iters[corr] = 0;
     sc->cg_relres[corr] = t[0] > 0.0 ? sqrt(t[1] / t[0]) : 0.0;
     if (!isfinite(t[0]) || !isfinite(t[1])) sc->status = 5;
+}
+
+// Mixed precision: the inner FP32 solve's tolerance is relative to the
+// initial residual r0 = b - A p'_prev (kept in b2); nothing to solve if r0 is
+// already at the FP64 tolerance relative to b.
+__device__ __forceinline__ void fin_helm_mixed(Scal *sc, const double (&t)[2], double tol2_fp64, int corr)
+{
+    sc->b2 = t[1];
+    sc->r2 = t[1];
+    sc->cg_it = 0;
+    sc->corr = corr;
+    sc->trips[LOOP_CG] = 0;
+    sc->rz = 0.0;
+    sc->beta = 0.0;
+    sc->done[LOOP_CG] = t[1] <= tol2_fp64 * t[0];
+    sc->cg_iters[corr] = 0;
+    sc->cg_relres[corr] = 1.0;
+    if (!isfinite(t[0]) || !isfinite(t[1])) sc->status = GEA_ERR_NONFINITE;
 }
 
 __device__ __forceinline__ void fin_rz(Scal *sc, const double (&t)[1])

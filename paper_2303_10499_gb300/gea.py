@@ -21,6 +21,7 @@ from .build import LIB
 GEA_OK, GEA_ERR_INVAL, GEA_ERR_NOMEM, GEA_ERR_CUDA, GEA_ERR_NOCONV, GEA_ERR_NONFINITE, \
     GEA_ERR_STATE = range(7)
 STATE_CONSERVATIVE, STATE_FULL = 0, 1
+FLAG_GRAPH, FLAG_MIXED = 1, 2
 MEM_HOST, MEM_DEVICE = 0, 1
 FIELDS = {"rho1": 0, "u1": 1, "w1": 2, "h1": 3, "rho2": 4, "Hx": 5, "Hz": 6, "b": 7,
           "Dx": 8, "Dz": 9}
@@ -42,7 +43,7 @@ class _Const(C.Structure):
                 ("mu", C.c_double), ("Pr", C.c_double), ("dt", C.c_double),
                 ("n_corr", C.c_int32), ("jac_rtol", C.c_double), ("jac_maxit", C.c_int32),
                 ("cg_rtol", C.c_double), ("cg_maxit", C.c_int32),
-                ("mg_min_cells", C.c_int32), ("flags", C.c_int32)]
+                ("mg_min_cells", C.c_int32), ("flags", C.c_int32), ("mp_rtol", C.c_double)]
 
 
 class _View(C.Structure):
@@ -112,15 +113,20 @@ def _is_device(a) -> bool:
 class Solver:
     """One context of the library: a grid, its constants and device state."""
 
-    def __init__(self, grid, const, mg_min_cells: int = 0, stream=None, graph: bool = False):
+    def __init__(self, grid, const, mg_min_cells: int = 0, stream=None, graph: bool = False,
+                 mixed: bool = False, mp_rtol: float = 0.0):
         """graph=True runs each step as a CUDA graph of per-phase kernels
-        instead of the persistent cooperative kernel (GEA_FLAG_GRAPH)."""
+        instead of the persistent cooperative kernel (GEA_FLAG_GRAPH).
+        mixed=True selects the mixed-precision step (GEA_FLAG_MIXED): FP32
+        inner solves for FP64 increments, to ||r|| <= mp_rtol ||r0|| (0: the
+        library default)."""
         self.lib = library()
         self.grid, self.const = grid, const
         g = _Grid(grid.nx, grid.nz, grid.lx, grid.lz)
+        flags = (FLAG_GRAPH if graph else 0) | (FLAG_MIXED if mixed else 0)
         c = _Const(const.R, const.cp, const.g, const.p0, const.mu, const.Pr, const.dt,
                    const.n_corr, const.jac_rtol, const.jac_maxit, const.cg_rtol, const.cg_maxit,
-                   mg_min_cells, 1 if graph else 0)
+                   mg_min_cells, flags, mp_rtol)
         h = C.c_void_p()
         rc = self.lib.gea_create(C.byref(g), C.byref(c), C.byref(h))
         if rc != GEA_OK:
@@ -216,7 +222,7 @@ class Solver:
         return {"steps_done": s.steps_done, "jac_u": s.jac_u, "jac_h": s.jac_h,
                 "cg_iters": list(s.cg_iters)[:n], "cg_relres": list(s.cg_relres)[:n],
                 "status": s.status, "mg_levels": s.mg_levels, "launches": s.launches,
-                "driver": "persistent" if s.driver == 1 else "graph"}
+                "driver": {0: "graph", 1: "persistent", 2: "mixed"}[s.driver]}
 
     def field(self, name: str) -> np.ndarray:
         nx, nz = self.grid.nx, self.grid.nz

@@ -61,3 +61,16 @@ def test_binding_fails_loudly_without_a_gpu():
     wl = W.get("bubble160x80")
     with pytest.raises(gea.GeaError):
         gea.Solver(wl.grid, wl.const)
+
+
+def test_create_rejects_bad_flags_and_mixed_tolerance():
+    """Argument checks run before any CUDA call, so they answer on a
+    machine without a GPU too."""
+    from paper_2303_10499_gb300 import gea
+    from paper_2303_10499_gb300 import workloads as W
+    wl = W.get("bubble160x80")
+    for kw in (dict(mixed=True, mp_rtol=2.0), dict(mixed=True, mp_rtol=1e-9),
+               dict(mixed=True, mp_rtol=-1e-3)):
+        with pytest.raises(gea.GeaError) as ei:
+            gea.Solver(wl.grid, wl.const, **kw)
+        assert ei.value.code == gea.GEA_ERR_INVAL, kw
