@@ -8,7 +8,10 @@ solve leaves an error of about mp_rtol times the increment it computes, and
 these errors accumulate over the run. The bar for this path is the accuracy
 the application needs: max |theta'| error <= 1e-3 K after 100 steps of the
 rising-bubble workloads, with the relative L2 errors of rho, rho u, rho w
-and rho e reported and bounded.
+and rho e reported and bounded. Measured, the path is far inside that bar
+(about 1e-9 K and 5e-10 in the momenta), because each solve only computes
+the step's increment of an FP64 field; the bounds below are regression
+bounds a factor ~10 above the measured errors.
 """
 import numpy as np
 import pytest
@@ -65,9 +68,12 @@ def test_mixed_100_steps_against_oracle(gea, oracle_mod, name):
     dth = np.abs(th_g - th_o).max()
     print(name, "max|dtheta'|", dth, errs, st)
     assert dth <= 1e-3
-    assert errs["rho"] <= 1e-8 and errs["rhoe"] <= 1e-8 and errs["T"] <= 1e-8
-    assert errs["p"] <= 1e-8 and errs["pp"] <= 1e-8
-    assert errs["rhou"] <= 1e-4 and errs["rhow"] <= 1e-4
+    # measured (default mp_rtol 1e-5): dtheta' 1.3e-9 K, rho u 4.7e-10, rho w
+    # 4.1e-10, rho 4.5e-13, rho e 1.4e-13; the bounds leave a factor ~10
+    assert dth <= 1e-7
+    assert errs["rho"] <= 1e-11 and errs["rhoe"] <= 1e-11 and errs["T"] <= 1e-11
+    assert errs["p"] <= 1e-11 and errs["pp"] <= 1e-11
+    assert errs["rhou"] <= 5e-9 and errs["rhow"] <= 5e-9
     # the FP32 solves change mass only by the FP64 flux update (conservative)
     assert abs(m_g - m_o) / m_o < 1e-11
 
@@ -87,8 +93,9 @@ def test_mixed_ragged_sizes(gea, oracle_mod, nx, nz, ncorr):
     s.step(20)
     errs = field_errors(s.get_full(), so, c, grid)
     print((nx, nz), errs, s.stats())
-    assert errs["rho"] <= 1e-8 and errs["rhoe"] <= 1e-8
-    assert errs["rhou"] <= 1e-4 and errs["rhow"] <= 1e-4
+    # measured: up to 3.3e-10 (rho, rho e) and 3.2e-8 (momenta, 4 x 4 grid)
+    assert errs["rho"] <= 5e-9 and errs["rhoe"] <= 5e-9
+    assert errs["rhou"] <= 5e-7 and errs["rhow"] <= 5e-7
 
 
 def test_mixed_rest_atmosphere(gea):
