@@ -93,6 +93,8 @@ def library() -> C.CDLL:
         lib.gea_last_error.restype = C.c_char_p
         lib.gea_destroy.argtypes = [P]
         lib.gea_destroy.restype = None
+        I = C.c_int32
+        lib.gea_conv3x3.argtypes = [I, I, I, I, I, I, I, P, P, P, P, P, P, P]
         _lib = lib
     return _lib
 
@@ -242,3 +244,25 @@ class Solver:
         self._check(self.lib.gea_profile_step(self.h, buf, 64, C.byref(n)))
         return {buf[i].name.decode(): {"launches": buf[i].launches, "cells": buf[i].cells,
                                        "ms": buf[i].ms} for i in range(min(n.value, 64))}
+
+
+CONV_PLAIN, CONV_POOL, CONV_UPADD = 0, 1, 2
+CONV_RELU, CONV_OUT_F32 = 1, 2
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def conv3x3(x0, wt, y, n, h, w, cin, cout, mode=CONV_PLAIN, flags=0, x1=None, bias=None,
+            status=None, stream=None):
+    """3x3 convolution on the tensor cores (gea_conv3x3): device tensors,
+    bfloat16 activations and weights (N x H x W x C, [cout][3][3][cin]),
+    FP32 bias; y is bfloat16 or, with CONV_OUT_F32, float32. Enqueued on
+    `stream` (a torch stream or None for the current one)."""
+    import torch
+    st = (stream or torch.cuda.current_stream()).cuda_stream
+    rc = library().gea_conv3x3(n, h, w, cin, cout, mode, flags, _ptr(x0), _ptr(x1), _ptr(wt),
+                               _ptr(bias), _ptr(y), _ptr(status), st)
+    if rc != GEA_OK:
+        raise GeaError(rc, "gea_conv3x3 failed")

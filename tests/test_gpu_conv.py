@@ -1,0 +1,96 @@
+"""The tensor-core 3x3 convolution (gea_conv3x3) against the oracle's
+convolution on the same bfloat16 operands.
+
+The kernel accumulates in FP32 and the oracle in FP64, so FP32 outputs agree
+to ~1e-6 of the accumulated magnitude, and bfloat16 outputs agree exactly
+except where the accumulation-order difference moves a value across a
+rounding boundary: there they differ by one bfloat16 unit in the last place.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required")
+    from paper_2303_10499_gb300 import build as B
+    B.build()
+    from paper_2303_10499_gb300 import gea as G
+    return torch, G
+
+
+def to_bf16(torch, a):
+    return torch.tensor(np.asarray(a, dtype=np.float32)).to(torch.bfloat16)
+
+
+def bits(torch, t):
+    return t.contiguous().view(torch.int16).cuda()
+
+
+@pytest.mark.parametrize("cin", [16, 32, 64])
+@pytest.mark.parametrize("cout", [16, 32, 64])
+@pytest.mark.parametrize("mode", [0, 1, 2], ids=["plain", "pool", "upadd"])
+def test_conv3x3_matches_oracle(env, oracle_mod, cin, cout, mode):
+    torch, G = env
+    from oracle import unet
+    rng = np.random.default_rng(1000 * cin + 10 * cout + mode)
+    n, h, w = 2, 6, 300          # 300 = 2 x 128 + 44: a ragged last tile
+    if mode == 1:
+        xs = rng.standard_normal((n, 2 * h, 2 * w, cin))
+    else:
+        xs = rng.standard_normal((n, h, w, cin))
+    x1 = rng.standard_normal((n, h // 2, w // 2, cin)) if mode == 2 else None
+    wt = rng.standard_normal((cout, 3, 3, cin)) / np.sqrt(9 * cin)
+    b = rng.standard_normal(cout) * 0.1
+    xs, wt = unet.bf16_round(xs), unet.bf16_round(wt)
+    x1 = unet.bf16_round(x1) if x1 is not None else None
+    if mode == 0:
+        xin = xs
+    elif mode == 1:
+        xin = unet.bf16_round(unet.pool(xs))
+    else:
+        xin = unet.bf16_round(xs + unet.up(x1))
+    ref = unet.conv(xin, wt, b)
+    dx0 = bits(torch, to_bf16(torch, xs))
+    dx1 = bits(torch, to_bf16(torch, x1)) if x1 is not None else None
+    dw = bits(torch, to_bf16(torch, wt))
+    db = torch.tensor(b, dtype=torch.float32).cuda()
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for flags in (0, 1, 2, 3):
+        r = np.maximum(ref, 0.0) if flags & 1 else ref
+        if flags & 2:
+            y = torch.zeros((n, h, w, cout), dtype=torch.float32, device="cuda")
+        else:
+            y = torch.zeros((n, h, w, cout), dtype=torch.int16, device="cuda")
+        G.conv3x3(dx0, dw, y, n, h, w, cin, cout, mode=mode, flags=flags, x1=dx1, bias=db,
+                  status=status)
+        torch.cuda.synchronize()
+        if flags & 2:
+            got = y.cpu().numpy().astype(np.float64)
+            scale = np.abs(r).max()
+            err = np.abs(got - r).max() / scale
+            assert err < 1e-5, (flags, err)
+        else:
+            got = y.cpu().view(torch.bfloat16).float().numpy().astype(np.float64)
+            want = unet.bf16_round(r)
+            diff = np.abs(got - want)
+            ulp = np.maximum(np.abs(want), 1e-30) * 2.0 ** -7
+            bad = diff > ulp * 1.01
+            assert not bad.any(), (flags, int(bad.sum()), float(diff.max()))
+            # at most a small fraction of boundary cases
+            assert (diff > 0).mean() < 1e-3, (flags, float((diff > 0).mean()))
+    assert int(status.item()) == 0
+
+
+def test_conv3x3_rejects_bad_arguments(env):
+    torch, G = env
+    x = torch.zeros(16, dtype=torch.int16, device="cuda")
+    for kw in (dict(cin=8, cout=16), dict(cin=16, cout=48), dict(cin=16, cout=16, mode=3)):
+        with pytest.raises(G.GeaError):
+            G.conv3x3(x, x, x, 1, 4, 4, kw["cin"], kw["cout"], mode=kw.get("mode", 0))
+    with pytest.raises(G.GeaError):   # UPADD needs even sizes and x1
+        G.conv3x3(x, x, x, 1, 3, 4, 16, 16, mode=2, x1=x)
