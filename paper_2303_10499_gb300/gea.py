@@ -95,6 +95,19 @@ def library() -> C.CDLL:
         lib.gea_destroy.restype = None
         I = C.c_int32
         lib.gea_conv3x3.argtypes = [I, I, I, I, I, I, I, P, P, P, P, P, P, P]
+        lib.gea_net_param_count.restype = C.c_int64
+        lib.gea_net_layout.argtypes = [P]
+        lib.gea_net_create.argtypes = [I, I, I, I, C.POINTER(P)]
+        lib.gea_net_set_stream.argtypes = [P, P]
+        lib.gea_net_set_params.argtypes = [P, P, I]
+        lib.gea_net_get_params.argtypes = [P, P, I]
+        lib.gea_net_forward.argtypes = [P, I, I, I, P, P]
+        lib.gea_net_energy.argtypes = [P, P, P, P, P, C.POINTER(C.c_float)]
+        lib.gea_net_backward.argtypes = [P, P, P]
+        lib.gea_net_adam.argtypes = [P, P, C.c_float]
+        lib.gea_net_train_step.argtypes = [P, I, I, I, P, P, P, P, C.c_float, C.POINTER(C.c_float)]
+        lib.gea_net_destroy.argtypes = [P]
+        lib.gea_net_destroy.restype = None
         _lib = lib
     return _lib
 
@@ -266,3 +279,87 @@ def conv3x3(x0, wt, y, n, h, w, cin, cout, mode=CONV_PLAIN, flags=0, x1=None, bi
                                _ptr(bias), _ptr(y), _ptr(status), st)
     if rc != GEA_OK:
         raise GeaError(rc, "gea_conv3x3 failed")
+
+
+NET_RELU = 1
+NET_LAYERS = 15
+
+
+def net_param_count() -> int:
+    return int(library().gea_net_param_count())
+
+
+def net_layout() -> np.ndarray:
+    """Per layer: cin, cout, k, activation, input kind, level."""
+    d = np.zeros(6 * NET_LAYERS, dtype=np.int32)
+    _chk(library().gea_net_layout(d.ctypes.data), "gea_net_layout")
+    return d.reshape(NET_LAYERS, 6)
+
+
+def _chk(rc, what):
+    if rc != GEA_OK:
+        raise GeaError(rc, f"{what} failed")
+
+
+class Net:
+    """The learned pressure-correction network (include/gea_net.h). Tensor
+    arguments are contiguous float32 CUDA tensors."""
+
+    def __init__(self, n_max: int, h_max: int, w_max: int, relu: bool = True, stream=None):
+        import torch
+        self.lib = library()
+        h = C.c_void_p()
+        _chk(self.lib.gea_net_create(n_max, h_max, w_max, NET_RELU if relu else 0, C.byref(h)),
+             "gea_net_create")
+        self.h = h
+        self.np = net_param_count()
+        self.stream = stream or torch.cuda.current_stream()
+        _chk(self.lib.gea_net_set_stream(self.h, self.stream.cuda_stream), "gea_net_set_stream")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gea_net_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, theta):
+        if isinstance(theta, np.ndarray):
+            t = np.ascontiguousarray(theta, dtype=np.float32)
+            assert t.size == self.np
+            _chk(self.lib.gea_net_set_params(self.h, t.ctypes.data, MEM_HOST), "gea_net_set_params")
+        else:
+            assert theta.numel() == self.np and theta.is_contiguous()
+            _chk(self.lib.gea_net_set_params(self.h, theta.data_ptr(), MEM_DEVICE), "gea_net_set_params")
+
+    def get_params(self) -> np.ndarray:
+        t = np.empty(self.np, dtype=np.float32)
+        _chk(self.lib.gea_net_get_params(self.h, t.ctypes.data, MEM_HOST), "gea_net_get_params")
+        return t
+
+    def forward(self, r, y):
+        n, hh, ww = r.shape
+        _chk(self.lib.gea_net_forward(self.h, n, hh, ww, r.data_ptr(), y.data_ptr()), "gea_net_forward")
+
+    def energy(self, c, ax, az, dy) -> float:
+        loss = C.c_float()
+        _chk(self.lib.gea_net_energy(self.h, c.data_ptr(), ax.data_ptr(), az.data_ptr(), dy.data_ptr(),
+                                     C.byref(loss)), "gea_net_energy")
+        return float(loss.value)
+
+    def backward(self, dy, grad):
+        _chk(self.lib.gea_net_backward(self.h, dy.data_ptr(), grad.data_ptr()), "gea_net_backward")
+
+    def adam(self, grad, lr: float):
+        _chk(self.lib.gea_net_adam(self.h, grad.data_ptr(), lr), "gea_net_adam")
+
+    def train_step(self, r, c, ax, az, lr: float) -> float:
+        n, hh, ww = r.shape
+        loss = C.c_float()
+        _chk(self.lib.gea_net_train_step(self.h, n, hh, ww, r.data_ptr(), c.data_ptr(), ax.data_ptr(),
+                                         az.data_ptr(), lr, C.byref(loss)), "gea_net_train_step")
+        return float(loss.value)

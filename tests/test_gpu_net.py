@@ -1,0 +1,196 @@
+"""The learned pressure-correction network on the GPU (include/gea_net.h)
+against the network oracle (oracle/unet.py) in its bfloat16 mode, which
+rounds at the same points as the kernels.
+
+Tolerances. The kernels accumulate in FP32 and the oracle in FP64; where
+that difference moves a value across a bfloat16 rounding boundary the two
+differ by one unit in the last place (2^-8 relative) in that element, and the
+difference travels through the following layers. Measured relative L2
+differences are ~1e-4 in the output and ~1e-3 in the gradients; the bounds
+are 3e-3 (output) and 2e-2 (per-layer gradients).
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required")
+    from paper_2303_10499_gb300 import build as B
+    B.build()
+    from paper_2303_10499_gb300 import gea as G
+    return torch, G
+
+
+def scaled_params(unet, seed):
+    rng = np.random.default_rng(seed)
+    parts = []
+    for _, ws, bs in unet.param_shapes():
+        fan = ws[1] * ws[2] * ws[3]
+        parts.append(rng.standard_normal(int(np.prod(ws))) * np.sqrt(2.0 / fan))
+        parts.append(0.05 * rng.standard_normal(bs[0]))
+    return np.concatenate(parts).astype(np.float32).astype(np.float64)
+
+
+def normalised(r):
+    """x = r / rms(r) per sample, in the kernels' arithmetic (FP64 sum of
+    squares, FP32 division)."""
+    out = np.empty_like(r, dtype=np.float32)
+    for b in range(r.shape[0]):
+        rms = np.float32(np.sqrt(np.mean(r[b].astype(np.float64) ** 2)))
+        out[b] = r[b].astype(np.float32) / rms
+    return out.astype(np.float64)
+
+
+def smooth_fields(seed, n, h, w):
+    rng = np.random.default_rng(seed)
+    y, x = np.meshgrid(np.arange(h) + 0.5, np.arange(w) + 0.5, indexing="ij")
+    r = np.zeros((n, h, w))
+    for b in range(n):
+        for _ in range(6):
+            kx, ky = rng.integers(1, 6, 2)
+            r[b] += rng.standard_normal() * np.cos(np.pi * kx * x / w + rng.random()) * np.cos(np.pi * ky * y / h)
+        r[b] += 0.3 * rng.standard_normal((h, w))
+    return r.astype(np.float32)
+
+
+def operators(seed, n, h, w, ratio=10.0):
+    """Helmholtz coefficients like the pressure equation's: c ~ 1, face
+    coefficients ~ ratio / 4, zero on the walls."""
+    rng = np.random.default_rng(seed)
+    c = (1.0 + 0.1 * rng.random((n, h, w))).astype(np.float32)
+    ax = (ratio / 4 * (1.0 + 0.1 * rng.random((n, h, w + 1)))).astype(np.float32)
+    az = (ratio / 4 * (1.0 + 0.1 * rng.random((n, h + 1, w)))).astype(np.float32)
+    ax[:, :, 0] = ax[:, :, -1] = 0.0
+    az[:, 0, :] = az[:, -1, :] = 0.0
+    return c, ax, az
+
+
+def cuda(torch, a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
+
+
+def test_layout_matches_oracle(env, oracle_mod):
+    torch, G = env
+    from oracle import unet
+    assert G.net_param_count() == unet.n_params()
+    lay = G.net_layout()
+    kinds = {"x": 0}
+    for l, (name, ci, co, k, act, src) in enumerate(unet.ARCH):
+        kind = 0 if src == "x" else (1 if isinstance(src, str) else (2 if src[0] == "pool" else 3))
+        assert list(lay[l][:5]) == [ci, co, k, int(act), kind], name
+
+
+@pytest.mark.parametrize("relu", [True, False], ids=["relu", "linear"])
+def test_forward_and_backward_match_oracle(env, oracle_mod, relu):
+    torch, G = env
+    from oracle import unet
+    n, h, w = 2, 16, 136         # 136 = 128 + 8: a ragged tile at every level
+    th = scaled_params(unet, 31)
+    r = smooth_fields(32, n, h, w)
+    net = G.Net(n, h, w, relu=relu)
+    net.set_params(th)
+    y = torch.zeros((n, h, w), dtype=torch.float32, device="cuda")
+    net.forward(cuda(torch, r), y)
+    yo, cache = unet.forward(th, normalised(r), act=relu, bf16=True)
+    yg = y.cpu().numpy().astype(np.float64)
+    ferr = np.linalg.norm(yg - yo) / np.linalg.norm(yo)
+    dy = np.random.default_rng(33).standard_normal((n, h, w)).astype(np.float32)
+    grad = torch.zeros(G.net_param_count(), dtype=torch.float32, device="cuda")
+    net.backward(cuda(torch, dy), grad)
+    go, _ = unet.backward(cache, dy.astype(np.float64))
+    gg = grad.cpu().numpy().astype(np.float64)
+    per = {}
+    o = 0
+    for name, ws, bs in unet.param_shapes():
+        m = int(np.prod(ws)) + bs[0]
+        a, b = gg[o:o + m], go[o:o + m]
+        per[name] = np.linalg.norm(a - b) / np.linalg.norm(b)
+        o += m
+    print("forward", ferr, "grad", per)
+    assert ferr < 3e-3
+    assert max(per.values()) < 2e-2, per
+    assert np.linalg.norm(gg - go) / np.linalg.norm(go) < 1e-2
+
+
+def test_energy_loss_and_adam_match_oracle(env, oracle_mod):
+    torch, G = env
+    from oracle import unet
+    n, h, w = 2, 16, 32
+    th = scaled_params(unet, 41)
+    r = smooth_fields(42, n, h, w)
+    c, ax, az = operators(43, n, h, w)
+    net = G.Net(n, h, w)
+    net.set_params(th)
+    y = torch.zeros((n, h, w), dtype=torch.float32, device="cuda")
+    net.forward(cuda(torch, r), y)
+    dy = torch.zeros_like(y)
+    loss = net.energy(cuda(torch, c), cuda(torch, ax), cuda(torch, az), dy)
+    yg = y.cpu().numpy().astype(np.float64)
+    lo, go = unet.energy_loss(yg, normalised(r), c.astype(np.float64), ax.astype(np.float64),
+                              az.astype(np.float64))
+    assert abs(loss - lo) <= 1e-5 * abs(lo)
+    assert np.abs(dy.cpu().numpy() - go).max() <= 1e-5 * np.abs(go).max()
+    # one Adam step
+    g = np.random.default_rng(44).standard_normal(th.size).astype(np.float32)
+    net.adam(cuda(torch, g), 1e-3)
+    t1, _, _ = unet.adam(th, g.astype(np.float64), np.zeros(th.size), np.zeros(th.size), 1, 1e-3)
+    got = net.get_params().astype(np.float64)
+    assert np.abs(got - t1).max() <= 1e-6 * max(1.0, np.abs(t1).max())
+
+
+def test_training_approaches_the_exact_correction(env, oracle_mod):
+    """Trained on one operator family, the network's output approaches
+    A_hat^-1 x: the relative energy-norm error
+    eps^2 = (L(y) - L*) / (-L*), 1 for y = 0, falls well below 1 (L* from a
+    dense solve of each sample)."""
+    torch, G = env
+    from oracle import unet
+    n, h, w = 4, 32, 64
+    c, ax, az = operators(51, n, h, w)
+    dc, dax, daz = cuda(torch, c), cuda(torch, ax), cuda(torch, az)
+    net = G.Net(n, h, w, relu=False)
+    net.set_params(scaled_params(unet, 52) * 0.5)
+    losses = []
+    for it in range(300):
+        r = smooth_fields(1000 + it, n, h, w)
+        losses.append(net.train_step(cuda(torch, r), dc, dax, daz, 2e-3))
+    r = smooth_fields(7, n, h, w)
+    y = torch.zeros((n, h, w), dtype=torch.float32, device="cuda")
+    net.forward(cuda(torch, r), y)
+    yg = y.cpu().numpy().astype(np.float64)
+    x = normalised(r)
+    eps2 = []
+    for b in range(n):
+        M = np.zeros((h * w, h * w))
+        for k in range(h * w):
+            e = np.zeros(h * w)
+            e[k] = 1.0
+            M[:, k] = unet.helmholtz_apply(e.reshape(h, w), c[b], ax[b], az[b]).ravel()
+        M /= c[b].mean()
+        ystar = np.linalg.solve(M, x[b].ravel())
+        d = yg[b].ravel() - ystar
+        eps2.append(float(d @ M @ d / (ystar @ M @ ystar)))
+    print("loss first/last", losses[0], losses[-1], "eps^2", eps2)
+    assert losses[-1] < losses[0]
+    assert max(eps2) < 0.3
+
+
+def test_training_is_deterministic(env, oracle_mod):
+    torch, G = env
+    from oracle import unet
+    n, h, w = 2, 16, 32
+    c, ax, az = operators(61, n, h, w)
+    out = []
+    for _ in range(2):
+        net = G.Net(n, h, w)
+        net.set_params(scaled_params(unet, 62))
+        for it in range(5):
+            r = smooth_fields(2000 + it, n, h, w)
+            net.train_step(cuda(torch, r), cuda(torch, c), cuda(torch, ax), cuda(torch, az), 1e-3)
+        out.append(net.get_params())
+    assert np.array_equal(out[0], out[1])
