@@ -54,7 +54,7 @@ enum {
 };
 
 enum { GEA_STATE_CONSERVATIVE = 0, GEA_STATE_FULL = 1 };
-enum { GEA_FLAG_GRAPH = 1, GEA_FLAG_MIXED = 2 };
+enum { GEA_FLAG_GRAPH = 1, GEA_FLAG_MIXED = 2, GEA_FLAG_KEEP_R0 = 4 };
 enum { GEA_MEM_HOST = 0, GEA_MEM_DEVICE = 1 };
 
 /* Uniform Cartesian grid: nx * nz cells on [0, lx] x [0, lz] (metres).
@@ -98,6 +98,9 @@ typedef struct gea_grid {
  *            update x = x_old + dx. The pressure solve is skipped when
  *            ||r0|| <= cg_rtol ||b||. jac_maxit and cg_maxit cap the FP32
  *            iterations; gea_stats.cg_relres is then relative to ||r0||.
+ *            GEA_FLAG_KEEP_R0: keep the initial residual of the first
+ *            corrector's pressure solve (GEA_FIELD_R0; CUDA-graph driver;
+ *            not with GEA_FLAG_MIXED).
  *            Other bits must be 0.
  *  mp_rtol   relative tolerance of the FP32 solves (GEA_FLAG_MIXED only);
  *            0 selects 1e-5, otherwise 1e-7 <= mp_rtol < 1. */
@@ -192,12 +195,32 @@ int gea_get_stats(gea_ctx *ctx, gea_stats *s);
  * face arrays as in phix/phiz for GEA_FIELD_DX/DZ):
  *  RHO1 = rho^{n+1/3}; U1, W1 = u^{n+1/3}; H1 = h^{n+1}; RHO2 = rho^{n+2/3};
  *  HX, HZ = H(u) and B = pressure right-hand side of the last corrector;
- *  DX, DZ = face coefficients D_f = dt rho2_f / rho1_f. */
+ *  DX, DZ = face coefficients D_f = dt rho2_f / rho1_f;
+ *  HC, HAX, HAZ = the pressure operator of the last step,
+ *      (A e)_i = c_i e_i + sum_f a_f (e_i - e_N): c (cells), a on the x-faces
+ *      (nz rows of nx+1, zero on the walls) and on the z-faces (nz+1 rows);
+ *  R0 = initial residual b - A p' of the first corrector's pressure solve
+ *      of the last step (needs GEA_FLAG_KEEP_R0). */
 enum {
     GEA_FIELD_RHO1 = 0, GEA_FIELD_U1 = 1, GEA_FIELD_W1 = 2, GEA_FIELD_H1 = 3,
     GEA_FIELD_RHO2 = 4, GEA_FIELD_HX = 5, GEA_FIELD_HZ = 6, GEA_FIELD_B = 7,
-    GEA_FIELD_DX = 8, GEA_FIELD_DZ = 9
+    GEA_FIELD_DX = 8, GEA_FIELD_DZ = 9, GEA_FIELD_HC = 10, GEA_FIELD_HAX = 11,
+    GEA_FIELD_HAZ = 12, GEA_FIELD_R0 = 13
 };
+
+/* Use a learned pressure-correction network (include/gea_net.h) in the
+ * pressure solves of this context (an extension beyond the paper). mode 1:
+ * before each solve's first preconditioning, the network proposes a
+ * correction e for the initial residual r, and the solve starts from
+ * x + alpha e, r - alpha A e with alpha = r.e / e.A e, the step that
+ * minimises the A-norm error along e (so the start is never worse); the
+ * solve then runs to the same tolerance as without the network. mode 0:
+ * detach. The context does not own the network; it must outlive the
+ * attachment, and must not be used elsewhere while this context steps.
+ * Steps then run through the CUDA-graph driver. nx, nz must be multiples of
+ * 8 within the network's size. Errors: GEA_ERR_INVAL, GEA_ERR_CUDA. */
+struct gea_net;
+int gea_attach_net(gea_ctx *ctx, struct gea_net *net, int32_t mode);
 int gea_get_field(gea_ctx *ctx, int32_t which, double *host);
 
 /* Event-timed duration (ms) of the pressure solves (all correctors) of the

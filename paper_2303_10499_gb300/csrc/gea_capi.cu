@@ -11,6 +11,7 @@
 // first step.
 #include "gea_internal.cuh"
 #include "../../include/gea.h"
+#include "../../include/gea_net.h"
 
 #include <stdarg.h>
 #include <stdio.h>
@@ -41,6 +42,9 @@ struct gea_ctx {
     bool mixed = false;                   // GEA_FLAG_MIXED
     MixedArgs mx{};                       // FP32 buffers of the mixed-precision step
     std::vector<LevelF> Lf;               // FP32 hierarchy of the mixed-precision step
+    double *r0keep = nullptr;             // GEA_FLAG_KEEP_R0: first corrector's initial residual
+    gea_net *net = nullptr;               // attached learned initial guess (not owned)
+    float *net_r = nullptr, *net_e = nullptr;   // its dense input and output
     Scal *sc = nullptr;
     double *partials = nullptr;
     cudaGraph_t graph[2] = {nullptr, nullptr};
@@ -218,6 +222,14 @@ int record_step(gea_ctx *ctx, int from, cudaStream_t s, bool graph, Tracer *tr)
         CK(graph ? cudaEventRecordWithFlags(ctx->ev[2 * c], s, cudaEventRecordExternal)
                  : cudaEventRecord(ctx->ev[2 * c], s));
         launch_helm_rhs(a, L[0], c == 0 ? a.S.pp : a.N.pp, a.N.pp, c, s, tr); ++fixed;
+        if (ctx->r0keep && c == 0)
+            CK(cudaMemcpyAsync(ctx->r0keep, L[0].r, arr_bytes(ctx->G, ctx->G.nz), cudaMemcpyDeviceToDevice, s));
+        if (ctx->net) {
+            const int k = launch_net_guess<double>(a, L[0], L[0].r, a.q, a.N.pp, a.cg_rtol2, ctx->net, ctx->net_r,
+                                                   ctx->net_e, s, tr);
+            if (k < 0) return fail(ctx, GEA_ERR_CUDA, "network forward failed");
+            fixed += k;
+        }
         fixed += launch_vcycle(a, L, nlev, kCoarseSweeps, s, tr);   // z = M^-1 r_0
         rc = loop(LOOP_CG, ctx->C.cg_maxit, [&](cudaStream_t bs, cudaGraphConditionalHandle h, bool g) {
             launch_cg_iter(a, L, nlev, kCoarseSweeps, a.N.pp, bs, tr);
@@ -277,6 +289,12 @@ int record_step_mixed(gea_ctx *ctx, int from, cudaStream_t s, bool graph, Tracer
         CK(graph ? cudaEventRecordWithFlags(ctx->ev[2 * c], s, cudaEventRecordExternal)
                  : cudaEventRecord(ctx->ev[2 * c], s));
         launch_mx_helm_rhs(a, L0, Lf[0], m, c == 0 ? a.S.pp : a.N.pp, a.N.pp, c, s, tr); ++fixed;
+        if (ctx->net) {
+            const int k = launch_net_guess<float>(a, Lf[0], Lf[0].r, m.q, m.x, m.tol2, ctx->net, ctx->net_r,
+                                                  ctx->net_e, s, tr);
+            if (k < 0) return fail(ctx, GEA_ERR_CUDA, "network forward failed");
+            fixed += k;
+        }
         fixed += launch_mx_vcycle(a, Lf, nlev, kCoarseSweeps, s, tr);
         rc = loop(LOOP_CG, ctx->C.cg_maxit, [&](cudaStream_t bs, cudaGraphConditionalHandle h, bool g) {
             launch_mx_cg_iter(a, m, Lf, nlev, kCoarseSweeps, bs, tr);
@@ -391,7 +409,8 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
     if (!(c->R > 0) || !(c->cp > c->R) || !(c->g >= 0) || !(c->p0 > 0) || !(c->mu >= 0) ||
         !(c->Pr > 0) || !(c->dt > 0) || c->n_corr < 1 || c->n_corr > 4 || !(c->jac_rtol > 0) ||
         c->jac_maxit < 1 || !(c->cg_rtol > 0) || c->cg_maxit < 1 || c->mg_min_cells < 0 ||
-        (c->flags & ~(GEA_FLAG_GRAPH | GEA_FLAG_MIXED)))
+        (c->flags & ~(GEA_FLAG_GRAPH | GEA_FLAG_MIXED | GEA_FLAG_KEEP_R0)) ||
+        ((c->flags & GEA_FLAG_KEEP_R0) && (c->flags & GEA_FLAG_MIXED)))
         return GEA_ERR_INVAL;
     if ((c->flags & GEA_FLAG_MIXED) && c->mp_rtol != 0.0 && !(c->mp_rtol >= 1e-7 && c->mp_rtol < 1.0))
         return GEA_ERR_INVAL;
@@ -432,6 +451,7 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
     total += 33 * cell + 2 * fz;                   // scratch (Dz has nz+1 rows)
     total += 4 * cell;                             // staging for conservative fields
     total += 2 * cell + round_up(G.nz * sizeof(double), 256);   // theta_bar, theta'
+    if (c->flags & GEA_FLAG_KEEP_R0) total += cell;
     // FP64 levels (mixed precision: the finest only, for the FP64 residual)
     const size_t nlev64 = ctx->mixed ? 1 : lg.size();
     for (size_t l = 0; l < nlev64; ++l) total += 8 * arr_bytes(lg[l], lg[l].nz) + arr_bytes(lg[l], lg[l].nz + 1);
@@ -470,6 +490,7 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
     ctx->stage = take(4 * cell);
     ctx->thout = take(cell);
     ctx->thbar = take(round_up(G.nz * sizeof(double), 256));
+    if (c->flags & GEA_FLAG_KEEP_R0) ctx->r0keep = take(cell);
     for (size_t lv = 0; lv < nlev64; ++lv) {
         const Geom &g = lg[lv];
         Level l;
@@ -512,7 +533,7 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
     // step driver: the persistent kernel pays off while a phase is a few
     // tiles per resident block (its phases are latency-bound); on larger
     // grids the per-phase kernels keep more blocks resident per SM
-    if (!(c->flags & (GEA_FLAG_GRAPH | GEA_FLAG_MIXED))) {
+    if (!(c->flags & (GEA_FLAG_GRAPH | GEA_FLAG_MIXED | GEA_FLAG_KEEP_R0))) {
         const int pmax = persistent_max_blocks();
         cudaGetLastError();
         if (pmax > 0 && (long long)nb <= (long long)kPersistTilesPerBlock * pmax)
@@ -585,7 +606,7 @@ int gea_step_async(gea_ctx *ctx, int32_t n)
     if (!ctx || n < 0) return GEA_ERR_INVAL;
     if (!ctx->have_state) return fail(ctx, GEA_ERR_STATE, "no state set");
     if (n == 0) return GEA_OK;
-    if (ctx->pers_blocks > 0) {
+    if (ctx->pers_blocks > 0 && !ctx->net) {
         StepArgs a[2] = {step_args(ctx, 0), step_args(ctx, 1)};
         const int first = (int)((ctx->base + ctx->steps_at_sync) & 1);
         CK(launch_persistent(a, ctx->L.data(), (int)ctx->L.size(), kCoarseSweeps, ctx->C.n_corr,
@@ -694,7 +715,7 @@ int gea_get_stats(gea_ctx *ctx, gea_stats *s)
     s->status = h.last_status;
     s->mg_levels = ctx->mixed ? (int)ctx->Lf.size() : (int)ctx->L.size();
     s->launches = h.launches;
-    s->driver = ctx->mixed ? 2 : ctx->pers_blocks > 0 ? 1 : 0;
+    s->driver = ctx->mixed ? 2 : (ctx->pers_blocks > 0 && !ctx->net) ? 1 : 0;
     return GEA_OK;
 }
 
@@ -721,6 +742,13 @@ int gea_get_field(gea_ctx *ctx, int32_t which, double *host)
     case GEA_FIELD_B: src = ctx->b; break;
     case GEA_FIELD_DX: src = ctx->Dx; cols = G.nx + 1; break;
     case GEA_FIELD_DZ: src = ctx->Dz; rows = G.nz + 1; break;
+    case GEA_FIELD_HC: src = ctx->L[0].c; break;
+    case GEA_FIELD_HAX: src = ctx->L[0].ax; cols = G.nx + 1; break;
+    case GEA_FIELD_HAZ: src = ctx->L[0].az; rows = G.nz + 1; break;
+    case GEA_FIELD_R0:
+        if (!ctx->r0keep) return fail(ctx, GEA_ERR_INVAL, "R0 needs GEA_FLAG_KEEP_R0");
+        src = ctx->r0keep;
+        break;
     default: return fail(ctx, GEA_ERR_INVAL, "unknown field %d", which);
     }
     int rc = copy_out(ctx, host, src, cols, rows);
@@ -732,7 +760,7 @@ int gea_get_field(gea_ctx *ctx, int32_t which, double *host)
 double gea_last_pressure_ms(gea_ctx *ctx)
 {
     if (!ctx) return -1.0;
-    if (ctx->pers_blocks > 0) {
+    if (ctx->pers_blocks > 0 && !ctx->net) {
         Scal h;
         if (read_scal(ctx, &h)) return -1.0;
         return (double)h.press_ns * 1e-6;
@@ -786,6 +814,42 @@ int gea_profile_step(gea_ctx *ctx, gea_kernel_time *out, int32_t max_entries, in
     return gea_sync(ctx);
 }
 
+int gea_attach_net(gea_ctx *ctx, gea_net *net, int32_t mode)
+{
+    if (!ctx || mode < 0 || mode > 1 || (mode == 1 && !net)) return GEA_ERR_INVAL;
+    const Geom &G = ctx->G;
+    if (mode == 1 && (G.nx % 8 || G.nz % 8 || !gea_net_fits(net, 1, G.nz, G.nx)))
+        return fail(ctx, GEA_ERR_INVAL, "grid %d x %d does not fit the network", G.nx, G.nz);
+    if (ctx->stream) CK(cudaStreamSynchronize(ctx->stream));
+    // the step graphs change
+    for (int f = 0; f < 2; ++f) {
+        if (ctx->exec[f]) cudaGraphExecDestroy(ctx->exec[f]);
+        if (ctx->graph[f]) cudaGraphDestroy(ctx->graph[f]);
+        ctx->exec[f] = nullptr;
+        ctx->graph[f] = nullptr;
+    }
+    if (ctx->net_r) cudaFree(ctx->net_r);
+    if (ctx->net_e) cudaFree(ctx->net_e);
+    ctx->net_r = ctx->net_e = nullptr;
+    ctx->net = nullptr;
+    if (mode == 0) return GEA_OK;
+    const size_t bytes = (size_t)G.nx * G.nz * sizeof(float);
+    if (cudaMalloc(&ctx->net_r, bytes) != cudaSuccess || cudaMalloc(&ctx->net_e, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        if (ctx->net_r) cudaFree(ctx->net_r);
+        ctx->net_r = nullptr;
+        return fail(ctx, GEA_ERR_NOMEM, "network buffers");
+    }
+    // one eager forward pass outside any capture sets up the network's
+    // kernels (launch attributes are set on first use)
+    CK(cudaMemsetAsync(ctx->net_r, 0, bytes, ctx->stream));
+    if (gea_net_run(net, ctx->stream, 1, G.nz, G.nx, ctx->net_r, ctx->net_e) < 0)
+        return fail(ctx, GEA_ERR_CUDA, "network forward failed");
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->net = net;
+    return GEA_OK;
+}
+
 const char *gea_last_error(const gea_ctx *ctx) { return ctx ? ctx->err : "null context"; }
 
 void gea_destroy(gea_ctx *ctx)
@@ -800,6 +864,8 @@ void gea_destroy(gea_ctx *ctx)
     if (ctx->cap) cudaStreamDestroy(ctx->cap);
     if (ctx->cap2) cudaStreamDestroy(ctx->cap2);
     if (ctx->mem) cudaFree(ctx->mem);
+    if (ctx->net_r) cudaFree(ctx->net_r);
+    if (ctx->net_e) cudaFree(ctx->net_e);
     delete ctx;
 }
 

@@ -14,6 +14,13 @@
 
 #include "../../include/gea.h"
 
+struct gea_net;
+// The network forward pass on stream st (gea_net.cu); returns the number of
+// kernels launched or -1.
+int gea_net_run(gea_net *net, cudaStream_t st, int n, int h, int w, const float *r, float *y);
+// Whether a network can take n samples of h x w.
+bool gea_net_fits(const gea_net *net, int n, int h, int w);
+
 namespace gea {
 
 constexpr int BX = 32;          // threads per block along x (one warp per row)
@@ -114,6 +121,7 @@ struct Scal {
     unsigned bar_count, bar_gen;
     int u1_slot, h1_slot;       // 1 if u^{n+1/3} / h^{n+1} ended in the b buffers
     unsigned long long press_ns; // globaltimer nanoseconds of the pressure solves, last step
+    double galpha;              // step length of the learned initial guess
 };
 
 // Optional per-launch hook (profiled eager steps only; never during graph
@@ -126,7 +134,7 @@ struct Tracer {
 
 enum {
     CNT_PRED = 0, CNT_MOM = 1, CNT_ENTH_RHS = 2, CNT_ENTH = 3, CNT_HELM = 4,
-    CNT_RZ = 5, CNT_PQ = 6, CNT_UPD = 7, CNT_DIAG = 8
+    CNT_RZ = 5, CNT_PQ = 6, CNT_UPD = 7, CNT_DIAG = 8, CNT_GUESS = 9
 };
 
 // Everything one time step's kernels need: the state read (S) and written
@@ -278,6 +286,13 @@ void launch_step_end(Scal *sc, int fixed_launches, cudaStream_t st, Tracer *tr);
 void launch_diag(const Geom &G, const Phys &F, const State &S, const double *theta_bar,
                  double *theta_out, Scal *sc, double *partials, cudaStream_t st);
 int max_blocks(const Geom &G);
+// learned initial guess of the pressure solve (gea_kernels.cu): the network
+// (gea_net.cu) proposes a correction e for the residual r of level L; the
+// step x += alpha e, r -= alpha A e minimises the A-norm error along e.
+// Returns the number of kernels launched, or -1 if the network failed.
+template <class R>
+int launch_net_guess(const StepArgs &a, const LevelT<R> &L, R *r, R *q, R *x, double tol2, gea_net *net,
+                     float *dense_r, float *dense_e, cudaStream_t st, Tracer *tr);
 // mixed-precision step (gea_mixed.cu)
 void launch_mx_pred(const StepArgs &a, const MixedArgs &m, cudaStream_t st, Tracer *tr);
 void launch_mx_mom(const StepArgs &a, const MixedArgs &m, const float *ui, const float *wi, float *uo,

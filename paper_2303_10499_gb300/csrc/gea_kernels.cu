@@ -438,6 +438,65 @@ int launch_cg_iter(const StepArgs &a, Level *L, int nlev, int ncoarse, double *x
     return 2 + launch_vcycle_rest(a, L, nlev, ncoarse, st, tr);
 }
 
+namespace {
+
+template <class R>
+__global__ void k_guess_in(Geom G, const R *r, float *dense, Scal *sc)
+{
+    if (loop_over(sc, LOOP_CG)) return;
+    int i, k;
+    if (!cell_of(G, blockIdx.x, blockIdx.y, i, k)) return;
+    dense[(size_t)k * G.nx + i] = (float)r[cidx(G, i, k)];
+}
+
+template <class R>
+__global__ void k_guess_dots(LevelT<R> L, const float *e, const R *r, R *q, Scal *sc, double *partials)
+{
+    if (loop_over(sc, LOOP_CG)) return;
+    __shared__ double sm[kT1];
+    __shared__ double red[2 * NTHREADS];
+    R acc[2] = {(R)0, (R)0};
+    double tot[2];
+    ph_guess_dots<R>(L, e, r, q, sm, blockIdx.x, blockIdx.y, acc);
+    if (grid_sum<2, R>(acc, red, partials, &sc->counters[CNT_GUESS], tot)) fin_guess_dots(sc, tot);
+}
+
+template <class R>
+__global__ void k_guess_apply(LevelT<R> L, const float *e, const R *q, R *r, R *x, Scal *sc, double *partials,
+                              double tol2)
+{
+    if (loop_over(sc, LOOP_CG)) return;
+    __shared__ double red[NTHREADS];
+    R acc[1] = {(R)0};
+    double tot[1];
+    ph_guess_apply<R>(L, e, q, r, x, sc->galpha, blockIdx.x, blockIdx.y, acc);
+    if (grid_sum<1, R>(acc, red, partials, &sc->counters[CNT_GUESS], tot)) fin_guess_apply(sc, tot, tol2);
+}
+
+}  // namespace
+
+template <class R>
+int launch_net_guess(const StepArgs &a, const LevelT<R> &L, R *r, R *q, R *x, double tol2, gea_net *net,
+                     float *dense_r, float *dense_e, cudaStream_t st, Tracer *tr)
+{
+    const Geom &G = L.G;
+    TRACED(tr, "guess_in", ncell(G), (k_guess_in<R><<<grid_of(G), kBlock, 0, st>>>(G, r, dense_r, a.sc)));
+    if (tr) tr->begin("net_forward", ncell(G), st);
+    const int nk = gea_net_run(net, st, 1, G.nz, G.nx, dense_r, dense_e);
+    if (tr) tr->end(st);
+    if (nk < 0) return -1;
+    TRACED(tr, "guess_dots", ncell(G),
+           (k_guess_dots<R><<<grid_of(G), kBlock, 0, st>>>(L, dense_e, r, q, a.sc, a.partials)));
+    TRACED(tr, "guess_apply", ncell(G),
+           (k_guess_apply<R><<<grid_of(G), kBlock, 0, st>>>(L, dense_e, q, r, x, a.sc, a.partials, tol2)));
+    return 3 + nk;
+}
+
+template int launch_net_guess<double>(const StepArgs &, const LevelT<double> &, double *, double *, double *,
+                                      double, gea_net *, float *, float *, cudaStream_t, Tracer *);
+template int launch_net_guess<float>(const StepArgs &, const LevelT<float> &, float *, float *, float *, double,
+                                     gea_net *, float *, float *, cudaStream_t, Tracer *);
+
 void launch_correct(const StepArgs &a, cudaStream_t st, Tracer *tr)
 {
     TRACED(tr, "correct", ncell(a.G), (k_correct<<<grid_of(a.G), kBlock, 0, st>>>(a)));

@@ -662,6 +662,20 @@ bool shape_ok(const gea_net *net, int n, int h, int w)
 
 }  // namespace
 
+int gea_net_run(gea_net *net, cudaStream_t st, int n, int h, int w, const float *r, float *y)
+{
+    if (!net || !shape_ok(net, n, h, w)) return -1;
+    cudaStream_t old = net->st;
+    net->st = st;
+    const int rc = forward(net, n, h, w, r, y);
+    net->st = old;
+    // per-sample statistics (2), input scaling, first layer, 13 tensor-core
+    // layers, output layer
+    return rc ? -1 : 2 + 1 + 1 + (kOut - 1) + 1;
+}
+
+bool gea_net_fits(const gea_net *net, int n, int h, int w) { return net && shape_ok(net, n, h, w); }
+
 extern "C" {
 
 int64_t gea_net_param_count(void) { return count_params(nullptr, nullptr); }

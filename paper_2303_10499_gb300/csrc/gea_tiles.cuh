@@ -903,6 +903,45 @@ __device__ __forceinline__ void ph_update_down(const LevelT<R> &f, const LevelT<
     __syncthreads();
 }
 
+// ---- learned initial guess of a pressure solve ----
+
+// The network's proposal e (dense FP32, row k at k nx): q = A e and
+// acc += (r . e, e . A e).
+template <class R>
+__device__ __forceinline__ void ph_guess_dots(const LevelT<R> &L, const float *e, const R *r, R *q, double *sm,
+                                              int bx, int bz, R (&acc)[2])
+{
+    const Geom &G = L.G;
+    Tile<1, R> &se = tile_at<1, R>(sm, 0);
+    load_tile_fn<1, R>(se, G, bx, bz, [&](int, int i, int k) { return (R)ld(&e[(size_t)k * G.nx + i]); });
+    __syncthreads();
+    int i, k;
+    if (cell_of(G, bx, bz, i, k)) {
+        const int qi = cidx(G, i, k);
+        const int y = threadIdx.y + 1, x = threadIdx.x + 1;
+        const R Ae = helm_tile<1, R>(L, qi, i, k, se, y, x);
+        q[qi] = Ae;
+        acc[0] = fma(ld(&r[qi]), se[y][x], acc[0]);
+        acc[1] = fma(se[y][x], Ae, acc[1]);
+    }
+    __syncthreads();
+}
+
+// x += alpha e, r -= alpha q; acc += r^2.
+template <class R>
+__device__ __forceinline__ void ph_guess_apply(const LevelT<R> &L, const float *e, const R *q, R *r, R *x,
+                                               double alpha_d, int bx, int bz, R (&acc)[1])
+{
+    int i, k;
+    if (!cell_of(L.G, bx, bz, i, k)) return;
+    const int qi = cidx(L.G, i, k);
+    const R alpha = (R)alpha_d;
+    x[qi] = fma(alpha, (R)ld(&e[(size_t)k * L.G.nx + i]), ld(&x[qi]));
+    const R rn = fma(-alpha, ld(&q[qi]), ld(&r[qi]));
+    r[qi] = rn;
+    acc[0] = fma(rn, rn, acc[0]);
+}
+
 // Flux and velocity correction: F_f = D_f (H_f - G_f) with
 // G_f = (p'_b - p'_a)/Delta - g z_f (rho2_b - rho2_a)/Delta; u = (dt/rho1)(H - G_cell);
 // p = p' - rho2 g z; rho = p / (R T^{n+1}) = p psi; phi = F |A|; p^{n-1} <- p^n.
@@ -1044,6 +1083,21 @@ __device__ __forceinline__ void fin_update(Scal *sc, const double (&t)[1], doubl
     sc->cg_iters[c] = it;
     sc->cg_relres[c] = sc->b2 > 0.0 ? sqrt(t[0] / sc->b2) : 0.0;
     if (!isfinite(t[0])) sc->status = 5;
+    else if (t[0] <= tol2 * sc->b2) sc->done[LOOP_CG] = 1;
+}
+
+// the step length minimising the A-norm error along e: alpha = r.e / e.Ae
+// (0 if e.Ae is not positive)
+__device__ __forceinline__ void fin_guess_dots(Scal *sc, const double (&t)[2])
+{
+    sc->galpha = (t[1] > 0.0 && isfinite(t[0]) && isfinite(t[1])) ? t[0] / t[1] : 0.0;
+}
+
+__device__ __forceinline__ void fin_guess_apply(Scal *sc, const double (&t)[1], double tol2)
+{
+    sc->r2 = t[0];
+    sc->cg_relres[sc->corr] = sc->b2 > 0.0 ? sqrt(t[0] / sc->b2) : 0.0;
+    if (!isfinite(t[0])) sc->status = GEA_ERR_NONFINITE;
     else if (t[0] <= tol2 * sc->b2) sc->done[LOOP_CG] = 1;
 }
 

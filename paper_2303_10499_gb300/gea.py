@@ -21,10 +21,10 @@ from .build import LIB
 GEA_OK, GEA_ERR_INVAL, GEA_ERR_NOMEM, GEA_ERR_CUDA, GEA_ERR_NOCONV, GEA_ERR_NONFINITE, \
     GEA_ERR_STATE = range(7)
 STATE_CONSERVATIVE, STATE_FULL = 0, 1
-FLAG_GRAPH, FLAG_MIXED = 1, 2
+FLAG_GRAPH, FLAG_MIXED, FLAG_KEEP_R0 = 1, 2, 4
 MEM_HOST, MEM_DEVICE = 0, 1
 FIELDS = {"rho1": 0, "u1": 1, "w1": 2, "h1": 3, "rho2": 4, "Hx": 5, "Hz": 6, "b": 7,
-          "Dx": 8, "Dz": 9}
+          "Dx": 8, "Dz": 9, "hc": 10, "hax": 11, "haz": 12, "r0": 13}
 FULL_FIELDS = ("rho", "u", "w", "T", "h", "p", "pp", "pold", "phix", "phiz")
 
 
@@ -95,6 +95,7 @@ def library() -> C.CDLL:
         lib.gea_destroy.restype = None
         I = C.c_int32
         lib.gea_conv3x3.argtypes = [I, I, I, I, I, I, I, P, P, P, P, P, P, P]
+        lib.gea_attach_net.argtypes = [P, P, I]
         lib.gea_net_param_count.restype = C.c_int64
         lib.gea_net_layout.argtypes = [P]
         lib.gea_net_create.argtypes = [I, I, I, I, C.POINTER(P)]
@@ -129,7 +130,7 @@ class Solver:
     """One context of the library: a grid, its constants and device state."""
 
     def __init__(self, grid, const, mg_min_cells: int = 0, stream=None, graph: bool = False,
-                 mixed: bool = False, mp_rtol: float = 0.0):
+                 mixed: bool = False, mp_rtol: float = 0.0, keep_r0: bool = False):
         """graph=True runs each step as a CUDA graph of per-phase kernels
         instead of the persistent cooperative kernel (GEA_FLAG_GRAPH).
         mixed=True selects the mixed-precision step (GEA_FLAG_MIXED): FP32
@@ -138,7 +139,8 @@ class Solver:
         self.lib = library()
         self.grid, self.const = grid, const
         g = _Grid(grid.nx, grid.nz, grid.lx, grid.lz)
-        flags = (FLAG_GRAPH if graph else 0) | (FLAG_MIXED if mixed else 0)
+        flags = (FLAG_GRAPH if graph else 0) | (FLAG_MIXED if mixed else 0) | \
+            (FLAG_KEEP_R0 if keep_r0 else 0)
         c = _Const(const.R, const.cp, const.g, const.p0, const.mu, const.Pr, const.dt,
                    const.n_corr, const.jac_rtol, const.jac_maxit, const.cg_rtol, const.cg_maxit,
                    mg_min_cells, flags, mp_rtol)
@@ -241,13 +243,20 @@ class Solver:
 
     def field(self, name: str) -> np.ndarray:
         nx, nz = self.grid.nx, self.grid.nz
-        shape = {"Dx": (nz, nx + 1), "Dz": (nz + 1, nx)}.get(name, (nz, nx))
+        shape = {"Dx": (nz, nx + 1), "Dz": (nz + 1, nx), "hax": (nz, nx + 1),
+                 "haz": (nz + 1, nx)}.get(name, (nz, nx))
         out = np.empty(shape)
         self._check(self.lib.gea_get_field(self.h, FIELDS[name], out.ctypes.data))
         return out
 
     def pressure_ms(self) -> float:
         return float(self.lib.gea_last_pressure_ms(self.h))
+
+    def attach_net(self, net, mode: int = 1):
+        """Use a Net as the learned initial guess of the pressure solves
+        (mode 1) or detach it (mode 0, net None)."""
+        self._check(self.lib.gea_attach_net(self.h, net.h if net is not None else None, mode))
+        self._net = net if mode else None   # keep it alive while attached
 
     def profile_step(self) -> Dict[str, Dict]:
         """Advance one step with every kernel launch timed by CUDA events on
