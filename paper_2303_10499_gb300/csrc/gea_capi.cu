@@ -160,6 +160,56 @@ int capture_while(gea_ctx *ctx, cudaStream_t s, Body body)
     return GEA_OK;
 }
 
+// The learned initial guess of a pressure solve: convert r0 for the network
+// and, in a graph, run the network and the step under an IF node that the
+// conversion kernel sets (skipped when the solve has already converged);
+// eagerly, skip them on the host in that case. Returns kernels launched
+// outside loops, or a negative value on failure.
+template <class R>
+int record_guess(gea_ctx *ctx, const StepArgs &a, const LevelT<R> &L, R *q, R *x, double tol2, cudaStream_t s,
+                 bool graph, Tracer *tr)
+{
+    if (!graph) {
+        launch_guess_in<R>(a, L, L.r, ctx->net_r, (cudaGraphConditionalHandle)0, false, s, tr);
+        Scal h;
+        if (cudaMemcpyAsync(&h, ctx->sc, sizeof(Scal), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return -1;
+        if (h.done[LOOP_CG] || h.status) return 1;
+        const int k = launch_net_guess<R>(a, L, L.r, q, x, tol2, ctx->net, ctx->net_r, ctx->net_e, s, tr);
+        return k < 0 ? -1 : 1 + k;
+    }
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g;
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *edges = nullptr;
+    size_t ndeps = 0;
+    if (cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, &edges, &ndeps) != cudaSuccess ||
+        cs != cudaStreamCaptureStatusActive)
+        return -1;
+    cudaGraphConditionalHandle h;
+    if (cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault) != cudaSuccess) return -1;
+    launch_guess_in<R>(a, L, L.r, ctx->net_r, h, true, s, tr);
+    if (cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, &edges, &ndeps) != cudaSuccess) return -1;
+    cudaGraphNodeParams prm = {cudaGraphNodeTypeConditional};
+    prm.conditional.handle = h;
+    prm.conditional.type = cudaGraphCondTypeIf;
+    prm.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (cudaGraphAddNode(&node, g, deps, edges, ndeps, &prm) != cudaSuccess) return -1;
+    cudaGraph_t bodyg = prm.conditional.phGraph_out[0];
+    if (cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies) !=
+            cudaSuccess ||
+        cudaStreamBeginCaptureToGraph(ctx->cap2, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+            cudaSuccess)
+        return -1;
+    const int k = launch_net_guess<R>(a, L, L.r, q, x, tol2, ctx->net, ctx->net_r, ctx->net_e, ctx->cap2, tr);
+    cudaGraph_t out = nullptr;
+    if (cudaStreamEndCapture(ctx->cap2, &out) != cudaSuccess || k < 0) return -1;
+    // the launches of the IF body are not counted (they may not run)
+    return 1;
+}
+
 // Run a loop body eagerly on `s` until its control kernel reports that the
 // loop is finished (converged, failed or at its trip cap).
 template <class Body>
@@ -225,9 +275,8 @@ int record_step(gea_ctx *ctx, int from, cudaStream_t s, bool graph, Tracer *tr)
         if (ctx->r0keep && c == 0)
             CK(cudaMemcpyAsync(ctx->r0keep, L[0].r, arr_bytes(ctx->G, ctx->G.nz), cudaMemcpyDeviceToDevice, s));
         if (ctx->net) {
-            const int k = launch_net_guess<double>(a, L[0], L[0].r, a.q, a.N.pp, a.cg_rtol2, ctx->net, ctx->net_r,
-                                                   ctx->net_e, s, tr);
-            if (k < 0) return fail(ctx, GEA_ERR_CUDA, "network forward failed");
+            const int k = record_guess<double>(ctx, a, L[0], a.q, a.N.pp, a.cg_rtol2, s, graph, tr);
+            if (k < 0) return fail(ctx, GEA_ERR_CUDA, "learned initial guess failed");
             fixed += k;
         }
         fixed += launch_vcycle(a, L, nlev, kCoarseSweeps, s, tr);   // z = M^-1 r_0
@@ -290,9 +339,8 @@ int record_step_mixed(gea_ctx *ctx, int from, cudaStream_t s, bool graph, Tracer
                  : cudaEventRecord(ctx->ev[2 * c], s));
         launch_mx_helm_rhs(a, L0, Lf[0], m, c == 0 ? a.S.pp : a.N.pp, a.N.pp, c, s, tr); ++fixed;
         if (ctx->net) {
-            const int k = launch_net_guess<float>(a, Lf[0], Lf[0].r, m.q, m.x, m.tol2, ctx->net, ctx->net_r,
-                                                  ctx->net_e, s, tr);
-            if (k < 0) return fail(ctx, GEA_ERR_CUDA, "network forward failed");
+            const int k = record_guess<float>(ctx, a, Lf[0], m.q, m.x, m.tol2, s, graph, tr);
+            if (k < 0) return fail(ctx, GEA_ERR_CUDA, "learned initial guess failed");
             fixed += k;
         }
         fixed += launch_mx_vcycle(a, Lf, nlev, kCoarseSweeps, s, tr);

@@ -204,10 +204,12 @@ __device__ __forceinline__ void stage_input(uint8_t *sA, const ConvArgs &a, int 
     }
 }
 
-template <int CIN, int COUT>
+// NB: output channels per CTA (the CTAs of one tile row split cout when the
+// full weight block would leave room for only one CTA per SM)
+template <int CIN, int NB>
 __host__ __device__ constexpr int smem_bytes()
 {
-    return 9 * CIN * COUT * 2 + 3 * (CIN / 8) * kGrpB + 64;
+    return 9 * CIN * NB * 2 + 3 * (CIN / 8) * kGrpB + 64;
 }
 
 template <int COUT>
@@ -216,35 +218,37 @@ __host__ __device__ constexpr uint32_t tmem_cols()
     return COUT < 32 ? 32u : (uint32_t)COUT;
 }
 
-template <int CIN, int COUT, int MODE>
+template <int CIN, int COUT, int MODE, int NB>
 __global__ void __launch_bounds__(kThreads) k_conv3x3(ConvArgs a)
 {
-    static_assert(CIN % 16 == 0 && COUT % 16 == 0 && COUT <= 256, "channel counts");
+    static_assert(CIN % 16 == 0 && NB % 16 == 0 && NB <= 256 && COUT % NB == 0, "channel counts");
     constexpr int G = CIN / 8;
     constexpr int rowB = G * kGrpB;
-    constexpr uint32_t lboB = (COUT / 8) * 128;   // between K-groups of the weight operand
+    constexpr uint32_t lboB = (NB / 8) * 128;   // between K-groups of the weight operand
     extern __shared__ __align__(128) uint8_t smem[];
     uint8_t *sW = smem;
-    uint8_t *sA = smem + 9 * CIN * COUT * 2;
+    uint8_t *sA = smem + 9 * CIN * NB * 2;
+    const int ob = blockIdx.y * NB;               // this CTA's first output channel
     uint64_t *mbar = reinterpret_cast<uint64_t *>(sA + 3 * rowB);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
     int *okflag = reinterpret_cast<int *>(tslot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    // weights: element (o, k = tap * CIN + c) at (k / 8) * lboB + (o / 8) * 128 + (o % 8) * 16 + (k % 8) * 2
-    for (int e = tid; e < COUT * 9 * G; e += kThreads) {
+    // weights of output channels ob .. ob + NB - 1: element (o, k = tap * CIN + c)
+    // at (k / 8) * lboB + (o / 8) * 128 + (o % 8) * 16 + (k % 8) * 2
+    for (int e = tid; e < NB * 9 * G; e += kThreads) {
         const int kg = e % (9 * G), o = e / (9 * G);
-        const uint4 v = ld16(a.wt + (size_t)o * 9 * CIN + kg * 8);
+        const uint4 v = ld16(a.wt + (size_t)(ob + o) * 9 * CIN + kg * 8);
         *reinterpret_cast<uint4 *>(sW + kg * lboB + (o / 8) * 128 + (o % 8) * 16) = v;
     }
     if (tid == 0) mbar_init(smem_u32(mbar), 1);
-    if (warp == 0) tmem_alloc(smem_u32(tslot), tmem_cols<COUT>());
+    if (warp == 0) tmem_alloc(smem_u32(tslot), tmem_cols<NB>());
     fence_proxy_async();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-    constexpr uint32_t idesc = instr_desc(COUT);
+    constexpr uint32_t idesc = instr_desc(NB);
 
     uint32_t phase = 0;
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
@@ -294,21 +298,21 @@ __global__ void __launch_bounds__(kThreads) k_conv3x3(ConvArgs a)
         const bool valid = xx < a.w;
         const size_t pix = ((size_t)b * a.h + y) * a.w + xx;
 #pragma unroll
-        for (int c0 = 0; c0 < COUT; c0 += 16) {
+        for (int c0 = 0; c0 < NB; c0 += 16) {
             float v[16];
             tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-                if (a.bias) v[j] += __ldg(&a.bias[c0 + j]);
+                if (a.bias) v[j] += __ldg(&a.bias[ob + c0 + j]);
                 if (a.relu) v[j] = fmaxf(v[j], 0.0f);
             }
             if (valid) {
                 if (a.out_f32) {
-                    float4 *dst = reinterpret_cast<float4 *>(static_cast<float *>(a.y) + pix * COUT + c0);
+                    float4 *dst = reinterpret_cast<float4 *>(static_cast<float *>(a.y) + pix * COUT + ob + c0);
 #pragma unroll
                     for (int j = 0; j < 4; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
                 } else {
-                    uint4 *dst = reinterpret_cast<uint4 *>(static_cast<uint16_t *>(a.y) + pix * COUT + c0);
+                    uint4 *dst = reinterpret_cast<uint4 *>(static_cast<uint16_t *>(a.y) + pix * COUT + ob + c0);
                     dst[0] = make_uint4(pack_bf2(v[0], v[1]), pack_bf2(v[2], v[3]), pack_bf2(v[4], v[5]),
                                         pack_bf2(v[6], v[7]));
                     dst[1] = make_uint4(pack_bf2(v[8], v[9]), pack_bf2(v[10], v[11]), pack_bf2(v[12], v[13]),
@@ -320,36 +324,57 @@ __global__ void __launch_bounds__(kThreads) k_conv3x3(ConvArgs a)
     }
     __syncthreads();
     tc_fence_after();
-    if (warp == 0) tmem_dealloc(tmem, tmem_cols<COUT>());
+    if (warp == 0) tmem_dealloc(tmem, tmem_cols<NB>());
 }
 
 template <int CIN, int COUT, int MODE>
 cudaError_t launch_one(const ConvArgs &a0, cudaStream_t st)
 {
-    constexpr int smem = smem_bytes<CIN, COUT>();
-    auto kern = k_conv3x3<CIN, COUT, MODE>;
+    // 64 x 64 layers: two CTAs per tile row of 32 output channels each, so
+    // that two CTAs fit on an SM
+    constexpr int NB = (CIN >= 64 && COUT >= 64) ? COUT / 2 : COUT;
+    constexpr int NOB = COUT / NB;
+    constexpr int smem = smem_bytes<CIN, NB>();
+    auto kern = k_conv3x3<CIN, COUT, MODE, NB>;
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     static int sms = 0, per_sm = 0;
     std::call_once(once, [&] {
+        // resident CTAs per SM from the kernel's own limits: threads, shared
+        // memory (with the carveout set to its maximum), registers and the
+        // 512 tensor-memory columns of an SM
         attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        int dev = 0;
+        if (attr_err == cudaSuccess)
+            attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                            (int)cudaSharedmemCarveoutMaxShared);
+        int dev = 0, smem_sm = 0, regs_sm = 0, thr_sm = 0;
+        cudaFuncAttributes fa{};
         if (attr_err == cudaSuccess) attr_err = cudaGetDevice(&dev);
         if (attr_err == cudaSuccess) attr_err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (attr_err == cudaSuccess)
-            attr_err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
-        // tensor memory: 512 columns per SM
-        const int by_tmem = 512 / (int)tmem_cols<COUT>();
-        if (per_sm > by_tmem) per_sm = by_tmem;
+            attr_err = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        if (attr_err == cudaSuccess)
+            attr_err = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+        if (attr_err == cudaSuccess)
+            attr_err = cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+        if (attr_err == cudaSuccess) attr_err = cudaFuncGetAttributes(&fa, kern);
+        if (attr_err != cudaSuccess) return;
+        per_sm = thr_sm / kThreads;
+        const int by_smem = smem_sm / (smem + (int)fa.sharedSizeBytes + 1024);
+        const int by_regs = regs_sm / (kThreads * (fa.numRegs > 0 ? fa.numRegs : 1));
+        const int by_tmem = 512 / (int)tmem_cols<NB>();
+        per_sm = per_sm < by_smem ? per_sm : by_smem;
+        per_sm = per_sm < by_regs ? per_sm : by_regs;
+        per_sm = per_sm < by_tmem ? per_sm : by_tmem;
         if (per_sm < 1) per_sm = 1;
     });
     if (attr_err != cudaSuccess) return attr_err;
     ConvArgs a = a0;
     a.tiles_per_row = (a.w + kM - 1) / kM;
     a.ntiles = a.n * a.h * a.tiles_per_row;
-    int grid = sms * per_sm;
-    if (grid > a.ntiles) grid = a.ntiles;
-    kern<<<grid, kThreads, smem, st>>>(a);
+    int gx = (sms * per_sm + NOB - 1) / NOB;
+    if (gx > a.ntiles) gx = a.ntiles;
+    kern<<<dim3(gx, NOB), kThreads, smem, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -18,6 +18,8 @@ struct gea_net;
 // The network forward pass on stream st (gea_net.cu); returns the number of
 // kernels launched or -1.
 int gea_net_run(gea_net *net, cudaStream_t st, int n, int h, int w, const float *r, float *y);
+// Kernels of one network forward pass.
+int gea_net_launches();
 // Whether a network can take n samples of h x w.
 bool gea_net_fits(const gea_net *net, int n, int h, int w);
 
@@ -289,7 +291,13 @@ int max_blocks(const Geom &G);
 // learned initial guess of the pressure solve (gea_kernels.cu): the network
 // (gea_net.cu) proposes a correction e for the residual r of level L; the
 // step x += alpha e, r -= alpha A e minimises the A-norm error along e.
-// Returns the number of kernels launched, or -1 if the network failed.
+// launch_guess_in converts r for the network and, in a graph, sets the IF
+// condition h of the pass (skipped once the solve has converged);
+// launch_net_guess runs the network and the step. Returns the number of
+// kernels launched, or -1 if the network failed.
+template <class R>
+void launch_guess_in(const StepArgs &a, const LevelT<R> &L, const R *r, float *dense_r,
+                     cudaGraphConditionalHandle h, bool graph, cudaStream_t st, Tracer *tr);
 template <class R>
 int launch_net_guess(const StepArgs &a, const LevelT<R> &L, R *r, R *q, R *x, double tol2, gea_net *net,
                      float *dense_r, float *dense_e, cudaStream_t st, Tracer *tr);

@@ -440,10 +440,18 @@ int launch_cg_iter(const StepArgs &a, Level *L, int nlev, int ncoarse, double *x
 
 namespace {
 
+// graph = 1: block (0,0) also sets the IF condition of the network pass
+// (run it only while the solve is not finished)
 template <class R>
-__global__ void k_guess_in(Geom G, const R *r, float *dense, Scal *sc)
+__global__ void k_guess_in(Geom G, const R *r, float *dense, Scal *sc, cudaGraphConditionalHandle h, int graph,
+                           int body_launches)
 {
-    if (loop_over(sc, LOOP_CG)) return;
+    const bool over = loop_over(sc, LOOP_CG);
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+        if (graph) cudaGraphSetConditional(h, over ? 0u : 1u);
+        if (!over) sc->launches += body_launches;
+    }
+    if (over) return;
     int i, k;
     if (!cell_of(G, blockIdx.x, blockIdx.y, i, k)) return;
     dense[(size_t)k * G.nx + i] = (float)r[cidx(G, i, k)];
@@ -476,11 +484,20 @@ __global__ void k_guess_apply(LevelT<R> L, const float *e, const R *q, R *r, R *
 }  // namespace
 
 template <class R>
+void launch_guess_in(const StepArgs &a, const LevelT<R> &L, const R *r, float *dense_r,
+                     cudaGraphConditionalHandle h, bool graph, cudaStream_t st, Tracer *tr)
+{
+    const Geom &G = L.G;
+    TRACED(tr, "guess_in", ncell(G),
+           (k_guess_in<R><<<grid_of(G), kBlock, 0, st>>>(G, r, dense_r, a.sc, h, graph ? 1 : 0,
+                                                          2 + gea_net_launches())));
+}
+
+template <class R>
 int launch_net_guess(const StepArgs &a, const LevelT<R> &L, R *r, R *q, R *x, double tol2, gea_net *net,
                      float *dense_r, float *dense_e, cudaStream_t st, Tracer *tr)
 {
     const Geom &G = L.G;
-    TRACED(tr, "guess_in", ncell(G), (k_guess_in<R><<<grid_of(G), kBlock, 0, st>>>(G, r, dense_r, a.sc)));
     if (tr) tr->begin("net_forward", ncell(G), st);
     const int nk = gea_net_run(net, st, 1, G.nz, G.nx, dense_r, dense_e);
     if (tr) tr->end(st);
@@ -489,9 +506,13 @@ int launch_net_guess(const StepArgs &a, const LevelT<R> &L, R *r, R *q, R *x, do
            (k_guess_dots<R><<<grid_of(G), kBlock, 0, st>>>(L, dense_e, r, q, a.sc, a.partials)));
     TRACED(tr, "guess_apply", ncell(G),
            (k_guess_apply<R><<<grid_of(G), kBlock, 0, st>>>(L, dense_e, q, r, x, a.sc, a.partials, tol2)));
-    return 3 + nk;
+    return 2 + nk;
 }
 
+template void launch_guess_in<double>(const StepArgs &, const LevelT<double> &, const double *, float *,
+                                      cudaGraphConditionalHandle, bool, cudaStream_t, Tracer *);
+template void launch_guess_in<float>(const StepArgs &, const LevelT<float> &, const float *, float *,
+                                     cudaGraphConditionalHandle, bool, cudaStream_t, Tracer *);
 template int launch_net_guess<double>(const StepArgs &, const LevelT<double> &, double *, double *, double *,
                                       double, gea_net *, float *, float *, cudaStream_t, Tracer *);
 template int launch_net_guess<float>(const StepArgs &, const LevelT<float> &, float *, float *, float *, double,

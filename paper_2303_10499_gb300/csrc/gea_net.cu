@@ -662,6 +662,8 @@ bool shape_ok(const gea_net *net, int n, int h, int w)
 
 }  // namespace
 
+int gea_net_launches();
+
 int gea_net_run(gea_net *net, cudaStream_t st, int n, int h, int w, const float *r, float *y)
 {
     if (!net || !shape_ok(net, n, h, w)) return -1;
@@ -669,10 +671,12 @@ int gea_net_run(gea_net *net, cudaStream_t st, int n, int h, int w, const float 
     net->st = st;
     const int rc = forward(net, n, h, w, r, y);
     net->st = old;
-    // per-sample statistics (2), input scaling, first layer, 13 tensor-core
-    // layers, output layer
-    return rc ? -1 : 2 + 1 + 1 + (kOut - 1) + 1;
+    return rc ? -1 : gea_net_launches();
 }
+
+// per-sample statistics (2), input scaling, first layer, 13 tensor-core
+// layers, output layer
+int gea_net_launches() { return 2 + 1 + 1 + (kOut - 1) + 1; }
 
 bool gea_net_fits(const gea_net *net, int n, int h, int w) { return net && shape_ok(net, n, h, w); }
 
