@@ -71,6 +71,7 @@ typedef struct {
     int32_t jac_maxit;
     double cg_rtol;
     int32_t cg_maxit;
+    double cs;          /* Smagorinsky constant; 0: constant viscosity mu only */
 } orc_cfg;
 
 /* The solution tuple of Section 3 (rho, u, h, p, p', T) plus what the
@@ -187,6 +188,64 @@ double orc_laplacian_cell(const orc_cfg *c, const double *X, int bc, int i, int 
     return s / V;
 }
 
+/* Strain-rate magnitude |S| = sqrt(2 S_ij S_ij) of cell (i,k) from central
+ * differences of the cell velocities (ghosts by the wall rules):
+ * 2 S_ij S_ij = 2 (du/dx)^2 + 2 (dw/dz)^2 + (du/dz + dw/dx)^2 in x-z. */
+double orc_strain_cell(const orc_cfg *c, const double *u, const double *w, int i, int k)
+{
+    double dx = dxof(c), dz = dzof(c);
+    double dudx = (at(c, u, i + 1, k, BC_U) - at(c, u, i - 1, k, BC_U)) / (2.0 * dx);
+    double dudz = (at(c, u, i, k + 1, BC_U) - at(c, u, i, k - 1, BC_U)) / (2.0 * dz);
+    double dwdx = (at(c, w, i + 1, k, BC_W) - at(c, w, i - 1, k, BC_W)) / (2.0 * dx);
+    double dwdz = (at(c, w, i, k + 1, BC_W) - at(c, w, i, k - 1, BC_W)) / (2.0 * dz);
+    double sh = dudz + dwdx;
+    return sqrt(2.0 * dudx * dudx + 2.0 * dwdz * dwdz + sh * sh);
+}
+
+/* Effective dynamic viscosity mu + mu_t with the Smagorinsky eddy viscosity
+ * mu_t = rho (cs Delta)^2 |S|, Delta = sqrt(dx dz), at every cell. */
+void orc_smagorinsky(const orc_cfg *c, const double *rho, const double *u, const double *w,
+                     double *mu_eff)
+{
+    double d2 = c->cs * c->cs * dxof(c) * dzof(c);
+    for (int k = 0; k < c->nz; ++k)
+        for (int i = 0; i < c->nx; ++i)
+            mu_eff[k * c->nx + i] = c->mu + rho[k * c->nx + i] * d2 * orc_strain_cell(c, u, w, i, k);
+}
+
+/* Variable-coefficient diffusive face sum (1/V) sum_j mu_j (grad X)_j . A_j of
+ * cell (i,k): mu_j the mean of the two cells' viscosities (a wall face takes
+ * the cell's own), the compact face-normal gradient through the ghost layer. */
+double orc_diffusion_cell(const orc_cfg *c, const double *mu, const double *X, int bc, int i, int k)
+{
+    double dx = dxof(c), dz = dzof(c), V = dx * dz;
+    double xc = at(c, X, i, k, bc), mc = at(c, mu, i, k, BC_EVEN);
+    double s = 0.0;
+    s += 0.5 * (mc + at(c, mu, i + 1, k, BC_EVEN)) * (at(c, X, i + 1, k, bc) - xc) / dx * dz;
+    s += 0.5 * (mc + at(c, mu, i - 1, k, BC_EVEN)) * (at(c, X, i - 1, k, bc) - xc) / dx * dz;
+    s += 0.5 * (mc + at(c, mu, i, k + 1, BC_EVEN)) * (at(c, X, i, k + 1, bc) - xc) / dz * dx;
+    s += 0.5 * (mc + at(c, mu, i, k - 1, BC_EVEN)) * (at(c, X, i, k - 1, bc) - xc) / dz * dx;
+    return s / V;
+}
+
+/* The diffusion term of the transport operators: nu L(X) with constant nu,
+ * or nu times the variable-coefficient sum with the viscosity field mu. */
+static double diffusion(const orc_cfg *c, const double *mu, double nu, const double *X, int bc,
+                        int i, int k)
+{
+    return mu ? nu * orc_diffusion_cell(c, mu, X, bc, i, k) : nu * orc_laplacian_cell(c, X, bc, i, k);
+}
+
+/* Coefficient of X_i in -diffusion() for an interior cell. */
+static double diffusion_diag(const orc_cfg *c, const double *mu, double nu, int i, int k)
+{
+    double dx = dxof(c), dz = dzof(c);
+    if (!mu) return nu * (2.0 / (dx * dx) + 2.0 / (dz * dz));
+    double mc = at(c, mu, i, k, BC_EVEN);
+    return nu * ((0.5 * (mc + at(c, mu, i + 1, k, BC_EVEN)) + 0.5 * (mc + at(c, mu, i - 1, k, BC_EVEN))) / (dx * dx)
+               + (0.5 * (mc + at(c, mu, i, k + 1, BC_EVEN)) + 0.5 * (mc + at(c, mu, i, k - 1, BC_EVEN))) / (dz * dz));
+}
+
 /* Flux divergence (1/V) sum_j phi_j of cell (i,k), outward positive. */
 double orc_divergence_cell(const orc_cfg *c, const double *phix, const double *phiz,
                            int i, int k)
@@ -239,10 +298,11 @@ static double norm2(const double *x, size_t n)
 /* implicit transport solves (Step 1 momentum, Step 2 enthalpy)          */
 /* ------------------------------------------------------------------ */
 
-/* Residual of (rho1/dt) X + C(X) - nu L(X) = b at every cell. */
+/* Residual of (rho1/dt) X + C(X) - diffusion(X) = b at every cell (mu NULL:
+ * constant viscosity nu). */
 static void transport_residual(const orc_cfg *c, const double *rho1, const double *phix,
-                               const double *phiz, double nu, const double *X, int bc,
-                               const double *b, double *r)
+                               const double *phiz, const double *mu, double nu, const double *X,
+                               int bc, const double *b, double *r)
 {
     int nx = c->nx, nz = c->nz;
     for (int k = 0; k < nz; ++k)
@@ -250,7 +310,7 @@ static void transport_residual(const orc_cfg *c, const double *rho1, const doubl
             int q = k * nx + i;
             double lhs = rho1[q] / c->dt * X[q]
                        + orc_convection_cell(c, phix, phiz, X, bc, i, k)
-                       - nu * orc_laplacian_cell(c, X, bc, i, k);
+                       - diffusion(c, mu, nu, X, bc, i, k);
             r[q] = b[q] - lhs;
         }
 }
@@ -262,7 +322,7 @@ void orc_transport_apply(const orc_cfg *c, const double *rho1, const double *phi
 {
     size_t n = (size_t)c->nx * c->nz;
     double *zero = calloc(n, sizeof(double));
-    transport_residual(c, rho1, phix, phiz, nu, X, bc, zero, out);
+    transport_residual(c, rho1, phix, phiz, NULL, nu, X, bc, zero, out);
     for (size_t q = 0; q < n; ++q) out[q] = -out[q];
     free(zero);
 }
@@ -274,25 +334,24 @@ void orc_transport_apply(const orc_cfg *c, const double *rho1, const double *phi
  * X <- X + r/d; the iteration stops after the sweep whose residual met
  * ||r|| <= jac_rtol ||b||, so the returned X is one contraction beyond the
  * tolerance. Returns the number of sweeps, or -1 if jac_maxit was reached. */
-int orc_transport_solve(const orc_cfg *c, const double *rho1, const double *phix,
-                        const double *phiz, double nu, int bc, const double *b,
-                        double *X)
+static int transport_solve(const orc_cfg *c, const double *rho1, const double *phix,
+                           const double *phiz, const double *mu, double nu, int bc, const double *b,
+                           double *X)
 {
     int nx = c->nx, nz = c->nz;
     size_t n = (size_t)nx * nz;
-    double dx = dxof(c), dz = dzof(c);
     double *r = malloc(n * sizeof(double));
     double bn = norm2(b, n);
     int sweeps = 0, ok = 0;
     while (sweeps < c->jac_maxit) {
-        transport_residual(c, rho1, phix, phiz, nu, X, bc, b, r);
+        transport_residual(c, rho1, phix, phiz, mu, nu, X, bc, b, r);
         double rn = norm2(r, n);
         for (int k = 0; k < nz; ++k)
             for (int i = 0; i < nx; ++i) {
                 int q = k * nx + i;
                 double d = rho1[q] / c->dt
                          + 7.0 / 12.0 * orc_divergence_cell(c, phix, phiz, i, k)
-                         + nu * (2.0 / (dx * dx) + 2.0 / (dz * dz));
+                         + diffusion_diag(c, mu, nu, i, k);
                 X[q] += r[q] / d;
             }
         ++sweeps;
@@ -300,6 +359,13 @@ int orc_transport_solve(const orc_cfg *c, const double *rho1, const double *phix
     }
     free(r);
     return ok ? sweeps : -1;
+}
+
+int orc_transport_solve(const orc_cfg *c, const double *rho1, const double *phix,
+                        const double *phiz, double nu, int bc, const double *b,
+                        double *X)
+{
+    return transport_solve(c, rho1, phix, phiz, NULL, nu, bc, b, X);
 }
 
 /* ------------------------------------------------------------------ */
@@ -451,8 +517,13 @@ int orc_step(const orc_cfg *c, orc_state *s, int32_t nsteps, orc_stats *st, orc_
     double *pnext = zalloc(n);
     double *Gx = zalloc(nfx), *Gz = zalloc(nfz), *Dx = zalloc(nfx), *Dz = zalloc(nfz);
     double *Fx = zalloc(nfx), *Fz = zalloc(nfz);
+    /* Smagorinsky LES: the viscosity field of the step (from rho^n, u^n); the
+     * constant-viscosity scheme of Remark 1 otherwise */
+    double *mu_eff = c->cs > 0.0 ? zalloc(n) : NULL;
+    double nu_u = mu_eff ? 1.0 : c->mu, nu_h = mu_eff ? 1.0 / c->Pr : c->mu / c->Pr;
 
     for (int step = 0; step < nsteps; ++step) {
+        if (mu_eff) orc_smagorinsky(c, s->rho, s->u, s->w, mu_eff);
         /* ---- Step 1, eq. (e1_d): rho^{n+1/3} = rho^n - dt sum_j phi^n_j / V ---- */
         for (int k = 0; k < nz; ++k)
             for (int i = 0; i < nx; ++i)
@@ -473,8 +544,8 @@ int orc_step(const orc_cfg *c, orc_state *s, int32_t nsteps, orc_stats *st, orc_
                 u1[q] = s->u[q];
                 w1[q] = s->w[q];
             }
-        int su = orc_transport_solve(c, rho1, s->phix, s->phiz, c->mu, BC_U, bu, u1);
-        int sw = orc_transport_solve(c, rho1, s->phix, s->phiz, c->mu, BC_W, bw, w1);
+        int su = transport_solve(c, rho1, s->phix, s->phiz, mu_eff, nu_u, BC_U, bu, u1);
+        int sw = transport_solve(c, rho1, s->phix, s->phiz, mu_eff, nu_u, BC_W, bw, w1);
         if (su < 0 || sw < 0) status = 1;
 
         /* ---- Step 1, eq. (step1_3sd): K^{n+1/3} = |u^{n+1/3}|^2 / 2 ---- */
@@ -493,7 +564,7 @@ int orc_step(const orc_cfg *c, orc_state *s, int32_t nsteps, orc_stats *st, orc_
                       + s->p[q] / dt - rho1[q] * g * w1[q];
                 h1[q] = s->h[q];
             }
-        int sh = orc_transport_solve(c, rho1, s->phix, s->phiz, c->mu / c->Pr, BC_H, bh, h1);
+        int sh = transport_solve(c, rho1, s->phix, s->phiz, mu_eff, nu_h, BC_H, bh, h1);
         if (sh < 0) status = 1;
 
         /* ---- Step 2, eq. (step3_2sd): T^{n+1} = T^n + (h^{n+1} - h^n)/cp;
@@ -537,10 +608,10 @@ int orc_step(const orc_cfg *c, orc_state *s, int32_t nsteps, orc_stats *st, orc_
                     int q = k * nx + i;
                     Hx[q] = s->rho[q] * s->u[q] / dt
                           - orc_convection_cell(c, s->phix, s->phiz, U, BC_U, i, k)
-                          + c->mu * orc_laplacian_cell(c, U, BC_U, i, k);
+                          + diffusion(c, mu_eff, nu_u, U, BC_U, i, k);
                     Hz[q] = s->rho[q] * s->w[q] / dt
                           - orc_convection_cell(c, s->phix, s->phiz, W, BC_W, i, k)
-                          + c->mu * orc_laplacian_cell(c, W, BC_W, i, k);
+                          + diffusion(c, mu_eff, nu_u, W, BC_W, i, k);
                 }
             /* right-hand side of the pressure equation (eq. p_prime_sd, Helmholtz
              * form from continuity with rho^{n+1} = psi (p' - rho2 g z)) */
@@ -648,6 +719,7 @@ int orc_step(const orc_cfg *c, orc_state *s, int32_t nsteps, orc_stats *st, orc_
     free(rho1); free(u1); free(w1); free(K1); free(bu); free(bw); free(bh); free(h1);
     free(T1); free(rho2); free(psi); free(Hx); free(Hz); free(b); free(U); free(W);
     free(pnew); free(rhonew); free(pnext); free(Gx); free(Gz); free(Dx); free(Dz); free(Fx); free(Fz);
+    free(mu_eff);
     return status;
 }
 
@@ -699,6 +771,18 @@ void orc_convection(const orc_cfg *c, const double *phix, const double *phiz,
     for (int k = 0; k < c->nz; ++k)
         for (int i = 0; i < c->nx; ++i)
             out[k * c->nx + i] = orc_convection_cell(c, phix, phiz, X, bc, i, k);
+}
+
+void orc_strain(const orc_cfg *c, const double *u, const double *w, double *out)
+{
+    for (int k = 0; k < c->nz; ++k)
+        for (int i = 0; i < c->nx; ++i) out[k * c->nx + i] = orc_strain_cell(c, u, w, i, k);
+}
+
+void orc_diffusion(const orc_cfg *c, const double *mu, const double *X, int bc, double *out)
+{
+    for (int k = 0; k < c->nz; ++k)
+        for (int i = 0; i < c->nx; ++i) out[k * c->nx + i] = orc_diffusion_cell(c, mu, X, bc, i, k);
 }
 
 void orc_laplacian(const orc_cfg *c, const double *X, int bc, double *out)

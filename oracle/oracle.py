@@ -43,7 +43,7 @@ class _Cfg(C.Structure):
                 ("R", C.c_double), ("cp", C.c_double), ("g", C.c_double), ("p0", C.c_double),
                 ("mu", C.c_double), ("Pr", C.c_double), ("dt", C.c_double),
                 ("n_corr", C.c_int32), ("jac_rtol", C.c_double), ("jac_maxit", C.c_int32),
-                ("cg_rtol", C.c_double), ("cg_maxit", C.c_int32)]
+                ("cg_rtol", C.c_double), ("cg_maxit", C.c_int32), ("cs", C.c_double)]
 
 
 _P = C.POINTER(C.c_double)
@@ -77,6 +77,9 @@ def _bind(path: str):
     lib.orc_continuity_residual.argtypes = [C.POINTER(_Cfg), _P, C.POINTER(_State), _P]
     lib.orc_convection.argtypes = [C.POINTER(_Cfg), _P, _P, _P, C.c_int, _P]
     lib.orc_laplacian.argtypes = [C.POINTER(_Cfg), _P, C.c_int, _P]
+    lib.orc_strain.argtypes = [C.POINTER(_Cfg), _P, _P, _P]
+    lib.orc_smagorinsky.argtypes = [C.POINTER(_Cfg), _P, _P, _P, _P]
+    lib.orc_diffusion.argtypes = [C.POINTER(_Cfg), _P, _P, C.c_int, _P]
     lib.orc_face_forces.argtypes = [C.POINTER(_Cfg), _P, _P, _P, _P]
     lib.orc_helmholtz_apply.argtypes = [C.POINTER(_Cfg), _P, _P, _P, _P, _P]
     lib.orc_pcg.argtypes = [C.POINTER(_Cfg), _P, _P, _P, _P, _P, _P]
@@ -148,7 +151,8 @@ class Oracle:
         self.grid, self.const = grid, const
         self.cfg = _Cfg(grid.nx, grid.nz, grid.lx, grid.lz, const.R, const.cp, const.g,
                         const.p0, const.mu, const.Pr, const.dt, const.n_corr,
-                        const.jac_rtol, const.jac_maxit, const.cg_rtol, const.cg_maxit)
+                        const.jac_rtol, const.jac_maxit, const.cg_rtol, const.cg_maxit,
+                        getattr(const, "cs", 0.0))
         self.lib = _lib_handle() if lib_path is None else _bind(lib_path)
         self.last_stats = None
 
@@ -217,6 +221,27 @@ class Oracle:
         out = np.zeros((self.grid.nz, self.grid.nx))
         x = np.ascontiguousarray(X, dtype=np.float64)
         self.lib.orc_laplacian(C.byref(self.cfg), _ptr(x), bc, _ptr(out))
+        return out
+
+    def strain(self, u, w) -> np.ndarray:
+        """|S| = sqrt(2 S_ij S_ij) per cell (Smagorinsky model)."""
+        out = np.zeros((self.grid.nz, self.grid.nx))
+        a = [np.ascontiguousarray(x, dtype=np.float64) for x in (u, w)]
+        self.lib.orc_strain(C.byref(self.cfg), _ptr(a[0]), _ptr(a[1]), _ptr(out))
+        return out
+
+    def smagorinsky(self, rho, u, w) -> np.ndarray:
+        """mu + rho (cs Delta)^2 |S| per cell."""
+        out = np.zeros((self.grid.nz, self.grid.nx))
+        a = [np.ascontiguousarray(x, dtype=np.float64) for x in (rho, u, w)]
+        self.lib.orc_smagorinsky(C.byref(self.cfg), _ptr(a[0]), _ptr(a[1]), _ptr(a[2]), _ptr(out))
+        return out
+
+    def diffusion(self, mu, X, bc) -> np.ndarray:
+        """(1/V) sum_f mu_f (grad X)_f . A_f with face-mean viscosities."""
+        out = np.zeros((self.grid.nz, self.grid.nx))
+        a = [np.ascontiguousarray(x, dtype=np.float64) for x in (mu, X)]
+        self.lib.orc_diffusion(C.byref(self.cfg), _ptr(a[0]), _ptr(a[1]), bc, _ptr(out))
         return out
 
     def face_forces(self, pp, rho):

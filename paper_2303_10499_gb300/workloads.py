@@ -81,6 +81,7 @@ class Constants:
     jac_maxit: int = 200
     cg_rtol: float = 1e-17
     cg_maxit: int = 400
+    cs: float = 0.0        # Smagorinsky constant (0: constant viscosity only)
 
     @property
     def cv(self) -> float:
