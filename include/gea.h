@@ -103,7 +103,13 @@ typedef struct gea_grid {
  *            not with GEA_FLAG_MIXED).
  *            Other bits must be 0.
  *  mp_rtol   relative tolerance of the FP32 solves (GEA_FLAG_MIXED only);
- *            0 selects 1e-5, otherwise 1e-7 <= mp_rtol < 1. */
+ *            0 selects 1e-5, otherwise 1e-7 <= mp_rtol < 1.
+ *  cs        Smagorinsky constant (LES; the paper names large eddy
+ *            simulation without a model): the viscosity of the momentum
+ *            and enthalpy diffusion becomes mu + rho (cs Delta)^2 |S| per
+ *            cell from rho^n, u^n (Delta = sqrt(dx dz), |S|^2 =
+ *            2 S_ij S_ij by central differences), with face values the mean
+ *            of the two cells. 0: constant mu. cs > 0 requires Pr = 1. */
 typedef struct gea_constants {
     double R, cp, g, p0, mu, Pr, dt;
     int32_t n_corr;
@@ -114,6 +120,7 @@ typedef struct gea_constants {
     int32_t mg_min_cells;
     int32_t flags;
     double mp_rtol;
+    double cs;
 } gea_constants;
 
 /* A view of caller-owned buffers (host or device, per mem). The library

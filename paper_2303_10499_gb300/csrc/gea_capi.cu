@@ -43,6 +43,7 @@ struct gea_ctx {
     MixedArgs mx{};                       // FP32 buffers of the mixed-precision step
     std::vector<LevelF> Lf;               // FP32 hierarchy of the mixed-precision step
     double *r0keep = nullptr;             // GEA_FLAG_KEEP_R0: first corrector's initial residual
+    double *mueff = nullptr;              // LES: mu + mu_t of the running step
     gea_net *net = nullptr;               // attached learned initial guess (not owned)
     float *net_r = nullptr, *net_e = nullptr;   // its dense input and output
     Scal *sc = nullptr;
@@ -107,6 +108,7 @@ StepArgs step_args(gea_ctx *c, int from)
     a.S = c->S[from];
     a.N = c->S[from ^ 1];
     a.T = c->T;
+    a.mueff = c->mueff;
     a.rho1 = c->rho1; a.dinvu = c->dinvu; a.dinvh = c->dinvh; a.bu = c->bu; a.bw = c->bw;
     a.ua = c->ua; a.wa = c->wa; a.ub = c->ub; a.wb = c->wb;
     a.bh = c->bh; a.ha = c->ha; a.hb = c->hb;
@@ -243,6 +245,7 @@ int record_step(gea_ctx *ctx, int from, cudaStream_t s, bool graph, Tracer *tr)
     };
 
     launch_step_begin(ctx->sc, s, tr); ++fixed;
+    if (ctx->mueff) { launch_les(a, s, tr); ++fixed; }
     // Step 1: continuity predictor and implicit momentum predictor
     launch_pred_setup(a, s, tr); ++fixed;
     rc = loop(LOOP_MOM, jtrips, [&](cudaStream_t bs, cudaGraphConditionalHandle h, bool g) {
@@ -314,6 +317,7 @@ int record_step_mixed(gea_ctx *ctx, int from, cudaStream_t s, bool graph, Tracer
     };
 
     launch_step_begin(ctx->sc, s, tr); ++fixed;
+    if (ctx->mueff) { launch_les(a, s, tr); ++fixed; }
     launch_mx_pred(a, m, s, tr); ++fixed;
     rc = loop(LOOP_MOM, jtrips, [&](cudaStream_t bs, cudaGraphConditionalHandle h, bool g) {
         launch_mx_mom(a, m, m.du[0], m.dw[0], m.du[1], m.dw[1], 0, bs, tr);
@@ -462,10 +466,13 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
         return GEA_ERR_INVAL;
     if ((c->flags & GEA_FLAG_MIXED) && c->mp_rtol != 0.0 && !(c->mp_rtol >= 1e-7 && c->mp_rtol < 1.0))
         return GEA_ERR_INVAL;
+    // LES: one viscosity field serves momentum and enthalpy, so Pr = 1
+    if (!(c->cs >= 0.0) || (c->cs > 0.0 && c->Pr != 1.0)) return GEA_ERR_INVAL;
 
     ctx = new gea_ctx();
     ctx->C = *c;
     ctx->G = make_geom(grid->nx, grid->nz, grid->lx, grid->lz);
+    ctx->F.les_d2 = c->cs * c->cs * ctx->G.dx * ctx->G.dz;
     ctx->F.R = c->R; ctx->F.cp = c->cp; ctx->F.g = c->g; ctx->F.p0 = c->p0;
     ctx->F.mu = c->mu; ctx->F.nuh = c->mu / c->Pr; ctx->F.dt = c->dt; ctx->F.idt = 1.0 / c->dt;
     ctx->F.omega = kOmega;
@@ -500,6 +507,7 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
     total += 4 * cell;                             // staging for conservative fields
     total += 2 * cell + round_up(G.nz * sizeof(double), 256);   // theta_bar, theta'
     if (c->flags & GEA_FLAG_KEEP_R0) total += cell;
+    if (c->cs > 0.0) total += cell;
     // FP64 levels (mixed precision: the finest only, for the FP64 residual)
     const size_t nlev64 = ctx->mixed ? 1 : lg.size();
     for (size_t l = 0; l < nlev64; ++l) total += 8 * arr_bytes(lg[l], lg[l].nz) + arr_bytes(lg[l], lg[l].nz + 1);
@@ -539,6 +547,7 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
     ctx->thout = take(cell);
     ctx->thbar = take(round_up(G.nz * sizeof(double), 256));
     if (c->flags & GEA_FLAG_KEEP_R0) ctx->r0keep = take(cell);
+    if (c->cs > 0.0) ctx->mueff = take(cell);
     for (size_t lv = 0; lv < nlev64; ++lv) {
         const Geom &g = lg[lv];
         Level l;

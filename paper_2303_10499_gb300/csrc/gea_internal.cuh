@@ -40,6 +40,7 @@ struct Geom {
 struct Phys {
     double R, cp, g, p0, mu, nuh, dt, idt;   // nuh = mu / Pr
     double omega;                            // damped-Jacobi weight of the smoother
+    double les_d2;                           // Smagorinsky (cs Delta)^2; 0: constant viscosity
 };
 
 // Persistent state of one time level (Section 3's solution tuple plus the
@@ -146,6 +147,7 @@ struct StepArgs {
     Phys F;
     State S, N;
     Stencil9 T;                                          // transport operator (with mu)
+    double *mueff;                                       // mu + mu_t per cell (LES)
     double *rho1, *dinvu, *dinvh, *bu, *bw, *ua, *wa, *ub, *wb;   // Step 1
     double *bh, *ha, *hb;                                // Step 2
     double *rho2, *psi, *Dx, *Dz, *Hx, *Hz, *b;          // Step 3
@@ -262,6 +264,7 @@ __device__ bool grid_sum(const T (&v)[NV], double *red, double *partials, unsign
 void launch_derive(const Geom &G, const Phys &F, const double *rho, const double *rhou,
                    const double *rhow, const double *rhoe, const State &S, Scal *sc,
                    cudaStream_t st);
+void launch_les(const StepArgs &a, cudaStream_t st, Tracer *tr);
 void launch_pred_setup(const StepArgs &a, cudaStream_t st, Tracer *tr);
 // second = 1: the second sweep of a pair (copies instead once converged)
 void launch_mom_jacobi(const StepArgs &a, const double *uin, const double *win, double *uout,

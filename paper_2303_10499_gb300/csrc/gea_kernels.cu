@@ -56,6 +56,13 @@ __global__ void k_derive(Geom G, Phys F, const double *__restrict__ rho,
 
 // ---- Step 1 ----
 
+__global__ void k_les(StepArgs a)
+{
+    if (a.sc->status) return;
+    __shared__ double sm[2 * kT1];
+    ph_les(a, sm, blockIdx.x, blockIdx.y);
+}
+
 __global__ void k_pred_setup(StepArgs a)
 {
     if (a.sc->status) return;
@@ -322,6 +329,11 @@ void launch_derive(const Geom &G, const Phys &F, const double *rho, const double
     } while (0)
 
 inline long long ncell(const Geom &G) { return (long long)G.nx * G.nz; }
+
+void launch_les(const StepArgs &a, cudaStream_t st, Tracer *tr)
+{
+    TRACED(tr, "les", ncell(a.G), (k_les<<<grid_of(a.G), kBlock, 0, st>>>(a)));
+}
 
 void launch_pred_setup(const StepArgs &a, cudaStream_t st, Tracer *tr)
 {

@@ -142,6 +142,12 @@ __device__ bool run_step(const PersistArgs &P, const StepArgs &a, double *sm, do
     const Level *L = P.L;
     const int nlev = P.nlev;
 
+    // ---- Smagorinsky eddy viscosity of the step (LES) ----
+    if (a.F.les_d2 > 0.0) {
+        for_tiles(G, [&](int bx, int bz) { ph_les(a, sm, bx, bz); });
+        gbar(sc);
+        if (stop(sc)) return false;
+    }
     // ---- Step 1: continuity predictor, transport operator, momentum RHS ----
     {
         double acc[2] = {0.0, 0.0};

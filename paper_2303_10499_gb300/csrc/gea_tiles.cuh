@@ -188,6 +188,33 @@ __device__ __forceinline__ R helm_tile(const LevelT<R> &L, int q, int i, int k, 
 }
 
 // ---------------------------------------------------------------------------
+// Smagorinsky eddy viscosity (LES): mu_eff = mu + rho (cs Delta)^2 |S| from
+// rho^n and u^n, |S|^2 = 2 (du/dx)^2 + 2 (dw/dz)^2 + (du/dz + dw/dx)^2 with
+// central differences (ghosts by the wall rules)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void ph_les(const StepArgs &a, double *sm, int bx, int bz)
+{
+    const Geom &G = a.G;
+    const Phys &F = a.F;
+    Tile<1> &su = tile_at<1>(sm, 0), &sw = tile_at<1>(sm, 1);
+    load_tile<BC_U, 1>(su, G, F, a.S.u, bx, bz);
+    load_tile<BC_W, 1>(sw, G, F, a.S.w, bx, bz);
+    __syncthreads();
+    int i, k;
+    if (cell_of(G, bx, bz, i, k)) {
+        const int q = cidx(G, i, k);
+        const int y = threadIdx.y + 1, x = threadIdx.x + 1;
+        const double hx = 0.5 * G.idx, hz = 0.5 * G.idz;
+        const double dudx = (su[y][x + 1] - su[y][x - 1]) * hx, dudz = (su[y + 1][x] - su[y - 1][x]) * hz;
+        const double dwdx = (sw[y][x + 1] - sw[y][x - 1]) * hx, dwdz = (sw[y + 1][x] - sw[y - 1][x]) * hz;
+        const double sh = dudz + dwdx;
+        const double S = sqrt(2.0 * dudx * dudx + 2.0 * dwdz * dwdz + sh * sh);
+        a.mueff[q] = fma(ld(&a.S.rho[q]) * F.les_d2, S, F.mu);
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
 // Step 1 (eq. e1_d and eq. step2_sd, first line)
 // ---------------------------------------------------------------------------
 
@@ -227,10 +254,23 @@ __device__ __forceinline__ void ph_pred_t(const StepArgs &a, const MixedArgs &m,
         const double rho1 = rq - F.dt * div;
         const double s12 = G.iV * (1.0 / 12.0);
         const double fe = pe * s12, fw = pw * s12, fn = pn * s12, fs = ps * s12;
-        const double mx = F.mu * G.idx * G.idx, mz = F.mu * G.idz * G.idz;
-        const double cC = rho1 * F.idt + (7.0 / 12.0) * div + 2.0 * (mx + mz);
-        const double cE1 = fma(7.0, fe, fw) - mx, cW1 = -fma(7.0, fw, fe) - mx;
-        const double cN1 = fma(7.0, fn, fs) - mz, cS1 = -fma(7.0, fs, fn) - mz;
+        // diffusion: mu/dx^2 per face, or with LES the face mean of mu_eff
+        // (a wall face takes the cell's own)
+        double me, mw, mn, ms;
+        if (F.les_d2 > 0.0) {
+            const double mc = ld(&a.mueff[q]);
+            const double ix2 = 0.5 * G.idx * G.idx, iz2 = 0.5 * G.idz * G.idz;
+            me = (mc + (i + 1 < G.nx ? ld(&a.mueff[q + 1]) : mc)) * ix2;
+            mw = (mc + (i > 0 ? ld(&a.mueff[q - 1]) : mc)) * ix2;
+            mn = (mc + (k + 1 < G.nz ? ld(&a.mueff[q + G.P]) : mc)) * iz2;
+            ms = (mc + (k > 0 ? ld(&a.mueff[q - G.P]) : mc)) * iz2;
+        } else {
+            me = mw = F.mu * G.idx * G.idx;
+            mn = ms = F.mu * G.idz * G.idz;
+        }
+        const double cC = rho1 * F.idt + (7.0 / 12.0) * div + ((me + mw) + (mn + ms));
+        const double cE1 = fma(7.0, fe, fw) - me, cW1 = -fma(7.0, fw, fe) - mw;
+        const double cN1 = fma(7.0, fn, fs) - mn, cS1 = -fma(7.0, fs, fn) - ms;
         const double cE2 = -fe, cW2 = fw, cN2 = -fn, cS2 = fs;
         a.T.cC[q] = cC;
         a.T.cE1[q] = cE1;

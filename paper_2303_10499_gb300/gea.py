@@ -43,7 +43,7 @@ class _Const(C.Structure):
                 ("mu", C.c_double), ("Pr", C.c_double), ("dt", C.c_double),
                 ("n_corr", C.c_int32), ("jac_rtol", C.c_double), ("jac_maxit", C.c_int32),
                 ("cg_rtol", C.c_double), ("cg_maxit", C.c_int32),
-                ("mg_min_cells", C.c_int32), ("flags", C.c_int32), ("mp_rtol", C.c_double)]
+                ("mg_min_cells", C.c_int32), ("flags", C.c_int32), ("mp_rtol", C.c_double), ("cs", C.c_double)]
 
 
 class _View(C.Structure):
@@ -143,7 +143,7 @@ class Solver:
             (FLAG_KEEP_R0 if keep_r0 else 0)
         c = _Const(const.R, const.cp, const.g, const.p0, const.mu, const.Pr, const.dt,
                    const.n_corr, const.jac_rtol, const.jac_maxit, const.cg_rtol, const.cg_maxit,
-                   mg_min_cells, flags, mp_rtol)
+                   mg_min_cells, flags, mp_rtol, getattr(const, "cs", 0.0))
         h = C.c_void_p()
         rc = self.lib.gea_create(C.byref(g), C.byref(c), C.byref(h))
         if rc != GEA_OK:

@@ -28,7 +28,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
-from typing import Dict, Optional
+from typing import List, Dict, Optional
 
 import numpy as np
 
@@ -275,6 +275,34 @@ def paper_nonsmooth_bubble(res: float = 10.0, **kw) -> Workload:
                          name=f"paper_nonsmooth_{n}x{n}", steps=6000)
 
 
+def les_member(n: int, amp: float = 0.5, xc: float = 500.0, zc: float = 260.0, cs: float = 0.17,
+               name: str = "") -> Workload:
+    """One member of the LES ensemble: the Section 4.2 non-smooth bubble
+    (1 km box, theta' = amp inside r_c = 250 m centred (xc, zc), mu = 0.3,
+    Pr = 1, dt = 0.1, c_v = 715.5) on n x n cells with the Smagorinsky
+    eddy viscosity of constant cs added."""
+    grid = Grid(n, n, 1000.0, 1000.0)
+    const = Constants(cp=287.0 + 715.5, dt=0.1, mu=0.3, cs=cs)
+    return rising_bubble(grid, const, 300.0, "step", amp, 250.0, xc, zc,
+                         name=name or f"les_bubble_{n}x{n}", steps=100)
+
+
+def les_ensemble(n_members: int = 256, seed: int = 0, sizes=(100, 200, 400),
+                 cs: float = 0.17) -> List[Workload]:
+    """The batched LES ensemble: non-smooth bubbles with seeded amplitudes
+    uniform in [0.3, 0.7] K and centres jittered uniformly by up to 50 m in
+    x and z, member m on sizes[m % len(sizes)] cells per side."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for m in range(n_members):
+        n = int(sizes[m % len(sizes)])
+        amp = float(rng.uniform(0.3, 0.7))
+        xc = 500.0 + float(rng.uniform(-50.0, 50.0))
+        zc = 260.0 + float(rng.uniform(-50.0, 50.0))
+        out.append(les_member(n, amp, xc, zc, cs, name=f"les_member{m}_{n}x{n}"))
+    return out
+
+
 WORKLOADS = {
     # 160 x 80 cells (125 m), dt = 0.1 s, 100 steps: the small parity case
     "bubble160x80": lambda: smooth_bubble_20km(160, 80, 0.1, 100),
@@ -282,6 +310,10 @@ WORKLOADS = {
     "bubble640x320": lambda: smooth_bubble_20km(640, 320, 0.05, 100),
     # 4096 x 2048 cells (about 4.9 m), dt = 0.05 s: larger than L2 at FP64
     "bubble4096x2048": lambda: smooth_bubble_20km(4096, 2048, 0.05, 3),
+    # the non-smooth bubble with Smagorinsky LES on the ensemble's grid sizes
+    "les100": lambda: les_member(100),
+    "les200": lambda: les_member(200),
+    "les400": lambda: les_member(400),
 }
 
 
