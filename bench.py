@@ -90,6 +90,10 @@ def parse():
                     help="the learned-preconditioner configuration: smooth bubble 4096 x 2048, pressure "
                          "solves to 1e-8 relative residual, plain MG-CG against the network's initial "
                          "guess (trained first on the solver's own pressure systems)")
+    ap.add_argument("--ensemble", type=int, default=0,
+                    help="the batched LES configuration: this many non-smooth bubbles (grids 100^2, 200^2, "
+                         "400^2, Smagorinsky cs = 0.17) advanced by one launch per step, against the same "
+                         "members stepped one after another")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle baseline sample")
     return ap.parse_args()
@@ -376,6 +380,77 @@ def run_learned(args):
         print(json.dumps(res), flush=True)
 
 
+def run_ensemble(args):
+    """The LES ensemble: one cooperative launch per step for all members
+    against one launch per member per step, same states, same step counts."""
+    import torch
+    from paper_2303_10499_gb300 import build as B
+    from paper_2303_10499_gb300 import gea
+    from paper_2303_10499_gb300 import workloads as W
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    B.build()
+    wls = W.les_ensemble(args.ensemble, seed=0)
+    cells = sum(wl.grid.cells for wl in wls)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    def timed(step_all, reset):
+        reset()
+        for _ in range(args.warmup):
+            step_all()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        clk = ClockSampler(local)
+        clk.start()
+        for e0, e1 in evs:
+            flush.zero_()
+            e0.record(stream)
+            step_all()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        clocks = clk.stop()
+        return [e0.elapsed_time(e1) for e0, e1 in evs], clocks
+
+    solvers = [gea.Solver(wl.grid, wl.const, stream=stream) for wl in wls]
+
+    def reset():
+        for sv, wl in zip(solvers, wls):
+            sv.set_conservative(wl.fields)
+
+    # one launch per member per step (each member's own driver)
+    ms_seq, _ = timed(lambda: [sv.step_async(1) for sv in solvers], reset)
+    for sv in solvers:
+        sv.sync()
+    E = gea.Ensemble(solvers, stream=stream)
+    ms_ens, clocks = timed(lambda: E.step_async(1), reset)
+    E.sync()
+    iters = [sv.stats()["cg_iters"] for sv in solvers[:3]]
+    nb = E.blocks()
+    E.close()
+    value = cells * args.steps / (sum(ms_ens) / 1e3)
+    seq = cells * args.steps / (sum(ms_seq) / 1e3)
+    sizes = sorted({wl.grid.nx for wl in wls})
+    res = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": statistics.mean(ms_ens), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"LES ensemble of {len(wls)} non-smooth bubbles", "grids": sizes,
+                   "cells_per_step": cells, "cs": wls[0].const.cs, "mu": wls[0].const.mu,
+                   "dt": wls[0].const.dt, "l2": "flushed between timed steps (256 MB write, untimed)",
+                   "blocks_per_member": {str(n): sorted({b for b, wl in zip(nb, wls) if wl.grid.nx == n})
+                                         for n in sizes}},
+        "one_launch_per_member": {"value": seq, "unit": UNIT, "ms_per_step": statistics.mean(ms_seq)},
+        "speedup_vs_one_launch_per_member": value / seq,
+        "cg_iters_last_step_first_members": iters,
+        "gpu_launches": 1, "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+
+
 def run_ours(args):
     import torch
     from paper_2303_10499_gb300 import build as B
@@ -538,6 +613,8 @@ def main():
         run_reference(args)
     elif args.learned:
         run_learned(args)
+    elif args.ensemble:
+        run_ensemble(args)
     else:
         run_ours(args)
 

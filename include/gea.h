@@ -276,6 +276,33 @@ int gea_mass_energy_noalloc(int32_t nx, int32_t nz, double lx, double lz, double
                             double g, const double *rho, const double *u, const double *w,
                             const double *T, double *out, void *stream);
 
+/* ---- ensembles: many independent contexts advanced by one launch ----
+ *
+ * An ensemble runs the steps of n FP64 contexts (members, each with its own
+ * grid, constants and state) in one cooperative launch: every member gets a
+ * contiguous share of the GPU's co-resident thread blocks, in proportion to
+ * its number of 32 x 8 tiles (at least one), and steps on those blocks with
+ * its own grid barrier and its own reductions, so members never wait for
+ * one another. The results of a member are those of its own persistent
+ * driver up to the order of the reduction sums. The ensemble takes over the
+ * members' streams (gea_ensemble_set_stream sets all of them); while it
+ * exists, step members only through it. Members must not use GEA_FLAG_MIXED
+ * or GEA_FLAG_KEEP_R0 or an attached network.
+ * Errors: GEA_ERR_INVAL (null or unsuitable members, more members than
+ * co-resident blocks), GEA_ERR_STATE (a member without state, on step),
+ * GEA_ERR_NOMEM, GEA_ERR_CUDA. */
+typedef struct gea_ensemble gea_ensemble;
+int gea_ensemble_create(gea_ctx **members, int32_t n, gea_ensemble **out);
+int gea_ensemble_set_stream(gea_ensemble *e, void *stream);
+/* Blocks given to member m (0 <= m < n), or -1. */
+int gea_ensemble_blocks(const gea_ensemble *e, int32_t m);
+/* Enqueue n steps of every member (one launch); gea_sync on a member, or
+ * gea_ensemble_sync, waits and reports. */
+int gea_ensemble_step(gea_ensemble *e, int32_t n);
+/* Wait for the launches; the first member error code, or GEA_OK. */
+int gea_ensemble_sync(gea_ensemble *e);
+void gea_ensemble_destroy(gea_ensemble *e);
+
 const char *gea_last_error(const gea_ctx *ctx);
 void gea_destroy(gea_ctx *ctx);
 

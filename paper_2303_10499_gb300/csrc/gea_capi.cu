@@ -907,6 +907,143 @@ int gea_attach_net(gea_ctx *ctx, gea_net *net, int32_t mode)
     return GEA_OK;
 }
 
+}  // extern "C"
+
+struct gea_ensemble {
+    std::vector<gea_ctx *> m;
+    std::vector<int> first;          // first block of each member, n + 1 entries
+    int blocks = 0;
+    cudaStream_t st = nullptr;
+    size_t argb = 0;                 // bytes of one member's argument block
+    char *hargs = nullptr;           // pinned host staging of the argument blocks
+    void *dargs = nullptr;
+    int *dfirst = nullptr;
+};
+
+extern "C" {
+
+int gea_ensemble_create(gea_ctx **members, int32_t n, gea_ensemble **out)
+{
+    if (!members || n < 1 || !out) return GEA_ERR_INVAL;
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        gea_ctx *c = members[i];
+        if (!c || c->mixed || c->net || c->r0keep) return GEA_ERR_INVAL;
+        for (int j = 0; j < i; ++j)
+            if (members[j] == c) return GEA_ERR_INVAL;
+    }
+    const int B = ensemble_max_blocks();
+    cudaGetLastError();
+    if (B < n) return GEA_ERR_INVAL;
+    // blocks in proportion to the members' tiles, at least one each and at
+    // most one per tile; the remainder by largest fractional share
+    std::vector<long long> tiles(n);
+    long long tot = 0;
+    for (int i = 0; i < n; ++i) tot += tiles[i] = max_blocks(members[i]->G);
+    std::vector<int> nb(n, 1);
+    int left = B - n;
+    std::vector<double> frac(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        const double share = (double)left * (double)tiles[i] / (double)tot;
+        int extra = (int)share;
+        if (extra > tiles[i] - 1) extra = (int)tiles[i] - 1;
+        nb[i] += extra;
+        frac[i] = share - extra;
+    }
+    int used = 0;
+    for (int i = 0; i < n; ++i) used += nb[i];
+    while (used < B) {
+        int best = -1;
+        for (int i = 0; i < n; ++i)
+            if (nb[i] < tiles[i] && (best < 0 || frac[i] > frac[best])) best = i;
+        if (best < 0) break;
+        nb[best] += 1;
+        frac[best] = -1.0;
+        used += 1;
+    }
+    gea_ensemble *e = new gea_ensemble();
+    e->m.assign(members, members + n);
+    e->first.resize(n + 1);
+    e->first[0] = 0;
+    for (int i = 0; i < n; ++i) e->first[i + 1] = e->first[i] + nb[i];
+    e->blocks = e->first[n];
+    e->argb = persist_args_bytes();   // the kernel indexes an array of argument blocks
+    e->st = members[0]->stream;
+    if (cudaMallocHost(&e->hargs, e->argb * n) != cudaSuccess ||
+        cudaMalloc(&e->dargs, e->argb * n) != cudaSuccess ||
+        cudaMalloc(&e->dfirst, sizeof(int) * (n + 1)) != cudaSuccess ||
+        cudaMemcpy(e->dfirst, e->first.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        gea_ensemble_destroy(e);
+        return GEA_ERR_NOMEM;
+    }
+    for (gea_ctx *c : e->m) c->stream = e->st;
+    *out = e;
+    return GEA_OK;
+}
+
+int gea_ensemble_set_stream(gea_ensemble *e, void *stream)
+{
+    if (!e) return GEA_ERR_INVAL;
+    if (e->st) cudaStreamSynchronize(e->st);
+    e->st = (cudaStream_t)stream;
+    for (gea_ctx *c : e->m) c->stream = e->st;
+    return GEA_OK;
+}
+
+int gea_ensemble_blocks(const gea_ensemble *e, int32_t m)
+{
+    if (!e || m < 0 || m >= (int)e->m.size()) return -1;
+    return e->first[m + 1] - e->first[m];
+}
+
+int gea_ensemble_step(gea_ensemble *e, int32_t n)
+{
+    if (!e || n < 0) return GEA_ERR_INVAL;
+    if (n == 0) return GEA_OK;
+    for (gea_ctx *c : e->m)
+        if (!c->have_state) return GEA_ERR_STATE;
+    // the staging buffer may still feed the previous launch's copy
+    if (cudaStreamSynchronize(e->st) != cudaSuccess) return GEA_ERR_CUDA;
+    for (size_t i = 0; i < e->m.size(); ++i) {
+        gea_ctx *c = e->m[i];
+        StepArgs a[2] = {step_args(c, 0), step_args(c, 1)};
+        const int first = (int)((c->base + c->steps_at_sync) & 1);
+        persist_args_fill(e->hargs + i * e->argb, a, c->L.data(), (int)c->L.size(), kCoarseSweeps, c->C.n_corr,
+                          c->C.jac_maxit, c->C.cg_maxit, first, n);
+    }
+    if (cudaMemcpyAsync(e->dargs, e->hargs, e->argb * e->m.size(), cudaMemcpyHostToDevice, e->st) !=
+            cudaSuccess ||
+        launch_ensemble(e->dargs, e->dfirst, (int)e->m.size(), e->blocks, e->st) != cudaSuccess) {
+        cudaGetLastError();
+        return GEA_ERR_CUDA;
+    }
+    for (gea_ctx *c : e->m) c->steps_at_sync += n;
+    return GEA_OK;
+}
+
+int gea_ensemble_sync(gea_ensemble *e)
+{
+    if (!e) return GEA_ERR_INVAL;
+    int first_err = GEA_OK;
+    for (gea_ctx *c : e->m) {
+        const int rc = gea_sync(c);
+        if (rc && !first_err) first_err = rc;
+    }
+    return first_err;
+}
+
+void gea_ensemble_destroy(gea_ensemble *e)
+{
+    if (!e) return;
+    if (e->st) cudaStreamSynchronize(e->st);
+    else cudaDeviceSynchronize();
+    if (e->hargs) cudaFreeHost(e->hargs);
+    if (e->dargs) cudaFree(e->dargs);
+    if (e->dfirst) cudaFree(e->dfirst);
+    delete e;
+}
+
 const char *gea_last_error(const gea_ctx *ctx) { return ctx ? ctx->err : "null context"; }
 
 void gea_destroy(gea_ctx *ctx)

@@ -325,5 +325,12 @@ int persistent_max_blocks();
 cudaError_t launch_persistent(const StepArgs a[2], const Level *L, int nlev, int ncoarse, int n_corr,
                               int jac_maxit, int cg_maxit, int first_slot, int nsteps, int blocks,
                               cudaStream_t st);
+// ensemble launch: one argument block per member (persist_args_fill) in
+// device memory, first[m] the member's first block (nmem + 1 entries)
+size_t persist_args_bytes();
+void persist_args_fill(void *dst, const StepArgs a[2], const Level *L, int nlev, int ncoarse, int n_corr,
+                       int jac_maxit, int cg_maxit, int first_slot, int nsteps);
+int ensemble_max_blocks();
+cudaError_t launch_ensemble(const void *Pm, const int *first, int nmem, int blocks, cudaStream_t st);
 
 }  // namespace gea

@@ -20,6 +20,8 @@
 #include "gea_internal.cuh"
 #include "gea_tiles.cuh"
 
+#include <string.h>
+
 namespace gea {
 
 namespace {
@@ -53,10 +55,17 @@ __device__ __forceinline__ unsigned long long globaltimer()
 
 __device__ __forceinline__ int tid_of() { return threadIdx.x + threadIdx.y * BX; }
 
+// The blocks that run one context's steps: this block's rank among them and
+// their number (the whole grid for one context; a contiguous share of the
+// grid per member in an ensemble launch).
+struct Grp {
+    int rank, nb;
+};
+
 // Arrive and wait. The last block to arrive runs last() (all its threads)
 // and then releases the others.
 template <class Last>
-__device__ __forceinline__ void barrier_with(Scal *sc, Last last)
+__device__ __forceinline__ void barrier_with(const Grp &g, Scal *sc, Last last)
 {
     __shared__ int am_last;
     __shared__ unsigned gen0;
@@ -67,7 +76,7 @@ __device__ __forceinline__ void barrier_with(Scal *sc, Last last)
     if (tid == 0) {
         gen0 = ld_acquire(&sc->bar_gen);
         __threadfence();
-        am_last = atomicAdd(&sc->bar_count, 1u) == gridDim.x - 1u;
+        am_last = atomicAdd(&sc->bar_count, 1u) == (unsigned)g.nb - 1u;
     }
     __syncthreads();
     if (am_last) {
@@ -92,26 +101,26 @@ __device__ __forceinline__ void barrier_with(Scal *sc, Last last)
     __syncthreads();
 }
 
-__device__ __forceinline__ void gbar(Scal *sc)
+__device__ __forceinline__ void gbar(const Grp &g, Scal *sc)
 {
-    barrier_with(sc, [] {});
+    barrier_with(g, sc, [] {});
 }
 
 // Barrier with a deterministic grid-wide sum of NV per-thread values; fin(tot)
 // runs in one thread of the last block before the release.
 template <int NV, class Fin>
-__device__ __forceinline__ void rbar(const double (&v)[NV], double *red, Scal *sc, double *partials,
-                                     Fin fin)
+__device__ __forceinline__ void rbar(const Grp &g, const double (&v)[NV], double *red, Scal *sc,
+                                     double *partials, Fin fin)
 {
     const int tid = tid_of();
-    const int nb = gridDim.x;
+    const int nb = g.nb;
     double bt[NV];
     block_sum<NV>(v, red, bt);
     if (tid == 0) {
 #pragma unroll
-        for (int j = 0; j < NV; ++j) partials[(size_t)j * nb + blockIdx.x] = bt[j];
+        for (int j = 0; j < NV; ++j) partials[(size_t)j * nb + g.rank] = bt[j];
     }
-    barrier_with(sc, [&] {
+    barrier_with(g, sc, [&] {
         double s[NV], tot[NV];
 #pragma unroll
         for (int j = 0; j < NV; ++j) {
@@ -124,18 +133,18 @@ __device__ __forceinline__ void rbar(const double (&v)[NV], double *red, Scal *s
 }
 
 template <class F>
-__device__ __forceinline__ void for_tiles(const Geom &G, F f)
+__device__ __forceinline__ void for_tiles(const Grp &g, const Geom &G, F f)
 {
     const int tx = (G.nx + BX - 1) / BX, tz = (G.nz + BZ - 1) / BZ;
     const int nt = tx * tz;
-    for (int t = blockIdx.x; t < nt; t += gridDim.x) f(t % tx, t / tx);
+    for (int t = g.rank; t < nt; t += g.nb) f(t % tx, t / tx);
 }
 
 __device__ __forceinline__ bool stop(const Scal *sc) { return rdi(&sc->status) != 0; }
 
 // One time step reading a.S and writing a.N. Returns false if the step did
 // not complete (a device error is set).
-__device__ bool run_step(const PersistArgs &P, const StepArgs &a, double *sm, double *red)
+__device__ bool run_step(const PersistArgs &P, const StepArgs &a, const Grp &g, double *sm, double *red)
 {
     Scal *sc = a.sc;
     const Geom &G = a.G;
@@ -144,15 +153,15 @@ __device__ bool run_step(const PersistArgs &P, const StepArgs &a, double *sm, do
 
     // ---- Smagorinsky eddy viscosity of the step (LES) ----
     if (a.F.les_d2 > 0.0) {
-        for_tiles(G, [&](int bx, int bz) { ph_les(a, sm, bx, bz); });
-        gbar(sc);
+        for_tiles(g, G, [&](int bx, int bz) { ph_les(a, sm, bx, bz); });
+        gbar(g, sc);
         if (stop(sc)) return false;
     }
     // ---- Step 1: continuity predictor, transport operator, momentum RHS ----
     {
         double acc[2] = {0.0, 0.0};
-        for_tiles(G, [&](int bx, int bz) { ph_pred(a, bx, bz, acc); });
-        rbar<2>(acc, red, sc, a.partials, [&](const double (&t)[2]) {
+        for_tiles(g, G, [&](int bx, int bz) { ph_pred(a, bx, bz, acc); });
+        rbar<2>(g, acc, red, sc, a.partials, [&](const double (&t)[2]) {
             fin_pred(sc, t);
             for (int c = 0; c < 4; ++c) { sc->cg_iters[c] = 0; sc->cg_relres[c] = 0.0; }
             sc->sweeps[1] = 0;
@@ -166,8 +175,8 @@ __device__ bool run_step(const PersistArgs &P, const StepArgs &a, double *sm, do
     double *uout = a.ub, *wout = a.wb;
     for (;;) {
         double acc[2] = {0.0, 0.0};
-        for_tiles(G, [&](int bx, int bz) { ph_mom(a, uin, win, uout, wout, sm, bx, bz, acc); });
-        rbar<2>(acc, red, sc, a.partials, [&](const double (&t)[2]) {
+        for_tiles(g, G, [&](int bx, int bz) { ph_mom(a, uin, win, uout, wout, sm, bx, bz, acc); });
+        rbar<2>(g, acc, red, sc, a.partials, [&](const double (&t)[2]) {
             fin_mom(sc, t, a.jac_rtol2);
             if (!sc->done[LOOP_MOM] && !sc->status && sc->sweeps[0] >= P.jac_maxit) sc->status = GEA_ERR_NOCONV;
         });
@@ -182,16 +191,16 @@ __device__ bool run_step(const PersistArgs &P, const StepArgs &a, double *sm, do
     // ---- Step 2: enthalpy, temperature, rho^{n+2/3} ----
     {
         double acc[1] = {0.0};
-        for_tiles(G, [&](int bx, int bz) { ph_enth_rhs(a, u1, w1, a.ha, sm, bx, bz, acc); });
-        rbar<1>(acc, red, sc, a.partials, [&](const double (&t)[1]) { fin_enth_rhs(sc, t); });
+        for_tiles(g, G, [&](int bx, int bz) { ph_enth_rhs(a, u1, w1, a.ha, sm, bx, bz, acc); });
+        rbar<1>(g, acc, red, sc, a.partials, [&](const double (&t)[1]) { fin_enth_rhs(sc, t); });
     }
     if (stop(sc)) return false;
     const double *hin = a.ha;
     double *hout = a.hb;
     for (;;) {
         double acc[1] = {0.0};
-        for_tiles(G, [&](int bx, int bz) { ph_enth(a, hin, hout, sm, bx, bz, acc); });
-        rbar<1>(acc, red, sc, a.partials, [&](const double (&t)[1]) {
+        for_tiles(g, G, [&](int bx, int bz) { ph_enth(a, hin, hout, sm, bx, bz, acc); });
+        rbar<1>(g, acc, red, sc, a.partials, [&](const double (&t)[1]) {
             fin_enth(sc, t, a.jac_rtol2);
             if (!sc->done[LOOP_ENTH] && !sc->status && sc->sweeps[1] >= P.jac_maxit) sc->status = GEA_ERR_NOCONV;
         });
@@ -202,14 +211,14 @@ __device__ bool run_step(const PersistArgs &P, const StepArgs &a, double *sm, do
     }
     if (stop(sc)) return false;
     const double *h1 = hin;
-    for_tiles(G, [&](int bx, int bz) { ph_eos(a, L[0], h1, sm, bx, bz); });
-    gbar(sc);
+    for_tiles(g, G, [&](int bx, int bz) { ph_eos(a, L[0], h1, sm, bx, bz); });
+    gbar(g, sc);
     for (int l = 0; l + 1 < nlev; ++l) {
-        for_tiles(L[l + 1].G, [&](int bx, int bz) { ph_coarsen(L[l], L[l + 1], a.F.omega, bx, bz); });
-        gbar(sc);
+        for_tiles(g, L[l + 1].G, [&](int bx, int bz) { ph_coarsen(L[l], L[l + 1], a.F.omega, bx, bz); });
+        gbar(g, sc);
     }
     if (stop(sc)) return false;
-    if (blockIdx.x == 0 && tid_of() == 0) {
+    if (g.rank == 0 && tid_of() == 0) {
         sc->u1_slot = (u1 == a.ub);
         sc->h1_slot = (h1 == a.hb);
     }
@@ -218,45 +227,45 @@ __device__ bool run_step(const PersistArgs &P, const StepArgs &a, double *sm, do
     for (int c = 0; c < P.n_corr; ++c) {
         const double *U = c == 0 ? u1 : a.N.u;
         const double *W = c == 0 ? w1 : a.N.w;
-        for_tiles(G, [&](int bx, int bz) { ph_H(a, U, W, sm, bx, bz); });
-        gbar(sc);
+        for_tiles(g, G, [&](int bx, int bz) { ph_H(a, U, W, sm, bx, bz); });
+        gbar(g, sc);
         unsigned long long t0 = 0;
-        if (blockIdx.x == 0 && tid_of() == 0) t0 = globaltimer();
+        if (g.rank == 0 && tid_of() == 0) t0 = globaltimer();
         {
             double acc[2] = {0.0, 0.0};
             const double *xin = c == 0 ? a.S.pp : a.N.pp;
-            for_tiles(G, [&](int bx, int bz) { ph_helm_rhs(a, L[0], xin, a.N.pp, sm, bx, bz, acc); });
-            rbar<2>(acc, red, sc, a.partials, [&](const double (&t)[2]) { fin_helm(sc, t, a.cg_rtol2, c); });
+            for_tiles(g, G, [&](int bx, int bz) { ph_helm_rhs(a, L[0], xin, a.N.pp, sm, bx, bz, acc); });
+            rbar<2>(g, acc, red, sc, a.partials, [&](const double (&t)[2]) { fin_helm(sc, t, a.cg_rtol2, c); });
         }
         // z = M^-1 r_0 (one V(1,1)-cycle), then the iterations
         auto vcycle_levels = [&](int lfirst) {
             for (int l = lfirst; l + 1 < nlev; ++l) {
-                for_tiles(L[l].G, [&](int bx, int bz) { ph_mg_down(L[l], L[l + 1], a.F.omega, sm, bx, bz); });
-                gbar(sc);
+                for_tiles(g, L[l].G, [&](int bx, int bz) { ph_mg_down(L[l], L[l + 1], a.F.omega, sm, bx, bz); });
+                gbar(g, sc);
             }
             const Level &C = L[nlev - 1];
             for (int s = 0; s < P.ncoarse; ++s) {
                 double *out = ((P.ncoarse - 1 - s) % 2 == 0) ? C.e2 : C.e;
                 const double *in = (out == C.e2) ? C.e : C.e2;
-                for_tiles(C.G, [&](int bx, int bz) { ph_mg_coarse(C, in, out, s == 0, sm, bx, bz); });
-                gbar(sc);
+                for_tiles(g, C.G, [&](int bx, int bz) { ph_mg_coarse(C, in, out, s == 0, sm, bx, bz); });
+                gbar(g, sc);
             }
             const double *res0 = res_of(L[0], rdi(&sc->cg_it));
             for (int l = nlev - 2; l >= 0; --l) {
                 double acc[1] = {0.0};
                 const double *res = l == 0 ? res0 : L[l].r;
-                for_tiles(L[l].G, [&](int bx, int bz) {
+                for_tiles(g, L[l].G, [&](int bx, int bz) {
                     ph_mg_up(L[l], res, L[l + 1].e2, L[l + 1].G.P, L[l].e2, sm, bx, bz, acc);
                 });
-                if (l > 0) gbar(sc);
-                else rbar<1>(acc, red, sc, a.partials, [&](const double (&t)[1]) { fin_rz(sc, t); });
+                if (l > 0) gbar(g, sc);
+                else rbar<1>(g, acc, red, sc, a.partials, [&](const double (&t)[1]) { fin_rz(sc, t); });
             }
         };
         if (!stop(sc) && !rdi(&sc->done[LOOP_CG])) {
             if (nlev == 1) {
                 double acc[1] = {0.0};
-                for_tiles(G, [&](int bx, int bz) { ph_mg_single(L[0], L[0].e2, sm, bx, bz, acc); });
-                rbar<1>(acc, red, sc, a.partials, [&](const double (&t)[1]) { fin_rz(sc, t); });
+                for_tiles(g, G, [&](int bx, int bz) { ph_mg_single(L[0], L[0].e2, sm, bx, bz, acc); });
+                rbar<1>(g, acc, red, sc, a.partials, [&](const double (&t)[1]) { fin_rz(sc, t); });
             } else {
                 vcycle_levels(0);
             }
@@ -269,8 +278,8 @@ __device__ bool run_step(const PersistArgs &P, const StepArgs &a, double *sm, do
             {
                 const double beta = rdd(&sc->beta);
                 double acc[1] = {0.0};
-                for_tiles(G, [&](int bx, int bz) { ph_pspmv<double>(L[0], pold, pnew, a.q, beta, sm, bx, bz, acc); });
-                rbar<1>(acc, red, sc, a.partials, [&](const double (&t)[1]) { fin_pq(sc, t); });
+                for_tiles(g, G, [&](int bx, int bz) { ph_pspmv<double>(L[0], pold, pnew, a.q, beta, sm, bx, bz, acc); });
+                rbar<1>(g, acc, red, sc, a.partials, [&](const double (&t)[1]) { fin_pq(sc, t); });
             }
             // x += alpha p, r -= alpha q, with the first step of the next V-cycle
             const double alpha = rdd(&sc->alpha);
@@ -279,11 +288,11 @@ __device__ bool run_step(const PersistArgs &P, const StepArgs &a, double *sm, do
             };
             if (nlev == 1) {
                 double acc[2] = {0.0, 0.0};
-                for_tiles(G, [&](int bx, int bz) {
+                for_tiles(g, G, [&](int bx, int bz) {
                     ph_update_single<double>(L[0], a.q, res_of(L[0], it), res_of(L[0], it + 1), a.N.pp,
                                              pnew, alpha, sm, bx, bz, acc);
                 });
-                rbar<2>(acc, red, sc, a.partials, [&](const double (&t)[2]) {
+                rbar<2>(g, acc, red, sc, a.partials, [&](const double (&t)[2]) {
                     const double t0[1] = {t[0]}, t1[1] = {t[1]};
                     fin_update(sc, t0, a.cg_rtol2);
                     fin_rz(sc, t1);
@@ -291,11 +300,11 @@ __device__ bool run_step(const PersistArgs &P, const StepArgs &a, double *sm, do
                 });
             } else {
                 double acc[1] = {0.0};
-                for_tiles(G, [&](int bx, int bz) {
+                for_tiles(g, G, [&](int bx, int bz) {
                     ph_update_down<double>(L[0], L[1], a.q, res_of(L[0], it), res_of(L[0], it + 1), a.N.pp,
                                            pnew, alpha, a.F.omega, sm, bx, bz, acc);
                 });
-                rbar<1>(acc, red, sc, a.partials, [&](const double (&t)[1]) {
+                rbar<1>(g, acc, red, sc, a.partials, [&](const double (&t)[1]) {
                     fin_update(sc, t, a.cg_rtol2);
                     cap();
                 });
@@ -303,12 +312,12 @@ __device__ bool run_step(const PersistArgs &P, const StepArgs &a, double *sm, do
             }
         }
         if (stop(sc)) return false;
-        if (blockIdx.x == 0 && tid_of() == 0) sc->press_ns += globaltimer() - t0;
-        for_tiles(G, [&](int bx, int bz) { ph_correct(a, sm, bx, bz); });
-        if (c + 1 < P.n_corr) gbar(sc);
+        if (g.rank == 0 && tid_of() == 0) sc->press_ns += globaltimer() - t0;
+        for_tiles(g, G, [&](int bx, int bz) { ph_correct(a, sm, bx, bz); });
+        if (c + 1 < P.n_corr) gbar(g, sc);
     }
     // end of step: publish the step's counters
-    barrier_with(sc, [&] {
+    barrier_with(g, sc, [&] {
         if (tid_of() == 0 && !sc->status) {
             sc->steps_done += 1;
             sc->last_sweeps[0] = sc->sweeps[0];
@@ -332,9 +341,10 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_persistent(PersistArgs P)
     // is sticky until the next set_state, which clears it
     if (rdi(&P.a[0].sc->status)) return;
     if (blockIdx.x == 0 && tid_of() == 0) P.a[0].sc->launches += 1;
+    const Grp g{(int)blockIdx.x, (int)gridDim.x};
     for (int s = 0; s < P.nsteps; ++s) {
         const int slot = (P.first_slot + s) & 1;
-        if (!run_step(P, P.a[slot], sm, red)) break;
+        if (!run_step(P, P.a[slot], g, sm, red)) break;
     }
     Scal *sc = P.a[0].sc;
     if (blockIdx.x == 0 && tid_of() == 0 && sc->status) sc->last_status = sc->status;
@@ -342,7 +352,88 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_persistent(PersistArgs P)
 
 constexpr size_t kPersistSmem = (size_t)(kTileSmem + 2 * NTHREADS) * sizeof(double);
 
+// An ensemble of independent contexts in one cooperative launch: member m
+// runs its steps on blocks first[m] .. first[m+1]-1 with its own grid
+// barrier and reductions over those blocks only, so members whose solves
+// take different iteration counts never wait for one another. Each block
+// keeps its member's arguments in shared memory.
+__global__ void __launch_bounds__(NTHREADS, 3) k_ensemble(const PersistArgs *Pm, const int *first, int nmem)
+{
+    extern __shared__ double dsm[];
+    double *sm = dsm;
+    double *red = dsm + kTileSmem;
+    PersistArgs *Ps = reinterpret_cast<PersistArgs *>(dsm + kTileSmem + 2 * NTHREADS);
+    const int tid = tid_of();
+    int lo = 0, hi = nmem - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (__ldg(&first[mid]) <= (int)blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    const int m = lo;
+    {
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(&Pm[m]);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(Ps);
+        for (int i = tid; i < (int)(sizeof(PersistArgs) / 4); i += NTHREADS) dst[i] = __ldg(&src[i]);
+    }
+    __syncthreads();
+    const PersistArgs &P = *Ps;
+    const Grp g{(int)blockIdx.x - __ldg(&first[m]), __ldg(&first[m + 1]) - __ldg(&first[m])};
+    Scal *sc = P.a[0].sc;
+    if (rdi(&sc->status)) return;
+    if (g.rank == 0 && tid == 0) sc->launches += 1;
+    for (int s = 0; s < P.nsteps; ++s) {
+        const int slot = (P.first_slot + s) & 1;
+        if (!run_step(P, P.a[slot], g, sm, red)) break;
+    }
+    if (g.rank == 0 && tid == 0 && sc->status) sc->last_status = sc->status;
+}
+
+constexpr size_t kEnsembleSmem = kPersistSmem + (sizeof(PersistArgs) + 15) / 16 * 16;
+
 }  // namespace
+
+size_t persist_args_bytes() { return sizeof(PersistArgs); }
+
+void persist_args_fill(void *dst, const StepArgs a[2], const Level *L, int nlev, int ncoarse, int n_corr,
+                       int jac_maxit, int cg_maxit, int first_slot, int nsteps)
+{
+    PersistArgs P;
+    memset(&P, 0, sizeof(P));
+    P.a[0] = a[0];
+    P.a[1] = a[1];
+    for (int l = 0; l < nlev && l < kMaxLevels; ++l) P.L[l] = L[l];
+    P.nlev = nlev;
+    P.ncoarse = ncoarse;
+    P.nsteps = nsteps;
+    P.first_slot = first_slot;
+    P.n_corr = n_corr;
+    P.jac_maxit = jac_maxit;
+    P.cg_maxit = cg_maxit;
+    memcpy(dst, &P, sizeof(P));
+}
+
+int ensemble_max_blocks()
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaFuncSetAttribute(k_ensemble, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEnsembleSmem) !=
+        cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ensemble, NTHREADS, kEnsembleSmem) !=
+        cudaSuccess)
+        return 0;
+    return per_sm * sms;
+}
+
+cudaError_t launch_ensemble(const void *Pm, const int *first, int nmem, int blocks, cudaStream_t st)
+{
+    const PersistArgs *P = static_cast<const PersistArgs *>(Pm);
+    void *args[] = {&P, &first, &nmem};
+    return cudaLaunchCooperativeKernel((const void *)k_ensemble, dim3(blocks), dim3(BX, BZ), args, kEnsembleSmem,
+                                       st);
+}
 
 int persistent_max_blocks()
 {

@@ -96,6 +96,13 @@ def library() -> C.CDLL:
         I = C.c_int32
         lib.gea_conv3x3.argtypes = [I, I, I, I, I, I, I, P, P, P, P, P, P, P]
         lib.gea_attach_net.argtypes = [P, P, I]
+        lib.gea_ensemble_create.argtypes = [C.POINTER(P), I, C.POINTER(P)]
+        lib.gea_ensemble_set_stream.argtypes = [P, P]
+        lib.gea_ensemble_blocks.argtypes = [P, I]
+        lib.gea_ensemble_step.argtypes = [P, I]
+        lib.gea_ensemble_sync.argtypes = [P]
+        lib.gea_ensemble_destroy.argtypes = [P]
+        lib.gea_ensemble_destroy.restype = None
         lib.gea_net_param_count.restype = C.c_int64
         lib.gea_net_layout.argtypes = [P]
         lib.gea_net_create.argtypes = [I, I, I, I, C.POINTER(P)]
@@ -372,3 +379,43 @@ class Net:
         _chk(self.lib.gea_net_train_step(self.h, n, hh, ww, r.data_ptr(), c.data_ptr(), ax.data_ptr(),
                                          az.data_ptr(), lr, C.byref(loss)), "gea_net_train_step")
         return float(loss.value)
+
+
+class Ensemble:
+    """Independent solvers advanced together by one cooperative launch per
+    call (gea_ensemble_*). The solvers stay usable for get/diagnostics; step
+    them only through the ensemble while it exists."""
+
+    def __init__(self, solvers, stream=None):
+        self.lib = library()
+        self.solvers = list(solvers)
+        arr = (C.c_void_p * len(self.solvers))(*[sv.h.value for sv in self.solvers])
+        h = C.c_void_p()
+        _chk(self.lib.gea_ensemble_create(arr, len(self.solvers), C.byref(h)), "gea_ensemble_create")
+        self.h = h
+        if stream is not None:
+            _chk(self.lib.gea_ensemble_set_stream(self.h, stream.cuda_stream), "gea_ensemble_set_stream")
+
+    def blocks(self):
+        return [int(self.lib.gea_ensemble_blocks(self.h, m)) for m in range(len(self.solvers))]
+
+    def step_async(self, n: int = 1):
+        _chk(self.lib.gea_ensemble_step(self.h, int(n)), "gea_ensemble_step")
+
+    def sync(self):
+        _chk(self.lib.gea_ensemble_sync(self.h), "gea_ensemble_sync")
+
+    def step(self, n: int = 1):
+        self.step_async(n)
+        self.sync()
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gea_ensemble_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

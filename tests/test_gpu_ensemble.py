@@ -1,0 +1,108 @@
+"""Ensembles of independent contexts in one cooperative launch
+(gea_ensemble_*): members of different sizes and constants, each on its own
+share of the blocks with its own barrier and reductions.
+
+A member's step is its persistent-driver step with the reduction sums taken
+over fewer blocks (a different summation order), so it matches the member
+stepped alone to rounding (bound 1e-12 relative L2; the solves run to
+round-off) and the oracle at the parity bound.
+"""
+import numpy as np
+import pytest
+
+from paper_2303_10499_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gea():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required")
+    from paper_2303_10499_gb300 import build as B
+    B.build()
+    from paper_2303_10499_gb300 import gea as G
+    return G
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def members():
+    """LES bubbles of the three ensemble sizes, a constant-viscosity bubble
+    and a ragged random flow."""
+    out = W.les_ensemble(6, seed=3)
+    out.append(W.get("bubble160x80"))
+    out.append(W.random_flow(W.Grid(37, 23, 370.0, 230.0), W.Constants(dt=0.2, mu=1.5), seed=5,
+                             uamp=3.0, thamp=2.0))
+    return out
+
+
+def test_ensemble_matches_members_stepped_alone(gea, oracle_mod):
+    wls = members()
+    steps = 10
+    solo = []
+    for wl in wls:
+        s = gea.Solver(wl.grid, wl.const)
+        s.set_conservative(wl.fields)
+        s.step(steps)
+        solo.append(s.get_full())
+        s.close()
+    ens = [gea.Solver(wl.grid, wl.const) for wl in wls]
+    for s, wl in zip(ens, wls):
+        s.set_conservative(wl.fields)
+    E = gea.Ensemble(ens)
+    nb = E.blocks()
+    assert min(nb) >= 1
+    E.step(steps // 2)
+    E.step(steps - steps // 2)
+    for k, (s, ref) in enumerate(zip(ens, solo)):
+        st = s.stats()
+        assert st["status"] == 0 and st["steps_done"] == steps, (k, st)
+        g = s.get_full()
+        vel = np.hypot(np.linalg.norm(ref["u"]), np.linalg.norm(ref["w"]))
+        for f in ("rho", "T", "pp"):
+            assert rel(g[f], ref[f]) < 1e-12, (k, f)
+        for f in ("u", "w"):
+            assert np.linalg.norm(g[f] - ref[f]) / vel < 1e-9, (k, f)
+    # the smallest LES member against the oracle
+    wl = wls[0]
+    o = oracle_mod.Oracle(wl.grid, wl.const)
+    so = o.derive(wl.fields)
+    o.step(so, steps)
+    g = ens[0].get_full()
+    vel = np.hypot(np.linalg.norm(so["u"]), np.linalg.norm(so["w"]))
+    assert rel(g["rho"], so["rho"]) < 1e-10
+    assert np.linalg.norm(g["w"] - so["w"]) / vel < 1e-10
+
+
+def test_ensemble_is_deterministic(gea):
+    wls = W.les_ensemble(9, seed=11)
+    out = []
+    for _ in range(2):
+        ss = [gea.Solver(wl.grid, wl.const) for wl in wls]
+        for s, wl in zip(ss, wls):
+            s.set_conservative(wl.fields)
+        E = gea.Ensemble(ss)
+        E.step(5)
+        out.append([s.get_full() for s in ss])
+        E.close()
+    for a, b in zip(*out):
+        for f in a:
+            assert np.array_equal(a[f], b[f]), f
+
+
+def test_ensemble_rejects_unsuitable_members(gea):
+    wl = W.get("les100")
+    a = gea.Solver(wl.grid, wl.const)
+    b = gea.Solver(wl.grid, wl.const, mixed=True)
+    with pytest.raises(gea.GeaError):
+        gea.Ensemble([a, b])
+    with pytest.raises(gea.GeaError):
+        gea.Ensemble([a, a])
+    E = gea.Ensemble([a])
+    with pytest.raises(gea.GeaError) as ei:
+        E.step(1)                       # no state set
+    assert ei.value.code == gea.GEA_ERR_STATE
