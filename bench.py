@@ -386,6 +386,7 @@ def run_ensemble(args):
     import torch
     from paper_2303_10499_gb300 import build as B
     from paper_2303_10499_gb300 import gea
+    from paper_2303_10499_gb300 import ensemble as ensemble_tuner
     from paper_2303_10499_gb300 import workloads as W
 
     world, rank, local = dist_env()
@@ -424,7 +425,13 @@ def run_ensemble(args):
     ms_seq, _ = timed(lambda: [sv.step_async(1) for sv in solvers], reset)
     for sv in solvers:
         sv.sync()
-    E = gea.Ensemble(solvers, stream=stream)
+    # block partition: tiles only, then the autotuner's choice
+    E0 = gea.Ensemble(solvers, stream=stream)
+    ms_tiles, _ = timed(lambda: E0.step_async(1), reset)
+    E0.sync()
+    E0.close()
+    reset()
+    E, tune = ensemble_tuner.autotune(solvers, stream=stream)
     ms_ens, clocks = timed(lambda: E.step_async(1), reset)
     E.sync()
     iters = [sv.stats()["cg_iters"] for sv in solvers[:3]]
@@ -443,6 +450,9 @@ def run_ensemble(args):
                    "blocks_per_member": {str(n): sorted({b for b, wl in zip(nb, wls) if wl.grid.nx == n})
                                          for n in sizes}},
         "one_launch_per_member": {"value": seq, "unit": UNIT, "ms_per_step": statistics.mean(ms_seq)},
+        "ensemble_blocks_by_tiles": {"value": cells * args.steps / (sum(ms_tiles) / 1e3), "unit": UNIT,
+                                     "ms_per_step": statistics.mean(ms_tiles)},
+        "autotune": tune if not isinstance(tune, dict) else {k: v for k, v in tune.items() if k != "blocks"},
         "speedup_vs_one_launch_per_member": value / seq,
         "cg_iters_last_step_first_members": iters,
         "gpu_launches": 1, "clocks": clocks,

@@ -281,7 +281,8 @@ int gea_mass_energy_noalloc(int32_t nx, int32_t nz, double lx, double lz, double
  * An ensemble runs the steps of n FP64 contexts (members, each with its own
  * grid, constants and state) in one cooperative launch: every member gets a
  * contiguous share of the GPU's co-resident thread blocks, in proportion to
- * its number of 32 x 8 tiles (at least one), and steps on those blocks with
+ * its weight (default: its number of 32 x 8 tiles; at least one block, at
+ * most one per tile), and steps on those blocks with
  * its own grid barrier and its own reductions, so members never wait for
  * one another. The results of a member are those of its own persistent
  * driver up to the order of the reduction sums. The ensemble takes over the
@@ -292,7 +293,9 @@ int gea_mass_energy_noalloc(int32_t nx, int32_t nz, double lx, double lz, double
  * co-resident blocks), GEA_ERR_STATE (a member without state, on step),
  * GEA_ERR_NOMEM, GEA_ERR_CUDA. */
 typedef struct gea_ensemble gea_ensemble;
-int gea_ensemble_create(gea_ctx **members, int32_t n, gea_ensemble **out);
+/* weights (optional, n positive values): blocks in proportion to weights[m]
+ * instead of the member's tile count. */
+int gea_ensemble_create(gea_ctx **members, int32_t n, const double *weights, gea_ensemble **out);
 int gea_ensemble_set_stream(gea_ensemble *e, void *stream);
 /* Blocks given to member m (0 <= m < n), or -1. */
 int gea_ensemble_blocks(const gea_ensemble *e, int32_t m);

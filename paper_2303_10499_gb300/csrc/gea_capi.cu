@@ -922,7 +922,7 @@ struct gea_ensemble {
 
 extern "C" {
 
-int gea_ensemble_create(gea_ctx **members, int32_t n, gea_ensemble **out)
+int gea_ensemble_create(gea_ctx **members, int32_t n, const double *weights, gea_ensemble **out)
 {
     if (!members || n < 1 || !out) return GEA_ERR_INVAL;
     *out = nullptr;
@@ -938,13 +938,19 @@ int gea_ensemble_create(gea_ctx **members, int32_t n, gea_ensemble **out)
     // blocks in proportion to the members' tiles, at least one each and at
     // most one per tile; the remainder by largest fractional share
     std::vector<long long> tiles(n);
-    long long tot = 0;
-    for (int i = 0; i < n; ++i) tot += tiles[i] = max_blocks(members[i]->G);
+    std::vector<double> wt(n);
+    double tot = 0.0;
+    for (int i = 0; i < n; ++i) {
+        tiles[i] = max_blocks(members[i]->G);
+        wt[i] = weights ? weights[i] : (double)tiles[i];
+        if (!(wt[i] > 0.0) || !(wt[i] < 1e300)) return GEA_ERR_INVAL;
+        tot += wt[i];
+    }
     std::vector<int> nb(n, 1);
     int left = B - n;
     std::vector<double> frac(n, 0.0);
     for (int i = 0; i < n; ++i) {
-        const double share = (double)left * (double)tiles[i] / (double)tot;
+        const double share = (double)left * wt[i] / tot;
         int extra = (int)share;
         if (extra > tiles[i] - 1) extra = (int)tiles[i] - 1;
         nb[i] += extra;

@@ -96,7 +96,7 @@ def library() -> C.CDLL:
         I = C.c_int32
         lib.gea_conv3x3.argtypes = [I, I, I, I, I, I, I, P, P, P, P, P, P, P]
         lib.gea_attach_net.argtypes = [P, P, I]
-        lib.gea_ensemble_create.argtypes = [C.POINTER(P), I, C.POINTER(P)]
+        lib.gea_ensemble_create.argtypes = [C.POINTER(P), I, P, C.POINTER(P)]
         lib.gea_ensemble_set_stream.argtypes = [P, P]
         lib.gea_ensemble_blocks.argtypes = [P, I]
         lib.gea_ensemble_step.argtypes = [P, I]
@@ -386,12 +386,19 @@ class Ensemble:
     call (gea_ensemble_*). The solvers stay usable for get/diagnostics; step
     them only through the ensemble while it exists."""
 
-    def __init__(self, solvers, stream=None):
+    def __init__(self, solvers, stream=None, weights=None):
+        """weights: optional per-member work weights (blocks in proportion;
+        default the members' tile counts)."""
         self.lib = library()
         self.solvers = list(solvers)
         arr = (C.c_void_p * len(self.solvers))(*[sv.h.value for sv in self.solvers])
+        w = None
+        if weights is not None:
+            self._w = np.ascontiguousarray(weights, dtype=np.float64)
+            assert self._w.size == len(self.solvers)
+            w = self._w.ctypes.data
         h = C.c_void_p()
-        _chk(self.lib.gea_ensemble_create(arr, len(self.solvers), C.byref(h)), "gea_ensemble_create")
+        _chk(self.lib.gea_ensemble_create(arr, len(self.solvers), w, C.byref(h)), "gea_ensemble_create")
         self.h = h
         if stream is not None:
             _chk(self.lib.gea_ensemble_set_stream(self.h, stream.cuda_stream), "gea_ensemble_set_stream")

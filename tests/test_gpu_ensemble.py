@@ -108,3 +108,27 @@ def test_ensemble_rejects_unsuitable_members(gea):
     with pytest.raises(gea.GeaError) as ei:
         E.step(1)                       # no state set
     assert ei.value.code == gea.GEA_ERR_STATE
+
+
+def test_weights_and_autotune(gea):
+    """Blocks follow the weights (at least one per member, at most one per
+    tile); the autotuner returns a working partition and its trial times."""
+    import torch
+    from paper_2303_10499_gb300 import ensemble
+    wls = W.les_ensemble(6, seed=2)
+    ss = [gea.Solver(wl.grid, wl.const) for wl in wls]
+    for s, wl in zip(ss, wls):
+        s.set_conservative(wl.fields)
+    tiles = [((wl.grid.nx + 31) // 32) * ((wl.grid.nz + 7) // 8) for wl in wls]
+    w = np.ones(len(wls))
+    w[2] = 1e6                      # one 400 x 400 member takes (almost) everything
+    E = gea.Ensemble(ss, weights=w)
+    nb = E.blocks()
+    assert all(b >= 1 for b in nb) and all(b <= t for b, t in zip(nb, tiles))
+    assert nb[2] == max(nb) and nb[2] > 10 * max(nb[:2])
+    E.close()
+    E, rep = ensemble.autotune(ss, stream=torch.cuda.current_stream(), betas=(0.0, 1.0), trial_steps=1)
+    assert set(rep["ms_per_step_by_beta"]) == {"0.0", "1.0"}
+    E.step(1)
+    steps = ss[0].stats()["steps_done"]
+    assert steps == 1 + 2 + 1 and all(s.stats()["status"] == 0 for s in ss)
