@@ -172,14 +172,19 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+# the sources of the FP64 step kernels whose DRAM traffic profiles/traffic.json
+# records (the per-phase kernels and the persistent step kernel)
+STEP_SOURCES = ("gea_internal.cuh", "gea_tiles.cuh", "gea_kernels.cu", "gea_persistent.cu")
+
+
 def kernels_sha256():
-    """Hash of the CUDA sources (any change invalidates recorded counters)."""
+    """Hash of the step kernels' CUDA sources (any change invalidates the
+    recorded counters)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2303_10499_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(f.encode())
-            h.update(open(os.path.join(d, f), "rb").read())
+    for f in STEP_SOURCES:
+        h.update(f.encode())
+        h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()
 
 
