@@ -303,6 +303,111 @@ def les_ensemble(n_members: int = 256, seed: int = 0, sizes=(100, 200, 400),
     return out
 
 
+# ---------------------------------------------------------------------------
+# Three dimensions: x, y horizontal, z up; fields are nz x ny x nx arrays
+# (cell (i, j, k) at [k, j, i]).
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Grid3:
+    nx: int
+    ny: int
+    nz: int
+    lx: float
+    ly: float
+    lz: float
+
+    @property
+    def dx(self) -> float:
+        return self.lx / self.nx
+
+    @property
+    def dy(self) -> float:
+        return self.ly / self.ny
+
+    @property
+    def dz(self) -> float:
+        return self.lz / self.nz
+
+    @property
+    def cells(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    def column(self) -> Grid:
+        """The x-z grid with this grid's vertical levels."""
+        return Grid(self.nx, self.nz, self.lx, self.lz)
+
+
+def conservative3(grid: Grid3, const: Constants, rho, u, v, w, T):
+    """(rho, rho u, rho v, rho w, rho e), e = cv T + |u|^2/2 + g z."""
+    z = ((np.arange(grid.nz) + 0.5) * grid.dz)[:, None, None]
+    e = const.cv * T + 0.5 * (u * u + v * v + w * w) + const.g * z
+    c = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+    return {"rho": c(rho), "rhou": c(rho * u), "rhov": c(rho * v), "rhow": c(rho * w), "rhoe": c(rho * e)}
+
+
+def rising_bubble3(grid: Grid3, const: Constants, theta0: float = 300.0, amp: float = 2.0,
+                   rc: float = 2000.0, xc: float = 5000.0, yc: float = 5000.0, zc: float = 2000.0,
+                   name: str = "bubble3d", steps: int = 200) -> Workload:
+    """Spherical cosine bubble at rest in the balanced background (the
+    smooth bubble of Section 4.1 in three dimensions)."""
+    Tb, rb, pb, thb = hydrostatic_background(grid.column(), const, theta0)
+    x = (np.arange(grid.nx) + 0.5) * grid.dx
+    y = (np.arange(grid.ny) + 0.5) * grid.dy
+    z = (np.arange(grid.nz) + 0.5) * grid.dz
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    r = np.sqrt((X - xc) ** 2 + (Y - yc) ** 2 + (Z - zc) ** 2)
+    thp = np.where(r <= rc, 0.5 * amp * (1.0 + np.cos(np.pi * r / rc)), 0.0)
+    T = Tb[:, None, None] * (theta0 + thp) / theta0
+    rho = pb[:, None, None] / (const.R * T)
+    zero = np.zeros_like(T)
+    return Workload(name, grid, const, conservative3(grid, const, rho, zero, zero, zero, T), thb.copy(), steps)
+
+
+def random_flow3(grid: Grid3, const: Constants, seed: int = 0, theta0: float = 300.0,
+                 uamp: float = 1.0, thamp: float = 1.0) -> Workload:
+    """A smooth seeded velocity field, zero in the wall-normal direction at
+    every wall, and a temperature perturbation, in the balanced background."""
+    rng = np.random.default_rng(seed)
+    Tb, rb, pb, thb = hydrostatic_background(grid.column(), const, theta0)
+    x = (np.arange(grid.nx) + 0.5) / grid.nx
+    y = (np.arange(grid.ny) + 0.5) / grid.ny
+    z = (np.arange(grid.nz) + 0.5) / grid.nz
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    u, v, w, th = (np.zeros_like(X) for _ in range(4))
+    for _ in range(3):
+        l, m, n = rng.integers(1, 4, size=3)
+        a, b, c, d = rng.uniform(-1, 1, size=4)
+        u += a * np.sin(l * np.pi * X) * np.cos(m * np.pi * Y) * np.cos(n * np.pi * Z)
+        v += b * np.cos(l * np.pi * X) * np.sin(m * np.pi * Y) * np.cos(n * np.pi * Z)
+        w += c * np.cos(l * np.pi * X) * np.cos(m * np.pi * Y) * np.sin(n * np.pi * Z)
+        th += d * np.cos(l * np.pi * X) * np.cos(m * np.pi * Y) * np.cos(n * np.pi * Z)
+    T = Tb[:, None, None] * (theta0 + thamp * th) / theta0
+    rho = pb[:, None, None] / (const.R * T)
+    return Workload("random_flow3", grid, const,
+                    conservative3(grid, const, rho, uamp * u, uamp * v, uamp * w, T), thb.copy(), 10)
+
+
+def extrude3(wl: Workload, ny: int, ly: float) -> Workload:
+    """A two-dimensional x-z workload repeated along y (v = 0): its
+    three-dimensional evolution stays y-invariant and equals the x-z one."""
+    g = wl.grid
+    grid = Grid3(g.nx, ny, g.nz, g.lx, ly, g.lz)
+    f = wl.fields
+    rep = lambda a: np.ascontiguousarray(np.repeat(a[:, None, :], ny, axis=1))
+    fields = {"rho": rep(f["rho"]), "rhou": rep(f["rhou"]), "rhov": np.zeros((g.nz, ny, g.nx)),
+              "rhow": rep(f["rhow"]), "rhoe": rep(f["rhoe"])}
+    return Workload(wl.name + f"_y{ny}", grid, wl.const, fields, wl.theta_bar, wl.steps)
+
+
+def bubble3d(nx: int, ny: int, nz: int, dt: float = 0.05, steps: int = 200) -> Workload:
+    """The 3D rising thermal bubble: 10 km x 10 km x 10 km, theta0 = 300 K,
+    spherical cosine bubble of 2 K, radius 2 km, centred (5, 5, 2) km, at
+    rest, mu = 0.15."""
+    return rising_bubble3(Grid3(nx, ny, nz, 10000.0, 10000.0, 10000.0), Constants(dt=dt), 300.0, 2.0,
+                          2000.0, 5000.0, 5000.0, 2000.0, name=f"bubble3d_{nx}x{ny}x{nz}", steps=steps)
+
+
 WORKLOADS = {
     # 160 x 80 cells (125 m), dt = 0.1 s, 100 steps: the small parity case
     "bubble160x80": lambda: smooth_bubble_20km(160, 80, 0.1, 100),
@@ -314,6 +419,9 @@ WORKLOADS = {
     "les100": lambda: les_member(100),
     "les200": lambda: les_member(200),
     "les400": lambda: les_member(400),
+    # three dimensions
+    "bubble3d_64x64x32": lambda: bubble3d(64, 64, 32, 0.05, 20),
+    "bubble3d_512x512x256": lambda: bubble3d(512, 512, 256, 0.05, 200),
 }
 
 
