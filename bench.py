@@ -94,6 +94,9 @@ def parse():
                     help="the batched LES configuration: this many non-smooth bubbles (grids 100^2, 200^2, "
                          "400^2, Smagorinsky cs = 0.17) advanced by one launch per step, against the same "
                          "members stepped one after another")
+    ap.add_argument("--three-d", default=None, metavar="WORKLOAD",
+                    help="the three-dimensional step on a 3D workload (bubble3d_512x512x256: the "
+                         "10 km cube bubble, 67M cells)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle baseline sample")
     return ap.parse_args()
@@ -466,6 +469,114 @@ def run_ensemble(args):
         print(json.dumps(res), flush=True)
 
 
+# Per-cell model of the three-dimensional kernels (same conventions as
+# KERNEL_MODEL; coarsening and restriction per coarse cell).
+KERNEL_MODEL_3D = {
+    "g3_pred": (30, 101, "f64"),
+    "g3_mom": (23, 93, "f64"),
+    "g3_enth_rhs": (16, 141, "f64"),
+    "g3_enth": (17, 31, "f64"),
+    "g3_eos": (9, 7, "f64"),
+    "g3_faces": (8, 15, "f64"),
+    "g3_diag": (6, 7, "f64"),
+    "g3_coarsen": (38, 32, "f64"),
+    "g3_H": (24, 87, "f64"),
+    "g3_helm_rhs": (18, 70, "f64"),
+    "g3_mg_down": (49, 137, "f64"),
+    "g3_mg_coarse": (7, 17, "f64"),
+    "g3_mg_up": (7.125, 20, "f64"),
+    "g3_mg_single": (6, 20, "f64"),
+    "g3_pspmv": (8, 17, "f64"),
+    "g3_update": (6, 6, "f64"),
+    "g3_correct": (20, 89, "f64"),
+}
+
+
+def run_3d(args):
+    """The three-dimensional step (include/gea3d.h) on a 3D workload, timed
+    like the main line; roofline of its dominant kernel from one eager
+    step; end to end through the C ABI with pinned host buffers."""
+    import torch
+    from paper_2303_10499_gb300 import build as B
+    from paper_2303_10499_gb300 import gea
+    from paper_2303_10499_gb300 import workloads as W
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    B.build()
+    wl = W.get(args.three_d)
+    g = wl.grid
+    cells = g.cells
+    stream = torch.cuda.current_stream()
+    s = gea.Solver3D(g, wl.const, stream=stream)
+    dev = {k: torch.from_numpy(v).cuda() for k, v in wl.fields.items()}
+    s.set_conservative(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    ms, launches, clocks = timed_steps(s, stream, flush, args.steps, args.warmup, world, local)
+    st = s.stats()
+    value = world * cells * args.steps / (sum(ms) / 1e3)
+    prof = s.profile_step()
+    KERNEL_MODEL.update(KERNEL_MODEL_3D)
+    roof = roofline(prof, peaks(), statistics.mean(ms), False, wl.name)
+
+    host = s.get_state()
+    pin_in = {k: torch.from_numpy(v).pin_memory().numpy() for k, v in wl.fields.items()}
+    out = {k: torch.empty(v.shape, dtype=torch.float64).pin_memory().numpy() for k, v in host.items()}
+    bi = sum(v.nbytes for v in pin_in.values())
+    bo = sum(v.nbytes for v in out.values())
+    ne = max(3, min(args.steps, 10))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ne):
+        s.set_conservative(pin_in)
+        s.step(1)
+        s.get_state(out)
+    t_e2e = time.perf_counter() - t0
+    e2e = {"value": world * cells * ne / t_e2e, "unit": UNIT, "h2d_bytes_per_step": bi,
+           "d2h_bytes_per_step": bo,
+           "path": "gea3d_set_conservative(host) + gea3d_step(1) + gea3d_get_state(host)"}
+    s.close()
+    res = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": statistics.mean(ms), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "grid": [g.nx, g.ny, g.nz], "cells": cells,
+                   "domain_m": [g.lx, g.ly, g.lz], "dt": wl.const.dt, "n_corr": wl.const.n_corr,
+                   "jac_rtol": wl.const.jac_rtol, "cg_rtol": wl.const.cg_rtol,
+                   "mg_levels": st["mg_levels"],
+                   "l2": "inputs larger than L2 (each field 0.5 GB) and 256 MB flush between steps",
+                   "driver": "graph", "parallelism": f"replicas x{world}"},
+        "cg_iters_last_step": st["cg_iters"], "jacobi_sweeps_last_step": [st["jac_u"], st["jac_h"]],
+        "ms_per_step_min": min(ms), "ms_per_step_median": statistics.median(ms),
+        "gpu_launches": int(launches) * world, "clocks": clocks, "e2e": e2e, "roofline": roof,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline3(args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+
+
+def cpu_baseline3(seconds):
+    """The FP64 3D CPU oracle as it stands, single-threaded, on a bounded
+    sample: the same bubble on a 64x64x32 grid, consecutive steps from t = 0
+    (per cell-step the work is that of the full grid's step up to the
+    solvers' iteration counts)."""
+    from paper_2303_10499_gb300 import workloads as W
+    from oracle import oracle3d
+    wl = W.get("bubble3d_64x64x32")
+    q = oracle3d.Oracle3D(wl.grid, wl.const)
+    st = q.derive(wl.fields)
+    t0 = time.perf_counter()
+    q.step(st, 1)
+    t1 = time.perf_counter() - t0
+    n = max(1, min(200, int(seconds / max(t1, 1e-6)) - 1))
+    t0 = time.perf_counter()
+    q.step(st, n)
+    dt = time.perf_counter() - t0
+    return {"value": wl.grid.cells * n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"steps 2..{n + 1} of {wl.name} from t=0 ({n} steps, {dt:.1f} s)"}
+
+
 def run_ours(args):
     import torch
     from paper_2303_10499_gb300 import build as B
@@ -630,6 +741,8 @@ def main():
         run_learned(args)
     elif args.ensemble:
         run_ensemble(args)
+    elif args.three_d:
+        run_3d(args)
     else:
         run_ours(args)
 

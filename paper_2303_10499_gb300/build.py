@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgea.so")
 SOURCES = ["gea_kernels.cu", "gea_persistent.cu", "gea_mixed.cu", "gea_capi.cu", "gea_noalloc.cu",
-           "gea_conv.cu", "gea_net.cu"]
+           "gea_conv.cu", "gea_net.cu", "gea3d.cu"]
 HEADERS = ["gea_internal.cuh", "gea_tiles.cuh"]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -26,7 +26,7 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [os.path.join(ROOT, "include", "gea.h")]
+    deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [os.path.join(ROOT, "include", h) for h in ("gea.h", "gea_net.h", "gea3d.h")]
     return any(os.path.getmtime(d) > t for d in deps)
 
 

@@ -1,0 +1,1389 @@
+// gea3d.cu -- the time step of the GEA pressure-based Euler solver
+// (Girfoglio, Quaini & Rozza, arXiv 2303.10499, Section 3) on a uniform
+// Cartesian x-y-z grid, FP64, and the C ABI of include/gea3d.h.
+//
+// One thread per cell on 32 x 8 x 1 blocks (grid z = the cell layer);
+// neighbour values are read through the read-only cache with the one-layer
+// wall ghosts applied on the fly (wall-normal velocity odd, tangential and
+// scalars even, h with dh/dz = -g). The transport operator
+// T(X) = (rho1/dt) X + C(X) - nu L(X) (fourth-order face values, 13-point
+// cross stencil) is evaluated from the face fluxes in every sweep. The
+// pressure equation is solved by CG preconditioned with a Galerkin V(1,1)
+// cycle (piecewise-constant transfer over 2 x 2 x 2 cells, damped Jacobi
+// smoothing), the loops as conditional WHILE nodes of a CUDA graph ended by
+// a one-thread control kernel. Reductions are deterministic (block partials
+// summed in a fixed order by the last block).
+//
+// Layout: every array (cells and faces) is indexed (k (ny+1) + j) P + i with
+// P = nx + 1 rounded up to 32: x-face i lies between cells i-1 and i,
+// y-face j between rows j-1 and j, z-face k between layers k-1 and k.
+#include "gea_internal.cuh"
+#include "../../include/gea3d.h"
+
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+namespace g3 {
+
+constexpr int TX = 32, TY = 8, NT = TX * TY;
+static_assert(NT == gea::NTHREADS, "block_sum reduces NTHREADS values");
+constexpr int kMaxLev = 12;
+constexpr int kCoarseSweeps = 2;
+constexpr double kOmega = 0.8;
+constexpr double kCoarsestRatio = 1.0;
+constexpr double kRefT = 300.0;
+enum { E3 = 0, U3 = 1, V3 = 2, W3 = 3, H3 = 4 };
+enum { L_MOM = 0, L_ENTH = 1, L_CG = 2 };
+enum { C_PRED = 0, C_MOM, C_ERHS, C_ENTH, C_HELM, C_RZ, C_PQ, C_UPD, C_DER };
+
+struct Geo {
+    int nx, ny, nz, P;
+    double dx, dy, dz;
+    double idx, idy, idz, idx2, idy2, idz2, ivol;   // 1/dx, ..., 1/dx^2, ..., 1/(dx dy dz)
+};
+
+__host__ __device__ inline long long id3(const Geo &G, int i, int j, int k)
+{
+    return ((long long)k * (G.ny + 1) + j) * G.P + i;
+}
+
+struct Phy {
+    double R, cp, g, mu, nuh, dt, idt, omega;
+};
+
+struct St {
+    double *rho, *u, *v, *w, *T, *h, *p, *pp, *pold, *phix, *phiy, *phiz;
+};
+
+// Helmholtz level: (A x)_i = c_i x_i + sum_f a_f (x_i - x_N), d = c + sum a,
+// a on the x-, y- and z-faces (zero on walls).
+struct Lev {
+    Geo G;
+    double *c, *d, *ax, *ay, *az, *r, *e, *e2;
+    double *w;   // omega / d (damped Jacobi weight)
+};
+
+// The transport operator T(X) = (rho1/dt) X + C(X) - mu L(X) of the step as
+// a 13-point stencil (slot 0 the cell, then x-2, x-1, x+1, x+2, y-2, ...,
+// z+2), the fourth-order face interpolation and the Laplacian folded into
+// the weights; set once per step from the fluxes phi^n and rho1.
+constexpr int NCF = 13;
+struct Cf {
+    double *c[NCF];
+};
+
+struct Sc {
+    double bn2[4];
+    double b2, r2, rz, pq, alpha, beta;
+    int done[3], trips[3], sweeps[2], cg_it, corr, cg_iters[4];
+    double cg_relres[4];
+    int status, bad_cells;
+    long long steps_done;
+    int last_sweeps[2], last_cg_iters[4];
+    double last_cg_relres[4];
+    int last_status;
+    long long launches;
+    unsigned counters[16];
+};
+
+struct Args {
+    Geo G;
+    Phy F;
+    St S, N;
+    double *rho1, *dinvu, *dinvh, *bu, *bv, *bw, *ua, *va, *wa, *ub, *vb, *wb, *bh, *ha, *hb;
+    double *rho2, *psi, *Dx, *Dy, *Dz, *Hx, *Hy, *Hz, *b, *p0, *p1, *q;
+    Cf cf;
+    Sc *sc;
+    double *part;
+    double jtol2, ctol2;
+};
+
+__device__ __forceinline__ double ld(const double *p) { return __ldg(p); }
+
+// Cell (i,j,k) of the thread, or false beyond the box.
+__device__ __forceinline__ bool cell(const Geo &G, int &i, int &j, int &k)
+{
+    i = blockIdx.x * TX + threadIdx.x;
+    j = blockIdx.y * TY + threadIdx.y;
+    k = blockIdx.z;
+    return i < G.nx && j < G.ny && k < G.nz;
+}
+
+// X at (i,j,k) with at most one index one layer outside the box: the ghost
+// of wall rule BC.
+template <int BC>
+__device__ __forceinline__ double at(const Geo &G, const Phy &F, const double *X, int i, int j, int k)
+{
+    if (i < 0) { const double v = ld(&X[id3(G, 0, j, k)]); return BC == U3 ? -v : v; }
+    if (i >= G.nx) { const double v = ld(&X[id3(G, G.nx - 1, j, k)]); return BC == U3 ? -v : v; }
+    if (j < 0) { const double v = ld(&X[id3(G, i, 0, k)]); return BC == V3 ? -v : v; }
+    if (j >= G.ny) { const double v = ld(&X[id3(G, i, G.ny - 1, k)]); return BC == V3 ? -v : v; }
+    if (k < 0) {
+        const double v = ld(&X[id3(G, i, j, 0)]);
+        return BC == W3 ? -v : (BC == H3 ? v + F.g * G.dz : v);
+    }
+    if (k >= G.nz) {
+        const double v = ld(&X[id3(G, i, j, G.nz - 1)]);
+        return BC == W3 ? -v : (BC == H3 ? v - F.g * G.dz : v);
+    }
+    return ld(&X[id3(G, i, j, k)]);
+}
+
+__device__ __forceinline__ double i4(double xm, double xa, double xb, double xp)
+{
+    return (-xm + 7.0 * xa + 7.0 * xb - xp) * (1.0 / 12.0);
+}
+
+// Compact 7-point Laplacian through the ghosts.
+template <int BC>
+__device__ double lap(const Args &a, const double *X, int i, int j, int k)
+{
+    const Geo &G = a.G;
+    const Phy &F = a.F;
+    const double xc = at<BC>(G, F, X, i, j, k);
+    return (at<BC>(G, F, X, i + 1, j, k) - xc + at<BC>(G, F, X, i - 1, j, k) - xc) * G.idx2 +
+           (at<BC>(G, F, X, i, j + 1, k) - xc + at<BC>(G, F, X, i, j - 1, k) - xc) * G.idy2 +
+           (at<BC>(G, F, X, i, j, k + 1) - xc + at<BC>(G, F, X, i, j, k - 1) - xc) * G.idz2;
+}
+
+__device__ double divg(const Args &a, int i, int j, int k)
+{
+    const Geo &G = a.G;
+    return (ld(&a.S.phix[id3(G, i + 1, j, k)]) - ld(&a.S.phix[id3(G, i, j, k)]) +
+            ld(&a.S.phiy[id3(G, i, j + 1, k)]) - ld(&a.S.phiy[id3(G, i, j, k)]) +
+            ld(&a.S.phiz[id3(G, i, j, k + 1)]) - ld(&a.S.phiz[id3(G, i, j, k)])) *
+           G.ivol;
+}
+
+// Deterministic grid sum of NV values per thread (3D grid of 32 x 8 blocks):
+// true in thread 0 of the last block, with the totals in tot.
+template <int NV>
+__device__ bool gsum(const double (&v)[NV], double *red, double *part, unsigned *counter, double (&tot)[NV])
+{
+    __shared__ int last;
+    const int tid = threadIdx.x + threadIdx.y * TX;
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const int nb = gridDim.x * gridDim.y * gridDim.z;
+    double bt[NV];
+    gea::block_sum<NV>(v, red, bt);
+    if (tid == 0) {
+#pragma unroll
+        for (int m = 0; m < NV; ++m) part[(size_t)m * nb + bid] = bt[m];
+        __threadfence();
+        last = atomicAdd(counter, 1u) == (unsigned)nb - 1u;
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double s[NV];
+#pragma unroll
+    for (int m = 0; m < NV; ++m) {
+        s[m] = 0.0;
+        for (int bb = tid; bb < nb; bb += NT) s[m] += __ldcg(&part[(size_t)m * nb + bb]);
+    }
+    gea::block_sum<NV>(s, red, tot);
+    if (tid == 0) *counter = 0u;
+    return tid == 0;
+}
+
+__device__ __forceinline__ bool over(const Sc *sc, int which) { return sc->status || sc->done[which]; }
+
+}  // namespace g3
+
+namespace g3 {
+
+// ---- set-up from conservative fields (dense nz x ny x nx arrays) ----
+
+__global__ void k_derive(Geo G, Phy F, const double *rho, const double *ru, const double *rv,
+                         const double *rw, const double *re, St S, Sc *sc)
+{
+    int i, j, k;
+    if (!cell(G, i, j, k)) return;
+    const long long n = ((long long)k * G.ny + j) * G.nx + i, q = id3(G, i, j, k);
+    const double z = (k + 0.5) * G.dz, cv = F.cp - F.R;
+    const double r = rho[n], u = ru[n] / r, v = rv[n] / r, w = rw[n] / r;
+    const double T = (re[n] / r - 0.5 * (u * u + v * v + w * w) - F.g * z) / cv;
+    if (!(r > 0.0) || !(T > 0.0)) atomicAdd(&sc->bad_cells, 1);
+    S.rho[q] = r; S.u[q] = u; S.v[q] = v; S.w[q] = w; S.T[q] = T; S.h[q] = F.cp * T;
+    const double p = r * F.R * T;
+    S.p[q] = p; S.pp[q] = p + r * F.g * z; S.pold[q] = p;
+    const long long sx = 1, sy = G.nx, sz = (long long)G.nx * G.ny;
+    S.phix[q] = i > 0 ? 0.5 * (ru[n - sx] + ru[n]) * G.dy * G.dz : 0.0;
+    S.phiy[q] = j > 0 ? 0.5 * (rv[n - sy] + rv[n]) * G.dx * G.dz : 0.0;
+    S.phiz[q] = k > 0 ? 0.5 * (rw[n - sz] + rw[n]) * G.dx * G.dy : 0.0;
+    if (i == G.nx - 1) S.phix[id3(G, G.nx, j, k)] = 0.0;
+    if (j == G.ny - 1) S.phiy[id3(G, i, G.ny, k)] = 0.0;
+    if (k == G.nz - 1) S.phiz[id3(G, i, j, G.nz)] = 0.0;
+}
+
+// Face force G_f = (p'_b - p'_a)/Delta - g z_f (rho_b - rho_a)/Delta of the
+// face between cell q - s (a) and q (b) in direction d; zero on walls.
+__device__ __forceinline__ double fforce(const double *pp, const double *rho, long long q, long long s,
+                                         double inv, double gz)
+{
+    return (ld(&pp[q]) - ld(&pp[q - s])) * inv - gz * (ld(&rho[q]) - ld(&rho[q - s])) * inv;
+}
+
+// Cell averages of the face forces in x, y, z of cell (i,j,k).
+__device__ void cell_forces(const Geo &G, const Phy &F, const double *pp, const double *rho, int i, int j,
+                            int k, double &gx, double &gy, double &gz)
+{
+    const long long q = id3(G, i, j, k), sx = 1, sy = G.P, sz = (long long)G.P * (G.ny + 1);
+    const double zc = (k + 0.5) * G.dz, idx = G.idx, idy = G.idy, idz = G.idz;
+    const double fw = i > 0 ? fforce(pp, rho, q, sx, idx, F.g * zc) : 0.0;
+    const double fe = i + 1 < G.nx ? fforce(pp, rho, q + sx, sx, idx, F.g * zc) : 0.0;
+    const double fs = j > 0 ? fforce(pp, rho, q, sy, idy, F.g * zc) : 0.0;
+    const double fn = j + 1 < G.ny ? fforce(pp, rho, q + sy, sy, idy, F.g * zc) : 0.0;
+    const double fb = k > 0 ? fforce(pp, rho, q, sz, idz, F.g * (k * G.dz)) : 0.0;
+    const double ft = k + 1 < G.nz ? fforce(pp, rho, q + sz, sz, idz, F.g * ((k + 1) * G.dz)) : 0.0;
+    gx = 0.5 * (fw + fe);
+    gy = 0.5 * (fs + fn);
+    gz = 0.5 * (fb + ft);
+}
+
+__device__ __forceinline__ void fin_pred(Sc *sc, const double (&t)[3])
+{
+    for (int m = 0; m < 3; ++m) sc->bn2[m] = t[m];
+    sc->done[L_MOM] = 0;
+    sc->trips[L_MOM] = 0;
+    sc->sweeps[0] = 0;
+}
+
+// ---- Step 1 (eq. e1_d, eq. step2_sd first line) ----
+
+// rho1, the Jacobi reciprocals, b = rho^n u^n / dt - G_cell, initial guesses
+// u^n; acc += |b|^2 per component.
+__global__ void k_pred(Args a)
+{
+    if (a.sc->status) return;
+    __shared__ double red[3 * NT];
+    double acc[3] = {0.0, 0.0, 0.0}, tot[3];
+    int i, j, k;
+    if (cell(a.G, i, j, k)) {
+        const Geo &G = a.G;
+        const Phy &F = a.F;
+        const long long q = id3(G, i, j, k), sy = G.P, sz = (long long)G.P * (G.ny + 1);
+        const double dv = divg(a, i, j, k), r = ld(&a.S.rho[q]);
+        const double rho1 = r - F.dt * dv;
+        a.rho1[q] = rho1;
+        const double lsum = 2.0 * (G.idx2 + G.idy2 + G.idz2);
+        const double cu = rho1 * F.idt + (7.0 / 12.0) * dv + F.mu * lsum;
+        a.dinvu[q] = 1.0 / cu;
+        a.dinvh[q] = 1.0 / (rho1 * F.idt + (7.0 / 12.0) * dv + F.nuh * lsum);
+        // T as a stencil: the outgoing flux of a face times its fourth-order
+        // value (-X_m + 7 X_a + 7 X_b - X_p)/12, minus mu times the Laplacian
+        const double i12 = G.ivol * (1.0 / 12.0);
+        const double pw = ld(&a.S.phix[q]), pe = ld(&a.S.phix[q + 1]);
+        const double ps = ld(&a.S.phiy[q]), pn = ld(&a.S.phiy[q + sy]);
+        const double pb = ld(&a.S.phiz[q]), pt = ld(&a.S.phiz[q + sz]);
+        const double mx = F.mu * G.idx2, my = F.mu * G.idy2, mz = F.mu * G.idz2;
+        const Cf &cf = a.cf;
+        cf.c[0][q] = cu;
+        cf.c[1][q] = pw * i12;
+        cf.c[2][q] = -(pe + 7.0 * pw) * i12 - mx;
+        cf.c[3][q] = (7.0 * pe + pw) * i12 - mx;
+        cf.c[4][q] = -pe * i12;
+        cf.c[5][q] = ps * i12;
+        cf.c[6][q] = -(pn + 7.0 * ps) * i12 - my;
+        cf.c[7][q] = (7.0 * pn + ps) * i12 - my;
+        cf.c[8][q] = -pn * i12;
+        cf.c[9][q] = pb * i12;
+        cf.c[10][q] = -(pt + 7.0 * pb) * i12 - mz;
+        cf.c[11][q] = (7.0 * pt + pb) * i12 - mz;
+        cf.c[12][q] = -pt * i12;
+        double gx, gy, gz;
+        cell_forces(G, F, a.S.pp, a.S.rho, i, j, k, gx, gy, gz);
+        const double u = ld(&a.S.u[q]), v = ld(&a.S.v[q]), w = ld(&a.S.w[q]);
+        const double bu = r * u * F.idt - gx, bv = r * v * F.idt - gy, bw = r * w * F.idt - gz;
+        a.bu[q] = bu; a.bv[q] = bv; a.bw[q] = bw;
+        a.ua[q] = u; a.va[q] = v; a.wa[q] = w;
+        acc[0] = bu * bu; acc[1] = bv * bv; acc[2] = bw * bw;
+    }
+    if (gsum<3>(acc, red, a.part, &a.sc->counters[C_PRED], tot)) fin_pred(a.sc, tot);
+}
+
+// The 13 stencil weights of a cell.
+struct W13 {
+    double w[NCF];
+};
+
+__device__ __forceinline__ W13 weights(const Args &a, long long q)
+{
+    W13 c;
+#pragma unroll
+    for (int m = 0; m < NCF; ++m) c.w[m] = ld(&a.cf.c[m][q]);
+    return c;
+}
+
+// Off-centre part of T(X): sum over the 12 neighbour slots of weight times
+// value (ghosts by rule BC; slots two cells beyond a wall carry weight 0).
+template <int BC>
+__device__ __forceinline__ double toff(const Args &a, const W13 &c, const double *X, int i, int j, int k)
+{
+    const Geo &G = a.G;
+    const Phy &F = a.F;
+    double t = c.w[1] * at<BC>(G, F, X, i - 2, j, k);
+    t = fma(c.w[2], at<BC>(G, F, X, i - 1, j, k), t);
+    t = fma(c.w[3], at<BC>(G, F, X, i + 1, j, k), t);
+    t = fma(c.w[4], at<BC>(G, F, X, i + 2, j, k), t);
+    t = fma(c.w[5], at<BC>(G, F, X, i, j - 2, k), t);
+    t = fma(c.w[6], at<BC>(G, F, X, i, j - 1, k), t);
+    t = fma(c.w[7], at<BC>(G, F, X, i, j + 1, k), t);
+    t = fma(c.w[8], at<BC>(G, F, X, i, j + 2, k), t);
+    t = fma(c.w[9], at<BC>(G, F, X, i, j, k - 2), t);
+    t = fma(c.w[10], at<BC>(G, F, X, i, j, k - 1), t);
+    t = fma(c.w[11], at<BC>(G, F, X, i, j, k + 1), t);
+    t = fma(c.w[12], at<BC>(G, F, X, i, j, k + 2), t);
+    return t;
+}
+
+__device__ __forceinline__ void copy_cell(const Geo &G, const double *x, double *y)
+{
+    int i, j, k;
+    if (cell(G, i, j, k)) y[id3(G, i, j, k)] = ld(&x[id3(G, i, j, k)]);
+}
+
+// One Jacobi sweep of the three momentum components (pairs of sweeps; the
+// second of a pair copies once the first met the tolerance).
+__global__ void k_mom(Args a, const double *ui, const double *vi, const double *wi, double *uo, double *vo,
+                      double *wo, int second)
+{
+    Sc *sc = a.sc;
+    if (sc->status) return;
+    if (second && sc->done[L_MOM]) {
+        copy_cell(a.G, ui, uo);
+        copy_cell(a.G, vi, vo);
+        copy_cell(a.G, wi, wo);
+        return;
+    }
+    __shared__ double red[3 * NT];
+    double acc[3] = {0.0, 0.0, 0.0}, tot[3];
+    int i, j, k;
+    if (cell(a.G, i, j, k)) {
+        const long long q = id3(a.G, i, j, k);
+        const double di = ld(&a.dinvu[q]);
+        const W13 c = weights(a, q);
+        // one component after the other (the empty asm keeps the compiler
+        // from interleaving their loads, which would cost registers)
+        const double u0 = ld(&ui[q]);
+        const double ru = ld(&a.bu[q]) - fma(c.w[0], u0, toff<U3>(a, c, ui, i, j, k));
+        uo[q] = fma(ru, di, u0);
+        asm volatile("" ::: "memory");
+        const double v0 = ld(&vi[q]);
+        const double rv = ld(&a.bv[q]) - fma(c.w[0], v0, toff<V3>(a, c, vi, i, j, k));
+        vo[q] = fma(rv, di, v0);
+        asm volatile("" ::: "memory");
+        const double w0 = ld(&wi[q]);
+        const double rw = ld(&a.bw[q]) - fma(c.w[0], w0, toff<W3>(a, c, wi, i, j, k));
+        wo[q] = fma(rw, di, w0);
+        acc[0] = ru * ru; acc[1] = rv * rv; acc[2] = rw * rw;
+    }
+    if (gsum<3>(acc, red, a.part, &sc->counters[C_MOM], tot)) {
+        sc->sweeps[0] += 1;
+        if (!isfinite(tot[0]) || !isfinite(tot[1]) || !isfinite(tot[2])) sc->status = GEA_ERR_NONFINITE;
+        else if (tot[0] <= a.jtol2 * sc->bn2[0] && tot[1] <= a.jtol2 * sc->bn2[1] && tot[2] <= a.jtol2 * sc->bn2[2])
+            sc->done[L_MOM] = 1;
+    }
+}
+
+// ---- Step 2 (eq. step3_sd) ----
+
+template <int BC>
+__device__ __forceinline__ double sq_at(const Args &a, const double *X, int i, int j, int k)
+{
+    const double v = at<BC>(a.G, a.F, X, i, j, k);
+    return v * v;
+}
+
+// K1 = |u1|^2/2 at a cell or ghost (the ghost's K is the mirrored cell's).
+__device__ __forceinline__ double K1at(const Args &a, const double *u, const double *v, const double *w, int i,
+                                      int j, int k)
+{
+    return 0.5 * (sq_at<U3>(a, u, i, j, k) + sq_at<V3>(a, v, i, j, k) + sq_at<W3>(a, w, i, j, k));
+}
+
+// Right-hand side of the enthalpy equation and its initial guess h^n:
+// (rho h + rho K - p^{n-1})/dt - rho1 K1/dt - C(K1) + p^n/dt - rho1 g w1.
+__global__ void k_enth_rhs(Args a, const double *u1, const double *v1, const double *w1)
+{
+    if (a.sc->status) return;
+    __shared__ double red[NT];
+    double acc[1] = {0.0}, tot[1];
+    int i, j, k;
+    if (cell(a.G, i, j, k)) {
+        const Geo &G = a.G;
+        const Phy &F = a.F;
+        const long long q = id3(G, i, j, k);
+        // C(K1) with K1 evaluated at the stencil points
+        double s = 0.0;
+        const double Kc = K1at(a, u1, v1, w1, i, j, k);
+        auto K = [&](int ii, int jj, int kk) { return K1at(a, u1, v1, w1, ii, jj, kk); };
+        if (i + 1 < G.nx) s += ld(&a.S.phix[id3(G, i + 1, j, k)]) * i4(K(i - 1, j, k), Kc, K(i + 1, j, k), K(i + 2, j, k));
+        if (i > 0) s -= ld(&a.S.phix[id3(G, i, j, k)]) * i4(K(i - 2, j, k), K(i - 1, j, k), Kc, K(i + 1, j, k));
+        if (j + 1 < G.ny) s += ld(&a.S.phiy[id3(G, i, j + 1, k)]) * i4(K(i, j - 1, k), Kc, K(i, j + 1, k), K(i, j + 2, k));
+        if (j > 0) s -= ld(&a.S.phiy[id3(G, i, j, k)]) * i4(K(i, j - 2, k), K(i, j - 1, k), Kc, K(i, j + 1, k));
+        if (k + 1 < G.nz) s += ld(&a.S.phiz[id3(G, i, j, k + 1)]) * i4(K(i, j, k - 1), Kc, K(i, j, k + 1), K(i, j, k + 2));
+        if (k > 0) s -= ld(&a.S.phiz[id3(G, i, j, k)]) * i4(K(i, j, k - 2), K(i, j, k - 1), Kc, K(i, j, k + 1));
+        s *= G.ivol;
+        const double r = ld(&a.S.rho[q]), u = ld(&a.S.u[q]), v = ld(&a.S.v[q]), w = ld(&a.S.w[q]);
+        const double h = ld(&a.S.h[q]), rho1 = ld(&a.rho1[q]);
+        const double Kn = 0.5 * (u * u + v * v + w * w);
+        const double be = (r * h + r * Kn - ld(&a.S.pold[q])) * F.idt;
+        const double bh = be - rho1 * Kc * F.idt - s + ld(&a.S.p[q]) * F.idt - rho1 * F.g * ld(&w1[q]);
+        a.bh[q] = bh;
+        a.ha[q] = h;
+        acc[0] = bh * bh;
+    }
+    if (gsum<1>(acc, red, a.part, &a.sc->counters[C_ERHS], tot)) {
+        a.sc->bn2[3] = tot[0];
+        a.sc->done[L_ENTH] = 0;
+        a.sc->trips[L_ENTH] = 0;
+        a.sc->sweeps[1] = 0;
+    }
+}
+
+__global__ void k_enth(Args a, const double *hi, double *ho, int second)
+{
+    Sc *sc = a.sc;
+    if (sc->status) return;
+    if (second && sc->done[L_ENTH]) {
+        copy_cell(a.G, hi, ho);
+        return;
+    }
+    __shared__ double red[NT];
+    double acc[1] = {0.0}, tot[1];
+    int i, j, k;
+    if (cell(a.G, i, j, k)) {
+        const long long q = id3(a.G, i, j, k);
+        const W13 c = weights(a, q);
+        const double h0 = ld(&hi[q]);
+        // T with nu_h = mu/Pr: the mu-stencil plus (mu - nu_h) L(h)
+        double t = fma(c.w[0], h0, toff<H3>(a, c, hi, i, j, k));
+        if (a.F.nuh != a.F.mu) t = fma(a.F.mu - a.F.nuh, lap<H3>(a, hi, i, j, k), t);
+        const double r = ld(&a.bh[q]) - t;
+        ho[q] = fma(r, ld(&a.dinvh[q]), h0);
+        acc[0] = r * r;
+    }
+    if (gsum<1>(acc, red, a.part, &sc->counters[C_ENTH], tot)) {
+        sc->sweeps[1] += 1;
+        if (!isfinite(tot[0])) sc->status = GEA_ERR_NONFINITE;
+        else if (tot[0] <= a.jtol2 * sc->bn2[3]) sc->done[L_ENTH] = 1;
+    }
+}
+
+// EOS update (eqs. step3_2sd, step3_3sd): T^{n+1} = T^n + (h^{n+1} - h^n)/cp,
+// psi = 1/(R T^{n+1}), rho2 = psi p^n, and c = psi/dt of the fine level.
+__global__ void k_eos(Args a, Lev L, const double *h1)
+{
+    if (a.sc->status) return;
+    int i, j, k;
+    if (!cell(a.G, i, j, k)) return;
+    const Phy &F = a.F;
+    const long long q = id3(a.G, i, j, k);
+    const double hq = ld(&h1[q]);
+    const double T1 = ld(&a.S.T[q]) + (hq - ld(&a.S.h[q])) / F.cp;
+    const double psi = 1.0 / (F.R * T1);
+    a.N.T[q] = T1;
+    a.N.h[q] = hq;
+    a.rho2[q] = ld(&a.S.p[q]) * psi;
+    a.psi[q] = psi;
+    L.c[q] = psi * F.idt;
+}
+
+// Face coefficients of the fine level: D_f = dt rho2_f / rho1_f with face
+// means of the two cells, on the cell's west, south and bottom faces (zero
+// on walls; the last cells also zero the east, north and top wall faces),
+// and a_f = D_f / Delta^2.
+__global__ void k_faces(Args a, Lev L)
+{
+    if (a.sc->status) return;
+    int i, j, k;
+    if (!cell(a.G, i, j, k)) return;
+    const Geo &G = a.G;
+    const long long q = id3(G, i, j, k), sx = 1, sy = G.P, sz = (long long)G.P * (G.ny + 1);
+    const double r2 = ld(&a.rho2[q]), r1 = ld(&a.rho1[q]), dt = a.F.dt;
+    // the halves of the two face means cancel exactly
+    auto D = [&](long long qn) { return dt * (r2 + ld(&a.rho2[qn])) / (r1 + ld(&a.rho1[qn])); };
+    const double Dw = i > 0 ? D(q - sx) : 0.0;
+    const double Ds = j > 0 ? D(q - sy) : 0.0;
+    const double Db = k > 0 ? D(q - sz) : 0.0;
+    a.Dx[q] = Dw; a.Dy[q] = Ds; a.Dz[q] = Db;
+    L.ax[q] = Dw * G.idx2; L.ay[q] = Ds * G.idy2; L.az[q] = Db * G.idz2;
+    if (i == G.nx - 1) { a.Dx[q + sx] = 0.0; L.ax[q + sx] = 0.0; }
+    if (j == G.ny - 1) { a.Dy[q + sy] = 0.0; L.ay[q + sy] = 0.0; }
+    if (k == G.nz - 1) { a.Dz[q + sz] = 0.0; L.az[q + sz] = 0.0; }
+}
+
+// Diagonal d = c + the six face coefficients, and the Jacobi weight omega/d.
+__global__ void k_diag(Lev L, Sc *sc)
+{
+    if (sc->status) return;
+    int i, j, k;
+    if (!cell(L.G, i, j, k)) return;
+    const Geo &G = L.G;
+    const long long q = id3(G, i, j, k), sy = G.P, sz = (long long)G.P * (G.ny + 1);
+    const double d = ld(&L.c[q]) + (ld(&L.ax[q]) + ld(&L.ax[q + 1])) + (ld(&L.ay[q]) + ld(&L.ay[q + sy])) +
+                     (ld(&L.az[q]) + ld(&L.az[q + sz]));
+    L.d[q] = d;
+    L.w[q] = kOmega / d;
+}
+
+// Galerkin coarsening (restriction = mean over the 8 children, piecewise-
+// constant prolongation): c_C = mean of the children's c, a coarse face =
+// (1/8) sum of its 4 fine faces, d_C = c_C + sum of its faces. One thread
+// per coarse cell.
+__global__ void k_coarsen(Lev f, Lev c)
+{
+    int I, J, K;
+    if (!cell(c.G, I, J, K)) return;
+    const Geo &G = f.G, &H = c.G;
+    const long long Q = id3(H, I, J, K);
+    double cs = 0.0, fx0 = 0.0, fx1 = 0.0, fy0 = 0.0, fy1 = 0.0, fz0 = 0.0, fz1 = 0.0;
+    for (int dk = 0; dk < 2; ++dk)
+        for (int dj = 0; dj < 2; ++dj)
+            for (int di = 0; di < 2; ++di) {
+                const int i = 2 * I + di, j = 2 * J + dj, k = 2 * K + dk;
+                const long long q = id3(G, i, j, k);
+                cs += ld(&f.c[q]);
+                if (di == 0) fx0 += ld(&f.ax[q]); else fx1 += ld(&f.ax[q + 1]);
+                if (dj == 0) fy0 += ld(&f.ay[q]); else fy1 += ld(&f.ay[q + G.P]);
+                if (dk == 0) fz0 += ld(&f.az[q]); else fz1 += ld(&f.az[q + (long long)G.P * (G.ny + 1)]);
+            }
+    const double cc = 0.125 * cs;
+    c.c[Q] = cc;
+    c.ax[Q] = 0.125 * fx0; c.ay[Q] = 0.125 * fy0; c.az[Q] = 0.125 * fz0;
+    if (I == H.nx - 1) c.ax[Q + 1] = 0.125 * fx1;
+    if (J == H.ny - 1) c.ay[Q + H.P] = 0.125 * fy1;
+    if (K == H.nz - 1) c.az[Q + (long long)H.P * (H.ny + 1)] = 0.125 * fz1;
+    const double d = cc + 0.125 * (fx0 + fx1 + fy0 + fy1 + fz0 + fz1);
+    c.d[Q] = d;
+    c.w[Q] = kOmega / d;
+}
+
+}  // namespace g3
+
+namespace g3 {
+
+// ---- Step 3 (eq. step2_sd second line, eq. p_prime_sd, eq. step4_4sd) ----
+
+// H(u) = rho^n u^n / dt - C(u) + mu L(u) at the newest velocity
+__global__ void k_H(Args a, const double *U, const double *V, const double *W)
+{
+    if (a.sc->status) return;
+    int i, j, k;
+    if (!cell(a.G, i, j, k)) return;
+    const long long q = id3(a.G, i, j, k);
+    const double r = ld(&a.S.rho[q]) * a.F.idt;
+    // C(X) - mu L(X) = T(X) - (rho1/dt) X
+    const W13 c = weights(a, q);
+    const double c0 = c.w[0] - ld(&a.rho1[q]) * a.F.idt;
+    a.Hx[q] = r * ld(&a.S.u[q]) - fma(c0, ld(&U[q]), toff<U3>(a, c, U, i, j, k));
+    a.Hy[q] = r * ld(&a.S.v[q]) - fma(c0, ld(&V[q]), toff<V3>(a, c, V, i, j, k));
+    a.Hz[q] = r * ld(&a.S.w[q]) - fma(c0, ld(&W[q]), toff<W3>(a, c, W, i, j, k));
+}
+
+// A x at cell (i,j,k) of level L for x given cellwise by xf(q, i, j, k) (interior
+// neighbours only; wall faces have zero coefficients).
+template <class XF>
+__device__ __forceinline__ double helm(const Lev &L, XF xf, int i, int j, int k)
+{
+    const Geo &G = L.G;
+    const long long q = id3(G, i, j, k), sy = G.P, sz = (long long)G.P * (G.ny + 1);
+    double t = ld(&L.d[q]) * xf(q, i, j, k);
+    if (i > 0) t -= ld(&L.ax[q]) * xf(q - 1, i - 1, j, k);
+    if (i + 1 < G.nx) t -= ld(&L.ax[q + 1]) * xf(q + 1, i + 1, j, k);
+    if (j > 0) t -= ld(&L.ay[q]) * xf(q - sy, i, j - 1, k);
+    if (j + 1 < G.ny) t -= ld(&L.ay[q + sy]) * xf(q + sy, i, j + 1, k);
+    if (k > 0) t -= ld(&L.az[q]) * xf(q - sz, i, j, k - 1);
+    if (k + 1 < G.nz) t -= ld(&L.az[q + sz]) * xf(q + sz, i, j, k + 1);
+    return t;
+}
+
+__device__ __forceinline__ void fin_helm(Sc *sc, const double (&t)[2], double tol2, int corr)
+{
+    sc->b2 = t[0];
+    sc->r2 = t[1];
+    sc->cg_it = 0;
+    sc->corr = corr;
+    sc->trips[L_CG] = 0;
+    sc->rz = 0.0;
+    sc->beta = 0.0;
+    sc->done[L_CG] = t[1] <= tol2 * t[0];
+    sc->cg_iters[corr] = 0;
+    sc->cg_relres[corr] = t[0] > 0.0 ? sqrt(t[1] / t[0]) : 0.0;
+    if (!isfinite(t[0]) || !isfinite(t[1])) sc->status = GEA_ERR_NONFINITE;
+}
+
+// b_i = (rho^n_i + psi_i rho2_i g z_i)/dt - sum_f D_f/Delta_f [H_f . n + g z_f (rho2_N - rho2_i)/Delta_f],
+// r = b - A x with x = xin (copied to xout), p0 = 0; acc += (b^2, r^2).
+__global__ void k_helm_rhs(Args a, Lev L, const double *xin, double *xout, int corr)
+{
+    if (a.sc->status) return;
+    __shared__ double red[2 * NT];
+    double acc[2] = {0.0, 0.0}, tot[2];
+    int i, j, k;
+    if (cell(a.G, i, j, k)) {
+        const Geo &G = a.G;
+        const Phy &F = a.F;
+        const long long q = id3(G, i, j, k), sx = 1, sy = G.P, sz = (long long)G.P * (G.ny + 1);
+        const double zc = (k + 0.5) * G.dz, r2 = ld(&a.rho2[q]);
+        double fl = 0.0;
+        // idl = 1/Delta of the face direction
+        auto face = [&](const double *D, const double *H, long long fq, long long nq, double sgn, double zf,
+                        double idl) {
+            return ld(&D[fq]) * idl * (sgn * 0.5 * (ld(&H[q]) + ld(&H[nq])) + F.g * zf * (ld(&a.rho2[nq]) - r2) * idl);
+        };
+        if (i + 1 < G.nx) fl += face(a.Dx, a.Hx, q + sx, q + sx, 1.0, zc, G.idx);
+        if (i > 0) fl += face(a.Dx, a.Hx, q, q - sx, -1.0, zc, G.idx);
+        if (j + 1 < G.ny) fl += face(a.Dy, a.Hy, q + sy, q + sy, 1.0, zc, G.idy);
+        if (j > 0) fl += face(a.Dy, a.Hy, q, q - sy, -1.0, zc, G.idy);
+        if (k + 1 < G.nz) fl += face(a.Dz, a.Hz, q + sz, q + sz, 1.0, (k + 1) * G.dz, G.idz);
+        if (k > 0) fl += face(a.Dz, a.Hz, q, q - sz, -1.0, k * G.dz, G.idz);
+        const double b = (ld(&a.S.rho[q]) + ld(&a.psi[q]) * r2 * F.g * zc) * F.idt - fl;
+        const double r = b - helm(L, [&](long long qq, int, int, int) { return ld(&xin[qq]); }, i, j, k);
+        a.b[q] = b;
+        L.r[q] = r;
+        xout[q] = ld(&xin[q]);
+        a.p0[q] = 0.0;
+        acc[0] = b * b;
+        acc[1] = r * r;
+    }
+    if (gsum<2>(acc, red, a.part, &a.sc->counters[C_HELM], tot)) fin_helm(a.sc, tot, a.ctol2, corr);
+}
+
+// ---- multigrid V(1,1) cycle ----
+
+// Pre-smoothing from zero, e = (omega/d) r, and restriction of r - A e to
+// the coarse level (mean of the 8 children). One thread per coarse cell.
+__global__ void k_mg_down(Lev f, Lev c, double omega, Sc *sc)
+{
+    if (over(sc, L_CG)) return;
+    int I, J, K;
+    if (!cell(c.G, I, J, K)) return;
+    const Geo &G = f.G;
+    auto e = [&](long long q, int, int, int) { return ld(&f.w[q]) * ld(&f.r[q]); };
+    double s = 0.0;
+    for (int dk = 0; dk < 2; ++dk)
+        for (int dj = 0; dj < 2; ++dj)
+            for (int di = 0; di < 2; ++di) {
+                const int i = 2 * I + di, j = 2 * J + dj, k = 2 * K + dk;
+                const long long q = id3(G, i, j, k);
+                f.e[q] = e(q, i, j, k);
+                s += ld(&f.r[q]) - helm(f, e, i, j, k);
+            }
+    c.r[id3(c.G, I, J, K)] = 0.125 * s;
+}
+
+// Coarsest level: damped Jacobi sweep (first: from zero).
+__global__ void k_mg_coarse(Lev L, const double *ein, double *eout, int first, Sc *sc)
+{
+    if (over(sc, L_CG)) return;
+    int i, j, k;
+    if (!cell(L.G, i, j, k)) return;
+    const long long q = id3(L.G, i, j, k);
+    const double w = ld(&L.w[q]);
+    if (first) {
+        eout[q] = w * ld(&L.r[q]);
+        return;
+    }
+    eout[q] = ld(&ein[q]) + w * (ld(&L.r[q]) - helm(L, [&](long long qq, int, int, int) { return ld(&ein[qq]); }, i, j, k));
+}
+
+__device__ __forceinline__ void fin_rz(Sc *sc, double t)
+{
+    sc->beta = (sc->cg_it == 0 || sc->rz == 0.0) ? 0.0 : t / sc->rz;
+    sc->rz = t;
+}
+
+// Prolongation e' = e + P e_c and post-smoothing z = e' + (omega/d)(r - A e')
+// into out; on the finest level acc += r.z.
+__global__ void k_mg_up(Lev f, const double *ec, Geo cg, double *out, int finest, Sc *sc, double *part)
+{
+    if (over(sc, L_CG)) return;
+    __shared__ double red[NT];
+    double acc[1] = {0.0}, tot[1];
+    int i, j, k;
+    if (cell(f.G, i, j, k)) {
+        const Geo &G = f.G;
+        const long long q = id3(G, i, j, k);
+        auto ef = [&](long long qq, int ii, int jj, int kk) {
+            return ld(&f.e[qq]) + ld(&ec[id3(cg, ii >> 1, jj >> 1, kk >> 1)]);
+        };
+        const double rq = ld(&f.r[q]);
+        const double z = ef(q, i, j, k) + ld(&f.w[q]) * (rq - helm(f, ef, i, j, k));
+        out[q] = z;
+        acc[0] = rq * z;
+    }
+    if (!finest) return;
+    if (gsum<1>(acc, red, part, &sc->counters[C_RZ], tot)) fin_rz(sc, tot[0]);
+}
+
+// One level only: z = e + (omega/d)(r - A e), e = (omega/d) r; acc += r.z.
+__global__ void k_mg_single(Lev f, double *out, Sc *sc, double *part)
+{
+    if (over(sc, L_CG)) return;
+    __shared__ double red[NT];
+    double acc[1] = {0.0}, tot[1];
+    int i, j, k;
+    if (cell(f.G, i, j, k)) {
+        const long long q = id3(f.G, i, j, k);
+        auto e = [&](long long qq, int, int, int) { return ld(&f.w[qq]) * ld(&f.r[qq]); };
+        const double rq = ld(&f.r[q]);
+        const double z = e(q, i, j, k) + ld(&f.w[q]) * (rq - helm(f, e, i, j, k));
+        out[q] = z;
+        acc[0] = rq * z;
+    }
+    if (gsum<1>(acc, red, part, &sc->counters[C_RZ], tot)) fin_rz(sc, tot[0]);
+}
+
+// ---- CG steps (directions alternate between p0 and p1 by parity) ----
+
+__global__ void k_pspmv(Args a, Lev L)
+{
+    Sc *sc = a.sc;
+    if (over(sc, L_CG)) return;
+    __shared__ double red[NT];
+    double acc[1] = {0.0}, tot[1];
+    const int it = sc->cg_it;
+    const double *pold = (it & 1) ? a.p1 : a.p0;
+    double *pnew = (it & 1) ? a.p0 : a.p1;
+    const double beta = sc->beta;
+    int i, j, k;
+    if (cell(L.G, i, j, k)) {
+        const long long q = id3(L.G, i, j, k);
+        auto p = [&](long long qq, int, int, int) { return fma(beta, ld(&pold[qq]), ld(&L.e2[qq])); };
+        const double pq = p(q, i, j, k), Ap = helm(L, p, i, j, k);
+        pnew[q] = pq;
+        a.q[q] = Ap;
+        acc[0] = pq * Ap;
+    }
+    if (gsum<1>(acc, red, a.part, &sc->counters[C_PQ], tot)) {
+        sc->pq = tot[0];
+        sc->alpha = tot[0] != 0.0 ? sc->rz / tot[0] : 0.0;
+        if (!isfinite(tot[0])) sc->status = GEA_ERR_NONFINITE;
+    }
+}
+
+// x += alpha p, r -= alpha q (in place, each cell its own); acc += r^2.
+__global__ void k_update(Args a, Lev L, double *x, int maxit)
+{
+    Sc *sc = a.sc;
+    if (over(sc, L_CG)) return;
+    __shared__ double red[NT];
+    double acc[1] = {0.0}, tot[1];
+    const int it = sc->cg_it;
+    const double *p = (it & 1) ? a.p0 : a.p1;
+    const double alpha = sc->alpha;
+    int i, j, k;
+    if (cell(L.G, i, j, k)) {
+        const long long q = id3(L.G, i, j, k);
+        x[q] = fma(alpha, ld(&p[q]), x[q]);
+        const double rn = fma(-alpha, ld(&a.q[q]), L.r[q]);
+        L.r[q] = rn;
+        acc[0] = rn * rn;
+    }
+    if (gsum<1>(acc, red, a.part, &sc->counters[C_UPD], tot)) {
+        const int n = sc->cg_it + 1;
+        sc->cg_it = n;
+        sc->r2 = tot[0];
+        sc->cg_iters[sc->corr] = n;
+        sc->cg_relres[sc->corr] = sc->b2 > 0.0 ? sqrt(tot[0] / sc->b2) : 0.0;
+        if (!isfinite(tot[0])) sc->status = GEA_ERR_NONFINITE;
+        else if (tot[0] <= a.ctol2 * sc->b2) sc->done[L_CG] = 1;
+    }
+}
+
+// Correction: face forces from the new p' and rho2, F_f = D_f (H_f - G_f),
+// u = (dt/rho1)(H - G_cell), p = p' - rho2 g z, rho = p psi, phi = F |A|,
+// p^{n-1} <- p^n. Each cell writes its west, south and bottom faces (and the
+// walls beyond its east, north and top faces).
+__global__ void k_correct(Args a)
+{
+    if (a.sc->status) return;
+    int i, j, k;
+    if (!cell(a.G, i, j, k)) return;
+    const Geo &G = a.G;
+    const Phy &F = a.F;
+    const long long q = id3(G, i, j, k), sx = 1, sy = G.P, sz = (long long)G.P * (G.ny + 1);
+    double gx, gy, gz;
+    cell_forces(G, F, a.N.pp, a.rho2, i, j, k, gx, gy, gz);
+    const double zc = (k + 0.5) * G.dz;
+    const double c1 = F.dt / ld(&a.rho1[q]);
+    const double hx = ld(&a.Hx[q]), hy = ld(&a.Hy[q]), hz = ld(&a.Hz[q]);
+    a.N.u[q] = c1 * (hx - gx);
+    a.N.v[q] = c1 * (hy - gy);
+    a.N.w[q] = c1 * (hz - gz);
+    const double pn = ld(&a.N.pp[q]) - ld(&a.rho2[q]) * F.g * zc;
+    a.N.p[q] = pn;
+    a.N.rho[q] = pn * ld(&a.psi[q]);
+    a.N.pold[q] = ld(&a.S.p[q]);
+    const double idx = G.idx, idy = G.idy, idz = G.idz;
+    a.N.phix[q] = i > 0 ? ld(&a.Dx[q]) * (0.5 * (hx + ld(&a.Hx[q - sx])) -
+                                           fforce(a.N.pp, a.rho2, q, sx, idx, F.g * zc)) * G.dy * G.dz : 0.0;
+    a.N.phiy[q] = j > 0 ? ld(&a.Dy[q]) * (0.5 * (hy + ld(&a.Hy[q - sy])) -
+                                           fforce(a.N.pp, a.rho2, q, sy, idy, F.g * zc)) * G.dx * G.dz : 0.0;
+    a.N.phiz[q] = k > 0 ? ld(&a.Dz[q]) * (0.5 * (hz + ld(&a.Hz[q - sz])) -
+                                           fforce(a.N.pp, a.rho2, q, sz, idz, F.g * (k * G.dz))) * G.dx * G.dy : 0.0;
+    if (i == G.nx - 1) a.N.phix[q + sx] = 0.0;
+    if (j == G.ny - 1) a.N.phiy[q + sy] = 0.0;
+    if (k == G.nz - 1) a.N.phiz[q + sz] = 0.0;
+}
+
+// ---- loop control and step bookkeeping (one thread) ----
+
+__global__ void k_ctl(Sc *sc, cudaGraphConditionalHandle h, int graph, int which, int maxtrips, int body)
+{
+    const int trips = ++sc->trips[which];
+    const int done = sc->done[which];
+    sc->launches += body;
+    if (!done && !sc->status && trips >= maxtrips) sc->status = GEA_ERR_NOCONV;
+    if (graph) cudaGraphSetConditional(h, (done || sc->status || trips >= maxtrips) ? 0u : 1u);
+}
+
+__global__ void k_begin(Sc *sc)
+{
+    for (int c = 0; c < 4; ++c) { sc->cg_iters[c] = 0; sc->cg_relres[c] = 0.0; }
+}
+
+__global__ void k_end(Sc *sc, int fixed)
+{
+    sc->launches += fixed;
+    if (sc->status) {
+        sc->last_status = sc->status;
+        return;
+    }
+    sc->steps_done += 1;
+    sc->last_sweeps[0] = sc->sweeps[0];
+    sc->last_sweeps[1] = sc->sweeps[1];
+    for (int c = 0; c < 4; ++c) {
+        sc->last_cg_iters[c] = sc->cg_iters[c];
+        sc->last_cg_relres[c] = sc->cg_relres[c];
+    }
+    sc->last_status = 0;
+}
+
+}  // namespace g3
+
+using namespace g3;
+
+struct gea3d_ctx {
+    Geo G;
+    Phy F;
+    gea_constants C;
+    cudaStream_t stream = nullptr, cap = nullptr, cap2 = nullptr;
+    std::vector<void *> allocs;
+    St S[2];
+    double *rho1, *dinvu, *dinvh, *bu, *bv, *bw, *ua, *va, *wa, *ub, *vb, *wb, *bh, *ha, *hb;
+    double *rho2, *psi, *Dx, *Dy, *Dz, *Hx, *Hy, *Hz, *b, *p0, *p1, *q;
+    Cf cf;                                // transport stencil weights
+    double *stage = nullptr;              // dense conservative fields (5 arrays)
+    std::vector<Lev> L;
+    Sc *sc = nullptr;
+    double *part = nullptr;
+    cudaGraph_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    bool have_state = false;
+    long long steps_at_sync = 0;
+    char err[256] = {0};
+};
+
+namespace {
+
+int fail3(gea3d_ctx *c, int code, const char *fmt, ...)
+{
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof(c->err), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+#define CK3(call)                                                                                   \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess)                                                                      \
+            return fail3(ctx, GEA_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                         __LINE__);                                                                 \
+    } while (0)
+
+Geo make_geo(int nx, int ny, int nz, double lx, double ly, double lz)
+{
+    Geo G;
+    G.nx = nx; G.ny = ny; G.nz = nz;
+    G.P = (nx + 1 + 31) / 32 * 32;
+    G.dx = lx / nx; G.dy = ly / ny; G.dz = lz / nz;
+    G.idx = 1.0 / G.dx; G.idy = 1.0 / G.dy; G.idz = 1.0 / G.dz;
+    G.idx2 = 1.0 / (G.dx * G.dx); G.idy2 = 1.0 / (G.dy * G.dy); G.idz2 = 1.0 / (G.dz * G.dz);
+    G.ivol = 1.0 / (G.dx * G.dy * G.dz);
+    return G;
+}
+
+// elements of one array (cells or faces) of a level
+size_t elems(const Geo &G) { return (size_t)(G.nz + 1) * (G.ny + 1) * G.P; }
+
+dim3 grid_of(const Geo &G) { return dim3((G.nx + TX - 1) / TX, (G.ny + TY - 1) / TY, G.nz); }
+const dim3 kBlk(TX, TY);
+size_t nblocks(const Geo &G)
+{
+    const dim3 g = grid_of(G);
+    return (size_t)g.x * g.y * g.z;
+}
+
+Args args_of(gea3d_ctx *c, int from)
+{
+    Args a;
+    a.G = c->G; a.F = c->F;
+    a.S = c->S[from]; a.N = c->S[from ^ 1];
+    a.rho1 = c->rho1; a.dinvu = c->dinvu; a.dinvh = c->dinvh;
+    a.bu = c->bu; a.bv = c->bv; a.bw = c->bw;
+    a.ua = c->ua; a.va = c->va; a.wa = c->wa; a.ub = c->ub; a.vb = c->vb; a.wb = c->wb;
+    a.bh = c->bh; a.ha = c->ha; a.hb = c->hb;
+    a.rho2 = c->rho2; a.psi = c->psi; a.Dx = c->Dx; a.Dy = c->Dy; a.Dz = c->Dz;
+    a.Hx = c->Hx; a.Hy = c->Hy; a.Hz = c->Hz; a.b = c->b; a.p0 = c->p0; a.p1 = c->p1; a.q = c->q;
+    a.cf = c->cf;
+    a.sc = c->sc; a.part = c->part;
+    a.jtol2 = c->C.jac_rtol * c->C.jac_rtol;
+    a.ctol2 = c->C.cg_rtol * c->C.cg_rtol;
+    return a;
+}
+
+// WHILE node on the graph captured on s; body(stream, handle) captured into it
+template <class Body>
+int capture_while3(gea3d_ctx *ctx, cudaStream_t s, Body body)
+{
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g;
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *edges = nullptr;
+    size_t ndeps = 0;
+    CK3(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, &edges, &ndeps));
+    if (cs != cudaStreamCaptureStatusActive) return fail3(ctx, GEA_ERR_CUDA, "capture not active");
+    cudaGraphConditionalHandle h;
+    CK3(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams prm = {cudaGraphNodeTypeConditional};
+    prm.conditional.handle = h;
+    prm.conditional.type = cudaGraphCondTypeWhile;
+    prm.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK3(cudaGraphAddNode(&node, g, deps, edges, ndeps, &prm));
+    CK3(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    CK3(cudaStreamBeginCaptureToGraph(ctx->cap2, prm.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal));
+    body(ctx->cap2, h);
+    cudaGraph_t out = nullptr;
+    CK3(cudaStreamEndCapture(ctx->cap2, &out));
+    return GEA_OK;
+}
+
+// Event pairs around the launches of an eager step (per-kernel timing).
+struct Trace3 {
+    struct Rec {
+        const char *name;
+        long long cells;
+        cudaEvent_t e0, e1;
+    };
+    std::vector<Rec> recs;
+    ~Trace3()
+    {
+        for (auto &r : recs) {
+            cudaEventDestroy(r.e0);
+            cudaEventDestroy(r.e1);
+        }
+    }
+};
+
+// Run go() (one launch on st), bracketed by an event pair when tracing.
+template <class Go>
+void traced(Trace3 *tr, const char *name, const Geo &G, cudaStream_t st, Go go)
+{
+    if (!tr) {
+        go();
+        return;
+    }
+    Trace3::Rec r{name, (long long)G.nx * G.ny * G.nz, nullptr, nullptr};
+    cudaEventCreate(&r.e0);
+    cudaEventCreate(&r.e1);
+    cudaEventRecord(r.e0, st);
+    go();
+    cudaEventRecord(r.e1, st);
+    tr->recs.push_back(r);
+}
+
+// Run a loop body eagerly until its control kernel reports the loop over.
+template <class Body>
+int eager_while3(gea3d_ctx *ctx, cudaStream_t s, int which, int maxtrips, Body body)
+{
+    for (int t = 0; t < maxtrips + 1; ++t) {
+        body(s, (cudaGraphConditionalHandle)0);
+        Sc h;
+        CK3(cudaMemcpyAsync(&h, ctx->sc, sizeof(Sc), cudaMemcpyDeviceToHost, s));
+        CK3(cudaStreamSynchronize(s));
+        if (h.done[which] || h.status || h.trips[which] >= maxtrips) break;
+    }
+    return GEA_OK;
+}
+
+// z = M^-1 r on the finest level (one V(1,1) cycle); returns launches
+int vcycle(gea3d_ctx *ctx, const Args &a, cudaStream_t st, Trace3 *tr)
+{
+    Lev *L = ctx->L.data();
+    const int nlev = (int)ctx->L.size();
+    if (nlev == 1) {
+        traced(tr, "g3_mg_single", L[0].G, st, [&] {
+            k_mg_single<<<grid_of(L[0].G), kBlk, 0, st>>>(L[0], L[0].e2, a.sc, a.part);
+        });
+        return 1;
+    }
+    int n = 0;
+    for (int l = 0; l + 1 < nlev; ++l, ++n)
+        traced(tr, "g3_mg_down", L[l + 1].G, st, [&] {
+            k_mg_down<<<grid_of(L[l + 1].G), kBlk, 0, st>>>(L[l], L[l + 1], kOmega, a.sc);
+        });
+    Lev &C = L[nlev - 1];
+    for (int s = 0; s < kCoarseSweeps; ++s, ++n) {
+        double *out = ((kCoarseSweeps - 1 - s) % 2 == 0) ? C.e2 : C.e;
+        const double *in = (out == C.e2) ? C.e : C.e2;
+        traced(tr, "g3_mg_coarse", C.G, st, [&] {
+            k_mg_coarse<<<grid_of(C.G), kBlk, 0, st>>>(C, in, out, s == 0, a.sc);
+        });
+    }
+    for (int l = nlev - 2; l >= 0; --l, ++n)
+        traced(tr, "g3_mg_up", L[l].G, st, [&] {
+            k_mg_up<<<grid_of(L[l].G), kBlk, 0, st>>>(L[l], L[l + 1].e2, L[l + 1].G, L[l].e2, l == 0, a.sc,
+                                                      a.part);
+        });
+    return n;
+}
+
+// The kernel sequence of one step reading slot `from` (Section 3: Step 1,
+// Step 2, n_corr PISO correctors). graph: captured on s, the loops as WHILE
+// nodes; otherwise launched eagerly with host-checked loops, each launch
+// bracketed by tr (if given).
+int record3(gea3d_ctx *ctx, int from, cudaStream_t s, bool graph, Trace3 *tr)
+{
+    const Args a = args_of(ctx, from);
+    Lev *L = ctx->L.data();
+    const int nlev = (int)ctx->L.size();
+    const Geo &G = ctx->G;
+    const dim3 grid = grid_of(G);
+    const int jtrips = (ctx->C.jac_maxit + 1) / 2;
+    const int gr = graph ? 1 : 0;
+    int fixed = 0, rc;
+    auto loop = [&](int which, int maxtrips, auto body) {
+        return graph ? capture_while3(ctx, s, body) : eager_while3(ctx, s, which, maxtrips, body);
+    };
+    k_begin<<<1, 1, 0, s>>>(a.sc); ++fixed;
+    traced(tr, "g3_pred", G, s, [&] { k_pred<<<grid, kBlk, 0, s>>>(a); }); ++fixed;
+    rc = loop(L_MOM, jtrips, [&](cudaStream_t bs, cudaGraphConditionalHandle h) {
+        traced(tr, "g3_mom", G, bs, [&] { k_mom<<<grid, kBlk, 0, bs>>>(a, a.ua, a.va, a.wa, a.ub, a.vb, a.wb, 0); });
+        traced(tr, "g3_mom", G, bs, [&] { k_mom<<<grid, kBlk, 0, bs>>>(a, a.ub, a.vb, a.wb, a.ua, a.va, a.wa, 1); });
+        k_ctl<<<1, 1, 0, bs>>>(a.sc, h, gr, L_MOM, jtrips, 3);
+    });
+    if (rc) return rc;
+    traced(tr, "g3_enth_rhs", G, s, [&] { k_enth_rhs<<<grid, kBlk, 0, s>>>(a, a.ua, a.va, a.wa); }); ++fixed;
+    rc = loop(L_ENTH, jtrips, [&](cudaStream_t bs, cudaGraphConditionalHandle h) {
+        traced(tr, "g3_enth", G, bs, [&] { k_enth<<<grid, kBlk, 0, bs>>>(a, a.ha, a.hb, 0); });
+        traced(tr, "g3_enth", G, bs, [&] { k_enth<<<grid, kBlk, 0, bs>>>(a, a.hb, a.ha, 1); });
+        k_ctl<<<1, 1, 0, bs>>>(a.sc, h, gr, L_ENTH, jtrips, 3);
+    });
+    if (rc) return rc;
+    traced(tr, "g3_eos", G, s, [&] { k_eos<<<grid, kBlk, 0, s>>>(a, L[0], a.ha); }); ++fixed;
+    traced(tr, "g3_faces", G, s, [&] { k_faces<<<grid, kBlk, 0, s>>>(a, L[0]); }); ++fixed;
+    traced(tr, "g3_diag", G, s, [&] { k_diag<<<grid, kBlk, 0, s>>>(L[0], a.sc); }); ++fixed;
+    for (int l = 0; l + 1 < nlev; ++l, ++fixed)
+        traced(tr, "g3_coarsen", L[l + 1].G, s, [&] {
+            k_coarsen<<<grid_of(L[l + 1].G), kBlk, 0, s>>>(L[l], L[l + 1]);
+        });
+    const int body_cg = (nlev == 1 ? 3 : 2 + (nlev - 1) + kCoarseSweeps + (nlev - 1)) + 1;
+    for (int c = 0; c < ctx->C.n_corr; ++c) {
+        const double *U = c == 0 ? a.ua : a.N.u, *V = c == 0 ? a.va : a.N.v, *W = c == 0 ? a.wa : a.N.w;
+        traced(tr, "g3_H", G, s, [&] { k_H<<<grid, kBlk, 0, s>>>(a, U, V, W); }); ++fixed;
+        traced(tr, "g3_helm_rhs", G, s, [&] {
+            k_helm_rhs<<<grid, kBlk, 0, s>>>(a, L[0], c == 0 ? a.S.pp : a.N.pp, a.N.pp, c);
+        });
+        ++fixed;
+        fixed += vcycle(ctx, a, s, tr);
+        rc = loop(L_CG, ctx->C.cg_maxit, [&](cudaStream_t bs, cudaGraphConditionalHandle h) {
+            traced(tr, "g3_pspmv", G, bs, [&] { k_pspmv<<<grid, kBlk, 0, bs>>>(a, L[0]); });
+            traced(tr, "g3_update", G, bs, [&] { k_update<<<grid, kBlk, 0, bs>>>(a, L[0], a.N.pp, ctx->C.cg_maxit); });
+            vcycle(ctx, a, bs, tr);
+            k_ctl<<<1, 1, 0, bs>>>(a.sc, h, gr, L_CG, ctx->C.cg_maxit, body_cg);
+        });
+        if (rc) return rc;
+        traced(tr, "g3_correct", G, s, [&] { k_correct<<<grid, kBlk, 0, s>>>(a); }); ++fixed;
+    }
+    ++fixed;
+    k_end<<<1, 1, 0, s>>>(a.sc, fixed);
+    return cudaGetLastError() == cudaSuccess ? GEA_OK : fail3(ctx, GEA_ERR_CUDA, "kernel launch failed");
+}
+
+int build3(gea3d_ctx *ctx, int from)
+{
+    cudaStream_t s = ctx->cap;
+    CK3(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    const int rc = record3(ctx, from, s, true, nullptr);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail3(ctx, GEA_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+    ctx->graph[from] = g;
+    CK3(cudaGraphInstantiate(&ctx->exec[from], g, 0));
+    return GEA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gea3d_create(const gea3d_grid *grid, const gea_constants *c, gea3d_ctx **out)
+{
+    if (!grid || !c || !out) return GEA_ERR_INVAL;
+    *out = nullptr;
+    if (grid->nx < 4 || grid->ny < 4 || grid->nz < 4 || !(grid->lx > 0) || !(grid->ly > 0) || !(grid->lz > 0))
+        return GEA_ERR_INVAL;
+    if ((long long)grid->nx * grid->ny * grid->nz > (1LL << 31) / 4) return GEA_ERR_INVAL;
+    if (!(c->R > 0) || !(c->cp > c->R) || !(c->g >= 0) || !(c->p0 > 0) || !(c->mu >= 0) || !(c->Pr > 0) ||
+        !(c->dt > 0) || c->n_corr < 1 || c->n_corr > 4 || !(c->jac_rtol > 0) || c->jac_maxit < 1 ||
+        !(c->cg_rtol > 0) || c->cg_maxit < 1 || c->mg_min_cells < 0 || c->flags != 0 || c->mp_rtol != 0.0 ||
+        c->cs != 0.0)
+        return GEA_ERR_INVAL;
+    gea3d_ctx *ctx = new gea3d_ctx();
+    ctx->C = *c;
+    ctx->G = make_geo(grid->nx, grid->ny, grid->nz, grid->lx, grid->ly, grid->lz);
+    ctx->F.R = c->R; ctx->F.cp = c->cp; ctx->F.g = c->g; ctx->F.mu = c->mu; ctx->F.nuh = c->mu / c->Pr;
+    ctx->F.dt = c->dt; ctx->F.idt = 1.0 / c->dt; ctx->F.omega = kOmega;
+    // multigrid levels: halve all three sizes while they are even and >= 8
+    // and (unless mg_min_cells is given) the Laplacian-to-diagonal estimate
+    // 2 dt^2 R T (1/dx^2 + 1/dy^2 + 1/dz^2) exceeds 1
+    std::vector<Geo> lg{ctx->G};
+    double ratio = 2.0 * c->dt * c->dt * c->R * kRefT *
+                   (1.0 / (ctx->G.dx * ctx->G.dx) + 1.0 / (ctx->G.dy * ctx->G.dy) + 1.0 / (ctx->G.dz * ctx->G.dz));
+    for (;;) {
+        const Geo &f = lg.back();
+        if (f.nx % 2 || f.ny % 2 || f.nz % 2 || f.nx < 8 || f.ny < 8 || f.nz < 8) break;
+        if (c->mg_min_cells > 0 && (long long)f.nx * f.ny * f.nz <= c->mg_min_cells) break;
+        if (c->mg_min_cells == 0 && ratio <= kCoarsestRatio) break;
+        if ((int)lg.size() >= kMaxLev) break;
+        lg.push_back(make_geo(f.nx / 2, f.ny / 2, f.nz / 2, f.nx * f.dx, f.ny * f.dy, f.nz * f.dz));
+        ratio *= 0.25;
+    }
+    bool ok = true;
+    auto take = [&](size_t n) -> double * {
+        void *p = nullptr;
+        if (!ok) return nullptr;
+        if (cudaMalloc(&p, n * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            ok = false;
+            return nullptr;
+        }
+        cudaMemset(p, 0, n * sizeof(double));
+        ctx->allocs.push_back(p);
+        return static_cast<double *>(p);
+    };
+    const size_t E = elems(ctx->G);
+    for (int s = 0; s < 2; ++s) {
+        St &S = ctx->S[s];
+        double **f[12] = {&S.rho, &S.u, &S.v, &S.w, &S.T, &S.h, &S.p, &S.pp, &S.pold, &S.phix, &S.phiy, &S.phiz};
+        for (auto pp : f) *pp = take(E);
+    }
+    double **sc[] = {&ctx->rho1, &ctx->dinvu, &ctx->dinvh, &ctx->bu, &ctx->bv, &ctx->bw, &ctx->ua, &ctx->va,
+                     &ctx->wa, &ctx->ub, &ctx->vb, &ctx->wb, &ctx->bh, &ctx->ha, &ctx->hb, &ctx->rho2,
+                     &ctx->psi, &ctx->Dx, &ctx->Dy, &ctx->Dz, &ctx->Hx, &ctx->Hy, &ctx->Hz, &ctx->b, &ctx->p0,
+                     &ctx->p1, &ctx->q};
+    for (auto pp : sc) *pp = take(E);
+    for (int m = 0; m < NCF; ++m) ctx->cf.c[m] = take(E);
+    ctx->stage = take(5 * (size_t)grid->nx * grid->ny * grid->nz);
+    for (const Geo &g : lg) {
+        Lev l;
+        l.G = g;
+        const size_t e = elems(g);
+        l.c = take(e); l.d = take(e); l.ax = take(e); l.ay = take(e); l.az = take(e);
+        l.r = take(e); l.e = take(e); l.e2 = take(e); l.w = take(e);
+        ctx->L.push_back(l);
+    }
+    ctx->part = take(3 * nblocks(ctx->G) + 64);
+    ctx->sc = reinterpret_cast<Sc *>(take((sizeof(Sc) + 7) / 8));
+    if (!ok) {
+        gea3d_destroy(ctx);
+        return GEA_ERR_NOMEM;
+    }
+    if (cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->cap2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess) {
+        gea3d_destroy(ctx);
+        return GEA_ERR_CUDA;
+    }
+    *out = ctx;
+    return GEA_OK;
+}
+
+int gea3d_set_stream(gea3d_ctx *ctx, void *stream)
+{
+    if (!ctx) return GEA_ERR_INVAL;
+    ctx->stream = (cudaStream_t)stream;
+    return GEA_OK;
+}
+
+int gea3d_set_conservative(gea3d_ctx *ctx, const double *rho, const double *rhou, const double *rhov,
+                           const double *rhow, const double *rhoe, int32_t mem)
+{
+    if (!ctx || !rho || !rhou || !rhov || !rhow || !rhoe || (mem != GEA_MEM_HOST && mem != GEA_MEM_DEVICE))
+        return GEA_ERR_INVAL;
+    const Geo &G = ctx->G;
+    const size_t n = (size_t)G.nx * G.ny * G.nz;
+    CK3(cudaMemsetAsync(ctx->sc, 0, sizeof(Sc), ctx->stream));
+    const double *src[5] = {rho, rhou, rhov, rhow, rhoe};
+    for (int f = 0; f < 5; ++f)
+        CK3(cudaMemcpyAsync(ctx->stage + f * n, src[f], n * sizeof(double), cudaMemcpyDefault, ctx->stream));
+    k_derive<<<grid_of(G), kBlk, 0, ctx->stream>>>(G, ctx->F, ctx->stage, ctx->stage + n, ctx->stage + 2 * n,
+                                                   ctx->stage + 3 * n, ctx->stage + 4 * n, ctx->S[0], ctx->sc);
+    CK3(cudaGetLastError());
+    Sc h;
+    CK3(cudaMemcpyAsync(&h, ctx->sc, sizeof(Sc), cudaMemcpyDeviceToHost, ctx->stream));
+    CK3(cudaStreamSynchronize(ctx->stream));
+    if (h.bad_cells) {
+        ctx->have_state = false;
+        return fail3(ctx, GEA_ERR_INVAL, "%d cells with rho <= 0 or T <= 0", h.bad_cells);
+    }
+    ctx->steps_at_sync = 0;
+    ctx->have_state = true;
+    return GEA_OK;
+}
+
+int gea3d_step_async(gea3d_ctx *ctx, int32_t n)
+{
+    if (!ctx || n < 0) return GEA_ERR_INVAL;
+    if (!ctx->have_state) return fail3(ctx, GEA_ERR_STATE, "no state set");
+    for (int f = 0; f < 2; ++f)
+        if (!ctx->exec[f]) {
+            const int rc = build3(ctx, f);
+            if (rc) return rc;
+        }
+    for (int s = 0; s < n; ++s) {
+        CK3(cudaGraphLaunch(ctx->exec[ctx->steps_at_sync & 1], ctx->stream));
+        ctx->steps_at_sync += 1;
+    }
+    return GEA_OK;
+}
+
+int gea3d_sync(gea3d_ctx *ctx)
+{
+    if (!ctx) return GEA_ERR_INVAL;
+    Sc h;
+    CK3(cudaMemcpyAsync(&h, ctx->sc, sizeof(Sc), cudaMemcpyDeviceToHost, ctx->stream));
+    CK3(cudaStreamSynchronize(ctx->stream));
+    ctx->steps_at_sync = h.steps_done;
+    if (h.last_status == GEA_ERR_NOCONV) return fail3(ctx, GEA_ERR_NOCONV, "a linear solve reached its iteration cap");
+    if (h.last_status) return fail3(ctx, h.last_status, "device status %d", h.last_status);
+    return GEA_OK;
+}
+
+int gea3d_step(gea3d_ctx *ctx, int32_t n)
+{
+    const int rc = gea3d_step_async(ctx, n);
+    return rc ? rc : gea3d_sync(ctx);
+}
+
+int gea3d_get_state(gea3d_ctx *ctx, double *rho, double *u, double *v, double *w, double *T, double *p,
+                    double *pp, int32_t mem)
+{
+    if (!ctx || (mem != GEA_MEM_HOST && mem != GEA_MEM_DEVICE)) return GEA_ERR_INVAL;
+    if (!ctx->have_state) return fail3(ctx, GEA_ERR_STATE, "no state set");
+    Sc h;
+    CK3(cudaMemcpyAsync(&h, ctx->sc, sizeof(Sc), cudaMemcpyDeviceToHost, ctx->stream));
+    CK3(cudaStreamSynchronize(ctx->stream));
+    const St &S = ctx->S[h.steps_done & 1];
+    const Geo &G = ctx->G;
+    double *dst[7] = {rho, u, v, w, T, p, pp};
+    const double *src[7] = {S.rho, S.u, S.v, S.w, S.T, S.p, S.pp};
+    for (int f = 0; f < 7; ++f) {
+        if (!dst[f]) continue;
+        // (k (ny+1) + j) P + i -> (k ny + j) nx + i: one 2D copy per layer
+        for (int k = 0; k < G.nz; ++k)
+            CK3(cudaMemcpy2DAsync(dst[f] + (size_t)k * G.ny * G.nx, (size_t)G.nx * sizeof(double),
+                                  src[f] + (size_t)k * (G.ny + 1) * G.P, (size_t)G.P * sizeof(double),
+                                  (size_t)G.nx * sizeof(double), G.ny, cudaMemcpyDefault, ctx->stream));
+    }
+    CK3(cudaStreamSynchronize(ctx->stream));
+    return GEA_OK;
+}
+
+int gea3d_get_stats(gea3d_ctx *ctx, gea_stats *s)
+{
+    if (!ctx || !s) return GEA_ERR_INVAL;
+    Sc h;
+    CK3(cudaMemcpyAsync(&h, ctx->sc, sizeof(Sc), cudaMemcpyDeviceToHost, ctx->stream));
+    CK3(cudaStreamSynchronize(ctx->stream));
+    memset(s, 0, sizeof(*s));
+    s->steps_done = h.steps_done;
+    s->jac_u = h.last_sweeps[0];
+    s->jac_h = h.last_sweeps[1];
+    for (int c = 0; c < 4; ++c) { s->cg_iters[c] = h.last_cg_iters[c]; s->cg_relres[c] = h.last_cg_relres[c]; }
+    s->status = h.last_status;
+    s->mg_levels = (int)ctx->L.size();
+    s->launches = h.launches;
+    s->driver = 0;
+    return GEA_OK;
+}
+
+int gea3d_profile_step(gea3d_ctx *ctx, gea_kernel_time *out, int32_t max_entries, int32_t *n_entries)
+{
+    if (!ctx || max_entries < 0 || (!out && max_entries > 0) || !n_entries) return GEA_ERR_INVAL;
+    if (!ctx->have_state) return fail3(ctx, GEA_ERR_STATE, "no state set");
+    Sc h;
+    CK3(cudaMemcpyAsync(&h, ctx->sc, sizeof(Sc), cudaMemcpyDeviceToHost, ctx->stream));
+    CK3(cudaStreamSynchronize(ctx->stream));
+    if (h.status) return fail3(ctx, h.status, "device status %d", h.status);
+    {
+        Trace3 tr;
+        const int rc = record3(ctx, (int)(h.steps_done & 1), ctx->stream, false, &tr);
+        if (rc) return rc;
+        CK3(cudaStreamSynchronize(ctx->stream));
+        std::vector<gea_kernel_time> agg;
+        for (auto &r : tr.recs) {
+            float ms = 0.f;
+            CK3(cudaEventElapsedTime(&ms, r.e0, r.e1));
+            size_t j = 0;
+            while (j < agg.size() && strcmp(agg[j].name, r.name)) ++j;
+            if (j == agg.size()) {
+                gea_kernel_time k;
+                memset(&k, 0, sizeof(k));
+                snprintf(k.name, sizeof(k.name), "%s", r.name);
+                agg.push_back(k);
+            }
+            agg[j].launches += 1;
+            agg[j].cells += r.cells;
+            agg[j].ms += ms;
+        }
+        *n_entries = (int32_t)agg.size();
+        for (size_t j = 0; j < agg.size() && (int32_t)j < max_entries; ++j) out[j] = agg[j];
+    }
+    return gea3d_sync(ctx);
+}
+
+const char *gea3d_last_error(const gea3d_ctx *ctx) { return ctx ? ctx->err : "null context"; }
+
+void gea3d_destroy(gea3d_ctx *ctx)
+{
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    else cudaDeviceSynchronize();
+    for (int f = 0; f < 2; ++f) {
+        if (ctx->exec[f]) cudaGraphExecDestroy(ctx->exec[f]);
+        if (ctx->graph[f]) cudaGraphDestroy(ctx->graph[f]);
+    }
+    if (ctx->cap) cudaStreamDestroy(ctx->cap);
+    if (ctx->cap2) cudaStreamDestroy(ctx->cap2);
+    for (void *p : ctx->allocs) cudaFree(p);
+    delete ctx;
+}
+
+}  // extern "C"

@@ -52,6 +52,11 @@ class _View(C.Structure):
                                   "pold", "phix", "phiz")]
 
 
+class _Grid3(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("lx", C.c_double), ("ly", C.c_double), ("lz", C.c_double)]
+
+
 class _Stats(C.Structure):
     _fields_ = [("steps_done", C.c_int64), ("jac_u", C.c_int32), ("jac_h", C.c_int32),
                 ("cg_iters", C.c_int32 * 4), ("cg_relres", C.c_double * 4),
@@ -115,6 +120,18 @@ def library() -> C.CDLL:
         lib.gea_net_adam.argtypes = [P, P, C.c_float]
         lib.gea_net_train_step.argtypes = [P, I, I, I, P, P, P, P, C.c_float, C.POINTER(C.c_float)]
         lib.gea_net_destroy.argtypes = [P]
+        lib.gea3d_create.argtypes = [C.POINTER(_Grid3), C.POINTER(_Const), C.POINTER(P)]
+        lib.gea3d_set_stream.argtypes = [P, P]
+        lib.gea3d_set_conservative.argtypes = [P, P, P, P, P, P, I]
+        lib.gea3d_step_async.argtypes = [P, I]
+        lib.gea3d_sync.argtypes = [P]
+        lib.gea3d_step.argtypes = [P, I]
+        lib.gea3d_get_state.argtypes = [P, P, P, P, P, P, P, P, I]
+        lib.gea3d_get_stats.argtypes = [P, C.POINTER(_Stats)]
+        lib.gea3d_profile_step.argtypes = [P, C.POINTER(_KTime), I, C.POINTER(I)]
+        lib.gea3d_last_error.argtypes = [P]
+        lib.gea3d_last_error.restype = C.c_char_p
+        lib.gea3d_destroy.argtypes = [P]
         lib.gea_net_destroy.restype = None
         _lib = lib
     return _lib
@@ -426,3 +443,85 @@ class Ensemble:
             self.close()
         except Exception:
             pass
+
+
+STATE3_FIELDS = ("rho", "u", "v", "w", "T", "p", "pp")
+
+
+class Solver3D:
+    """One context of the three-dimensional step (include/gea3d.h): cell
+    fields are (nz, ny, nx) float64 arrays, x fastest."""
+
+    def __init__(self, grid, const, mg_min_cells: int = 0, stream=None):
+        self.lib = library()
+        self.grid, self.const = grid, const
+        g = _Grid3(grid.nx, grid.ny, grid.nz, grid.lx, grid.ly, grid.lz)
+        c = _Const(const.R, const.cp, const.g, const.p0, const.mu, const.Pr, const.dt,
+                   const.n_corr, const.jac_rtol, const.jac_maxit, const.cg_rtol, const.cg_maxit,
+                   mg_min_cells, 0, 0.0, getattr(const, "cs", 0.0))
+        h = C.c_void_p()
+        rc = self.lib.gea3d_create(C.byref(g), C.byref(c), C.byref(h))
+        if rc != GEA_OK:
+            raise GeaError(rc, "gea3d_create failed")
+        self.h = h
+        if stream is not None:
+            self.set_stream(stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gea3d_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc: int):
+        if rc != GEA_OK:
+            msg = self.lib.gea3d_last_error(self.h)
+            raise GeaError(rc, msg.decode() if msg else "")
+
+    def set_stream(self, stream):
+        s = getattr(stream, "cuda_stream", stream)
+        self._check(self.lib.gea3d_set_stream(self.h, C.c_void_p(s or 0)))
+
+    def set_conservative(self, fields: Dict):
+        mem = MEM_DEVICE if _is_device(fields["rho"]) else MEM_HOST
+        ptrs = [_addr(fields[k]) for k in ("rho", "rhou", "rhov", "rhow", "rhoe")]
+        self._check(self.lib.gea3d_set_conservative(self.h, *ptrs, mem))
+
+    def get_state(self, out: Optional[Dict] = None) -> Dict:
+        g = self.grid
+        if out is None:
+            out = {k: np.empty((g.nz, g.ny, g.nx)) for k in STATE3_FIELDS}
+        mem = MEM_DEVICE if _is_device(next(iter(out.values()))) else MEM_HOST
+        ptrs = [_addr(out[k]) if k in out else None for k in STATE3_FIELDS]
+        self._check(self.lib.gea3d_get_state(self.h, *ptrs, mem))
+        return out
+
+    def step(self, n: int = 1):
+        self._check(self.lib.gea3d_step(self.h, int(n)))
+
+    def step_async(self, n: int = 1):
+        self._check(self.lib.gea3d_step_async(self.h, int(n)))
+
+    def sync(self):
+        self._check(self.lib.gea3d_sync(self.h))
+
+    def stats(self) -> Dict:
+        s = _Stats()
+        self._check(self.lib.gea3d_get_stats(self.h, C.byref(s)))
+        n = self.const.n_corr
+        return {"steps_done": s.steps_done, "jac_u": s.jac_u, "jac_h": s.jac_h,
+                "cg_iters": list(s.cg_iters)[:n], "cg_relres": list(s.cg_relres)[:n],
+                "status": s.status, "mg_levels": s.mg_levels, "launches": s.launches}
+
+    def profile_step(self) -> Dict[str, Dict]:
+        """One eagerly launched step with per-kernel CUDA-event totals."""
+        buf = (_KTime * 32)()
+        n = C.c_int32()
+        self._check(self.lib.gea3d_profile_step(self.h, buf, 32, C.byref(n)))
+        return {buf[i].name.decode(): {"launches": buf[i].launches, "cells": buf[i].cells, "ms": buf[i].ms}
+                for i in range(min(n.value, 32))}

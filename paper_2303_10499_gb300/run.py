@@ -6,6 +6,7 @@ per-kernel times of each step.
         [--mixed] [--graph] [--eager]
     python -m paper_2303_10499_gb300.run --ensemble 12 --steps 2
     python -m paper_2303_10499_gb300.run --conv 16,16,0 --h 2048 --w 4096 --steps 5
+    python -m paper_2303_10499_gb300.run --workload bubble3d_192x192x96 --steps 3 [--eager]
 
 --eager advances every step with gea_profile_step: the kernels of the CUDA
 graph launched one by one from the host, each bracketed by CUDA events (the
@@ -44,7 +45,10 @@ def main(argv=None):
     if args.ensemble:
         return run_ensemble(args)
     wl = W.get(args.workload)
-    s = gea.Solver(wl.grid, wl.const, graph=args.graph, mixed=args.mixed)
+    if isinstance(wl.grid, W.Grid3):
+        s = gea.Solver3D(wl.grid, wl.const)
+    else:
+        s = gea.Solver(wl.grid, wl.const, graph=args.graph, mixed=args.mixed)
     s.set_conservative(wl.fields)
     per_kernel = {}
     t0 = time.perf_counter()

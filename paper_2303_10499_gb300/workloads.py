@@ -421,6 +421,7 @@ WORKLOADS = {
     "les400": lambda: les_member(400),
     # three dimensions
     "bubble3d_64x64x32": lambda: bubble3d(64, 64, 32, 0.05, 20),
+    "bubble3d_192x192x96": lambda: bubble3d(192, 192, 96, 0.05, 20),
     "bubble3d_512x512x256": lambda: bubble3d(512, 512, 256, 0.05, 200),
 }
 

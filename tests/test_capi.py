@@ -79,3 +79,36 @@ def test_create_rejects_bad_flags_and_mixed_tolerance():
         with pytest.raises(gea.GeaError) as ei:
             gea.Solver(wl.grid, wl.const, **kw)
         assert ei.value.code == gea.GEA_ERR_INVAL, kw
+
+
+def test_grid3_struct_matches_header():
+    import subprocess
+    import tempfile
+    from paper_2303_10499_gb300 import gea
+    code = r'''
+#include <stdio.h>
+#include "gea3d.h"
+int main(void){printf("%zu\n", sizeof(gea3d_grid)); return 0;}
+'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "s.c")
+        open(c, "w").write(code)
+        exe = os.path.join(d, "s")
+        subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
+        size = int(subprocess.check_output([exe]))
+    assert size == ctypes.sizeof(gea._Grid3)
+
+
+def test_create3_rejects_bad_arguments():
+    """gea3d_create validates sizes and constants before any CUDA call."""
+    from paper_2303_10499_gb300 import gea
+    from paper_2303_10499_gb300 import workloads as W
+    c = W.Constants(dt=0.2)
+    for g in (W.Grid3(3, 8, 8, 1.0, 1.0, 1.0), W.Grid3(8, 8, 2, 1.0, 1.0, 1.0),
+              W.Grid3(8, 8, 8, 1.0, -1.0, 1.0)):
+        with pytest.raises(gea.GeaError) as ei:
+            gea.Solver3D(g, c)
+        assert ei.value.code == gea.GEA_ERR_INVAL
+    with pytest.raises(gea.GeaError) as ei:
+        gea.Solver3D(W.Grid3(8, 8, 8, 1.0, 1.0, 1.0), W.Constants(dt=0.2, cs=0.17))
+    assert ei.value.code == gea.GEA_ERR_INVAL
