@@ -472,7 +472,7 @@ def run_ensemble(args):
 # Per-cell model of the three-dimensional kernels (same conventions as
 # KERNEL_MODEL; coarsening and restriction per coarse cell).
 KERNEL_MODEL_3D = {
-    "g3_pred": (30, 101, "f64"),
+    "g3_pred": (31, 102, "f64"),
     "g3_mom": (23, 93, "f64"),
     "g3_enth_rhs": (16, 141, "f64"),
     "g3_enth": (17, 31, "f64"),
@@ -486,9 +486,10 @@ KERNEL_MODEL_3D = {
     "g3_mg_coarse": (7, 17, "f64"),
     "g3_mg_up": (7.125, 20, "f64"),
     "g3_mg_single": (6, 20, "f64"),
-    "g3_pspmv": (8, 17, "f64"),
+    "g3_pupd": (3, 2, "f64"),
+    "g3_spmv": (6, 15, "f64"),
     "g3_update": (6, 6, "f64"),
-    "g3_correct": (20, 89, "f64"),
+    "g3_correct": (20, 61, "f64"),
 }
 
 

@@ -43,6 +43,7 @@ struct Geo {
     int nx, ny, nz, P;
     double dx, dy, dz;
     double idx, idy, idz, idx2, idy2, idz2, ivol;   // 1/dx, ..., 1/dx^2, ..., 1/(dx dy dz)
+    double ax, ay, az;                              // face areas dy dz, dx dz, dx dy
 };
 
 __host__ __device__ inline long long id3(const Geo &G, int i, int j, int k)
@@ -62,8 +63,15 @@ struct St {
 // a on the x-, y- and z-faces (zero on walls).
 struct Lev {
     Geo G;
-    double *c, *d, *ax, *ay, *az, *r, *e, *e2;
-    double *w;   // omega / d (damped Jacobi weight)
+    double *c, *d, *ax, *ay, *az, *r, *e2;   // e2: the preconditioned residual z
+};
+
+// FP32 level of the multigrid preconditioner (on the finest level the twin
+// of the FP64 operator; r, e2 unused there): w = omega/d, e and e2 the
+// smoothed corrections.
+struct Lev32 {
+    Geo G;
+    float *c, *d, *ax, *ay, *az, *w, *r, *e, *e2;
 };
 
 // The transport operator T(X) = (rho1/dt) X + C(X) - mu L(X) of the step as
@@ -95,6 +103,7 @@ struct Args {
     St S, N;
     double *rho1, *dinvu, *dinvh, *bu, *bv, *bw, *ua, *va, *wa, *ub, *vb, *wb, *bh, *ha, *hb;
     double *rho2, *psi, *Dx, *Dy, *Dz, *Hx, *Hy, *Hz, *b, *p0, *p1, *q;
+    double *dtr1;   // dt / rho1
     Cf cf;
     Sc *sc;
     double *part;
@@ -102,6 +111,7 @@ struct Args {
 };
 
 __device__ __forceinline__ double ld(const double *p) { return __ldg(p); }
+__device__ __forceinline__ float ldf(const float *p) { return __ldg(p); }
 
 // Cell (i,j,k) of the thread, or false beyond the box.
 __device__ __forceinline__ bool cell(const Geo &G, int &i, int &j, int &k)
@@ -224,24 +234,25 @@ __global__ void k_derive(Geo G, Phy F, const double *rho, const double *ru, cons
 __device__ __forceinline__ double fforce(const double *pp, const double *rho, long long q, long long s,
                                          double inv, double gz)
 {
-    return (ld(&pp[q]) - ld(&pp[q - s])) * inv - gz * (ld(&rho[q]) - ld(&rho[q - s])) * inv;
+    return fma(-gz, ld(&rho[q]) - ld(&rho[q - s]), ld(&pp[q]) - ld(&pp[q - s])) * inv;
 }
 
-// Cell averages of the face forces in x, y, z of cell (i,j,k).
+// The face forces of cell (i,j,k): its west, south and bottom faces in fl
+// (zero on walls) and the cell averages of the two faces per direction in g.
 __device__ void cell_forces(const Geo &G, const Phy &F, const double *pp, const double *rho, int i, int j,
-                            int k, double &gx, double &gy, double &gz)
+                            int k, double (&fl)[3], double (&g)[3])
 {
     const long long q = id3(G, i, j, k), sx = 1, sy = G.P, sz = (long long)G.P * (G.ny + 1);
-    const double zc = (k + 0.5) * G.dz, idx = G.idx, idy = G.idy, idz = G.idz;
-    const double fw = i > 0 ? fforce(pp, rho, q, sx, idx, F.g * zc) : 0.0;
-    const double fe = i + 1 < G.nx ? fforce(pp, rho, q + sx, sx, idx, F.g * zc) : 0.0;
-    const double fs = j > 0 ? fforce(pp, rho, q, sy, idy, F.g * zc) : 0.0;
-    const double fn = j + 1 < G.ny ? fforce(pp, rho, q + sy, sy, idy, F.g * zc) : 0.0;
-    const double fb = k > 0 ? fforce(pp, rho, q, sz, idz, F.g * (k * G.dz)) : 0.0;
-    const double ft = k + 1 < G.nz ? fforce(pp, rho, q + sz, sz, idz, F.g * ((k + 1) * G.dz)) : 0.0;
-    gx = 0.5 * (fw + fe);
-    gy = 0.5 * (fs + fn);
-    gz = 0.5 * (fb + ft);
+    const double gzc = F.g * ((k + 0.5) * G.dz);
+    fl[0] = i > 0 ? fforce(pp, rho, q, sx, G.idx, gzc) : 0.0;
+    const double fe = i + 1 < G.nx ? fforce(pp, rho, q + sx, sx, G.idx, gzc) : 0.0;
+    fl[1] = j > 0 ? fforce(pp, rho, q, sy, G.idy, gzc) : 0.0;
+    const double fn = j + 1 < G.ny ? fforce(pp, rho, q + sy, sy, G.idy, gzc) : 0.0;
+    fl[2] = k > 0 ? fforce(pp, rho, q, sz, G.idz, F.g * (k * G.dz)) : 0.0;
+    const double ft = k + 1 < G.nz ? fforce(pp, rho, q + sz, sz, G.idz, F.g * ((k + 1) * G.dz)) : 0.0;
+    g[0] = 0.5 * (fl[0] + fe);
+    g[1] = 0.5 * (fl[1] + fn);
+    g[2] = 0.5 * (fl[2] + ft);
 }
 
 __device__ __forceinline__ void fin_pred(Sc *sc, const double (&t)[3])
@@ -294,8 +305,10 @@ __global__ void k_pred(Args a)
         cf.c[10][q] = -(pt + 7.0 * pb) * i12 - mz;
         cf.c[11][q] = (7.0 * pt + pb) * i12 - mz;
         cf.c[12][q] = -pt * i12;
-        double gx, gy, gz;
-        cell_forces(G, F, a.S.pp, a.S.rho, i, j, k, gx, gy, gz);
+        double fl[3], gc[3];
+        cell_forces(G, F, a.S.pp, a.S.rho, i, j, k, fl, gc);
+        const double gx = gc[0], gy = gc[1], gz = gc[2];
+        a.dtr1[q] = F.dt / rho1;
         const double u = ld(&a.S.u[q]), v = ld(&a.S.v[q]), w = ld(&a.S.w[q]);
         const double bu = r * u * F.idt - gx, bv = r * v * F.idt - gy, bw = r * w * F.idt - gz;
         a.bu[q] = bu; a.bv[q] = bv; a.bw[q] = bw;
@@ -476,7 +489,7 @@ __global__ void k_enth(Args a, const double *hi, double *ho, int second)
 
 // EOS update (eqs. step3_2sd, step3_3sd): T^{n+1} = T^n + (h^{n+1} - h^n)/cp,
 // psi = 1/(R T^{n+1}), rho2 = psi p^n, and c = psi/dt of the fine level.
-__global__ void k_eos(Args a, Lev L, const double *h1)
+__global__ void k_eos(Args a, Lev L, Lev32 m, const double *h1)
 {
     if (a.sc->status) return;
     int i, j, k;
@@ -490,14 +503,16 @@ __global__ void k_eos(Args a, Lev L, const double *h1)
     a.N.h[q] = hq;
     a.rho2[q] = ld(&a.S.p[q]) * psi;
     a.psi[q] = psi;
-    L.c[q] = psi * F.idt;
+    const double c = psi * F.idt;
+    L.c[q] = c;
+    m.c[q] = (float)c;
 }
 
 // Face coefficients of the fine level: D_f = dt rho2_f / rho1_f with face
 // means of the two cells, on the cell's west, south and bottom faces (zero
 // on walls; the last cells also zero the east, north and top wall faces),
 // and a_f = D_f / Delta^2.
-__global__ void k_faces(Args a, Lev L)
+__global__ void k_faces(Args a, Lev L, Lev32 m)
 {
     if (a.sc->status) return;
     int i, j, k;
@@ -511,14 +526,16 @@ __global__ void k_faces(Args a, Lev L)
     const double Ds = j > 0 ? D(q - sy) : 0.0;
     const double Db = k > 0 ? D(q - sz) : 0.0;
     a.Dx[q] = Dw; a.Dy[q] = Ds; a.Dz[q] = Db;
-    L.ax[q] = Dw * G.idx2; L.ay[q] = Ds * G.idy2; L.az[q] = Db * G.idz2;
-    if (i == G.nx - 1) { a.Dx[q + sx] = 0.0; L.ax[q + sx] = 0.0; }
-    if (j == G.ny - 1) { a.Dy[q + sy] = 0.0; L.ay[q + sy] = 0.0; }
-    if (k == G.nz - 1) { a.Dz[q + sz] = 0.0; L.az[q + sz] = 0.0; }
+    const double ax = Dw * G.idx2, ay = Ds * G.idy2, az = Db * G.idz2;
+    L.ax[q] = ax; L.ay[q] = ay; L.az[q] = az;
+    m.ax[q] = (float)ax; m.ay[q] = (float)ay; m.az[q] = (float)az;
+    if (i == G.nx - 1) { a.Dx[q + sx] = 0.0; L.ax[q + sx] = 0.0; m.ax[q + sx] = 0.0f; }
+    if (j == G.ny - 1) { a.Dy[q + sy] = 0.0; L.ay[q + sy] = 0.0; m.ay[q + sy] = 0.0f; }
+    if (k == G.nz - 1) { a.Dz[q + sz] = 0.0; L.az[q + sz] = 0.0; m.az[q + sz] = 0.0f; }
 }
 
 // Diagonal d = c + the six face coefficients, and the Jacobi weight omega/d.
-__global__ void k_diag(Lev L, Sc *sc)
+__global__ void k_diag(Lev L, Lev32 m, Sc *sc)
 {
     if (sc->status) return;
     int i, j, k;
@@ -528,39 +545,8 @@ __global__ void k_diag(Lev L, Sc *sc)
     const double d = ld(&L.c[q]) + (ld(&L.ax[q]) + ld(&L.ax[q + 1])) + (ld(&L.ay[q]) + ld(&L.ay[q + sy])) +
                      (ld(&L.az[q]) + ld(&L.az[q + sz]));
     L.d[q] = d;
-    L.w[q] = kOmega / d;
-}
-
-// Galerkin coarsening (restriction = mean over the 8 children, piecewise-
-// constant prolongation): c_C = mean of the children's c, a coarse face =
-// (1/8) sum of its 4 fine faces, d_C = c_C + sum of its faces. One thread
-// per coarse cell.
-__global__ void k_coarsen(Lev f, Lev c)
-{
-    int I, J, K;
-    if (!cell(c.G, I, J, K)) return;
-    const Geo &G = f.G, &H = c.G;
-    const long long Q = id3(H, I, J, K);
-    double cs = 0.0, fx0 = 0.0, fx1 = 0.0, fy0 = 0.0, fy1 = 0.0, fz0 = 0.0, fz1 = 0.0;
-    for (int dk = 0; dk < 2; ++dk)
-        for (int dj = 0; dj < 2; ++dj)
-            for (int di = 0; di < 2; ++di) {
-                const int i = 2 * I + di, j = 2 * J + dj, k = 2 * K + dk;
-                const long long q = id3(G, i, j, k);
-                cs += ld(&f.c[q]);
-                if (di == 0) fx0 += ld(&f.ax[q]); else fx1 += ld(&f.ax[q + 1]);
-                if (dj == 0) fy0 += ld(&f.ay[q]); else fy1 += ld(&f.ay[q + G.P]);
-                if (dk == 0) fz0 += ld(&f.az[q]); else fz1 += ld(&f.az[q + (long long)G.P * (G.ny + 1)]);
-            }
-    const double cc = 0.125 * cs;
-    c.c[Q] = cc;
-    c.ax[Q] = 0.125 * fx0; c.ay[Q] = 0.125 * fy0; c.az[Q] = 0.125 * fz0;
-    if (I == H.nx - 1) c.ax[Q + 1] = 0.125 * fx1;
-    if (J == H.ny - 1) c.ay[Q + H.P] = 0.125 * fy1;
-    if (K == H.nz - 1) c.az[Q + (long long)H.P * (H.ny + 1)] = 0.125 * fz1;
-    const double d = cc + 0.125 * (fx0 + fx1 + fy0 + fy1 + fz0 + fz1);
-    c.d[Q] = d;
-    c.w[Q] = kOmega / d;
+    m.d[q] = (float)d;
+    m.w[q] = (float)(kOmega / d);
 }
 
 }  // namespace g3
@@ -654,42 +640,98 @@ __global__ void k_helm_rhs(Args a, Lev L, const double *xin, double *xout, int c
     if (gsum<2>(acc, red, a.part, &a.sc->counters[C_HELM], tot)) fin_helm(a.sc, tot, a.ctol2, corr);
 }
 
-// ---- multigrid V(1,1) cycle ----
+// ---- multigrid V(1,1) cycle in FP32 (the preconditioner of the FP64 CG) ----
+//
+// The preconditioner only shapes the search directions: the CG residual and
+// its stopping test stay FP64, so the converged pressure is that of the FP64
+// system. Every level's operator, weights and vectors are FP32 twins (Lev32);
+// the finest level reads the FP64 residual and writes z in FP64.
+
+template <class XF>
+__device__ __forceinline__ float helm32(const Lev32 &L, XF xf, int i, int j, int k)
+{
+    const Geo &G = L.G;
+    const long long q = id3(G, i, j, k), sy = G.P, sz = (long long)G.P * (G.ny + 1);
+    float t = ldf(&L.d[q]) * xf(q, i, j, k);
+    if (i > 0) t -= ldf(&L.ax[q]) * xf(q - 1, i - 1, j, k);
+    if (i + 1 < G.nx) t -= ldf(&L.ax[q + 1]) * xf(q + 1, i + 1, j, k);
+    if (j > 0) t -= ldf(&L.ay[q]) * xf(q - sy, i, j - 1, k);
+    if (j + 1 < G.ny) t -= ldf(&L.ay[q + sy]) * xf(q + sy, i, j + 1, k);
+    if (k > 0) t -= ldf(&L.az[q]) * xf(q - sz, i, j, k - 1);
+    if (k + 1 < G.nz) t -= ldf(&L.az[q + sz]) * xf(q + sz, i, j, k + 1);
+    return t;
+}
+
+__device__ __forceinline__ float tof(double v) { return (float)v; }
+__device__ __forceinline__ float tof(float v) { return v; }
+
+// Galerkin coarsening (restriction = mean over the 8 children, piecewise-
+// constant prolongation): c_C = mean of the children's c, a coarse face =
+// (1/8) sum of its 4 fine faces, d_C = c_C + sum of its faces. One thread
+// per coarse cell; sums in FP64, stored FP32.
+__global__ void k_coarsen(Lev32 f, Lev32 c)
+{
+    int I, J, K;
+    if (!cell(c.G, I, J, K)) return;
+    const Geo &G = f.G, &H = c.G;
+    const long long Q = id3(H, I, J, K);
+    double cs = 0.0, fx0 = 0.0, fx1 = 0.0, fy0 = 0.0, fy1 = 0.0, fz0 = 0.0, fz1 = 0.0;
+    for (int dk = 0; dk < 2; ++dk)
+        for (int dj = 0; dj < 2; ++dj)
+            for (int di = 0; di < 2; ++di) {
+                const int i = 2 * I + di, j = 2 * J + dj, k = 2 * K + dk;
+                const long long q = id3(G, i, j, k);
+                cs += ldf(&f.c[q]);
+                if (di == 0) fx0 += ldf(&f.ax[q]); else fx1 += ldf(&f.ax[q + 1]);
+                if (dj == 0) fy0 += ldf(&f.ay[q]); else fy1 += ldf(&f.ay[q + G.P]);
+                if (dk == 0) fz0 += ldf(&f.az[q]); else fz1 += ldf(&f.az[q + (long long)G.P * (G.ny + 1)]);
+            }
+    const double cc = 0.125 * cs;
+    c.c[Q] = (float)cc;
+    c.ax[Q] = (float)(0.125 * fx0); c.ay[Q] = (float)(0.125 * fy0); c.az[Q] = (float)(0.125 * fz0);
+    if (I == H.nx - 1) c.ax[Q + 1] = (float)(0.125 * fx1);
+    if (J == H.ny - 1) c.ay[Q + H.P] = (float)(0.125 * fy1);
+    if (K == H.nz - 1) c.az[Q + (long long)H.P * (H.ny + 1)] = (float)(0.125 * fz1);
+    const double d = cc + 0.125 * (fx0 + fx1 + fy0 + fy1 + fz0 + fz1);
+    c.d[Q] = (float)d;
+    c.w[Q] = (float)(kOmega / d);
+}
 
 // Pre-smoothing from zero, e = (omega/d) r, and restriction of r - A e to
 // the coarse level (mean of the 8 children). One thread per coarse cell.
-__global__ void k_mg_down(Lev f, Lev c, double omega, Sc *sc)
+template <class RT>
+__global__ void k_mg_down(Lev32 f, const RT *r, Lev32 c, Sc *sc)
 {
     if (over(sc, L_CG)) return;
     int I, J, K;
     if (!cell(c.G, I, J, K)) return;
     const Geo &G = f.G;
-    auto e = [&](long long q, int, int, int) { return ld(&f.w[q]) * ld(&f.r[q]); };
-    double s = 0.0;
+    auto e = [&](long long q, int, int, int) { return ldf(&f.w[q]) * tof(__ldg(&r[q])); };
+    float s = 0.0f;
     for (int dk = 0; dk < 2; ++dk)
         for (int dj = 0; dj < 2; ++dj)
             for (int di = 0; di < 2; ++di) {
                 const int i = 2 * I + di, j = 2 * J + dj, k = 2 * K + dk;
                 const long long q = id3(G, i, j, k);
                 f.e[q] = e(q, i, j, k);
-                s += ld(&f.r[q]) - helm(f, e, i, j, k);
+                s += tof(__ldg(&r[q])) - helm32(f, e, i, j, k);
             }
-    c.r[id3(c.G, I, J, K)] = 0.125 * s;
+    c.r[id3(c.G, I, J, K)] = 0.125f * s;
 }
 
 // Coarsest level: damped Jacobi sweep (first: from zero).
-__global__ void k_mg_coarse(Lev L, const double *ein, double *eout, int first, Sc *sc)
+__global__ void k_mg_coarse(Lev32 L, const float *ein, float *eout, int first, Sc *sc)
 {
     if (over(sc, L_CG)) return;
     int i, j, k;
     if (!cell(L.G, i, j, k)) return;
     const long long q = id3(L.G, i, j, k);
-    const double w = ld(&L.w[q]);
+    const float w = ldf(&L.w[q]);
     if (first) {
-        eout[q] = w * ld(&L.r[q]);
+        eout[q] = w * ldf(&L.r[q]);
         return;
     }
-    eout[q] = ld(&ein[q]) + w * (ld(&L.r[q]) - helm(L, [&](long long qq, int, int, int) { return ld(&ein[qq]); }, i, j, k));
+    eout[q] = ldf(&ein[q]) + w * (ldf(&L.r[q]) - helm32(L, [&](long long qq, int, int, int) { return ldf(&ein[qq]); }, i, j, k));
 }
 
 __device__ __forceinline__ void fin_rz(Sc *sc, double t)
@@ -699,8 +741,9 @@ __device__ __forceinline__ void fin_rz(Sc *sc, double t)
 }
 
 // Prolongation e' = e + P e_c and post-smoothing z = e' + (omega/d)(r - A e')
-// into out; on the finest level acc += r.z.
-__global__ void k_mg_up(Lev f, const double *ec, Geo cg, double *out, int finest, Sc *sc, double *part)
+// into out; on the finest level (FP64 r and z) acc += r.z in FP64.
+template <class RT, class OT>
+__global__ void k_mg_up(Lev32 f, const RT *r, const float *ec, Geo cg, OT *out, int finest, Sc *sc, double *part)
 {
     if (over(sc, L_CG)) return;
     __shared__ double red[NT];
@@ -710,19 +753,19 @@ __global__ void k_mg_up(Lev f, const double *ec, Geo cg, double *out, int finest
         const Geo &G = f.G;
         const long long q = id3(G, i, j, k);
         auto ef = [&](long long qq, int ii, int jj, int kk) {
-            return ld(&f.e[qq]) + ld(&ec[id3(cg, ii >> 1, jj >> 1, kk >> 1)]);
+            return ldf(&f.e[qq]) + ldf(&ec[id3(cg, ii >> 1, jj >> 1, kk >> 1)]);
         };
-        const double rq = ld(&f.r[q]);
-        const double z = ef(q, i, j, k) + ld(&f.w[q]) * (rq - helm(f, ef, i, j, k));
-        out[q] = z;
-        acc[0] = rq * z;
+        const RT rq = __ldg(&r[q]);
+        const float z = ef(q, i, j, k) + ldf(&f.w[q]) * (tof(rq) - helm32(f, ef, i, j, k));
+        out[q] = (OT)z;
+        acc[0] = (double)rq * (double)z;
     }
     if (!finest) return;
     if (gsum<1>(acc, red, part, &sc->counters[C_RZ], tot)) fin_rz(sc, tot[0]);
 }
 
 // One level only: z = e + (omega/d)(r - A e), e = (omega/d) r; acc += r.z.
-__global__ void k_mg_single(Lev f, double *out, Sc *sc, double *part)
+__global__ void k_mg_single(Lev32 f, const double *r, double *out, Sc *sc, double *part)
 {
     if (over(sc, L_CG)) return;
     __shared__ double red[NT];
@@ -730,33 +773,44 @@ __global__ void k_mg_single(Lev f, double *out, Sc *sc, double *part)
     int i, j, k;
     if (cell(f.G, i, j, k)) {
         const long long q = id3(f.G, i, j, k);
-        auto e = [&](long long qq, int, int, int) { return ld(&f.w[qq]) * ld(&f.r[qq]); };
-        const double rq = ld(&f.r[q]);
-        const double z = e(q, i, j, k) + ld(&f.w[q]) * (rq - helm(f, e, i, j, k));
-        out[q] = z;
-        acc[0] = rq * z;
+        auto e = [&](long long qq, int, int, int) { return ldf(&f.w[qq]) * (float)__ldg(&r[qq]); };
+        const double rq = __ldg(&r[q]);
+        const float z = e(q, i, j, k) + ldf(&f.w[q]) * ((float)rq - helm32(f, e, i, j, k));
+        out[q] = (double)z;
+        acc[0] = rq * (double)z;
     }
     if (gsum<1>(acc, red, part, &sc->counters[C_RZ], tot)) fin_rz(sc, tot[0]);
 }
 
 // ---- CG steps (directions alternate between p0 and p1 by parity) ----
 
-__global__ void k_pspmv(Args a, Lev L)
+// p = z + beta p_old (the new direction into the other buffer)
+__global__ void k_pupd(Args a, Lev L)
+{
+    Sc *sc = a.sc;
+    if (over(sc, L_CG)) return;
+    int i, j, k;
+    if (!cell(L.G, i, j, k)) return;
+    const int it = sc->cg_it;
+    const double *pold = (it & 1) ? a.p1 : a.p0;
+    double *pnew = (it & 1) ? a.p0 : a.p1;
+    const long long q = id3(L.G, i, j, k);
+    pnew[q] = fma(sc->beta, ld(&pold[q]), ld(&L.e2[q]));
+}
+
+// q = A p, acc += p.q; alpha = rz / p.q
+__global__ void k_spmv(Args a, Lev L)
 {
     Sc *sc = a.sc;
     if (over(sc, L_CG)) return;
     __shared__ double red[NT];
     double acc[1] = {0.0}, tot[1];
-    const int it = sc->cg_it;
-    const double *pold = (it & 1) ? a.p1 : a.p0;
-    double *pnew = (it & 1) ? a.p0 : a.p1;
-    const double beta = sc->beta;
+    const double *p = (sc->cg_it & 1) ? a.p0 : a.p1;
     int i, j, k;
     if (cell(L.G, i, j, k)) {
         const long long q = id3(L.G, i, j, k);
-        auto p = [&](long long qq, int, int, int) { return fma(beta, ld(&pold[qq]), ld(&L.e2[qq])); };
-        const double pq = p(q, i, j, k), Ap = helm(L, p, i, j, k);
-        pnew[q] = pq;
+        const double pq = ld(&p[q]);
+        const double Ap = helm(L, [&](long long qq, int, int, int) { return ld(&p[qq]); }, i, j, k);
         a.q[q] = Ap;
         acc[0] = pq * Ap;
     }
@@ -808,25 +862,21 @@ __global__ void k_correct(Args a)
     const Geo &G = a.G;
     const Phy &F = a.F;
     const long long q = id3(G, i, j, k), sx = 1, sy = G.P, sz = (long long)G.P * (G.ny + 1);
-    double gx, gy, gz;
-    cell_forces(G, F, a.N.pp, a.rho2, i, j, k, gx, gy, gz);
-    const double zc = (k + 0.5) * G.dz;
-    const double c1 = F.dt / ld(&a.rho1[q]);
+    double fl[3], gc[3];
+    cell_forces(G, F, a.N.pp, a.rho2, i, j, k, fl, gc);
+    const double c1 = ld(&a.dtr1[q]);
     const double hx = ld(&a.Hx[q]), hy = ld(&a.Hy[q]), hz = ld(&a.Hz[q]);
-    a.N.u[q] = c1 * (hx - gx);
-    a.N.v[q] = c1 * (hy - gy);
-    a.N.w[q] = c1 * (hz - gz);
-    const double pn = ld(&a.N.pp[q]) - ld(&a.rho2[q]) * F.g * zc;
+    a.N.u[q] = c1 * (hx - gc[0]);
+    a.N.v[q] = c1 * (hy - gc[1]);
+    a.N.w[q] = c1 * (hz - gc[2]);
+    const double pn = fma(-ld(&a.rho2[q]), F.g * ((k + 0.5) * G.dz), ld(&a.N.pp[q]));
     a.N.p[q] = pn;
     a.N.rho[q] = pn * ld(&a.psi[q]);
     a.N.pold[q] = ld(&a.S.p[q]);
-    const double idx = G.idx, idy = G.idy, idz = G.idz;
-    a.N.phix[q] = i > 0 ? ld(&a.Dx[q]) * (0.5 * (hx + ld(&a.Hx[q - sx])) -
-                                           fforce(a.N.pp, a.rho2, q, sx, idx, F.g * zc)) * G.dy * G.dz : 0.0;
-    a.N.phiy[q] = j > 0 ? ld(&a.Dy[q]) * (0.5 * (hy + ld(&a.Hy[q - sy])) -
-                                           fforce(a.N.pp, a.rho2, q, sy, idy, F.g * zc)) * G.dx * G.dz : 0.0;
-    a.N.phiz[q] = k > 0 ? ld(&a.Dz[q]) * (0.5 * (hz + ld(&a.Hz[q - sz])) -
-                                           fforce(a.N.pp, a.rho2, q, sz, idz, F.g * (k * G.dz))) * G.dx * G.dy : 0.0;
+    // F_f = D_f (H_f - G_f) |A_f| on the west, south and bottom faces
+    a.N.phix[q] = i > 0 ? ld(&a.Dx[q]) * fma(0.5, hx + ld(&a.Hx[q - sx]), -fl[0]) * G.ax : 0.0;
+    a.N.phiy[q] = j > 0 ? ld(&a.Dy[q]) * fma(0.5, hy + ld(&a.Hy[q - sy]), -fl[1]) * G.ay : 0.0;
+    a.N.phiz[q] = k > 0 ? ld(&a.Dz[q]) * fma(0.5, hz + ld(&a.Hz[q - sz]), -fl[2]) * G.az : 0.0;
     if (i == G.nx - 1) a.N.phix[q + sx] = 0.0;
     if (j == G.ny - 1) a.N.phiy[q + sy] = 0.0;
     if (k == G.nz - 1) a.N.phiz[q + sz] = 0.0;
@@ -878,9 +928,11 @@ struct gea3d_ctx {
     St S[2];
     double *rho1, *dinvu, *dinvh, *bu, *bv, *bw, *ua, *va, *wa, *ub, *vb, *wb, *bh, *ha, *hb;
     double *rho2, *psi, *Dx, *Dy, *Dz, *Hx, *Hy, *Hz, *b, *p0, *p1, *q;
+    double *dtr1;                         // dt / rho1
     Cf cf;                                // transport stencil weights
     double *stage = nullptr;              // dense conservative fields (5 arrays)
-    std::vector<Lev> L;
+    std::vector<Lev> L;                   // the FP64 fine-level operator
+    std::vector<Lev32> M;                 // the FP32 multigrid hierarchy
     Sc *sc = nullptr;
     double *part = nullptr;
     cudaGraph_t graph[2] = {nullptr, nullptr};
@@ -920,6 +972,7 @@ Geo make_geo(int nx, int ny, int nz, double lx, double ly, double lz)
     G.idx = 1.0 / G.dx; G.idy = 1.0 / G.dy; G.idz = 1.0 / G.dz;
     G.idx2 = 1.0 / (G.dx * G.dx); G.idy2 = 1.0 / (G.dy * G.dy); G.idz2 = 1.0 / (G.dz * G.dz);
     G.ivol = 1.0 / (G.dx * G.dy * G.dz);
+    G.ax = G.dy * G.dz; G.ay = G.dx * G.dz; G.az = G.dx * G.dy;
     return G;
 }
 
@@ -946,6 +999,7 @@ Args args_of(gea3d_ctx *c, int from)
     a.rho2 = c->rho2; a.psi = c->psi; a.Dx = c->Dx; a.Dy = c->Dy; a.Dz = c->Dz;
     a.Hx = c->Hx; a.Hy = c->Hy; a.Hz = c->Hz; a.b = c->b; a.p0 = c->p0; a.p1 = c->p1; a.q = c->q;
     a.cf = c->cf;
+    a.dtr1 = c->dtr1;
     a.sc = c->sc; a.part = c->part;
     a.jtol2 = c->C.jac_rtol * c->C.jac_rtol;
     a.ctol2 = c->C.cg_rtol * c->C.cg_rtol;
@@ -1028,36 +1082,45 @@ int eager_while3(gea3d_ctx *ctx, cudaStream_t s, int which, int maxtrips, Body b
     return GEA_OK;
 }
 
-// z = M^-1 r on the finest level (one V(1,1) cycle); returns launches
+// z = M^-1 r on the finest level (one FP32 V(1,1) cycle); returns launches
 int vcycle(gea3d_ctx *ctx, const Args &a, cudaStream_t st, Trace3 *tr)
 {
-    Lev *L = ctx->L.data();
-    const int nlev = (int)ctx->L.size();
+    Lev32 *M = ctx->M.data();
+    Lev &F = ctx->L[0];
+    const int nlev = (int)ctx->M.size();
     if (nlev == 1) {
-        traced(tr, "g3_mg_single", L[0].G, st, [&] {
-            k_mg_single<<<grid_of(L[0].G), kBlk, 0, st>>>(L[0], L[0].e2, a.sc, a.part);
+        traced(tr, "g3_mg_single", F.G, st, [&] {
+            k_mg_single<<<grid_of(F.G), kBlk, 0, st>>>(M[0], F.r, F.e2, a.sc, a.part);
         });
         return 1;
     }
     int n = 0;
-    for (int l = 0; l + 1 < nlev; ++l, ++n)
-        traced(tr, "g3_mg_down", L[l + 1].G, st, [&] {
-            k_mg_down<<<grid_of(L[l + 1].G), kBlk, 0, st>>>(L[l], L[l + 1], kOmega, a.sc);
+    traced(tr, "g3_mg_down", M[1].G, st, [&] {
+        k_mg_down<double><<<grid_of(M[1].G), kBlk, 0, st>>>(M[0], F.r, M[1], a.sc);
+    });
+    ++n;
+    for (int l = 1; l + 1 < nlev; ++l, ++n)
+        traced(tr, "g3_mg_down", M[l + 1].G, st, [&] {
+            k_mg_down<float><<<grid_of(M[l + 1].G), kBlk, 0, st>>>(M[l], M[l].r, M[l + 1], a.sc);
         });
-    Lev &C = L[nlev - 1];
+    Lev32 &C = M[nlev - 1];
     for (int s = 0; s < kCoarseSweeps; ++s, ++n) {
-        double *out = ((kCoarseSweeps - 1 - s) % 2 == 0) ? C.e2 : C.e;
-        const double *in = (out == C.e2) ? C.e : C.e2;
+        float *out = ((kCoarseSweeps - 1 - s) % 2 == 0) ? C.e2 : C.e;
+        const float *in = (out == C.e2) ? C.e : C.e2;
         traced(tr, "g3_mg_coarse", C.G, st, [&] {
             k_mg_coarse<<<grid_of(C.G), kBlk, 0, st>>>(C, in, out, s == 0, a.sc);
         });
     }
-    for (int l = nlev - 2; l >= 0; --l, ++n)
-        traced(tr, "g3_mg_up", L[l].G, st, [&] {
-            k_mg_up<<<grid_of(L[l].G), kBlk, 0, st>>>(L[l], L[l + 1].e2, L[l + 1].G, L[l].e2, l == 0, a.sc,
-                                                      a.part);
+    for (int l = nlev - 2; l >= 1; --l, ++n)
+        traced(tr, "g3_mg_up", M[l].G, st, [&] {
+            k_mg_up<float, float><<<grid_of(M[l].G), kBlk, 0, st>>>(M[l], M[l].r, M[l + 1].e2, M[l + 1].G,
+                                                                     M[l].e2, 0, a.sc, a.part);
         });
-    return n;
+    traced(tr, "g3_mg_up", F.G, st, [&] {
+        k_mg_up<double, double><<<grid_of(F.G), kBlk, 0, st>>>(M[0], F.r, M[1].e2, M[1].G, F.e2, 1, a.sc,
+                                                                a.part);
+    });
+    return n + 1;
 }
 
 // The kernel sequence of one step reading slot `from` (Section 3: Step 1,
@@ -1068,7 +1131,8 @@ int record3(gea3d_ctx *ctx, int from, cudaStream_t s, bool graph, Trace3 *tr)
 {
     const Args a = args_of(ctx, from);
     Lev *L = ctx->L.data();
-    const int nlev = (int)ctx->L.size();
+    Lev32 *M = ctx->M.data();
+    const int nlev = (int)ctx->M.size();
     const Geo &G = ctx->G;
     const dim3 grid = grid_of(G);
     const int jtrips = (ctx->C.jac_maxit + 1) / 2;
@@ -1092,14 +1156,14 @@ int record3(gea3d_ctx *ctx, int from, cudaStream_t s, bool graph, Trace3 *tr)
         k_ctl<<<1, 1, 0, bs>>>(a.sc, h, gr, L_ENTH, jtrips, 3);
     });
     if (rc) return rc;
-    traced(tr, "g3_eos", G, s, [&] { k_eos<<<grid, kBlk, 0, s>>>(a, L[0], a.ha); }); ++fixed;
-    traced(tr, "g3_faces", G, s, [&] { k_faces<<<grid, kBlk, 0, s>>>(a, L[0]); }); ++fixed;
-    traced(tr, "g3_diag", G, s, [&] { k_diag<<<grid, kBlk, 0, s>>>(L[0], a.sc); }); ++fixed;
+    traced(tr, "g3_eos", G, s, [&] { k_eos<<<grid, kBlk, 0, s>>>(a, L[0], M[0], a.ha); }); ++fixed;
+    traced(tr, "g3_faces", G, s, [&] { k_faces<<<grid, kBlk, 0, s>>>(a, L[0], M[0]); }); ++fixed;
+    traced(tr, "g3_diag", G, s, [&] { k_diag<<<grid, kBlk, 0, s>>>(L[0], M[0], a.sc); }); ++fixed;
     for (int l = 0; l + 1 < nlev; ++l, ++fixed)
-        traced(tr, "g3_coarsen", L[l + 1].G, s, [&] {
-            k_coarsen<<<grid_of(L[l + 1].G), kBlk, 0, s>>>(L[l], L[l + 1]);
+        traced(tr, "g3_coarsen", M[l + 1].G, s, [&] {
+            k_coarsen<<<grid_of(M[l + 1].G), kBlk, 0, s>>>(M[l], M[l + 1]);
         });
-    const int body_cg = (nlev == 1 ? 3 : 2 + (nlev - 1) + kCoarseSweeps + (nlev - 1)) + 1;
+    const int body_cg = (nlev == 1 ? 4 : 3 + (nlev - 1) + kCoarseSweeps + (nlev - 1)) + 1;
     for (int c = 0; c < ctx->C.n_corr; ++c) {
         const double *U = c == 0 ? a.ua : a.N.u, *V = c == 0 ? a.va : a.N.v, *W = c == 0 ? a.wa : a.N.w;
         traced(tr, "g3_H", G, s, [&] { k_H<<<grid, kBlk, 0, s>>>(a, U, V, W); }); ++fixed;
@@ -1109,7 +1173,8 @@ int record3(gea3d_ctx *ctx, int from, cudaStream_t s, bool graph, Trace3 *tr)
         ++fixed;
         fixed += vcycle(ctx, a, s, tr);
         rc = loop(L_CG, ctx->C.cg_maxit, [&](cudaStream_t bs, cudaGraphConditionalHandle h) {
-            traced(tr, "g3_pspmv", G, bs, [&] { k_pspmv<<<grid, kBlk, 0, bs>>>(a, L[0]); });
+            traced(tr, "g3_pupd", G, bs, [&] { k_pupd<<<grid, kBlk, 0, bs>>>(a, L[0]); });
+            traced(tr, "g3_spmv", G, bs, [&] { k_spmv<<<grid, kBlk, 0, bs>>>(a, L[0]); });
             traced(tr, "g3_update", G, bs, [&] { k_update<<<grid, kBlk, 0, bs>>>(a, L[0], a.N.pp, ctx->C.cg_maxit); });
             vcycle(ctx, a, bs, tr);
             k_ctl<<<1, 1, 0, bs>>>(a.sc, h, gr, L_CG, ctx->C.cg_maxit, body_cg);
@@ -1200,14 +1265,28 @@ int gea3d_create(const gea3d_grid *grid, const gea_constants *c, gea3d_ctx **out
                      &ctx->p1, &ctx->q};
     for (auto pp : sc) *pp = take(E);
     for (int m = 0; m < NCF; ++m) ctx->cf.c[m] = take(E);
+    ctx->dtr1 = take(E);
     ctx->stage = take(5 * (size_t)grid->nx * grid->ny * grid->nz);
-    for (const Geo &g : lg) {
+    {
         Lev l;
-        l.G = g;
-        const size_t e = elems(g);
-        l.c = take(e); l.d = take(e); l.ax = take(e); l.ay = take(e); l.az = take(e);
-        l.r = take(e); l.e = take(e); l.e2 = take(e); l.w = take(e);
+        l.G = ctx->G;
+        l.c = take(E); l.d = take(E); l.ax = take(E); l.ay = take(E); l.az = take(E);
+        l.r = take(E); l.e2 = take(E);
         ctx->L.push_back(l);
+    }
+    auto takef = [&](size_t n) -> float * {
+        // FP32 arrays: half as many doubles, rounded up
+        return reinterpret_cast<float *>(take((n + 1) / 2));
+    };
+    for (size_t lv = 0; lv < lg.size(); ++lv) {
+        Lev32 m;
+        m.G = lg[lv];
+        const size_t e = elems(lg[lv]);
+        m.c = takef(e); m.d = takef(e); m.ax = takef(e); m.ay = takef(e); m.az = takef(e);
+        m.w = takef(e); m.e = takef(e);
+        m.r = lv ? takef(e) : nullptr;
+        m.e2 = lv ? takef(e) : nullptr;
+        ctx->M.push_back(m);
     }
     ctx->part = take(3 * nblocks(ctx->G) + 64);
     ctx->sc = reinterpret_cast<Sc *>(take((sizeof(Sc) + 7) / 8));
@@ -1328,7 +1407,7 @@ int gea3d_get_stats(gea3d_ctx *ctx, gea_stats *s)
     s->jac_h = h.last_sweeps[1];
     for (int c = 0; c < 4; ++c) { s->cg_iters[c] = h.last_cg_iters[c]; s->cg_relres[c] = h.last_cg_relres[c]; }
     s->status = h.last_status;
-    s->mg_levels = (int)ctx->L.size();
+    s->mg_levels = (int)ctx->M.size();
     s->launches = h.launches;
     s->driver = 0;
     return GEA_OK;
