@@ -180,12 +180,16 @@ class ClockSampler:
 STEP_SOURCES = ("gea_internal.cuh", "gea_tiles.cuh", "gea_kernels.cu", "gea_persistent.cu")
 
 
-def kernels_sha256():
+# the sources of the three-dimensional step kernels
+STEP_SOURCES_3D = ("gea_internal.cuh", "gea3d.cu")
+
+
+def kernels_sha256(sources=STEP_SOURCES):
     """Hash of the step kernels' CUDA sources (any change invalidates the
     recorded counters)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2303_10499_gb300", "csrc")
-    for f in STEP_SOURCES:
+    for f in sources:
         h.update(f.encode())
         h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()
@@ -194,10 +198,13 @@ def kernels_sha256():
 def traffic_for(kernel, workload):
     """DRAM bytes per launch of `kernel` on `workload` from the committed ncu
     summary (profiles/traffic.json), if it was taken on the current CUDA
-    sources (else None)."""
+    sources (else None). The 3D kernels (g3_*) have their own hash."""
     try:
         t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-        if t.get("kernels_sha256") != kernels_sha256():
+        if kernel.startswith("g3_"):
+            if t.get("kernels3d_sha256") != kernels_sha256(STEP_SOURCES_3D):
+                return None
+        elif t.get("kernels_sha256") != kernels_sha256():
             return None
         return t.get("per_launch_bytes", {}).get(workload, {}).get(kernel)
     except Exception:
@@ -474,7 +481,8 @@ def run_ensemble(args):
 KERNEL_MODEL_3D = {
     "g3_pred": (31, 102, "f64"),
     "g3_mom": (23, 93, "f64"),
-    "g3_enth_rhs": (16, 141, "f64"),
+    "g3_kin": (4, 6, "f64"),
+    "g3_enth_rhs": (15, 45, "f64"),
     "g3_enth": (17, 31, "f64"),
     "g3_eos": (9, 7, "f64"),
     "g3_faces": (8, 15, "f64"),

@@ -104,6 +104,7 @@ struct Args {
     double *rho1, *dinvu, *dinvh, *bu, *bv, *bw, *ua, *va, *wa, *ub, *vb, *wb, *bh, *ha, *hb;
     double *rho2, *psi, *Dx, *Dy, *Dz, *Hx, *Hy, *Hz, *b, *p0, *p1, *q;
     double *dtr1;   // dt / rho1
+    double *kin;    // K1 = |u1|^2 / 2
     Cf cf;
     Sc *sc;
     double *part;
@@ -168,31 +169,58 @@ __device__ double divg(const Args &a, int i, int j, int k)
            G.ivol;
 }
 
-// Deterministic grid sum of NV values per thread (3D grid of 32 x 8 blocks):
-// true in thread 0 of the last block, with the totals in tot.
+// Deterministic grid sum of NV values per thread (3D grid of 32 x 8 blocks)
+// in two levels: the last block of each group of kGroup blocks adds its
+// group's block totals, the last group adds the group totals, each in a fixed
+// order. True in thread 0 of the very last block, with the totals in tot.
+// part holds kCntSlots doubles of group counters (zero between launches),
+// then NV x blocks block totals, then NV x groups group totals.
+constexpr int kGroup = 1024;
+constexpr int kCntSlots = 2048;   // 4096 group counters
 template <int NV>
 __device__ bool gsum(const double (&v)[NV], double *red, double *part, unsigned *counter, double (&tot)[NV])
 {
-    __shared__ int last;
+    __shared__ int flag;
     const int tid = threadIdx.x + threadIdx.y * TX;
     const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     const int nb = gridDim.x * gridDim.y * gridDim.z;
+    const int ng = (nb + kGroup - 1) / kGroup, grp = bid / kGroup, g0 = grp * kGroup;
+    const int gn = min(kGroup, nb - g0);
+    unsigned *gcnt = reinterpret_cast<unsigned *>(part);
+    double *p1 = part + kCntSlots, *p2 = p1 + (size_t)NV * nb;
     double bt[NV];
     gea::block_sum<NV>(v, red, bt);
     if (tid == 0) {
 #pragma unroll
-        for (int m = 0; m < NV; ++m) part[(size_t)m * nb + bid] = bt[m];
+        for (int m = 0; m < NV; ++m) p1[(size_t)m * nb + bid] = bt[m];
         __threadfence();
-        last = atomicAdd(counter, 1u) == (unsigned)nb - 1u;
+        flag = atomicAdd(&gcnt[grp], 1u) == (unsigned)gn - 1u;
     }
     __syncthreads();
-    if (!last) return false;
+    if (!flag) return false;
     __threadfence();
     double s[NV];
 #pragma unroll
     for (int m = 0; m < NV; ++m) {
         s[m] = 0.0;
-        for (int bb = tid; bb < nb; bb += NT) s[m] += __ldcg(&part[(size_t)m * nb + bb]);
+        for (int bb = tid; bb < gn; bb += NT) s[m] += __ldcg(&p1[(size_t)m * nb + g0 + bb]);
+    }
+    double gt[NV];
+    gea::block_sum<NV>(s, red, gt);
+    if (tid == 0) {
+        gcnt[grp] = 0u;
+#pragma unroll
+        for (int m = 0; m < NV; ++m) p2[(size_t)m * ng + grp] = gt[m];
+        __threadfence();
+        flag = atomicAdd(counter, 1u) == (unsigned)ng - 1u;
+    }
+    __syncthreads();
+    if (!flag) return false;
+    __threadfence();
+#pragma unroll
+    for (int m = 0; m < NV; ++m) {
+        s[m] = 0.0;
+        for (int bb = tid; bb < ng; bb += NT) s[m] += __ldcg(&p2[(size_t)m * ng + bb]);
     }
     gea::block_sum<NV>(s, red, tot);
     if (tid == 0) *counter = 0u;
@@ -404,23 +432,21 @@ __global__ void k_mom(Args a, const double *ui, const double *vi, const double *
 
 // ---- Step 2 (eq. step3_sd) ----
 
-template <int BC>
-__device__ __forceinline__ double sq_at(const Args &a, const double *X, int i, int j, int k)
+// K1 = |u1|^2/2 per cell (eq. step1_3sd); its wall ghosts are the mirrored
+// cells' values (the squares of odd and even ghosts agree).
+__global__ void k_kin(Args a, const double *u1, const double *v1, const double *w1)
 {
-    const double v = at<BC>(a.G, a.F, X, i, j, k);
-    return v * v;
-}
-
-// K1 = |u1|^2/2 at a cell or ghost (the ghost's K is the mirrored cell's).
-__device__ __forceinline__ double K1at(const Args &a, const double *u, const double *v, const double *w, int i,
-                                      int j, int k)
-{
-    return 0.5 * (sq_at<U3>(a, u, i, j, k) + sq_at<V3>(a, v, i, j, k) + sq_at<W3>(a, w, i, j, k));
+    if (a.sc->status) return;
+    int i, j, k;
+    if (!cell(a.G, i, j, k)) return;
+    const long long q = id3(a.G, i, j, k);
+    const double u = ld(&u1[q]), v = ld(&v1[q]), w = ld(&w1[q]);
+    a.kin[q] = 0.5 * (u * u + v * v + w * w);
 }
 
 // Right-hand side of the enthalpy equation and its initial guess h^n:
 // (rho h + rho K - p^{n-1})/dt - rho1 K1/dt - C(K1) + p^n/dt - rho1 g w1.
-__global__ void k_enth_rhs(Args a, const double *u1, const double *v1, const double *w1)
+__global__ void k_enth_rhs(Args a, const double *w1)
 {
     if (a.sc->status) return;
     __shared__ double red[NT];
@@ -430,10 +456,10 @@ __global__ void k_enth_rhs(Args a, const double *u1, const double *v1, const dou
         const Geo &G = a.G;
         const Phy &F = a.F;
         const long long q = id3(G, i, j, k);
-        // C(K1) with K1 evaluated at the stencil points
+        // C(K1), fourth-order face values of K1 with even ghosts
         double s = 0.0;
-        const double Kc = K1at(a, u1, v1, w1, i, j, k);
-        auto K = [&](int ii, int jj, int kk) { return K1at(a, u1, v1, w1, ii, jj, kk); };
+        const double Kc = ld(&a.kin[q]);
+        auto K = [&](int ii, int jj, int kk) { return at<E3>(G, F, a.kin, ii, jj, kk); };
         if (i + 1 < G.nx) s += ld(&a.S.phix[id3(G, i + 1, j, k)]) * i4(K(i - 1, j, k), Kc, K(i + 1, j, k), K(i + 2, j, k));
         if (i > 0) s -= ld(&a.S.phix[id3(G, i, j, k)]) * i4(K(i - 2, j, k), K(i - 1, j, k), Kc, K(i + 1, j, k));
         if (j + 1 < G.ny) s += ld(&a.S.phiy[id3(G, i, j + 1, k)]) * i4(K(i, j - 1, k), Kc, K(i, j + 1, k), K(i, j + 2, k));
@@ -929,6 +955,7 @@ struct gea3d_ctx {
     double *rho1, *dinvu, *dinvh, *bu, *bv, *bw, *ua, *va, *wa, *ub, *vb, *wb, *bh, *ha, *hb;
     double *rho2, *psi, *Dx, *Dy, *Dz, *Hx, *Hy, *Hz, *b, *p0, *p1, *q;
     double *dtr1;                         // dt / rho1
+    double *kin;                          // K1
     Cf cf;                                // transport stencil weights
     double *stage = nullptr;              // dense conservative fields (5 arrays)
     std::vector<Lev> L;                   // the FP64 fine-level operator
@@ -1000,6 +1027,7 @@ Args args_of(gea3d_ctx *c, int from)
     a.Hx = c->Hx; a.Hy = c->Hy; a.Hz = c->Hz; a.b = c->b; a.p0 = c->p0; a.p1 = c->p1; a.q = c->q;
     a.cf = c->cf;
     a.dtr1 = c->dtr1;
+    a.kin = c->kin;
     a.sc = c->sc; a.part = c->part;
     a.jtol2 = c->C.jac_rtol * c->C.jac_rtol;
     a.ctol2 = c->C.cg_rtol * c->C.cg_rtol;
@@ -1149,7 +1177,8 @@ int record3(gea3d_ctx *ctx, int from, cudaStream_t s, bool graph, Trace3 *tr)
         k_ctl<<<1, 1, 0, bs>>>(a.sc, h, gr, L_MOM, jtrips, 3);
     });
     if (rc) return rc;
-    traced(tr, "g3_enth_rhs", G, s, [&] { k_enth_rhs<<<grid, kBlk, 0, s>>>(a, a.ua, a.va, a.wa); }); ++fixed;
+    traced(tr, "g3_kin", G, s, [&] { k_kin<<<grid, kBlk, 0, s>>>(a, a.ua, a.va, a.wa); }); ++fixed;
+    traced(tr, "g3_enth_rhs", G, s, [&] { k_enth_rhs<<<grid, kBlk, 0, s>>>(a, a.wa); }); ++fixed;
     rc = loop(L_ENTH, jtrips, [&](cudaStream_t bs, cudaGraphConditionalHandle h) {
         traced(tr, "g3_enth", G, bs, [&] { k_enth<<<grid, kBlk, 0, bs>>>(a, a.ha, a.hb, 0); });
         traced(tr, "g3_enth", G, bs, [&] { k_enth<<<grid, kBlk, 0, bs>>>(a, a.hb, a.ha, 1); });
@@ -1266,6 +1295,7 @@ int gea3d_create(const gea3d_grid *grid, const gea_constants *c, gea3d_ctx **out
     for (auto pp : sc) *pp = take(E);
     for (int m = 0; m < NCF; ++m) ctx->cf.c[m] = take(E);
     ctx->dtr1 = take(E);
+    ctx->kin = take(E);
     ctx->stage = take(5 * (size_t)grid->nx * grid->ny * grid->nz);
     {
         Lev l;
@@ -1288,7 +1318,14 @@ int gea3d_create(const gea3d_grid *grid, const gea_constants *c, gea3d_ctx **out
         m.e2 = lv ? takef(e) : nullptr;
         ctx->M.push_back(m);
     }
-    ctx->part = take(3 * nblocks(ctx->G) + 64);
+    {
+        const size_t nb = nblocks(ctx->G), ng = (nb + kGroup - 1) / kGroup;
+        if (ng > 2 * (size_t)kCntSlots) {
+            gea3d_destroy(ctx);
+            return GEA_ERR_INVAL;
+        }
+        ctx->part = take(kCntSlots + 3 * nb + 3 * ng + 64);
+    }
     ctx->sc = reinterpret_cast<Sc *>(take((sizeof(Sc) + 7) / 8));
     if (!ok) {
         gea3d_destroy(ctx);
