@@ -28,7 +28,7 @@ namespace {
 
 using namespace tiles;
 
-constexpr unsigned long long kSpinLimit = 1ull << 25;   // x ~64 ns: a few seconds
+constexpr unsigned long long kSpinLimit = 1ull << 23;   // polls of ~0.7 us each: a few seconds
 
 struct PersistArgs {
     StepArgs a[2];          // a[s] reads state slot s and writes slot s ^ 1
@@ -41,6 +41,21 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
+}
+
+// Arrival with acquire-release semantics: publishes this block's writes of
+// the phase (ordered before it by the block barrier) and observes those of
+// the blocks that arrived earlier.
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned *p, unsigned v)
+{
+    unsigned old;
+    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+__device__ __forceinline__ void red_add_release(unsigned *p, unsigned v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 __device__ __forceinline__ int rdi(const int *p) { return __ldcg(p); }
@@ -57,47 +72,45 @@ __device__ __forceinline__ int tid_of() { return threadIdx.x + threadIdx.y * BX;
 
 // The blocks that run one context's steps: this block's rank among them and
 // their number (the whole grid for one context; a contiguous share of the
-// grid per member in an ensemble launch).
+// grid per member in an ensemble launch), and the block's count of the
+// barrier generations it has passed (shared memory; every block passes the
+// same barriers, so it need not be re-read before each wait).
 struct Grp {
     int rank, nb;
+    unsigned *gen;
 };
 
 // Arrive and wait. The last block to arrive runs last() (all its threads)
-// and then releases the others.
+// and then releases the others by advancing the generation. Every data read
+// across blocks goes through L2 (ld.global.cg), so the acquire by thread 0
+// and the block barrier order them after the release.
 template <class Last>
 __device__ __forceinline__ void barrier_with(const Grp &g, Scal *sc, Last last)
 {
     __shared__ int am_last;
-    __shared__ unsigned gen0;
     const int tid = tid_of();
     // every thread of the block has finished its writes of this phase before
-    // thread 0 arrives (its fence then publishes them, cumulatively)
+    // thread 0 arrives (its release then publishes them, cumulatively)
     __syncthreads();
-    if (tid == 0) {
-        gen0 = ld_acquire(&sc->bar_gen);
-        __threadfence();
-        am_last = atomicAdd(&sc->bar_count, 1u) == (unsigned)g.nb - 1u;
-    }
+    if (tid == 0) am_last = atom_add_acq_rel(&sc->bar_count, 1u) == (unsigned)g.nb - 1u;
     __syncthreads();
     if (am_last) {
-        __threadfence();
         last();
         if (tid == 0) {
             sc->bar_count = 0u;
-            __threadfence();
-            atomicAdd(&sc->bar_gen, 1u);
+            red_add_release(&sc->bar_gen, 1u);
         }
     } else if (tid == 0) {
+        const unsigned gen0 = *g.gen;
         unsigned long long spins = 0;
         while (ld_acquire(&sc->bar_gen) == gen0) {
             if (++spins > kSpinLimit) {
                 atomicCAS(&sc->status, 0, GEA_ERR_TIMEOUT);
                 break;
             }
-            __nanosleep(64);
         }
-        __threadfence();
     }
+    if (tid == 0) *g.gen += 1u;
     __syncthreads();
 }
 
@@ -341,7 +354,12 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_persistent(PersistArgs P)
     // is sticky until the next set_state, which clears it
     if (rdi(&P.a[0].sc->status)) return;
     if (blockIdx.x == 0 && tid_of() == 0) P.a[0].sc->launches += 1;
-    const Grp g{(int)blockIdx.x, (int)gridDim.x};
+    // the generation before this launch's first barrier (no block can pass
+    // that barrier before every block has arrived at it)
+    __shared__ unsigned gen;
+    if (tid_of() == 0) gen = ld_acquire(&P.a[0].sc->bar_gen);
+    __syncthreads();
+    const Grp g{(int)blockIdx.x, (int)gridDim.x, &gen};
     for (int s = 0; s < P.nsteps; ++s) {
         const int slot = (P.first_slot + s) & 1;
         if (!run_step(P, P.a[slot], g, sm, red)) break;
@@ -378,8 +396,11 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_ensemble(const PersistArgs *Pm,
     }
     __syncthreads();
     const PersistArgs &P = *Ps;
-    const Grp g{(int)blockIdx.x - __ldg(&first[m]), __ldg(&first[m + 1]) - __ldg(&first[m])};
     Scal *sc = P.a[0].sc;
+    __shared__ unsigned gen;
+    if (tid == 0) gen = ld_acquire(&sc->bar_gen);
+    __syncthreads();
+    const Grp g{(int)blockIdx.x - __ldg(&first[m]), __ldg(&first[m + 1]) - __ldg(&first[m]), &gen};
     if (rdi(&sc->status)) return;
     if (g.rank == 0 && tid == 0) sc->launches += 1;
     for (int s = 0; s < P.nsteps; ++s) {
