@@ -29,6 +29,9 @@ namespace {
 using namespace tiles;
 
 constexpr unsigned long long kSpinLimit = 1ull << 23;   // polls of ~0.7 us each: a few seconds
+// values per thread a grid reduction may carry: the block-sum scratch after
+// the tile area holds kRedVals x NTHREADS doubles
+constexpr int kRedVals = 4;
 
 struct PersistArgs {
     StepArgs a[2];          // a[s] reads state slot s and writes slot s ^ 1
@@ -125,6 +128,7 @@ template <int NV, class Fin>
 __device__ __forceinline__ void rbar(const Grp &g, const double (&v)[NV], double *red, Scal *sc,
                                      double *partials, Fin fin)
 {
+    static_assert(NV <= kRedVals, "the block-sum scratch holds kRedVals values per thread");
     const int tid = tid_of();
     const int nb = g.nb;
     double bt[NV];
@@ -170,15 +174,20 @@ __device__ bool run_step(const PersistArgs &P, const StepArgs &a, const Grp &g, 
         gbar(g, sc);
         if (stop(sc)) return false;
     }
-    // ---- Step 1: continuity predictor, transport operator, momentum RHS ----
+    // ---- Step 1: continuity predictor, transport operator, momentum RHS,
+    // and the first Jacobi sweep of the momentum predictor (from u^n, which
+    // needs no barrier) into ua, wa ----
     {
-        double acc[2] = {0.0, 0.0};
-        for_tiles(g, G, [&](int bx, int bz) { ph_pred(a, bx, bz, acc); });
-        rbar<2>(g, acc, red, sc, a.partials, [&](const double (&t)[2]) {
-            fin_pred(sc, t);
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        for_tiles(g, G, [&](int bx, int bz) { ph_pred_sweep(a, sm, bx, bz, acc); });
+        rbar<4>(g, acc, red, sc, a.partials, [&](const double (&t)[4]) {
+            const double tb[2] = {t[0], t[1]}, tr[2] = {t[2], t[3]};
+            fin_pred(sc, tb);
             for (int c = 0; c < 4; ++c) { sc->cg_iters[c] = 0; sc->cg_relres[c] = 0.0; }
             sc->sweeps[1] = 0;
             sc->press_ns = 0ull;
+            fin_mom(sc, tr, a.jac_rtol2);
+            if (!sc->done[LOOP_MOM] && !sc->status && sc->sweeps[0] >= P.jac_maxit) sc->status = GEA_ERR_NOCONV;
         });
     }
     if (stop(sc)) return false;
@@ -186,7 +195,7 @@ __device__ bool run_step(const PersistArgs &P, const StepArgs &a, const Grp &g, 
     // the tolerance
     const double *uin = a.ua, *win = a.wa;
     double *uout = a.ub, *wout = a.wb;
-    for (;;) {
+    while (!rdi(&sc->done[LOOP_MOM])) {
         double acc[2] = {0.0, 0.0};
         for_tiles(g, G, [&](int bx, int bz) { ph_mom(a, uin, win, uout, wout, sm, bx, bz, acc); });
         rbar<2>(g, acc, red, sc, a.partials, [&](const double (&t)[2]) {
@@ -196,21 +205,27 @@ __device__ bool run_step(const PersistArgs &P, const StepArgs &a, const Grp &g, 
         const double *tu = uin, *tw = win;
         uin = uout; win = wout;
         uout = const_cast<double *>(tu); wout = const_cast<double *>(tw);
-        if (stop(sc) || rdi(&sc->done[LOOP_MOM])) break;
+        if (stop(sc)) break;
     }
     if (stop(sc)) return false;
     const double *u1 = uin, *w1 = win;
 
-    // ---- Step 2: enthalpy, temperature, rho^{n+2/3} ----
+    // ---- Step 2: enthalpy right-hand side with the first enthalpy sweep
+    // (from h^n) into ha, then temperature, rho^{n+2/3} ----
     {
-        double acc[1] = {0.0};
-        for_tiles(g, G, [&](int bx, int bz) { ph_enth_rhs(a, u1, w1, a.ha, sm, bx, bz, acc); });
-        rbar<1>(g, acc, red, sc, a.partials, [&](const double (&t)[1]) { fin_enth_rhs(sc, t); });
+        double acc[2] = {0.0, 0.0};
+        for_tiles(g, G, [&](int bx, int bz) { ph_enth_rhs_sweep(a, u1, w1, a.ha, sm, bx, bz, acc); });
+        rbar<2>(g, acc, red, sc, a.partials, [&](const double (&t)[2]) {
+            const double tb[1] = {t[0]}, tr[1] = {t[1]};
+            fin_enth_rhs(sc, tb);
+            fin_enth(sc, tr, a.jac_rtol2);
+            if (!sc->done[LOOP_ENTH] && !sc->status && sc->sweeps[1] >= P.jac_maxit) sc->status = GEA_ERR_NOCONV;
+        });
     }
     if (stop(sc)) return false;
     const double *hin = a.ha;
     double *hout = a.hb;
-    for (;;) {
+    while (!rdi(&sc->done[LOOP_ENTH])) {
         double acc[1] = {0.0};
         for_tiles(g, G, [&](int bx, int bz) { ph_enth(a, hin, hout, sm, bx, bz, acc); });
         rbar<1>(g, acc, red, sc, a.partials, [&](const double (&t)[1]) {
@@ -220,11 +235,14 @@ __device__ bool run_step(const PersistArgs &P, const StepArgs &a, const Grp &g, 
         const double *t = hin;
         hin = hout;
         hout = const_cast<double *>(t);
-        if (stop(sc) || rdi(&sc->done[LOOP_ENTH])) break;
+        if (stop(sc)) break;
     }
     if (stop(sc)) return false;
     const double *h1 = hin;
+    // the EOS update, and H(u^{n+1/3}) of the first corrector, which reads
+    // nothing the EOS phase writes
     for_tiles(g, G, [&](int bx, int bz) { ph_eos(a, L[0], h1, sm, bx, bz); });
+    for_tiles(g, G, [&](int bx, int bz) { ph_H(a, u1, w1, sm, bx, bz); });
     gbar(g, sc);
     for (int l = 0; l + 1 < nlev; ++l) {
         for_tiles(g, L[l + 1].G, [&](int bx, int bz) { ph_coarsen(L[l], L[l + 1], a.F.omega, bx, bz); });
@@ -238,10 +256,10 @@ __device__ bool run_step(const PersistArgs &P, const StepArgs &a, const Grp &g, 
 
     // ---- Step 3: PISO correctors ----
     for (int c = 0; c < P.n_corr; ++c) {
-        const double *U = c == 0 ? u1 : a.N.u;
-        const double *W = c == 0 ? w1 : a.N.w;
-        for_tiles(g, G, [&](int bx, int bz) { ph_H(a, U, W, sm, bx, bz); });
-        gbar(g, sc);
+        if (c > 0) {
+            for_tiles(g, G, [&](int bx, int bz) { ph_H(a, a.N.u, a.N.w, sm, bx, bz); });
+            gbar(g, sc);
+        }
         unsigned long long t0 = 0;
         if (g.rank == 0 && tid_of() == 0) t0 = globaltimer();
         {
@@ -368,7 +386,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_persistent(PersistArgs P)
     if (blockIdx.x == 0 && tid_of() == 0 && sc->status) sc->last_status = sc->status;
 }
 
-constexpr size_t kPersistSmem = (size_t)(kTileSmem + 2 * NTHREADS) * sizeof(double);
+constexpr size_t kPersistSmem = (size_t)(kTileSmem + kRedVals * NTHREADS) * sizeof(double);
 
 // An ensemble of independent contexts in one cooperative launch: member m
 // runs its steps on blocks first[m] .. first[m+1]-1 with its own grid
@@ -380,7 +398,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_ensemble(const PersistArgs *Pm,
     extern __shared__ double dsm[];
     double *sm = dsm;
     double *red = dsm + kTileSmem;
-    PersistArgs *Ps = reinterpret_cast<PersistArgs *>(dsm + kTileSmem + 2 * NTHREADS);
+    PersistArgs *Ps = reinterpret_cast<PersistArgs *>(dsm + kTileSmem + kRedVals * NTHREADS);
     const int tid = tid_of();
     int lo = 0, hi = nmem - 1;
     while (lo < hi) {

@@ -233,14 +233,19 @@ __device__ __forceinline__ void ph_les(const StepArgs &a, double *sm, int bx, in
 // guess, the FP64 residuals r0 = b - T(u^n) of both components, FP32 copies
 // of the operator, the reciprocals and r0, and the first FP32 Jacobi sweep
 // from zero, du = r0 / T_CC; acc += (r0_u^2, r0_w^2).
-template <bool MX>
+//
+// SW1 (FP64): also the first Jacobi sweep of the momentum predictor from the
+// guess u^n, r0 = b - T(u^n), u = u^n + r0 / T_CC into ua, wa (the stencil of
+// the cell is at hand and u^n needs no barrier); acc += (b_u^2, b_w^2,
+// r0_u^2, r0_w^2).
+template <bool MX, bool SW1 = false>
 __device__ __forceinline__ void ph_pred_t(const StepArgs &a, const MixedArgs &m, double *sm, int bx,
-                                          int bz, double (&acc)[2])
+                                          int bz, double (&acc)[SW1 ? 4 : 2])
 {
     const Geom &G = a.G;
     const Phys &F = a.F;
     const State &S = a.S;
-    if (MX) {
+    if (MX || SW1) {
         load_tile<BC_U, 2>(tile_at<2>(sm, 0), G, F, S.u, bx, bz);
         load_tile<BC_W, 2>(tile_at<2>(sm, 1), G, F, S.w, bx, bz);
         __syncthreads();
@@ -300,27 +305,36 @@ __device__ __forceinline__ void ph_pred_t(const StepArgs &a, const MixedArgs &m,
         const double bu = rq * u * F.idt - 0.5 * (gxw + gxe);
         const double bw = rq * w * F.idt - 0.5 * (gzs + gzn);
         a.rho1[q] = rho1;
+        const int y = threadIdx.y + 2, x = threadIdx.x + 2;
+        // T(X) at the cell from a halo-2 tile, in apply9's order
+        auto t9 = [&](const Tile<2> &t) {
+            double v = cC * t[y][x];
+            v = fma(cE1, t[y][x + 1], v);
+            v = fma(cW1, t[y][x - 1], v);
+            v = fma(cN1, t[y + 1][x], v);
+            v = fma(cS1, t[y - 1][x], v);
+            v = fma(cE2, t[y][x + 2], v);
+            v = fma(cW2, t[y][x - 2], v);
+            v = fma(cN2, t[y + 2][x], v);
+            v = fma(cS2, t[y - 2][x], v);
+            return v;
+        };
         if (!MX) {
             a.bu[q] = bu;
             a.bw[q] = bw;
-            a.ua[q] = u;
-            a.wa[q] = w;
             acc[0] = fma(bu, bu, acc[0]);
             acc[1] = fma(bw, bw, acc[1]);
+            if (SW1) {
+                const double r0u = bu - t9(tile_at<2>(sm, 0)), r0w = bw - t9(tile_at<2>(sm, 1));
+                a.ua[q] = fma(r0u, diu, u);
+                a.wa[q] = fma(r0w, diu, w);
+                acc[SW1 ? 2 : 0] = fma(r0u, r0u, acc[SW1 ? 2 : 0]);
+                acc[SW1 ? 3 : 1] = fma(r0w, r0w, acc[SW1 ? 3 : 1]);
+            } else {
+                a.ua[q] = u;
+                a.wa[q] = w;
+            }
         } else {
-            const int y = threadIdx.y + 2, x = threadIdx.x + 2;
-            auto t9 = [&](const Tile<2> &t) {
-                double v = cC * t[y][x];
-                v = fma(cE1, t[y][x + 1], v);
-                v = fma(cW1, t[y][x - 1], v);
-                v = fma(cN1, t[y + 1][x], v);
-                v = fma(cS1, t[y - 1][x], v);
-                v = fma(cE2, t[y][x + 2], v);
-                v = fma(cW2, t[y][x - 2], v);
-                v = fma(cN2, t[y + 2][x], v);
-                v = fma(cS2, t[y - 2][x], v);
-                return v;
-            };
             const double r0u = bu - t9(tile_at<2>(sm, 0)), r0w = bw - t9(tile_at<2>(sm, 1));
             m.T.cC[q] = (float)cC;
             m.T.cE1[q] = (float)cE1;
@@ -343,12 +357,17 @@ __device__ __forceinline__ void ph_pred_t(const StepArgs &a, const MixedArgs &m,
             acc[1] = fma(r0w, r0w, acc[1]);
         }
     }
-    if (MX) __syncthreads();
+    if (MX || SW1) __syncthreads();
 }
 
 __device__ __forceinline__ void ph_pred(const StepArgs &a, int bx, int bz, double (&acc)[2])
 {
     ph_pred_t<false>(a, MixedArgs{}, nullptr, bx, bz, acc);
+}
+
+__device__ __forceinline__ void ph_pred_sweep(const StepArgs &a, double *sm, int bx, int bz, double (&acc)[4])
+{
+    ph_pred_t<false, true>(a, MixedArgs{}, sm, bx, bz, acc);
 }
 
 // One Jacobi sweep of T(X) = b for two fields with wall rules BCA, BCB:
@@ -422,10 +441,12 @@ __device__ __forceinline__ void ph_mom(const StepArgs &a, const double *uin, con
 // MX: u^{n+1/3} = u^n + du (written to ua, wa), and instead of b_h and h0 the
 // FP64 residual r0 = b_h - T_h(h^n) (h^n with its wall rule), its FP32 copy
 // and the first FP32 sweep dh = r0 / T_h,CC; acc += r0^2 instead.
-template <bool MX>
+// SW1 (FP64): h0 receives the first Jacobi sweep from h^n instead of h^n,
+// r0 = b_h - T_h(h^n), h = h^n + r0 / T_h,CC; acc += (b_h^2, r0^2).
+template <bool MX, bool SW1 = false>
 __device__ __forceinline__ void ph_enth_rhs_t(const StepArgs &a, const MixedArgs &m, const double *u1,
                                               const double *w1, double *h0, double *sm, int bx,
-                                              int bz, double (&acc)[1])
+                                              int bz, double (&acc)[SW1 ? 2 : 1])
 {
     const Geom &G = a.G;
     const Phys &F = a.F;
@@ -438,6 +459,7 @@ __device__ __forceinline__ void ph_enth_rhs_t(const StepArgs &a, const MixedArgs
     } else {
         load_tile<BC_U, 2>(su, G, F, u1, bx, bz);
         load_tile<BC_W, 2>(sw, G, F, w1, bx, bz);
+        if (SW1) load_tile<BC_H, 2>(tile_at<2>(sm, 2), G, F, S.h, bx, bz);
     }
     __syncthreads();
     // K1 in place of u (ghost velocities give the mirrored cell's K); u1 and
@@ -471,8 +493,17 @@ __device__ __forceinline__ void ph_enth_rhs_t(const StepArgs &a, const MixedArgs
         const double bh = be - rho1 * K[y][x] * F.idt - c + ld(&S.p[q]) * F.idt - rho1 * F.g * w1c;
         if (!MX) {
             a.bh[q] = bh;
-            h0[q] = h;
             acc[0] = fma(bh, bh, acc[0]);
+            if (SW1) {
+                const Tile<2> &sh = tile_at<2>(sm, 2);
+                double t = apply9<2>(a.T, q, sh, y, x);
+                if (F.nuh != F.mu) t = fma(F.mu - F.nuh, lap5<2>(G, sh, y, x), t);
+                const double r0 = bh - t;
+                h0[q] = fma(r0, ld(&a.dinvh[q]), sh[y][x]);
+                acc[SW1 ? 1 : 0] = fma(r0, r0, acc[SW1 ? 1 : 0]);
+            } else {
+                h0[q] = h;
+            }
         } else {
             a.ua[q] = u1c;
             a.wa[q] = w1c;
@@ -493,6 +524,12 @@ __device__ __forceinline__ void ph_enth_rhs(const StepArgs &a, const double *u1,
                                             double *h0, double *sm, int bx, int bz, double (&acc)[1])
 {
     ph_enth_rhs_t<false>(a, MixedArgs{}, u1, w1, h0, sm, bx, bz, acc);
+}
+
+__device__ __forceinline__ void ph_enth_rhs_sweep(const StepArgs &a, const double *u1, const double *w1,
+                                                  double *h0, double *sm, int bx, int bz, double (&acc)[2])
+{
+    ph_enth_rhs_t<false, true>(a, MixedArgs{}, u1, w1, h0, sm, bx, bz, acc);
 }
 
 // One Jacobi sweep of (rho1/dt) h + C(h) - (mu/Pr) L(h) = b_h (dh/dz = -g on
