@@ -89,7 +89,8 @@ typedef struct gea_grid {
  *            cooperative kernel when the grid has at most 4 tiles (32 x 8
  *            cells) per block that fits on the GPU at once, where a phase is
  *            latency-bound, and the graph otherwise.
- *            GEA_FLAG_MIXED: mixed-precision step (CUDA graph driver). The
+ *            GEA_FLAG_MIXED: mixed-precision step (the driver is chosen as
+ *            for the FP64 step; with GEA_FLAG_GRAPH the graph). The
  *            state, the hydrostatic split p' = p + rho g z, the face forces,
  *            every right-hand side and H(u) stay FP64; each of the three
  *            linear solves becomes one defect correction: an FP64 residual
@@ -146,7 +147,8 @@ typedef struct gea_stats {
     int32_t mg_levels;         /* multigrid levels in use */
     int64_t launches;          /* kernel launches since the last set_state */
     int32_t driver;            /* 0: CUDA graph, 1: persistent cooperative kernel,
-                                  2: mixed-precision CUDA graph */
+                                  2: mixed-precision CUDA graph,
+                                  3: mixed-precision persistent kernel */
     int32_t reserved;
 } gea_stats;
 

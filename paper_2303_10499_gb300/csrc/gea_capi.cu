@@ -590,8 +590,8 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
     // step driver: the persistent kernel pays off while a phase is a few
     // tiles per resident block (its phases are latency-bound); on larger
     // grids the per-phase kernels keep more blocks resident per SM
-    if (!(c->flags & (GEA_FLAG_GRAPH | GEA_FLAG_MIXED | GEA_FLAG_KEEP_R0))) {
-        const int pmax = persistent_max_blocks();
+    if (!(c->flags & (GEA_FLAG_GRAPH | GEA_FLAG_KEEP_R0))) {
+        const int pmax = ctx->mixed ? persistent_mixed_max_blocks() : persistent_max_blocks();
         cudaGetLastError();
         if (pmax > 0 && (long long)nb <= (long long)kPersistTilesPerBlock * pmax)
             ctx->pers_blocks = pmax < (int)nb ? pmax : (int)nb;
@@ -666,9 +666,14 @@ int gea_step_async(gea_ctx *ctx, int32_t n)
     if (ctx->pers_blocks > 0 && !ctx->net) {
         StepArgs a[2] = {step_args(ctx, 0), step_args(ctx, 1)};
         const int first = (int)((ctx->base + ctx->steps_at_sync) & 1);
-        CK(launch_persistent(a, ctx->L.data(), (int)ctx->L.size(), kCoarseSweeps, ctx->C.n_corr,
-                             ctx->C.jac_maxit, ctx->C.cg_maxit, first, n, ctx->pers_blocks,
-                             ctx->stream));
+        if (ctx->mixed)
+            CK(launch_persistent_mixed(a, ctx->L[0], ctx->mx, ctx->Lf.data(), (int)ctx->Lf.size(), kCoarseSweeps,
+                                       ctx->C.n_corr, ctx->C.jac_maxit, ctx->C.cg_maxit, first, n,
+                                       ctx->pers_blocks, ctx->stream));
+        else
+            CK(launch_persistent(a, ctx->L.data(), (int)ctx->L.size(), kCoarseSweeps, ctx->C.n_corr,
+                                 ctx->C.jac_maxit, ctx->C.cg_maxit, first, n, ctx->pers_blocks,
+                                 ctx->stream));
         ctx->steps_at_sync += n;
         return GEA_OK;
     }
@@ -772,7 +777,8 @@ int gea_get_stats(gea_ctx *ctx, gea_stats *s)
     s->status = h.last_status;
     s->mg_levels = ctx->mixed ? (int)ctx->Lf.size() : (int)ctx->L.size();
     s->launches = h.launches;
-    s->driver = ctx->mixed ? 2 : (ctx->pers_blocks > 0 && !ctx->net) ? 1 : 0;
+    const bool pers = ctx->pers_blocks > 0 && !ctx->net;
+    s->driver = ctx->mixed ? (pers ? 3 : 2) : pers ? 1 : 0;
     return GEA_OK;
 }
 

@@ -326,6 +326,13 @@ int launch_mx_cg_iter(const StepArgs &a, const MixedArgs &m, LevelF *L, int nlev
 void launch_mx_p_apply(const StepArgs &a, const MixedArgs &m, cudaStream_t st, Tracer *tr);
 // persistent cooperative step kernel (gea_persistent.cu)
 int persistent_max_blocks();
+// The mixed-precision step (GEA_FLAG_MIXED) as one cooperative launch: the
+// FP64 finest level L0, the FP32 operator and vectors m, the FP32 hierarchy
+// Lf[0 .. nlev-1].
+int persistent_mixed_max_blocks();
+cudaError_t launch_persistent_mixed(const StepArgs a[2], const Level &L0, const MixedArgs &m, const LevelF *Lf,
+                                    int nlev, int ncoarse, int n_corr, int jac_maxit, int cg_maxit,
+                                    int first_slot, int nsteps, int blocks, cudaStream_t st);
 cudaError_t launch_persistent(const StepArgs a[2], const Level *L, int nlev, int ncoarse, int n_corr,
                               int jac_maxit, int cg_maxit, int first_slot, int nsteps, int blocks,
                               cudaStream_t st);

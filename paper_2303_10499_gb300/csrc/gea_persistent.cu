@@ -123,19 +123,21 @@ __device__ __forceinline__ void gbar(const Grp &g, Scal *sc)
 }
 
 // Barrier with a deterministic grid-wide sum of NV per-thread values; fin(tot)
-// runs in one thread of the last block before the release.
-template <int NV, class Fin>
-__device__ __forceinline__ void rbar(const Grp &g, const double (&v)[NV], double *red, Scal *sc,
+// runs in one thread of the last block before the release. T is the type of
+// the per-thread values and of the block sums (FP32 for the inner solves of
+// the mixed-precision step); block partials and the total are FP64.
+template <int NV, class T, class Fin>
+__device__ __forceinline__ void rbar(const Grp &g, const T (&v)[NV], double *red, Scal *sc,
                                      double *partials, Fin fin)
 {
     static_assert(NV <= kRedVals, "the block-sum scratch holds kRedVals values per thread");
     const int tid = tid_of();
     const int nb = g.nb;
-    double bt[NV];
-    block_sum<NV>(v, red, bt);
+    T bt[NV];
+    block_sum<NV, T>(v, reinterpret_cast<T *>(red), bt);
     if (tid == 0) {
 #pragma unroll
-        for (int j = 0; j < NV; ++j) partials[(size_t)j * nb + g.rank] = bt[j];
+        for (int j = 0; j < NV; ++j) partials[(size_t)j * nb + g.rank] = (double)bt[j];
     }
     barrier_with(g, sc, [&] {
         double s[NV], tot[NV];
@@ -363,6 +365,223 @@ __device__ bool run_step(const PersistArgs &P, const StepArgs &a, const Grp &g, 
     return !stop(sc);
 }
 
+// FP32 data of the mixed-precision step for the persistent kernel: the
+// increments' operator, vectors and CG buffers, and the FP32 multigrid
+// hierarchy (nlev levels).
+struct MixedPersist {
+    MixedArgs m;
+    LevelF Lf[kMaxLevels];
+    int nlev;
+};
+
+// One mixed-precision time step (the phases of the graph's mixed step, in
+// its order): FP64 residuals, FP32 Jacobi and MG-CG solves of the
+// increments, FP64 updates. Returns false if the step did not complete.
+__device__ bool run_step_mixed(const PersistArgs &P, const MixedPersist &X, const StepArgs &a, const Grp &g,
+                               double *sm, double *red)
+{
+    Scal *sc = a.sc;
+    const Geom &G = a.G;
+    const MixedArgs &m = X.m;
+    const LevelF *L = X.Lf;
+    const int nlev = X.nlev;
+    const Level &L0 = P.L[0];
+
+    if (a.F.les_d2 > 0.0) {
+        for_tiles(g, G, [&](int bx, int bz) { ph_les(a, sm, bx, bz); });
+        gbar(g, sc);
+        if (stop(sc)) return false;
+    }
+    // ---- Step 1: FP64 residuals r0 = b - T(u^n), FP32 operator, first FP32
+    // sweep from zero ----
+    {
+        double acc[2] = {0.0, 0.0};
+        for_tiles(g, G, [&](int bx, int bz) { ph_pred_t<true>(a, m, sm, bx, bz, acc); });
+        rbar<2>(g, acc, red, sc, a.partials, [&](const double (&t)[2]) {
+            fin_pred(sc, t);
+            for (int c = 0; c < 4; ++c) { sc->cg_iters[c] = 0; sc->cg_relres[c] = 0.0; }
+            sc->sweeps[1] = 0;
+            sc->press_ns = 0ull;
+            sc->u1_slot = sc->h1_slot = 0;
+        });
+    }
+    if (stop(sc)) return false;
+    const float *ui = m.du[0], *wi = m.dw[0];
+    float *uo = m.du[1], *wo = m.dw[1];
+    for (;;) {
+        float acc[2] = {0.0f, 0.0f};
+        for_tiles(g, G, [&](int bx, int bz) {
+            ph_sweep2<float, BC_U, BC_W>(G, a.F, m.T, m.dinvu, m.r0u, m.r0w, ui, wi, uo, wo, sm, bx, bz, acc);
+        });
+        rbar<2>(g, acc, red, sc, a.partials, [&](const double (&t)[2]) {
+            fin_mom(sc, t, m.tol2);
+            if (!sc->done[LOOP_MOM] && !sc->status && sc->sweeps[0] >= P.jac_maxit) sc->status = GEA_ERR_NOCONV;
+        });
+        const float *tu = ui, *tw = wi;
+        ui = uo; wi = wo;
+        uo = const_cast<float *>(tu); wo = const_cast<float *>(tw);
+        if (stop(sc) || rdi(&sc->done[LOOP_MOM])) break;
+    }
+    if (stop(sc)) return false;
+
+    // ---- Step 2: u^{n+1/3} = u^n + du, the enthalpy residual at h^n and the
+    // first FP32 sweep; FP32 Jacobi on dh ----
+    {
+        MixedArgs mm = m;   // the momentum increments end in the buffers ui, wi
+        mm.du[0] = const_cast<float *>(ui);
+        mm.dw[0] = const_cast<float *>(wi);
+        double acc[1] = {0.0};
+        for_tiles(g, G, [&](int bx, int bz) {
+            ph_enth_rhs_t<true>(a, mm, nullptr, nullptr, nullptr, sm, bx, bz, acc);
+        });
+        rbar<1>(g, acc, red, sc, a.partials, [&](const double (&t)[1]) { fin_enth_rhs(sc, t); });
+    }
+    if (stop(sc)) return false;
+    const float *hi = m.dh[0];
+    float *ho = m.dh[1];
+    const float lc = (float)(a.F.mu - a.F.nuh);
+    for (;;) {
+        float acc[1] = {0.0f};
+        for_tiles(g, G, [&](int bx, int bz) {
+            ph_sweep1<float, BC_EVEN>(G, a.F, m.T, m.dinvh, m.r0h, lc, hi, ho, sm, bx, bz, acc);
+        });
+        rbar<1>(g, acc, red, sc, a.partials, [&](const double (&t)[1]) {
+            fin_enth(sc, t, m.tol2);
+            if (!sc->done[LOOP_ENTH] && !sc->status && sc->sweeps[1] >= P.jac_maxit) sc->status = GEA_ERR_NOCONV;
+        });
+        const float *t = hi;
+        hi = ho;
+        ho = const_cast<float *>(t);
+        if (stop(sc) || rdi(&sc->done[LOOP_ENTH])) break;
+    }
+    if (stop(sc)) return false;
+    // h^{n+1} = h^n + dh, the EOS update, the FP64 finest Helmholtz level and
+    // its FP32 copy; H(u^{n+1/3}) of the first corrector reads nothing of it
+    for_tiles(g, G, [&](int bx, int bz) { ph_eos_t<true>(a, L0, L[0], nullptr, hi, sm, bx, bz); });
+    for_tiles(g, G, [&](int bx, int bz) { ph_H(a, a.ua, a.wa, sm, bx, bz); });
+    gbar(g, sc);
+    for (int l = 0; l + 1 < nlev; ++l) {
+        for_tiles(g, L[l + 1].G, [&](int bx, int bz) { ph_coarsen<float>(L[l], L[l + 1], a.F.omega, bx, bz); });
+        gbar(g, sc);
+    }
+    if (stop(sc)) return false;
+
+    // ---- Step 3: PISO correctors, each pressure solve one defect correction ----
+    for (int c = 0; c < P.n_corr; ++c) {
+        if (c > 0) {
+            for_tiles(g, G, [&](int bx, int bz) { ph_H(a, a.N.u, a.N.w, sm, bx, bz); });
+            gbar(g, sc);
+        }
+        unsigned long long t0 = 0;
+        if (g.rank == 0 && tid_of() == 0) t0 = globaltimer();
+        {
+            double acc[2] = {0.0, 0.0};
+            const double *xin = c == 0 ? a.S.pp : a.N.pp;
+            for_tiles(g, G, [&](int bx, int bz) {
+                ph_helm_rhs_t<true>(a, L0, L[0], m, xin, a.N.pp, sm, bx, bz, acc);
+            });
+            rbar<2>(g, acc, red, sc, a.partials, [&](const double (&t)[2]) {
+                fin_helm_mixed(sc, t, a.cg_rtol2, c);
+            });
+        }
+        auto vcycle_levels = [&](int lfirst) {
+            for (int l = lfirst; l + 1 < nlev; ++l) {
+                for_tiles(g, L[l].G, [&](int bx, int bz) {
+                    ph_mg_down<float>(L[l], L[l + 1], a.F.omega, sm, bx, bz);
+                });
+                gbar(g, sc);
+            }
+            const LevelF &C = L[nlev - 1];
+            for (int s = 0; s < P.ncoarse; ++s) {
+                float *out = ((P.ncoarse - 1 - s) % 2 == 0) ? C.e2 : C.e;
+                const float *in = (out == C.e2) ? C.e : C.e2;
+                for_tiles(g, C.G, [&](int bx, int bz) { ph_mg_coarse<float>(C, in, out, s == 0, sm, bx, bz); });
+                gbar(g, sc);
+            }
+            const float *res0 = res_of(L[0], rdi(&sc->cg_it));
+            for (int l = nlev - 2; l >= 0; --l) {
+                float acc[1] = {0.0f};
+                const float *res = l == 0 ? res0 : L[l].r;
+                for_tiles(g, L[l].G, [&](int bx, int bz) {
+                    ph_mg_up<float>(L[l], res, L[l + 1].e2, L[l + 1].G.P, L[l].e2, sm, bx, bz, acc);
+                });
+                if (l > 0) gbar(g, sc);
+                else rbar<1>(g, acc, red, sc, a.partials, [&](const double (&t)[1]) { fin_rz(sc, t); });
+            }
+        };
+        if (!stop(sc) && !rdi(&sc->done[LOOP_CG])) {
+            if (nlev == 1) {
+                float acc[1] = {0.0f};
+                for_tiles(g, G, [&](int bx, int bz) { ph_mg_single<float>(L[0], L[0].e2, sm, bx, bz, acc); });
+                rbar<1>(g, acc, red, sc, a.partials, [&](const double (&t)[1]) { fin_rz(sc, t); });
+            } else {
+                vcycle_levels(0);
+            }
+        }
+        while (!stop(sc) && !rdi(&sc->done[LOOP_CG])) {
+            const int it = rdi(&sc->cg_it);
+            const float *pold = (it & 1) ? m.p1 : m.p0;
+            float *pnew = (it & 1) ? m.p0 : m.p1;
+            {
+                const double beta = rdd(&sc->beta);
+                float acc[1] = {0.0f};
+                for_tiles(g, G, [&](int bx, int bz) {
+                    ph_pspmv<float>(L[0], pold, pnew, m.q, beta, sm, bx, bz, acc);
+                });
+                rbar<1>(g, acc, red, sc, a.partials, [&](const double (&t)[1]) { fin_pq(sc, t); });
+            }
+            const double alpha = rdd(&sc->alpha);
+            auto cap = [&] {
+                if (!sc->done[LOOP_CG] && !sc->status && sc->cg_it >= P.cg_maxit) sc->status = GEA_ERR_NOCONV;
+            };
+            if (nlev == 1) {
+                float acc[2] = {0.0f, 0.0f};
+                for_tiles(g, G, [&](int bx, int bz) {
+                    ph_update_single<float>(L[0], m.q, res_of(L[0], it), res_of(L[0], it + 1), m.x, pnew, alpha,
+                                            sm, bx, bz, acc);
+                });
+                rbar<2>(g, acc, red, sc, a.partials, [&](const double (&t)[2]) {
+                    const double t0[1] = {t[0]}, t1[1] = {t[1]};
+                    fin_update(sc, t0, m.tol2);
+                    fin_rz(sc, t1);
+                    cap();
+                });
+            } else {
+                float acc[1] = {0.0f};
+                for_tiles(g, G, [&](int bx, int bz) {
+                    ph_update_down<float>(L[0], L[1], m.q, res_of(L[0], it), res_of(L[0], it + 1), m.x, pnew,
+                                          alpha, a.F.omega, sm, bx, bz, acc);
+                });
+                rbar<1>(g, acc, red, sc, a.partials, [&](const double (&t)[1]) {
+                    fin_update(sc, t, m.tol2);
+                    cap();
+                });
+                if (!stop(sc) && !rdi(&sc->done[LOOP_CG])) vcycle_levels(1);
+            }
+        }
+        if (stop(sc)) return false;
+        // p' += dp, then the FP64 correction
+        for_tiles(g, G, [&](int bx, int bz) { ph_p_apply(a, m, bx, bz); });
+        gbar(g, sc);
+        if (g.rank == 0 && tid_of() == 0) sc->press_ns += globaltimer() - t0;
+        for_tiles(g, G, [&](int bx, int bz) { ph_correct(a, sm, bx, bz); });
+        if (c + 1 < P.n_corr) gbar(g, sc);
+    }
+    barrier_with(g, sc, [&] {
+        if (tid_of() == 0 && !sc->status) {
+            sc->steps_done += 1;
+            sc->last_sweeps[0] = sc->sweeps[0];
+            sc->last_sweeps[1] = sc->sweeps[1];
+            for (int c = 0; c < 4; ++c) {
+                sc->last_cg_iters[c] = sc->cg_iters[c];
+                sc->last_cg_relres[c] = sc->cg_relres[c];
+            }
+            sc->last_status = 0;
+        }
+    });
+    return !stop(sc);
+}
+
 __global__ void __launch_bounds__(NTHREADS, 3) k_persistent(PersistArgs P)
 {
     extern __shared__ double dsm[];
@@ -387,6 +606,26 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_persistent(PersistArgs P)
 }
 
 constexpr size_t kPersistSmem = (size_t)(kTileSmem + kRedVals * NTHREADS) * sizeof(double);
+
+// The mixed-precision step as one cooperative launch (small grids).
+__global__ void __launch_bounds__(NTHREADS, 3) k_persistent_mixed(PersistArgs P, MixedPersist X)
+{
+    extern __shared__ double dsm[];
+    double *sm = dsm;
+    double *red = dsm + kTileSmem;
+    if (rdi(&P.a[0].sc->status)) return;
+    if (blockIdx.x == 0 && tid_of() == 0) P.a[0].sc->launches += 1;
+    __shared__ unsigned gen;
+    if (tid_of() == 0) gen = ld_acquire(&P.a[0].sc->bar_gen);
+    __syncthreads();
+    const Grp g{(int)blockIdx.x, (int)gridDim.x, &gen};
+    for (int s = 0; s < P.nsteps; ++s) {
+        const int slot = (P.first_slot + s) & 1;
+        if (!run_step_mixed(P, X, P.a[slot], g, sm, red)) break;
+    }
+    Scal *sc = P.a[0].sc;
+    if (blockIdx.x == 0 && tid_of() == 0 && sc->status) sc->last_status = sc->status;
+}
 
 // An ensemble of independent contexts in one cooperative launch: member m
 // runs its steps on blocks first[m] .. first[m+1]-1 with its own grid
@@ -505,6 +744,47 @@ cudaError_t launch_persistent(const StepArgs a[2], const Level *L, int nlev, int
     P.cg_maxit = cg_maxit;
     void *args[] = {&P};
     return cudaLaunchCooperativeKernel((const void *)k_persistent, dim3(blocks), dim3(BX, BZ), args,
+                                       kPersistSmem, st);
+}
+
+int persistent_mixed_max_blocks()
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaFuncSetAttribute(k_persistent_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kPersistSmem) != cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent_mixed, NTHREADS, kPersistSmem) !=
+        cudaSuccess)
+        return 0;
+    return per_sm * sms;
+}
+
+cudaError_t launch_persistent_mixed(const StepArgs a[2], const Level &L0, const MixedArgs &m, const LevelF *Lf,
+                                    int nlev, int ncoarse, int n_corr, int jac_maxit, int cg_maxit,
+                                    int first_slot, int nsteps, int blocks, cudaStream_t st)
+{
+    if (nlev < 1 || nlev > kMaxLevels) return cudaErrorInvalidValue;
+    PersistArgs P;
+    memset(&P, 0, sizeof(P));
+    P.a[0] = a[0];
+    P.a[1] = a[1];
+    P.L[0] = L0;
+    P.nlev = 1;
+    P.ncoarse = ncoarse;
+    P.nsteps = nsteps;
+    P.first_slot = first_slot;
+    P.n_corr = n_corr;
+    P.jac_maxit = jac_maxit;
+    P.cg_maxit = cg_maxit;
+    MixedPersist X;
+    memset(&X, 0, sizeof(X));
+    X.m = m;
+    for (int l = 0; l < nlev; ++l) X.Lf[l] = Lf[l];
+    X.nlev = nlev;
+    void *args[] = {&P, &X};
+    return cudaLaunchCooperativeKernel((const void *)k_persistent_mixed, dim3(blocks), dim3(BX, BZ), args,
                                        kPersistSmem, st);
 }
 

@@ -263,7 +263,7 @@ class Solver:
         return {"steps_done": s.steps_done, "jac_u": s.jac_u, "jac_h": s.jac_h,
                 "cg_iters": list(s.cg_iters)[:n], "cg_relres": list(s.cg_relres)[:n],
                 "status": s.status, "mg_levels": s.mg_levels, "launches": s.launches,
-                "driver": {0: "graph", 1: "persistent", 2: "mixed"}[s.driver]}
+                "driver": {0: "graph", 1: "persistent", 2: "mixed", 3: "mixed_persistent"}[s.driver]}
 
     def field(self, name: str) -> np.ndarray:
         nx, nz = self.grid.nx, self.grid.nz

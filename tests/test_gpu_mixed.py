@@ -51,17 +51,31 @@ def field_errors(gs, so, const, grid):
     return out
 
 
+_ORACLE_100 = {}
+
+
+def oracle_100(oracle_mod, name):
+    """The oracle's state after 100 steps of a named workload (computed once)."""
+    if name not in _ORACLE_100:
+        wl = W.get(name)
+        o = oracle_mod.Oracle(wl.grid, wl.const)
+        so = o.derive(wl.fields)
+        o.step(so, 100)
+        _ORACLE_100[name] = (o, so)
+    return _ORACLE_100[name]
+
+
+@pytest.mark.parametrize("graph", [False, True], ids=["persistent", "graph"])
 @pytest.mark.parametrize("name", ["bubble160x80", "bubble640x320"])
-def test_mixed_100_steps_against_oracle(gea, oracle_mod, name):
+def test_mixed_100_steps_against_oracle(gea, oracle_mod, name, graph):
     wl = W.get(name)
-    o = oracle_mod.Oracle(wl.grid, wl.const)
-    so = o.derive(wl.fields)
-    o.step(so, 100)
-    s = gea.Solver(wl.grid, wl.const, mixed=True)
+    o, so = oracle_100(oracle_mod, name)
+    s = gea.Solver(wl.grid, wl.const, mixed=True, graph=graph)
     s.set_conservative(wl.fields)
     s.step(100)
     st = s.stats()
-    assert st["driver"] == "mixed" and st["status"] == 0 and st["steps_done"] == 100
+    assert st["driver"] == ("mixed" if graph else "mixed_persistent")
+    assert st["status"] == 0 and st["steps_done"] == 100
     errs = field_errors(s.get_full(), so, wl.const, wl.grid)
     th_g, m_g, _ = s.diagnostics(wl.theta_bar)
     th_o, m_o, _ = o.diagnostics(so, wl.theta_bar)
@@ -115,10 +129,10 @@ def test_mixed_profiled_step_equals_graph_step(gea):
     """The per-kernel profiled step launches the same kernels in the same
     order as the graph: identical results, bit for bit."""
     wl = W.get("bubble640x320")
-    a = gea.Solver(wl.grid, wl.const, mixed=True)
+    a = gea.Solver(wl.grid, wl.const, mixed=True, graph=True)
     a.set_conservative(wl.fields)
     a.step(3)
-    b = gea.Solver(wl.grid, wl.const, mixed=True)
+    b = gea.Solver(wl.grid, wl.const, mixed=True, graph=True)
     b.set_conservative(wl.fields)
     b.step(2)
     prof = b.profile_step()
@@ -177,3 +191,40 @@ def test_mixed_tolerance_controls_error(gea, oracle_mod):
         e[rt] = field_errors(s.get_full(), so, wl.const, wl.grid)
     print(e)
     assert e[1e-6]["rhow"] < e[1e-3]["rhow"]
+
+
+def test_mixed_persistent_and_graph_agree(gea):
+    """The two drivers of the mixed step run the same tile functions; the
+    FP32 reductions are grouped differently (a persistent block sums several
+    tiles), so the inner solves differ at FP32 rounding and the FP64 fields
+    agree to far below the step's own error against the FP64 solution."""
+    wl = W.get("bubble640x320")
+    out = []
+    for graph in (False, True):
+        s = gea.Solver(wl.grid, wl.const, mixed=True, graph=graph)
+        s.set_conservative(wl.fields)
+        s.step(20)
+        assert s.stats()["status"] == 0
+        out.append(s.get_full())
+    for k in ("rho", "T", "pp"):
+        assert np.abs(out[0][k] - out[1][k]).max() <= 1e-11 * np.abs(out[1][k]).max(), k
+    vmax = max(np.abs(out[1]["u"]).max(), np.abs(out[1]["w"]).max())
+    for k in ("u", "w"):
+        assert np.abs(out[0][k] - out[1][k]).max() <= 1e-8 * vmax, k
+
+
+def test_mixed_persistent_multi_step_launch(gea):
+    """n steps in one persistent launch equal n launches of one step, bit
+    for bit, and the persistent driver is deterministic."""
+    wl = W.get("bubble160x80")
+    a = gea.Solver(wl.grid, wl.const, mixed=True)
+    a.set_conservative(wl.fields)
+    a.step(6)
+    assert a.stats()["driver"] == "mixed_persistent"
+    b = gea.Solver(wl.grid, wl.const, mixed=True)
+    b.set_conservative(wl.fields)
+    for _ in range(6):
+        b.step(1)
+    ra, rb = a.get_full(), b.get_full()
+    for k in ra:
+        assert np.array_equal(ra[k], rb[k]), k
