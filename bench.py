@@ -479,6 +479,7 @@ def run_ensemble(args):
 # Per-cell model of the three-dimensional kernels (same conventions as
 # KERNEL_MODEL; coarsening and restriction per coarse cell).
 KERNEL_MODEL_3D = {
+    "g3_les": (5, 60, "f64"),
     "g3_pred": (31, 102, "f64"),
     "g3_mom": (23, 93, "f64"),
     "g3_kin": (4, 6, "f64"),
@@ -551,7 +552,7 @@ def run_3d(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl.name, "grid": [g.nx, g.ny, g.nz], "cells": cells,
                    "domain_m": [g.lx, g.ly, g.lz], "dt": wl.const.dt, "n_corr": wl.const.n_corr,
-                   "jac_rtol": wl.const.jac_rtol, "cg_rtol": wl.const.cg_rtol,
+                   "jac_rtol": wl.const.jac_rtol, "cg_rtol": wl.const.cg_rtol, "cs": wl.const.cs,
                    "mg_levels": st["mg_levels"],
                    "l2": "inputs larger than L2 (each field 0.5 GB) and 256 MB flush between steps",
                    "driver": "graph", "parallelism": f"replicas x{world}"},

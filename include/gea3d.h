@@ -5,7 +5,8 @@
  * 2303.10499: continuity and implicit momentum predictor, implicit enthalpy
  * equation, EOS update, PISO correctors with the Helmholtz pressure
  * equation) on a uniform Cartesian x-y-z grid: x and y horizontal, z up,
- * free-slip walls on all six sides, constant viscosity mu (Remark 1), FP64.
+ * free-slip walls on all six sides, constant viscosity mu (Remark 1) or a
+ * Smagorinsky eddy viscosity, FP64.
  * The pressure equation is solved by conjugate gradients preconditioned by a
  * Galerkin geometric multigrid V(1,1) cycle (coarsening 2 x 2 x 2); the
  * solver loops run on the device inside a CUDA graph.
@@ -15,8 +16,12 @@
  *    centred at ((i+1/2) dx, (j+1/2) dy, (k+1/2) dz) at index
  *    (k ny + j) nx + i.
  *  - Pressure split p = p' - rho g z (g > 0, z up), as in gea.h.
- *  - The constants are gea_constants of gea.h; flags, mp_rtol and cs must
- *    be 0 (no mixed precision, no LES in three dimensions).
+ *  - The constants are gea_constants of gea.h; flags and mp_rtol must be 0
+ *    (no mixed precision in three dimensions). cs > 0 turns on Smagorinsky
+ *    LES: mu_eff = mu + rho^n (cs Delta)^2 |S| per cell, Delta =
+ *    (dx dy dz)^(1/3), |S| = sqrt(2 S_ij S_ij) from central differences of
+ *    u^n, and the diffusion of momentum and enthalpy takes the face means
+ *    of mu_eff; it requires Pr = 1.
  *  - All calls are ordered on the context's stream; calls with host
  *    buffers return after the copies.
  *  - Functions return GEA_OK or a GEA_ERR_* code of gea.h.

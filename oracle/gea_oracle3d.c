@@ -43,6 +43,7 @@ typedef struct {
     int32_t jac_maxit;
     double cg_rtol;
     int32_t cg_maxit;
+    double cs;          /* Smagorinsky constant; 0: constant viscosity mu only */
 } o3_cfg;
 
 typedef struct {
@@ -132,6 +133,78 @@ double o3_laplacian_cell(const o3_cfg *c, const double *X, int bc, int i, int j,
     return s;
 }
 
+/* Strain-rate magnitude |S| = sqrt(2 S_ij S_ij) of cell (i,j,k) from central
+ * differences of the cell velocities (ghosts by the wall rules):
+ * 2 S_ij S_ij = 2 (u_x^2 + v_y^2 + w_z^2) + (u_y + v_x)^2 + (u_z + w_x)^2
+ * + (v_z + w_y)^2. */
+double o3_strain_cell(const o3_cfg *c, const double *u, const double *v, const double *w, int i, int j, int k)
+{
+    double hx = 1.0 / (2.0 * DX(c)), hy = 1.0 / (2.0 * DY(c)), hz = 1.0 / (2.0 * DZ(c));
+    double ux = (at3(c, u, i + 1, j, k, B3_U) - at3(c, u, i - 1, j, k, B3_U)) * hx;
+    double uy = (at3(c, u, i, j + 1, k, B3_U) - at3(c, u, i, j - 1, k, B3_U)) * hy;
+    double uz = (at3(c, u, i, j, k + 1, B3_U) - at3(c, u, i, j, k - 1, B3_U)) * hz;
+    double vx = (at3(c, v, i + 1, j, k, B3_V) - at3(c, v, i - 1, j, k, B3_V)) * hx;
+    double vy = (at3(c, v, i, j + 1, k, B3_V) - at3(c, v, i, j - 1, k, B3_V)) * hy;
+    double vz = (at3(c, v, i, j, k + 1, B3_V) - at3(c, v, i, j, k - 1, B3_V)) * hz;
+    double wx = (at3(c, w, i + 1, j, k, B3_W) - at3(c, w, i - 1, j, k, B3_W)) * hx;
+    double wy = (at3(c, w, i, j + 1, k, B3_W) - at3(c, w, i, j - 1, k, B3_W)) * hy;
+    double wz = (at3(c, w, i, j, k + 1, B3_W) - at3(c, w, i, j, k - 1, B3_W)) * hz;
+    double sxy = uy + vx, sxz = uz + wx, syz = vz + wy;
+    return sqrt(2.0 * (ux * ux + vy * vy + wz * wz) + sxy * sxy + sxz * sxz + syz * syz);
+}
+
+/* Effective dynamic viscosity mu + rho (cs Delta)^2 |S| at every cell, with
+ * the filter width Delta = (dx dy dz)^(1/3). */
+void o3_smagorinsky(const o3_cfg *c, const double *rho, const double *u, const double *v, const double *w,
+                    double *mu_eff)
+{
+    double delta = cbrt(DX(c) * DY(c) * DZ(c));
+    double d2 = c->cs * c->cs * delta * delta;
+    for (int k = 0; k < c->nz; ++k)
+        for (int j = 0; j < c->ny; ++j)
+            for (int i = 0; i < c->nx; ++i) {
+                size_t q = cid(c, i, j, k);
+                mu_eff[q] = c->mu + rho[q] * d2 * o3_strain_cell(c, u, v, w, i, j, k);
+            }
+}
+
+/* Variable-coefficient diffusive face sum (1/V) sum_j mu_j (grad X)_j . A_j of
+ * cell (i,j,k): mu_j the mean of the two cells' viscosities (a wall face takes
+ * the cell's own, the even ghost), compact face gradients through the ghosts. */
+double o3_diffusion_cell(const o3_cfg *c, const double *mu, const double *X, int bc, int i, int j, int k)
+{
+    double dx = DX(c), dy = DY(c), dz = DZ(c);
+    double xc = at3(c, X, i, j, k, bc), mc = at3(c, mu, i, j, k, B3_EVEN);
+    double s = 0.0;
+    s += 0.5 * (mc + at3(c, mu, i + 1, j, k, B3_EVEN)) * (at3(c, X, i + 1, j, k, bc) - xc) / (dx * dx);
+    s += 0.5 * (mc + at3(c, mu, i - 1, j, k, B3_EVEN)) * (at3(c, X, i - 1, j, k, bc) - xc) / (dx * dx);
+    s += 0.5 * (mc + at3(c, mu, i, j + 1, k, B3_EVEN)) * (at3(c, X, i, j + 1, k, bc) - xc) / (dy * dy);
+    s += 0.5 * (mc + at3(c, mu, i, j - 1, k, B3_EVEN)) * (at3(c, X, i, j - 1, k, bc) - xc) / (dy * dy);
+    s += 0.5 * (mc + at3(c, mu, i, j, k + 1, B3_EVEN)) * (at3(c, X, i, j, k + 1, bc) - xc) / (dz * dz);
+    s += 0.5 * (mc + at3(c, mu, i, j, k - 1, B3_EVEN)) * (at3(c, X, i, j, k - 1, bc) - xc) / (dz * dz);
+    return s;
+}
+
+/* The diffusion term of the transport operators: nu L(X) with constant nu,
+ * or nu times the variable-coefficient sum with the viscosity field mu. */
+static double diffusion3(const o3_cfg *c, const double *mu, double nu, const double *X, int bc, int i, int j,
+                         int k)
+{
+    return mu ? nu * o3_diffusion_cell(c, mu, X, bc, i, j, k) : nu * o3_laplacian_cell(c, X, bc, i, j, k);
+}
+
+/* Coefficient of X_i in -diffusion3() (interior cell). */
+static double diffusion_diag3(const o3_cfg *c, const double *mu, double nu, int i, int j, int k)
+{
+    double dx = DX(c), dy = DY(c), dz = DZ(c);
+    if (!mu) return nu * (2.0 / (dx * dx) + 2.0 / (dy * dy) + 2.0 / (dz * dz));
+    double mc = at3(c, mu, i, j, k, B3_EVEN);
+    double fx = 0.5 * (mc + at3(c, mu, i + 1, j, k, B3_EVEN)) + 0.5 * (mc + at3(c, mu, i - 1, j, k, B3_EVEN));
+    double fy = 0.5 * (mc + at3(c, mu, i, j + 1, k, B3_EVEN)) + 0.5 * (mc + at3(c, mu, i, j - 1, k, B3_EVEN));
+    double fz = 0.5 * (mc + at3(c, mu, i, j, k + 1, B3_EVEN)) + 0.5 * (mc + at3(c, mu, i, j, k - 1, B3_EVEN));
+    return nu * (fx / (dx * dx) + fy / (dy * dy) + fz / (dz * dz));
+}
+
 /* (1/V) sum_j phi_j, outward positive. */
 double o3_divergence_cell(const o3_cfg *c, const double *phix, const double *phiy, const double *phiz,
                           int i, int j, int k)
@@ -193,39 +266,40 @@ static double norm2(const double *x, size_t n)
 
 /* r = b - [(rho1/dt) X + C(X) - nu L(X)] at every cell. */
 static void transport_residual3(const o3_cfg *c, const double *rho1, const double *phix, const double *phiy,
-                                const double *phiz, double nu, const double *X, int bc, const double *b,
-                                double *r)
+                                const double *phiz, const double *mu, double nu, const double *X, int bc,
+                                const double *b, double *r)
 {
     for (int k = 0; k < c->nz; ++k)
         for (int j = 0; j < c->ny; ++j)
             for (int i = 0; i < c->nx; ++i) {
                 size_t q = cid(c, i, j, k);
                 double lhs = rho1[q] / c->dt * X[q] + o3_convection_cell(c, phix, phiy, phiz, X, bc, i, j, k)
-                           - nu * o3_laplacian_cell(c, X, bc, i, j, k);
+                           - diffusion3(c, mu, nu, X, bc, i, j, k);
                 r[q] = b[q] - lhs;
             }
 }
 
-/* Jacobi for (rho1/dt) X + C(X) - nu L(X) = b from the initial X; divisor
- * rho1/dt + (7/12) sum_j phi_j/V + nu (2/dx^2 + 2/dy^2 + 2/dz^2); stops after
- * the sweep whose residual met ||r|| <= jac_rtol ||b||. Returns sweeps or -1. */
+/* Jacobi for (rho1/dt) X + C(X) - D(X) = b from the initial X, D the
+ * diffusion term (nu L(X), or nu times the variable-coefficient sum when mu
+ * is given); divisor rho1/dt + (7/12) sum_j phi_j/V + the diagonal of -D;
+ * stops after the sweep whose residual met ||r|| <= jac_rtol ||b||. Returns
+ * sweeps or -1. */
 int o3_transport_solve(const o3_cfg *c, const double *rho1, const double *phix, const double *phiy,
-                       const double *phiz, double nu, int bc, const double *b, double *X)
+                       const double *phiz, const double *mu, double nu, int bc, const double *b, double *X)
 {
     size_t n = ncell(c);
-    double dx = DX(c), dy = DY(c), dz = DZ(c);
     double *r = malloc(n * sizeof(double));
     double bn = norm2(b, n);
     int sweeps = 0, ok = 0;
     while (sweeps < c->jac_maxit) {
-        transport_residual3(c, rho1, phix, phiy, phiz, nu, X, bc, b, r);
+        transport_residual3(c, rho1, phix, phiy, phiz, mu, nu, X, bc, b, r);
         double rn = norm2(r, n);
         for (int k = 0; k < c->nz; ++k)
             for (int j = 0; j < c->ny; ++j)
                 for (int i = 0; i < c->nx; ++i) {
                     size_t q = cid(c, i, j, k);
                     double d = rho1[q] / c->dt + 7.0 / 12.0 * o3_divergence_cell(c, phix, phiy, phiz, i, j, k)
-                             + nu * (2.0 / (dx * dx) + 2.0 / (dy * dy) + 2.0 / (dz * dz));
+                             + diffusion_diag3(c, mu, nu, i, j, k);
                     X[q] += r[q] / d;
                 }
         ++sweeps;
@@ -399,8 +473,13 @@ int o3_step(const o3_cfg *c, o3_state *s, int32_t nsteps, o3_stats *st)
     double *Gx = zal(nfx), *Gy = zal(nfy), *Gz = zal(nfz), *Dx = zal(nfx), *Dy = zal(nfy), *Dz = zal(nfz);
     double *Fx = zal(nfx), *Fy = zal(nfy), *Fz = zal(nfz);
     int su = 0, sv = 0, sw = 0, sh = 0;
+    /* LES: mu_eff from rho^n, u^n once per step; the diffusion of momentum and
+     * enthalpy then takes its face means (Pr = 1: one field for both) */
+    double *mu_eff = c->cs > 0.0 ? zal(n) : NULL;
+    double nu_u = mu_eff ? 1.0 : c->mu, nu_h = mu_eff ? 1.0 / c->Pr : c->mu / c->Pr;
 
     for (int step = 0; step < nsteps; ++step) {
+        if (mu_eff) o3_smagorinsky(c, s->rho, s->u, s->v, s->w, mu_eff);
         /* Step 1, eq. (e1_d): rho^{n+1/3} = rho^n - dt sum_j phi^n_j / V */
         for (int k = 0; k < nz; ++k)
             for (int j = 0; j < ny; ++j)
@@ -423,9 +502,9 @@ int o3_step(const o3_cfg *c, o3_state *s, int32_t nsteps, o3_stats *st)
                     bw[q] = s->rho[q] * s->w[q] / dt - gcz;
                     u1[q] = s->u[q]; v1[q] = s->v[q]; w1[q] = s->w[q];
                 }
-        su = o3_transport_solve(c, rho1, s->phix, s->phiy, s->phiz, c->mu, B3_U, bu, u1);
-        sv = o3_transport_solve(c, rho1, s->phix, s->phiy, s->phiz, c->mu, B3_V, bv, v1);
-        sw = o3_transport_solve(c, rho1, s->phix, s->phiy, s->phiz, c->mu, B3_W, bw, w1);
+        su = o3_transport_solve(c, rho1, s->phix, s->phiy, s->phiz, mu_eff, nu_u, B3_U, bu, u1);
+        sv = o3_transport_solve(c, rho1, s->phix, s->phiy, s->phiz, mu_eff, nu_u, B3_V, bv, v1);
+        sw = o3_transport_solve(c, rho1, s->phix, s->phiy, s->phiz, mu_eff, nu_u, B3_W, bw, w1);
         if (su < 0 || sv < 0 || sw < 0) status = 1;
         /* eq. (step1_3sd) */
         for (size_t q = 0; q < n; ++q) K1[q] = 0.5 * (u1[q] * u1[q] + v1[q] * v1[q] + w1[q] * w1[q]);
@@ -442,7 +521,7 @@ int o3_step(const o3_cfg *c, o3_state *s, int32_t nsteps, o3_stats *st)
                           + s->p[q] / dt - rho1[q] * g * w1[q];
                     h1[q] = s->h[q];
                 }
-        sh = o3_transport_solve(c, rho1, s->phix, s->phiy, s->phiz, c->mu / c->Pr, B3_H, bh, h1);
+        sh = o3_transport_solve(c, rho1, s->phix, s->phiy, s->phiz, mu_eff, nu_h, B3_H, bh, h1);
         if (sh < 0) status = 1;
         /* eqs. (step3_2sd), (step3_3sd) */
         for (size_t q = 0; q < n; ++q) {
@@ -476,11 +555,11 @@ int o3_step(const o3_cfg *c, o3_state *s, int32_t nsteps, o3_stats *st)
                     for (int i = 0; i < nx; ++i) {
                         size_t q = cid(c, i, j, k);
                         Hx[q] = s->rho[q] * s->u[q] / dt - o3_convection_cell(c, s->phix, s->phiy, s->phiz, U, B3_U, i, j, k)
-                              + c->mu * o3_laplacian_cell(c, U, B3_U, i, j, k);
+                              + diffusion3(c, mu_eff, nu_u, U, B3_U, i, j, k);
                         Hy[q] = s->rho[q] * s->v[q] / dt - o3_convection_cell(c, s->phix, s->phiy, s->phiz, Vv, B3_V, i, j, k)
-                              + c->mu * o3_laplacian_cell(c, Vv, B3_V, i, j, k);
+                              + diffusion3(c, mu_eff, nu_u, Vv, B3_V, i, j, k);
                         Hz[q] = s->rho[q] * s->w[q] / dt - o3_convection_cell(c, s->phix, s->phiy, s->phiz, W, B3_W, i, j, k)
-                              + c->mu * o3_laplacian_cell(c, W, B3_W, i, j, k);
+                              + diffusion3(c, mu_eff, nu_u, W, B3_W, i, j, k);
                     }
             /* right-hand side of the Helmholtz pressure equation */
             for (int k = 0; k < nz; ++k)
@@ -582,5 +661,6 @@ int o3_step(const o3_cfg *c, o3_state *s, int32_t nsteps, o3_stats *st)
     free(T1); free(rho2); free(psi); free(Hx); free(Hy); free(Hz); free(b); free(U); free(Vv); free(W);
     free(pnew); free(rhonew); free(pnext); free(Gx); free(Gy); free(Gz); free(Dx); free(Dy); free(Dz);
     free(Fx); free(Fy); free(Fz);
+    free(mu_eff);
     return status;
 }

@@ -41,7 +41,7 @@ class _Cfg(C.Structure):
                 ("R", C.c_double), ("cp", C.c_double), ("g", C.c_double), ("p0", C.c_double),
                 ("mu", C.c_double), ("Pr", C.c_double), ("dt", C.c_double),
                 ("n_corr", C.c_int32), ("jac_rtol", C.c_double), ("jac_maxit", C.c_int32),
-                ("cg_rtol", C.c_double), ("cg_maxit", C.c_int32)]
+                ("cg_rtol", C.c_double), ("cg_maxit", C.c_int32), ("cs", C.c_double)]
 
 
 _P = C.POINTER(C.c_double)
@@ -69,6 +69,11 @@ def _load():
             lib.o3_laplacian_cell.restype = C.c_double
             lib.o3_divergence_cell.argtypes = [C.POINTER(_Cfg), P, P, P, C.c_int, C.c_int, C.c_int]
             lib.o3_divergence_cell.restype = C.c_double
+            lib.o3_strain_cell.argtypes = [C.POINTER(_Cfg), P, P, P, C.c_int, C.c_int, C.c_int]
+            lib.o3_strain_cell.restype = C.c_double
+            lib.o3_smagorinsky.argtypes = [C.POINTER(_Cfg), P, P, P, P, P]
+            lib.o3_diffusion_cell.argtypes = [C.POINTER(_Cfg), P, P, C.c_int, C.c_int, C.c_int, C.c_int]
+            lib.o3_diffusion_cell.restype = C.c_double
             _lib = lib
     return _lib
 
@@ -107,7 +112,7 @@ class Oracle3D:
         self.grid, self.const = grid, const
         self.cfg = _Cfg(grid.nx, grid.ny, grid.nz, grid.lx, grid.ly, grid.lz, const.R, const.cp, const.g,
                         const.p0, const.mu, const.Pr, const.dt, const.n_corr, const.jac_rtol,
-                        const.jac_maxit, const.cg_rtol, const.cg_maxit)
+                        const.jac_maxit, const.cg_rtol, const.cg_maxit, getattr(const, "cs", 0.0))
 
     def derive(self, fields: Dict[str, np.ndarray]) -> State3:
         s = State3(self.grid)
@@ -134,3 +139,18 @@ class Oracle3D:
     def laplacian_cell(self, X, bc, i, j, k):
         x = np.ascontiguousarray(X, dtype=np.float64)
         return self.lib.o3_laplacian_cell(C.byref(self.cfg), _ptr(x), bc, i, j, k)
+
+    def strain_cell(self, u, v, w, i, j, k):
+        a = [np.ascontiguousarray(x, dtype=np.float64) for x in (u, v, w)]
+        return self.lib.o3_strain_cell(C.byref(self.cfg), *[_ptr(x) for x in a], i, j, k)
+
+    def smagorinsky(self, rho, u, v, w):
+        a = [np.ascontiguousarray(x, dtype=np.float64) for x in (rho, u, v, w)]
+        out = np.empty_like(a[0])
+        self.lib.o3_smagorinsky(C.byref(self.cfg), *[_ptr(x) for x in a], _ptr(out))
+        return out
+
+    def diffusion_cell(self, mu, X, bc, i, j, k):
+        m = np.ascontiguousarray(mu, dtype=np.float64)
+        x = np.ascontiguousarray(X, dtype=np.float64)
+        return self.lib.o3_diffusion_cell(C.byref(self.cfg), _ptr(m), _ptr(x), bc, i, j, k)

@@ -53,6 +53,7 @@ __host__ __device__ inline long long id3(const Geo &G, int i, int j, int k)
 
 struct Phy {
     double R, cp, g, mu, nuh, dt, idt, omega;
+    double les_d2;   // (cs Delta)^2 with Delta = (dx dy dz)^(1/3); 0: constant mu
 };
 
 struct St {
@@ -105,6 +106,7 @@ struct Args {
     double *rho2, *psi, *Dx, *Dy, *Dz, *Hx, *Hy, *Hz, *b, *p0, *p1, *q;
     double *dtr1;   // dt / rho1
     double *kin;    // K1 = |u1|^2 / 2
+    double *mueff;  // mu + mu_t (LES only)
     Cf cf;
     Sc *sc;
     double *part;
@@ -293,6 +295,32 @@ __device__ __forceinline__ void fin_pred(Sc *sc, const double (&t)[3])
 
 // ---- Step 1 (eq. e1_d, eq. step2_sd first line) ----
 
+// Smagorinsky LES: mu_eff = mu + rho^n (cs Delta)^2 |S|, |S| = sqrt(2 S_ij S_ij)
+// from central differences of u^n (ghosts by the wall rules).
+__global__ void k_les(Args a)
+{
+    if (a.sc->status) return;
+    int i, j, k;
+    if (!cell(a.G, i, j, k)) return;
+    const Geo &G = a.G;
+    const Phy &F = a.F;
+    const double hx = 0.5 * G.idx, hy = 0.5 * G.idy, hz = 0.5 * G.idz;
+    const double *u = a.S.u, *v = a.S.v, *w = a.S.w;
+    const double ux = (at<U3>(G, F, u, i + 1, j, k) - at<U3>(G, F, u, i - 1, j, k)) * hx;
+    const double uy = (at<U3>(G, F, u, i, j + 1, k) - at<U3>(G, F, u, i, j - 1, k)) * hy;
+    const double uz = (at<U3>(G, F, u, i, j, k + 1) - at<U3>(G, F, u, i, j, k - 1)) * hz;
+    const double vx = (at<V3>(G, F, v, i + 1, j, k) - at<V3>(G, F, v, i - 1, j, k)) * hx;
+    const double vy = (at<V3>(G, F, v, i, j + 1, k) - at<V3>(G, F, v, i, j - 1, k)) * hy;
+    const double vz = (at<V3>(G, F, v, i, j, k + 1) - at<V3>(G, F, v, i, j, k - 1)) * hz;
+    const double wx = (at<W3>(G, F, w, i + 1, j, k) - at<W3>(G, F, w, i - 1, j, k)) * hx;
+    const double wy = (at<W3>(G, F, w, i, j + 1, k) - at<W3>(G, F, w, i, j - 1, k)) * hy;
+    const double wz = (at<W3>(G, F, w, i, j, k + 1) - at<W3>(G, F, w, i, j, k - 1)) * hz;
+    const double sxy = uy + vx, sxz = uz + wx, syz = vz + wy;
+    const double S = sqrt(2.0 * (ux * ux + vy * vy + wz * wz) + sxy * sxy + sxz * sxz + syz * syz);
+    const long long q = id3(G, i, j, k);
+    a.mueff[q] = F.mu + ld(&a.S.rho[q]) * F.les_d2 * S;
+}
+
 // rho1, the Jacobi reciprocals, b = rho^n u^n / dt - G_cell, initial guesses
 // u^n; acc += |b|^2 per component.
 __global__ void k_pred(Args a)
@@ -308,30 +336,45 @@ __global__ void k_pred(Args a)
         const double dv = divg(a, i, j, k), r = ld(&a.S.rho[q]);
         const double rho1 = r - F.dt * dv;
         a.rho1[q] = rho1;
-        const double lsum = 2.0 * (G.idx2 + G.idy2 + G.idz2);
-        const double cu = rho1 * F.idt + (7.0 / 12.0) * dv + F.mu * lsum;
+        // diffusion weights per face: mu/Delta^2, or with LES the face mean of
+        // mu_eff over Delta^2 (a wall face takes the cell's own, the even ghost)
+        double mw, me, ms, mn, mb, mt;
+        if (F.les_d2 > 0.0) {
+            const double mc = ld(&a.mueff[q]);
+            auto face = [&](int ii, int jj, int kk) { return 0.5 * (mc + at<E3>(G, F, a.mueff, ii, jj, kk)); };
+            mw = face(i - 1, j, k) * G.idx2; me = face(i + 1, j, k) * G.idx2;
+            ms = face(i, j - 1, k) * G.idy2; mn = face(i, j + 1, k) * G.idy2;
+            mb = face(i, j, k - 1) * G.idz2; mt = face(i, j, k + 1) * G.idz2;
+        } else {
+            mw = me = F.mu * G.idx2;
+            ms = mn = F.mu * G.idy2;
+            mb = mt = F.mu * G.idz2;
+        }
+        const double cu = rho1 * F.idt + (7.0 / 12.0) * dv + ((mw + me) + (ms + mn) + (mb + mt));
         a.dinvu[q] = 1.0 / cu;
-        a.dinvh[q] = 1.0 / (rho1 * F.idt + (7.0 / 12.0) * dv + F.nuh * lsum);
+        // the enthalpy diagonal: the diffusion scaled by 1/Pr (LES requires Pr = 1)
+        a.dinvh[q] = F.les_d2 > 0.0 ? 1.0 / cu
+                                    : 1.0 / (rho1 * F.idt + (7.0 / 12.0) * dv +
+                                             F.nuh * 2.0 * (G.idx2 + G.idy2 + G.idz2));
         // T as a stencil: the outgoing flux of a face times its fourth-order
-        // value (-X_m + 7 X_a + 7 X_b - X_p)/12, minus mu times the Laplacian
+        // value (-X_m + 7 X_a + 7 X_b - X_p)/12, minus the diffusion
         const double i12 = G.ivol * (1.0 / 12.0);
         const double pw = ld(&a.S.phix[q]), pe = ld(&a.S.phix[q + 1]);
         const double ps = ld(&a.S.phiy[q]), pn = ld(&a.S.phiy[q + sy]);
         const double pb = ld(&a.S.phiz[q]), pt = ld(&a.S.phiz[q + sz]);
-        const double mx = F.mu * G.idx2, my = F.mu * G.idy2, mz = F.mu * G.idz2;
         const Cf &cf = a.cf;
         cf.c[0][q] = cu;
         cf.c[1][q] = pw * i12;
-        cf.c[2][q] = -(pe + 7.0 * pw) * i12 - mx;
-        cf.c[3][q] = (7.0 * pe + pw) * i12 - mx;
+        cf.c[2][q] = -(pe + 7.0 * pw) * i12 - mw;
+        cf.c[3][q] = (7.0 * pe + pw) * i12 - me;
         cf.c[4][q] = -pe * i12;
         cf.c[5][q] = ps * i12;
-        cf.c[6][q] = -(pn + 7.0 * ps) * i12 - my;
-        cf.c[7][q] = (7.0 * pn + ps) * i12 - my;
+        cf.c[6][q] = -(pn + 7.0 * ps) * i12 - ms;
+        cf.c[7][q] = (7.0 * pn + ps) * i12 - mn;
         cf.c[8][q] = -pn * i12;
         cf.c[9][q] = pb * i12;
-        cf.c[10][q] = -(pt + 7.0 * pb) * i12 - mz;
-        cf.c[11][q] = (7.0 * pt + pb) * i12 - mz;
+        cf.c[10][q] = -(pt + 7.0 * pb) * i12 - mb;
+        cf.c[11][q] = (7.0 * pt + pb) * i12 - mt;
         cf.c[12][q] = -pt * i12;
         double fl[3], gc[3];
         cell_forces(G, F, a.S.pp, a.S.rho, i, j, k, fl, gc);
@@ -956,6 +999,7 @@ struct gea3d_ctx {
     double *rho2, *psi, *Dx, *Dy, *Dz, *Hx, *Hy, *Hz, *b, *p0, *p1, *q;
     double *dtr1;                         // dt / rho1
     double *kin;                          // K1
+    double *mueff = nullptr;              // LES eddy viscosity field
     Cf cf;                                // transport stencil weights
     double *stage = nullptr;              // dense conservative fields (5 arrays)
     std::vector<Lev> L;                   // the FP64 fine-level operator
@@ -1028,6 +1072,7 @@ Args args_of(gea3d_ctx *c, int from)
     a.cf = c->cf;
     a.dtr1 = c->dtr1;
     a.kin = c->kin;
+    a.mueff = c->mueff;
     a.sc = c->sc; a.part = c->part;
     a.jtol2 = c->C.jac_rtol * c->C.jac_rtol;
     a.ctol2 = c->C.cg_rtol * c->C.cg_rtol;
@@ -1170,6 +1215,7 @@ int record3(gea3d_ctx *ctx, int from, cudaStream_t s, bool graph, Trace3 *tr)
         return graph ? capture_while3(ctx, s, body) : eager_while3(ctx, s, which, maxtrips, body);
     };
     k_begin<<<1, 1, 0, s>>>(a.sc); ++fixed;
+    if (ctx->mueff) { traced(tr, "g3_les", G, s, [&] { k_les<<<grid, kBlk, 0, s>>>(a); }); ++fixed; }
     traced(tr, "g3_pred", G, s, [&] { k_pred<<<grid, kBlk, 0, s>>>(a); }); ++fixed;
     rc = loop(L_MOM, jtrips, [&](cudaStream_t bs, cudaGraphConditionalHandle h) {
         traced(tr, "g3_mom", G, bs, [&] { k_mom<<<grid, kBlk, 0, bs>>>(a, a.ua, a.va, a.wa, a.ub, a.vb, a.wb, 0); });
@@ -1247,13 +1293,17 @@ int gea3d_create(const gea3d_grid *grid, const gea_constants *c, gea3d_ctx **out
     if (!(c->R > 0) || !(c->cp > c->R) || !(c->g >= 0) || !(c->p0 > 0) || !(c->mu >= 0) || !(c->Pr > 0) ||
         !(c->dt > 0) || c->n_corr < 1 || c->n_corr > 4 || !(c->jac_rtol > 0) || c->jac_maxit < 1 ||
         !(c->cg_rtol > 0) || c->cg_maxit < 1 || c->mg_min_cells < 0 || c->flags != 0 || c->mp_rtol != 0.0 ||
-        c->cs != 0.0)
+        !(c->cs >= 0.0) || (c->cs > 0.0 && c->Pr != 1.0))
         return GEA_ERR_INVAL;
     gea3d_ctx *ctx = new gea3d_ctx();
     ctx->C = *c;
     ctx->G = make_geo(grid->nx, grid->ny, grid->nz, grid->lx, grid->ly, grid->lz);
     ctx->F.R = c->R; ctx->F.cp = c->cp; ctx->F.g = c->g; ctx->F.mu = c->mu; ctx->F.nuh = c->mu / c->Pr;
     ctx->F.dt = c->dt; ctx->F.idt = 1.0 / c->dt; ctx->F.omega = kOmega;
+    {
+        const double delta = cbrt(ctx->G.dx * ctx->G.dy * ctx->G.dz);
+        ctx->F.les_d2 = c->cs * c->cs * delta * delta;
+    }
     // multigrid levels: halve all three sizes while they are even and >= 8
     // and (unless mg_min_cells is given) the Laplacian-to-diagonal estimate
     // 2 dt^2 R T (1/dx^2 + 1/dy^2 + 1/dz^2) exceeds 1
@@ -1296,6 +1346,7 @@ int gea3d_create(const gea3d_grid *grid, const gea_constants *c, gea3d_ctx **out
     for (int m = 0; m < NCF; ++m) ctx->cf.c[m] = take(E);
     ctx->dtr1 = take(E);
     ctx->kin = take(E);
+    if (c->cs > 0.0) ctx->mueff = take(E);
     ctx->stage = take(5 * (size_t)grid->nx * grid->ny * grid->nz);
     {
         Lev l;

@@ -403,8 +403,8 @@ def extrude3(wl: Workload, ny: int, ly: float) -> Workload:
 def bubble3d(nx: int, ny: int, nz: int, dt: float = 0.05, steps: int = 200) -> Workload:
     """The 3D rising thermal bubble: 10 km x 10 km x 10 km, theta0 = 300 K,
     spherical cosine bubble of 2 K, radius 2 km, centred (5, 5, 2) km, at
-    rest, mu = 0.15."""
-    return rising_bubble3(Grid3(nx, ny, nz, 10000.0, 10000.0, 10000.0), Constants(dt=dt), 300.0, 2.0,
+    rest, mu = 0.15, Smagorinsky LES with cs = 0.17 (Pr = 1)."""
+    return rising_bubble3(Grid3(nx, ny, nz, 10000.0, 10000.0, 10000.0), Constants(dt=dt, cs=0.17), 300.0, 2.0,
                           2000.0, 5000.0, 5000.0, 2000.0, name=f"bubble3d_{nx}x{ny}x{nz}", steps=steps)
 
 

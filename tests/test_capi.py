@@ -109,6 +109,8 @@ def test_create3_rejects_bad_arguments():
         with pytest.raises(gea.GeaError) as ei:
             gea.Solver3D(g, c)
         assert ei.value.code == gea.GEA_ERR_INVAL
-    with pytest.raises(gea.GeaError) as ei:
-        gea.Solver3D(W.Grid3(8, 8, 8, 1.0, 1.0, 1.0), W.Constants(dt=0.2, cs=0.17))
-    assert ei.value.code == gea.GEA_ERR_INVAL
+    # LES needs Pr = 1 (one viscosity field for momentum and enthalpy), and cs >= 0
+    for kw in (dict(cs=0.17, Pr=0.7), dict(cs=-0.1)):
+        with pytest.raises(gea.GeaError) as ei:
+            gea.Solver3D(W.Grid3(8, 8, 8, 1.0, 1.0, 1.0), W.Constants(dt=0.2, **kw))
+        assert ei.value.code == gea.GEA_ERR_INVAL, kw

@@ -83,6 +83,39 @@ def test_parity_prandtl_and_three_correctors(gea, o3):
     compare(s.get_state(), so, 1e-10)
 
 
+@pytest.mark.parametrize("shape", [(24, 20, 12), (33, 9, 5)], ids=["24x20x12", "33x9x5"])
+def test_parity_les(gea, o3, shape):
+    """Smagorinsky LES (cs = 0.17, Pr = 1) on a sheared stratified flow: the
+    eddy viscosity, its face means in the transport stencil and in H(u)."""
+    nx, ny, nz = shape
+    g = W.Grid3(nx, ny, nz, 100.0 * nx, 100.0 * ny, 100.0 * nz)
+    c = W.Constants(dt=0.2, mu=0.5, cs=0.17)
+    wl = W.random_flow3(g, c, seed=12, uamp=4.0, thamp=2.0)
+    so, sto, s = run_both(gea, o3, wl, 20)
+    st = s.stats()
+    assert st["status"] == 0
+    compare(s.get_state(), so, 1e-10)
+
+
+def test_les_bubble_mirror_symmetry_and_mass(gea):
+    """LES on the centred bubble keeps the x, y mirror symmetries and mass."""
+    g = W.Grid3(64, 64, 32, 10000.0, 10000.0, 10000.0)
+    c = W.Constants(dt=0.2, cs=0.17)
+    wl = W.rising_bubble3(g, c, amp=2.0, rc=2000.0, xc=5000.0, yc=5000.0, zc=2000.0)
+    s = gea.Solver3D(g, c)
+    s.set_conservative(wl.fields)
+    s.step(20)
+    assert s.stats()["status"] == 0
+    f = s.get_state()
+    w, u, v = f["w"], f["u"], f["v"]
+    sc = np.abs(w).max()
+    assert sc > 1e-4
+    assert np.abs(w - w[:, :, ::-1]).max() < 1e-8 * sc and np.abs(w - w[:, ::-1, :]).max() < 1e-8 * sc
+    assert np.abs(u + u[:, :, ::-1]).max() < 1e-8 * sc and np.abs(v + v[:, ::-1, :]).max() < 1e-8 * sc
+    m0 = wl.fields["rho"].sum()
+    assert abs(f["rho"].sum() - m0) < 1e-13 * m0
+
+
 def test_parity_bubble_multigrid_levels(gea, o3):
     """The rising bubble on a grid with three multigrid levels
     (48x32x16 -> 24x16x8 -> 12x8x4)."""
