@@ -480,6 +480,16 @@ def run_ensemble(args):
 # KERNEL_MODEL; coarsening and restriction per coarse cell).
 KERNEL_MODEL_3D = {
     "g3_les": (5, 60, "f64"),
+    "g3_mx_r0mom": (31.5, 87, "f64"),
+    "g3_mx_mom": (11.5, 93, "f32"),
+    "g3_mx_u1": (7.5, 3, "f64"),
+    "g3_mx_r0h": (16.5, 31, "f64"),
+    "g3_mx_enth": (8.5, 31, "f32"),
+    "g3_mx_h1": (2.5, 1, "f64"),
+    "g3_mx_pupd": (1.5, 2, "f32"),
+    "g3_mx_spmv": (3, 15, "f32"),
+    "g3_mx_update": (3, 6, "f32"),
+    "g3_mx_papply": (2.5, 1, "f64"),
     "g3_pred": (31, 102, "f64"),
     "g3_mom": (23, 93, "f64"),
     "g3_kin": (4, 6, "f64"),
@@ -560,10 +570,46 @@ def run_3d(args):
         "ms_per_step_min": min(ms), "ms_per_step_median": statistics.median(ms),
         "gpu_launches": int(launches) * world, "clocks": clocks, "e2e": e2e, "roofline": roof,
     }
+    # the mixed-precision 3D step timed the same way, and its difference from
+    # the FP64 GPU step (equal to the 3D oracle to <= 1e-10) after 20 steps
+    sm = gea.Solver3D(g, wl.const, stream=stream, mixed=True)
+    sm.set_conservative(dev)
+    ms_m, launches_m, clocks_m = timed_steps(sm, stream, flush, args.steps, args.warmup, world, local)
+    st_m = sm.stats()
+    value_m = world * cells * args.steps / (sum(ms_m) / 1e3)
+    res["mixed_precision"] = {
+        "value": value_m, "unit": UNIT, "ms_per_step": statistics.mean(ms_m), "speedup_vs_fp64": value_m / value,
+        "cg_iters_last_step": st_m["cg_iters"], "jacobi_sweeps_last_step": [st_m["jac_u"], st_m["jac_h"]],
+        "gpu_launches": int(launches_m) * world, "clocks": clocks_m, "driver": st_m["driver"],
+        "error_vs_fp64": matched_error3(gea, wl, dev, stream, 20) if rank == 0 else None,
+    }
+    sm.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline3(args.cpu_seconds)
     if rank == 0:
         print(json.dumps(res), flush=True)
+
+
+def matched_error3(gea, wl, dev, stream, steps):
+    """The mixed 3D step against the FP64 3D step, both on this GPU from the
+    initial state: max |theta'| difference (K) and relative L2 per field
+    (velocities against the velocity vector's norm) after `steps` steps."""
+    import numpy as np
+    out = []
+    for mixed in (False, True):
+        s = gea.Solver3D(wl.grid, wl.const, stream=stream, mixed=mixed)
+        s.set_conservative(dev)
+        s.step(steps)
+        out.append(s.get_state())
+        s.close()
+    a, b = out
+    c = wl.const
+    th = lambda f: f["T"] * (c.p0 / f["p"]) ** (c.R / c.cp)
+    vel = np.sqrt(sum(np.linalg.norm(a[k]) ** 2 for k in ("u", "v", "w")))
+    rel = {k: float(np.linalg.norm(b[k] - a[k]) / np.linalg.norm(a[k])) for k in ("rho", "T", "p", "pp")}
+    rel.update({k: float(np.linalg.norm(b[k] - a[k]) / vel) for k in ("u", "v", "w")})
+    return {"steps": steps, "max_abs_dtheta_K": float(np.abs(th(b) - th(a)).max()), "rel_l2": rel,
+            "against": "FP64 GPU 3D step (equal to the 3D oracle to <= 1e-10 rel. L2)"}
 
 
 def cpu_baseline3(seconds):

@@ -16,8 +16,12 @@
  *    centred at ((i+1/2) dx, (j+1/2) dy, (k+1/2) dz) at index
  *    (k ny + j) nx + i.
  *  - Pressure split p = p' - rho g z (g > 0, z up), as in gea.h.
- *  - The constants are gea_constants of gea.h; flags and mp_rtol must be 0
- *    (no mixed precision in three dimensions). cs > 0 turns on Smagorinsky
+ *  - The constants are gea_constants of gea.h. flags: 0 or GEA_FLAG_MIXED,
+ *    the mixed-precision step as in gea.h (FP64 state, residuals and
+ *    updates; FP32 Jacobi on the momentum and enthalpy increments and FP32
+ *    multigrid CG on the pressure increment, each to mp_rtol times its
+ *    initial residual; mp_rtol 0 selects 1e-5, else 1e-7 <= mp_rtol < 1;
+ *    gea_stats.driver is then 2). cs > 0 turns on Smagorinsky
  *    LES: mu_eff = mu + rho^n (cs Delta)^2 |S| per cell, Delta =
  *    (dx dy dz)^(1/3), |S| = sqrt(2 S_ij S_ij) from central differences of
  *    u^n, and the diffusion of momentum and enthalpy takes the face means

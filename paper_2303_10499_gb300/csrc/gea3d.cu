@@ -176,11 +176,13 @@ __device__ double divg(const Args &a, int i, int j, int k)
 // group's block totals, the last group adds the group totals, each in a fixed
 // order. True in thread 0 of the very last block, with the totals in tot.
 // part holds kCntSlots doubles of group counters (zero between launches),
-// then NV x blocks block totals, then NV x groups group totals.
+// then NV x blocks block totals, then NV x groups group totals. T is the
+// type of the per-thread values and of the block sums (FP32 in the inner
+// solves of the mixed step); block totals onward are FP64.
 constexpr int kGroup = 1024;
 constexpr int kCntSlots = 2048;   // 4096 group counters
-template <int NV>
-__device__ bool gsum(const double (&v)[NV], double *red, double *part, unsigned *counter, double (&tot)[NV])
+template <int NV, class T = double>
+__device__ bool gsum(const T (&v)[NV], double *red, double *part, unsigned *counter, double (&tot)[NV])
 {
     __shared__ int flag;
     const int tid = threadIdx.x + threadIdx.y * TX;
@@ -190,11 +192,11 @@ __device__ bool gsum(const double (&v)[NV], double *red, double *part, unsigned 
     const int gn = min(kGroup, nb - g0);
     unsigned *gcnt = reinterpret_cast<unsigned *>(part);
     double *p1 = part + kCntSlots, *p2 = p1 + (size_t)NV * nb;
-    double bt[NV];
-    gea::block_sum<NV>(v, red, bt);
+    T bt[NV];
+    gea::block_sum<NV, T>(v, reinterpret_cast<T *>(red), bt);
     if (tid == 0) {
 #pragma unroll
-        for (int m = 0; m < NV; ++m) p1[(size_t)m * nb + bid] = bt[m];
+        for (int m = 0; m < NV; ++m) p1[(size_t)m * nb + bid] = (double)bt[m];
         __threadfence();
         flag = atomicAdd(&gcnt[grp], 1u) == (unsigned)gn - 1u;
     }
@@ -672,9 +674,30 @@ __device__ __forceinline__ void fin_helm(Sc *sc, const double (&t)[2], double to
     if (!isfinite(t[0]) || !isfinite(t[1])) sc->status = GEA_ERR_NONFINITE;
 }
 
+// Mixed step: the inner FP32 solve's tolerance is relative to the initial
+// residual r0 = b - A p'_prev (kept in b2); nothing to solve if r0 is already
+// at the FP64 tolerance relative to b.
+__device__ __forceinline__ void fin_helm_mixed(Sc *sc, const double (&t)[2], double tol2, int corr)
+{
+    sc->b2 = t[1];
+    sc->r2 = t[1];
+    sc->cg_it = 0;
+    sc->corr = corr;
+    sc->trips[L_CG] = 0;
+    sc->rz = 0.0;
+    sc->beta = 0.0;
+    sc->done[L_CG] = t[1] <= tol2 * t[0];
+    sc->cg_iters[corr] = 0;
+    sc->cg_relres[corr] = 1.0;
+    if (!isfinite(t[0]) || !isfinite(t[1])) sc->status = GEA_ERR_NONFINITE;
+}
+
 // b_i = (rho^n_i + psi_i rho2_i g z_i)/dt - sum_f D_f/Delta_f [H_f . n + g z_f (rho2_N - rho2_i)/Delta_f],
 // r = b - A x with x = xin (copied to xout), p0 = 0; acc += (b^2, r^2).
-__global__ void k_helm_rhs(Args a, Lev L, const double *xin, double *xout, int corr)
+// Mixed step (mr given): r0 rounded to FP32 into mr, and a zero FP32
+// increment mx and first direction mp0.
+__global__ void k_helm_rhs(Args a, Lev L, const double *xin, double *xout, int corr, float *mr = nullptr,
+                           float *mx = nullptr, float *mp0 = nullptr)
 {
     if (a.sc->status) return;
     __shared__ double red[2 * NT];
@@ -703,10 +726,18 @@ __global__ void k_helm_rhs(Args a, Lev L, const double *xin, double *xout, int c
         L.r[q] = r;
         xout[q] = ld(&xin[q]);
         a.p0[q] = 0.0;
+        if (mr) {
+            mr[q] = (float)r;
+            mx[q] = 0.0f;
+            mp0[q] = 0.0f;
+        }
         acc[0] = b * b;
         acc[1] = r * r;
     }
-    if (gsum<2>(acc, red, a.part, &a.sc->counters[C_HELM], tot)) fin_helm(a.sc, tot, a.ctol2, corr);
+    if (gsum<2>(acc, red, a.part, &a.sc->counters[C_HELM], tot)) {
+        if (mr) fin_helm_mixed(a.sc, tot, a.ctol2, corr);
+        else fin_helm(a.sc, tot, a.ctol2, corr);
+    }
 }
 
 // ---- multigrid V(1,1) cycle in FP32 (the preconditioner of the FP64 CG) ----
@@ -816,7 +847,9 @@ __global__ void k_mg_up(Lev32 f, const RT *r, const float *ec, Geo cg, OT *out, 
 {
     if (over(sc, L_CG)) return;
     __shared__ double red[NT];
-    double acc[1] = {0.0}, tot[1];
+    OT acc[1] = {(OT)0}, dtot[1];
+    double tot[1];
+    (void)dtot;
     int i, j, k;
     if (cell(f.G, i, j, k)) {
         const Geo &G = f.G;
@@ -827,28 +860,31 @@ __global__ void k_mg_up(Lev32 f, const RT *r, const float *ec, Geo cg, OT *out, 
         const RT rq = __ldg(&r[q]);
         const float z = ef(q, i, j, k) + ldf(&f.w[q]) * (tof(rq) - helm32(f, ef, i, j, k));
         out[q] = (OT)z;
-        acc[0] = (double)rq * (double)z;
+        acc[0] = (OT)rq * (OT)z;   // FP64 for the FP64 CG, FP32 for the mixed step's
     }
     if (!finest) return;
-    if (gsum<1>(acc, red, part, &sc->counters[C_RZ], tot)) fin_rz(sc, tot[0]);
+    if (gsum<1, OT>(acc, red, part, &sc->counters[C_RZ], tot)) fin_rz(sc, tot[0]);
 }
 
-// One level only: z = e + (omega/d)(r - A e), e = (omega/d) r; acc += r.z.
-__global__ void k_mg_single(Lev32 f, const double *r, double *out, Sc *sc, double *part)
+// One level only: z = e + (omega/d)(r - A e), e = (omega/d) r; acc += r.z
+// (T = double: the FP64 CG; T = float: the mixed step's FP32 CG).
+template <class T>
+__global__ void k_mg_single(Lev32 f, const T *r, T *out, Sc *sc, double *part)
 {
     if (over(sc, L_CG)) return;
     __shared__ double red[NT];
-    double acc[1] = {0.0}, tot[1];
+    T acc[1] = {(T)0};
+    double tot[1];
     int i, j, k;
     if (cell(f.G, i, j, k)) {
         const long long q = id3(f.G, i, j, k);
         auto e = [&](long long qq, int, int, int) { return ldf(&f.w[qq]) * (float)__ldg(&r[qq]); };
-        const double rq = __ldg(&r[q]);
+        const T rq = __ldg(&r[q]);
         const float z = e(q, i, j, k) + ldf(&f.w[q]) * ((float)rq - helm32(f, e, i, j, k));
-        out[q] = (double)z;
-        acc[0] = rq * (double)z;
+        out[q] = (T)z;
+        acc[0] = rq * (T)z;
     }
-    if (gsum<1>(acc, red, part, &sc->counters[C_RZ], tot)) fin_rz(sc, tot[0]);
+    if (gsum<1, T>(acc, red, part, &sc->counters[C_RZ], tot)) fin_rz(sc, tot[0]);
 }
 
 // ---- CG steps (directions alternate between p0 and p1 by parity) ----
@@ -951,6 +987,329 @@ __global__ void k_correct(Args a)
     if (k == G.nz - 1) a.N.phiz[q + sz] = 0.0;
 }
 
+// ---- the mixed-precision step (GEA_FLAG_MIXED) ----
+//
+// Each implicit solve is one defect correction: an FP64 residual r0 of the
+// FP64 operator at the previous value, an FP32 solve for the increment with
+// FP32 copies of the operator to ||r|| <= mp_rtol ||r0||, and the FP64
+// update. Increments take the homogeneous form of each wall rule (the h
+// ghost offset cancels). FP32 reductions are summed in FP32 within a block
+// and in FP64 across blocks.
+
+// FP32 data of the mixed step: the stencil weights and reciprocals, the
+// FP64 residuals rounded to FP32, the increments (Jacobi ping-pong), and the
+// pressure increment with its CG vectors (r the FP32 residual, z the
+// preconditioned residual).
+struct Mx {
+    float *c[NCF];
+    float *dinvu, *dinvh, *r0u, *r0v, *r0w, *r0h;
+    float *du[2], *dv[2], *dw[2], *dh[2];
+    float *x, *p0, *p1, *q, *r, *z;
+    double tol2;
+};
+
+// Increment at (i,j,k) with at most one index one layer outside the box: the
+// homogeneous ghost of wall rule BC (odd for the wall-normal velocity, even
+// otherwise).
+template <int BC>
+__device__ __forceinline__ float atf(const Geo &G, const float *X, int i, int j, int k)
+{
+    if (i < 0) { const float v = ldf(&X[id3(G, 0, j, k)]); return BC == U3 ? -v : v; }
+    if (i >= G.nx) { const float v = ldf(&X[id3(G, G.nx - 1, j, k)]); return BC == U3 ? -v : v; }
+    if (j < 0) { const float v = ldf(&X[id3(G, i, 0, k)]); return BC == V3 ? -v : v; }
+    if (j >= G.ny) { const float v = ldf(&X[id3(G, i, G.ny - 1, k)]); return BC == V3 ? -v : v; }
+    if (k < 0) { const float v = ldf(&X[id3(G, i, j, 0)]); return BC == W3 ? -v : v; }
+    if (k >= G.nz) { const float v = ldf(&X[id3(G, i, j, G.nz - 1)]); return BC == W3 ? -v : v; }
+    return ldf(&X[id3(G, i, j, k)]);
+}
+
+struct W13f {
+    float w[NCF];
+};
+
+__device__ __forceinline__ W13f weightsf(const Mx &m, long long q)
+{
+    W13f c;
+#pragma unroll
+    for (int s = 0; s < NCF; ++s) c.w[s] = ldf(&m.c[s][q]);
+    return c;
+}
+
+// Off-centre part of the FP32 stencil applied to an increment.
+template <int BC>
+__device__ __forceinline__ float tofff(const Geo &G, const W13f &c, const float *X, int i, int j, int k)
+{
+    float t = c.w[1] * atf<BC>(G, X, i - 2, j, k);
+    t = fmaf(c.w[2], atf<BC>(G, X, i - 1, j, k), t);
+    t = fmaf(c.w[3], atf<BC>(G, X, i + 1, j, k), t);
+    t = fmaf(c.w[4], atf<BC>(G, X, i + 2, j, k), t);
+    t = fmaf(c.w[5], atf<BC>(G, X, i, j - 2, k), t);
+    t = fmaf(c.w[6], atf<BC>(G, X, i, j - 1, k), t);
+    t = fmaf(c.w[7], atf<BC>(G, X, i, j + 1, k), t);
+    t = fmaf(c.w[8], atf<BC>(G, X, i, j + 2, k), t);
+    t = fmaf(c.w[9], atf<BC>(G, X, i, j, k - 2), t);
+    t = fmaf(c.w[10], atf<BC>(G, X, i, j, k - 1), t);
+    t = fmaf(c.w[11], atf<BC>(G, X, i, j, k + 1), t);
+    t = fmaf(c.w[12], atf<BC>(G, X, i, j, k + 2), t);
+    return t;
+}
+
+// Compact Laplacian of an increment with even ghosts (the enthalpy's Pr
+// correction).
+__device__ __forceinline__ float lapf(const Geo &G, const float *X, int i, int j, int k)
+{
+    const float xc = atf<E3>(G, X, i, j, k);
+    return (atf<E3>(G, X, i + 1, j, k) - xc + atf<E3>(G, X, i - 1, j, k) - xc) * (float)G.idx2 +
+           (atf<E3>(G, X, i, j + 1, k) - xc + atf<E3>(G, X, i, j - 1, k) - xc) * (float)G.idy2 +
+           (atf<E3>(G, X, i, j, k + 1) - xc + atf<E3>(G, X, i, j, k - 1) - xc) * (float)G.idz2;
+}
+
+__device__ __forceinline__ void copy_cellf(const Geo &G, const float *x, float *y)
+{
+    int i, j, k;
+    if (cell(G, i, j, k)) y[id3(G, i, j, k)] = ldf(&x[id3(G, i, j, k)]);
+}
+
+// FP64 residuals r0 = b - T(u^n) of the three momentum components, the FP32
+// copies of the stencil and the reciprocals, and the first FP32 sweep from
+// zero, du = r0 / T_CC; the loop's reference norms are ||r0||^2.
+__global__ void k_mx_r0mom(Args a, Mx m)
+{
+    Sc *sc = a.sc;
+    if (sc->status) return;
+    __shared__ double red[3 * NT];
+    double acc[3] = {0.0, 0.0, 0.0}, tot[3];
+    int i, j, k;
+    if (cell(a.G, i, j, k)) {
+        const long long q = id3(a.G, i, j, k);
+        const W13 c = weights(a, q);
+        const double u0 = ld(&a.S.u[q]);
+        const double ru = ld(&a.bu[q]) - fma(c.w[0], u0, toff<U3>(a, c, a.S.u, i, j, k));
+        asm volatile("" ::: "memory");
+        const double v0 = ld(&a.S.v[q]);
+        const double rv = ld(&a.bv[q]) - fma(c.w[0], v0, toff<V3>(a, c, a.S.v, i, j, k));
+        asm volatile("" ::: "memory");
+        const double w0 = ld(&a.S.w[q]);
+        const double rw = ld(&a.bw[q]) - fma(c.w[0], w0, toff<W3>(a, c, a.S.w, i, j, k));
+#pragma unroll
+        for (int s = 0; s < NCF; ++s) m.c[s][q] = (float)c.w[s];
+        const float di = (float)ld(&a.dinvu[q]);
+        m.dinvu[q] = di;
+        m.dinvh[q] = (float)ld(&a.dinvh[q]);
+        const float fu = (float)ru, fv = (float)rv, fw = (float)rw;
+        m.r0u[q] = fu; m.r0v[q] = fv; m.r0w[q] = fw;
+        m.du[0][q] = fu * di; m.dv[0][q] = fv * di; m.dw[0][q] = fw * di;
+        acc[0] = ru * ru; acc[1] = rv * rv; acc[2] = rw * rw;
+    }
+    if (gsum<3>(acc, red, a.part, &sc->counters[C_MOM], tot)) {
+        for (int s = 0; s < 3; ++s) sc->bn2[s] = tot[s];
+        sc->done[L_MOM] = 0;
+        sc->trips[L_MOM] = 0;
+        sc->sweeps[0] = 0;
+        if (!isfinite(tot[0]) || !isfinite(tot[1]) || !isfinite(tot[2])) sc->status = GEA_ERR_NONFINITE;
+    }
+}
+
+// One FP32 Jacobi sweep of the momentum increments (pairs as in the FP64
+// step: the second copies once the first met the tolerance).
+__global__ void k_mx_mom(Args a, Mx m, const float *ui, const float *vi, const float *wi, float *uo, float *vo,
+                         float *wo, int second)
+{
+    Sc *sc = a.sc;
+    if (sc->status) return;
+    if (second && sc->done[L_MOM]) {
+        copy_cellf(a.G, ui, uo);
+        copy_cellf(a.G, vi, vo);
+        copy_cellf(a.G, wi, wo);
+        return;
+    }
+    __shared__ double red[3 * NT];
+    float acc[3] = {0.0f, 0.0f, 0.0f};
+    double tot[3];
+    int i, j, k;
+    if (cell(a.G, i, j, k)) {
+        const Geo &G = a.G;
+        const long long q = id3(G, i, j, k);
+        const W13f c = weightsf(m, q);
+        const float di = ldf(&m.dinvu[q]);
+        const float u0 = ldf(&ui[q]), v0 = ldf(&vi[q]), w0 = ldf(&wi[q]);
+        const float ru = ldf(&m.r0u[q]) - fmaf(c.w[0], u0, tofff<U3>(G, c, ui, i, j, k));
+        const float rv = ldf(&m.r0v[q]) - fmaf(c.w[0], v0, tofff<V3>(G, c, vi, i, j, k));
+        const float rw = ldf(&m.r0w[q]) - fmaf(c.w[0], w0, tofff<W3>(G, c, wi, i, j, k));
+        uo[q] = fmaf(ru, di, u0);
+        vo[q] = fmaf(rv, di, v0);
+        wo[q] = fmaf(rw, di, w0);
+        acc[0] = ru * ru; acc[1] = rv * rv; acc[2] = rw * rw;
+    }
+    if (gsum<3, float>(acc, red, a.part, &sc->counters[C_MOM], tot)) {
+        sc->sweeps[0] += 1;
+        if (!isfinite(tot[0]) || !isfinite(tot[1]) || !isfinite(tot[2])) sc->status = GEA_ERR_NONFINITE;
+        else if (tot[0] <= m.tol2 * sc->bn2[0] && tot[1] <= m.tol2 * sc->bn2[1] && tot[2] <= m.tol2 * sc->bn2[2])
+            sc->done[L_MOM] = 1;
+    }
+}
+
+// u^{n+1/3} = u^n + du (FP64).
+__global__ void k_mx_u1(Args a, const float *du, const float *dv, const float *dw)
+{
+    if (a.sc->status) return;
+    int i, j, k;
+    if (!cell(a.G, i, j, k)) return;
+    const long long q = id3(a.G, i, j, k);
+    a.ua[q] = ld(&a.S.u[q]) + (double)ldf(&du[q]);
+    a.va[q] = ld(&a.S.v[q]) + (double)ldf(&dv[q]);
+    a.wa[q] = ld(&a.S.w[q]) + (double)ldf(&dw[q]);
+}
+
+// FP64 residual r0 = b_h - T_h(h^n) (h^n with its wall rule), rounded to FP32,
+// and the first FP32 sweep dh = r0 / T_h,CC; the loop's reference ||r0||^2.
+__global__ void k_mx_r0h(Args a, Mx m)
+{
+    Sc *sc = a.sc;
+    if (sc->status) return;
+    __shared__ double red[NT];
+    double acc[1] = {0.0}, tot[1];
+    int i, j, k;
+    if (cell(a.G, i, j, k)) {
+        const long long q = id3(a.G, i, j, k);
+        const W13 c = weights(a, q);
+        const double h0 = ld(&a.S.h[q]);
+        double t = fma(c.w[0], h0, toff<H3>(a, c, a.S.h, i, j, k));
+        if (a.F.nuh != a.F.mu) t = fma(a.F.mu - a.F.nuh, lap<H3>(a, a.S.h, i, j, k), t);
+        const double r0 = ld(&a.bh[q]) - t;
+        const float f = (float)r0;
+        m.r0h[q] = f;
+        m.dh[0][q] = f * ldf(&m.dinvh[q]);
+        acc[0] = r0 * r0;
+    }
+    if (gsum<1>(acc, red, a.part, &sc->counters[C_ENTH], tot)) {
+        sc->bn2[3] = tot[0];
+        sc->done[L_ENTH] = 0;
+        sc->trips[L_ENTH] = 0;
+        sc->sweeps[1] = 0;
+        if (!isfinite(tot[0])) sc->status = GEA_ERR_NONFINITE;
+    }
+}
+
+// One FP32 Jacobi sweep of the enthalpy increment (even ghosts).
+__global__ void k_mx_enth(Args a, Mx m, const float *hi, float *ho, int second)
+{
+    Sc *sc = a.sc;
+    if (sc->status) return;
+    if (second && sc->done[L_ENTH]) {
+        copy_cellf(a.G, hi, ho);
+        return;
+    }
+    __shared__ double red[NT];
+    float acc[1] = {0.0f};
+    double tot[1];
+    int i, j, k;
+    if (cell(a.G, i, j, k)) {
+        const Geo &G = a.G;
+        const long long q = id3(G, i, j, k);
+        const W13f c = weightsf(m, q);
+        const float h0 = ldf(&hi[q]);
+        float t = fmaf(c.w[0], h0, tofff<E3>(G, c, hi, i, j, k));
+        if (a.F.nuh != a.F.mu) t = fmaf((float)(a.F.mu - a.F.nuh), lapf(G, hi, i, j, k), t);
+        const float r = ldf(&m.r0h[q]) - t;
+        ho[q] = fmaf(r, ldf(&m.dinvh[q]), h0);
+        acc[0] = r * r;
+    }
+    if (gsum<1, float>(acc, red, a.part, &sc->counters[C_ENTH], tot)) {
+        sc->sweeps[1] += 1;
+        if (!isfinite(tot[0])) sc->status = GEA_ERR_NONFINITE;
+        else if (tot[0] <= m.tol2 * sc->bn2[3]) sc->done[L_ENTH] = 1;
+    }
+}
+
+// h^{n+1} = h^n + dh into ha (FP64).
+__global__ void k_mx_h1(Args a, const float *dh)
+{
+    if (a.sc->status) return;
+    int i, j, k;
+    if (!cell(a.G, i, j, k)) return;
+    const long long q = id3(a.G, i, j, k);
+    a.ha[q] = ld(&a.S.h[q]) + (double)ldf(&dh[q]);
+}
+
+// FP32 CG on the pressure increment with the FP32 finest operator M0.
+
+// p = z + beta p_old
+__global__ void k_mx_pupd(Args a, Mx m, Lev32 M0)
+{
+    Sc *sc = a.sc;
+    if (over(sc, L_CG)) return;
+    int i, j, k;
+    if (!cell(M0.G, i, j, k)) return;
+    const int it = sc->cg_it;
+    const float *pold = (it & 1) ? m.p1 : m.p0;
+    float *pnew = (it & 1) ? m.p0 : m.p1;
+    const long long q = id3(M0.G, i, j, k);
+    pnew[q] = fmaf((float)sc->beta, ldf(&pold[q]), ldf(&m.z[q]));
+}
+
+// q = A p, acc += p.q; alpha = rz / p.q
+__global__ void k_mx_spmv(Args a, Mx m, Lev32 M0)
+{
+    Sc *sc = a.sc;
+    if (over(sc, L_CG)) return;
+    __shared__ double red[NT];
+    float acc[1] = {0.0f};
+    double tot[1];
+    const float *p = (sc->cg_it & 1) ? m.p0 : m.p1;
+    int i, j, k;
+    if (cell(M0.G, i, j, k)) {
+        const long long q = id3(M0.G, i, j, k);
+        const float Ap = helm32(M0, [&](long long qq, int, int, int) { return ldf(&p[qq]); }, i, j, k);
+        m.q[q] = Ap;
+        acc[0] = ldf(&p[q]) * Ap;
+    }
+    if (gsum<1, float>(acc, red, a.part, &sc->counters[C_PQ], tot)) {
+        sc->pq = tot[0];
+        sc->alpha = tot[0] != 0.0 ? sc->rz / tot[0] : 0.0;
+        if (!isfinite(tot[0])) sc->status = GEA_ERR_NONFINITE;
+    }
+}
+
+// x += alpha p, r -= alpha q; acc += r^2, relative to ||r0||^2 with mp_rtol.
+__global__ void k_mx_update(Args a, Mx m, Lev32 M0)
+{
+    Sc *sc = a.sc;
+    if (over(sc, L_CG)) return;
+    __shared__ double red[NT];
+    float acc[1] = {0.0f};
+    double tot[1];
+    const float *p = (sc->cg_it & 1) ? m.p0 : m.p1;
+    const float alpha = (float)sc->alpha;
+    int i, j, k;
+    if (cell(M0.G, i, j, k)) {
+        const long long q = id3(M0.G, i, j, k);
+        m.x[q] = fmaf(alpha, ldf(&p[q]), m.x[q]);
+        const float rn = fmaf(-alpha, ldf(&m.q[q]), m.r[q]);
+        m.r[q] = rn;
+        acc[0] = rn * rn;
+    }
+    if (gsum<1, float>(acc, red, a.part, &sc->counters[C_UPD], tot)) {
+        const int n = sc->cg_it + 1;
+        sc->cg_it = n;
+        sc->r2 = tot[0];
+        sc->cg_iters[sc->corr] = n;
+        sc->cg_relres[sc->corr] = sc->b2 > 0.0 ? sqrt(tot[0] / sc->b2) : 0.0;
+        if (!isfinite(tot[0])) sc->status = GEA_ERR_NONFINITE;
+        else if (tot[0] <= m.tol2 * sc->b2) sc->done[L_CG] = 1;
+    }
+}
+
+// p' += dp (FP64).
+__global__ void k_mx_papply(Args a, Mx m)
+{
+    if (a.sc->status) return;
+    int i, j, k;
+    if (!cell(a.G, i, j, k)) return;
+    const long long q = id3(a.G, i, j, k);
+    a.N.pp[q] = ld(&a.N.pp[q]) + (double)ldf(&m.x[q]);
+}
+
 // ---- loop control and step bookkeeping (one thread) ----
 
 __global__ void k_ctl(Sc *sc, cudaGraphConditionalHandle h, int graph, int which, int maxtrips, int body)
@@ -1000,6 +1359,8 @@ struct gea3d_ctx {
     double *dtr1;                         // dt / rho1
     double *kin;                          // K1
     double *mueff = nullptr;              // LES eddy viscosity field
+    bool mixed = false;                   // GEA_FLAG_MIXED
+    Mx mx{};                              // FP32 data of the mixed step
     Cf cf;                                // transport stencil weights
     double *stage = nullptr;              // dense conservative fields (5 arrays)
     std::vector<Lev> L;                   // the FP64 fine-level operator
@@ -1161,9 +1522,45 @@ int vcycle(gea3d_ctx *ctx, const Args &a, cudaStream_t st, Trace3 *tr)
     Lev32 *M = ctx->M.data();
     Lev &F = ctx->L[0];
     const int nlev = (int)ctx->M.size();
+    if (ctx->mixed) {
+        // the mixed step's FP32 CG: from the FP32 residual r to z, both FP32
+        const Mx &m = ctx->mx;
+        if (nlev == 1) {
+            traced(tr, "g3_mg_single", F.G, st, [&] {
+                k_mg_single<float><<<grid_of(F.G), kBlk, 0, st>>>(M[0], m.r, m.z, a.sc, a.part);
+            });
+            return 1;
+        }
+        int n = 0;
+        traced(tr, "g3_mg_down", M[1].G, st, [&] {
+            k_mg_down<float><<<grid_of(M[1].G), kBlk, 0, st>>>(M[0], m.r, M[1], a.sc);
+        });
+        ++n;
+        for (int l = 1; l + 1 < nlev; ++l, ++n)
+            traced(tr, "g3_mg_down", M[l + 1].G, st, [&] {
+                k_mg_down<float><<<grid_of(M[l + 1].G), kBlk, 0, st>>>(M[l], M[l].r, M[l + 1], a.sc);
+            });
+        Lev32 &C = M[nlev - 1];
+        for (int s = 0; s < kCoarseSweeps; ++s, ++n) {
+            float *out = ((kCoarseSweeps - 1 - s) % 2 == 0) ? C.e2 : C.e;
+            const float *in = (out == C.e2) ? C.e : C.e2;
+            traced(tr, "g3_mg_coarse", C.G, st, [&] {
+                k_mg_coarse<<<grid_of(C.G), kBlk, 0, st>>>(C, in, out, s == 0, a.sc);
+            });
+        }
+        for (int l = nlev - 2; l >= 1; --l, ++n)
+            traced(tr, "g3_mg_up", M[l].G, st, [&] {
+                k_mg_up<float, float><<<grid_of(M[l].G), kBlk, 0, st>>>(M[l], M[l].r, M[l + 1].e2, M[l + 1].G,
+                                                                         M[l].e2, 0, a.sc, a.part);
+            });
+        traced(tr, "g3_mg_up", F.G, st, [&] {
+            k_mg_up<float, float><<<grid_of(F.G), kBlk, 0, st>>>(M[0], m.r, M[1].e2, M[1].G, m.z, 1, a.sc, a.part);
+        });
+        return n + 1;
+    }
     if (nlev == 1) {
         traced(tr, "g3_mg_single", F.G, st, [&] {
-            k_mg_single<<<grid_of(F.G), kBlk, 0, st>>>(M[0], F.r, F.e2, a.sc, a.part);
+            k_mg_single<double><<<grid_of(F.G), kBlk, 0, st>>>(M[0], F.r, F.e2, a.sc, a.part);
         });
         return 1;
     }
@@ -1217,20 +1614,48 @@ int record3(gea3d_ctx *ctx, int from, cudaStream_t s, bool graph, Trace3 *tr)
     k_begin<<<1, 1, 0, s>>>(a.sc); ++fixed;
     if (ctx->mueff) { traced(tr, "g3_les", G, s, [&] { k_les<<<grid, kBlk, 0, s>>>(a); }); ++fixed; }
     traced(tr, "g3_pred", G, s, [&] { k_pred<<<grid, kBlk, 0, s>>>(a); }); ++fixed;
-    rc = loop(L_MOM, jtrips, [&](cudaStream_t bs, cudaGraphConditionalHandle h) {
-        traced(tr, "g3_mom", G, bs, [&] { k_mom<<<grid, kBlk, 0, bs>>>(a, a.ua, a.va, a.wa, a.ub, a.vb, a.wb, 0); });
-        traced(tr, "g3_mom", G, bs, [&] { k_mom<<<grid, kBlk, 0, bs>>>(a, a.ub, a.vb, a.wb, a.ua, a.va, a.wa, 1); });
-        k_ctl<<<1, 1, 0, bs>>>(a.sc, h, gr, L_MOM, jtrips, 3);
-    });
-    if (rc) return rc;
+    const Mx &m = ctx->mx;
+    if (ctx->mixed) {
+        // FP64 residuals, FP32 Jacobi on the increments (pairs end in du[0]), FP64 update
+        traced(tr, "g3_mx_r0mom", G, s, [&] { k_mx_r0mom<<<grid, kBlk, 0, s>>>(a, m); }); ++fixed;
+        rc = loop(L_MOM, jtrips, [&](cudaStream_t bs, cudaGraphConditionalHandle h) {
+            traced(tr, "g3_mx_mom", G, bs, [&] {
+                k_mx_mom<<<grid, kBlk, 0, bs>>>(a, m, m.du[0], m.dv[0], m.dw[0], m.du[1], m.dv[1], m.dw[1], 0);
+            });
+            traced(tr, "g3_mx_mom", G, bs, [&] {
+                k_mx_mom<<<grid, kBlk, 0, bs>>>(a, m, m.du[1], m.dv[1], m.dw[1], m.du[0], m.dv[0], m.dw[0], 1);
+            });
+            k_ctl<<<1, 1, 0, bs>>>(a.sc, h, gr, L_MOM, jtrips, 3);
+        });
+        if (rc) return rc;
+        traced(tr, "g3_mx_u1", G, s, [&] { k_mx_u1<<<grid, kBlk, 0, s>>>(a, m.du[0], m.dv[0], m.dw[0]); }); ++fixed;
+    } else {
+        rc = loop(L_MOM, jtrips, [&](cudaStream_t bs, cudaGraphConditionalHandle h) {
+            traced(tr, "g3_mom", G, bs, [&] { k_mom<<<grid, kBlk, 0, bs>>>(a, a.ua, a.va, a.wa, a.ub, a.vb, a.wb, 0); });
+            traced(tr, "g3_mom", G, bs, [&] { k_mom<<<grid, kBlk, 0, bs>>>(a, a.ub, a.vb, a.wb, a.ua, a.va, a.wa, 1); });
+            k_ctl<<<1, 1, 0, bs>>>(a.sc, h, gr, L_MOM, jtrips, 3);
+        });
+        if (rc) return rc;
+    }
     traced(tr, "g3_kin", G, s, [&] { k_kin<<<grid, kBlk, 0, s>>>(a, a.ua, a.va, a.wa); }); ++fixed;
     traced(tr, "g3_enth_rhs", G, s, [&] { k_enth_rhs<<<grid, kBlk, 0, s>>>(a, a.wa); }); ++fixed;
-    rc = loop(L_ENTH, jtrips, [&](cudaStream_t bs, cudaGraphConditionalHandle h) {
-        traced(tr, "g3_enth", G, bs, [&] { k_enth<<<grid, kBlk, 0, bs>>>(a, a.ha, a.hb, 0); });
-        traced(tr, "g3_enth", G, bs, [&] { k_enth<<<grid, kBlk, 0, bs>>>(a, a.hb, a.ha, 1); });
-        k_ctl<<<1, 1, 0, bs>>>(a.sc, h, gr, L_ENTH, jtrips, 3);
-    });
-    if (rc) return rc;
+    if (ctx->mixed) {
+        traced(tr, "g3_mx_r0h", G, s, [&] { k_mx_r0h<<<grid, kBlk, 0, s>>>(a, m); }); ++fixed;
+        rc = loop(L_ENTH, jtrips, [&](cudaStream_t bs, cudaGraphConditionalHandle h) {
+            traced(tr, "g3_mx_enth", G, bs, [&] { k_mx_enth<<<grid, kBlk, 0, bs>>>(a, m, m.dh[0], m.dh[1], 0); });
+            traced(tr, "g3_mx_enth", G, bs, [&] { k_mx_enth<<<grid, kBlk, 0, bs>>>(a, m, m.dh[1], m.dh[0], 1); });
+            k_ctl<<<1, 1, 0, bs>>>(a.sc, h, gr, L_ENTH, jtrips, 3);
+        });
+        if (rc) return rc;
+        traced(tr, "g3_mx_h1", G, s, [&] { k_mx_h1<<<grid, kBlk, 0, s>>>(a, m.dh[0]); }); ++fixed;
+    } else {
+        rc = loop(L_ENTH, jtrips, [&](cudaStream_t bs, cudaGraphConditionalHandle h) {
+            traced(tr, "g3_enth", G, bs, [&] { k_enth<<<grid, kBlk, 0, bs>>>(a, a.ha, a.hb, 0); });
+            traced(tr, "g3_enth", G, bs, [&] { k_enth<<<grid, kBlk, 0, bs>>>(a, a.hb, a.ha, 1); });
+            k_ctl<<<1, 1, 0, bs>>>(a.sc, h, gr, L_ENTH, jtrips, 3);
+        });
+        if (rc) return rc;
+    }
     traced(tr, "g3_eos", G, s, [&] { k_eos<<<grid, kBlk, 0, s>>>(a, L[0], M[0], a.ha); }); ++fixed;
     traced(tr, "g3_faces", G, s, [&] { k_faces<<<grid, kBlk, 0, s>>>(a, L[0], M[0]); }); ++fixed;
     traced(tr, "g3_diag", G, s, [&] { k_diag<<<grid, kBlk, 0, s>>>(L[0], M[0], a.sc); }); ++fixed;
@@ -1243,18 +1668,31 @@ int record3(gea3d_ctx *ctx, int from, cudaStream_t s, bool graph, Trace3 *tr)
         const double *U = c == 0 ? a.ua : a.N.u, *V = c == 0 ? a.va : a.N.v, *W = c == 0 ? a.wa : a.N.w;
         traced(tr, "g3_H", G, s, [&] { k_H<<<grid, kBlk, 0, s>>>(a, U, V, W); }); ++fixed;
         traced(tr, "g3_helm_rhs", G, s, [&] {
-            k_helm_rhs<<<grid, kBlk, 0, s>>>(a, L[0], c == 0 ? a.S.pp : a.N.pp, a.N.pp, c);
+            if (ctx->mixed)
+                k_helm_rhs<<<grid, kBlk, 0, s>>>(a, L[0], c == 0 ? a.S.pp : a.N.pp, a.N.pp, c, m.r, m.x, m.p0);
+            else
+                k_helm_rhs<<<grid, kBlk, 0, s>>>(a, L[0], c == 0 ? a.S.pp : a.N.pp, a.N.pp, c);
         });
         ++fixed;
         fixed += vcycle(ctx, a, s, tr);
         rc = loop(L_CG, ctx->C.cg_maxit, [&](cudaStream_t bs, cudaGraphConditionalHandle h) {
-            traced(tr, "g3_pupd", G, bs, [&] { k_pupd<<<grid, kBlk, 0, bs>>>(a, L[0]); });
-            traced(tr, "g3_spmv", G, bs, [&] { k_spmv<<<grid, kBlk, 0, bs>>>(a, L[0]); });
-            traced(tr, "g3_update", G, bs, [&] { k_update<<<grid, kBlk, 0, bs>>>(a, L[0], a.N.pp, ctx->C.cg_maxit); });
+            if (ctx->mixed) {
+                traced(tr, "g3_mx_pupd", G, bs, [&] { k_mx_pupd<<<grid, kBlk, 0, bs>>>(a, m, M[0]); });
+                traced(tr, "g3_mx_spmv", G, bs, [&] { k_mx_spmv<<<grid, kBlk, 0, bs>>>(a, m, M[0]); });
+                traced(tr, "g3_mx_update", G, bs, [&] { k_mx_update<<<grid, kBlk, 0, bs>>>(a, m, M[0]); });
+            } else {
+                traced(tr, "g3_pupd", G, bs, [&] { k_pupd<<<grid, kBlk, 0, bs>>>(a, L[0]); });
+                traced(tr, "g3_spmv", G, bs, [&] { k_spmv<<<grid, kBlk, 0, bs>>>(a, L[0]); });
+                traced(tr, "g3_update", G, bs, [&] { k_update<<<grid, kBlk, 0, bs>>>(a, L[0], a.N.pp, ctx->C.cg_maxit); });
+            }
             vcycle(ctx, a, bs, tr);
             k_ctl<<<1, 1, 0, bs>>>(a.sc, h, gr, L_CG, ctx->C.cg_maxit, body_cg);
         });
         if (rc) return rc;
+        if (ctx->mixed) {
+            traced(tr, "g3_mx_papply", G, s, [&] { k_mx_papply<<<grid, kBlk, 0, s>>>(a, m); });
+            ++fixed;
+        }
         traced(tr, "g3_correct", G, s, [&] { k_correct<<<grid, kBlk, 0, s>>>(a); }); ++fixed;
     }
     ++fixed;
@@ -1292,7 +1730,9 @@ int gea3d_create(const gea3d_grid *grid, const gea_constants *c, gea3d_ctx **out
     if ((long long)grid->nx * grid->ny * grid->nz > (1LL << 31) / 4) return GEA_ERR_INVAL;
     if (!(c->R > 0) || !(c->cp > c->R) || !(c->g >= 0) || !(c->p0 > 0) || !(c->mu >= 0) || !(c->Pr > 0) ||
         !(c->dt > 0) || c->n_corr < 1 || c->n_corr > 4 || !(c->jac_rtol > 0) || c->jac_maxit < 1 ||
-        !(c->cg_rtol > 0) || c->cg_maxit < 1 || c->mg_min_cells < 0 || c->flags != 0 || c->mp_rtol != 0.0 ||
+        !(c->cg_rtol > 0) || c->cg_maxit < 1 || c->mg_min_cells < 0 || (c->flags & ~GEA_FLAG_MIXED) != 0 ||
+        (!(c->flags & GEA_FLAG_MIXED) && c->mp_rtol != 0.0) ||
+        ((c->flags & GEA_FLAG_MIXED) && c->mp_rtol != 0.0 && !(c->mp_rtol >= 1e-7 && c->mp_rtol < 1.0)) ||
         !(c->cs >= 0.0) || (c->cs > 0.0 && c->Pr != 1.0))
         return GEA_ERR_INVAL;
     gea3d_ctx *ctx = new gea3d_ctx();
@@ -1347,6 +1787,17 @@ int gea3d_create(const gea3d_grid *grid, const gea_constants *c, gea3d_ctx **out
     ctx->dtr1 = take(E);
     ctx->kin = take(E);
     if (c->cs > 0.0) ctx->mueff = take(E);
+    ctx->mixed = (c->flags & GEA_FLAG_MIXED) != 0;
+    if (ctx->mixed) {
+        Mx &m = ctx->mx;
+        auto tf = [&]() { return reinterpret_cast<float *>(take((E + 1) / 2)); };
+        for (int s = 0; s < NCF; ++s) m.c[s] = tf();
+        m.dinvu = tf(); m.dinvh = tf(); m.r0u = tf(); m.r0v = tf(); m.r0w = tf(); m.r0h = tf();
+        for (int b = 0; b < 2; ++b) { m.du[b] = tf(); m.dv[b] = tf(); m.dw[b] = tf(); m.dh[b] = tf(); }
+        m.x = tf(); m.p0 = tf(); m.p1 = tf(); m.q = tf(); m.r = tf(); m.z = tf();
+        const double rt = c->mp_rtol != 0.0 ? c->mp_rtol : 1e-5;
+        m.tol2 = rt * rt;
+    }
     ctx->stage = take(5 * (size_t)grid->nx * grid->ny * grid->nz);
     {
         Lev l;
@@ -1497,7 +1948,7 @@ int gea3d_get_stats(gea3d_ctx *ctx, gea_stats *s)
     s->status = h.last_status;
     s->mg_levels = (int)ctx->M.size();
     s->launches = h.launches;
-    s->driver = 0;
+    s->driver = ctx->mixed ? 2 : 0;
     return GEA_OK;
 }
 

@@ -452,13 +452,16 @@ class Solver3D:
     """One context of the three-dimensional step (include/gea3d.h): cell
     fields are (nz, ny, nx) float64 arrays, x fastest."""
 
-    def __init__(self, grid, const, mg_min_cells: int = 0, stream=None):
+    def __init__(self, grid, const, mg_min_cells: int = 0, stream=None, mixed: bool = False,
+                 mp_rtol: float = 0.0):
+        """mixed=True selects the mixed-precision step (GEA_FLAG_MIXED) with
+        inner tolerance mp_rtol (0: the library default)."""
         self.lib = library()
         self.grid, self.const = grid, const
         g = _Grid3(grid.nx, grid.ny, grid.nz, grid.lx, grid.ly, grid.lz)
         c = _Const(const.R, const.cp, const.g, const.p0, const.mu, const.Pr, const.dt,
                    const.n_corr, const.jac_rtol, const.jac_maxit, const.cg_rtol, const.cg_maxit,
-                   mg_min_cells, 0, 0.0, getattr(const, "cs", 0.0))
+                   mg_min_cells, FLAG_MIXED if mixed else 0, mp_rtol, getattr(const, "cs", 0.0))
         h = C.c_void_p()
         rc = self.lib.gea3d_create(C.byref(g), C.byref(c), C.byref(h))
         if rc != GEA_OK:
@@ -516,7 +519,8 @@ class Solver3D:
         n = self.const.n_corr
         return {"steps_done": s.steps_done, "jac_u": s.jac_u, "jac_h": s.jac_h,
                 "cg_iters": list(s.cg_iters)[:n], "cg_relres": list(s.cg_relres)[:n],
-                "status": s.status, "mg_levels": s.mg_levels, "launches": s.launches}
+                "status": s.status, "mg_levels": s.mg_levels, "launches": s.launches,
+                "driver": {0: "graph", 2: "mixed"}[s.driver]}
 
     def profile_step(self) -> Dict[str, Dict]:
         """One eagerly launched step with per-kernel CUDA-event totals."""

@@ -109,6 +109,11 @@ def test_create3_rejects_bad_arguments():
         with pytest.raises(gea.GeaError) as ei:
             gea.Solver3D(g, c)
         assert ei.value.code == gea.GEA_ERR_INVAL
+    # only GEA_FLAG_MIXED, with 1e-7 <= mp_rtol < 1 (or 0), and mp_rtol only with it
+    for kw in (dict(mixed=True, mp_rtol=2.0), dict(mixed=True, mp_rtol=1e-9), dict(mp_rtol=1e-4)):
+        with pytest.raises(gea.GeaError) as ei:
+            gea.Solver3D(W.Grid3(8, 8, 8, 1.0, 1.0, 1.0), W.Constants(dt=0.2), **kw)
+        assert ei.value.code == gea.GEA_ERR_INVAL, kw
     # LES needs Pr = 1 (one viscosity field for momentum and enthalpy), and cs >= 0
     for kw in (dict(cs=0.17, Pr=0.7), dict(cs=-0.1)):
         with pytest.raises(gea.GeaError) as ei:
