@@ -145,6 +145,17 @@ __device__ __forceinline__ double at(const Geo &G, const Phy &F, const double *X
     return ld(&X[id3(G, i, j, k)]);
 }
 
+// X at the neighbour (i+di, j+dj, k+dk) of cell q: a fixed offset from q
+// when the whole stencil of the cell lies inside the box (interior), the
+// ghost rule otherwise.
+template <int BC>
+__device__ __forceinline__ double nbr(const Geo &G, const Phy &F, const double *X, long long q, bool interior,
+                                      int i, int j, int k, int di, int dj, int dk)
+{
+    if (interior) return ld(X + q + di + (long long)dj * G.P + (long long)dk * G.P * (G.ny + 1));
+    return at<BC>(G, F, X, i + di, j + dj, k + dk);
+}
+
 __device__ __forceinline__ double i4(double xm, double xa, double xb, double xp)
 {
     return (-xm + 7.0 * xa + 7.0 * xb - xp) * (1.0 / 12.0);
@@ -308,18 +319,22 @@ __global__ void k_les(Args a)
     const Phy &F = a.F;
     const double hx = 0.5 * G.idx, hy = 0.5 * G.idy, hz = 0.5 * G.idz;
     const double *u = a.S.u, *v = a.S.v, *w = a.S.w;
-    const double ux = (at<U3>(G, F, u, i + 1, j, k) - at<U3>(G, F, u, i - 1, j, k)) * hx;
-    const double uy = (at<U3>(G, F, u, i, j + 1, k) - at<U3>(G, F, u, i, j - 1, k)) * hy;
-    const double uz = (at<U3>(G, F, u, i, j, k + 1) - at<U3>(G, F, u, i, j, k - 1)) * hz;
-    const double vx = (at<V3>(G, F, v, i + 1, j, k) - at<V3>(G, F, v, i - 1, j, k)) * hx;
-    const double vy = (at<V3>(G, F, v, i, j + 1, k) - at<V3>(G, F, v, i, j - 1, k)) * hy;
-    const double vz = (at<V3>(G, F, v, i, j, k + 1) - at<V3>(G, F, v, i, j, k - 1)) * hz;
-    const double wx = (at<W3>(G, F, w, i + 1, j, k) - at<W3>(G, F, w, i - 1, j, k)) * hx;
-    const double wy = (at<W3>(G, F, w, i, j + 1, k) - at<W3>(G, F, w, i, j - 1, k)) * hy;
-    const double wz = (at<W3>(G, F, w, i, j, k + 1) - at<W3>(G, F, w, i, j, k - 1)) * hz;
+    const long long q = id3(G, i, j, k);
+    const bool in = i >= 1 && i + 1 < G.nx && j >= 1 && j + 1 < G.ny && k >= 1 && k + 1 < G.nz;
+    auto U = [&](int di, int dj, int dk) { return nbr<U3>(G, F, u, q, in, i, j, k, di, dj, dk); };
+    auto V = [&](int di, int dj, int dk) { return nbr<V3>(G, F, v, q, in, i, j, k, di, dj, dk); };
+    auto Wv = [&](int di, int dj, int dk) { return nbr<W3>(G, F, w, q, in, i, j, k, di, dj, dk); };
+    const double ux = (U(1, 0, 0) - U(-1, 0, 0)) * hx;
+    const double uy = (U(0, 1, 0) - U(0, -1, 0)) * hy;
+    const double uz = (U(0, 0, 1) - U(0, 0, -1)) * hz;
+    const double vx = (V(1, 0, 0) - V(-1, 0, 0)) * hx;
+    const double vy = (V(0, 1, 0) - V(0, -1, 0)) * hy;
+    const double vz = (V(0, 0, 1) - V(0, 0, -1)) * hz;
+    const double wx = (Wv(1, 0, 0) - Wv(-1, 0, 0)) * hx;
+    const double wy = (Wv(0, 1, 0) - Wv(0, -1, 0)) * hy;
+    const double wz = (Wv(0, 0, 1) - Wv(0, 0, -1)) * hz;
     const double sxy = uy + vx, sxz = uz + wx, syz = vz + wy;
     const double S = sqrt(2.0 * (ux * ux + vy * vy + wz * wz) + sxy * sxy + sxz * sxz + syz * syz);
-    const long long q = id3(G, i, j, k);
     a.mueff[q] = F.mu + ld(&a.S.rho[q]) * F.les_d2 * S;
 }
 
@@ -411,6 +426,24 @@ __device__ __forceinline__ double toff(const Args &a, const W13 &c, const double
 {
     const Geo &G = a.G;
     const Phy &F = a.F;
+    if (i >= 2 && i + 2 < G.nx && j >= 2 && j + 2 < G.ny && k >= 2 && k + 2 < G.nz) {
+        // away from the walls: the neighbours at fixed offsets (same order)
+        const long long sy = G.P, sz = (long long)G.P * (G.ny + 1);
+        const double *x = X + id3(G, i, j, k);
+        double t = c.w[1] * ld(x - 2);
+        t = fma(c.w[2], ld(x - 1), t);
+        t = fma(c.w[3], ld(x + 1), t);
+        t = fma(c.w[4], ld(x + 2), t);
+        t = fma(c.w[5], ld(x - 2 * sy), t);
+        t = fma(c.w[6], ld(x - sy), t);
+        t = fma(c.w[7], ld(x + sy), t);
+        t = fma(c.w[8], ld(x + 2 * sy), t);
+        t = fma(c.w[9], ld(x - 2 * sz), t);
+        t = fma(c.w[10], ld(x - sz), t);
+        t = fma(c.w[11], ld(x + sz), t);
+        t = fma(c.w[12], ld(x + 2 * sz), t);
+        return t;
+    }
     double t = c.w[1] * at<BC>(G, F, X, i - 2, j, k);
     t = fma(c.w[2], at<BC>(G, F, X, i - 1, j, k), t);
     t = fma(c.w[3], at<BC>(G, F, X, i + 1, j, k), t);
@@ -504,7 +537,10 @@ __global__ void k_enth_rhs(Args a, const double *w1)
         // C(K1), fourth-order face values of K1 with even ghosts
         double s = 0.0;
         const double Kc = ld(&a.kin[q]);
-        auto K = [&](int ii, int jj, int kk) { return at<E3>(G, F, a.kin, ii, jj, kk); };
+        const bool in = i >= 2 && i + 2 < G.nx && j >= 2 && j + 2 < G.ny && k >= 2 && k + 2 < G.nz;
+        auto K = [&](int ii, int jj, int kk) {
+            return nbr<E3>(G, F, a.kin, q, in, i, j, k, ii - i, jj - j, kk - k);
+        };
         if (i + 1 < G.nx) s += ld(&a.S.phix[id3(G, i + 1, j, k)]) * i4(K(i - 1, j, k), Kc, K(i + 1, j, k), K(i + 2, j, k));
         if (i > 0) s -= ld(&a.S.phix[id3(G, i, j, k)]) * i4(K(i - 2, j, k), K(i - 1, j, k), Kc, K(i + 1, j, k));
         if (j + 1 < G.ny) s += ld(&a.S.phiy[id3(G, i, j + 1, k)]) * i4(K(i, j - 1, k), Kc, K(i, j + 1, k), K(i, j + 2, k));
@@ -1039,6 +1075,23 @@ __device__ __forceinline__ W13f weightsf(const Mx &m, long long q)
 template <int BC>
 __device__ __forceinline__ float tofff(const Geo &G, const W13f &c, const float *X, int i, int j, int k)
 {
+    if (i >= 2 && i + 2 < G.nx && j >= 2 && j + 2 < G.ny && k >= 2 && k + 2 < G.nz) {
+        const long long sy = G.P, sz = (long long)G.P * (G.ny + 1);
+        const float *x = X + id3(G, i, j, k);
+        float t = c.w[1] * ldf(x - 2);
+        t = fmaf(c.w[2], ldf(x - 1), t);
+        t = fmaf(c.w[3], ldf(x + 1), t);
+        t = fmaf(c.w[4], ldf(x + 2), t);
+        t = fmaf(c.w[5], ldf(x - 2 * sy), t);
+        t = fmaf(c.w[6], ldf(x - sy), t);
+        t = fmaf(c.w[7], ldf(x + sy), t);
+        t = fmaf(c.w[8], ldf(x + 2 * sy), t);
+        t = fmaf(c.w[9], ldf(x - 2 * sz), t);
+        t = fmaf(c.w[10], ldf(x - sz), t);
+        t = fmaf(c.w[11], ldf(x + sz), t);
+        t = fmaf(c.w[12], ldf(x + 2 * sz), t);
+        return t;
+    }
     float t = c.w[1] * atf<BC>(G, X, i - 2, j, k);
     t = fmaf(c.w[2], atf<BC>(G, X, i - 1, j, k), t);
     t = fmaf(c.w[3], atf<BC>(G, X, i + 1, j, k), t);
