@@ -890,8 +890,15 @@ __global__ void k_mg_up(Lev32 f, const RT *r, const float *ec, Geo cg, OT *out, 
     if (cell(f.G, i, j, k)) {
         const Geo &G = f.G;
         const long long q = id3(G, i, j, k);
+        // coarse parent of the cell, and of a neighbour one cell away: the
+        // same parent or the adjacent one, by the parity of the cell's index
+        const long long Q = id3(cg, i >> 1, j >> 1, k >> 1), cy = cg.P, cz = (long long)cg.P * (cg.ny + 1);
+        auto step = [](int d, int idx, long long s) -> long long {
+            return d > 0 ? ((idx & 1) ? s : 0) : d < 0 ? ((idx & 1) ? 0 : -s) : 0;
+        };
         auto ef = [&](long long qq, int ii, int jj, int kk) {
-            return ldf(&f.e[qq]) + ldf(&ec[id3(cg, ii >> 1, jj >> 1, kk >> 1)]);
+            const long long Qn = Q + step(ii - i, i, 1) + step(jj - j, j, cy) + step(kk - k, k, cz);
+            return ldf(&f.e[qq]) + ldf(&ec[Qn]);
         };
         const RT rq = __ldg(&r[q]);
         const float z = ef(q, i, j, k) + ldf(&f.w[q]) * (tof(rq) - helm32(f, ef, i, j, k));
