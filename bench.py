@@ -115,6 +115,20 @@ def peaks():
     return p
 
 
+def job_rate(local_seconds, units_per_rank, world, device="cuda"):
+    """Whole-job throughput of `world` independent replicas: every rank
+    processed `units_per_rank` units in its own `local_seconds`; the job took
+    the slowest rank's time (max over ranks with an all-reduce on `device`,
+    "cuda" for NCCL, "cpu" for gloo), so the rate is world x units / max."""
+    t = float(local_seconds)
+    if world > 1:
+        import torch
+        x = torch.tensor([t], device=device, dtype=torch.float64)
+        torch.distributed.all_reduce(x, op=torch.distributed.ReduceOp.MAX)
+        t = float(x.item())
+    return world * units_per_rank / t, t
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -523,6 +537,9 @@ def run_3d(args):
 
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     B.build()
     wl = W.get(args.three_d)
     g = wl.grid
@@ -534,7 +551,7 @@ def run_3d(args):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     ms, launches, clocks = timed_steps(s, stream, flush, args.steps, args.warmup, world, local)
     st = s.stats()
-    value = world * cells * args.steps / (sum(ms) / 1e3)
+    value, _ = job_rate(sum(ms) / 1e3, cells * args.steps, world)
     prof = s.profile_step()
     KERNEL_MODEL.update(KERNEL_MODEL_3D)
     roof = roofline(prof, peaks(), statistics.mean(ms), False, wl.name)
@@ -576,7 +593,7 @@ def run_3d(args):
     sm.set_conservative(dev)
     ms_m, launches_m, clocks_m = timed_steps(sm, stream, flush, args.steps, args.warmup, world, local)
     st_m = sm.stats()
-    value_m = world * cells * args.steps / (sum(ms_m) / 1e3)
+    value_m, _ = job_rate(sum(ms_m) / 1e3, cells * args.steps, world)
     res["mixed_precision"] = {
         "value": value_m, "unit": UNIT, "ms_per_step": statistics.mean(ms_m), "speedup_vs_fp64": value_m / value,
         "cg_iters_last_step": st_m["cg_iters"], "jacobi_sweeps_last_step": [st_m["jac_u"], st_m["jac_h"]],
@@ -586,6 +603,9 @@ def run_3d(args):
     sm.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline3(args.cpu_seconds)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
     if rank == 0:
         print(json.dumps(res), flush=True)
 
@@ -657,12 +677,7 @@ def run_ours(args):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     ms, launches, clocks = timed_steps(s, stream, flush, args.steps, args.warmup, world, local)
     st = s.stats()
-    tot_s = sum(ms) / 1e3
-    if world > 1:
-        t = torch.tensor([tot_s], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_s = float(t.item())
-    value = world * cells * args.steps / tot_s
+    value, _ = job_rate(sum(ms) / 1e3, cells * args.steps, world)
 
     pms = pressure_ms(s)
     prof = s.profile_step()
@@ -714,14 +729,9 @@ def run_ours(args):
         ms_m, launches_m, clocks_m = timed_steps(sm, stream, flush, args.steps, args.warmup, world,
                                                  local)
         st_m = sm.stats()
-        tot_m = sum(ms_m) / 1e3
-        if world > 1:
-            t = torch.tensor([tot_m], device="cuda", dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            tot_m = float(t.item())
+        value_m, _ = job_rate(sum(ms_m) / 1e3, cells * args.steps, world)
         pms_m = pressure_ms(sm)
         sm.close()
-        value_m = world * cells * args.steps / tot_m
         res["mixed_precision"] = {
             "value": value_m, "unit": UNIT, "ms_per_step": statistics.mean(ms_m),
             "pressure_solve_ms_per_step": pms_m, "speedup_vs_fp64": value_m / value,
