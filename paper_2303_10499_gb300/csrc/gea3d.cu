@@ -125,6 +125,20 @@ __device__ __forceinline__ bool cell(const Geo &G, int &i, int &j, int &k)
     return i < G.nx && j < G.ny && k < G.nz;
 }
 
+// The FP64 CG kernels' blocks walk kLayers consecutive cell layers of their
+// column tile (one block reduction per kLayers cells a thread; the
+// memory-bound FP32 kernels keep one cell per thread): (i, j) of the thread
+// and its layer range [k0, k1).
+constexpr int kLayers = 8;
+__device__ __forceinline__ bool column(const Geo &G, int &i, int &j, int &k0, int &k1)
+{
+    i = blockIdx.x * TX + threadIdx.x;
+    j = blockIdx.y * TY + threadIdx.y;
+    k0 = blockIdx.z * kLayers;
+    k1 = min(G.nz, k0 + kLayers);
+    return i < G.nx && j < G.ny;
+}
+
 // X at (i,j,k) with at most one index one layer outside the box: the ghost
 // of wall rule BC.
 template <int BC>
@@ -954,14 +968,15 @@ __global__ void k_spmv(Args a, Lev L)
     __shared__ double red[NT];
     double acc[1] = {0.0}, tot[1];
     const double *p = (sc->cg_it & 1) ? a.p0 : a.p1;
-    int i, j, k;
-    if (cell(L.G, i, j, k)) {
-        const long long q = id3(L.G, i, j, k);
-        const double pq = ld(&p[q]);
-        const double Ap = helm(L, [&](long long qq, int, int, int) { return ld(&p[qq]); }, i, j, k);
-        a.q[q] = Ap;
-        acc[0] = pq * Ap;
-    }
+    int i, j, k0, k1;
+    if (column(L.G, i, j, k0, k1))
+        for (int k = k0; k < k1; ++k) {
+            const long long q = id3(L.G, i, j, k);
+            const double pq = ld(&p[q]);
+            const double Ap = helm(L, [&](long long qq, int, int, int) { return ld(&p[qq]); }, i, j, k);
+            a.q[q] = Ap;
+            acc[0] = fma(pq, Ap, acc[0]);
+        }
     if (gsum<1>(acc, red, a.part, &sc->counters[C_PQ], tot)) {
         sc->pq = tot[0];
         sc->alpha = tot[0] != 0.0 ? sc->rz / tot[0] : 0.0;
@@ -979,14 +994,15 @@ __global__ void k_update(Args a, Lev L, double *x, int maxit)
     const int it = sc->cg_it;
     const double *p = (it & 1) ? a.p0 : a.p1;
     const double alpha = sc->alpha;
-    int i, j, k;
-    if (cell(L.G, i, j, k)) {
-        const long long q = id3(L.G, i, j, k);
-        x[q] = fma(alpha, ld(&p[q]), x[q]);
-        const double rn = fma(-alpha, ld(&a.q[q]), L.r[q]);
-        L.r[q] = rn;
-        acc[0] = rn * rn;
-    }
+    int i, j, k0, k1;
+    if (column(L.G, i, j, k0, k1))
+        for (int k = k0; k < k1; ++k) {
+            const long long q = id3(L.G, i, j, k);
+            x[q] = fma(alpha, ld(&p[q]), x[q]);
+            const double rn = fma(-alpha, ld(&a.q[q]), L.r[q]);
+            L.r[q] = rn;
+            acc[0] = fma(rn, rn, acc[0]);
+        }
     if (gsum<1>(acc, red, a.part, &sc->counters[C_UPD], tot)) {
         const int n = sc->cg_it + 1;
         sc->cg_it = n;
@@ -1665,6 +1681,7 @@ int record3(gea3d_ctx *ctx, int from, cudaStream_t s, bool graph, Trace3 *tr)
     const int nlev = (int)ctx->M.size();
     const Geo &G = ctx->G;
     const dim3 grid = grid_of(G);
+    const dim3 gridc(grid.x, grid.y, (G.nz + kLayers - 1) / kLayers);   // column kernels
     const int jtrips = (ctx->C.jac_maxit + 1) / 2;
     const int gr = graph ? 1 : 0;
     int fixed = 0, rc;
@@ -1742,8 +1759,8 @@ int record3(gea3d_ctx *ctx, int from, cudaStream_t s, bool graph, Trace3 *tr)
                 traced(tr, "g3_mx_update", G, bs, [&] { k_mx_update<<<grid, kBlk, 0, bs>>>(a, m, M[0]); });
             } else {
                 traced(tr, "g3_pupd", G, bs, [&] { k_pupd<<<grid, kBlk, 0, bs>>>(a, L[0]); });
-                traced(tr, "g3_spmv", G, bs, [&] { k_spmv<<<grid, kBlk, 0, bs>>>(a, L[0]); });
-                traced(tr, "g3_update", G, bs, [&] { k_update<<<grid, kBlk, 0, bs>>>(a, L[0], a.N.pp, ctx->C.cg_maxit); });
+                traced(tr, "g3_spmv", G, bs, [&] { k_spmv<<<gridc, kBlk, 0, bs>>>(a, L[0]); });
+                traced(tr, "g3_update", G, bs, [&] { k_update<<<gridc, kBlk, 0, bs>>>(a, L[0], a.N.pp, ctx->C.cg_maxit); });
             }
             vcycle(ctx, a, bs, tr);
             k_ctl<<<1, 1, 0, bs>>>(a.sc, h, gr, L_CG, ctx->C.cg_maxit, body_cg);
