@@ -83,6 +83,11 @@ struct Grp {
     unsigned *gen;
 };
 
+// Block-uniform copy of the context's status, taken by thread 0 at kernel
+// entry and at the end of every grid barrier, so that all threads of a block
+// leave a step at the same phase boundary.
+__shared__ int s_stop;
+
 // Arrive and wait. The last block to arrive runs last() (all its threads)
 // and then releases the others by advancing the generation. Every data read
 // across blocks goes through L2 (ld.global.cg), so the acquire by thread 0
@@ -113,7 +118,10 @@ __device__ __forceinline__ void barrier_with(const Grp &g, Scal *sc, Last last)
             }
         }
     }
-    if (tid == 0) *g.gen += 1u;
+    if (tid == 0) {
+        *g.gen += 1u;
+        s_stop = rdi(&sc->status) != 0;
+    }
     __syncthreads();
 }
 
@@ -159,7 +167,7 @@ __device__ __forceinline__ void for_tiles(const Grp &g, const Geom &G, F f)
     for (int t = g.rank; t < nt; t += g.nb) f(t % tx, t / tx);
 }
 
-__device__ __forceinline__ bool stop(const Scal *sc) { return rdi(&sc->status) != 0; }
+__device__ __forceinline__ bool stop(const Scal *) { return s_stop != 0; }
 
 // One time step reading a.S and writing a.N. Returns false if the step did
 // not complete (a device error is set).
@@ -588,14 +596,17 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_persistent(PersistArgs P)
     double *sm = dsm;
     double *red = dsm + kTileSmem;
     // a failed earlier launch may have left the barrier mid-count; the error
-    // is sticky until the next set_state, which clears it
-    if (rdi(&P.a[0].sc->status)) return;
-    if (blockIdx.x == 0 && tid_of() == 0) P.a[0].sc->launches += 1;
-    // the generation before this launch's first barrier (no block can pass
-    // that barrier before every block has arrived at it)
+    // is sticky until the next set_state, which clears it. The generation is
+    // the one before this launch's first barrier (no block can pass that
+    // barrier before every block has arrived at it).
     __shared__ unsigned gen;
-    if (tid_of() == 0) gen = ld_acquire(&P.a[0].sc->bar_gen);
+    if (tid_of() == 0) {
+        s_stop = rdi(&P.a[0].sc->status) != 0;
+        gen = ld_acquire(&P.a[0].sc->bar_gen);
+    }
     __syncthreads();
+    if (s_stop) return;
+    if (blockIdx.x == 0 && tid_of() == 0) P.a[0].sc->launches += 1;
     const Grp g{(int)blockIdx.x, (int)gridDim.x, &gen};
     for (int s = 0; s < P.nsteps; ++s) {
         const int slot = (P.first_slot + s) & 1;
@@ -613,11 +624,14 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_persistent_mixed(PersistArgs P,
     extern __shared__ double dsm[];
     double *sm = dsm;
     double *red = dsm + kTileSmem;
-    if (rdi(&P.a[0].sc->status)) return;
-    if (blockIdx.x == 0 && tid_of() == 0) P.a[0].sc->launches += 1;
     __shared__ unsigned gen;
-    if (tid_of() == 0) gen = ld_acquire(&P.a[0].sc->bar_gen);
+    if (tid_of() == 0) {
+        s_stop = rdi(&P.a[0].sc->status) != 0;
+        gen = ld_acquire(&P.a[0].sc->bar_gen);
+    }
     __syncthreads();
+    if (s_stop) return;
+    if (blockIdx.x == 0 && tid_of() == 0) P.a[0].sc->launches += 1;
     const Grp g{(int)blockIdx.x, (int)gridDim.x, &gen};
     for (int s = 0; s < P.nsteps; ++s) {
         const int slot = (P.first_slot + s) & 1;
@@ -655,10 +669,13 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_ensemble(const PersistArgs *Pm,
     const PersistArgs &P = *Ps;
     Scal *sc = P.a[0].sc;
     __shared__ unsigned gen;
-    if (tid == 0) gen = ld_acquire(&sc->bar_gen);
+    if (tid == 0) {
+        s_stop = rdi(&sc->status) != 0;
+        gen = ld_acquire(&sc->bar_gen);
+    }
     __syncthreads();
     const Grp g{(int)blockIdx.x - __ldg(&first[m]), __ldg(&first[m + 1]) - __ldg(&first[m]), &gen};
-    if (rdi(&sc->status)) return;
+    if (s_stop) return;
     if (g.rank == 0 && tid == 0) sc->launches += 1;
     for (int s = 0; s < P.nsteps; ++s) {
         const int slot = (P.first_slot + s) & 1;
