@@ -189,18 +189,26 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-# the sources of the FP64 step kernels whose DRAM traffic profiles/traffic.json
-# records (the per-phase kernels and the persistent step kernel)
-STEP_SOURCES = ("gea_internal.cuh", "gea_tiles.cuh", "gea_kernels.cu", "gea_persistent.cu")
+# the CUDA sources each kernel with a recorded DRAM traffic figure is built
+# from (profiles/traffic.json keys every figure by the hash of its kernel's
+# sources; a change to any of them invalidates that figure alone)
+KERNEL_SOURCES = {
+    "k_persistent": ("gea_internal.cuh", "gea_tiles.cuh", "gea_persistent.cu"),
+    "mg_up": ("gea_internal.cuh", "gea_tiles.cuh", "gea_kernels.cu"),
+    "g3_": ("gea_internal.cuh", "gea3d.cu"),
+}
 
 
-# the sources of the three-dimensional step kernels
-STEP_SOURCES_3D = ("gea_internal.cuh", "gea3d.cu")
+def kernel_sources(kernel):
+    for k, v in KERNEL_SOURCES.items():
+        if kernel == k or (k.endswith("_") and kernel.startswith(k)):
+            return v
+    return None
 
 
-def kernels_sha256(sources=STEP_SOURCES):
-    """Hash of the step kernels' CUDA sources (any change invalidates the
-    recorded counters)."""
+def kernels_sha256(sources):
+    """Hash of a kernel's CUDA sources (any change invalidates the recorded
+    counters)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2303_10499_gb300", "csrc")
     for f in sources:
@@ -211,16 +219,15 @@ def kernels_sha256(sources=STEP_SOURCES):
 
 def traffic_for(kernel, workload):
     """DRAM bytes per launch of `kernel` on `workload` from the committed ncu
-    summary (profiles/traffic.json), if it was taken on the current CUDA
-    sources (else None). The 3D kernels (g3_*) have their own hash."""
+    summary (profiles/traffic.json), if it was taken on the kernel's current
+    CUDA sources (else None)."""
     try:
         t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-        if kernel.startswith("g3_"):
-            if t.get("kernels3d_sha256") != kernels_sha256(STEP_SOURCES_3D):
-                return None
-        elif t.get("kernels_sha256") != kernels_sha256():
+        e = t.get("per_launch", {}).get(workload, {}).get(kernel)
+        src = kernel_sources(kernel)
+        if not e or src is None or e.get("sources_sha256") != kernels_sha256(src):
             return None
-        return t.get("per_launch_bytes", {}).get(workload, {}).get(kernel)
+        return e.get("bytes")
     except Exception:
         return None
 
