@@ -517,7 +517,7 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
         for (const Geom &g : lg) total += 8 * arr_bytes_f(g, g.nz) + arr_bytes_f(g, g.nz + 1);
     }
     const size_t nb = (size_t)max_blocks(G);
-    total += round_up(4 * nb * sizeof(double), 256);
+    total += round_up(8 * nb * sizeof(double), 256);      // reduction partials (two buffers)
     total += round_up(sizeof(Scal), 256);
     ctx->mem_bytes = total;
     if (cudaMalloc(&ctx->mem, total) != cudaSuccess) {
@@ -579,7 +579,8 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
             ctx->Lf.push_back(l);
         }
     }
-    ctx->partials = take(round_up(4 * nb * sizeof(double), 256));
+    // two buffers of 4 x (blocks <= tiles) partials for the persistent kernels
+    ctx->partials = take(round_up(8 * nb * sizeof(double), 256));
     ctx->sc = (Scal *)take(round_up(sizeof(Scal), 256));
     if ((size_t)(ptr - ctx->mem) > total) {
         gea_destroy(ctx);

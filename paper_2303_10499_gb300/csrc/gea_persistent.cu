@@ -7,11 +7,11 @@
 // on launch latency. Here the blocks stay resident for the whole step: each
 // phase is a block-stride loop over tiles running the tile functions of
 // gea_tiles.cuh, phases are separated by a grid barrier, and every residual
-// norm or CG dot product is folded into the barrier (the last block to
-// arrive adds the block partials in a fixed order and publishes the result
-// before releasing the others). The Jacobi and CG loops run inside the
-// kernel; every block takes the same decisions because it reads the same
-// published scalars.
+// norm or CG dot product rides on the barrier: each block writes its
+// partial before arriving and, once released, adds all the partials itself
+// in a fixed order. The Jacobi and CG loops run inside the kernel; every
+// block takes the same decisions because it computes the same totals, bit
+// for bit, and updates its own copy of the loop scalars with them.
 //
 // The barrier waits spin on an acquire load with an iteration cap; a block
 // that gives up sets GEA_ERR_TIMEOUT in the context status, and every block
@@ -62,7 +62,6 @@ __device__ __forceinline__ void red_add_release(unsigned *p, unsigned v)
 }
 
 __device__ __forceinline__ int rdi(const int *p) { return __ldcg(p); }
-__device__ __forceinline__ double rdd(const double *p) { return __ldcg(p); }
 
 __device__ __forceinline__ unsigned long long globaltimer()
 {
@@ -81,82 +80,99 @@ __device__ __forceinline__ int tid_of() { return threadIdx.x + threadIdx.y * BX;
 struct Grp {
     int rank, nb;
     unsigned *gen;
+    Scal *gs;        // the context's scalars in global memory (barrier words, status, results)
 };
 
-// Block-uniform copy of the context's status, taken by thread 0 at kernel
-// entry and at the end of every grid barrier, so that all threads of a block
-// leave a step at the same phase boundary.
+// The block's own copy of the context's scalars. Every block finishes every
+// grid reduction itself (the same partials added in the same order give
+// every block the same totals, bit for bit) and applies the same update to
+// its copy, so the loop decisions (convergence flags, iteration counts, CG
+// step lengths) are taken from shared memory, identically in every block.
+// Block rank 0 publishes what the host reads.
+__shared__ Scal s_ctl;
+
+// Block-uniform stop flag, set by thread 0 at kernel entry and at the end of
+// every grid barrier (the context's status, or an error of the block's own
+// reductions), so that all threads of a block leave a step at the same
+// phase boundary.
 __shared__ int s_stop;
 
-// Arrive and wait. The last block to arrive runs last() (all its threads)
-// and then releases the others by advancing the generation. Every data read
-// across blocks goes through L2 (ld.global.cg), so the acquire by thread 0
-// and the block barrier order them after the release.
-template <class Last>
-__device__ __forceinline__ void barrier_with(const Grp &g, Scal *sc, Last last)
+// Copy the context's scalars into the block's copy (all threads; kernel entry).
+__device__ __forceinline__ void load_ctl(const Scal *gs)
 {
-    __shared__ int am_last;
-    const int tid = tid_of();
-    // every thread of the block has finished its writes of this phase before
-    // thread 0 arrives (its release then publishes them, cumulatively)
+    static_assert(sizeof(Scal) % 4 == 0, "Scal is copied as 32-bit words");
+    const int *src = reinterpret_cast<const int *>(gs);
+    int *dst = reinterpret_cast<int *>(&s_ctl);
+    for (int w = tid_of(); w < (int)(sizeof(Scal) / 4); w += NTHREADS) dst[w] = __ldcg(&src[w]);
+}
+
+// Grid barrier. A block arrives with one acquire-release atomic (thread 0,
+// after the block barrier: it publishes the block's writes of the phase);
+// the last to arrive resets the counter and releases the others by a
+// release add on the generation, which they poll with acquire loads. Every
+// data read across blocks goes through L2 (ld.global.cg), so the acquire by
+// thread 0 and the block barrier order them after the release.
+__device__ __forceinline__ void gbar(const Grp &g)
+{
+    Scal *gs = g.gs;
     __syncthreads();
-    if (tid == 0) am_last = atom_add_acq_rel(&sc->bar_count, 1u) == (unsigned)g.nb - 1u;
-    __syncthreads();
-    if (am_last) {
-        last();
-        if (tid == 0) {
-            sc->bar_count = 0u;
-            red_add_release(&sc->bar_gen, 1u);
-        }
-    } else if (tid == 0) {
-        const unsigned gen0 = *g.gen;
-        unsigned long long spins = 0;
-        while (ld_acquire(&sc->bar_gen) == gen0) {
-            if (++spins > kSpinLimit) {
-                atomicCAS(&sc->status, 0, GEA_ERR_TIMEOUT);
-                break;
+    if (tid_of() == 0) {
+        if (atom_add_acq_rel(&gs->bar_count, 1u) == (unsigned)g.nb - 1u) {
+            gs->bar_count = 0u;
+            red_add_release(&gs->bar_gen, 1u);
+        } else {
+            const unsigned gen0 = *g.gen;
+            unsigned long long spins = 0;
+            while (ld_acquire(&gs->bar_gen) == gen0) {
+                if (++spins > kSpinLimit) {
+                    atomicCAS(&gs->status, 0, GEA_ERR_TIMEOUT);
+                    break;
+                }
             }
         }
-    }
-    if (tid == 0) {
         *g.gen += 1u;
-        s_stop = rdi(&sc->status) != 0;
+        s_stop = rdi(&gs->status) != 0 || s_ctl.status != 0;
     }
     __syncthreads();
 }
 
-__device__ __forceinline__ void gbar(const Grp &g, Scal *sc)
-{
-    barrier_with(g, sc, [] {});
-}
-
-// Barrier with a deterministic grid-wide sum of NV per-thread values; fin(tot)
-// runs in one thread of the last block before the release. T is the type of
-// the per-thread values and of the block sums (FP32 for the inner solves of
-// the mixed-precision step); block partials and the total are FP64.
+// Barrier with a deterministic grid-wide sum of NV per-thread values, which
+// every block completes: it adds the block partials in a fixed order and
+// thread 0 runs fin(tot) on the block's copy of the scalars. T is the type
+// of the per-thread values and of the block sums (FP32 for the inner solves
+// of the mixed-precision step); block partials and the total are FP64. The
+// partials alternate between two buffers by barrier generation: a block
+// writes a buffer again only two barriers later, after every block has read
+// it.
 template <int NV, class T, class Fin>
-__device__ __forceinline__ void rbar(const Grp &g, const T (&v)[NV], double *red, Scal *sc,
-                                     double *partials, Fin fin)
+__device__ __forceinline__ void rbar(const Grp &g, const T (&v)[NV], double *red, double *partials, Fin fin)
 {
     static_assert(NV <= kRedVals, "the block-sum scratch holds kRedVals values per thread");
     const int tid = tid_of();
     const int nb = g.nb;
+    double *pb = partials + (size_t)(*g.gen & 1u) * kRedVals * nb;
     T bt[NV];
     block_sum<NV, T>(v, reinterpret_cast<T *>(red), bt);
     if (tid == 0) {
 #pragma unroll
-        for (int j = 0; j < NV; ++j) partials[(size_t)j * nb + g.rank] = (double)bt[j];
+        for (int j = 0; j < NV; ++j) pb[(size_t)j * nb + g.rank] = (double)bt[j];
     }
-    barrier_with(g, sc, [&] {
-        double s[NV], tot[NV];
+    gbar(g);
+    double s[NV], tot[NV];
 #pragma unroll
-        for (int j = 0; j < NV; ++j) {
-            s[j] = 0.0;
-            for (int b = tid; b < nb; b += NTHREADS) s[j] += __ldcg(&partials[(size_t)j * nb + b]);
+    for (int j = 0; j < NV; ++j) {
+        s[j] = 0.0;
+        for (int b = tid; b < nb; b += NTHREADS) s[j] += __ldcg(&pb[(size_t)j * nb + b]);
+    }
+    block_sum<NV>(s, red, tot);
+    if (tid == 0) {
+        fin(tot);
+        if (s_ctl.status) {
+            s_stop = 1;
+            if (g.rank == 0) atomicCAS(&g.gs->status, 0, s_ctl.status);
         }
-        block_sum<NV>(s, red, tot);
-        if (tid == 0) fin(tot);
-    });
+    }
+    __syncthreads();
 }
 
 template <class F>
@@ -169,11 +185,41 @@ __device__ __forceinline__ void for_tiles(const Grp &g, const Geom &G, F f)
 
 __device__ __forceinline__ bool stop(const Scal *) { return s_stop != 0; }
 
+// End of a step: its counters into the block's copy and, from block rank 0,
+// into the context (what the host reads).
+__device__ __forceinline__ void end_step(const Grp &g)
+{
+    gbar(g);
+    if (tid_of() == 0 && !s_stop) {
+        Scal &c = s_ctl;
+        c.steps_done += 1;
+        c.last_sweeps[0] = c.sweeps[0];
+        c.last_sweeps[1] = c.sweeps[1];
+        for (int k = 0; k < 4; ++k) {
+            c.last_cg_iters[k] = c.cg_iters[k];
+            c.last_cg_relres[k] = c.cg_relres[k];
+        }
+        c.last_status = 0;
+        if (g.rank == 0) {
+            Scal *gs = g.gs;
+            gs->steps_done = c.steps_done;
+            gs->last_sweeps[0] = c.last_sweeps[0];
+            gs->last_sweeps[1] = c.last_sweeps[1];
+            for (int k = 0; k < 4; ++k) {
+                gs->last_cg_iters[k] = c.last_cg_iters[k];
+                gs->last_cg_relres[k] = c.last_cg_relres[k];
+            }
+            gs->last_status = 0;
+            gs->press_ns = c.press_ns;
+        }
+    }
+}
+
 // One time step reading a.S and writing a.N. Returns false if the step did
 // not complete (a device error is set).
 __device__ bool run_step(const PersistArgs &P, const StepArgs &a, const Grp &g, double *sm, double *red)
 {
-    Scal *sc = a.sc;
+    Scal *sc = &s_ctl;   // the block's copy (decisions); g.gs holds the published values
     const Geom &G = a.G;
     const Level *L = P.L;
     const int nlev = P.nlev;
@@ -181,7 +227,7 @@ __device__ bool run_step(const PersistArgs &P, const StepArgs &a, const Grp &g, 
     // ---- Smagorinsky eddy viscosity of the step (LES) ----
     if (a.F.les_d2 > 0.0) {
         for_tiles(g, G, [&](int bx, int bz) { ph_les(a, sm, bx, bz); });
-        gbar(g, sc);
+        gbar(g);
         if (stop(sc)) return false;
     }
     // ---- Step 1: continuity predictor, transport operator, momentum RHS,
@@ -190,7 +236,7 @@ __device__ bool run_step(const PersistArgs &P, const StepArgs &a, const Grp &g, 
     {
         double acc[4] = {0.0, 0.0, 0.0, 0.0};
         for_tiles(g, G, [&](int bx, int bz) { ph_pred_sweep(a, sm, bx, bz, acc); });
-        rbar<4>(g, acc, red, sc, a.partials, [&](const double (&t)[4]) {
+        rbar<4>(g, acc, red, a.partials, [&](const double (&t)[4]) {
             const double tb[2] = {t[0], t[1]}, tr[2] = {t[2], t[3]};
             fin_pred(sc, tb);
             for (int c = 0; c < 4; ++c) { sc->cg_iters[c] = 0; sc->cg_relres[c] = 0.0; }
@@ -205,10 +251,10 @@ __device__ bool run_step(const PersistArgs &P, const StepArgs &a, const Grp &g, 
     // the tolerance
     const double *uin = a.ua, *win = a.wa;
     double *uout = a.ub, *wout = a.wb;
-    while (!rdi(&sc->done[LOOP_MOM])) {
+    while (!sc->done[LOOP_MOM]) {
         double acc[2] = {0.0, 0.0};
         for_tiles(g, G, [&](int bx, int bz) { ph_mom(a, uin, win, uout, wout, sm, bx, bz, acc); });
-        rbar<2>(g, acc, red, sc, a.partials, [&](const double (&t)[2]) {
+        rbar<2>(g, acc, red, a.partials, [&](const double (&t)[2]) {
             fin_mom(sc, t, a.jac_rtol2);
             if (!sc->done[LOOP_MOM] && !sc->status && sc->sweeps[0] >= P.jac_maxit) sc->status = GEA_ERR_NOCONV;
         });
@@ -225,7 +271,7 @@ __device__ bool run_step(const PersistArgs &P, const StepArgs &a, const Grp &g, 
     {
         double acc[2] = {0.0, 0.0};
         for_tiles(g, G, [&](int bx, int bz) { ph_enth_rhs_sweep(a, u1, w1, a.ha, sm, bx, bz, acc); });
-        rbar<2>(g, acc, red, sc, a.partials, [&](const double (&t)[2]) {
+        rbar<2>(g, acc, red, a.partials, [&](const double (&t)[2]) {
             const double tb[1] = {t[0]}, tr[1] = {t[1]};
             fin_enth_rhs(sc, tb);
             fin_enth(sc, tr, a.jac_rtol2);
@@ -235,10 +281,10 @@ __device__ bool run_step(const PersistArgs &P, const StepArgs &a, const Grp &g, 
     if (stop(sc)) return false;
     const double *hin = a.ha;
     double *hout = a.hb;
-    while (!rdi(&sc->done[LOOP_ENTH])) {
+    while (!sc->done[LOOP_ENTH]) {
         double acc[1] = {0.0};
         for_tiles(g, G, [&](int bx, int bz) { ph_enth(a, hin, hout, sm, bx, bz, acc); });
-        rbar<1>(g, acc, red, sc, a.partials, [&](const double (&t)[1]) {
+        rbar<1>(g, acc, red, a.partials, [&](const double (&t)[1]) {
             fin_enth(sc, t, a.jac_rtol2);
             if (!sc->done[LOOP_ENTH] && !sc->status && sc->sweeps[1] >= P.jac_maxit) sc->status = GEA_ERR_NOCONV;
         });
@@ -253,22 +299,22 @@ __device__ bool run_step(const PersistArgs &P, const StepArgs &a, const Grp &g, 
     // nothing the EOS phase writes
     for_tiles(g, G, [&](int bx, int bz) { ph_eos(a, L[0], h1, sm, bx, bz); });
     for_tiles(g, G, [&](int bx, int bz) { ph_H(a, u1, w1, sm, bx, bz); });
-    gbar(g, sc);
+    gbar(g);
     for (int l = 0; l + 1 < nlev; ++l) {
         for_tiles(g, L[l + 1].G, [&](int bx, int bz) { ph_coarsen(L[l], L[l + 1], a.F.omega, bx, bz); });
-        gbar(g, sc);
+        gbar(g);
     }
     if (stop(sc)) return false;
     if (g.rank == 0 && tid_of() == 0) {
-        sc->u1_slot = (u1 == a.ub);
-        sc->h1_slot = (h1 == a.hb);
+        g.gs->u1_slot = (u1 == a.ub);
+        g.gs->h1_slot = (h1 == a.hb);
     }
 
     // ---- Step 3: PISO correctors ----
     for (int c = 0; c < P.n_corr; ++c) {
         if (c > 0) {
             for_tiles(g, G, [&](int bx, int bz) { ph_H(a, a.N.u, a.N.w, sm, bx, bz); });
-            gbar(g, sc);
+            gbar(g);
         }
         unsigned long long t0 = 0;
         if (g.rank == 0 && tid_of() == 0) t0 = globaltimer();
@@ -276,54 +322,54 @@ __device__ bool run_step(const PersistArgs &P, const StepArgs &a, const Grp &g, 
             double acc[2] = {0.0, 0.0};
             const double *xin = c == 0 ? a.S.pp : a.N.pp;
             for_tiles(g, G, [&](int bx, int bz) { ph_helm_rhs(a, L[0], xin, a.N.pp, sm, bx, bz, acc); });
-            rbar<2>(g, acc, red, sc, a.partials, [&](const double (&t)[2]) { fin_helm(sc, t, a.cg_rtol2, c); });
+            rbar<2>(g, acc, red, a.partials, [&](const double (&t)[2]) { fin_helm(sc, t, a.cg_rtol2, c); });
         }
         // z = M^-1 r_0 (one V(1,1)-cycle), then the iterations
         auto vcycle_levels = [&](int lfirst) {
             for (int l = lfirst; l + 1 < nlev; ++l) {
                 for_tiles(g, L[l].G, [&](int bx, int bz) { ph_mg_down(L[l], L[l + 1], a.F.omega, sm, bx, bz); });
-                gbar(g, sc);
+                gbar(g);
             }
             const Level &C = L[nlev - 1];
             for (int s = 0; s < P.ncoarse; ++s) {
                 double *out = ((P.ncoarse - 1 - s) % 2 == 0) ? C.e2 : C.e;
                 const double *in = (out == C.e2) ? C.e : C.e2;
                 for_tiles(g, C.G, [&](int bx, int bz) { ph_mg_coarse(C, in, out, s == 0, sm, bx, bz); });
-                gbar(g, sc);
+                gbar(g);
             }
-            const double *res0 = res_of(L[0], rdi(&sc->cg_it));
+            const double *res0 = res_of(L[0], sc->cg_it);
             for (int l = nlev - 2; l >= 0; --l) {
                 double acc[1] = {0.0};
                 const double *res = l == 0 ? res0 : L[l].r;
                 for_tiles(g, L[l].G, [&](int bx, int bz) {
                     ph_mg_up(L[l], res, L[l + 1].e2, L[l + 1].G.P, L[l].e2, sm, bx, bz, acc);
                 });
-                if (l > 0) gbar(g, sc);
-                else rbar<1>(g, acc, red, sc, a.partials, [&](const double (&t)[1]) { fin_rz(sc, t); });
+                if (l > 0) gbar(g);
+                else rbar<1>(g, acc, red, a.partials, [&](const double (&t)[1]) { fin_rz(sc, t); });
             }
         };
-        if (!stop(sc) && !rdi(&sc->done[LOOP_CG])) {
+        if (!stop(sc) && !sc->done[LOOP_CG]) {
             if (nlev == 1) {
                 double acc[1] = {0.0};
                 for_tiles(g, G, [&](int bx, int bz) { ph_mg_single(L[0], L[0].e2, sm, bx, bz, acc); });
-                rbar<1>(g, acc, red, sc, a.partials, [&](const double (&t)[1]) { fin_rz(sc, t); });
+                rbar<1>(g, acc, red, a.partials, [&](const double (&t)[1]) { fin_rz(sc, t); });
             } else {
                 vcycle_levels(0);
             }
         }
-        while (!stop(sc) && !rdi(&sc->done[LOOP_CG])) {
+        while (!stop(sc) && !sc->done[LOOP_CG]) {
             // p = z + beta p, q = A p
-            const int it = rdi(&sc->cg_it);
+            const int it = sc->cg_it;
             const double *pold = (it & 1) ? a.p1 : a.p0;
             double *pnew = (it & 1) ? a.p0 : a.p1;
             {
-                const double beta = rdd(&sc->beta);
+                const double beta = sc->beta;
                 double acc[1] = {0.0};
                 for_tiles(g, G, [&](int bx, int bz) { ph_pspmv<double>(L[0], pold, pnew, a.q, beta, sm, bx, bz, acc); });
-                rbar<1>(g, acc, red, sc, a.partials, [&](const double (&t)[1]) { fin_pq(sc, t); });
+                rbar<1>(g, acc, red, a.partials, [&](const double (&t)[1]) { fin_pq(sc, t); });
             }
             // x += alpha p, r -= alpha q, with the first step of the next V-cycle
-            const double alpha = rdd(&sc->alpha);
+            const double alpha = sc->alpha;
             auto cap = [&] {
                 if (!sc->done[LOOP_CG] && !sc->status && sc->cg_it >= P.cg_maxit) sc->status = GEA_ERR_NOCONV;
             };
@@ -333,7 +379,7 @@ __device__ bool run_step(const PersistArgs &P, const StepArgs &a, const Grp &g, 
                     ph_update_single<double>(L[0], a.q, res_of(L[0], it), res_of(L[0], it + 1), a.N.pp,
                                              pnew, alpha, sm, bx, bz, acc);
                 });
-                rbar<2>(g, acc, red, sc, a.partials, [&](const double (&t)[2]) {
+                rbar<2>(g, acc, red, a.partials, [&](const double (&t)[2]) {
                     const double t0[1] = {t[0]}, t1[1] = {t[1]};
                     fin_update(sc, t0, a.cg_rtol2);
                     fin_rz(sc, t1);
@@ -345,31 +391,19 @@ __device__ bool run_step(const PersistArgs &P, const StepArgs &a, const Grp &g, 
                     ph_update_down<double>(L[0], L[1], a.q, res_of(L[0], it), res_of(L[0], it + 1), a.N.pp,
                                            pnew, alpha, a.F.omega, sm, bx, bz, acc);
                 });
-                rbar<1>(g, acc, red, sc, a.partials, [&](const double (&t)[1]) {
+                rbar<1>(g, acc, red, a.partials, [&](const double (&t)[1]) {
                     fin_update(sc, t, a.cg_rtol2);
                     cap();
                 });
-                if (!stop(sc) && !rdi(&sc->done[LOOP_CG])) vcycle_levels(1);
+                if (!stop(sc) && !sc->done[LOOP_CG]) vcycle_levels(1);
             }
         }
         if (stop(sc)) return false;
         if (g.rank == 0 && tid_of() == 0) sc->press_ns += globaltimer() - t0;
         for_tiles(g, G, [&](int bx, int bz) { ph_correct(a, sm, bx, bz); });
-        if (c + 1 < P.n_corr) gbar(g, sc);
+        if (c + 1 < P.n_corr) gbar(g);
     }
-    // end of step: publish the step's counters
-    barrier_with(g, sc, [&] {
-        if (tid_of() == 0 && !sc->status) {
-            sc->steps_done += 1;
-            sc->last_sweeps[0] = sc->sweeps[0];
-            sc->last_sweeps[1] = sc->sweeps[1];
-            for (int c = 0; c < 4; ++c) {
-                sc->last_cg_iters[c] = sc->cg_iters[c];
-                sc->last_cg_relres[c] = sc->cg_relres[c];
-            }
-            sc->last_status = 0;
-        }
-    });
+    end_step(g);
     return !stop(sc);
 }
 
@@ -388,16 +422,17 @@ struct MixedPersist {
 __device__ bool run_step_mixed(const PersistArgs &P, const MixedPersist &X, const StepArgs &a, const Grp &g,
                                double *sm, double *red)
 {
-    Scal *sc = a.sc;
+    Scal *sc = &s_ctl;   // the block's copy (decisions); g.gs holds the published values
     const Geom &G = a.G;
     const MixedArgs &m = X.m;
     const LevelF *L = X.Lf;
     const int nlev = X.nlev;
     const Level &L0 = P.L[0];
+    if (g.rank == 0 && tid_of() == 0) g.gs->u1_slot = g.gs->h1_slot = 0;
 
     if (a.F.les_d2 > 0.0) {
         for_tiles(g, G, [&](int bx, int bz) { ph_les(a, sm, bx, bz); });
-        gbar(g, sc);
+        gbar(g);
         if (stop(sc)) return false;
     }
     // ---- Step 1: FP64 residuals r0 = b - T(u^n), FP32 operator, first FP32
@@ -405,12 +440,11 @@ __device__ bool run_step_mixed(const PersistArgs &P, const MixedPersist &X, cons
     {
         double acc[2] = {0.0, 0.0};
         for_tiles(g, G, [&](int bx, int bz) { ph_pred_t<true>(a, m, sm, bx, bz, acc); });
-        rbar<2>(g, acc, red, sc, a.partials, [&](const double (&t)[2]) {
+        rbar<2>(g, acc, red, a.partials, [&](const double (&t)[2]) {
             fin_pred(sc, t);
             for (int c = 0; c < 4; ++c) { sc->cg_iters[c] = 0; sc->cg_relres[c] = 0.0; }
             sc->sweeps[1] = 0;
             sc->press_ns = 0ull;
-            sc->u1_slot = sc->h1_slot = 0;
         });
     }
     if (stop(sc)) return false;
@@ -421,14 +455,14 @@ __device__ bool run_step_mixed(const PersistArgs &P, const MixedPersist &X, cons
         for_tiles(g, G, [&](int bx, int bz) {
             ph_sweep2<float, BC_U, BC_W>(G, a.F, m.T, m.dinvu, m.r0u, m.r0w, ui, wi, uo, wo, sm, bx, bz, acc);
         });
-        rbar<2>(g, acc, red, sc, a.partials, [&](const double (&t)[2]) {
+        rbar<2>(g, acc, red, a.partials, [&](const double (&t)[2]) {
             fin_mom(sc, t, m.tol2);
             if (!sc->done[LOOP_MOM] && !sc->status && sc->sweeps[0] >= P.jac_maxit) sc->status = GEA_ERR_NOCONV;
         });
         const float *tu = ui, *tw = wi;
         ui = uo; wi = wo;
         uo = const_cast<float *>(tu); wo = const_cast<float *>(tw);
-        if (stop(sc) || rdi(&sc->done[LOOP_MOM])) break;
+        if (stop(sc) || sc->done[LOOP_MOM]) break;
     }
     if (stop(sc)) return false;
 
@@ -442,7 +476,7 @@ __device__ bool run_step_mixed(const PersistArgs &P, const MixedPersist &X, cons
         for_tiles(g, G, [&](int bx, int bz) {
             ph_enth_rhs_t<true>(a, mm, nullptr, nullptr, nullptr, sm, bx, bz, acc);
         });
-        rbar<1>(g, acc, red, sc, a.partials, [&](const double (&t)[1]) { fin_enth_rhs(sc, t); });
+        rbar<1>(g, acc, red, a.partials, [&](const double (&t)[1]) { fin_enth_rhs(sc, t); });
     }
     if (stop(sc)) return false;
     const float *hi = m.dh[0];
@@ -453,24 +487,24 @@ __device__ bool run_step_mixed(const PersistArgs &P, const MixedPersist &X, cons
         for_tiles(g, G, [&](int bx, int bz) {
             ph_sweep1<float, BC_EVEN>(G, a.F, m.T, m.dinvh, m.r0h, lc, hi, ho, sm, bx, bz, acc);
         });
-        rbar<1>(g, acc, red, sc, a.partials, [&](const double (&t)[1]) {
+        rbar<1>(g, acc, red, a.partials, [&](const double (&t)[1]) {
             fin_enth(sc, t, m.tol2);
             if (!sc->done[LOOP_ENTH] && !sc->status && sc->sweeps[1] >= P.jac_maxit) sc->status = GEA_ERR_NOCONV;
         });
         const float *t = hi;
         hi = ho;
         ho = const_cast<float *>(t);
-        if (stop(sc) || rdi(&sc->done[LOOP_ENTH])) break;
+        if (stop(sc) || sc->done[LOOP_ENTH]) break;
     }
     if (stop(sc)) return false;
     // h^{n+1} = h^n + dh, the EOS update, the FP64 finest Helmholtz level and
     // its FP32 copy; H(u^{n+1/3}) of the first corrector reads nothing of it
     for_tiles(g, G, [&](int bx, int bz) { ph_eos_t<true>(a, L0, L[0], nullptr, hi, sm, bx, bz); });
     for_tiles(g, G, [&](int bx, int bz) { ph_H(a, a.ua, a.wa, sm, bx, bz); });
-    gbar(g, sc);
+    gbar(g);
     for (int l = 0; l + 1 < nlev; ++l) {
         for_tiles(g, L[l + 1].G, [&](int bx, int bz) { ph_coarsen<float>(L[l], L[l + 1], a.F.omega, bx, bz); });
-        gbar(g, sc);
+        gbar(g);
     }
     if (stop(sc)) return false;
 
@@ -478,7 +512,7 @@ __device__ bool run_step_mixed(const PersistArgs &P, const MixedPersist &X, cons
     for (int c = 0; c < P.n_corr; ++c) {
         if (c > 0) {
             for_tiles(g, G, [&](int bx, int bz) { ph_H(a, a.N.u, a.N.w, sm, bx, bz); });
-            gbar(g, sc);
+            gbar(g);
         }
         unsigned long long t0 = 0;
         if (g.rank == 0 && tid_of() == 0) t0 = globaltimer();
@@ -488,7 +522,7 @@ __device__ bool run_step_mixed(const PersistArgs &P, const MixedPersist &X, cons
             for_tiles(g, G, [&](int bx, int bz) {
                 ph_helm_rhs_t<true>(a, L0, L[0], m, xin, a.N.pp, sm, bx, bz, acc);
             });
-            rbar<2>(g, acc, red, sc, a.partials, [&](const double (&t)[2]) {
+            rbar<2>(g, acc, red, a.partials, [&](const double (&t)[2]) {
                 fin_helm_mixed(sc, t, a.cg_rtol2, c);
             });
         }
@@ -497,48 +531,48 @@ __device__ bool run_step_mixed(const PersistArgs &P, const MixedPersist &X, cons
                 for_tiles(g, L[l].G, [&](int bx, int bz) {
                     ph_mg_down<float>(L[l], L[l + 1], a.F.omega, sm, bx, bz);
                 });
-                gbar(g, sc);
+                gbar(g);
             }
             const LevelF &C = L[nlev - 1];
             for (int s = 0; s < P.ncoarse; ++s) {
                 float *out = ((P.ncoarse - 1 - s) % 2 == 0) ? C.e2 : C.e;
                 const float *in = (out == C.e2) ? C.e : C.e2;
                 for_tiles(g, C.G, [&](int bx, int bz) { ph_mg_coarse<float>(C, in, out, s == 0, sm, bx, bz); });
-                gbar(g, sc);
+                gbar(g);
             }
-            const float *res0 = res_of(L[0], rdi(&sc->cg_it));
+            const float *res0 = res_of(L[0], sc->cg_it);
             for (int l = nlev - 2; l >= 0; --l) {
                 float acc[1] = {0.0f};
                 const float *res = l == 0 ? res0 : L[l].r;
                 for_tiles(g, L[l].G, [&](int bx, int bz) {
                     ph_mg_up<float>(L[l], res, L[l + 1].e2, L[l + 1].G.P, L[l].e2, sm, bx, bz, acc);
                 });
-                if (l > 0) gbar(g, sc);
-                else rbar<1>(g, acc, red, sc, a.partials, [&](const double (&t)[1]) { fin_rz(sc, t); });
+                if (l > 0) gbar(g);
+                else rbar<1>(g, acc, red, a.partials, [&](const double (&t)[1]) { fin_rz(sc, t); });
             }
         };
-        if (!stop(sc) && !rdi(&sc->done[LOOP_CG])) {
+        if (!stop(sc) && !sc->done[LOOP_CG]) {
             if (nlev == 1) {
                 float acc[1] = {0.0f};
                 for_tiles(g, G, [&](int bx, int bz) { ph_mg_single<float>(L[0], L[0].e2, sm, bx, bz, acc); });
-                rbar<1>(g, acc, red, sc, a.partials, [&](const double (&t)[1]) { fin_rz(sc, t); });
+                rbar<1>(g, acc, red, a.partials, [&](const double (&t)[1]) { fin_rz(sc, t); });
             } else {
                 vcycle_levels(0);
             }
         }
-        while (!stop(sc) && !rdi(&sc->done[LOOP_CG])) {
-            const int it = rdi(&sc->cg_it);
+        while (!stop(sc) && !sc->done[LOOP_CG]) {
+            const int it = sc->cg_it;
             const float *pold = (it & 1) ? m.p1 : m.p0;
             float *pnew = (it & 1) ? m.p0 : m.p1;
             {
-                const double beta = rdd(&sc->beta);
+                const double beta = sc->beta;
                 float acc[1] = {0.0f};
                 for_tiles(g, G, [&](int bx, int bz) {
                     ph_pspmv<float>(L[0], pold, pnew, m.q, beta, sm, bx, bz, acc);
                 });
-                rbar<1>(g, acc, red, sc, a.partials, [&](const double (&t)[1]) { fin_pq(sc, t); });
+                rbar<1>(g, acc, red, a.partials, [&](const double (&t)[1]) { fin_pq(sc, t); });
             }
-            const double alpha = rdd(&sc->alpha);
+            const double alpha = sc->alpha;
             auto cap = [&] {
                 if (!sc->done[LOOP_CG] && !sc->status && sc->cg_it >= P.cg_maxit) sc->status = GEA_ERR_NOCONV;
             };
@@ -548,7 +582,7 @@ __device__ bool run_step_mixed(const PersistArgs &P, const MixedPersist &X, cons
                     ph_update_single<float>(L[0], m.q, res_of(L[0], it), res_of(L[0], it + 1), m.x, pnew, alpha,
                                             sm, bx, bz, acc);
                 });
-                rbar<2>(g, acc, red, sc, a.partials, [&](const double (&t)[2]) {
+                rbar<2>(g, acc, red, a.partials, [&](const double (&t)[2]) {
                     const double t0[1] = {t[0]}, t1[1] = {t[1]};
                     fin_update(sc, t0, m.tol2);
                     fin_rz(sc, t1);
@@ -560,33 +594,22 @@ __device__ bool run_step_mixed(const PersistArgs &P, const MixedPersist &X, cons
                     ph_update_down<float>(L[0], L[1], m.q, res_of(L[0], it), res_of(L[0], it + 1), m.x, pnew,
                                           alpha, a.F.omega, sm, bx, bz, acc);
                 });
-                rbar<1>(g, acc, red, sc, a.partials, [&](const double (&t)[1]) {
+                rbar<1>(g, acc, red, a.partials, [&](const double (&t)[1]) {
                     fin_update(sc, t, m.tol2);
                     cap();
                 });
-                if (!stop(sc) && !rdi(&sc->done[LOOP_CG])) vcycle_levels(1);
+                if (!stop(sc) && !sc->done[LOOP_CG]) vcycle_levels(1);
             }
         }
         if (stop(sc)) return false;
         // p' += dp, then the FP64 correction
         for_tiles(g, G, [&](int bx, int bz) { ph_p_apply(a, m, bx, bz); });
-        gbar(g, sc);
+        gbar(g);
         if (g.rank == 0 && tid_of() == 0) sc->press_ns += globaltimer() - t0;
         for_tiles(g, G, [&](int bx, int bz) { ph_correct(a, sm, bx, bz); });
-        if (c + 1 < P.n_corr) gbar(g, sc);
+        if (c + 1 < P.n_corr) gbar(g);
     }
-    barrier_with(g, sc, [&] {
-        if (tid_of() == 0 && !sc->status) {
-            sc->steps_done += 1;
-            sc->last_sweeps[0] = sc->sweeps[0];
-            sc->last_sweeps[1] = sc->sweeps[1];
-            for (int c = 0; c < 4; ++c) {
-                sc->last_cg_iters[c] = sc->cg_iters[c];
-                sc->last_cg_relres[c] = sc->cg_relres[c];
-            }
-            sc->last_status = 0;
-        }
-    });
+    end_step(g);
     return !stop(sc);
 }
 
@@ -600,20 +623,22 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_persistent(PersistArgs P)
     // the one before this launch's first barrier (no block can pass that
     // barrier before every block has arrived at it).
     __shared__ unsigned gen;
+    Scal *gs = P.a[0].sc;
     if (tid_of() == 0) {
-        s_stop = rdi(&P.a[0].sc->status) != 0;
-        gen = ld_acquire(&P.a[0].sc->bar_gen);
+        s_stop = rdi(&gs->status) != 0;
+        gen = ld_acquire(&gs->bar_gen);
     }
+    load_ctl(gs);
     __syncthreads();
     if (s_stop) return;
-    if (blockIdx.x == 0 && tid_of() == 0) P.a[0].sc->launches += 1;
-    const Grp g{(int)blockIdx.x, (int)gridDim.x, &gen};
+    if (blockIdx.x == 0 && tid_of() == 0) gs->launches += 1;
+    const Grp g{(int)blockIdx.x, (int)gridDim.x, &gen, gs};
     for (int s = 0; s < P.nsteps; ++s) {
         const int slot = (P.first_slot + s) & 1;
         if (!run_step(P, P.a[slot], g, sm, red)) break;
     }
     Scal *sc = P.a[0].sc;
-    if (blockIdx.x == 0 && tid_of() == 0 && sc->status) sc->last_status = sc->status;
+    if (blockIdx.x == 0 && tid_of() == 0 && rdi(&sc->status)) sc->last_status = rdi(&sc->status);
 }
 
 constexpr size_t kPersistSmem = (size_t)(kTileSmem + kRedVals * NTHREADS) * sizeof(double);
@@ -625,20 +650,22 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_persistent_mixed(PersistArgs P,
     double *sm = dsm;
     double *red = dsm + kTileSmem;
     __shared__ unsigned gen;
+    Scal *gs = P.a[0].sc;
     if (tid_of() == 0) {
-        s_stop = rdi(&P.a[0].sc->status) != 0;
-        gen = ld_acquire(&P.a[0].sc->bar_gen);
+        s_stop = rdi(&gs->status) != 0;
+        gen = ld_acquire(&gs->bar_gen);
     }
+    load_ctl(gs);
     __syncthreads();
     if (s_stop) return;
-    if (blockIdx.x == 0 && tid_of() == 0) P.a[0].sc->launches += 1;
-    const Grp g{(int)blockIdx.x, (int)gridDim.x, &gen};
+    if (blockIdx.x == 0 && tid_of() == 0) gs->launches += 1;
+    const Grp g{(int)blockIdx.x, (int)gridDim.x, &gen, gs};
     for (int s = 0; s < P.nsteps; ++s) {
         const int slot = (P.first_slot + s) & 1;
         if (!run_step_mixed(P, X, P.a[slot], g, sm, red)) break;
     }
     Scal *sc = P.a[0].sc;
-    if (blockIdx.x == 0 && tid_of() == 0 && sc->status) sc->last_status = sc->status;
+    if (blockIdx.x == 0 && tid_of() == 0 && rdi(&sc->status)) sc->last_status = rdi(&sc->status);
 }
 
 // An ensemble of independent contexts in one cooperative launch: member m
@@ -673,15 +700,16 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_ensemble(const PersistArgs *Pm,
         s_stop = rdi(&sc->status) != 0;
         gen = ld_acquire(&sc->bar_gen);
     }
+    load_ctl(sc);
     __syncthreads();
-    const Grp g{(int)blockIdx.x - __ldg(&first[m]), __ldg(&first[m + 1]) - __ldg(&first[m]), &gen};
+    const Grp g{(int)blockIdx.x - __ldg(&first[m]), __ldg(&first[m + 1]) - __ldg(&first[m]), &gen, sc};
     if (s_stop) return;
     if (g.rank == 0 && tid == 0) sc->launches += 1;
     for (int s = 0; s < P.nsteps; ++s) {
         const int slot = (P.first_slot + s) & 1;
         if (!run_step(P, P.a[slot], g, sm, red)) break;
     }
-    if (g.rank == 0 && tid == 0 && sc->status) sc->last_status = sc->status;
+    if (g.rank == 0 && tid == 0 && rdi(&sc->status)) sc->last_status = rdi(&sc->status);
 }
 
 constexpr size_t kEnsembleSmem = kPersistSmem + (sizeof(PersistArgs) + 15) / 16 * 16;
