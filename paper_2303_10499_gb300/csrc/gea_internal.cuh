@@ -120,11 +120,11 @@ struct Scal {
     double mass, energy;        // diagnostics
     long long launches;         // kernel launches of completed and running steps
     unsigned counters[32];      // reduction arrival counters, one per kernel kind
-    // persistent step kernel: grid barrier (arrival counter and generation on
-    // cache lines of their own: the waiting blocks poll the generation while
-    // the others arrive) and per-step results
+    // persistent step kernels: grid barrier (a monotone arrival counter,
+    // zero at the start of every launch, and the count of blocks that left
+    // the launch, each on a cache line of its own) and per-step results
     alignas(128) unsigned bar_count;
-    alignas(128) unsigned bar_gen;
+    alignas(128) unsigned bar_exit;
     alignas(128) int u1_slot;   // 1 if u^{n+1/3} / h^{n+1} ended in the b buffers
     int h1_slot;
     unsigned long long press_ns; // globaltimer nanoseconds of the pressure solves, last step

@@ -56,10 +56,6 @@ __device__ __forceinline__ unsigned atom_add_acq_rel(unsigned *p, unsigned v)
     return old;
 }
 
-__device__ __forceinline__ void red_add_release(unsigned *p, unsigned v)
-{
-    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
 
 __device__ __forceinline__ int rdi(const int *p) { return __ldcg(p); }
 
@@ -79,7 +75,7 @@ __device__ __forceinline__ int tid_of() { return threadIdx.x + threadIdx.y * BX;
 // same barriers, so it need not be re-read before each wait).
 struct Grp {
     int rank, nb;
-    unsigned *gen;
+    unsigned *gen;   // barriers this block has passed in this launch
     Scal *gs;        // the context's scalars in global memory (barrier words, status, results)
 };
 
@@ -106,34 +102,47 @@ __device__ __forceinline__ void load_ctl(const Scal *gs)
     for (int w = tid_of(); w < (int)(sizeof(Scal) / 4); w += NTHREADS) dst[w] = __ldcg(&src[w]);
 }
 
-// Grid barrier. A block arrives with one acquire-release atomic (thread 0,
-// after the block barrier: it publishes the block's writes of the phase);
-// the last to arrive resets the counter and releases the others by a
-// release add on the generation, which they poll with acquire loads. Every
-// data read across blocks goes through L2 (ld.global.cg), so the acquire by
-// thread 0 and the block barrier order them after the release.
+// Grid barrier on a monotone arrival counter: barrier k of a launch is
+// passed once the counter reaches k x (blocks), so the last block to arrive
+// releases the others by its arrival alone. A block arrives with one
+// acquire-release add (thread 0, after the block barrier: it publishes the
+// block's writes of the phase) and polls the counter with acquire loads
+// (the adds form one release sequence, so reading the final count acquires
+// every block's writes). Every data read across blocks goes through L2
+// (ld.global.cg), ordered after the acquire by the block barrier. The count
+// wraps modulo 2^32; the comparison is of the signed difference.
 __device__ __forceinline__ void gbar(const Grp &g)
 {
     Scal *gs = g.gs;
     __syncthreads();
     if (tid_of() == 0) {
-        if (atom_add_acq_rel(&gs->bar_count, 1u) == (unsigned)g.nb - 1u) {
-            gs->bar_count = 0u;
-            red_add_release(&gs->bar_gen, 1u);
-        } else {
-            const unsigned gen0 = *g.gen;
-            unsigned long long spins = 0;
-            while (ld_acquire(&gs->bar_gen) == gen0) {
-                if (++spins > kSpinLimit) {
-                    atomicCAS(&gs->status, 0, GEA_ERR_TIMEOUT);
-                    break;
-                }
+        const unsigned k = *g.gen + 1u;
+        const unsigned target = k * (unsigned)g.nb;
+        unsigned c = atom_add_acq_rel(&gs->bar_count, 1u) + 1u;
+        unsigned long long spins = 0;
+        while ((int)(c - target) < 0) {
+            if (++spins > kSpinLimit) {
+                atomicCAS(&gs->status, 0, GEA_ERR_TIMEOUT);
+                break;
             }
+            c = ld_acquire(&gs->bar_count);
         }
-        *g.gen += 1u;
+        *g.gen = k;
         s_stop = rdi(&gs->status) != 0 || s_ctl.status != 0;
     }
     __syncthreads();
+}
+
+// Every block leaves through here (all threads): the last of the launch's
+// blocks to leave sets the arrival counter back to zero for the next launch
+// (no block of this launch arrives again).
+__device__ __forceinline__ void leave(const Grp &g)
+{
+    __syncthreads();
+    if (tid_of() == 0 && atom_add_acq_rel(&g.gs->bar_exit, 1u) == (unsigned)g.nb - 1u) {
+        g.gs->bar_count = 0u;
+        g.gs->bar_exit = 0u;
+    }
 }
 
 // Barrier with a deterministic grid-wide sum of NV per-thread values, which
@@ -618,27 +627,25 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_persistent(PersistArgs P)
     extern __shared__ double dsm[];
     double *sm = dsm;
     double *red = dsm + kTileSmem;
-    // a failed earlier launch may have left the barrier mid-count; the error
-    // is sticky until the next set_state, which clears it. The generation is
-    // the one before this launch's first barrier (no block can pass that
-    // barrier before every block has arrived at it).
+    // an error status is sticky until the next set_state, which clears it
     __shared__ unsigned gen;
     Scal *gs = P.a[0].sc;
     if (tid_of() == 0) {
         s_stop = rdi(&gs->status) != 0;
-        gen = ld_acquire(&gs->bar_gen);
+        gen = 0u;
     }
     load_ctl(gs);
     __syncthreads();
-    if (s_stop) return;
-    if (blockIdx.x == 0 && tid_of() == 0) gs->launches += 1;
     const Grp g{(int)blockIdx.x, (int)gridDim.x, &gen, gs};
-    for (int s = 0; s < P.nsteps; ++s) {
-        const int slot = (P.first_slot + s) & 1;
-        if (!run_step(P, P.a[slot], g, sm, red)) break;
+    if (!s_stop) {
+        if (blockIdx.x == 0 && tid_of() == 0) gs->launches += 1;
+        for (int s = 0; s < P.nsteps; ++s) {
+            const int slot = (P.first_slot + s) & 1;
+            if (!run_step(P, P.a[slot], g, sm, red)) break;
+        }
+        if (blockIdx.x == 0 && tid_of() == 0 && rdi(&gs->status)) gs->last_status = rdi(&gs->status);
     }
-    Scal *sc = P.a[0].sc;
-    if (blockIdx.x == 0 && tid_of() == 0 && rdi(&sc->status)) sc->last_status = rdi(&sc->status);
+    leave(g);
 }
 
 constexpr size_t kPersistSmem = (size_t)(kTileSmem + kRedVals * NTHREADS) * sizeof(double);
@@ -653,19 +660,20 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_persistent_mixed(PersistArgs P,
     Scal *gs = P.a[0].sc;
     if (tid_of() == 0) {
         s_stop = rdi(&gs->status) != 0;
-        gen = ld_acquire(&gs->bar_gen);
+        gen = 0u;
     }
     load_ctl(gs);
     __syncthreads();
-    if (s_stop) return;
-    if (blockIdx.x == 0 && tid_of() == 0) gs->launches += 1;
     const Grp g{(int)blockIdx.x, (int)gridDim.x, &gen, gs};
-    for (int s = 0; s < P.nsteps; ++s) {
-        const int slot = (P.first_slot + s) & 1;
-        if (!run_step_mixed(P, X, P.a[slot], g, sm, red)) break;
+    if (!s_stop) {
+        if (blockIdx.x == 0 && tid_of() == 0) gs->launches += 1;
+        for (int s = 0; s < P.nsteps; ++s) {
+            const int slot = (P.first_slot + s) & 1;
+            if (!run_step_mixed(P, X, P.a[slot], g, sm, red)) break;
+        }
+        if (blockIdx.x == 0 && tid_of() == 0 && rdi(&gs->status)) gs->last_status = rdi(&gs->status);
     }
-    Scal *sc = P.a[0].sc;
-    if (blockIdx.x == 0 && tid_of() == 0 && rdi(&sc->status)) sc->last_status = rdi(&sc->status);
+    leave(g);
 }
 
 // An ensemble of independent contexts in one cooperative launch: member m
@@ -698,18 +706,20 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_ensemble(const PersistArgs *Pm,
     __shared__ unsigned gen;
     if (tid == 0) {
         s_stop = rdi(&sc->status) != 0;
-        gen = ld_acquire(&sc->bar_gen);
+        gen = 0u;
     }
     load_ctl(sc);
     __syncthreads();
     const Grp g{(int)blockIdx.x - __ldg(&first[m]), __ldg(&first[m + 1]) - __ldg(&first[m]), &gen, sc};
-    if (s_stop) return;
-    if (g.rank == 0 && tid == 0) sc->launches += 1;
-    for (int s = 0; s < P.nsteps; ++s) {
-        const int slot = (P.first_slot + s) & 1;
-        if (!run_step(P, P.a[slot], g, sm, red)) break;
+    if (!s_stop) {
+        if (g.rank == 0 && tid == 0) sc->launches += 1;
+        for (int s = 0; s < P.nsteps; ++s) {
+            const int slot = (P.first_slot + s) & 1;
+            if (!run_step(P, P.a[slot], g, sm, red)) break;
+        }
+        if (g.rank == 0 && tid == 0 && rdi(&sc->status)) sc->last_status = rdi(&sc->status);
     }
-    if (g.rank == 0 && tid == 0 && rdi(&sc->status)) sc->last_status = rdi(&sc->status);
+    leave(g);
 }
 
 constexpr size_t kEnsembleSmem = kPersistSmem + (sizeof(PersistArgs) + 15) / 16 * 16;
