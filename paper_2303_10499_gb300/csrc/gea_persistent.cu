@@ -71,8 +71,8 @@ __device__ __forceinline__ int tid_of() { return threadIdx.x + threadIdx.y * BX;
 // The blocks that run one context's steps: this block's rank among them and
 // their number (the whole grid for one context; a contiguous share of the
 // grid per member in an ensemble launch), and the block's count of the
-// barrier generations it has passed (shared memory; every block passes the
-// same barriers, so it need not be re-read before each wait).
+// barriers it has passed in this launch (shared memory; every block passes
+// the same barriers).
 struct Grp {
     int rank, nb;
     unsigned *gen;   // barriers this block has passed in this launch
@@ -150,7 +150,7 @@ __device__ __forceinline__ void leave(const Grp &g)
 // thread 0 runs fin(tot) on the block's copy of the scalars. T is the type
 // of the per-thread values and of the block sums (FP32 for the inner solves
 // of the mixed-precision step); block partials and the total are FP64. The
-// partials alternate between two buffers by barrier generation: a block
+// partials alternate between two buffers by barrier parity: a block
 // writes a buffer again only two barriers later, after every block has read
 // it.
 template <int NV, class T, class Fin>
