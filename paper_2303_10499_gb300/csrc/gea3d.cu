@@ -107,6 +107,7 @@ struct Args {
     double *dtr1;   // dt / rho1
     double *kin;    // K1 = |u1|^2 / 2
     double *mueff;  // mu + mu_t (LES only)
+    const double *gzc, *gzf;   // g z of the cell centres (layer k) and of the horizontal faces (k = 0..nz)
     Cf cf;
     Sc *sc;
     double *part;
@@ -298,17 +299,18 @@ __device__ __forceinline__ double fforce(const double *pp, const double *rho, lo
 
 // The face forces of cell (i,j,k): its west, south and bottom faces in fl
 // (zero on walls) and the cell averages of the two faces per direction in g.
-__device__ void cell_forces(const Geo &G, const Phy &F, const double *pp, const double *rho, int i, int j,
-                            int k, double (&fl)[3], double (&g)[3])
+__device__ void cell_forces(const Args &a, const double *pp, const double *rho, int i, int j, int k,
+                            double (&fl)[3], double (&g)[3])
 {
+    const Geo &G = a.G;
     const long long q = id3(G, i, j, k), sx = 1, sy = G.P, sz = (long long)G.P * (G.ny + 1);
-    const double gzc = F.g * ((k + 0.5) * G.dz);
+    const double gzc = ld(&a.gzc[k]);
     fl[0] = i > 0 ? fforce(pp, rho, q, sx, G.idx, gzc) : 0.0;
     const double fe = i + 1 < G.nx ? fforce(pp, rho, q + sx, sx, G.idx, gzc) : 0.0;
     fl[1] = j > 0 ? fforce(pp, rho, q, sy, G.idy, gzc) : 0.0;
     const double fn = j + 1 < G.ny ? fforce(pp, rho, q + sy, sy, G.idy, gzc) : 0.0;
-    fl[2] = k > 0 ? fforce(pp, rho, q, sz, G.idz, F.g * (k * G.dz)) : 0.0;
-    const double ft = k + 1 < G.nz ? fforce(pp, rho, q + sz, sz, G.idz, F.g * ((k + 1) * G.dz)) : 0.0;
+    fl[2] = k > 0 ? fforce(pp, rho, q, sz, G.idz, ld(&a.gzf[k])) : 0.0;
+    const double ft = k + 1 < G.nz ? fforce(pp, rho, q + sz, sz, G.idz, ld(&a.gzf[k + 1])) : 0.0;
     g[0] = 0.5 * (fl[0] + fe);
     g[1] = 0.5 * (fl[1] + fn);
     g[2] = 0.5 * (fl[2] + ft);
@@ -410,7 +412,7 @@ __global__ void k_pred(Args a)
         cf.c[11][q] = (7.0 * pt + pb) * i12 - mt;
         cf.c[12][q] = -pt * i12;
         double fl[3], gc[3];
-        cell_forces(G, F, a.S.pp, a.S.rho, i, j, k, fl, gc);
+        cell_forces(a, a.S.pp, a.S.rho, i, j, k, fl, gc);
         const double gx = gc[0], gy = gc[1], gz = gc[2];
         a.dtr1[q] = F.dt / rho1;
         const double u = ld(&a.S.u[q]), v = ld(&a.S.v[q]), w = ld(&a.S.w[q]);
@@ -759,20 +761,22 @@ __global__ void k_helm_rhs(Args a, Lev L, const double *xin, double *xout, int c
         const Geo &G = a.G;
         const Phy &F = a.F;
         const long long q = id3(G, i, j, k), sx = 1, sy = G.P, sz = (long long)G.P * (G.ny + 1);
-        const double zc = (k + 0.5) * G.dz, r2 = ld(&a.rho2[q]);
-        double fl = 0.0;
-        // idl = 1/Delta of the face direction
-        auto face = [&](const double *D, const double *H, long long fq, long long nq, double sgn, double zf,
+        const double gc = ld(&a.gzc[k]), r2 = ld(&a.rho2[q]);
+        // a face's D_f/Delta (s (H_c + H_N)/2 + g z_f (rho2_N - rho2_c)/Delta):
+        // hs = s/2 with s the sign of the outward normal, gzi = g z_f/Delta
+        auto face = [&](const double *D, const double *H, long long fq, long long nq, double hs, double gzi,
                         double idl) {
-            return ld(&D[fq]) * idl * (sgn * 0.5 * (ld(&H[q]) + ld(&H[nq])) + F.g * zf * (ld(&a.rho2[nq]) - r2) * idl);
+            return ld(&D[fq]) * idl * fma(gzi, ld(&a.rho2[nq]) - r2, hs * (ld(&H[q]) + ld(&H[nq])));
         };
-        if (i + 1 < G.nx) fl += face(a.Dx, a.Hx, q + sx, q + sx, 1.0, zc, G.idx);
-        if (i > 0) fl += face(a.Dx, a.Hx, q, q - sx, -1.0, zc, G.idx);
-        if (j + 1 < G.ny) fl += face(a.Dy, a.Hy, q + sy, q + sy, 1.0, zc, G.idy);
-        if (j > 0) fl += face(a.Dy, a.Hy, q, q - sy, -1.0, zc, G.idy);
-        if (k + 1 < G.nz) fl += face(a.Dz, a.Hz, q + sz, q + sz, 1.0, (k + 1) * G.dz, G.idz);
-        if (k > 0) fl += face(a.Dz, a.Hz, q, q - sz, -1.0, k * G.dz, G.idz);
-        const double b = (ld(&a.S.rho[q]) + ld(&a.psi[q]) * r2 * F.g * zc) * F.idt - fl;
+        const double gx = gc * G.idx, gy = gc * G.idy;
+        double fl = 0.0;
+        if (i + 1 < G.nx) fl += face(a.Dx, a.Hx, q + sx, q + sx, 0.5, gx, G.idx);
+        if (i > 0) fl += face(a.Dx, a.Hx, q, q - sx, -0.5, gx, G.idx);
+        if (j + 1 < G.ny) fl += face(a.Dy, a.Hy, q + sy, q + sy, 0.5, gy, G.idy);
+        if (j > 0) fl += face(a.Dy, a.Hy, q, q - sy, -0.5, gy, G.idy);
+        if (k + 1 < G.nz) fl += face(a.Dz, a.Hz, q + sz, q + sz, 0.5, ld(&a.gzf[k + 1]) * G.idz, G.idz);
+        if (k > 0) fl += face(a.Dz, a.Hz, q, q - sz, -0.5, ld(&a.gzf[k]) * G.idz, G.idz);
+        const double b = fma(ld(&a.psi[q]) * r2, gc, ld(&a.S.rho[q])) * F.idt - fl;
         const double r = b - helm(L, [&](long long qq, int, int, int) { return ld(&xin[qq]); }, i, j, k);
         a.b[q] = b;
         L.r[q] = r;
@@ -1028,16 +1032,15 @@ __global__ void k_correct(Args a)
     int i, j, k;
     if (!cell(a.G, i, j, k)) return;
     const Geo &G = a.G;
-    const Phy &F = a.F;
     const long long q = id3(G, i, j, k), sx = 1, sy = G.P, sz = (long long)G.P * (G.ny + 1);
     double fl[3], gc[3];
-    cell_forces(G, F, a.N.pp, a.rho2, i, j, k, fl, gc);
+    cell_forces(a, a.N.pp, a.rho2, i, j, k, fl, gc);
     const double c1 = ld(&a.dtr1[q]);
     const double hx = ld(&a.Hx[q]), hy = ld(&a.Hy[q]), hz = ld(&a.Hz[q]);
     a.N.u[q] = c1 * (hx - gc[0]);
     a.N.v[q] = c1 * (hy - gc[1]);
     a.N.w[q] = c1 * (hz - gc[2]);
-    const double pn = fma(-ld(&a.rho2[q]), F.g * ((k + 0.5) * G.dz), ld(&a.N.pp[q]));
+    const double pn = fma(-ld(&a.rho2[q]), ld(&a.gzc[k]), ld(&a.N.pp[q]));
     a.N.p[q] = pn;
     a.N.rho[q] = pn * ld(&a.psi[q]);
     a.N.pold[q] = ld(&a.S.p[q]);
@@ -1439,6 +1442,7 @@ struct gea3d_ctx {
     double *dtr1;                         // dt / rho1
     double *kin;                          // K1
     double *mueff = nullptr;              // LES eddy viscosity field
+    double *gz = nullptr;                 // g z: nz cell centres, then nz + 1 horizontal faces
     bool mixed = false;                   // GEA_FLAG_MIXED
     Mx mx{};                              // FP32 data of the mixed step
     Cf cf;                                // transport stencil weights
@@ -1514,6 +1518,8 @@ Args args_of(gea3d_ctx *c, int from)
     a.dtr1 = c->dtr1;
     a.kin = c->kin;
     a.mueff = c->mueff;
+    a.gzc = c->gz;
+    a.gzf = c->gz + c->G.nz;
     a.sc = c->sc; a.part = c->part;
     a.jtol2 = c->C.jac_rtol * c->C.jac_rtol;
     a.ctol2 = c->C.cg_rtol * c->C.cg_rtol;
@@ -1868,6 +1874,17 @@ int gea3d_create(const gea3d_grid *grid, const gea_constants *c, gea3d_ctx **out
     ctx->dtr1 = take(E);
     ctx->kin = take(E);
     if (c->cs > 0.0) ctx->mueff = take(E);
+    {
+        // the heights g z of the cell centres and of the horizontal faces,
+        // rounded as the expressions g ((k + 1/2) dz) and g (k dz)
+        const int nz = ctx->G.nz;
+        std::vector<double> h(2 * (size_t)nz + 1);
+        for (int k = 0; k < nz; ++k) h[k] = c->g * ((k + 0.5) * ctx->G.dz);
+        for (int k = 0; k <= nz; ++k) h[nz + k] = c->g * (k * ctx->G.dz);
+        ctx->gz = take(h.size());
+        if (ctx->gz && cudaMemcpy(ctx->gz, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+            ok = false;
+    }
     ctx->mixed = (c->flags & GEA_FLAG_MIXED) != 0;
     if (ctx->mixed) {
         Mx &m = ctx->mx;
