@@ -53,6 +53,7 @@ __host__ __device__ inline long long id3(const Geo &G, int i, int j, int k)
 
 struct Phy {
     double R, cp, g, mu, nuh, dt, idt, omega;
+    double icp;      // 1/cp
     double les_d2;   // (cs Delta)^2 with Delta = (dx dy dz)^(1/3); 0: constant mu
 };
 
@@ -622,7 +623,7 @@ __global__ void k_eos(Args a, Lev L, Lev32 m, const double *h1)
     const Phy &F = a.F;
     const long long q = id3(a.G, i, j, k);
     const double hq = ld(&h1[q]);
-    const double T1 = ld(&a.S.T[q]) + (hq - ld(&a.S.h[q])) / F.cp;
+    const double T1 = fma(hq - ld(&a.S.h[q]), F.icp, ld(&a.S.T[q]));
     const double psi = 1.0 / (F.R * T1);
     a.N.T[q] = T1;
     a.N.h[q] = hq;
@@ -671,7 +672,7 @@ __global__ void k_diag(Lev L, Lev32 m, Sc *sc)
                      (ld(&L.az[q]) + ld(&L.az[q + sz]));
     L.d[q] = d;
     m.d[q] = (float)d;
-    m.w[q] = (float)(kOmega / d);
+    m.w[q] = (float)kOmega / (float)d;   // FP32 smoother weight: an FP32 division
 }
 
 }  // namespace g3
@@ -896,36 +897,59 @@ __device__ __forceinline__ void fin_rz(Sc *sc, double t)
     sc->rz = t;
 }
 
-// Prolongation e' = e + P e_c and post-smoothing z = e' + (omega/d)(r - A e')
-// into out; on the finest level (FP64 r and z) acc += r.z in FP64.
+// z = e + w (r - A e) at cell (i,j,k) of level f, with e the cell's own
+// smoothed correction plus its coarse parent's (prolongation and one
+// damped-Jacobi post-smoothing sweep); the residual value in rq.
+template <class RT>
+__device__ __forceinline__ float mg_up_cell(const Lev32 &f, const RT *r, const float *ec, const Geo &cg, int i,
+                                            int j, int k, RT &rq)
+{
+    const Geo &G = f.G;
+    const long long q = id3(G, i, j, k);
+    // coarse parent of the cell, and of a neighbour one cell away: the
+    // same parent or the adjacent one, by the parity of the cell's index
+    const long long Q = id3(cg, i >> 1, j >> 1, k >> 1), cy = cg.P, cz = (long long)cg.P * (cg.ny + 1);
+    auto step = [](int d, int idx, long long s) -> long long {
+        return d > 0 ? ((idx & 1) ? s : 0) : d < 0 ? ((idx & 1) ? 0 : -s) : 0;
+    };
+    auto ef = [&](long long qq, int ii, int jj, int kk) {
+        const long long Qn = Q + step(ii - i, i, 1) + step(jj - j, j, cy) + step(kk - k, k, cz);
+        return ldf(&f.e[qq]) + ldf(&ec[Qn]);
+    };
+    rq = __ldg(&r[q]);
+    return ef(q, i, j, k) + ldf(&f.w[q]) * (tof(rq) - helm32(f, ef, i, j, k));
+}
+
+// Intermediate levels: one thread per cell, no reduction.
 template <class RT, class OT>
-__global__ void k_mg_up(Lev32 f, const RT *r, const float *ec, Geo cg, OT *out, int finest, Sc *sc, double *part)
+__global__ void k_mg_up(Lev32 f, const RT *r, const float *ec, Geo cg, OT *out, Sc *sc)
+{
+    if (over(sc, L_CG)) return;
+    int i, j, k;
+    if (!cell(f.G, i, j, k)) return;
+    RT rq;
+    out[id3(f.G, i, j, k)] = (OT)mg_up_cell(f, r, ec, cg, i, j, k, rq);
+}
+
+// Finest level: column tiles of kLayers cells a thread (one block reduction
+// per column), with the r.z reduction of CG in OT (FP64 for the FP64 CG,
+// FP32 for the mixed step's).
+template <class RT, class OT>
+__global__ void k_mg_up_fin(Lev32 f, const RT *r, const float *ec, Geo cg, OT *out, Sc *sc, double *part)
 {
     if (over(sc, L_CG)) return;
     __shared__ double red[NT];
-    OT acc[1] = {(OT)0}, dtot[1];
+    OT acc[1] = {(OT)0};
     double tot[1];
-    (void)dtot;
-    int i, j, k;
-    if (cell(f.G, i, j, k)) {
-        const Geo &G = f.G;
-        const long long q = id3(G, i, j, k);
-        // coarse parent of the cell, and of a neighbour one cell away: the
-        // same parent or the adjacent one, by the parity of the cell's index
-        const long long Q = id3(cg, i >> 1, j >> 1, k >> 1), cy = cg.P, cz = (long long)cg.P * (cg.ny + 1);
-        auto step = [](int d, int idx, long long s) -> long long {
-            return d > 0 ? ((idx & 1) ? s : 0) : d < 0 ? ((idx & 1) ? 0 : -s) : 0;
-        };
-        auto ef = [&](long long qq, int ii, int jj, int kk) {
-            const long long Qn = Q + step(ii - i, i, 1) + step(jj - j, j, cy) + step(kk - k, k, cz);
-            return ldf(&f.e[qq]) + ldf(&ec[Qn]);
-        };
-        const RT rq = __ldg(&r[q]);
-        const float z = ef(q, i, j, k) + ldf(&f.w[q]) * (tof(rq) - helm32(f, ef, i, j, k));
-        out[q] = (OT)z;
-        acc[0] = (OT)rq * (OT)z;   // FP64 for the FP64 CG, FP32 for the mixed step's
-    }
-    if (!finest) return;
+    int i, j, k0, k1;
+    if (column(f.G, i, j, k0, k1))
+#pragma unroll 1
+        for (int k = k0; k < k1; ++k) {
+            RT rq;
+            const float z = mg_up_cell(f, r, ec, cg, i, j, k, rq);
+            out[id3(f.G, i, j, k)] = (OT)z;
+            acc[0] = fma((OT)rq, (OT)z, acc[0]);
+        }
     if (gsum<1, OT>(acc, red, part, &sc->counters[C_RZ], tot)) fin_rz(sc, tot[0]);
 }
 
@@ -1496,6 +1520,8 @@ Geo make_geo(int nx, int ny, int nz, double lx, double ly, double lz)
 size_t elems(const Geo &G) { return (size_t)(G.nz + 1) * (G.ny + 1) * G.P; }
 
 dim3 grid_of(const Geo &G) { return dim3((G.nx + TX - 1) / TX, (G.ny + TY - 1) / TY, G.nz); }
+// the grid of the column kernels (kLayers cell layers per block)
+dim3 gridc_of(const Geo &G) { return dim3((G.nx + TX - 1) / TX, (G.ny + TY - 1) / TY, (G.nz + kLayers - 1) / kLayers); }
 const dim3 kBlk(TX, TY);
 size_t nblocks(const Geo &G)
 {
@@ -1637,10 +1663,11 @@ int vcycle(gea3d_ctx *ctx, const Args &a, cudaStream_t st, Trace3 *tr)
         for (int l = nlev - 2; l >= 1; --l, ++n)
             traced(tr, "g3_mg_up", M[l].G, st, [&] {
                 k_mg_up<float, float><<<grid_of(M[l].G), kBlk, 0, st>>>(M[l], M[l].r, M[l + 1].e2, M[l + 1].G,
-                                                                         M[l].e2, 0, a.sc, a.part);
+                                                                         M[l].e2, a.sc);
             });
         traced(tr, "g3_mg_up", F.G, st, [&] {
-            k_mg_up<float, float><<<grid_of(F.G), kBlk, 0, st>>>(M[0], m.r, M[1].e2, M[1].G, m.z, 1, a.sc, a.part);
+            k_mg_up_fin<float, float><<<gridc_of(F.G), kBlk, 0, st>>>(M[0], m.r, M[1].e2, M[1].G, m.z, a.sc,
+                                                                      a.part);
         });
         return n + 1;
     }
@@ -1670,11 +1697,11 @@ int vcycle(gea3d_ctx *ctx, const Args &a, cudaStream_t st, Trace3 *tr)
     for (int l = nlev - 2; l >= 1; --l, ++n)
         traced(tr, "g3_mg_up", M[l].G, st, [&] {
             k_mg_up<float, float><<<grid_of(M[l].G), kBlk, 0, st>>>(M[l], M[l].r, M[l + 1].e2, M[l + 1].G,
-                                                                     M[l].e2, 0, a.sc, a.part);
+                                                                     M[l].e2, a.sc);
         });
     traced(tr, "g3_mg_up", F.G, st, [&] {
-        k_mg_up<double, double><<<grid_of(F.G), kBlk, 0, st>>>(M[0], F.r, M[1].e2, M[1].G, F.e2, 1, a.sc,
-                                                                a.part);
+        k_mg_up_fin<double, double><<<gridc_of(F.G), kBlk, 0, st>>>(M[0], F.r, M[1].e2, M[1].G, F.e2, a.sc,
+                                                                    a.part);
     });
     return n + 1;
 }
@@ -1826,7 +1853,7 @@ int gea3d_create(const gea3d_grid *grid, const gea_constants *c, gea3d_ctx **out
     ctx->C = *c;
     ctx->G = make_geo(grid->nx, grid->ny, grid->nz, grid->lx, grid->ly, grid->lz);
     ctx->F.R = c->R; ctx->F.cp = c->cp; ctx->F.g = c->g; ctx->F.mu = c->mu; ctx->F.nuh = c->mu / c->Pr;
-    ctx->F.dt = c->dt; ctx->F.idt = 1.0 / c->dt; ctx->F.omega = kOmega;
+    ctx->F.dt = c->dt; ctx->F.idt = 1.0 / c->dt; ctx->F.omega = kOmega; ctx->F.icp = 1.0 / c->cp;
     {
         const double delta = cbrt(ctx->G.dx * ctx->G.dy * ctx->G.dz);
         ctx->F.les_d2 = c->cs * c->cs * delta * delta;
