@@ -69,8 +69,8 @@ struct Lev {
 };
 
 // FP32 level of the multigrid preconditioner (on the finest level the twin
-// of the FP64 operator; r, e2 unused there): w = omega/d, e and e2 the
-// smoothed corrections.
+// of the FP64 operator, r the FP32 copy of the FP64 step's CG residual and
+// e2 unused): w = omega/d, e and e2 the smoothed corrections.
 struct Lev32 {
     Geo G;
     float *c, *d, *ax, *ay, *az, *w, *r, *e, *e2;
@@ -752,7 +752,7 @@ __device__ __forceinline__ void fin_helm_mixed(Sc *sc, const double (&t)[2], dou
 // Mixed step (mr given): r0 rounded to FP32 into mr, and a zero FP32
 // increment mx and first direction mp0.
 __global__ void k_helm_rhs(Args a, Lev L, const double *xin, double *xout, int corr, float *mr = nullptr,
-                           float *mx = nullptr, float *mp0 = nullptr)
+                           float *mx = nullptr, float *mp0 = nullptr, float *rf = nullptr)
 {
     if (a.sc->status) return;
     __shared__ double red[2 * NT];
@@ -788,6 +788,7 @@ __global__ void k_helm_rhs(Args a, Lev L, const double *xin, double *xout, int c
             mx[q] = 0.0f;
             mp0[q] = 0.0f;
         }
+        if (rf) rf[q] = (float)r;
         acc[0] = b * b;
         acc[1] = r * r;
     }
@@ -1015,8 +1016,9 @@ __global__ void k_spmv(Args a, Lev L)
     }
 }
 
-// x += alpha p, r -= alpha q (in place, each cell its own); acc += r^2.
-__global__ void k_update(Args a, Lev L, double *x, int maxit)
+// x += alpha p, r -= alpha q (in place, each cell its own) with an FP32 copy
+// of r for the multigrid restriction; acc += r^2.
+__global__ void k_update(Args a, Lev L, double *x, float *rf, int maxit)
 {
     Sc *sc = a.sc;
     if (over(sc, L_CG)) return;
@@ -1033,6 +1035,7 @@ __global__ void k_update(Args a, Lev L, double *x, int maxit)
             x[q] = fma(alpha, ld(&p[q]), x[q]);
             const double rn = fma(-alpha, ld(&a.q[q]), L.r[q]);
             L.r[q] = rn;
+            rf[q] = (float)rn;
             acc[0] = fma(rn, rn, acc[0]);
         }
     if (gsum<1>(acc, red, a.part, &sc->counters[C_UPD], tot)) {
@@ -1679,7 +1682,7 @@ int vcycle(gea3d_ctx *ctx, const Args &a, cudaStream_t st, Trace3 *tr)
     }
     int n = 0;
     traced(tr, "g3_mg_down", M[1].G, st, [&] {
-        k_mg_down<double><<<grid_of(M[1].G), kBlk, 0, st>>>(M[0], F.r, M[1], a.sc);
+        k_mg_down<float><<<grid_of(M[1].G), kBlk, 0, st>>>(M[0], M[0].r, M[1], a.sc);
     });
     ++n;
     for (int l = 1; l + 1 < nlev; ++l, ++n)
@@ -1785,7 +1788,8 @@ int record3(gea3d_ctx *ctx, int from, cudaStream_t s, bool graph, Trace3 *tr)
             if (ctx->mixed)
                 k_helm_rhs<<<grid, kBlk, 0, s>>>(a, L[0], c == 0 ? a.S.pp : a.N.pp, a.N.pp, c, m.r, m.x, m.p0);
             else
-                k_helm_rhs<<<grid, kBlk, 0, s>>>(a, L[0], c == 0 ? a.S.pp : a.N.pp, a.N.pp, c);
+                k_helm_rhs<<<grid, kBlk, 0, s>>>(a, L[0], c == 0 ? a.S.pp : a.N.pp, a.N.pp, c, nullptr, nullptr,
+                                                 nullptr, ctx->M[0].r);
         });
         ++fixed;
         fixed += vcycle(ctx, a, s, tr);
@@ -1797,7 +1801,7 @@ int record3(gea3d_ctx *ctx, int from, cudaStream_t s, bool graph, Trace3 *tr)
             } else {
                 traced(tr, "g3_pupd", G, bs, [&] { k_pupd<<<grid, kBlk, 0, bs>>>(a, L[0]); });
                 traced(tr, "g3_spmv", G, bs, [&] { k_spmv<<<gridc, kBlk, 0, bs>>>(a, L[0]); });
-                traced(tr, "g3_update", G, bs, [&] { k_update<<<gridc, kBlk, 0, bs>>>(a, L[0], a.N.pp, ctx->C.cg_maxit); });
+                traced(tr, "g3_update", G, bs, [&] { k_update<<<gridc, kBlk, 0, bs>>>(a, L[0], a.N.pp, ctx->M[0].r, ctx->C.cg_maxit); });
             }
             vcycle(ctx, a, bs, tr);
             k_ctl<<<1, 1, 0, bs>>>(a.sc, h, gr, L_CG, ctx->C.cg_maxit, body_cg);
@@ -1941,7 +1945,9 @@ int gea3d_create(const gea3d_grid *grid, const gea_constants *c, gea3d_ctx **out
         const size_t e = elems(lg[lv]);
         m.c = takef(e); m.d = takef(e); m.ax = takef(e); m.ay = takef(e); m.az = takef(e);
         m.w = takef(e); m.e = takef(e);
-        m.r = lv ? takef(e) : nullptr;
+        // the FP64 step keeps an FP32 copy of the CG residual on the finest
+        // level for the restriction (the mixed step's residual is FP32)
+        m.r = (lv || !ctx->mixed) ? takef(e) : nullptr;
         m.e2 = lv ? takef(e) : nullptr;
         ctx->M.push_back(m);
     }
