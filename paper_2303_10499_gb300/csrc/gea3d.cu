@@ -24,6 +24,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <climits>
 #include <vector>
 
 namespace g3 {
@@ -46,9 +47,9 @@ struct Geo {
     double ax, ay, az;                              // face areas dy dz, dx dz, dx dy
 };
 
-__host__ __device__ inline long long id3(const Geo &G, int i, int j, int k)
+__host__ __device__ inline int id3(const Geo &G, int i, int j, int k)
 {
-    return ((long long)k * (G.ny + 1) + j) * G.P + i;
+    return (k * (G.ny + 1) + j) * G.P + i;
 }
 
 struct Phy {
@@ -167,10 +168,10 @@ __device__ __forceinline__ double at(const Geo &G, const Phy &F, const double *X
 // when the whole stencil of the cell lies inside the box (interior), the
 // ghost rule otherwise.
 template <int BC>
-__device__ __forceinline__ double nbr(const Geo &G, const Phy &F, const double *X, long long q, bool interior,
+__device__ __forceinline__ double nbr(const Geo &G, const Phy &F, const double *X, int q, bool interior,
                                       int i, int j, int k, int di, int dj, int dk)
 {
-    if (interior) return ld(X + q + di + (long long)dj * G.P + (long long)dk * G.P * (G.ny + 1));
+    if (interior) return ld(X + q + di + dj * G.P + dk * G.P * (G.ny + 1));
     return at<BC>(G, F, X, i + di, j + dj, k + dk);
 }
 
@@ -273,7 +274,7 @@ __global__ void k_derive(Geo G, Phy F, const double *rho, const double *ru, cons
 {
     int i, j, k;
     if (!cell(G, i, j, k)) return;
-    const long long n = ((long long)k * G.ny + j) * G.nx + i, q = id3(G, i, j, k);
+    const int n = (k * G.ny + j) * G.nx + i, q = id3(G, i, j, k);
     const double z = (k + 0.5) * G.dz, cv = F.cp - F.R;
     const double r = rho[n], u = ru[n] / r, v = rv[n] / r, w = rw[n] / r;
     const double T = (re[n] / r - 0.5 * (u * u + v * v + w * w) - F.g * z) / cv;
@@ -281,7 +282,7 @@ __global__ void k_derive(Geo G, Phy F, const double *rho, const double *ru, cons
     S.rho[q] = r; S.u[q] = u; S.v[q] = v; S.w[q] = w; S.T[q] = T; S.h[q] = F.cp * T;
     const double p = r * F.R * T;
     S.p[q] = p; S.pp[q] = p + r * F.g * z; S.pold[q] = p;
-    const long long sx = 1, sy = G.nx, sz = (long long)G.nx * G.ny;
+    const int sx = 1, sy = G.nx, sz = G.nx * G.ny;
     S.phix[q] = i > 0 ? 0.5 * (ru[n - sx] + ru[n]) * G.dy * G.dz : 0.0;
     S.phiy[q] = j > 0 ? 0.5 * (rv[n - sy] + rv[n]) * G.dx * G.dz : 0.0;
     S.phiz[q] = k > 0 ? 0.5 * (rw[n - sz] + rw[n]) * G.dx * G.dy : 0.0;
@@ -292,7 +293,7 @@ __global__ void k_derive(Geo G, Phy F, const double *rho, const double *ru, cons
 
 // Face force G_f = (p'_b - p'_a)/Delta - g z_f (rho_b - rho_a)/Delta of the
 // face between cell q - s (a) and q (b) in direction d; zero on walls.
-__device__ __forceinline__ double fforce(const double *pp, const double *rho, long long q, long long s,
+__device__ __forceinline__ double fforce(const double *pp, const double *rho, int q, int s,
                                          double inv, double gz)
 {
     return fma(-gz, ld(&rho[q]) - ld(&rho[q - s]), ld(&pp[q]) - ld(&pp[q - s])) * inv;
@@ -304,7 +305,7 @@ __device__ void cell_forces(const Args &a, const double *pp, const double *rho, 
                             double (&fl)[3], double (&g)[3])
 {
     const Geo &G = a.G;
-    const long long q = id3(G, i, j, k), sx = 1, sy = G.P, sz = (long long)G.P * (G.ny + 1);
+    const int q = id3(G, i, j, k), sx = 1, sy = G.P, sz = G.P * (G.ny + 1);
     const double gzc = ld(&a.gzc[k]);
     fl[0] = i > 0 ? fforce(pp, rho, q, sx, G.idx, gzc) : 0.0;
     const double fe = i + 1 < G.nx ? fforce(pp, rho, q + sx, sx, G.idx, gzc) : 0.0;
@@ -338,7 +339,7 @@ __global__ void k_les(Args a)
     const Phy &F = a.F;
     const double hx = 0.5 * G.idx, hy = 0.5 * G.idy, hz = 0.5 * G.idz;
     const double *u = a.S.u, *v = a.S.v, *w = a.S.w;
-    const long long q = id3(G, i, j, k);
+    const int q = id3(G, i, j, k);
     const bool in = i >= 1 && i + 1 < G.nx && j >= 1 && j + 1 < G.ny && k >= 1 && k + 1 < G.nz;
     auto U = [&](int di, int dj, int dk) { return nbr<U3>(G, F, u, q, in, i, j, k, di, dj, dk); };
     auto V = [&](int di, int dj, int dk) { return nbr<V3>(G, F, v, q, in, i, j, k, di, dj, dk); };
@@ -368,7 +369,7 @@ __global__ void k_pred(Args a)
     if (cell(a.G, i, j, k)) {
         const Geo &G = a.G;
         const Phy &F = a.F;
-        const long long q = id3(G, i, j, k), sy = G.P, sz = (long long)G.P * (G.ny + 1);
+        const int q = id3(G, i, j, k), sy = G.P, sz = G.P * (G.ny + 1);
         const double dv = divg(a, i, j, k), r = ld(&a.S.rho[q]);
         const double rho1 = r - F.dt * dv;
         a.rho1[q] = rho1;
@@ -430,7 +431,7 @@ struct W13 {
     double w[NCF];
 };
 
-__device__ __forceinline__ W13 weights(const Args &a, long long q)
+__device__ __forceinline__ W13 weights(const Args &a, int q)
 {
     W13 c;
 #pragma unroll
@@ -447,7 +448,7 @@ __device__ __forceinline__ double toff(const Args &a, const W13 &c, const double
     const Phy &F = a.F;
     if (i >= 2 && i + 2 < G.nx && j >= 2 && j + 2 < G.ny && k >= 2 && k + 2 < G.nz) {
         // away from the walls: the neighbours at fixed offsets (same order)
-        const long long sy = G.P, sz = (long long)G.P * (G.ny + 1);
+        const int sy = G.P, sz = G.P * (G.ny + 1);
         const double *x = X + id3(G, i, j, k);
         double t = c.w[1] * ld(x - 2);
         t = fma(c.w[2], ld(x - 1), t);
@@ -501,7 +502,7 @@ __global__ void k_mom(Args a, const double *ui, const double *vi, const double *
     double acc[3] = {0.0, 0.0, 0.0}, tot[3];
     int i, j, k;
     if (cell(a.G, i, j, k)) {
-        const long long q = id3(a.G, i, j, k);
+        const int q = id3(a.G, i, j, k);
         const double di = ld(&a.dinvu[q]);
         const W13 c = weights(a, q);
         // one component after the other (the empty asm keeps the compiler
@@ -536,7 +537,7 @@ __global__ void k_kin(Args a, const double *u1, const double *v1, const double *
     if (a.sc->status) return;
     int i, j, k;
     if (!cell(a.G, i, j, k)) return;
-    const long long q = id3(a.G, i, j, k);
+    const int q = id3(a.G, i, j, k);
     const double u = ld(&u1[q]), v = ld(&v1[q]), w = ld(&w1[q]);
     a.kin[q] = 0.5 * (u * u + v * v + w * w);
 }
@@ -552,7 +553,7 @@ __global__ void k_enth_rhs(Args a, const double *w1)
     if (cell(a.G, i, j, k)) {
         const Geo &G = a.G;
         const Phy &F = a.F;
-        const long long q = id3(G, i, j, k);
+        const int q = id3(G, i, j, k);
         // C(K1), fourth-order face values of K1 with even ghosts
         double s = 0.0;
         const double Kc = ld(&a.kin[q]);
@@ -596,7 +597,7 @@ __global__ void k_enth(Args a, const double *hi, double *ho, int second)
     double acc[1] = {0.0}, tot[1];
     int i, j, k;
     if (cell(a.G, i, j, k)) {
-        const long long q = id3(a.G, i, j, k);
+        const int q = id3(a.G, i, j, k);
         const W13 c = weights(a, q);
         const double h0 = ld(&hi[q]);
         // T with nu_h = mu/Pr: the mu-stencil plus (mu - nu_h) L(h)
@@ -621,7 +622,7 @@ __global__ void k_eos(Args a, Lev L, Lev32 m, const double *h1)
     int i, j, k;
     if (!cell(a.G, i, j, k)) return;
     const Phy &F = a.F;
-    const long long q = id3(a.G, i, j, k);
+    const int q = id3(a.G, i, j, k);
     const double hq = ld(&h1[q]);
     const double T1 = fma(hq - ld(&a.S.h[q]), F.icp, ld(&a.S.T[q]));
     const double psi = 1.0 / (F.R * T1);
@@ -644,10 +645,10 @@ __global__ void k_faces(Args a, Lev L, Lev32 m)
     int i, j, k;
     if (!cell(a.G, i, j, k)) return;
     const Geo &G = a.G;
-    const long long q = id3(G, i, j, k), sx = 1, sy = G.P, sz = (long long)G.P * (G.ny + 1);
+    const int q = id3(G, i, j, k), sx = 1, sy = G.P, sz = G.P * (G.ny + 1);
     const double r2 = ld(&a.rho2[q]), r1 = ld(&a.rho1[q]), dt = a.F.dt;
     // the halves of the two face means cancel exactly
-    auto D = [&](long long qn) { return dt * (r2 + ld(&a.rho2[qn])) / (r1 + ld(&a.rho1[qn])); };
+    auto D = [&](int qn) { return dt * (r2 + ld(&a.rho2[qn])) / (r1 + ld(&a.rho1[qn])); };
     const double Dw = i > 0 ? D(q - sx) : 0.0;
     const double Ds = j > 0 ? D(q - sy) : 0.0;
     const double Db = k > 0 ? D(q - sz) : 0.0;
@@ -667,7 +668,7 @@ __global__ void k_diag(Lev L, Lev32 m, Sc *sc)
     int i, j, k;
     if (!cell(L.G, i, j, k)) return;
     const Geo &G = L.G;
-    const long long q = id3(G, i, j, k), sy = G.P, sz = (long long)G.P * (G.ny + 1);
+    const int q = id3(G, i, j, k), sy = G.P, sz = G.P * (G.ny + 1);
     const double d = ld(&L.c[q]) + (ld(&L.ax[q]) + ld(&L.ax[q + 1])) + (ld(&L.ay[q]) + ld(&L.ay[q + sy])) +
                      (ld(&L.az[q]) + ld(&L.az[q + sz]));
     L.d[q] = d;
@@ -687,7 +688,7 @@ __global__ void k_H(Args a, const double *U, const double *V, const double *W)
     if (a.sc->status) return;
     int i, j, k;
     if (!cell(a.G, i, j, k)) return;
-    const long long q = id3(a.G, i, j, k);
+    const int q = id3(a.G, i, j, k);
     const double r = ld(&a.S.rho[q]) * a.F.idt;
     // C(X) - mu L(X) = T(X) - (rho1/dt) X
     const W13 c = weights(a, q);
@@ -703,7 +704,7 @@ template <class XF>
 __device__ __forceinline__ double helm(const Lev &L, XF xf, int i, int j, int k)
 {
     const Geo &G = L.G;
-    const long long q = id3(G, i, j, k), sy = G.P, sz = (long long)G.P * (G.ny + 1);
+    const int q = id3(G, i, j, k), sy = G.P, sz = G.P * (G.ny + 1);
     double t = ld(&L.d[q]) * xf(q, i, j, k);
     if (i > 0) t -= ld(&L.ax[q]) * xf(q - 1, i - 1, j, k);
     if (i + 1 < G.nx) t -= ld(&L.ax[q + 1]) * xf(q + 1, i + 1, j, k);
@@ -761,11 +762,11 @@ __global__ void k_helm_rhs(Args a, Lev L, const double *xin, double *xout, int c
     if (cell(a.G, i, j, k)) {
         const Geo &G = a.G;
         const Phy &F = a.F;
-        const long long q = id3(G, i, j, k), sx = 1, sy = G.P, sz = (long long)G.P * (G.ny + 1);
+        const int q = id3(G, i, j, k), sx = 1, sy = G.P, sz = G.P * (G.ny + 1);
         const double gc = ld(&a.gzc[k]), r2 = ld(&a.rho2[q]);
         // a face's D_f/Delta (s (H_c + H_N)/2 + g z_f (rho2_N - rho2_c)/Delta):
         // hs = s/2 with s the sign of the outward normal, gzi = g z_f/Delta
-        auto face = [&](const double *D, const double *H, long long fq, long long nq, double hs, double gzi,
+        auto face = [&](const double *D, const double *H, int fq, int nq, double hs, double gzi,
                         double idl) {
             return ld(&D[fq]) * idl * fma(gzi, ld(&a.rho2[nq]) - r2, hs * (ld(&H[q]) + ld(&H[nq])));
         };
@@ -778,7 +779,7 @@ __global__ void k_helm_rhs(Args a, Lev L, const double *xin, double *xout, int c
         if (k + 1 < G.nz) fl += face(a.Dz, a.Hz, q + sz, q + sz, 0.5, ld(&a.gzf[k + 1]) * G.idz, G.idz);
         if (k > 0) fl += face(a.Dz, a.Hz, q, q - sz, -0.5, ld(&a.gzf[k]) * G.idz, G.idz);
         const double b = fma(ld(&a.psi[q]) * r2, gc, ld(&a.S.rho[q])) * F.idt - fl;
-        const double r = b - helm(L, [&](long long qq, int, int, int) { return ld(&xin[qq]); }, i, j, k);
+        const double r = b - helm(L, [&](int qq, int, int, int) { return ld(&xin[qq]); }, i, j, k);
         a.b[q] = b;
         L.r[q] = r;
         xout[q] = ld(&xin[q]);
@@ -809,7 +810,7 @@ template <class XF>
 __device__ __forceinline__ float helm32(const Lev32 &L, XF xf, int i, int j, int k)
 {
     const Geo &G = L.G;
-    const long long q = id3(G, i, j, k), sy = G.P, sz = (long long)G.P * (G.ny + 1);
+    const int q = id3(G, i, j, k), sy = G.P, sz = G.P * (G.ny + 1);
     float t = ldf(&L.d[q]) * xf(q, i, j, k);
     if (i > 0) t -= ldf(&L.ax[q]) * xf(q - 1, i - 1, j, k);
     if (i + 1 < G.nx) t -= ldf(&L.ax[q + 1]) * xf(q + 1, i + 1, j, k);
@@ -832,24 +833,24 @@ __global__ void k_coarsen(Lev32 f, Lev32 c)
     int I, J, K;
     if (!cell(c.G, I, J, K)) return;
     const Geo &G = f.G, &H = c.G;
-    const long long Q = id3(H, I, J, K);
+    const int Q = id3(H, I, J, K);
     double cs = 0.0, fx0 = 0.0, fx1 = 0.0, fy0 = 0.0, fy1 = 0.0, fz0 = 0.0, fz1 = 0.0;
     for (int dk = 0; dk < 2; ++dk)
         for (int dj = 0; dj < 2; ++dj)
             for (int di = 0; di < 2; ++di) {
                 const int i = 2 * I + di, j = 2 * J + dj, k = 2 * K + dk;
-                const long long q = id3(G, i, j, k);
+                const int q = id3(G, i, j, k);
                 cs += ldf(&f.c[q]);
                 if (di == 0) fx0 += ldf(&f.ax[q]); else fx1 += ldf(&f.ax[q + 1]);
                 if (dj == 0) fy0 += ldf(&f.ay[q]); else fy1 += ldf(&f.ay[q + G.P]);
-                if (dk == 0) fz0 += ldf(&f.az[q]); else fz1 += ldf(&f.az[q + (long long)G.P * (G.ny + 1)]);
+                if (dk == 0) fz0 += ldf(&f.az[q]); else fz1 += ldf(&f.az[q + G.P * (G.ny + 1)]);
             }
     const double cc = 0.125 * cs;
     c.c[Q] = (float)cc;
     c.ax[Q] = (float)(0.125 * fx0); c.ay[Q] = (float)(0.125 * fy0); c.az[Q] = (float)(0.125 * fz0);
     if (I == H.nx - 1) c.ax[Q + 1] = (float)(0.125 * fx1);
     if (J == H.ny - 1) c.ay[Q + H.P] = (float)(0.125 * fy1);
-    if (K == H.nz - 1) c.az[Q + (long long)H.P * (H.ny + 1)] = (float)(0.125 * fz1);
+    if (K == H.nz - 1) c.az[Q + H.P * (H.ny + 1)] = (float)(0.125 * fz1);
     const double d = cc + 0.125 * (fx0 + fx1 + fy0 + fy1 + fz0 + fz1);
     c.d[Q] = (float)d;
     c.w[Q] = (float)(kOmega / d);
@@ -864,13 +865,13 @@ __global__ void k_mg_down(Lev32 f, const RT *r, Lev32 c, Sc *sc)
     int I, J, K;
     if (!cell(c.G, I, J, K)) return;
     const Geo &G = f.G;
-    auto e = [&](long long q, int, int, int) { return ldf(&f.w[q]) * tof(__ldg(&r[q])); };
+    auto e = [&](int q, int, int, int) { return ldf(&f.w[q]) * tof(__ldg(&r[q])); };
     float s = 0.0f;
     for (int dk = 0; dk < 2; ++dk)
         for (int dj = 0; dj < 2; ++dj)
             for (int di = 0; di < 2; ++di) {
                 const int i = 2 * I + di, j = 2 * J + dj, k = 2 * K + dk;
-                const long long q = id3(G, i, j, k);
+                const int q = id3(G, i, j, k);
                 f.e[q] = e(q, i, j, k);
                 s += tof(__ldg(&r[q])) - helm32(f, e, i, j, k);
             }
@@ -883,13 +884,13 @@ __global__ void k_mg_coarse(Lev32 L, const float *ein, float *eout, int first, S
     if (over(sc, L_CG)) return;
     int i, j, k;
     if (!cell(L.G, i, j, k)) return;
-    const long long q = id3(L.G, i, j, k);
+    const int q = id3(L.G, i, j, k);
     const float w = ldf(&L.w[q]);
     if (first) {
         eout[q] = w * ldf(&L.r[q]);
         return;
     }
-    eout[q] = ldf(&ein[q]) + w * (ldf(&L.r[q]) - helm32(L, [&](long long qq, int, int, int) { return ldf(&ein[qq]); }, i, j, k));
+    eout[q] = ldf(&ein[q]) + w * (ldf(&L.r[q]) - helm32(L, [&](int qq, int, int, int) { return ldf(&ein[qq]); }, i, j, k));
 }
 
 __device__ __forceinline__ void fin_rz(Sc *sc, double t)
@@ -906,15 +907,15 @@ __device__ __forceinline__ float mg_up_cell(const Lev32 &f, const RT *r, const f
                                             int j, int k, RT &rq)
 {
     const Geo &G = f.G;
-    const long long q = id3(G, i, j, k);
+    const int q = id3(G, i, j, k);
     // coarse parent of the cell, and of a neighbour one cell away: the
     // same parent or the adjacent one, by the parity of the cell's index
-    const long long Q = id3(cg, i >> 1, j >> 1, k >> 1), cy = cg.P, cz = (long long)cg.P * (cg.ny + 1);
-    auto step = [](int d, int idx, long long s) -> long long {
+    const int Q = id3(cg, i >> 1, j >> 1, k >> 1), cy = cg.P, cz = cg.P * (cg.ny + 1);
+    auto step = [](int d, int idx, int s) -> int {
         return d > 0 ? ((idx & 1) ? s : 0) : d < 0 ? ((idx & 1) ? 0 : -s) : 0;
     };
-    auto ef = [&](long long qq, int ii, int jj, int kk) {
-        const long long Qn = Q + step(ii - i, i, 1) + step(jj - j, j, cy) + step(kk - k, k, cz);
+    auto ef = [&](int qq, int ii, int jj, int kk) {
+        const int Qn = Q + step(ii - i, i, 1) + step(jj - j, j, cy) + step(kk - k, k, cz);
         return ldf(&f.e[qq]) + ldf(&ec[Qn]);
     };
     rq = __ldg(&r[q]);
@@ -965,8 +966,8 @@ __global__ void k_mg_single(Lev32 f, const T *r, T *out, Sc *sc, double *part)
     double tot[1];
     int i, j, k;
     if (cell(f.G, i, j, k)) {
-        const long long q = id3(f.G, i, j, k);
-        auto e = [&](long long qq, int, int, int) { return ldf(&f.w[qq]) * (float)__ldg(&r[qq]); };
+        const int q = id3(f.G, i, j, k);
+        auto e = [&](int qq, int, int, int) { return ldf(&f.w[qq]) * (float)__ldg(&r[qq]); };
         const T rq = __ldg(&r[q]);
         const float z = e(q, i, j, k) + ldf(&f.w[q]) * ((float)rq - helm32(f, e, i, j, k));
         out[q] = (T)z;
@@ -987,7 +988,7 @@ __global__ void k_pupd(Args a, Lev L)
     const int it = sc->cg_it;
     const double *pold = (it & 1) ? a.p1 : a.p0;
     double *pnew = (it & 1) ? a.p0 : a.p1;
-    const long long q = id3(L.G, i, j, k);
+    const int q = id3(L.G, i, j, k);
     pnew[q] = fma(sc->beta, ld(&pold[q]), ld(&L.e2[q]));
 }
 
@@ -1003,9 +1004,9 @@ __global__ void k_spmv(Args a, Lev L)
     if (column(L.G, i, j, k0, k1))
 #pragma unroll 1
         for (int k = k0; k < k1; ++k) {
-            const long long q = id3(L.G, i, j, k);
+            const int q = id3(L.G, i, j, k);
             const double pq = ld(&p[q]);
-            const double Ap = helm(L, [&](long long qq, int, int, int) { return ld(&p[qq]); }, i, j, k);
+            const double Ap = helm(L, [&](int qq, int, int, int) { return ld(&p[qq]); }, i, j, k);
             a.q[q] = Ap;
             acc[0] = fma(pq, Ap, acc[0]);
         }
@@ -1031,7 +1032,7 @@ __global__ void k_update(Args a, Lev L, double *x, float *rf, int maxit)
     if (column(L.G, i, j, k0, k1))
 #pragma unroll 1
         for (int k = k0; k < k1; ++k) {
-            const long long q = id3(L.G, i, j, k);
+            const int q = id3(L.G, i, j, k);
             x[q] = fma(alpha, ld(&p[q]), x[q]);
             const double rn = fma(-alpha, ld(&a.q[q]), L.r[q]);
             L.r[q] = rn;
@@ -1059,7 +1060,7 @@ __global__ void k_correct(Args a)
     int i, j, k;
     if (!cell(a.G, i, j, k)) return;
     const Geo &G = a.G;
-    const long long q = id3(G, i, j, k), sx = 1, sy = G.P, sz = (long long)G.P * (G.ny + 1);
+    const int q = id3(G, i, j, k), sx = 1, sy = G.P, sz = G.P * (G.ny + 1);
     double fl[3], gc[3];
     cell_forces(a, a.N.pp, a.rho2, i, j, k, fl, gc);
     const double c1 = ld(&a.dtr1[q]);
@@ -1120,7 +1121,7 @@ struct W13f {
     float w[NCF];
 };
 
-__device__ __forceinline__ W13f weightsf(const Mx &m, long long q)
+__device__ __forceinline__ W13f weightsf(const Mx &m, int q)
 {
     W13f c;
 #pragma unroll
@@ -1133,7 +1134,7 @@ template <int BC>
 __device__ __forceinline__ float tofff(const Geo &G, const W13f &c, const float *X, int i, int j, int k)
 {
     if (i >= 2 && i + 2 < G.nx && j >= 2 && j + 2 < G.ny && k >= 2 && k + 2 < G.nz) {
-        const long long sy = G.P, sz = (long long)G.P * (G.ny + 1);
+        const int sy = G.P, sz = G.P * (G.ny + 1);
         const float *x = X + id3(G, i, j, k);
         float t = c.w[1] * ldf(x - 2);
         t = fmaf(c.w[2], ldf(x - 1), t);
@@ -1191,7 +1192,7 @@ __global__ void k_mx_r0mom(Args a, Mx m)
     double acc[3] = {0.0, 0.0, 0.0}, tot[3];
     int i, j, k;
     if (cell(a.G, i, j, k)) {
-        const long long q = id3(a.G, i, j, k);
+        const int q = id3(a.G, i, j, k);
         const W13 c = weights(a, q);
         const double u0 = ld(&a.S.u[q]);
         const double ru = ld(&a.bu[q]) - fma(c.w[0], u0, toff<U3>(a, c, a.S.u, i, j, k));
@@ -1239,7 +1240,7 @@ __global__ void k_mx_mom(Args a, Mx m, const float *ui, const float *vi, const f
     int i, j, k;
     if (cell(a.G, i, j, k)) {
         const Geo &G = a.G;
-        const long long q = id3(G, i, j, k);
+        const int q = id3(G, i, j, k);
         const W13f c = weightsf(m, q);
         const float di = ldf(&m.dinvu[q]);
         const float u0 = ldf(&ui[q]), v0 = ldf(&vi[q]), w0 = ldf(&wi[q]);
@@ -1265,7 +1266,7 @@ __global__ void k_mx_u1(Args a, const float *du, const float *dv, const float *d
     if (a.sc->status) return;
     int i, j, k;
     if (!cell(a.G, i, j, k)) return;
-    const long long q = id3(a.G, i, j, k);
+    const int q = id3(a.G, i, j, k);
     a.ua[q] = ld(&a.S.u[q]) + (double)ldf(&du[q]);
     a.va[q] = ld(&a.S.v[q]) + (double)ldf(&dv[q]);
     a.wa[q] = ld(&a.S.w[q]) + (double)ldf(&dw[q]);
@@ -1281,7 +1282,7 @@ __global__ void k_mx_r0h(Args a, Mx m)
     double acc[1] = {0.0}, tot[1];
     int i, j, k;
     if (cell(a.G, i, j, k)) {
-        const long long q = id3(a.G, i, j, k);
+        const int q = id3(a.G, i, j, k);
         const W13 c = weights(a, q);
         const double h0 = ld(&a.S.h[q]);
         double t = fma(c.w[0], h0, toff<H3>(a, c, a.S.h, i, j, k));
@@ -1316,7 +1317,7 @@ __global__ void k_mx_enth(Args a, Mx m, const float *hi, float *ho, int second)
     int i, j, k;
     if (cell(a.G, i, j, k)) {
         const Geo &G = a.G;
-        const long long q = id3(G, i, j, k);
+        const int q = id3(G, i, j, k);
         const W13f c = weightsf(m, q);
         const float h0 = ldf(&hi[q]);
         float t = fmaf(c.w[0], h0, tofff<E3>(G, c, hi, i, j, k));
@@ -1338,7 +1339,7 @@ __global__ void k_mx_h1(Args a, const float *dh)
     if (a.sc->status) return;
     int i, j, k;
     if (!cell(a.G, i, j, k)) return;
-    const long long q = id3(a.G, i, j, k);
+    const int q = id3(a.G, i, j, k);
     a.ha[q] = ld(&a.S.h[q]) + (double)ldf(&dh[q]);
 }
 
@@ -1354,7 +1355,7 @@ __global__ void k_mx_pupd(Args a, Mx m, Lev32 M0)
     const int it = sc->cg_it;
     const float *pold = (it & 1) ? m.p1 : m.p0;
     float *pnew = (it & 1) ? m.p0 : m.p1;
-    const long long q = id3(M0.G, i, j, k);
+    const int q = id3(M0.G, i, j, k);
     pnew[q] = fmaf((float)sc->beta, ldf(&pold[q]), ldf(&m.z[q]));
 }
 
@@ -1369,8 +1370,8 @@ __global__ void k_mx_spmv(Args a, Mx m, Lev32 M0)
     const float *p = (sc->cg_it & 1) ? m.p0 : m.p1;
     int i, j, k;
     if (cell(M0.G, i, j, k)) {
-        const long long q = id3(M0.G, i, j, k);
-        const float Ap = helm32(M0, [&](long long qq, int, int, int) { return ldf(&p[qq]); }, i, j, k);
+        const int q = id3(M0.G, i, j, k);
+        const float Ap = helm32(M0, [&](int qq, int, int, int) { return ldf(&p[qq]); }, i, j, k);
         m.q[q] = Ap;
         acc[0] = ldf(&p[q]) * Ap;
     }
@@ -1393,7 +1394,7 @@ __global__ void k_mx_update(Args a, Mx m, Lev32 M0)
     const float alpha = (float)sc->alpha;
     int i, j, k;
     if (cell(M0.G, i, j, k)) {
-        const long long q = id3(M0.G, i, j, k);
+        const int q = id3(M0.G, i, j, k);
         m.x[q] = fmaf(alpha, ldf(&p[q]), m.x[q]);
         const float rn = fmaf(-alpha, ldf(&m.q[q]), m.r[q]);
         m.r[q] = rn;
@@ -1416,7 +1417,7 @@ __global__ void k_mx_papply(Args a, Mx m)
     if (a.sc->status) return;
     int i, j, k;
     if (!cell(a.G, i, j, k)) return;
-    const long long q = id3(a.G, i, j, k);
+    const int q = id3(a.G, i, j, k);
     a.N.pp[q] = ld(&a.N.pp[q]) + (double)ldf(&m.x[q]);
 }
 
@@ -1846,6 +1847,9 @@ int gea3d_create(const gea3d_grid *grid, const gea_constants *c, gea3d_ctx **out
     if (grid->nx < 4 || grid->ny < 4 || grid->nz < 4 || !(grid->lx > 0) || !(grid->ly > 0) || !(grid->lz > 0))
         return GEA_ERR_INVAL;
     if ((long long)grid->nx * grid->ny * grid->nz > (1LL << 31) / 4) return GEA_ERR_INVAL;
+    // the kernels index a field (ghost layers and row padding included) with
+    // 32-bit integers
+    if ((long long)(grid->nz + 1) * (grid->ny + 1) * ((grid->nx + 1 + 31) / 32 * 32) > INT_MAX) return GEA_ERR_INVAL;
     if (!(c->R > 0) || !(c->cp > c->R) || !(c->g >= 0) || !(c->p0 > 0) || !(c->mu >= 0) || !(c->Pr > 0) ||
         !(c->dt > 0) || c->n_corr < 1 || c->n_corr > 4 || !(c->jac_rtol > 0) || c->jac_maxit < 1 ||
         !(c->cg_rtol > 0) || c->cg_maxit < 1 || c->mg_min_cells < 0 || (c->flags & ~GEA_FLAG_MIXED) != 0 ||
