@@ -347,10 +347,11 @@ def matched_error(gea, wl, steps):
 
 
 def run_learned(args):
-    """Plain MG-CG against the learned initial guess on the 4096 x 2048 bubble
-    with pressure solves to 1e-8 (relative to ||b||): both timed like the main
-    line, after the network is trained on the FP64 solver's own pressure
-    systems of the first 8 steps (training time reported separately)."""
+    """Plain MG-CG against the learned initial guess, and against flexible CG
+    with the network as the preconditioner, on the 4096 x 2048 bubble with
+    pressure solves to 1e-8 (relative to ||b||): all timed like the main line,
+    after the network is trained on the FP64 solver's own pressure systems of
+    the first 8 steps (training time reported separately)."""
     import copy
     import numpy as np
     import torch
@@ -373,11 +374,11 @@ def run_learned(args):
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     arms = {}
-    for use in (False, True):
+    for use in (0, 1, 2):
         s = gea.Solver(wl.grid, const, stream=stream, graph=True)
         s.set_conservative(wl.fields)
         if use:
-            s.attach_net(net)
+            s.attach_net(net, use)
         ms, launches, clocks = timed_steps(s, stream, flush, args.steps, args.warmup, world, local)
         its = []
         for _ in range(5):
@@ -392,22 +393,28 @@ def run_learned(args):
                      "kernel_ms_eager_step": {k: round(v["ms"], 4) for k, v in prof.items()
                                               if k in ("net_forward", "guess_in", "guess_dots",
                                                        "guess_apply", "cg_pspmv", "cg_update_down",
-                                                       "mg_up", "mg_down", "helm_rhs")},
+                                                       "mg_up", "mg_down", "helm_rhs", "fcg_stage_in",
+                                                       "fcg_stage_out", "fcg_pspmv", "fcg_update")},
                      "_theta": th}
         s.close()
-    dth = float(np.abs(arms[True].pop("_theta") - arms[False].pop("_theta")).max())
+    th0 = arms[0].pop("_theta")
+    dth = float(np.abs(arms[1].pop("_theta") - th0).max())
+    dth2 = float(np.abs(arms[2].pop("_theta") - th0).max())
     res = {
-        "metric": METRIC, "value": arms[True]["value"], "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": arms[True]["ms_per_step"],
+        "metric": METRIC, "value": arms[1]["value"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": arms[1]["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+bf16",
         "data": "synthetic",
         "config": {"workload": wl.name + " learned initial guess", "grid": [wl.grid.nx, wl.grid.nz],
                    "cg_rtol": const.cg_rtol, "network": "4-level U-Net, 16 base channels, linear, "
                    f"{gea.net_param_count()} parameters, bfloat16 tensor-core layers",
                    "l2": "flushed between timed steps (256 MB write, untimed)"},
-        "plain_mg_cg": arms[False], "learned_guess": arms[True],
-        "speedup_vs_plain": arms[True]["value"] / arms[False]["value"],
+        "plain_mg_cg": arms[0], "learned_guess": arms[1],
+        "speedup_vs_plain": arms[1]["value"] / arms[0]["value"],
         "max_abs_dtheta_K_learned_vs_plain": dth,
+        "network_preconditioner_fcg": arms[2],
+        "fcg_speedup_vs_plain": arms[2]["value"] / arms[0]["value"],
+        "max_abs_dtheta_K_fcg_vs_plain": dth2,
         "training": {"samples": len(samples), "collect_s": t_collect, "iterations": 400,
                      "batch": "8 x 256 x 256 crops", "seconds": tr["seconds"],
                      "loss_first": tr["losses"][0], "loss_last20": float(np.mean(tr["losses"][-20:]))},

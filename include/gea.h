@@ -223,8 +223,12 @@ enum {
  * correction e for the initial residual r, and the solve starts from
  * x + alpha e, r - alpha A e with alpha = r.e / e.A e, the step that
  * minimises the A-norm error along e (so the start is never worse); the
- * solve then runs to the same tolerance as without the network. mode 0:
- * detach. The context does not own the network; it must outlive the
+ * solve then runs to the same tolerance as without the network. mode 2
+ * (FP64 step only): the network replaces the multigrid V-cycle as the
+ * preconditioner, z = N(r), in a flexible CG truncated to one previous
+ * direction (beta = -z.q_old / p_old.q_old, alpha = r.p / p.A p), which
+ * stays a descent method for a nonlinear preconditioner; the stopping test
+ * is unchanged. mode 3: both. mode 0: detach. The context does not own the network; it must outlive the
  * attachment, and must not be used elsewhere while this context steps.
  * Steps then run through the CUDA-graph driver. nx, nz must be multiples of
  * 8 within the network's size. Errors: GEA_ERR_INVAL, GEA_ERR_CUDA. */

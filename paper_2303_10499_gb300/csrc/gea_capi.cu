@@ -44,7 +44,9 @@ struct gea_ctx {
     std::vector<LevelF> Lf;               // FP32 hierarchy of the mixed-precision step
     double *r0keep = nullptr;             // GEA_FLAG_KEEP_R0: first corrector's initial residual
     double *mueff = nullptr;              // LES: mu + mu_t of the running step
-    gea_net *net = nullptr;               // attached learned initial guess (not owned)
+    gea_net *net = nullptr;               // attached learned network (not owned)
+    int net_mode = 0;                     // 1: initial guess; 2: flexible-CG preconditioner; 3: both
+    double *net_s = nullptr;              // mode 2: the residual the network leaves (V-cycle input)
     float *net_r = nullptr, *net_e = nullptr;   // its dense input and output
     Scal *sc = nullptr;
     double *partials = nullptr;
@@ -135,7 +137,7 @@ constexpr double kMixedRtol = 1e-5;  // default tolerance of the FP32 solves (re
 // Append a WHILE conditional node to the graph being captured on `s`; its
 // body is captured from body(body_stream, handle, true).
 template <class Body>
-int capture_while(gea_ctx *ctx, cudaStream_t s, Body body)
+int capture_while(gea_ctx *ctx, cudaStream_t s, Body body, int gate = -1)
 {
     cudaStreamCaptureStatus cs;
     cudaGraph_t g;
@@ -146,6 +148,13 @@ int capture_while(gea_ctx *ctx, cudaStream_t s, Body body)
     if (cs != cudaStreamCaptureStatusActive) return fail(ctx, GEA_ERR_CUDA, "capture not active");
     cudaGraphConditionalHandle h;
     CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+    if (gate >= 0) {
+        // a gated loop runs no trip when it is already finished: a kernel
+        // ahead of the node sets the condition from the loop's flags
+        launch_loop_gate(ctx->sc, h, gate, s);
+        CK(cudaGetLastError());
+        CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, &edges, &ndeps));
+    }
     cudaGraphNodeParams prm = {cudaGraphNodeTypeConditional};
     prm.conditional.handle = h;
     prm.conditional.type = cudaGraphCondTypeWhile;
@@ -215,8 +224,14 @@ int record_guess(gea_ctx *ctx, const StepArgs &a, const LevelT<R> &L, R *q, R *x
 // Run a loop body eagerly on `s` until its control kernel reports that the
 // loop is finished (converged, failed or at its trip cap).
 template <class Body>
-int eager_while(gea_ctx *ctx, cudaStream_t s, int which, int maxtrips, Body body)
+int eager_while(gea_ctx *ctx, cudaStream_t s, int which, int maxtrips, Body body, bool gated = false)
 {
+    if (gated) {
+        Scal h;
+        CK(cudaMemcpyAsync(&h, ctx->sc, sizeof(Scal), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (h.done[which] || h.status) return GEA_OK;
+    }
     for (int t = 0; t < maxtrips + 1; ++t) {
         body(s, (cudaGraphConditionalHandle)0, false);
         Scal h;
@@ -277,17 +292,36 @@ int record_step(gea_ctx *ctx, int from, cudaStream_t s, bool graph, Tracer *tr)
         launch_helm_rhs(a, L[0], c == 0 ? a.S.pp : a.N.pp, a.N.pp, c, s, tr); ++fixed;
         if (ctx->r0keep && c == 0)
             CK(cudaMemcpyAsync(ctx->r0keep, L[0].r, arr_bytes(ctx->G, ctx->G.nz), cudaMemcpyDeviceToDevice, s));
-        if (ctx->net) {
+        if (ctx->net && (ctx->net_mode & 1)) {
             const int k = record_guess<double>(ctx, a, L[0], a.q, a.N.pp, a.cg_rtol2, s, graph, tr);
             if (k < 0) return fail(ctx, GEA_ERR_CUDA, "learned initial guess failed");
             fixed += k;
         }
-        fixed += launch_vcycle(a, L, nlev, kCoarseSweeps, s, tr);   // z = M^-1 r_0
-        rc = loop(LOOP_CG, ctx->C.cg_maxit, [&](cudaStream_t bs, cudaGraphConditionalHandle h, bool g) {
-            launch_cg_iter(a, L, nlev, kCoarseSweeps, a.N.pp, bs, tr);
-            launch_loop_ctl(a.sc, h, g, LOOP_CG, ctx->C.cg_maxit, body_cg, bs, tr);
-        });
-        if (rc) return rc;
+        if (ctx->net && (ctx->net_mode & 2)) {
+            // flexible CG with the two-stage preconditioner (the network,
+            // then a V-cycle on what it leaves): each trip preconditions the
+            // current residual, then steps; gated, so that a solve that is
+            // already converged runs no network pass
+            int bad = 0;
+            auto body = [&](cudaStream_t bs, cudaGraphConditionalHandle h, bool g) {
+                const int nb = launch_fcg_iter(a, L, nlev, kCoarseSweeps, a.N.pp, ctx->net, ctx->net_r,
+                                               ctx->net_e, ctx->net_s, bs, tr);
+                if (nb < 0) bad = 1;
+                launch_loop_ctl(a.sc, h, g, LOOP_CG, ctx->C.cg_maxit, nb < 0 ? 0 : nb + 1, bs, tr);
+            };
+            rc = graph ? capture_while(ctx, s, body, LOOP_CG)
+                       : eager_while(ctx, s, LOOP_CG, ctx->C.cg_maxit, body, true);
+            if (graph) ++fixed;   // the gate kernel
+            if (rc) return rc;
+            if (bad) return fail(ctx, GEA_ERR_CUDA, "network preconditioner failed");
+        } else {
+            fixed += launch_vcycle(a, L, nlev, kCoarseSweeps, s, tr);   // z = M^-1 r_0
+            rc = loop(LOOP_CG, ctx->C.cg_maxit, [&](cudaStream_t bs, cudaGraphConditionalHandle h, bool g) {
+                launch_cg_iter(a, L, nlev, kCoarseSweeps, a.N.pp, bs, tr);
+                launch_loop_ctl(a.sc, h, g, LOOP_CG, ctx->C.cg_maxit, body_cg, bs, tr);
+            });
+            if (rc) return rc;
+        }
         CK(graph ? cudaEventRecordWithFlags(ctx->ev[2 * c + 1], s, cudaEventRecordExternal)
                  : cudaEventRecord(ctx->ev[2 * c + 1], s));
         launch_correct(a, s, tr); ++fixed;
@@ -342,7 +376,7 @@ int record_step_mixed(gea_ctx *ctx, int from, cudaStream_t s, bool graph, Tracer
         CK(graph ? cudaEventRecordWithFlags(ctx->ev[2 * c], s, cudaEventRecordExternal)
                  : cudaEventRecord(ctx->ev[2 * c], s));
         launch_mx_helm_rhs(a, L0, Lf[0], m, c == 0 ? a.S.pp : a.N.pp, a.N.pp, c, s, tr); ++fixed;
-        if (ctx->net) {
+        if (ctx->net && (ctx->net_mode & 1)) {
             const int k = record_guess<float>(ctx, a, Lf[0], m.q, m.x, m.tol2, s, graph, tr);
             if (k < 0) return fail(ctx, GEA_ERR_CUDA, "learned initial guess failed");
             fixed += k;
@@ -880,9 +914,11 @@ int gea_profile_step(gea_ctx *ctx, gea_kernel_time *out, int32_t max_entries, in
 
 int gea_attach_net(gea_ctx *ctx, gea_net *net, int32_t mode)
 {
-    if (!ctx || mode < 0 || mode > 1 || (mode == 1 && !net)) return GEA_ERR_INVAL;
+    if (!ctx || mode < 0 || mode > 3 || (mode != 0 && !net)) return GEA_ERR_INVAL;
     const Geom &G = ctx->G;
-    if (mode == 1 && (G.nx % 8 || G.nz % 8 || !gea_net_fits(net, 1, G.nz, G.nx)))
+    if ((mode & 2) && ctx->mixed)
+        return fail(ctx, GEA_ERR_INVAL, "the network preconditioner is for the FP64 step (mode 2 and 3)");
+    if (mode != 0 && (G.nx % 8 || G.nz % 8 || !gea_net_fits(net, 1, G.nz, G.nx)))
         return fail(ctx, GEA_ERR_INVAL, "grid %d x %d does not fit the network", G.nx, G.nz);
     if (ctx->stream) CK(cudaStreamSynchronize(ctx->stream));
     // the step graphs change
@@ -894,16 +930,23 @@ int gea_attach_net(gea_ctx *ctx, gea_net *net, int32_t mode)
     }
     if (ctx->net_r) cudaFree(ctx->net_r);
     if (ctx->net_e) cudaFree(ctx->net_e);
+    if (ctx->net_s) cudaFree(ctx->net_s);
     ctx->net_r = ctx->net_e = nullptr;
+    ctx->net_s = nullptr;
     ctx->net = nullptr;
+    ctx->net_mode = 0;
     if (mode == 0) return GEA_OK;
     const size_t bytes = (size_t)G.nx * G.nz * sizeof(float);
-    if (cudaMalloc(&ctx->net_r, bytes) != cudaSuccess || cudaMalloc(&ctx->net_e, bytes) != cudaSuccess) {
+    if (cudaMalloc(&ctx->net_r, bytes) != cudaSuccess || cudaMalloc(&ctx->net_e, bytes) != cudaSuccess ||
+        ((mode & 2) && cudaMalloc(&ctx->net_s, arr_bytes(G, G.nz)) != cudaSuccess)) {
         cudaGetLastError();
         if (ctx->net_r) cudaFree(ctx->net_r);
-        ctx->net_r = nullptr;
+        if (ctx->net_e) cudaFree(ctx->net_e);
+        ctx->net_r = ctx->net_e = nullptr;
+        ctx->net_s = nullptr;
         return fail(ctx, GEA_ERR_NOMEM, "network buffers");
     }
+    if (ctx->net_s) CK(cudaMemsetAsync(ctx->net_s, 0, arr_bytes(G, G.nz), ctx->stream));
     // one eager forward pass outside any capture sets up the network's
     // kernels (launch attributes are set on first use)
     CK(cudaMemsetAsync(ctx->net_r, 0, bytes, ctx->stream));
@@ -911,6 +954,7 @@ int gea_attach_net(gea_ctx *ctx, gea_net *net, int32_t mode)
         return fail(ctx, GEA_ERR_CUDA, "network forward failed");
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->net = net;
+    ctx->net_mode = mode;
     return GEA_OK;
 }
 
@@ -1073,6 +1117,7 @@ void gea_destroy(gea_ctx *ctx)
     if (ctx->mem) cudaFree(ctx->mem);
     if (ctx->net_r) cudaFree(ctx->net_r);
     if (ctx->net_e) cudaFree(ctx->net_e);
+    if (ctx->net_s) cudaFree(ctx->net_s);
     delete ctx;
 }
 

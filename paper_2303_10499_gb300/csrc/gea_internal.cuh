@@ -290,6 +290,8 @@ void launch_correct(const StepArgs &a, cudaStream_t st, Tracer *tr);
 // graph: set the WHILE condition through h; otherwise bookkeeping only
 void launch_loop_ctl(Scal *sc, cudaGraphConditionalHandle h, bool graph, int which,
                      int maxtrips, int body_launches, cudaStream_t st, Tracer *tr);
+// sets the condition of the WHILE node that follows from the loop's flags
+void launch_loop_gate(Scal *sc, cudaGraphConditionalHandle h, int which, cudaStream_t st);
 void launch_step_begin(Scal *sc, cudaStream_t st, Tracer *tr);
 void launch_step_end(Scal *sc, int fixed_launches, cudaStream_t st, Tracer *tr);
 void launch_diag(const Geom &G, const Phys &F, const State &S, const double *theta_bar,
@@ -308,6 +310,12 @@ void launch_guess_in(const StepArgs &a, const LevelT<R> &L, const R *r, float *d
 template <class R>
 int launch_net_guess(const StepArgs &a, const LevelT<R> &L, R *r, R *q, R *x, double tol2, gea_net *net,
                      float *dense_r, float *dense_e, cudaStream_t st, Tracer *tr);
+// One iteration of flexible CG with the two-stage preconditioner (FP64
+// levels L): z = g N(r) + M(r - g A N(r)) with the network N and one
+// V-cycle M (s_buf: a field for r - g A N(r)), the direction update, q = A p,
+// x and r. Returns the number of launches, or -1.
+int launch_fcg_iter(const StepArgs &a, Level *L, int nlev, int ncoarse, double *x, gea_net *net,
+                    float *dense_r, float *dense_e, double *s_buf, cudaStream_t st, Tracer *tr);
 // mixed-precision step (gea_mixed.cu)
 void launch_mx_pred(const StepArgs &a, const MixedArgs &m, cudaStream_t st, Tracer *tr);
 void launch_mx_mom(const StepArgs &a, const MixedArgs &m, const float *ui, const float *wi, float *uo,

@@ -253,6 +253,12 @@ __global__ void k_loop_ctl(Scal *sc, cudaGraphConditionalHandle h, int graph, in
     if (graph) cudaGraphSetConditional(h, (done || sc->status || trips >= maxtrips) ? 0u : 1u);
 }
 
+// Before a gated loop: run it only while it is not finished.
+__global__ void k_loop_gate(Scal *sc, cudaGraphConditionalHandle h, int which)
+{
+    cudaGraphSetConditional(h, (sc->done[which] || sc->status) ? 0u : 1u);
+}
+
 __global__ void k_step_begin(Scal *sc)
 {
     sc->u1_slot = sc->h1_slot = 0;
@@ -493,6 +499,166 @@ __global__ void k_guess_apply(LevelT<R> L, const float *e, const R *q, R *r, R *
     if (grid_sum<1, R>(acc, red, partials, &sc->counters[CNT_GUESS], tot)) fin_guess_apply(sc, tot, tol2);
 }
 
+// ---- flexible CG with a two-stage preconditioner (attach mode 2) ----
+//
+// z = g e + M(r - g A e): the network's correction e = N(r) with the step g
+// that minimises the A-norm error along it, then one multigrid V-cycle M on
+// the residual it leaves. The network alone stagnates (it cannot represent
+// the residual its own step leaves), the V-cycle keeps the linear part.
+// The preconditioner is nonlinear, so the one-term recurrence is written in
+// the form that stays a descent method for a changing preconditioner
+// (flexible CG truncated to one previous direction): beta = -(z.q_old) /
+// (p_old.q_old), p = z + beta p_old, alpha = r.p / p.A p.
+
+// A e at cell (i, k) of a tile holding e (FP64, halo 1).
+__device__ __forceinline__ double fcg_ae(const Level &L, int q, int i, int k, const Tile<1> &se, int y, int x)
+{
+    return helm_tile<1, double>(L, q, i, k, se, y, x);
+}
+
+// The network's correction e (FP32, dense) on the tile and its halo.
+__device__ __forceinline__ void fcg_load_e(Tile<1> &se, const Geom &G, const float *e, int bx, int bz)
+{
+    load_tile_fn<1, double>(se, G, bx, bz, [&](int, int i, int k) { return (double)e[(size_t)k * G.nx + i]; });
+}
+
+// acc += (r.e, e.A e); g = r.e / e.A e (0 unless e.A e > 0).
+__global__ void k_fcg_dots(Level L, const float *e, Scal *sc, double *partials)
+{
+    if (loop_over(sc, LOOP_CG)) return;
+    __shared__ double sm[kT1];
+    __shared__ double red[2 * NTHREADS];
+    const Geom &G = L.G;
+    const double *r = res_of(L, sc->cg_it);
+    Tile<1> &se = tile_at<1>(sm, 0);
+    fcg_load_e(se, G, e, blockIdx.x, blockIdx.y);
+    __syncthreads();
+    double acc[2] = {0.0, 0.0}, tot[2];
+    int i, k;
+    if (cell_of(G, blockIdx.x, blockIdx.y, i, k)) {
+        const int q = cidx(G, i, k);
+        const int y = threadIdx.y + 1, x = threadIdx.x + 1;
+        const double ev = se[y][x];
+        acc[0] = ld(&r[q]) * ev;
+        acc[1] = ev * fcg_ae(L, q, i, k, se, y, x);
+    }
+    if (grid_sum<2>(acc, red, partials, &sc->counters[CNT_GUESS], tot))
+        sc->galpha = (tot[1] > 0.0 && isfinite(tot[0]) && isfinite(tot[1])) ? tot[0] / tot[1] : 0.0;
+}
+
+// s = r - g A e, the V-cycle's input.
+__global__ void k_fcg_rest(Level L, const float *e, double *s, Scal *sc)
+{
+    if (loop_over(sc, LOOP_CG)) return;
+    __shared__ double sm[kT1];
+    const Geom &G = L.G;
+    const double *r = res_of(L, sc->cg_it);
+    const double g = sc->galpha;
+    Tile<1> &se = tile_at<1>(sm, 0);
+    fcg_load_e(se, G, e, blockIdx.x, blockIdx.y);
+    __syncthreads();
+    int i, k;
+    if (cell_of(G, blockIdx.x, blockIdx.y, i, k)) {
+        const int q = cidx(G, i, k);
+        const int y = threadIdx.y + 1, x = threadIdx.x + 1;
+        s[q] = fma(-g, fcg_ae(L, q, i, k, se, y, x), ld(&r[q]));
+    }
+}
+
+// z = g e + z_MG (the V-cycle's output in e2), written to e2; acc += z.q_old
+// (none before the first direction); beta = -z.q_old / p_old.q_old.
+__global__ void k_fcg_out(Level L, const float *e, const double *q_old, Scal *sc, double *partials)
+{
+    if (loop_over(sc, LOOP_CG)) return;
+    __shared__ double red[NTHREADS];
+    const Geom &G = L.G;
+    const bool first = sc->cg_it == 0;
+    const double g = sc->galpha;
+    double acc[1] = {0.0}, tot[1];
+    int i, k;
+    if (cell_of(G, blockIdx.x, blockIdx.y, i, k)) {
+        const int q = cidx(G, i, k);
+        const double z = fma(g, (double)e[(size_t)k * G.nx + i], L.e2[q]);
+        L.e2[q] = z;
+        if (!first) acc[0] = z * ld(&q_old[q]);
+    }
+    if (grid_sum<1>(acc, red, partials, &sc->counters[CNT_RZ], tot)) {
+        sc->beta = (first || sc->pq == 0.0) ? 0.0 : -tot[0] / sc->pq;
+        if (!isfinite(tot[0])) sc->status = GEA_ERR_NONFINITE;
+    }
+}
+
+// r for the network (FP32, dense), from the residual of the current iteration.
+__global__ void k_fcg_stage_in(Level L, float *dense, Scal *sc)
+{
+    if (loop_over(sc, LOOP_CG)) return;
+    const Geom &G = L.G;
+    int i, k;
+    if (!cell_of(G, blockIdx.x, blockIdx.y, i, k)) return;
+    dense[(size_t)k * G.nx + i] = (float)ld(&res_of(L, sc->cg_it)[cidx(G, i, k)]);
+}
+
+// p = z + beta p_old (on the tile and its halo), q = A p; acc += (p.q, r.p);
+// alpha = r.p / p.q.
+__global__ void k_fcg_pspmv(StepArgs a, Level L)
+{
+    Scal *sc = a.sc;
+    if (loop_over(sc, LOOP_CG)) return;
+    __shared__ double sm[kT1];
+    __shared__ double red[2 * NTHREADS];
+    const Geom &G = L.G;
+    const int it = sc->cg_it;
+    const double *pold = (it & 1) ? a.p1 : a.p0;
+    double *pnew = (it & 1) ? a.p0 : a.p1;
+    const double *r = res_of(L, it);
+    const double beta = sc->beta;
+    const int bx = blockIdx.x, bz = blockIdx.y;
+    Tile<1> &sp = tile_at<1>(sm, 0);
+    load_tile_fn<1, double>(sp, G, bx, bz, [&](int q, int, int) { return fma(beta, ld(&pold[q]), ld(&L.e2[q])); });
+    __syncthreads();
+    double acc[2] = {0.0, 0.0}, tot[2];
+    int i, k;
+    if (cell_of(G, bx, bz, i, k)) {
+        const int q = cidx(G, i, k);
+        const int y = threadIdx.y + 1, x = threadIdx.x + 1;
+        const double pq = sp[y][x];
+        const double Ap = helm_tile<1, double>(L, q, i, k, sp, y, x);
+        pnew[q] = pq;
+        a.q[q] = Ap;
+        acc[0] = pq * Ap;
+        acc[1] = ld(&r[q]) * pq;
+    }
+    if (grid_sum<2>(acc, red, a.partials, &sc->counters[CNT_PQ], tot)) {
+        sc->pq = tot[0];
+        sc->alpha = tot[0] != 0.0 ? tot[1] / tot[0] : 0.0;
+        if (!isfinite(tot[0]) || !isfinite(tot[1])) sc->status = GEA_ERR_NONFINITE;
+    }
+}
+
+// x += alpha p, r_new = r - alpha q (into the other residual buffer); acc += r_new^2.
+__global__ void k_fcg_update(StepArgs a, Level L, double *x)
+{
+    Scal *sc = a.sc;
+    if (loop_over(sc, LOOP_CG)) return;
+    __shared__ double red[NTHREADS];
+    const Geom &G = L.G;
+    const int it = sc->cg_it;
+    const double *p = (it & 1) ? a.p0 : a.p1;
+    const double *rin = res_of(L, it);
+    double *rout = res_of(L, it + 1);
+    const double alpha = sc->alpha;
+    double acc[1] = {0.0}, tot[1];
+    int i, k;
+    if (cell_of(G, blockIdx.x, blockIdx.y, i, k)) {
+        const int q = cidx(G, i, k);
+        x[q] = fma(alpha, ld(&p[q]), x[q]);
+        const double rn = fma(-alpha, ld(&a.q[q]), ld(&rin[q]));
+        rout[q] = rn;
+        acc[0] = rn * rn;
+    }
+    if (grid_sum<1>(acc, red, a.partials, &sc->counters[CNT_UPD], tot)) fin_update(sc, tot, a.cg_rtol2);
+}
+
 }  // namespace
 
 template <class R>
@@ -521,6 +687,31 @@ int launch_net_guess(const StepArgs &a, const LevelT<R> &L, R *r, R *q, R *x, do
     return 2 + nk;
 }
 
+int launch_fcg_iter(const StepArgs &a, Level *L, int nlev, int ncoarse, double *x, gea_net *net,
+                    float *dense_r, float *dense_e, double *s_buf, cudaStream_t st, Tracer *tr)
+{
+    const Geom &G = L[0].G;
+    TRACED(tr, "fcg_stage_in", ncell(G), (k_fcg_stage_in<<<grid_of(G), kBlock, 0, st>>>(L[0], dense_r, a.sc)));
+    if (tr) tr->begin("net_forward", ncell(G), st);
+    const int nk = gea_net_run(net, st, 1, G.nz, G.nx, dense_r, dense_e);
+    if (tr) tr->end(st);
+    if (nk < 0) return -1;
+    TRACED(tr, "fcg_dots", ncell(G), (k_fcg_dots<<<grid_of(G), kBlock, 0, st>>>(L[0], dense_e, a.sc, a.partials)));
+    TRACED(tr, "fcg_rest", ncell(G),
+           (k_fcg_rest<<<grid_of(G), kBlock, 0, st>>>(L[0], dense_e, s_buf, a.sc)));
+    // the V-cycle on s: a copy of the levels whose finest residual buffers
+    // both name s_buf
+    Level M[kMaxLevels];
+    for (int l = 0; l < nlev; ++l) M[l] = L[l];
+    M[0].r = M[0].r_alt = s_buf;
+    const int nv = launch_vcycle(a, M, nlev, ncoarse, st, tr);
+    TRACED(tr, "fcg_out", ncell(G),
+           (k_fcg_out<<<grid_of(G), kBlock, 0, st>>>(L[0], dense_e, a.q, a.sc, a.partials)));
+    TRACED(tr, "fcg_pspmv", ncell(G), (k_fcg_pspmv<<<grid_of(G), kBlock, 0, st>>>(a, L[0])));
+    TRACED(tr, "fcg_update", ncell(G), (k_fcg_update<<<grid_of(G), kBlock, 0, st>>>(a, L[0], x)));
+    return 6 + nk + nv;
+}
+
 template void launch_guess_in<double>(const StepArgs &, const LevelT<double> &, const double *, float *,
                                       cudaGraphConditionalHandle, bool, cudaStream_t, Tracer *);
 template void launch_guess_in<float>(const StepArgs &, const LevelT<float> &, const float *, float *,
@@ -540,6 +731,11 @@ void launch_loop_ctl(Scal *sc, cudaGraphConditionalHandle h, bool graph, int whi
 {
     TRACED(tr, "loop_ctl", 1,
            (k_loop_ctl<<<1, 1, 0, st>>>(sc, h, graph ? 1 : 0, which, maxtrips, body_launches)));
+}
+
+void launch_loop_gate(Scal *sc, cudaGraphConditionalHandle h, int which, cudaStream_t st)
+{
+    k_loop_gate<<<1, 1, 0, st>>>(sc, h, which);
 }
 
 void launch_step_begin(Scal *sc, cudaStream_t st, Tracer *tr)

@@ -277,8 +277,10 @@ class Solver:
         return float(self.lib.gea_last_pressure_ms(self.h))
 
     def attach_net(self, net, mode: int = 1):
-        """Use a Net as the learned initial guess of the pressure solves
-        (mode 1) or detach it (mode 0, net None)."""
+        """Use a Net in the pressure solves: as their learned initial guess
+        (mode 1), as the preconditioner of a flexible CG in place of the
+        multigrid V-cycle (mode 2, FP64 step only), or both (mode 3); mode 0
+        (net None) detaches it."""
         self._check(self.lib.gea_attach_net(self.h, net.h if net is not None else None, mode))
         self._net = net if mode else None   # keep it alive while attached
 

@@ -116,3 +116,50 @@ def test_trained_guess_saves_iterations_at_4096(env):
         s.close()
     print(its)
     assert sum(its[True]) < sum(its[False])
+
+
+def test_network_preconditioner_keeps_parity(env, oracle_mod):
+    """Flexible CG with the network as the preconditioner in place of the
+    V-cycle (mode 2): the network, trained briefly on the same bubble's own
+    pressure systems, only shapes the search directions, and each solve still
+    runs to the same tolerance, so the FP64 step matches the oracle at the
+    parity bound."""
+    torch, G, learned = env
+    wl = W.get("bubble160x80")
+    samples = learned.collect(wl, 6, every=1)
+    net = G.Net(4, 80, 160, relu=False)
+    net.set_params(learned.initial_params(2) * 0.5)
+    learned.train(net, samples, 150, n=4, h=80, w=160, lr=2e-3)
+    steps = 20
+    o = oracle_mod.Oracle(wl.grid, wl.const)
+    so = o.derive(wl.fields)
+    o.step(so, steps)
+    s = G.Solver(wl.grid, wl.const)
+    s.set_conservative(wl.fields)
+    s.attach_net(net, 2)
+    its = []
+    for _ in range(steps):
+        s.step(1)
+        st = s.stats()
+        assert st["status"] == 0, st
+        its.append(st["cg_iters"])
+    assert st["driver"] == "graph"
+    assert all(i[0] > 0 for i in its), its
+    g = s.get_full()
+    for k in ("rho", "T", "pp"):
+        assert rel_l2(g[k], so[k]) < 1e-10, k
+    vel = np.hypot(np.linalg.norm(so["u"]), np.linalg.norm(so["w"]))
+    for k in ("u", "w"):
+        assert np.linalg.norm(g[k] - so[k]) / vel < 1e-10, k
+    print(its)
+
+
+def test_network_preconditioner_is_fp64_only(env):
+    torch, G, learned = env
+    wl = W.get("bubble160x80")
+    net = G.Net(1, 80, 160, relu=False)
+    s = G.Solver(wl.grid, wl.const, mixed=True)
+    with pytest.raises(G.GeaError) as ei:
+        s.attach_net(net, 2)
+    assert ei.value.code == G.GEA_ERR_INVAL
+    s.attach_net(net, 1)          # the guess is fine for the mixed step
