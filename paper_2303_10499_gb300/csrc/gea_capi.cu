@@ -492,6 +492,9 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
     *out = nullptr;
     if (grid->nx < 4 || grid->nz < 4 || !(grid->lx > 0) || !(grid->lz > 0)) return GEA_ERR_INVAL;
     if ((long long)grid->nx * grid->nz > (1LL << 31) / 2) return GEA_ERR_INVAL;
+    // the grid sums' group counters cover this many tiles (blocks)
+    if ((long long)((grid->nx + BX - 1) / BX) * ((grid->nz + BZ - 1) / BZ) > (long long)kGroupCounters * kSumGroup)
+        return GEA_ERR_INVAL;
     if (!(c->R > 0) || !(c->cp > c->R) || !(c->g >= 0) || !(c->p0 > 0) || !(c->mu >= 0) ||
         !(c->Pr > 0) || !(c->dt > 0) || c->n_corr < 1 || c->n_corr > 4 || !(c->jac_rtol > 0) ||
         c->jac_maxit < 1 || !(c->cg_rtol > 0) || c->cg_maxit < 1 || c->mg_min_cells < 0 ||
@@ -551,7 +554,7 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
         for (const Geom &g : lg) total += 8 * arr_bytes_f(g, g.nz) + arr_bytes_f(g, g.nz + 1);
     }
     const size_t nb = (size_t)max_blocks(G);
-    total += round_up(8 * nb * sizeof(double), 256);      // reduction partials (two buffers)
+    total += round_up((kGcntDoubles + 8 * nb) * sizeof(double), 256);   // group counters, reduction partials
     total += round_up(sizeof(Scal), 256);
     ctx->mem_bytes = total;
     if (cudaMalloc(&ctx->mem, total) != cudaSuccess) {
@@ -613,8 +616,10 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
             ctx->Lf.push_back(l);
         }
     }
-    // two buffers of 4 x (blocks <= tiles) partials for the persistent kernels
-    ctx->partials = take(round_up(8 * nb * sizeof(double), 256));
+    // group counters of the grid sums, then two buffers of 4 x (blocks <=
+    // tiles) partials for the persistent kernels (or a grid sum's block and
+    // group totals)
+    ctx->partials = take(round_up((kGcntDoubles + 8 * nb) * sizeof(double), 256));
     ctx->sc = (Scal *)take(round_up(sizeof(Scal), 256));
     if ((size_t)(ptr - ctx->mem) > total) {
         gea_destroy(ctx);

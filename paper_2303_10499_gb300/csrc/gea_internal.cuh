@@ -227,10 +227,20 @@ __device__ __forceinline__ void block_sum(const T (&v)[NV], T *red, T (&out)[NV]
     __syncthreads();
 }
 
-// Deterministic grid-wide sum of NV values per thread (one launch). Each
-// block writes its totals; the block that arrives last adds the partials in
-// a fixed order and returns true in its thread 0 with the totals in tot[].
-// Every thread of every block must call it.
+// The partials buffer of a context: kGcntDoubles doubles of group counters
+// (unsigned, zero between launches; the two-level grid sums below), then the
+// block partials (the grid sums' block and group totals, or the persistent
+// kernels' two buffers of kRedVals x blocks values).
+constexpr int kSumGroup = 1024;                 // blocks per group of a grid sum
+constexpr int kGroupCounters = 4096;            // groups a grid sum may have
+constexpr int kGcntDoubles = kGroupCounters / 2;
+
+// Deterministic grid-wide sum of NV values per thread (one launch), in two
+// levels: the last block of each group of kSumGroup blocks adds the group's
+// block totals, the last group adds the group totals, each in a fixed order
+// (the arrivals spread over one counter per group instead of all blocks on
+// one). Returns true in thread 0 of the very last block, with the totals in
+// tot[]. Every thread of every block must call it.
 // T is the type of the per-thread values and of the block sums (FP32 for the
 // inner solves of the mixed-precision path); block partials and the grid
 // total are FP64. red holds NV * NTHREADS doubles.
@@ -238,26 +248,46 @@ template <int NV, class T = double>
 __device__ bool grid_sum(const T (&v)[NV], double *red, double *partials, unsigned *counter,
                          double (&tot)[NV])
 {
-    __shared__ int am_last;
+    __shared__ int flag;
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     const int bid = blockIdx.x + blockIdx.y * gridDim.x;
     const int nb = gridDim.x * gridDim.y;
+    const int ng = (nb + kSumGroup - 1) / kSumGroup, grp = bid / kSumGroup, g0 = grp * kSumGroup;
+    const int gn = min(kSumGroup, nb - g0);
+    unsigned *gcnt = reinterpret_cast<unsigned *>(partials);
+    double *p1 = partials + kGcntDoubles, *p2 = p1 + (size_t)NV * nb;
     T bt[NV];
     block_sum<NV, T>(v, reinterpret_cast<T *>(red), bt);
     if (tid == 0) {
 #pragma unroll
-        for (int j = 0; j < NV; ++j) partials[(size_t)j * nb + bid] = (double)bt[j];
+        for (int j = 0; j < NV; ++j) p1[(size_t)j * nb + bid] = (double)bt[j];
         __threadfence();
-        am_last = atomicAdd(counter, 1u) == (unsigned)nb - 1u;
+        flag = atomicAdd(&gcnt[grp], 1u) == (unsigned)gn - 1u;
     }
     __syncthreads();
-    if (!am_last) return false;
+    if (!flag) return false;
     __threadfence();
-    double s[NV];
+    double s[NV], gt[NV];
 #pragma unroll
     for (int j = 0; j < NV; ++j) {
         s[j] = 0.0;
-        for (int b = tid; b < nb; b += NTHREADS) s[j] += __ldcg(&partials[(size_t)j * nb + b]);
+        for (int b = tid; b < gn; b += NTHREADS) s[j] += __ldcg(&p1[(size_t)j * nb + g0 + b]);
+    }
+    block_sum<NV>(s, red, gt);
+    if (tid == 0) {
+        gcnt[grp] = 0u;
+#pragma unroll
+        for (int j = 0; j < NV; ++j) p2[(size_t)j * ng + grp] = gt[j];
+        __threadfence();
+        flag = atomicAdd(counter, 1u) == (unsigned)ng - 1u;
+    }
+    __syncthreads();
+    if (!flag) return false;
+    __threadfence();
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        s[j] = 0.0;
+        for (int b = tid; b < ng; b += NTHREADS) s[j] += __ldcg(&p2[(size_t)j * ng + b]);
     }
     block_sum<NV>(s, red, tot);
     if (tid == 0) *counter = 0u;

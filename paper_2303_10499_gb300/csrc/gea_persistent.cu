@@ -159,7 +159,7 @@ __device__ __forceinline__ void rbar(const Grp &g, const T (&v)[NV], double *red
     static_assert(NV <= kRedVals, "the block-sum scratch holds kRedVals values per thread");
     const int tid = tid_of();
     const int nb = g.nb;
-    double *pb = partials + (size_t)(*g.gen & 1u) * kRedVals * nb;
+    double *pb = partials + kGcntDoubles + (size_t)(*g.gen & 1u) * kRedVals * nb;
     T bt[NV];
     block_sum<NV, T>(v, reinterpret_cast<T *>(red), bt);
     if (tid == 0) {

@@ -79,6 +79,12 @@ def test_create_rejects_bad_flags_and_mixed_tolerance():
         with pytest.raises(gea.GeaError) as ei:
             gea.Solver(wl.grid, wl.const, **kw)
         assert ei.value.code == gea.GEA_ERR_INVAL, kw
+    # more tiles (32 x 8 cells) than the grid sums' 4096 groups of 1024
+    # blocks cover, though within the cell limit: 33 columns are two tiles wide
+    big = W.Grid(33, (1 << 30) // 33 // 8 * 8, 33.0, 1e6)
+    with pytest.raises(gea.GeaError) as ei:
+        gea.Solver(big, wl.const)
+    assert ei.value.code == gea.GEA_ERR_INVAL
 
 
 def test_grid3_struct_matches_header():
