@@ -128,9 +128,9 @@ __device__ __forceinline__ bool cell(const Geo &G, int &i, int &j, int &k)
     return i < G.nx && j < G.ny && k < G.nz;
 }
 
-// The FP64 CG kernels' blocks walk kLayers consecutive cell layers of their
-// column tile (one block reduction per kLayers cells a thread; the
-// memory-bound FP32 kernels keep one cell per thread): (i, j) of the thread
+// The CG kernels with a reduction (FP64 and FP32) and the finest
+// prolongation walk kLayers consecutive cell layers of their column tile
+// (one block reduction per kLayers cells a thread): (i, j) of the thread
 // and its layer range [k0, k1). The layer loop stays rolled: unrolled, its
 // interleaved loads took 56-79 registers a thread and the kernels ran
 // 30-40 % slower at the lower occupancy.
@@ -1371,13 +1371,15 @@ __global__ void k_mx_spmv(Args a, Mx m, Lev32 M0)
     float acc[1] = {0.0f};
     double tot[1];
     const float *p = (sc->cg_it & 1) ? m.p0 : m.p1;
-    int i, j, k;
-    if (cell(M0.G, i, j, k)) {
-        const int q = id3(M0.G, i, j, k);
-        const float Ap = helm32(M0, [&](int qq, int, int, int) { return ldf(&p[qq]); }, i, j, k);
-        m.q[q] = Ap;
-        acc[0] = ldf(&p[q]) * Ap;
-    }
+    int i, j, k0, k1;
+    if (column(M0.G, i, j, k0, k1))
+#pragma unroll 1
+        for (int k = k0; k < k1; ++k) {
+            const int q = id3(M0.G, i, j, k);
+            const float Ap = helm32(M0, [&](int qq, int, int, int) { return ldf(&p[qq]); }, i, j, k);
+            m.q[q] = Ap;
+            acc[0] = fmaf(ldf(&p[q]), Ap, acc[0]);
+        }
     if (gsum<1, float>(acc, red, a.part, &sc->counters[C_PQ], tot)) {
         sc->pq = tot[0];
         sc->alpha = tot[0] != 0.0 ? sc->rz / tot[0] : 0.0;
@@ -1395,14 +1397,16 @@ __global__ void k_mx_update(Args a, Mx m, Lev32 M0)
     double tot[1];
     const float *p = (sc->cg_it & 1) ? m.p0 : m.p1;
     const float alpha = (float)sc->alpha;
-    int i, j, k;
-    if (cell(M0.G, i, j, k)) {
-        const int q = id3(M0.G, i, j, k);
-        m.x[q] = fmaf(alpha, ldf(&p[q]), m.x[q]);
-        const float rn = fmaf(-alpha, ldf(&m.q[q]), m.r[q]);
-        m.r[q] = rn;
-        acc[0] = rn * rn;
-    }
+    int i, j, k0, k1;
+    if (column(M0.G, i, j, k0, k1))
+#pragma unroll 1
+        for (int k = k0; k < k1; ++k) {
+            const int q = id3(M0.G, i, j, k);
+            m.x[q] = fmaf(alpha, ldf(&p[q]), m.x[q]);
+            const float rn = fmaf(-alpha, ldf(&m.q[q]), m.r[q]);
+            m.r[q] = rn;
+            acc[0] = fmaf(rn, rn, acc[0]);
+        }
     if (gsum<1, float>(acc, red, a.part, &sc->counters[C_UPD], tot)) {
         const int n = sc->cg_it + 1;
         sc->cg_it = n;
@@ -1800,8 +1804,8 @@ int record3(gea3d_ctx *ctx, int from, cudaStream_t s, bool graph, Trace3 *tr)
         rc = loop(L_CG, ctx->C.cg_maxit, [&](cudaStream_t bs, cudaGraphConditionalHandle h) {
             if (ctx->mixed) {
                 traced(tr, "g3_mx_pupd", G, bs, [&] { k_mx_pupd<<<grid, kBlk, 0, bs>>>(a, m, M[0]); });
-                traced(tr, "g3_mx_spmv", G, bs, [&] { k_mx_spmv<<<grid, kBlk, 0, bs>>>(a, m, M[0]); });
-                traced(tr, "g3_mx_update", G, bs, [&] { k_mx_update<<<grid, kBlk, 0, bs>>>(a, m, M[0]); });
+                traced(tr, "g3_mx_spmv", G, bs, [&] { k_mx_spmv<<<gridc, kBlk, 0, bs>>>(a, m, M[0]); });
+                traced(tr, "g3_mx_update", G, bs, [&] { k_mx_update<<<gridc, kBlk, 0, bs>>>(a, m, M[0]); });
             } else {
                 traced(tr, "g3_pupd", G, bs, [&] { k_pupd<<<grid, kBlk, 0, bs>>>(a, L[0]); });
                 traced(tr, "g3_spmv", G, bs, [&] { k_spmv<<<gridc, kBlk, 0, bs>>>(a, L[0]); });
