@@ -294,6 +294,28 @@ __device__ bool grid_sum(const T (&v)[NV], double *red, double *partials, unsign
     return tid == 0;
 }
 
+// The light per-phase kernels with a grid reduction (the CG and V-cycle
+// steps) run kTilesPerBlock tiles of a tile column per block: a quarter of
+// the blocks, so a quarter of the block reductions and arrivals.
+constexpr int kTilesPerBlock = 4;
+inline dim3 grid_tiles(const Geom &G)
+{
+    const int tz = (G.nz + BZ - 1) / BZ;
+    return dim3((G.nx + BX - 1) / BX, (tz + kTilesPerBlock - 1) / kTilesPerBlock);
+}
+// f(bx, bz) for the block's tiles (block-uniform loop; each f ends with a
+// block barrier).
+template <class F>
+__device__ __forceinline__ void block_tiles(const Geom &G, F f)
+{
+    const int tz = (G.nz + BZ - 1) / BZ;
+    for (int t = 0; t < kTilesPerBlock; ++t) {
+        const int bz = blockIdx.y * kTilesPerBlock + t;
+        if (bz >= tz) break;
+        f((int)blockIdx.x, bz);
+    }
+}
+
 // ---- host-side launchers (gea_kernels.cu); tr may be null ----
 void launch_derive(const Geom &G, const Phys &F, const double *rho, const double *rhou,
                    const double *rhow, const double *rhoe, const State &S, Scal *sc,

@@ -171,7 +171,7 @@ __global__ void k_mg_up(Level f, const double *ec, int Pc, double *out, int fine
     double acc[1] = {0.0}, tot[1];
     // the finest level's residual alternates between two buffers
     const double *res = finest ? res_of(f, a.sc->cg_it) : f.r;
-    ph_mg_up(f, res, ec, Pc, out, sm, blockIdx.x, blockIdx.y, acc);
+    block_tiles(f.G, [&](int bx, int bz) { ph_mg_up(f, res, ec, Pc, out, sm, bx, bz, acc); });
     if (!finest) return;
     if (grid_sum<1>(acc, red, a.partials, &a.sc->counters[CNT_RZ], tot)) fin_rz(a.sc, tot);
 }
@@ -182,7 +182,7 @@ __global__ void k_mg_single(Level f, double *out, StepArgs a)
     __shared__ double sm[kT1];
     __shared__ double red[NTHREADS];
     double acc[1] = {0.0}, tot[1];
-    ph_mg_single(f, out, sm, blockIdx.x, blockIdx.y, acc);
+    block_tiles(f.G, [&](int bx, int bz) { ph_mg_single(f, out, sm, bx, bz, acc); });
     if (grid_sum<1>(acc, red, a.partials, &a.sc->counters[CNT_RZ], tot)) fin_rz(a.sc, tot);
 }
 
@@ -198,7 +198,7 @@ __global__ void k_cg_pspmv(StepArgs a, Level L)
     const double *pold = (it & 1) ? a.p1 : a.p0;
     double *pnew = (it & 1) ? a.p0 : a.p1;
     double acc[1] = {0.0}, tot[1];
-    ph_pspmv<double>(L, pold, pnew, a.q, sc->beta, sm, blockIdx.x, blockIdx.y, acc);
+    block_tiles(L.G, [&](int bx, int bz) { ph_pspmv<double>(L, pold, pnew, a.q, sc->beta, sm, bx, bz, acc); });
     if (grid_sum<1>(acc, red, a.partials, &sc->counters[CNT_PQ], tot)) fin_pq(sc, tot);
 }
 
@@ -211,8 +211,9 @@ __global__ void k_cg_update_single(StepArgs a, Level L, double *x)
     const int it = sc->cg_it;
     const double *p = (it & 1) ? a.p0 : a.p1;
     double acc[2] = {0.0, 0.0}, tot[2];
-    ph_update_single<double>(L, a.q, res_of(L, it), res_of(L, it + 1), x, p, sc->alpha, sm, blockIdx.x,
-                             blockIdx.y, acc);
+    block_tiles(L.G, [&](int bx, int bz) {
+        ph_update_single<double>(L, a.q, res_of(L, it), res_of(L, it + 1), x, p, sc->alpha, sm, bx, bz, acc);
+    });
     if (grid_sum<2>(acc, red, a.partials, &sc->counters[CNT_UPD], tot)) {
         const double t0[1] = {tot[0]}, t1[1] = {tot[1]};
         fin_update(sc, t0, a.cg_rtol2);
@@ -229,8 +230,10 @@ __global__ void k_cg_update_down(StepArgs a, Level f, Level c, double *x)
     const int it = sc->cg_it;
     const double *p = (it & 1) ? a.p0 : a.p1;
     double acc[1] = {0.0}, tot[1];
-    ph_update_down<double>(f, c, a.q, res_of(f, it), res_of(f, it + 1), x, p, sc->alpha, a.F.omega, sm,
-                           blockIdx.x, blockIdx.y, acc);
+    block_tiles(f.G, [&](int bx, int bz) {
+        ph_update_down<double>(f, c, a.q, res_of(f, it), res_of(f, it + 1), x, p, sc->alpha, a.F.omega, sm,
+                               bx, bz, acc);
+    });
     if (grid_sum<1>(acc, red, a.partials, &sc->counters[CNT_UPD], tot)) fin_update(sc, tot, a.cg_rtol2);
 }
 
@@ -393,7 +396,7 @@ int launch_vcycle(const StepArgs &a, Level *L, int nlev, int ncoarse, cudaStream
 {
     if (nlev == 1) {
         TRACED(tr, "mg_single", ncell(L[0].G),
-               (k_mg_single<<<grid_of(L[0].G), kBlock, 0, st>>>(L[0], L[0].e2, a)));
+               (k_mg_single<<<grid_tiles(L[0].G), kBlock, 0, st>>>(L[0], L[0].e2, a)));
         return 1;
     }
     int n = 0;
@@ -410,7 +413,7 @@ int launch_vcycle(const StepArgs &a, Level *L, int nlev, int ncoarse, cudaStream
     }
     for (int l = nlev - 2; l >= 0; --l, ++n)
         TRACED(tr, "mg_up", ncell(L[l].G),
-               (k_mg_up<<<grid_of(L[l].G), kBlock, 0, st>>>(L[l], L[l + 1].e2, L[l + 1].G.P, L[l].e2,
+               (k_mg_up<<<grid_tiles(L[l].G), kBlock, 0, st>>>(L[l], L[l + 1].e2, L[l + 1].G.P, L[l].e2,
                                                              l == 0, a)));
     return n;
 }
@@ -434,7 +437,7 @@ static int launch_vcycle_rest(const StepArgs &a, Level *L, int nlev, int ncoarse
     }
     for (int l = nlev - 2; l >= 0; --l, ++n)
         TRACED(tr, "mg_up", ncell(L[l].G),
-               (k_mg_up<<<grid_of(L[l].G), kBlock, 0, st>>>(L[l], L[l + 1].e2, L[l + 1].G.P, L[l].e2,
+               (k_mg_up<<<grid_tiles(L[l].G), kBlock, 0, st>>>(L[l], L[l + 1].e2, L[l + 1].G.P, L[l].e2,
                                                              l == 0, a)));
     return n;
 }
@@ -445,14 +448,14 @@ static int launch_vcycle_rest(const StepArgs &a, Level *L, int nlev, int ncoarse
 int launch_cg_iter(const StepArgs &a, Level *L, int nlev, int ncoarse, double *x, cudaStream_t st,
                    Tracer *tr)
 {
-    TRACED(tr, "cg_pspmv", ncell(a.G), (k_cg_pspmv<<<grid_of(a.G), kBlock, 0, st>>>(a, L[0])));
+    TRACED(tr, "cg_pspmv", ncell(a.G), (k_cg_pspmv<<<grid_tiles(a.G), kBlock, 0, st>>>(a, L[0])));
     if (nlev == 1) {
         TRACED(tr, "cg_update_single", ncell(a.G),
-               (k_cg_update_single<<<grid_of(a.G), kBlock, 0, st>>>(a, L[0], x)));
+               (k_cg_update_single<<<grid_tiles(a.G), kBlock, 0, st>>>(a, L[0], x)));
         return 2;
     }
     TRACED(tr, "cg_update_down", ncell(a.G),
-           (k_cg_update_down<<<grid_of(a.G), kBlock, 0, st>>>(a, L[0], L[1], x)));
+           (k_cg_update_down<<<grid_tiles(a.G), kBlock, 0, st>>>(a, L[0], L[1], x)));
     return 2 + launch_vcycle_rest(a, L, nlev, ncoarse, st, tr);
 }
 

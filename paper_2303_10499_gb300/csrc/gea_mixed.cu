@@ -131,7 +131,7 @@ __global__ void k_mx_mg_up(LevelF f, const float *ec, int Pc, float *out, int fi
     float acc[1] = {0.0f};
     double tot[1];
     const float *res = finest ? res_of(f, a.sc->cg_it) : f.r;
-    ph_mg_up<float>(f, res, ec, Pc, out, sm, blockIdx.x, blockIdx.y, acc);
+    block_tiles(f.G, [&](int bx, int bz) { ph_mg_up<float>(f, res, ec, Pc, out, sm, bx, bz, acc); });
     if (!finest) return;
     if (grid_sum<1, float>(acc, red, a.partials, &a.sc->counters[CNT_RZ], tot)) fin_rz(a.sc, tot);
 }
@@ -143,7 +143,7 @@ __global__ void k_mx_mg_single(LevelF f, float *out, StepArgs a)
     __shared__ double red[NTHREADS];
     float acc[1] = {0.0f};
     double tot[1];
-    ph_mg_single<float>(f, out, sm, blockIdx.x, blockIdx.y, acc);
+    block_tiles(f.G, [&](int bx, int bz) { ph_mg_single<float>(f, out, sm, bx, bz, acc); });
     if (grid_sum<1, float>(acc, red, a.partials, &a.sc->counters[CNT_RZ], tot)) fin_rz(a.sc, tot);
 }
 
@@ -158,7 +158,7 @@ __global__ void k_mx_pspmv(StepArgs a, LevelF L, MixedArgs m)
     float *pnew = (it & 1) ? m.p0 : m.p1;
     float acc[1] = {0.0f};
     double tot[1];
-    ph_pspmv<float>(L, pold, pnew, m.q, sc->beta, sm, blockIdx.x, blockIdx.y, acc);
+    block_tiles(L.G, [&](int bx, int bz) { ph_pspmv<float>(L, pold, pnew, m.q, sc->beta, sm, bx, bz, acc); });
     if (grid_sum<1, float>(acc, red, a.partials, &sc->counters[CNT_PQ], tot)) fin_pq(sc, tot);
 }
 
@@ -172,8 +172,9 @@ __global__ void k_mx_update_single(StepArgs a, LevelF L, MixedArgs m)
     const float *p = (it & 1) ? m.p0 : m.p1;
     float acc[2] = {0.0f, 0.0f};
     double tot[2];
-    ph_update_single<float>(L, m.q, res_of(L, it), res_of(L, it + 1), m.x, p, sc->alpha, sm, blockIdx.x,
-                            blockIdx.y, acc);
+    block_tiles(L.G, [&](int bx, int bz) {
+        ph_update_single<float>(L, m.q, res_of(L, it), res_of(L, it + 1), m.x, p, sc->alpha, sm, bx, bz, acc);
+    });
     if (grid_sum<2, float>(acc, red, a.partials, &sc->counters[CNT_UPD], tot)) {
         const double t0[1] = {tot[0]}, t1[1] = {tot[1]};
         fin_update(sc, t0, m.tol2);
@@ -191,8 +192,10 @@ __global__ void k_mx_update_down(StepArgs a, LevelF f, LevelF c, MixedArgs m)
     const float *p = (it & 1) ? m.p0 : m.p1;
     float acc[1] = {0.0f};
     double tot[1];
-    ph_update_down<float>(f, c, m.q, res_of(f, it), res_of(f, it + 1), m.x, p, sc->alpha, a.F.omega, sm,
-                          blockIdx.x, blockIdx.y, acc);
+    block_tiles(f.G, [&](int bx, int bz) {
+        ph_update_down<float>(f, c, m.q, res_of(f, it), res_of(f, it + 1), m.x, p, sc->alpha, a.F.omega, sm,
+                              bx, bz, acc);
+    });
     if (grid_sum<1, float>(acc, red, a.partials, &sc->counters[CNT_UPD], tot)) fin_update(sc, tot, m.tol2);
 }
 
@@ -230,7 +233,7 @@ int vcycle32(const StepArgs &a, LevelF *L, int nlev, int ncoarse, int lfirst, cu
     }
     for (int l = nlev - 2; l >= 0; --l, ++n)
         TRACED(tr, "mx_mg_up", ncell(L[l].G),
-               (k_mx_mg_up<<<grid_of(L[l].G), kBlock, 0, st>>>(L[l], L[l + 1].e2, L[l + 1].G.P, L[l].e2,
+               (k_mx_mg_up<<<grid_tiles(L[l].G), kBlock, 0, st>>>(L[l], L[l + 1].e2, L[l + 1].G.P, L[l].e2,
                                                                 l == 0, a)));
     return n;
 }
@@ -283,7 +286,7 @@ int launch_mx_vcycle(const StepArgs &a, LevelF *L, int nlev, int ncoarse, cudaSt
 {
     if (nlev == 1) {
         TRACED(tr, "mx_mg_single", ncell(L[0].G),
-               (k_mx_mg_single<<<grid_of(L[0].G), kBlock, 0, st>>>(L[0], L[0].e2, a)));
+               (k_mx_mg_single<<<grid_tiles(L[0].G), kBlock, 0, st>>>(L[0], L[0].e2, a)));
         return 1;
     }
     return vcycle32(a, L, nlev, ncoarse, 0, st, tr);
@@ -293,14 +296,14 @@ int launch_mx_vcycle(const StepArgs &a, LevelF *L, int nlev, int ncoarse, cudaSt
 int launch_mx_cg_iter(const StepArgs &a, const MixedArgs &m, LevelF *L, int nlev, int ncoarse,
                       cudaStream_t st, Tracer *tr)
 {
-    TRACED(tr, "mx_pspmv", ncell(a.G), (k_mx_pspmv<<<grid_of(a.G), kBlock, 0, st>>>(a, L[0], m)));
+    TRACED(tr, "mx_pspmv", ncell(a.G), (k_mx_pspmv<<<grid_tiles(a.G), kBlock, 0, st>>>(a, L[0], m)));
     if (nlev == 1) {
         TRACED(tr, "mx_update_single", ncell(a.G),
-               (k_mx_update_single<<<grid_of(a.G), kBlock, 0, st>>>(a, L[0], m)));
+               (k_mx_update_single<<<grid_tiles(a.G), kBlock, 0, st>>>(a, L[0], m)));
         return 2;
     }
     TRACED(tr, "mx_update_down", ncell(a.G),
-           (k_mx_update_down<<<grid_of(a.G), kBlock, 0, st>>>(a, L[0], L[1], m)));
+           (k_mx_update_down<<<grid_tiles(a.G), kBlock, 0, st>>>(a, L[0], L[1], m)));
     return 2 + vcycle32(a, L, nlev, ncoarse, 1, st, tr);
 }
 
