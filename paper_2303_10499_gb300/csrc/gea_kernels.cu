@@ -80,14 +80,16 @@ __global__ void k_mom_jacobi(StepArgs a, const double *uin, const double *win, d
 {
     if (a.sc->status) return;
     if (second && a.sc->done[LOOP_MOM]) {
-        ph_copy(a.G, uin, uout, blockIdx.x, blockIdx.y);
-        ph_copy(a.G, win, wout, blockIdx.x, blockIdx.y);
+        block_tiles(a.G, [&](int bx, int bz) {
+            ph_copy(a.G, uin, uout, bx, bz);
+            ph_copy(a.G, win, wout, bx, bz);
+        });
         return;
     }
     __shared__ double sm[2 * kT2];
     __shared__ double red[2 * NTHREADS];
     double acc[2] = {0.0, 0.0}, tot[2];
-    ph_mom(a, uin, win, uout, wout, sm, blockIdx.x, blockIdx.y, acc);
+    block_tiles(a.G, [&](int bx, int bz) { ph_mom(a, uin, win, uout, wout, sm, bx, bz, acc); });
     if (grid_sum<2>(acc, red, a.partials, &a.sc->counters[CNT_MOM], tot)) fin_mom(a.sc, tot, a.jac_rtol2);
 }
 
@@ -107,13 +109,13 @@ __global__ void k_enth_jacobi(StepArgs a, const double *hin, double *hout, int s
 {
     if (a.sc->status) return;
     if (second && a.sc->done[LOOP_ENTH]) {
-        ph_copy(a.G, hin, hout, blockIdx.x, blockIdx.y);
+        block_tiles(a.G, [&](int bx, int bz) { ph_copy(a.G, hin, hout, bx, bz); });
         return;
     }
     __shared__ double sm[kT2];
     __shared__ double red[NTHREADS];
     double acc[1] = {0.0}, tot[1];
-    ph_enth(a, hin, hout, sm, blockIdx.x, blockIdx.y, acc);
+    block_tiles(a.G, [&](int bx, int bz) { ph_enth(a, hin, hout, sm, bx, bz, acc); });
     if (grid_sum<1>(acc, red, a.partials, &a.sc->counters[CNT_ENTH], tot)) fin_enth(a.sc, tot, a.jac_rtol2);
 }
 
@@ -353,7 +355,7 @@ void launch_mom_jacobi(const StepArgs &a, const double *uin, const double *win, 
                        double *wout, int second, cudaStream_t st, Tracer *tr)
 {
     TRACED(tr, "mom_jacobi", ncell(a.G),
-           (k_mom_jacobi<<<grid_of(a.G), kBlock, 0, st>>>(a, uin, win, uout, wout, second)));
+           (k_mom_jacobi<<<grid_tiles(a.G), kBlock, 0, st>>>(a, uin, win, uout, wout, second)));
 }
 
 void launch_enth_rhs(const StepArgs &a, cudaStream_t st, Tracer *tr)
@@ -365,7 +367,7 @@ void launch_enth_jacobi(const StepArgs &a, const double *hin, double *hout, int 
                         cudaStream_t st, Tracer *tr)
 {
     TRACED(tr, "enth_jacobi", ncell(a.G),
-           (k_enth_jacobi<<<grid_of(a.G), kBlock, 0, st>>>(a, hin, hout, second)));
+           (k_enth_jacobi<<<grid_tiles(a.G), kBlock, 0, st>>>(a, hin, hout, second)));
 }
 
 void launch_eos_coef(const StepArgs &a, const Level &L0, cudaStream_t st, Tracer *tr)

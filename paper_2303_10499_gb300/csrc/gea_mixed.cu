@@ -44,16 +44,19 @@ __global__ void k_mx_mom(StepArgs a, MixedArgs m, const float *ui, const float *
 {
     if (a.sc->status) return;
     if (second && a.sc->done[LOOP_MOM]) {
-        ph_copy(a.G, ui, uo, blockIdx.x, blockIdx.y);
-        ph_copy(a.G, wi, wo, blockIdx.x, blockIdx.y);
+        block_tiles(a.G, [&](int bx, int bz) {
+            ph_copy(a.G, ui, uo, bx, bz);
+            ph_copy(a.G, wi, wo, bx, bz);
+        });
         return;
     }
     __shared__ double sm[kT2];
     __shared__ double red[2 * NTHREADS];
     float acc[2] = {0.0f, 0.0f};
     double tot[2];
-    ph_sweep2<float, BC_U, BC_W>(a.G, a.F, m.T, m.dinvu, m.r0u, m.r0w, ui, wi, uo, wo, sm, blockIdx.x,
-                                 blockIdx.y, acc);
+    block_tiles(a.G, [&](int bx, int bz) {
+        ph_sweep2<float, BC_U, BC_W>(a.G, a.F, m.T, m.dinvu, m.r0u, m.r0w, ui, wi, uo, wo, sm, bx, bz, acc);
+    });
     if (grid_sum<2, float>(acc, red, a.partials, &a.sc->counters[CNT_MOM], tot)) fin_mom(a.sc, tot, m.tol2);
 }
 
@@ -71,15 +74,17 @@ __global__ void k_mx_enth(StepArgs a, MixedArgs m, const float *hi, float *ho, i
 {
     if (a.sc->status) return;
     if (second && a.sc->done[LOOP_ENTH]) {
-        ph_copy(a.G, hi, ho, blockIdx.x, blockIdx.y);
+        block_tiles(a.G, [&](int bx, int bz) { ph_copy(a.G, hi, ho, bx, bz); });
         return;
     }
     __shared__ double sm[kT2];
     __shared__ double red[NTHREADS];
     float acc[1] = {0.0f};
     double tot[1];
-    ph_sweep1<float, BC_EVEN>(a.G, a.F, m.T, m.dinvh, m.r0h, (float)(a.F.mu - a.F.nuh), hi, ho, sm,
-                              blockIdx.x, blockIdx.y, acc);
+    block_tiles(a.G, [&](int bx, int bz) {
+        ph_sweep1<float, BC_EVEN>(a.G, a.F, m.T, m.dinvh, m.r0h, (float)(a.F.mu - a.F.nuh), hi, ho, sm, bx, bz,
+                                  acc);
+    });
     if (grid_sum<1, float>(acc, red, a.partials, &a.sc->counters[CNT_ENTH], tot)) fin_enth(a.sc, tot, m.tol2);
 }
 
@@ -249,7 +254,7 @@ void launch_mx_mom(const StepArgs &a, const MixedArgs &m, const float *ui, const
                    float *wo, int second, cudaStream_t st, Tracer *tr)
 {
     TRACED(tr, "mx_mom", ncell(a.G),
-           (k_mx_mom<<<grid_of(a.G), kBlock, 0, st>>>(a, m, ui, wi, uo, wo, second)));
+           (k_mx_mom<<<grid_tiles(a.G), kBlock, 0, st>>>(a, m, ui, wi, uo, wo, second)));
 }
 
 void launch_mx_enth_rhs(const StepArgs &a, const MixedArgs &m, cudaStream_t st, Tracer *tr)
@@ -260,7 +265,7 @@ void launch_mx_enth_rhs(const StepArgs &a, const MixedArgs &m, cudaStream_t st, 
 void launch_mx_enth(const StepArgs &a, const MixedArgs &m, const float *hi, float *ho, int second,
                     cudaStream_t st, Tracer *tr)
 {
-    TRACED(tr, "mx_enth", ncell(a.G), (k_mx_enth<<<grid_of(a.G), kBlock, 0, st>>>(a, m, hi, ho, second)));
+    TRACED(tr, "mx_enth", ncell(a.G), (k_mx_enth<<<grid_tiles(a.G), kBlock, 0, st>>>(a, m, hi, ho, second)));
 }
 
 void launch_mx_eos(const StepArgs &a, const Level &L0, const LevelF &L32, const float *dh, cudaStream_t st,
