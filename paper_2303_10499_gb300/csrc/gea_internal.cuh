@@ -274,6 +274,15 @@ __device__ bool grid_sum(const T (&v)[NV], double *red, double *partials, unsign
         for (int b = tid; b < gn; b += NTHREADS) s[j] += __ldcg(&p1[(size_t)j * nb + g0 + b]);
     }
     block_sum<NV>(s, red, gt);
+    if (ng == 1) {
+        // one group: its sum is the total
+        if (tid == 0) {
+            gcnt[0] = 0u;
+#pragma unroll
+            for (int j = 0; j < NV; ++j) tot[j] = gt[j];
+        }
+        return tid == 0;
+    }
     if (tid == 0) {
         gcnt[grp] = 0u;
 #pragma unroll
@@ -295,13 +304,18 @@ __device__ bool grid_sum(const T (&v)[NV], double *red, double *partials, unsign
 }
 
 // The light per-phase kernels with a grid reduction (the CG and V-cycle
-// steps) run kTilesPerBlock tiles of a tile column per block: a quarter of
-// the blocks, so a quarter of the block reductions and arrivals.
+// steps, the Jacobi sweeps) run kTilesPerBlock tiles of a tile column per
+// block on grids of at least kMultiTileMin tiles: a quarter of the blocks,
+// so a quarter of the block reductions and arrivals. Smaller grids keep one
+// tile per block (fewer blocks would leave SMs idle). The kernels read the
+// count back from the launch shape.
 constexpr int kTilesPerBlock = 4;
+constexpr int kMultiTileMin = 16384;
 inline dim3 grid_tiles(const Geom &G)
 {
-    const int tz = (G.nz + BZ - 1) / BZ;
-    return dim3((G.nx + BX - 1) / BX, (tz + kTilesPerBlock - 1) / kTilesPerBlock);
+    const int tx = (G.nx + BX - 1) / BX, tz = (G.nz + BZ - 1) / BZ;
+    const int tpb = (long long)tx * tz >= kMultiTileMin ? kTilesPerBlock : 1;
+    return dim3(tx, (tz + tpb - 1) / tpb);
 }
 // f(bx, bz) for the block's tiles (block-uniform loop; each f ends with a
 // block barrier).
@@ -309,8 +323,9 @@ template <class F>
 __device__ __forceinline__ void block_tiles(const Geom &G, F f)
 {
     const int tz = (G.nz + BZ - 1) / BZ;
-    for (int t = 0; t < kTilesPerBlock; ++t) {
-        const int bz = blockIdx.y * kTilesPerBlock + t;
+    const int tpb = (tz + gridDim.y - 1) / gridDim.y;
+    for (int t = 0; t < tpb; ++t) {
+        const int bz = blockIdx.y * tpb + t;
         if (bz >= tz) break;
         f((int)blockIdx.x, bz);
     }
