@@ -169,8 +169,12 @@ int gea_set_stream(gea_ctx *ctx, void *stream);
 /* Load a state. CONSERVATIVE derives the rest on the device: u = (rho u)/rho,
  * T = (e - K - g z)/cv, p = rho R T (eq. p), h = cp T (eq. K_h),
  * p' = p + rho g z, p^{n-1} = p, and phi on interior faces the average of the
- * two cells' normal momentum times the face area (Section 3).
- * Errors: GEA_ERR_INVAL (null pointers, rho <= 0 or T <= 0 anywhere). */
+ * two cells' normal momentum times the face area (Section 3), and checks
+ * rho and T (one synchronisation). FULL copies the fields as given (no
+ * check; enqueued on the stream without waiting; host buffers must stay
+ * unchanged until the stream reaches the copies).
+ * Errors: GEA_ERR_INVAL (null pointers; CONSERVATIVE: rho <= 0 or T <= 0
+ * anywhere). */
 int gea_set_state(gea_ctx *ctx, const gea_state_view *v);
 
 /* Advance n >= 0 steps (Section 3, Steps 1-3). Returns after the launches

@@ -685,6 +685,14 @@ int gea_set_state(gea_ctx *ctx, const gea_state_view *v)
     } else {
         return fail(ctx, GEA_ERR_INVAL, "unknown state kind %d", v->kind);
     }
+    if (v->kind == GEA_STATE_FULL) {
+        // a full state is taken as given (only the derivation from the
+        // conservative fields checks rho and T): no round trip to the device
+        ctx->base = 0;
+        ctx->steps_at_sync = 0;
+        ctx->have_state = true;
+        return GEA_OK;
+    }
     Scal h;
     int rc = read_scal(ctx, &h);
     if (rc) return rc;
