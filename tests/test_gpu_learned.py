@@ -1,9 +1,11 @@
-"""The learned initial guess inside the pressure solve (gea_attach_net).
+"""The learned network inside the pressure solve (gea_attach_net): as the
+initial guess and as a flexible-CG preconditioner stage.
 
 The guess only changes where each solve starts: x + alpha e with the A-norm
 optimal alpha, then the same solve to the same tolerance. So with any
 network, trained or not, the FP64 step still matches the oracle at the
-parity bound, and the mixed step stays within its bounds.
+parity bound, and the mixed step stays within its bounds. The stage only
+shapes the search directions of a solve that runs to the same tolerance.
 """
 import numpy as np
 import pytest
@@ -118,25 +120,35 @@ def test_trained_guess_saves_iterations_at_4096(env):
     assert sum(its[True]) < sum(its[False])
 
 
-def test_network_preconditioner_keeps_parity(env, oracle_mod):
-    """Flexible CG with the network as the preconditioner in place of the
-    V-cycle (mode 2): the network, trained briefly on the same bubble's own
-    pressure systems, only shapes the search directions, and each solve still
-    runs to the same tolerance, so the FP64 step matches the oracle at the
-    parity bound."""
+@pytest.fixture(scope="module")
+def small_net(env):
+    """A network trained briefly on the 160 x 80 bubble's own pressure
+    systems."""
     torch, G, learned = env
     wl = W.get("bubble160x80")
     samples = learned.collect(wl, 6, every=1)
     net = G.Net(4, 80, 160, relu=False)
     net.set_params(learned.initial_params(2) * 0.5)
     learned.train(net, samples, 150, n=4, h=80, w=160, lr=2e-3)
+    return net
+
+
+@pytest.mark.parametrize("mode", [2, 3], ids=["stage", "guess+stage"])
+def test_network_preconditioner_keeps_parity(env, oracle_mod, small_net, mode):
+    """Flexible CG with the two-stage preconditioner (the network, then a
+    V-cycle on the residual its step leaves; mode 2, and with the learned
+    initial guess as well, mode 3): the network only shapes the search
+    directions, and each solve still runs to the same tolerance, so the FP64
+    step matches the oracle at the parity bound."""
+    torch, G, learned = env
+    wl = W.get("bubble160x80")
     steps = 20
     o = oracle_mod.Oracle(wl.grid, wl.const)
     so = o.derive(wl.fields)
     o.step(so, steps)
     s = G.Solver(wl.grid, wl.const)
     s.set_conservative(wl.fields)
-    s.attach_net(net, 2)
+    s.attach_net(small_net, mode)
     its = []
     for _ in range(steps):
         s.step(1)
@@ -151,7 +163,7 @@ def test_network_preconditioner_keeps_parity(env, oracle_mod):
     vel = np.hypot(np.linalg.norm(so["u"]), np.linalg.norm(so["w"]))
     for k in ("u", "w"):
         assert np.linalg.norm(g[k] - so[k]) / vel < 1e-10, k
-    print(its)
+    print(mode, its)
 
 
 def test_network_preconditioner_is_fp64_only(env):
@@ -163,3 +175,6 @@ def test_network_preconditioner_is_fp64_only(env):
         s.attach_net(net, 2)
     assert ei.value.code == G.GEA_ERR_INVAL
     s.attach_net(net, 1)          # the guess is fine for the mixed step
+    with pytest.raises(G.GeaError) as ei:
+        s.attach_net(net, 4)      # modes are 0..3
+    assert ei.value.code == G.GEA_ERR_INVAL
