@@ -238,6 +238,16 @@ enum {
  * 8 within the network's size. Errors: GEA_ERR_INVAL, GEA_ERR_CUDA. */
 struct gea_net;
 int gea_attach_net(gea_ctx *ctx, struct gea_net *net, int32_t mode);
+
+/* Tile column of the per-phase kernels with a grid reduction (the CG and
+ * V-cycle steps and the Jacobi sweeps of the graph driver): each block walks
+ * n tiles (32 x 8 cells each) of a column, so a launch has 1/n of the blocks
+ * and of the block reductions. n = 0 (the default): 4 on grids of at least
+ * 16384 tiles, else 1. The persistent kernels ignore it. The results depend
+ * on n only through the order of the reduction sums. Synchronises the
+ * stream; the step graphs are recorded anew. Errors: GEA_ERR_INVAL (n
+ * outside 0..16). */
+int gea_set_tiles_per_block(gea_ctx *ctx, int32_t n);
 int gea_get_field(gea_ctx *ctx, int32_t which, double *host);
 
 /* Event-timed duration (ms) of the pressure solves (all correctors) of the

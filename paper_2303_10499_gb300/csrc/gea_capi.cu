@@ -47,6 +47,7 @@ struct gea_ctx {
     gea_net *net = nullptr;               // attached learned network (not owned)
     int net_mode = 0;                     // 1: initial guess; 2: flexible-CG preconditioner; 3: both
     double *net_s = nullptr;              // mode 2: the residual the network leaves (V-cycle input)
+    int tiles_per_block = 0;              // per-phase reduction kernels (0: the size rule)
     float *net_r = nullptr, *net_e = nullptr;   // its dense input and output
     Scal *sc = nullptr;
     double *partials = nullptr;
@@ -120,6 +121,7 @@ StepArgs step_args(gea_ctx *c, int from)
     a.partials = c->partials;
     a.jac_rtol2 = c->C.jac_rtol * c->C.jac_rtol;
     a.cg_rtol2 = c->C.cg_rtol * c->C.cg_rtol;
+    a.tiles_per_block = c->tiles_per_block;
     return a;
 }
 
@@ -923,6 +925,21 @@ int gea_profile_step(gea_ctx *ctx, gea_kernel_time *out, int32_t max_entries, in
     for (size_t j = 0; j < agg.size() && (int32_t)j < max_entries; ++j) out[j] = agg[j];
     ctx->steps_at_sync += 1;
     return gea_sync(ctx);
+}
+
+int gea_set_tiles_per_block(gea_ctx *ctx, int32_t n)
+{
+    if (!ctx || n < 0 || n > kMaxTilesPerBlock) return GEA_ERR_INVAL;
+    if (ctx->stream) CK(cudaStreamSynchronize(ctx->stream));
+    // the step graphs hold the launch shapes
+    for (int f = 0; f < 2; ++f) {
+        if (ctx->exec[f]) cudaGraphExecDestroy(ctx->exec[f]);
+        if (ctx->graph[f]) cudaGraphDestroy(ctx->graph[f]);
+        ctx->exec[f] = nullptr;
+        ctx->graph[f] = nullptr;
+    }
+    ctx->tiles_per_block = n;
+    return GEA_OK;
 }
 
 int gea_attach_net(gea_ctx *ctx, gea_net *net, int32_t mode)

@@ -159,6 +159,7 @@ struct StepArgs {
     Scal *sc;
     double *partials;
     double jac_rtol2, cg_rtol2;
+    int tiles_per_block;   // per-phase kernels with a reduction: tiles a block walks (0: the size rule)
 };
 
 __device__ __forceinline__ int cidx(const Geom &G, int i, int k) { return k * G.P + i; }
@@ -304,17 +305,19 @@ __device__ bool grid_sum(const T (&v)[NV], double *red, double *partials, unsign
 }
 
 // The light per-phase kernels with a grid reduction (the CG and V-cycle
-// steps, the Jacobi sweeps) run kTilesPerBlock tiles of a tile column per
-// block on grids of at least kMultiTileMin tiles: a quarter of the blocks,
-// so a quarter of the block reductions and arrivals. Smaller grids keep one
-// tile per block (fewer blocks would leave SMs idle). The kernels read the
-// count back from the launch shape.
+// steps, the Jacobi sweeps) walk the tiles of a column of tpb tiles per
+// block: fewer blocks, so fewer block reductions and arrivals. By the size
+// rule (tpb = 0) grids of at least kMultiTileMin tiles take kTilesPerBlock
+// and smaller grids one tile per block (fewer blocks would leave SMs idle);
+// gea_set_tiles_per_block fixes tpb (the tile-column autotuner times the
+// candidates). The kernels read the count back from the launch shape.
 constexpr int kTilesPerBlock = 4;
 constexpr int kMultiTileMin = 16384;
-inline dim3 grid_tiles(const Geom &G)
+constexpr int kMaxTilesPerBlock = 16;
+inline dim3 grid_tiles(const Geom &G, int tpb)
 {
     const int tx = (G.nx + BX - 1) / BX, tz = (G.nz + BZ - 1) / BZ;
-    const int tpb = (long long)tx * tz >= kMultiTileMin ? kTilesPerBlock : 1;
+    if (tpb <= 0) tpb = (long long)tx * tz >= kMultiTileMin ? kTilesPerBlock : 1;
     return dim3(tx, (tz + tpb - 1) / tpb);
 }
 // f(bx, bz) for the block's tiles (block-uniform loop; each f ends with a

@@ -355,7 +355,7 @@ void launch_mom_jacobi(const StepArgs &a, const double *uin, const double *win, 
                        double *wout, int second, cudaStream_t st, Tracer *tr)
 {
     TRACED(tr, "mom_jacobi", ncell(a.G),
-           (k_mom_jacobi<<<grid_tiles(a.G), kBlock, 0, st>>>(a, uin, win, uout, wout, second)));
+           (k_mom_jacobi<<<grid_tiles(a.G, a.tiles_per_block), kBlock, 0, st>>>(a, uin, win, uout, wout, second)));
 }
 
 void launch_enth_rhs(const StepArgs &a, cudaStream_t st, Tracer *tr)
@@ -367,7 +367,7 @@ void launch_enth_jacobi(const StepArgs &a, const double *hin, double *hout, int 
                         cudaStream_t st, Tracer *tr)
 {
     TRACED(tr, "enth_jacobi", ncell(a.G),
-           (k_enth_jacobi<<<grid_tiles(a.G), kBlock, 0, st>>>(a, hin, hout, second)));
+           (k_enth_jacobi<<<grid_tiles(a.G, a.tiles_per_block), kBlock, 0, st>>>(a, hin, hout, second)));
 }
 
 void launch_eos_coef(const StepArgs &a, const Level &L0, cudaStream_t st, Tracer *tr)
@@ -398,7 +398,7 @@ int launch_vcycle(const StepArgs &a, Level *L, int nlev, int ncoarse, cudaStream
 {
     if (nlev == 1) {
         TRACED(tr, "mg_single", ncell(L[0].G),
-               (k_mg_single<<<grid_tiles(L[0].G), kBlock, 0, st>>>(L[0], L[0].e2, a)));
+               (k_mg_single<<<grid_tiles(L[0].G, a.tiles_per_block), kBlock, 0, st>>>(L[0], L[0].e2, a)));
         return 1;
     }
     int n = 0;
@@ -415,7 +415,7 @@ int launch_vcycle(const StepArgs &a, Level *L, int nlev, int ncoarse, cudaStream
     }
     for (int l = nlev - 2; l >= 0; --l, ++n)
         TRACED(tr, "mg_up", ncell(L[l].G),
-               (k_mg_up<<<grid_tiles(L[l].G), kBlock, 0, st>>>(L[l], L[l + 1].e2, L[l + 1].G.P, L[l].e2,
+               (k_mg_up<<<grid_tiles(L[l].G, a.tiles_per_block), kBlock, 0, st>>>(L[l], L[l + 1].e2, L[l + 1].G.P, L[l].e2,
                                                              l == 0, a)));
     return n;
 }
@@ -439,7 +439,7 @@ static int launch_vcycle_rest(const StepArgs &a, Level *L, int nlev, int ncoarse
     }
     for (int l = nlev - 2; l >= 0; --l, ++n)
         TRACED(tr, "mg_up", ncell(L[l].G),
-               (k_mg_up<<<grid_tiles(L[l].G), kBlock, 0, st>>>(L[l], L[l + 1].e2, L[l + 1].G.P, L[l].e2,
+               (k_mg_up<<<grid_tiles(L[l].G, a.tiles_per_block), kBlock, 0, st>>>(L[l], L[l + 1].e2, L[l + 1].G.P, L[l].e2,
                                                              l == 0, a)));
     return n;
 }
@@ -450,14 +450,14 @@ static int launch_vcycle_rest(const StepArgs &a, Level *L, int nlev, int ncoarse
 int launch_cg_iter(const StepArgs &a, Level *L, int nlev, int ncoarse, double *x, cudaStream_t st,
                    Tracer *tr)
 {
-    TRACED(tr, "cg_pspmv", ncell(a.G), (k_cg_pspmv<<<grid_tiles(a.G), kBlock, 0, st>>>(a, L[0])));
+    TRACED(tr, "cg_pspmv", ncell(a.G), (k_cg_pspmv<<<grid_tiles(a.G, a.tiles_per_block), kBlock, 0, st>>>(a, L[0])));
     if (nlev == 1) {
         TRACED(tr, "cg_update_single", ncell(a.G),
-               (k_cg_update_single<<<grid_tiles(a.G), kBlock, 0, st>>>(a, L[0], x)));
+               (k_cg_update_single<<<grid_tiles(a.G, a.tiles_per_block), kBlock, 0, st>>>(a, L[0], x)));
         return 2;
     }
     TRACED(tr, "cg_update_down", ncell(a.G),
-           (k_cg_update_down<<<grid_tiles(a.G), kBlock, 0, st>>>(a, L[0], L[1], x)));
+           (k_cg_update_down<<<grid_tiles(a.G, a.tiles_per_block), kBlock, 0, st>>>(a, L[0], L[1], x)));
     return 2 + launch_vcycle_rest(a, L, nlev, ncoarse, st, tr);
 }
 

@@ -238,7 +238,7 @@ int vcycle32(const StepArgs &a, LevelF *L, int nlev, int ncoarse, int lfirst, cu
     }
     for (int l = nlev - 2; l >= 0; --l, ++n)
         TRACED(tr, "mx_mg_up", ncell(L[l].G),
-               (k_mx_mg_up<<<grid_tiles(L[l].G), kBlock, 0, st>>>(L[l], L[l + 1].e2, L[l + 1].G.P, L[l].e2,
+               (k_mx_mg_up<<<grid_tiles(L[l].G, a.tiles_per_block), kBlock, 0, st>>>(L[l], L[l + 1].e2, L[l + 1].G.P, L[l].e2,
                                                                 l == 0, a)));
     return n;
 }
@@ -254,7 +254,7 @@ void launch_mx_mom(const StepArgs &a, const MixedArgs &m, const float *ui, const
                    float *wo, int second, cudaStream_t st, Tracer *tr)
 {
     TRACED(tr, "mx_mom", ncell(a.G),
-           (k_mx_mom<<<grid_tiles(a.G), kBlock, 0, st>>>(a, m, ui, wi, uo, wo, second)));
+           (k_mx_mom<<<grid_tiles(a.G, a.tiles_per_block), kBlock, 0, st>>>(a, m, ui, wi, uo, wo, second)));
 }
 
 void launch_mx_enth_rhs(const StepArgs &a, const MixedArgs &m, cudaStream_t st, Tracer *tr)
@@ -265,7 +265,7 @@ void launch_mx_enth_rhs(const StepArgs &a, const MixedArgs &m, cudaStream_t st, 
 void launch_mx_enth(const StepArgs &a, const MixedArgs &m, const float *hi, float *ho, int second,
                     cudaStream_t st, Tracer *tr)
 {
-    TRACED(tr, "mx_enth", ncell(a.G), (k_mx_enth<<<grid_tiles(a.G), kBlock, 0, st>>>(a, m, hi, ho, second)));
+    TRACED(tr, "mx_enth", ncell(a.G), (k_mx_enth<<<grid_tiles(a.G, a.tiles_per_block), kBlock, 0, st>>>(a, m, hi, ho, second)));
 }
 
 void launch_mx_eos(const StepArgs &a, const Level &L0, const LevelF &L32, const float *dh, cudaStream_t st,
@@ -291,7 +291,7 @@ int launch_mx_vcycle(const StepArgs &a, LevelF *L, int nlev, int ncoarse, cudaSt
 {
     if (nlev == 1) {
         TRACED(tr, "mx_mg_single", ncell(L[0].G),
-               (k_mx_mg_single<<<grid_tiles(L[0].G), kBlock, 0, st>>>(L[0], L[0].e2, a)));
+               (k_mx_mg_single<<<grid_tiles(L[0].G, a.tiles_per_block), kBlock, 0, st>>>(L[0], L[0].e2, a)));
         return 1;
     }
     return vcycle32(a, L, nlev, ncoarse, 0, st, tr);
@@ -301,14 +301,14 @@ int launch_mx_vcycle(const StepArgs &a, LevelF *L, int nlev, int ncoarse, cudaSt
 int launch_mx_cg_iter(const StepArgs &a, const MixedArgs &m, LevelF *L, int nlev, int ncoarse,
                       cudaStream_t st, Tracer *tr)
 {
-    TRACED(tr, "mx_pspmv", ncell(a.G), (k_mx_pspmv<<<grid_tiles(a.G), kBlock, 0, st>>>(a, L[0], m)));
+    TRACED(tr, "mx_pspmv", ncell(a.G), (k_mx_pspmv<<<grid_tiles(a.G, a.tiles_per_block), kBlock, 0, st>>>(a, L[0], m)));
     if (nlev == 1) {
         TRACED(tr, "mx_update_single", ncell(a.G),
-               (k_mx_update_single<<<grid_tiles(a.G), kBlock, 0, st>>>(a, L[0], m)));
+               (k_mx_update_single<<<grid_tiles(a.G, a.tiles_per_block), kBlock, 0, st>>>(a, L[0], m)));
         return 2;
     }
     TRACED(tr, "mx_update_down", ncell(a.G),
-           (k_mx_update_down<<<grid_tiles(a.G), kBlock, 0, st>>>(a, L[0], L[1], m)));
+           (k_mx_update_down<<<grid_tiles(a.G, a.tiles_per_block), kBlock, 0, st>>>(a, L[0], L[1], m)));
     return 2 + vcycle32(a, L, nlev, ncoarse, 1, st, tr);
 }
 

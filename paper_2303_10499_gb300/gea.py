@@ -101,6 +101,7 @@ def library() -> C.CDLL:
         I = C.c_int32
         lib.gea_conv3x3.argtypes = [I, I, I, I, I, I, I, P, P, P, P, P, P, P]
         lib.gea_attach_net.argtypes = [P, P, I]
+        lib.gea_set_tiles_per_block.argtypes = [P, I]
         lib.gea_ensemble_create.argtypes = [C.POINTER(P), I, P, C.POINTER(P)]
         lib.gea_ensemble_set_stream.argtypes = [P, P]
         lib.gea_ensemble_blocks.argtypes = [P, I]
@@ -283,6 +284,29 @@ class Solver:
         (net None) detaches it."""
         self._check(self.lib.gea_attach_net(self.h, net.h if net is not None else None, mode))
         self._net = net if mode else None   # keep it alive while attached
+
+    def set_tiles_per_block(self, n: int):
+        """Tiles a block walks in the per-phase kernels with a grid reduction
+        (gea_set_tiles_per_block; 0: the size rule)."""
+        self._check(self.lib.gea_set_tiles_per_block(self.h, int(n)))
+
+    def tune_tiles(self, candidates=(1, 2, 4, 8), steps: int = 3) -> Dict:
+        """Tile-column autotuner of the graph driver's per-phase kernels: for
+        each candidate number of tiles a block walks, one untimed step (which
+        records the step graph) and `steps` timed steps (gea_step
+        synchronises, so host time brackets the device work); keeps the
+        fastest. The state advances by len(candidates) x (steps + 1) steps."""
+        import time
+        times = {}
+        for n in candidates:
+            self.set_tiles_per_block(n)
+            self.step(1)
+            t0 = time.perf_counter()
+            self.step(steps)
+            times[int(n)] = (time.perf_counter() - t0) / steps * 1e3
+        best = min(times, key=times.get)
+        self.set_tiles_per_block(best)
+        return {"ms_per_step": times, "tiles_per_block": best}
 
     def profile_step(self) -> Dict[str, Dict]:
         """Advance one step with every kernel launch timed by CUDA events on
