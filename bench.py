@@ -83,6 +83,9 @@ def parse():
     ap.add_argument("--graph", action="store_true",
                     help="always step through the CUDA graph of per-phase kernels (default: the "
                          "library picks the persistent kernel on small grids)")
+    ap.add_argument("--tune-tiles", action="store_true",
+                    help="graph driver: run the tile-column autotuner (tiles a block walks in the "
+                         "per-phase reduction kernels) before timing, from the same initial state")
     ap.add_argument("--mixed", action="store_true",
                     help="time the mixed-precision step (FP32 inner solves) on the main line; by "
                          "default it is timed beside the FP64 step under 'mixed_precision'")
@@ -688,6 +691,10 @@ def run_ours(args):
     s = gea.Solver(wl.grid, wl.const, stream=stream, graph=args.graph, mixed=args.mixed)
     dev = {k: torch.from_numpy(v).cuda() for k, v in wl.fields.items()}
     s.set_conservative(dev)
+    tuned = None
+    if args.tune_tiles and s.stats()["driver"] != "persistent":
+        tuned = s.tune_tiles()
+        s.set_conservative(dev)   # time from the initial state again
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     ms, launches, clocks = timed_steps(s, stream, flush, args.steps, args.warmup, world, local)
     st = s.stats()
@@ -729,6 +736,7 @@ def run_ours(args):
                    "cg_rtol": wl.const.cg_rtol, "mg_levels": st["mg_levels"],
                    "l2": "flushed between timed steps (256 MB write, untimed)",
                    "driver": st["driver"],
+                   "tiles_per_block": tuned if tuned else "size rule (4 on grids of >= 16384 tiles, else 1)",
                    "parallelism": f"replicas x{world}"},
         "pressure_solve_ms_per_step": pms,
         "cg_iters_last_step": st["cg_iters"], "jacobi_sweeps_last_step": [st["jac_u"], st["jac_h"]],
