@@ -2066,11 +2066,16 @@ int gea3d_get_state(gea3d_ctx *ctx, double *rho, double *u, double *v, double *w
     const double *src[7] = {S.rho, S.u, S.v, S.w, S.T, S.p, S.pp};
     for (int f = 0; f < 7; ++f) {
         if (!dst[f]) continue;
-        // (k (ny+1) + j) P + i -> (k ny + j) nx + i: one 2D copy per layer
-        for (int k = 0; k < G.nz; ++k)
-            CK3(cudaMemcpy2DAsync(dst[f] + (size_t)k * G.ny * G.nx, (size_t)G.nx * sizeof(double),
-                                  src[f] + (size_t)k * (G.ny + 1) * G.P, (size_t)G.P * sizeof(double),
-                                  (size_t)G.nx * sizeof(double), G.ny, cudaMemcpyDefault, ctx->stream));
+        // (k (ny+1) + j) P + i -> (k ny + j) nx + i: one 3D copy per field (rows
+        // of nx values, ny rows a layer out of the source's ny + 1, nz layers)
+        cudaMemcpy3DParms c = {};
+        c.srcPtr = make_cudaPitchedPtr(const_cast<double *>(src[f]), (size_t)G.P * sizeof(double),
+                                       (size_t)G.nx * sizeof(double), (size_t)G.ny + 1);
+        c.dstPtr = make_cudaPitchedPtr(dst[f], (size_t)G.nx * sizeof(double), (size_t)G.nx * sizeof(double),
+                                       (size_t)G.ny);
+        c.extent = make_cudaExtent((size_t)G.nx * sizeof(double), (size_t)G.ny, (size_t)G.nz);
+        c.kind = cudaMemcpyDefault;
+        CK3(cudaMemcpy3DAsync(&c, ctx->stream));
     }
     CK3(cudaStreamSynchronize(ctx->stream));
     return GEA_OK;
