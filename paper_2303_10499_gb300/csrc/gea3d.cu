@@ -588,7 +588,9 @@ __global__ void k_enth_rhs(Args a, const double *w1)
     }
 }
 
-__global__ void k_enth(Args a, const double *hi, double *ho, int second)
+// One Jacobi sweep of h (pairs as for momentum); five blocks per SM (48
+// registers) measured 8 % faster than four.
+__global__ void __launch_bounds__(NT, 5) k_enth(Args a, const double *hi, double *ho, int second)
 {
     Sc *sc = a.sc;
     if (sc->status) return;
