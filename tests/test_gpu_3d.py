@@ -250,3 +250,26 @@ def test_deterministic_and_multi_step_equals_single_steps(gea):
     for k in FIELDS:
         assert np.array_equal(out[0][k], out[1][k]), k
         assert np.array_equal(out[0][k], out[2][k]), k
+
+
+def test_full_size_les_bubble_properties(gea):
+    """The bench's 3D workload at its full size (512 x 512 x 256, 67 M cells,
+    Smagorinsky LES, two multigrid levels), where no oracle can follow: two
+    steps through the graph driver keep mass to round-off and the centred
+    bubble's mirror symmetries in x and y and its x <-> y symmetry."""
+    wl = W.get("bubble3d_512x512x256")
+    s = gea.Solver3D(wl.grid, wl.const)
+    s.set_conservative(wl.fields)
+    s.step(2)
+    st = s.stats()
+    assert st["status"] == 0 and st["mg_levels"] == 2, st
+    f = s.get_state()
+    s.close()
+    w, u, v = f["w"], f["u"], f["v"]
+    sc = np.abs(w).max()
+    assert sc > 1e-6
+    assert np.abs(w - w[:, :, ::-1]).max() < 1e-8 * sc and np.abs(w - w[:, ::-1, :]).max() < 1e-8 * sc
+    assert np.abs(u + u[:, :, ::-1]).max() < 1e-8 * sc and np.abs(v + v[:, ::-1, :]).max() < 1e-8 * sc
+    assert np.abs(u - v.transpose(0, 2, 1)).max() < 1e-8 * sc
+    m0 = wl.fields["rho"].sum()
+    assert abs(f["rho"].sum() - m0) < 1e-12 * m0
