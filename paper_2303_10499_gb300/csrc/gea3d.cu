@@ -378,19 +378,22 @@ __global__ void k_pred(Args a)
         double mw, me, ms, mn, mb, mt;
         if (F.les_d2 > 0.0) {
             const double mc = ld(&a.mueff[q]);
-            auto face = [&](int ii, int jj, int kk) { return 0.5 * (mc + at<E3>(G, F, a.mueff, ii, jj, kk)); };
-            mw = face(i - 1, j, k) * G.idx2; me = face(i + 1, j, k) * G.idx2;
-            ms = face(i, j - 1, k) * G.idy2; mn = face(i, j + 1, k) * G.idy2;
-            mb = face(i, j, k - 1) * G.idz2; mt = face(i, j, k + 1) * G.idz2;
+            // (mu_c + mu_N)/2 / Delta^2, the halves folded into the factors
+            const double hx = 0.5 * G.idx2, hy = 0.5 * G.idy2, hz = 0.5 * G.idz2;
+            auto face = [&](int ii, int jj, int kk, double h) { return (mc + at<E3>(G, F, a.mueff, ii, jj, kk)) * h; };
+            mw = face(i - 1, j, k, hx); me = face(i + 1, j, k, hx);
+            ms = face(i, j - 1, k, hy); mn = face(i, j + 1, k, hy);
+            mb = face(i, j, k - 1, hz); mt = face(i, j, k + 1, hz);
         } else {
             mw = me = F.mu * G.idx2;
             ms = mn = F.mu * G.idy2;
             mb = mt = F.mu * G.idz2;
         }
         const double cu = rho1 * F.idt + (7.0 / 12.0) * dv + ((mw + me) + (ms + mn) + (mb + mt));
-        a.dinvu[q] = 1.0 / cu;
+        const double icu = 1.0 / cu;
+        a.dinvu[q] = icu;
         // the enthalpy diagonal: the diffusion scaled by 1/Pr (LES requires Pr = 1)
-        a.dinvh[q] = F.les_d2 > 0.0 ? 1.0 / cu
+        a.dinvh[q] = F.les_d2 > 0.0 ? icu
                                     : 1.0 / (rho1 * F.idt + (7.0 / 12.0) * dv +
                                              F.nuh * 2.0 * (G.idx2 + G.idy2 + G.idz2));
         // T as a stencil: the outgoing flux of a face times its fourth-order
