@@ -80,6 +80,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="bubble640x320")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-w3", action="store_true",
+                    help="skip the nested 4096 x 2048 FP64 record (w3) of the default line")
     ap.add_argument("--graph", action="store_true",
                     help="always step through the CUDA graph of per-phase kernels (default: the "
                          "library picks the persistent kernel on small grids)")
@@ -105,16 +107,29 @@ def parse():
     return ap.parse_args()
 
 
-def peaks():
-    # FP64 and FP32 issue rates are nominal (the measured peaks file has
-    # neither): 152 SMs x (2 FP64 | 128 FP32) FMA lanes x 2 flops x 2.07 GHz
-    p = {"hbm_gbs": 6800.0, "fp64_tflops": 1.25, "fp32_tflops": 80.5, "src": "fallback"}
+def peaks(measure=False):
+    """Roofline denominators. HBM: the measured copy bandwidth of the peaks
+    file. FP64 and FP32: with measure=True the FMA-chain probe of the library
+    (gea_probe_fma) on this GPU, in this run; otherwise the nominal rates,
+    152 SMs x (2 FP64 | 128 FP32) FMA lanes x 2 flops x 2.07 GHz."""
+    p = {"hbm_gbs": 6800.0, "fp64_tflops": 1.25, "fp32_tflops": 80.5, "src": "fallback",
+         "fp64_src": "nominal", "fp32_src": "nominal"}
     try:
         m = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
         p["hbm_gbs"] = float(m["hbm_gbs"])
         p["src"] = "measured"
     except Exception:
         pass
+    if measure:
+        from paper_2303_10499_gb300 import gea
+        f64 = gea.probe_fma(64, iters=16384)
+        f32 = gea.probe_fma(32, iters=16384 * 32)
+        p["fp64_tflops"], p["fp32_tflops"] = f64["tflops"], f32["tflops"]
+        p["fp64_src"] = (f"measured in this run: gea_probe_fma FP64, {f64['blocks']} x 256 threads x 8 "
+                         f"FMA chains x {f64['iters']} steps, best of 5 CUDA-event timed launches "
+                         f"({f64['ms']:.2f} ms)")
+        p["fp32_src"] = (f"measured in this run: gea_probe_fma FP32, {f32['blocks']} x 256 threads x 8 "
+                         f"FMA chains x {f32['iters']} steps ({f32['ms']:.2f} ms)")
     return p
 
 
@@ -266,13 +281,14 @@ def roofline(prof, pk, ms_per_step, persistent, workload):
     tfl = flops_l / t / 1e12
     alu = pk["fp64_tflops"] if prec == "f64" else pk["fp32_tflops"]
     if flops_l / (alu * 1e12) >= bytes_l / (pk["hbm_gbs"] * 1e9):
+        src = pk["fp64_src"] if prec == "f64" else pk["fp32_src"]
+        if src == "nominal":
+            src = ("FP64 nominal 1.25 TFLOP/s of GB300 (152 SMs x 2 FP64 FMA lanes x 2 flops x 2.07 GHz)"
+                   if prec == "f64" else
+                   "FP32 nominal 80.5 TFLOP/s (152 SMs x 128 FP32 lanes x 2 x 2.07 GHz)")
         out = {"bound": "alu", "achieved": tfl, "peak": alu, "unit": "TFLOP/s",
                "frac": tfl / alu,
-               "peak_source": ("FP64 nominal 1.25 TFLOP/s of GB300 (152 SMs x 2 FP64 FMA lanes x "
-                               "2 flops x ~2.06 GHz; 1.20 measured by an FMA-chain probe)"
-                               if prec == "f64" else
-                               "FP32 nominal 80.5 TFLOP/s (152 SMs x 128 FP32 lanes x 2 x 2.07 GHz)")
-                              + "; the measured peaks file has no entry for this precision"}
+               "peak_source": src + " (the measured peaks file has no entry for this precision)"}
     else:
         out = {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
                "frac": gbs / pk["hbm_gbs"], "peak_source": f"{pk['src']} hbm_gbs"}
@@ -316,6 +332,60 @@ def timed_steps(s, stream, flush, steps, warmup, world, local):
     s.sync()
     launches = s.stats()["launches"] - l0
     return [e0.elapsed_time(e1) for e0, e1 in evs], launches, clocks
+
+
+def whole_step(prof, pk, ms_per_step):
+    """The whole step against both ceilings: the model's FP64 operations and
+    algorithmic bytes of one step (per-phase model x cells of the eager
+    profiled step's launches) over the event-timed step."""
+    step_bytes, step_flops = step_model(prof)
+    t = ms_per_step * 1e-3
+    tfl, gbs = step_flops / t / 1e12, step_bytes / t / 1e9
+    t_alu = step_flops / (pk["fp64_tflops"] * 1e12)
+    t_hbm = step_bytes / (pk["hbm_gbs"] * 1e9)
+    return {"flops_per_step": step_flops, "bytes_per_step": step_bytes,
+            "fp64_tflops": tfl, "frac_fp64": tfl / pk["fp64_tflops"],
+            "hbm_gbs": gbs, "frac_hbm": gbs / pk["hbm_gbs"],
+            "bound": "alu" if t_alu >= t_hbm else "hbm",
+            "frac_binding": max(t_alu, t_hbm) / t,
+            "ms_at_binding_roofline": max(t_alu, t_hbm) * 1e3}
+
+
+def w3_record(gea, W, stream, flush, pk, local, steps=10, warmup=3):
+    """The 4096 x 2048 smooth bubble (larger than L2: the HBM/FP64-roofline
+    workload), FP64, CUDA-graph driver: pressure solves to 1e-8 of ||b|| (the
+    timing tolerance) and to the parity tolerance 1e-17, each timed like the
+    main line, with the whole step's roofline fractions and the dominant
+    kernel's."""
+    import copy
+    import torch
+    wl = W.get("bubble4096x2048")
+    dev = {k: torch.from_numpy(v).cuda() for k, v in wl.fields.items()}
+    out = {"workload": wl.name, "grid": [wl.grid.nx, wl.grid.nz], "cells": wl.grid.cells,
+           "dt": wl.const.dt, "driver": None, "runs": {}}
+    for rtol in (1e-8, wl.const.cg_rtol):
+        const = copy.copy(wl.const)
+        const.cg_rtol = rtol
+        s = gea.Solver(wl.grid, const, stream=stream)
+        s.set_conservative(dev)
+        ms, launches, clocks = timed_steps(s, stream, flush, steps, warmup, 1, local)
+        st = s.stats()
+        prof = s.profile_step()
+        mean = statistics.mean(ms)
+        out["driver"] = st["driver"]
+        out["mg_levels"] = st["mg_levels"]
+        out["runs"][f"{rtol:g}"] = {
+            "cg_rtol": rtol, "value": wl.grid.cells * steps / (sum(ms) / 1e3), "unit": UNIT,
+            "steps": steps, "warmup": warmup, "ms_per_step": mean, "ms_per_step_min": min(ms),
+            "pressure_solve_ms_per_step": pressure_ms(s),
+            "cg_iters_last_step": st["cg_iters"], "jacobi_sweeps_last_step": [st["jac_u"], st["jac_h"]],
+            "gpu_launches": int(launches), "clocks": clocks,
+            "whole_step": whole_step(prof, pk, mean),
+            "dominant_kernel": roofline(prof, pk, mean, False, wl.name),
+        }
+        s.close()
+    del dev
+    return out
 
 
 def pressure_ms(s):
@@ -571,7 +641,7 @@ def run_3d(args):
     value, _ = job_rate(sum(ms) / 1e3, cells * args.steps, world)
     prof = s.profile_step()
     KERNEL_MODEL.update(KERNEL_MODEL_3D)
-    roof = roofline(prof, peaks(), statistics.mean(ms), False, wl.name)
+    roof = roofline(prof, peaks(measure=True), statistics.mean(ms), False, wl.name)
 
     host = s.get_state()
     pin_in = {k: torch.from_numpy(v).pin_memory().numpy() for k, v in wl.fields.items()}
@@ -702,8 +772,9 @@ def run_ours(args):
 
     pms = pressure_ms(s)
     prof = s.profile_step()
-    pk = peaks()
+    pk = peaks(measure=True)
     roof = roofline(prof, pk, statistics.mean(ms), st["driver"] == "persistent", wl.name)
+    roof["whole_step"] = whole_step(prof, pk, statistics.mean(ms))
 
     # end to end through the C ABI with host buffers: H2D of the full state,
     # one step, D2H of the full state, every step
@@ -763,6 +834,9 @@ def run_ours(args):
             "gpu_launches": int(launches_m) * world, "clocks": clocks_m, "driver": st_m["driver"],
             "error_vs_fp64": matched_error(gea, wl, 100) if rank == 0 else None,
         }
+    if rank == 0 and not args.no_w3 and wl.name != "bubble4096x2048":
+        res["w3"] = w3_record(gea, W, stream, flush, pk, local)
+    res["peaks"] = {k: v for k, v in pk.items()}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds, args.workload)
     if world > 1:

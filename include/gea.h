@@ -191,7 +191,10 @@ int gea_step(gea_ctx *ctx, int32_t n);
 int gea_step_async(gea_ctx *ctx, int32_t n);
 int gea_sync(gea_ctx *ctx);
 
-/* Copy the state out (kind/mem as in set_state). Synchronises. */
+/* Copy the state out (kind/mem as in set_state; null destination pointers
+ * are skipped). CONSERVATIVE is computed on the device from the state:
+ * rho, rho u, rho w and rho e = rho (cv T + |u|^2/2 + g z) (Section 2.1,
+ * the total energy of eq. ent). Synchronises. */
 int gea_get_state(gea_ctx *ctx, gea_state_view *out);
 
 /* Diagnostics (Remark 2): theta' = T (p0/p)^(R/cp) - theta_bar(z) per cell
@@ -248,7 +251,29 @@ int gea_attach_net(gea_ctx *ctx, struct gea_net *net, int32_t mode);
  * stream; the step graphs are recorded anew. Errors: GEA_ERR_INVAL (n
  * outside 0..16). */
 int gea_set_tiles_per_block(gea_ctx *ctx, int32_t n);
+
+/* Poll limit of the grid barriers of the persistent step kernels (and of
+ * this context's share of an ensemble launch): a block that has polled the
+ * barrier `polls` times without every block arriving gives up, sets
+ * GEA_ERR_TIMEOUT and leaves the step at the next phase boundary, as does
+ * every other block, so the launch always ends; the state stays at the last
+ * completed step, and the error is sticky until the next gea_set_state.
+ * polls < 0 restores the default (2^23 polls, a few seconds); 0 makes every
+ * block that is not the last to arrive give up at once, which tests the
+ * failure path without a hang. The CUDA-graph driver has no such waits.
+ * Errors: GEA_ERR_INVAL (null ctx). */
+int gea_set_wait_limit(gea_ctx *ctx, int64_t polls);
 int gea_get_field(gea_ctx *ctx, int32_t which, double *host);
+
+/* Apply the pressure solve's preconditioner to r: z = M r with M one
+ * V(1,1)-cycle of the Galerkin multigrid hierarchy of the last completed step
+ * (the operator of eq. p_prime_sd in its Helmholtz form, as the CG of Step 3
+ * uses it; two damped Jacobi sweeps when the hierarchy has one level). r, z:
+ * nz*nx doubles, host or device. Lets a caller check what CG needs of M: it
+ * is linear, symmetric and positive definite. FP64 contexts only.
+ * Synchronises. Errors: GEA_ERR_INVAL (null pointers, a mixed-precision
+ * context), GEA_ERR_STATE (no completed step since the last set_state). */
+int gea_apply_precond(gea_ctx *ctx, const double *r, double *z);
 
 /* Event-timed duration (ms) of the pressure solves (all correctors) of the
  * last step launched by gea_step/gea_step_async, or -1 if unavailable. */
@@ -285,7 +310,9 @@ int gea_profile_step(gea_ctx *ctx, gea_kernel_time *out, int32_t max_entries,
  * live in a fixed 1 MiB file-scope device array that every GPU that loads
  * the library keeps until the process exits. Its device address is looked
  * up on the first call on each device (cudaGetSymbolAddress, with that
- * device current); make that first call before any stream capture. Every
+ * device current) and kept; make that first call before any stream capture.
+ * A cudaDeviceReset of that device invalidates the kept address: do not call
+ * this entry point on a device after resetting it. Every
  * call shares the array: the counter is cleared at the start of each call,
  * and calls whose kernels overlap on the GPU (on different streams or
  * threads) race on it -- order them on one stream.
@@ -295,6 +322,17 @@ int gea_profile_step(gea_ctx *ctx, gea_kernel_time *out, int32_t max_entries,
 int gea_mass_energy_noalloc(int32_t nx, int32_t nz, double lx, double lz, double cp, double R,
                             double g, const double *rho, const double *u, const double *w,
                             const double *T, double *out, void *stream);
+
+/* Arithmetic peak probe (the paper has no counterpart): `blocks` blocks of
+ * 256 threads, each thread running 8 independent fused multiply-add chains
+ * of `iters` steps in FP64 (bits = 64) or FP32 (bits = 32), so one launch
+ * does blocks x 256 x 8 x iters FMAs (x 2 flops). out: device array of
+ * blocks x 256 values of that type (the chains' sums, which keep them from
+ * being removed). Enqueued on `stream` (cudaStream_t, NULL: legacy default);
+ * the caller times it with CUDA events to measure the FMA issue rate that
+ * bounds the FP64 stencil and solver kernels. Errors: GEA_ERR_INVAL,
+ * GEA_ERR_CUDA. */
+int gea_probe_fma(int32_t bits, int32_t blocks, int32_t iters, void *out, void *stream);
 
 /* ---- ensembles: many independent contexts advanced by one launch ----
  *

@@ -44,6 +44,10 @@ enum { GEA_CONV_RELU = 1, GEA_CONV_OUT_F32 = 2 };
  * (bias may be NULL: zero), accumulated in FP32. cin, cout in {16, 32, 64};
  * n, h, w >= 1. status (optional device int) receives GEA_ERR_TIMEOUT if a
  * wait for the tensor cores gave up (never expected); it is not cleared.
+ * After such a give-up the CTA waits once more, again bounded, for its MMA
+ * batch before it frees its tensor memory; if that wait also runs out, the
+ * batch may still be writing, so after GEA_ERR_TIMEOUT treat the CUDA context
+ * as lost (destroy it before further GPU work in the process).
  * Errors: GEA_ERR_INVAL (sizes, channel counts, mode, odd h or w with
  * UPADD, null x0 / wt / y, null x1 with UPADD), GEA_ERR_CUDA. */
 int gea_conv3x3(int32_t n, int32_t h, int32_t w, int32_t cin, int32_t cout, int32_t mode,

@@ -287,12 +287,24 @@ static void face_forces(const orc_cfg *c, const double *pp, const double *rho,
     }
 }
 
-static double norm2(const double *x, size_t n)
+/* Order of the reductions (the residual norms and the CG dot products):
+ * index order by default, reverse index order after orc_set_reverse_sums(1).
+ * Both are correct evaluations of the same sums; the tests compare the two
+ * runs to measure the round-off floor of a result without any GPU. */
+static int g_reverse_sums = 0;
+void orc_set_reverse_sums(int on) { g_reverse_sums = on != 0; }
+
+static double dot(const double *x, const double *y, size_t n)
 {
     double s = 0.0;
-    for (size_t q = 0; q < n; ++q) s += x[q] * x[q];
-    return sqrt(s);
+    if (g_reverse_sums)
+        for (size_t q = n; q-- > 0;) s += x[q] * y[q];
+    else
+        for (size_t q = 0; q < n; ++q) s += x[q] * y[q];
+    return s;
 }
+
+static double norm2(const double *x, size_t n) { return sqrt(dot(x, x, n)); }
 
 /* ------------------------------------------------------------------ */
 /* implicit transport solves (Step 1 momentum, Step 2 enthalpy)          */
@@ -425,18 +437,17 @@ int orc_pcg(const orc_cfg *c, const double *psi, const double *Dx, const double 
     double bn = norm2(b, n);
     double rn = norm2(r, n);
     int it = 0, ok = 0;
-    double rz = 0.0;
-    for (size_t i = 0; i < n; ++i) { z[i] = r[i] / d[i]; p[i] = z[i]; rz += r[i] * z[i]; }
+    for (size_t i = 0; i < n; ++i) { z[i] = r[i] / d[i]; p[i] = z[i]; }
+    double rz = dot(r, z, n);
     for (;;) {
         if (rn <= c->cg_rtol * bn || rn == 0.0) { ok = 1; break; }
         if (it >= c->cg_maxit) break;
         orc_helmholtz_apply(c, psi, Dx, Dz, p, q);
-        double pq = 0.0;
-        for (size_t i = 0; i < n; ++i) pq += p[i] * q[i];
+        double pq = dot(p, q, n);
         double alpha = rz / pq;
         for (size_t i = 0; i < n; ++i) { x[i] += alpha * p[i]; r[i] -= alpha * q[i]; }
-        double rz_new = 0.0;
-        for (size_t i = 0; i < n; ++i) { z[i] = r[i] / d[i]; rz_new += r[i] * z[i]; }
+        for (size_t i = 0; i < n; ++i) z[i] = r[i] / d[i];
+        double rz_new = dot(r, z, n);
         double beta = rz_new / rz;
         rz = rz_new;
         for (size_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];

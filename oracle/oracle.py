@@ -89,7 +89,15 @@ def _bind(path: str):
     lib.orc_transport_solve.argtypes = [C.POINTER(_Cfg), _P, _P, _P, C.c_double,
                                         C.c_int, _P, _P]
     lib.orc_transport_solve.restype = C.c_int
+    lib.orc_set_reverse_sums.argtypes = [C.c_int]
     return lib
+
+
+def set_reverse_sums(on: bool):
+    """Evaluate the oracle's reductions (norms, CG dot products) in reverse
+    index order (on) or in index order (off, the default): two correct
+    evaluations whose difference is a round-off floor."""
+    _lib_handle().orc_set_reverse_sums(1 if on else 0)
 
 
 def _lib_handle():

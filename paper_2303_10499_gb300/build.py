@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgea.so")
 SOURCES = ["gea_kernels.cu", "gea_persistent.cu", "gea_mixed.cu", "gea_capi.cu", "gea_noalloc.cu",
-           "gea_conv.cu", "gea_net.cu", "gea3d.cu"]
+           "gea_conv.cu", "gea_net.cu", "gea3d.cu", "gea_probe.cu"]
 HEADERS = ["gea_internal.cuh", "gea_tiles.cuh"]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

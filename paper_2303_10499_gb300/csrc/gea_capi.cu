@@ -58,6 +58,7 @@ struct gea_ctx {
     bool have_state = false;
     int base = 0;                         // state slot loaded by the last set_state
     int pers_blocks = 0;                  // persistent-kernel grid (0: graph path only)
+    long long wait_polls = -1;            // grid-barrier poll limit of the persistent kernels (< 0: default)
     long long steps_at_sync = 0;          // device steps_done at the last sync
     char err[256] = {0};
 };
@@ -719,11 +720,11 @@ int gea_step_async(gea_ctx *ctx, int32_t n)
         if (ctx->mixed)
             CK(launch_persistent_mixed(a, ctx->L[0], ctx->mx, ctx->Lf.data(), (int)ctx->Lf.size(), kCoarseSweeps,
                                        ctx->C.n_corr, ctx->C.jac_maxit, ctx->C.cg_maxit, first, n,
-                                       ctx->pers_blocks, ctx->stream));
+                                       ctx->pers_blocks, ctx->wait_polls, ctx->stream));
         else
             CK(launch_persistent(a, ctx->L.data(), (int)ctx->L.size(), kCoarseSweeps, ctx->C.n_corr,
                                  ctx->C.jac_maxit, ctx->C.cg_maxit, first, n, ctx->pers_blocks,
-                                 ctx->stream));
+                                 ctx->wait_polls, ctx->stream));
         ctx->steps_at_sync += n;
         return GEA_OK;
     }
@@ -780,7 +781,16 @@ int gea_get_state(gea_ctx *ctx, gea_state_view *v)
             if ((rc = copy_out(ctx, dst[f], src[f], cols, rows))) return rc;
         }
     } else if (v->kind == GEA_STATE_CONSERVATIVE) {
-        return fail(ctx, GEA_ERR_INVAL, "conservative get is computed by the caller from FULL");
+        // computed on the device into the staging area, then copied out
+        const size_t cellw = arr_bytes(G, nz) / sizeof(double);
+        double *st = ctx->stage;
+        launch_conserve(G, ctx->F, S, st, st + cellw, st + 2 * cellw, st + 3 * cellw, ctx->stream);
+        CK(cudaGetLastError());
+        double *dst[4] = {v->rho, v->rhou, v->rhow, v->rhoe};
+        for (int f = 0; f < 4; ++f) {
+            if (!dst[f]) continue;
+            if ((rc = copy_out(ctx, dst[f], st + f * cellw, nx, nz))) return rc;
+        }
     } else {
         return fail(ctx, GEA_ERR_INVAL, "unknown state kind %d", v->kind);
     }
@@ -942,6 +952,40 @@ int gea_set_tiles_per_block(gea_ctx *ctx, int32_t n)
     return GEA_OK;
 }
 
+int gea_apply_precond(gea_ctx *ctx, const double *r, double *z)
+{
+    if (!ctx || !r || !z) return GEA_ERR_INVAL;
+    if (ctx->mixed) return fail(ctx, GEA_ERR_INVAL, "the FP64 preconditioner of a mixed-precision context is not kept");
+    if (!ctx->have_state) return fail(ctx, GEA_ERR_STATE, "no state set");
+    Scal h;
+    int rc = read_scal(ctx, &h);
+    if (rc) return rc;
+    if (h.steps_done < 1) return fail(ctx, GEA_ERR_STATE, "no completed step: the operator is not assembled");
+    // the V-cycle kernels run while the CG loop is open; their reduction
+    // (r.z) writes the loop scalars, which are put back afterwards
+    Scal run = h;
+    run.done[LOOP_CG] = 0;
+    run.status = 0;
+    run.cg_it = 0;
+    CK(cudaMemcpyAsync(ctx->sc, &run, sizeof(Scal), cudaMemcpyHostToDevice, ctx->stream));
+    Level *L = ctx->L.data();
+    if ((rc = copy_in(ctx, L[0].r, r, ctx->G.nx, ctx->G.nz))) return rc;
+    StepArgs a = step_args(ctx, 0);
+    launch_vcycle(a, L, (int)ctx->L.size(), kCoarseSweeps, ctx->stream, nullptr);
+    CK(cudaGetLastError());
+    if ((rc = copy_out(ctx, z, L[0].e2, ctx->G.nx, ctx->G.nz))) return rc;
+    CK(cudaMemcpyAsync(ctx->sc, &h, sizeof(Scal), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return GEA_OK;
+}
+
+int gea_set_wait_limit(gea_ctx *ctx, int64_t polls)
+{
+    if (!ctx) return GEA_ERR_INVAL;
+    ctx->wait_polls = polls < 0 ? -1 : polls;
+    return GEA_OK;
+}
+
 int gea_attach_net(gea_ctx *ctx, gea_net *net, int32_t mode)
 {
     if (!ctx || mode < 0 || mode > 3 || (mode != 0 && !net)) return GEA_ERR_INVAL;
@@ -1097,7 +1141,7 @@ int gea_ensemble_step(gea_ensemble *e, int32_t n)
         StepArgs a[2] = {step_args(c, 0), step_args(c, 1)};
         const int first = (int)((c->base + c->steps_at_sync) & 1);
         persist_args_fill(e->hargs + i * e->argb, a, c->L.data(), (int)c->L.size(), kCoarseSweeps, c->C.n_corr,
-                          c->C.jac_maxit, c->C.cg_maxit, first, n);
+                          c->C.jac_maxit, c->C.cg_maxit, first, n, c->wait_polls);
     }
     if (cudaMemcpyAsync(e->dargs, e->hargs, e->argb * e->m.size(), cudaMemcpyHostToDevice, e->st) !=
             cudaSuccess ||

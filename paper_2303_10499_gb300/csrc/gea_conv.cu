@@ -285,8 +285,18 @@ __global__ void __launch_bounds__(kThreads) k_conv3x3(ConvArgs a)
                 }
                 __nanosleep(32);
             }
+            if (!ok) {
+                // gave up: the committed MMA batch may still be running and
+                // reading sA/sW and writing TMEM, so wait for it once more
+                // (bounded) before the CTA releases its TMEM columns and
+                // shared memory. If that wait gives up too, nothing can
+                // contain the batch: the status says so, and the caller must
+                // treat the CUDA context as lost.
+                unsigned drain = 0;
+                while (!mbar_try_wait(smem_u32(mbar), phase) && ++drain <= kWaitLimit) __nanosleep(32);
+                if (a.status) atomicExch(a.status, GEA_ERR_TIMEOUT);
+            }
             *okflag = ok ? 1 : 0;
-            if (!ok && a.status) atomicExch(a.status, GEA_ERR_TIMEOUT);
         }
         __syncthreads();
         tc_fence_after();

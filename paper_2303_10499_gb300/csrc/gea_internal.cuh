@@ -338,6 +338,9 @@ __device__ __forceinline__ void block_tiles(const Geom &G, F f)
 void launch_derive(const Geom &G, const Phys &F, const double *rho, const double *rhou,
                    const double *rhow, const double *rhoe, const State &S, Scal *sc,
                    cudaStream_t st);
+// conservative variables rho, rho u, rho w, rho e of state S (pitched arrays)
+void launch_conserve(const Geom &G, const Phys &F, const State &S, double *rho, double *rhou, double *rhow,
+                     double *rhoe, cudaStream_t st);
 void launch_les(const StepArgs &a, cudaStream_t st, Tracer *tr);
 void launch_pred_setup(const StepArgs &a, cudaStream_t st, Tracer *tr);
 // second = 1: the second sweep of a pair (copies instead once converged)
@@ -408,17 +411,20 @@ int persistent_max_blocks();
 // FP64 finest level L0, the FP32 operator and vectors m, the FP32 hierarchy
 // Lf[0 .. nlev-1].
 int persistent_mixed_max_blocks();
+// wait_polls: polls of a grid barrier before a block gives up and sets
+// GEA_ERR_TIMEOUT (< 0: the default limit of a few seconds).
 cudaError_t launch_persistent_mixed(const StepArgs a[2], const Level &L0, const MixedArgs &m, const LevelF *Lf,
                                     int nlev, int ncoarse, int n_corr, int jac_maxit, int cg_maxit,
-                                    int first_slot, int nsteps, int blocks, cudaStream_t st);
+                                    int first_slot, int nsteps, int blocks, long long wait_polls,
+                                    cudaStream_t st);
 cudaError_t launch_persistent(const StepArgs a[2], const Level *L, int nlev, int ncoarse, int n_corr,
                               int jac_maxit, int cg_maxit, int first_slot, int nsteps, int blocks,
-                              cudaStream_t st);
+                              long long wait_polls, cudaStream_t st);
 // ensemble launch: one argument block per member (persist_args_fill) in
 // device memory, first[m] the member's first block (nmem + 1 entries)
 size_t persist_args_bytes();
 void persist_args_fill(void *dst, const StepArgs a[2], const Level *L, int nlev, int ncoarse, int n_corr,
-                       int jac_maxit, int cg_maxit, int first_slot, int nsteps);
+                       int jac_maxit, int cg_maxit, int first_slot, int nsteps, long long wait_polls);
 int ensemble_max_blocks();
 cudaError_t launch_ensemble(const void *Pm, const int *first, int nmem, int blocks, cudaStream_t st);
 

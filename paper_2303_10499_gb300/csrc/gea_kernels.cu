@@ -53,6 +53,22 @@ __global__ void k_derive(Geom G, Phys F, const double *__restrict__ rho,
     if (k == G.nz - 1) S.phiz[G.nz * G.P + i] = 0.0;
 }
 
+// Conservative variables of a state (Section 2.1), the inverse of k_derive:
+// rho, rho u, rho w and rho e with the total energy e = cv T + |u|^2/2 + g z.
+__global__ void k_conserve(Geom G, Phys F, State S, double *__restrict__ rho, double *__restrict__ rhou,
+                           double *__restrict__ rhow, double *__restrict__ rhoe)
+{
+    int i, k;
+    if (!cell_of(G, blockIdx.x, blockIdx.y, i, k)) return;
+    const int q = cidx(G, i, k);
+    const double z = (k + 0.5) * G.dz;
+    const double r = S.rho[q], u = S.u[q], w = S.w[q];
+    const double K = 0.5 * (u * u + w * w);
+    rho[q] = r;
+    rhou[q] = r * u;
+    rhow[q] = r * w;
+    rhoe[q] = r * ((F.cp - F.R) * S.T[q] + K + F.g * z);
+}
 
 // ---- Step 1 ----
 
@@ -329,6 +345,12 @@ void launch_derive(const Geom &G, const Phys &F, const double *rho, const double
                    cudaStream_t st)
 {
     k_derive<<<grid_of(G), kBlock, 0, st>>>(G, F, rho, rhou, rhow, rhoe, S, sc);
+}
+
+void launch_conserve(const Geom &G, const Phys &F, const State &S, double *rho, double *rhou, double *rhow,
+                     double *rhoe, cudaStream_t st)
+{
+    k_conserve<<<grid_of(G), kBlock, 0, st>>>(G, F, S, rho, rhou, rhow, rhoe);
 }
 
 // Launch with an optional trace bracket.

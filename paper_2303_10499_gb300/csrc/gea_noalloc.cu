@@ -21,7 +21,10 @@
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kMaxBlocks = GEA_NOALLOC_MAX_CELLS / kThreads;
+// blocks of the largest accepted launch, ceil(GEA_NOALLOC_MAX_CELLS / kThreads):
+// every block of a launch has a partial slot
+constexpr int kMaxBlocks = (GEA_NOALLOC_MAX_CELLS + kThreads - 1) / kThreads;
+static_assert((long long)kMaxBlocks * kThreads >= GEA_NOALLOC_MAX_CELLS, "a partial slot per block");
 constexpr int kMaxDevices = 64;
 
 // [0, kMaxBlocks): mass partials, [kMaxBlocks, 2 kMaxBlocks): energy partials,
@@ -95,7 +98,8 @@ __global__ void k_mass_energy_fixed(int nx, int nz, double dx, double dz, double
 }
 
 // Device address of g_scratch on the current device, looked up once per
-// device.
+// device and kept for the life of the process (a cudaDeviceReset unloads the
+// module, after which the kept address is stale: the header says so).
 cudaError_t scratch_address(double **ptr)
 {
     int dev = 0;

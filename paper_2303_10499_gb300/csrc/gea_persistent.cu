@@ -28,7 +28,7 @@ namespace {
 
 using namespace tiles;
 
-constexpr unsigned long long kSpinLimit = 1ull << 23;   // polls of ~0.7 us each: a few seconds
+constexpr unsigned long long kSpinLimit = 1ull << 23;   // polls of ~0.7 us each: a few seconds (the default)
 // values per thread a grid reduction may carry: the block-sum scratch after
 // the tile area holds kRedVals x NTHREADS doubles
 constexpr int kRedVals = 4;
@@ -37,6 +37,7 @@ struct PersistArgs {
     StepArgs a[2];          // a[s] reads state slot s and writes slot s ^ 1
     Level L[kMaxLevels];
     int nlev, ncoarse, nsteps, first_slot, n_corr, jac_maxit, cg_maxit;
+    unsigned long long spin_limit;   // polls of a grid barrier before giving up
 };
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
@@ -77,6 +78,7 @@ struct Grp {
     int rank, nb;
     unsigned *gen;   // barriers this block has passed in this launch
     Scal *gs;        // the context's scalars in global memory (barrier words, status, results)
+    unsigned long long spin_limit;   // polls of a barrier before the block gives up
 };
 
 // The block's own copy of the context's scalars. Every block finishes every
@@ -121,7 +123,7 @@ __device__ __forceinline__ void gbar(const Grp &g)
         unsigned c = atom_add_acq_rel(&gs->bar_count, 1u) + 1u;
         unsigned long long spins = 0;
         while ((int)(c - target) < 0) {
-            if (++spins > kSpinLimit) {
+            if (spins++ >= g.spin_limit) {
                 atomicCAS(&gs->status, 0, GEA_ERR_TIMEOUT);
                 break;
             }
@@ -636,7 +638,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_persistent(PersistArgs P)
     }
     load_ctl(gs);
     __syncthreads();
-    const Grp g{(int)blockIdx.x, (int)gridDim.x, &gen, gs};
+    const Grp g{(int)blockIdx.x, (int)gridDim.x, &gen, gs, P.spin_limit};
     if (!s_stop) {
         if (blockIdx.x == 0 && tid_of() == 0) gs->launches += 1;
         for (int s = 0; s < P.nsteps; ++s) {
@@ -664,7 +666,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_persistent_mixed(PersistArgs P,
     }
     load_ctl(gs);
     __syncthreads();
-    const Grp g{(int)blockIdx.x, (int)gridDim.x, &gen, gs};
+    const Grp g{(int)blockIdx.x, (int)gridDim.x, &gen, gs, P.spin_limit};
     if (!s_stop) {
         if (blockIdx.x == 0 && tid_of() == 0) gs->launches += 1;
         for (int s = 0; s < P.nsteps; ++s) {
@@ -710,7 +712,8 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_ensemble(const PersistArgs *Pm,
     }
     load_ctl(sc);
     __syncthreads();
-    const Grp g{(int)blockIdx.x - __ldg(&first[m]), __ldg(&first[m + 1]) - __ldg(&first[m]), &gen, sc};
+    const Grp g{(int)blockIdx.x - __ldg(&first[m]), __ldg(&first[m + 1]) - __ldg(&first[m]), &gen, sc,
+                P.spin_limit};
     if (!s_stop) {
         if (g.rank == 0 && tid == 0) sc->launches += 1;
         for (int s = 0; s < P.nsteps; ++s) {
@@ -724,12 +727,20 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_ensemble(const PersistArgs *Pm,
 
 constexpr size_t kEnsembleSmem = kPersistSmem + (sizeof(PersistArgs) + 15) / 16 * 16;
 
+// Barrier polls before a block gives up: wait_polls < 0 selects the
+// default, 0 makes every block that is not the last to arrive give up at
+// once.
+unsigned long long spin_limit_of(long long wait_polls)
+{
+    return wait_polls < 0 ? kSpinLimit : (unsigned long long)wait_polls;
+}
+
 }  // namespace
 
 size_t persist_args_bytes() { return sizeof(PersistArgs); }
 
 void persist_args_fill(void *dst, const StepArgs a[2], const Level *L, int nlev, int ncoarse, int n_corr,
-                       int jac_maxit, int cg_maxit, int first_slot, int nsteps)
+                       int jac_maxit, int cg_maxit, int first_slot, int nsteps, long long wait_polls)
 {
     PersistArgs P;
     memset(&P, 0, sizeof(P));
@@ -743,6 +754,7 @@ void persist_args_fill(void *dst, const StepArgs a[2], const Level *L, int nlev,
     P.n_corr = n_corr;
     P.jac_maxit = jac_maxit;
     P.cg_maxit = cg_maxit;
+    P.spin_limit = spin_limit_of(wait_polls);
     memcpy(dst, &P, sizeof(P));
 }
 
@@ -784,7 +796,7 @@ int persistent_max_blocks()
 
 cudaError_t launch_persistent(const StepArgs a[2], const Level *L, int nlev, int ncoarse, int n_corr,
                               int jac_maxit, int cg_maxit, int first_slot, int nsteps, int blocks,
-                              cudaStream_t st)
+                              long long wait_polls, cudaStream_t st)
 {
     PersistArgs P;
     P.a[0] = a[0];
@@ -797,6 +809,7 @@ cudaError_t launch_persistent(const StepArgs a[2], const Level *L, int nlev, int
     P.n_corr = n_corr;
     P.jac_maxit = jac_maxit;
     P.cg_maxit = cg_maxit;
+    P.spin_limit = spin_limit_of(wait_polls);
     void *args[] = {&P};
     return cudaLaunchCooperativeKernel((const void *)k_persistent, dim3(blocks), dim3(BX, BZ), args,
                                        kPersistSmem, st);
@@ -818,7 +831,8 @@ int persistent_mixed_max_blocks()
 
 cudaError_t launch_persistent_mixed(const StepArgs a[2], const Level &L0, const MixedArgs &m, const LevelF *Lf,
                                     int nlev, int ncoarse, int n_corr, int jac_maxit, int cg_maxit,
-                                    int first_slot, int nsteps, int blocks, cudaStream_t st)
+                                    int first_slot, int nsteps, int blocks, long long wait_polls,
+                                    cudaStream_t st)
 {
     if (nlev < 1 || nlev > kMaxLevels) return cudaErrorInvalidValue;
     PersistArgs P;
@@ -833,6 +847,7 @@ cudaError_t launch_persistent_mixed(const StepArgs a[2], const Level &L0, const 
     P.n_corr = n_corr;
     P.jac_maxit = jac_maxit;
     P.cg_maxit = cg_maxit;
+    P.spin_limit = spin_limit_of(wait_polls);
     MixedPersist X;
     memset(&X, 0, sizeof(X));
     X.m = m;

@@ -19,7 +19,7 @@ import numpy as np
 from .build import LIB
 
 GEA_OK, GEA_ERR_INVAL, GEA_ERR_NOMEM, GEA_ERR_CUDA, GEA_ERR_NOCONV, GEA_ERR_NONFINITE, \
-    GEA_ERR_STATE = range(7)
+    GEA_ERR_STATE, GEA_ERR_TIMEOUT = range(8)
 STATE_CONSERVATIVE, STATE_FULL = 0, 1
 FLAG_GRAPH, FLAG_MIXED, FLAG_KEEP_R0 = 1, 2, 4
 MEM_HOST, MEM_DEVICE = 0, 1
@@ -102,6 +102,9 @@ def library() -> C.CDLL:
         lib.gea_conv3x3.argtypes = [I, I, I, I, I, I, I, P, P, P, P, P, P, P]
         lib.gea_attach_net.argtypes = [P, P, I]
         lib.gea_set_tiles_per_block.argtypes = [P, I]
+        lib.gea_set_wait_limit.argtypes = [P, C.c_int64]
+        lib.gea_apply_precond.argtypes = [P, P, P]
+        lib.gea_probe_fma.argtypes = [I, I, I, P, P]
         lib.gea_ensemble_create.argtypes = [C.POINTER(P), I, P, C.POINTER(P)]
         lib.gea_ensemble_set_stream.argtypes = [P, P]
         lib.gea_ensemble_blocks.argtypes = [P, I]
@@ -229,13 +232,19 @@ class Solver:
         self._check(self.lib.gea_get_state(self.h, C.byref(v)))
         return out
 
-    def get_conservative(self) -> Dict[str, np.ndarray]:
-        s = self.get_full()
-        z = (np.arange(self.grid.nz) + 0.5)[:, None] * self.grid.dz
-        cv = self.const.cp - self.const.R
-        rho, u, w, T = s["rho"], s["u"], s["w"], s["T"]
-        return {"rho": rho, "rhou": rho * u, "rhow": rho * w,
-                "rhoe": rho * (cv * T + 0.5 * (u * u + w * w) + self.const.g * z)}
+    def get_conservative(self, out: Optional[Dict] = None) -> Dict[str, np.ndarray]:
+        """rho, rho u, rho w, rho e of the current state, computed by the
+        library on the device (gea_get_state with kind CONSERVATIVE)."""
+        nx, nz = self.grid.nx, self.grid.nz
+        if out is None:
+            out = {k: np.empty((nz, nx)) for k in ("rho", "rhou", "rhow", "rhoe")}
+        v = _View()
+        v.kind = STATE_CONSERVATIVE
+        v.mem = MEM_DEVICE if _is_device(out["rho"]) else MEM_HOST
+        for k in ("rho", "rhou", "rhow", "rhoe"):
+            setattr(v, k, _addr(out[k]))
+        self._check(self.lib.gea_get_state(self.h, C.byref(v)))
+        return out
 
     # -- stepping ----------------------------------------------------------
     def step(self, n: int = 1):
@@ -273,6 +282,19 @@ class Solver:
         out = np.empty(shape)
         self._check(self.lib.gea_get_field(self.h, FIELDS[name], out.ctypes.data))
         return out
+
+    def apply_precond(self, r: np.ndarray) -> np.ndarray:
+        """z = M r with the pressure solve's multigrid preconditioner of the
+        last completed step (gea_apply_precond)."""
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        z = np.empty((self.grid.nz, self.grid.nx))
+        self._check(self.lib.gea_apply_precond(self.h, r.ctypes.data, z.ctypes.data))
+        return z
+
+    def set_wait_limit(self, polls: int):
+        """Grid-barrier poll limit of the persistent kernels (gea_set_wait_limit;
+        < 0: the default)."""
+        self._check(self.lib.gea_set_wait_limit(self.h, int(polls)))
 
     def pressure_ms(self) -> float:
         return float(self.lib.gea_last_pressure_ms(self.h))
@@ -316,6 +338,31 @@ class Solver:
         self._check(self.lib.gea_profile_step(self.h, buf, 64, C.byref(n)))
         return {buf[i].name.decode(): {"launches": buf[i].launches, "cells": buf[i].cells,
                                        "ms": buf[i].ms} for i in range(min(n.value, 64))}
+
+
+def probe_fma(bits: int = 64, blocks: int = 608, iters: int = 16384, stream=None, repeats: int = 5) -> Dict:
+    """Measured FMA rate (gea_probe_fma): the best of `repeats` CUDA-event
+    timed launches on `stream`, in TFLOP/s (an FMA counts 2 flops)."""
+    import torch
+    lib = library()
+    stream = stream or torch.cuda.current_stream()
+    dt = torch.float64 if bits == 64 else torch.float32
+    out = torch.empty(blocks * 256, dtype=dt, device="cuda")
+    flops = blocks * 256 * 8 * iters * 2.0
+    _chk(lib.gea_probe_fma(bits, blocks, max(1, iters // 16), out.data_ptr(), stream.cuda_stream),
+         "gea_probe_fma")   # warm-up
+    best = None
+    for _ in range(repeats):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _chk(lib.gea_probe_fma(bits, blocks, iters, out.data_ptr(), stream.cuda_stream), "gea_probe_fma")
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    assert torch.isfinite(out).all()
+    return {"tflops": flops / (best * 1e-3) / 1e12, "ms": best, "blocks": blocks, "iters": iters,
+            "flops": flops}
 
 
 CONV_PLAIN, CONV_POOL, CONV_UPADD = 0, 1, 2
