@@ -211,8 +211,8 @@ class ClockSampler:
 # from (profiles/traffic.json keys every figure by the hash of its kernel's
 # sources; a change to any of them invalidates that figure alone)
 KERNEL_SOURCES = {
-    "k_persistent": ("gea_internal.cuh", "gea_tiles.cuh", "gea_persistent.cu"),
-    "mg_up": ("gea_internal.cuh", "gea_tiles.cuh", "gea_kernels.cu"),
+    "k_persistent": ("gea_internal.cuh", "gea_tiles_body.cuh", "gea_persistent_body.cuh"),
+    "mg_up": ("gea_internal.cuh", "gea_tiles_body.cuh", "gea_kernels.cu"),
     "g3_": ("gea_internal.cuh", "gea3d.cu"),
 }
 
@@ -569,6 +569,12 @@ def run_ensemble(args):
         "ensemble_blocks_by_tiles": {"value": cells * args.steps / (sum(ms_tiles) / 1e3), "unit": UNIT,
                                      "ms_per_step": statistics.mean(ms_tiles)},
         "autotune": tune if not isinstance(tune, dict) else {k: v for k, v in tune.items() if k != "blocks"},
+        "tile_shape": {"chosen": tune["tile_shape"],
+                       "note": "one block shape per cooperative launch, so one shape for all members",
+                       "best_ms_32x8": min(tune["ms_per_step_by_shape_and_beta"]["32x8"].values()),
+                       "best_ms_chosen": min(tune["ms_per_step_by_shape_and_beta"][tune["tile_shape"]].values()),
+                       "gain_vs_32x8": min(tune["ms_per_step_by_shape_and_beta"]["32x8"].values()) /
+                       min(tune["ms_per_step_by_shape_and_beta"][tune["tile_shape"]].values())},
         "speedup_vs_one_launch_per_member": value / seq,
         "cg_iters_last_step_first_members": iters,
         "gpu_launches": 1, "clocks": clocks,

@@ -252,6 +252,20 @@ int gea_attach_net(gea_ctx *ctx, struct gea_net *net, int32_t mode);
  * outside 0..16). */
 int gea_set_tiles_per_block(gea_ctx *ctx, int32_t n);
 
+/* Tile shape of the persistent step kernels (FP64, mixed precision and the
+ * ensemble launch): 0 = 32 x 8 cells (the default, and the tile of the
+ * per-phase kernels of the CUDA-graph driver), 1 = 16 x 16, 2 = 64 x 4; one
+ * thread per cell, 256 threads a block. Halos cost less on squarer tiles,
+ * rows load in longer runs on wider ones, and the number of tiles per block
+ * changes the load balance, so the fastest shape depends on the grid; the
+ * tile-shape autotuner of the Python binding times the candidates on real
+ * steps. The results depend on the shape only through the order of the
+ * reduction sums. Members of an ensemble must share one shape. The CUDA-graph
+ * driver ignores it. Synchronises the stream. Errors: GEA_ERR_INVAL (shape
+ * outside 0..2), GEA_ERR_CUDA. */
+enum { GEA_TILE_32x8 = 0, GEA_TILE_16x16 = 1, GEA_TILE_64x4 = 2 };
+int gea_set_tile_shape(gea_ctx *ctx, int32_t shape);
+
 /* Poll limit of the grid barriers of the persistent step kernels (and of
  * this context's share of an ensemble launch): a block that has polled the
  * barrier `polls` times without every block arriving gives up, sets

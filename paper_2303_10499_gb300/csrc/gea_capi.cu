@@ -17,6 +17,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 using namespace gea;
@@ -59,6 +60,7 @@ struct gea_ctx {
     int base = 0;                         // state slot loaded by the last set_state
     int pers_blocks = 0;                  // persistent-kernel grid (0: graph path only)
     long long wait_polls = -1;            // grid-barrier poll limit of the persistent kernels (< 0: default)
+    int shape = SHAPE_32x8;               // tile shape of the persistent kernels (gea_set_tile_shape)
     long long steps_at_sync = 0;          // device steps_done at the last sync
     char err[256] = {0};
 };
@@ -556,8 +558,16 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
         total += 24 * cellf;                                        // MixedArgs
         for (const Geom &g : lg) total += 8 * arr_bytes_f(g, g.nz) + arr_bytes_f(g, g.nz + 1);
     }
+    // reduction partials: the per-phase kernels' grid sums need one slot per
+    // 32 x 8 tile, the persistent kernels two buffers of kRedVals per block
+    // (at most one block per tile of their shape)
     const size_t nb = (size_t)max_blocks(G);
-    total += round_up((kGcntDoubles + 8 * nb) * sizeof(double), 256);   // group counters, reduction partials
+    size_t nb_all = nb;
+    for (int sh = 0; sh < NSHAPES; ++sh) {
+        const PersistOps &o = persist_ops(sh);
+        nb_all = std::max(nb_all, (size_t)shape_tiles(G, o.bx, o.bz));
+    }
+    total += round_up((kGcntDoubles + 8 * nb_all) * sizeof(double), 256);   // group counters, reduction partials
     total += round_up(sizeof(Scal), 256);
     ctx->mem_bytes = total;
     if (cudaMalloc(&ctx->mem, total) != cudaSuccess) {
@@ -622,7 +632,7 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
     // group counters of the grid sums, then two buffers of 4 x (blocks <=
     // tiles) partials for the persistent kernels (or a grid sum's block and
     // group totals)
-    ctx->partials = take(round_up((kGcntDoubles + 8 * nb) * sizeof(double), 256));
+    ctx->partials = take(round_up((kGcntDoubles + 8 * nb_all) * sizeof(double), 256));
     ctx->sc = (Scal *)take(round_up(sizeof(Scal), 256));
     if ((size_t)(ptr - ctx->mem) > total) {
         gea_destroy(ctx);
@@ -634,7 +644,8 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
     // tiles per resident block (its phases are latency-bound); on larger
     // grids the per-phase kernels keep more blocks resident per SM
     if (!(c->flags & (GEA_FLAG_GRAPH | GEA_FLAG_KEEP_R0))) {
-        const int pmax = ctx->mixed ? persistent_mixed_max_blocks() : persistent_max_blocks();
+        const PersistOps &o = persist_ops(ctx->shape);
+        const int pmax = ctx->mixed ? o.mixed_max_blocks() : o.max_blocks();
         cudaGetLastError();
         if (pmax > 0 && (long long)nb <= (long long)kPersistTilesPerBlock * pmax)
             ctx->pers_blocks = pmax < (int)nb ? pmax : (int)nb;
@@ -717,12 +728,13 @@ int gea_step_async(gea_ctx *ctx, int32_t n)
     if (ctx->pers_blocks > 0 && !ctx->net) {
         StepArgs a[2] = {step_args(ctx, 0), step_args(ctx, 1)};
         const int first = (int)((ctx->base + ctx->steps_at_sync) & 1);
+        const PersistOps &o = persist_ops(ctx->shape);
         if (ctx->mixed)
-            CK(launch_persistent_mixed(a, ctx->L[0], ctx->mx, ctx->Lf.data(), (int)ctx->Lf.size(), kCoarseSweeps,
+            CK(o.launch_mixed(a, ctx->L[0], ctx->mx, ctx->Lf.data(), (int)ctx->Lf.size(), kCoarseSweeps,
                                        ctx->C.n_corr, ctx->C.jac_maxit, ctx->C.cg_maxit, first, n,
                                        ctx->pers_blocks, ctx->wait_polls, ctx->stream));
         else
-            CK(launch_persistent(a, ctx->L.data(), (int)ctx->L.size(), kCoarseSweeps, ctx->C.n_corr,
+            CK(o.launch(a, ctx->L.data(), (int)ctx->L.size(), kCoarseSweeps, ctx->C.n_corr,
                                  ctx->C.jac_maxit, ctx->C.cg_maxit, first, n, ctx->pers_blocks,
                                  ctx->wait_polls, ctx->stream));
         ctx->steps_at_sync += n;
@@ -979,6 +991,24 @@ int gea_apply_precond(gea_ctx *ctx, const double *r, double *z)
     return GEA_OK;
 }
 
+int gea_set_tile_shape(gea_ctx *ctx, int32_t shape)
+{
+    if (!ctx || shape < 0 || shape >= NSHAPES) return GEA_ERR_INVAL;
+    if (ctx->stream) CK(cudaStreamSynchronize(ctx->stream));
+    if (ctx->pers_blocks > 0) {
+        // the persistent driver stays; its grid follows the shape's occupancy
+        // and tile count
+        const PersistOps &o = persist_ops(shape);
+        const int pmax = ctx->mixed ? o.mixed_max_blocks() : o.max_blocks();
+        cudaGetLastError();
+        if (pmax <= 0) return fail(ctx, GEA_ERR_CUDA, "no resident blocks for tile shape %d", shape);
+        const long long nt = shape_tiles(ctx->G, o.bx, o.bz);
+        ctx->pers_blocks = (long long)pmax < nt ? pmax : (int)nt;
+    }
+    ctx->shape = shape;
+    return GEA_OK;
+}
+
 int gea_set_wait_limit(gea_ctx *ctx, int64_t polls)
 {
     if (!ctx) return GEA_ERR_INVAL;
@@ -1043,6 +1073,7 @@ struct gea_ensemble {
     char *hargs = nullptr;           // pinned host staging of the argument blocks
     void *dargs = nullptr;
     int *dfirst = nullptr;
+    int shape = SHAPE_32x8;          // the members' tile shape
 };
 
 extern "C" {
@@ -1057,7 +1088,12 @@ int gea_ensemble_create(gea_ctx **members, int32_t n, const double *weights, gea
         for (int j = 0; j < i; ++j)
             if (members[j] == c) return GEA_ERR_INVAL;
     }
-    const int B = ensemble_max_blocks();
+    // one launch, one block shape: the members' tile shape
+    const int shape = members[0]->shape;
+    for (int i = 1; i < n; ++i)
+        if (members[i]->shape != shape) return GEA_ERR_INVAL;
+    const PersistOps &ops = persist_ops(shape);
+    const int B = ops.ensemble_max_blocks();
     cudaGetLastError();
     if (B < n) return GEA_ERR_INVAL;
     // blocks in proportion to the members' tiles, at least one each and at
@@ -1066,7 +1102,7 @@ int gea_ensemble_create(gea_ctx **members, int32_t n, const double *weights, gea
     std::vector<double> wt(n);
     double tot = 0.0;
     for (int i = 0; i < n; ++i) {
-        tiles[i] = max_blocks(members[i]->G);
+        tiles[i] = shape_tiles(members[i]->G, ops.bx, ops.bz);
         wt[i] = weights ? weights[i] : (double)tiles[i];
         if (!(wt[i] > 0.0) || !(wt[i] < 1e300)) return GEA_ERR_INVAL;
         tot += wt[i];
@@ -1098,6 +1134,7 @@ int gea_ensemble_create(gea_ctx **members, int32_t n, const double *weights, gea
     e->first[0] = 0;
     for (int i = 0; i < n; ++i) e->first[i + 1] = e->first[i] + nb[i];
     e->blocks = e->first[n];
+    e->shape = shape;
     e->argb = persist_args_bytes();   // the kernel indexes an array of argument blocks
     e->st = members[0]->stream;
     if (cudaMallocHost(&e->hargs, e->argb * n) != cudaSuccess ||
@@ -1145,7 +1182,8 @@ int gea_ensemble_step(gea_ensemble *e, int32_t n)
     }
     if (cudaMemcpyAsync(e->dargs, e->hargs, e->argb * e->m.size(), cudaMemcpyHostToDevice, e->st) !=
             cudaSuccess ||
-        launch_ensemble(e->dargs, e->dfirst, (int)e->m.size(), e->blocks, e->st) != cudaSuccess) {
+        persist_ops(e->shape).launch_ensemble(e->dargs, e->dfirst, (int)e->m.size(), e->blocks, e->st) !=
+            cudaSuccess) {
         cudaGetLastError();
         return GEA_ERR_CUDA;
     }

@@ -405,27 +405,58 @@ int launch_mx_vcycle(const StepArgs &a, LevelF *L, int nlev, int ncoarse, cudaSt
 int launch_mx_cg_iter(const StepArgs &a, const MixedArgs &m, LevelF *L, int nlev, int ncoarse,
                       cudaStream_t st, Tracer *tr);
 void launch_mx_p_apply(const StepArgs &a, const MixedArgs &m, cudaStream_t st, Tracer *tr);
-// persistent cooperative step kernel (gea_persistent.cu)
-int persistent_max_blocks();
-// The mixed-precision step (GEA_FLAG_MIXED) as one cooperative launch: the
-// FP64 finest level L0, the FP32 operator and vectors m, the FP32 hierarchy
-// Lf[0 .. nlev-1].
-int persistent_mixed_max_blocks();
-// wait_polls: polls of a grid barrier before a block gives up and sets
-// GEA_ERR_TIMEOUT (< 0: the default limit of a few seconds).
-cudaError_t launch_persistent_mixed(const StepArgs a[2], const Level &L0, const MixedArgs &m, const LevelF *Lf,
-                                    int nlev, int ncoarse, int n_corr, int jac_maxit, int cg_maxit,
-                                    int first_slot, int nsteps, int blocks, long long wait_polls,
-                                    cudaStream_t st);
-cudaError_t launch_persistent(const StepArgs a[2], const Level *L, int nlev, int ncoarse, int n_corr,
-                              int jac_maxit, int cg_maxit, int first_slot, int nsteps, int blocks,
-                              long long wait_polls, cudaStream_t st);
-// ensemble launch: one argument block per member (persist_args_fill) in
-// device memory, first[m] the member's first block (nmem + 1 entries)
+// ---- persistent cooperative step kernels (gea_persistent_body.cuh) ----
+
+// Arguments of one context's persistent launch (or of one member of an
+// ensemble launch): both state slots' step arguments and the FP64 hierarchy.
+struct PersistArgs {
+    StepArgs a[2];          // a[s] reads state slot s and writes slot s ^ 1
+    Level L[kMaxLevels];
+    int nlev, ncoarse, nsteps, first_slot, n_corr, jac_maxit, cg_maxit;
+    unsigned long long spin_limit;   // polls of a grid barrier before giving up
+};
+
+// Grid-barrier polls before a block gives up (GEA_ERR_TIMEOUT): a few
+// seconds of ~0.7 us polls by default (wait_polls < 0); 0 makes every block
+// that is not the last to arrive give up at once.
+constexpr unsigned long long kSpinLimit = 1ull << 23;
+inline unsigned long long spin_limit_of(long long wait_polls)
+{
+    return wait_polls < 0 ? kSpinLimit : (unsigned long long)wait_polls;
+}
+
+// The persistent kernels exist for several tile shapes of NTHREADS threads
+// (BX x BZ cells, one per thread); the tile-shape autotuner picks one per
+// context. Each shape's host entry points:
+//  max_blocks / mixed_max_blocks / ensemble_max_blocks: co-resident blocks of
+//      the FP64, mixed-precision and ensemble kernels on this GPU (0 on error);
+//  launch / launch_mixed: n steps of one context (the FP64 finest-to-coarsest
+//      hierarchy L, or the FP64 finest level L0 with the FP32 operator m and
+//      hierarchy Lf), wait_polls as in spin_limit_of;
+//  launch_ensemble: one argument block per member (persist_args_fill) in
+//      device memory, first[m] the member's first block (nmem + 1 entries).
+struct PersistOps {
+    int bx, bz;
+    int (*max_blocks)();
+    int (*mixed_max_blocks)();
+    int (*ensemble_max_blocks)();
+    cudaError_t (*launch)(const StepArgs a[2], const Level *L, int nlev, int ncoarse, int n_corr, int jac_maxit,
+                          int cg_maxit, int first_slot, int nsteps, int blocks, long long wait_polls,
+                          cudaStream_t st);
+    cudaError_t (*launch_mixed)(const StepArgs a[2], const Level &L0, const MixedArgs &m, const LevelF *Lf,
+                                int nlev, int ncoarse, int n_corr, int jac_maxit, int cg_maxit, int first_slot,
+                                int nsteps, int blocks, long long wait_polls, cudaStream_t st);
+    cudaError_t (*launch_ensemble)(const void *Pm, const int *first, int nmem, int blocks, cudaStream_t st);
+};
+enum { SHAPE_32x8 = 0, SHAPE_16x16 = 1, SHAPE_64x4 = 2, NSHAPES = 3 };
+const PersistOps &persist_ops(int shape);
+// tiles of a grid for a tile shape
+inline long long shape_tiles(const Geom &G, int bx, int bz)
+{
+    return (long long)((G.nx + bx - 1) / bx) * ((G.nz + bz - 1) / bz);
+}
 size_t persist_args_bytes();
 void persist_args_fill(void *dst, const StepArgs a[2], const Level *L, int nlev, int ncoarse, int n_corr,
                        int jac_maxit, int cg_maxit, int first_slot, int nsteps, long long wait_polls);
-int ensemble_max_blocks();
-cudaError_t launch_ensemble(const void *Pm, const int *first, int nmem, int blocks, cudaStream_t st);
 
 }  // namespace gea

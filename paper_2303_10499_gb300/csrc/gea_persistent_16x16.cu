@@ -1,0 +1,15 @@
+// gea_persistent_16x16.cu -- the persistent step kernels (FP64, mixed
+// precision, ensemble) for the 16 x 16 tile, one of the shapes the
+// tile-shape autotuner chooses from (gea_set_tile_shape).
+#include "gea_internal.cuh"
+
+#include <string.h>
+
+namespace gea {
+namespace tiles_16x16 {
+constexpr int BX = 16;   // cells (threads) per tile row
+constexpr int BZ = 16;   // rows per tile
+#include "gea_tiles_body.cuh"
+#include "gea_persistent_body.cuh"
+}  // namespace tiles_16x16
+}  // namespace gea

@@ -26,6 +26,8 @@ MEM_HOST, MEM_DEVICE = 0, 1
 FIELDS = {"rho1": 0, "u1": 1, "w1": 2, "h1": 3, "rho2": 4, "Hx": 5, "Hz": 6, "b": 7,
           "Dx": 8, "Dz": 9, "hc": 10, "hax": 11, "haz": 12, "r0": 13}
 FULL_FIELDS = ("rho", "u", "w", "T", "h", "p", "pp", "pold", "phix", "phiz")
+# tile shapes of the persistent kernels (gea_set_tile_shape): cells in x by z
+TILE_SHAPES = {0: "32x8", 1: "16x16", 2: "64x4"}
 
 
 class GeaError(RuntimeError):
@@ -103,6 +105,7 @@ def library() -> C.CDLL:
         lib.gea_attach_net.argtypes = [P, P, I]
         lib.gea_set_tiles_per_block.argtypes = [P, I]
         lib.gea_set_wait_limit.argtypes = [P, C.c_int64]
+        lib.gea_set_tile_shape.argtypes = [P, I]
         lib.gea_apply_precond.argtypes = [P, P, P]
         lib.gea_probe_fma.argtypes = [I, I, I, P, P]
         lib.gea_ensemble_create.argtypes = [C.POINTER(P), I, P, C.POINTER(P)]
@@ -198,6 +201,7 @@ class Solver:
 
     def set_stream(self, stream):
         """stream: a torch.cuda.Stream, a raw cudaStream_t integer or None."""
+        self._stream = stream if hasattr(stream, "cuda_stream") else None
         s = getattr(stream, "cuda_stream", stream)
         self._check(self.lib.gea_set_stream(self.h, C.c_void_p(s or 0)))
 
@@ -329,6 +333,34 @@ class Solver:
         best = min(times, key=times.get)
         self.set_tiles_per_block(best)
         return {"ms_per_step": times, "tiles_per_block": best}
+
+    def set_tile_shape(self, shape: int):
+        """Tile shape of the persistent kernels (gea_set_tile_shape): one of
+        TILE_SHAPES' keys."""
+        self._check(self.lib.gea_set_tile_shape(self.h, int(shape)))
+        self.tile_shape = int(shape)
+
+    def tune_tile_shape(self, candidates=None, steps: int = 3) -> Dict:
+        """Tile-shape autotuner of the persistent kernels: for each candidate
+        shape, one untimed step and `steps` steps timed with CUDA events on
+        the context's stream; keeps the fastest. The state advances by
+        len(candidates) x (steps + 1) steps."""
+        import torch
+        candidates = tuple(TILE_SHAPES) if candidates is None else tuple(candidates)
+        stream = getattr(self, "_stream", None) or torch.cuda.current_stream()
+        times = {}
+        for sh in candidates:
+            self.set_tile_shape(sh)
+            self.step(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            self.step_async(steps)
+            e1.record(stream)
+            self.sync()
+            times[TILE_SHAPES[sh]] = e0.elapsed_time(e1) / steps
+        best = min(candidates, key=lambda sh: times[TILE_SHAPES[sh]])
+        self.set_tile_shape(best)
+        return {"ms_per_step": times, "tile_shape": TILE_SHAPES[best]}
 
     def profile_step(self) -> Dict[str, Dict]:
         """Advance one step with every kernel launch timed by CUDA events on
@@ -594,6 +626,34 @@ class Solver3D:
                 "cg_iters": list(s.cg_iters)[:n], "cg_relres": list(s.cg_relres)[:n],
                 "status": s.status, "mg_levels": s.mg_levels, "launches": s.launches,
                 "driver": {0: "graph", 2: "mixed"}[s.driver]}
+
+    def set_tile_shape(self, shape: int):
+        """Tile shape of the persistent kernels (gea_set_tile_shape): one of
+        TILE_SHAPES' keys."""
+        self._check(self.lib.gea_set_tile_shape(self.h, int(shape)))
+        self.tile_shape = int(shape)
+
+    def tune_tile_shape(self, candidates=None, steps: int = 3) -> Dict:
+        """Tile-shape autotuner of the persistent kernels: for each candidate
+        shape, one untimed step and `steps` steps timed with CUDA events on
+        the context's stream; keeps the fastest. The state advances by
+        len(candidates) x (steps + 1) steps."""
+        import torch
+        candidates = tuple(TILE_SHAPES) if candidates is None else tuple(candidates)
+        stream = getattr(self, "_stream", None) or torch.cuda.current_stream()
+        times = {}
+        for sh in candidates:
+            self.set_tile_shape(sh)
+            self.step(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            self.step_async(steps)
+            e1.record(stream)
+            self.sync()
+            times[TILE_SHAPES[sh]] = e0.elapsed_time(e1) / steps
+        best = min(candidates, key=lambda sh: times[TILE_SHAPES[sh]])
+        self.set_tile_shape(best)
+        return {"ms_per_step": times, "tile_shape": TILE_SHAPES[best]}
 
     def profile_step(self) -> Dict[str, Dict]:
         """One eagerly launched step with per-kernel CUDA-event totals."""

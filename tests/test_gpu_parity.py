@@ -225,18 +225,53 @@ def test_device_tensors_in_and_out(gea):
         assert np.array_equal(out[k].cpu().numpy(), host[k]), k
 
 
+def roundoff_floor_4096():
+    """Per-field round-off floor of one oracle step on the 4096 x 2048 bubble
+    (tests/golden/roundoff_floor_bubble4096x2048.txt, written by
+    make_roundoff_floor.py from the oracle alone): the larger of the
+    differences caused by reversing the oracle's reduction order and by
+    moving every input value by one ulp at random."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "roundoff_floor_bubble4096x2048.txt")
+    out = {}
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        k, rev, ulp = line.split()
+        out[k] = max(float(rev), float(ulp))
+    return out
+
+
 def test_full_size_one_step(gea, oracle_mod):
     """4096 x 2048 (larger than L2 at FP64): one step against the oracle,
-    plus mass conservation and mirror symmetry of the GPU state. After one
-    step the velocities are ~3e-3 m/s and the round-off floor (the oracle
-    against itself with the initial density perturbed by one ulp) is 1.9e-10
-    (rho u), 2.5e-10 (rho w), 3.6e-10 (phix), 4.8e-10 (phiz) of the vector
-    norms. The two sides differ by rounding in every operation, not one ulp
-    of the input: measured 8e-10 (rho w) and 1.0e-9 (phiz); the bar is 3e-9."""
+    plus mass conservation and mirror symmetry of the GPU state.
+
+    The bar comes from the oracle's own round-off floor F (file above). One
+    step leaves velocities of ~3e-3 m/s that the near-hydrostatic state makes
+    sensitive to rounding: moving each input value by one ulp moves rho u,
+    rho w by 2-3e-10 and the face fluxes by 4-5e-10 of their vector norm. The
+    GPU rounds differently in every stage of the step (the derivation of p',
+    both predictors, the EOS update, the assembly, each CG iteration and the
+    correction of both correctors: about ten independent injections of
+    one-ulp differences), and independent perturbations add in quadrature,
+    so the expected difference is about sqrt(10) F ~ 3 F. The bar is 4 F,
+    with F the larger of the two components of a vector (they share its
+    norm), and 64 ulps (1.4e-14) for scalar fields, whose floor is a few
+    ulps."""
     wl = W.get("bubble4096x2048")
     so, s = run_both(gea, oracle_mod, wl, 1)
     g = s.get_full()
-    compare_state(g, so, 3e-9, wl.const, wl.grid, vector_norm=True)
+    F = roundoff_floor_4096()
+    eps = np.finfo(np.float64).eps
+    mom = 4.0 * max(F["rhou"], F["rhow"])
+    flx = 4.0 * max(F["phix"], F["phiz"])
+    bars = {k: max(4.0 * v, 64 * eps) for k, v in F.items()}
+    bars.update({"rhou": mom, "rhow": mom, "phix": flx, "phiz": flx})
+    errs = compare_state(g, so, 1.0, wl.const, wl.grid, vector_norm=True)
+    ratio = {k: errs[k] / bars[k] for k in errs}
+    print("4096x2048 one step:", errs, "error / bar:", ratio)
+    bad = {k: (errs[k], bars[k]) for k in errs if not errs[k] <= bars[k]}
+    assert not bad, bad
     _, m1, _ = s.diagnostics(wl.theta_bar)
     s2 = gea.Solver(wl.grid, wl.const)
     s2.set_conservative(wl.fields)
