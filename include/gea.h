@@ -122,19 +122,41 @@ typedef struct gea_constants {
     int32_t flags;
     double mp_rtol;
     double cs;
+    uint32_t reading_flags;
 } gea_constants;
+
+/* gea_constants.reading_flags: where the paper's printed scheme admits more
+ * than one reading, 0 selects the library's default and a bit selects the
+ * alternative.
+ *  GEA_READING_K_LAGGED  eq. step3_sd as printed: the enthalpy right-hand side
+ *            b~_e = (rho^n h^n + rho^n K^{n-1} - p^{n-1}) / dt uses the kinetic
+ *            energy of the previous time level, K^{n-1} = |u^{n-1}|^2 / 2 (with
+ *            K^{-1} := K^0 after a conservative set_state). The default uses
+ *            rho^n K^n, the consistent first-order difference of rho K (the
+ *            printed K^{n-1} and p^{n-1} are then the lagged terms of the
+ *            time derivative of rho h + rho K - p). The state then carries
+ *            K^{n-1} (gea_state_view.Kold).
+ * Not built: the printed form of eq. p_prime_sd as a pure Poisson equation
+ * (its time term uses the known rho^{n+2/3}, so on the closed boxes of the
+ * paper's cases it is singular and, in general, inconsistent); the library
+ * solves the Helmholtz form that follows from rho^{n+1} = p^{n+1}/(R T^{n+1})
+ * (eq. step4_4sd). Other bits must be 0. */
+enum { GEA_READING_K_LAGGED = 1 };
 
 /* A view of caller-owned buffers (host or device, per mem). The library
  * copies from/to them; it never keeps the pointers.
  *  CONSERVATIVE: rho, rhou, rhow, rhoe (rho e = rho (cv T + |u|^2/2 + g z)).
- *  FULL: rho, u, w, T, h, p, pp (= p'), pold (= p^{n-1}), phix, phiz -- the
- *        complete state carried between steps; a FULL get followed by a FULL
- *        set continues bit for bit as if the run had not been interrupted. */
+ *  FULL: rho, u, w, T, h, p, pp (= p'), pold (= p^{n-1}), phix, phiz, and
+ *        Kold (= K^{n-1}; only with GEA_READING_K_LAGGED, otherwise ignored
+ *        and may be NULL) -- the complete state carried between steps; a
+ *        FULL get followed by a FULL set continues bit for bit as if the run
+ *        had not been interrupted. */
 typedef struct gea_state_view {
     int32_t kind;
     int32_t mem;
     double *rho, *rhou, *rhow, *rhoe;
     double *u, *w, *T, *h, *p, *pp, *pold, *phix, *phiz;
+    double *Kold;
 } gea_state_view;
 
 /* Counters of the last completed step. */

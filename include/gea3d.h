@@ -16,7 +16,8 @@
  *    centred at ((i+1/2) dx, (j+1/2) dy, (k+1/2) dz) at index
  *    (k ny + j) nx + i.
  *  - Pressure split p = p' - rho g z (g > 0, z up), as in gea.h.
- *  - The constants are gea_constants of gea.h. flags: 0 or GEA_FLAG_MIXED,
+ *  - The constants are gea_constants of gea.h (reading_flags must be 0: the
+ *    three-dimensional step has the default readings only). flags: 0 or GEA_FLAG_MIXED,
  *    the mixed-precision step as in gea.h (FP64 state, residuals and
  *    updates; FP32 Jacobi on the momentum and enthalpy increments and FP32
  *    multigrid CG on the pressure increment, each to mp_rtol times its

@@ -72,12 +72,19 @@ typedef struct {
     double cg_rtol;
     int32_t cg_maxit;
     double cs;          /* Smagorinsky constant; 0: constant viscosity mu only */
+    uint32_t reading_flags;   /* ORC_READING_* bits; 0: the default readings */
 } orc_cfg;
 
+/* Reading of eq. (step3_sd): b~_e = (rho^n h^n + rho^n K^{n-1} - p^{n-1})/dt as
+ * printed (K of the previous time level, K^{-1} := K^0), instead of the
+ * default rho^n K^n. */
+enum { ORC_READING_K_LAGGED = 1 };
+
 /* The solution tuple of Section 3 (rho, u, h, p, p', T) plus what the
- * scheme carries between steps: the face mass fluxes phi^n and p^{n-1}. */
+ * scheme carries between steps: the face mass fluxes phi^n, p^{n-1} and
+ * K^{n-1} = |u^{n-1}|^2/2 (used by the literal reading of eq. step3_sd). */
 typedef struct {
-    double *rho, *u, *w, *T, *h, *p, *pp, *pold, *phix, *phiz;
+    double *rho, *u, *w, *T, *h, *p, *pp, *pold, *phix, *phiz, *Kold;
 } orc_state;
 
 typedef struct {
@@ -92,6 +99,7 @@ typedef struct {
     double *rho1, *u1, *w1, *h1, *T1, *rho2, *psi;
     double *Hx, *Hz, *b;           /* from the last corrector */
     double *Dx, *Dz;               /* face coefficients, nz*(nx+1) and (nz+1)*nx */
+    double *bh;                    /* right-hand side of the enthalpy equation */
 } orc_dump;
 
 enum { BC_EVEN = 0, BC_U = 1, BC_W = 2, BC_H = 3 };
@@ -465,9 +473,9 @@ int orc_pcg(const orc_cfg *c, const double *psi, const double *Dx, const double 
 
 /* From (rho, rho u, rho w, rho e) with e = cv T + |u|^2/2 + g z (Section 2.1):
  * u = (rho u)/rho, T = (e - K - g z)/cv, p = rho R T (eq. p), h = cp T
- * (eq. K_h), p' = p + rho g z, p^{n-1} = p, and phi on interior faces the
- * linear average of the two cells' normal momentum times the face area
- * (zero on walls). */
+ * (eq. K_h), p' = p + rho g z, p^{n-1} = p, K^{n-1} = K, and phi on interior
+ * faces the linear average of the two cells' normal momentum times the face
+ * area (zero on walls). */
 int orc_derive(const orc_cfg *c, const double *rho, const double *rhou,
                const double *rhow, const double *rhoe, orc_state *s)
 {
@@ -490,6 +498,7 @@ int orc_derive(const orc_cfg *c, const double *rho, const double *rhou,
             s->p[q] = rho[q] * c->R * T;
             s->pp[q] = s->p[q] + rho[q] * c->g * z;
             s->pold[q] = s->p[q];
+            s->Kold[q] = K;
         }
     }
     for (int k = 0; k < nz; ++k)
@@ -564,11 +573,14 @@ int orc_step(const orc_cfg *c, orc_state *s, int32_t nsteps, orc_stats *st, orc_
 
         /* ---- Step 2, eq. (step3_sd): enthalpy, implicit in h^{n+1}. Right-hand
          * side b~_e - rho1 K1/dt - sum_j phi_j K1_j / V + p^n/dt - rho1 g w1 with
-         * b~_e = (rho^n h^n + rho^n K^n - p^{n-1})/dt ---- */
+         * b~_e = (rho^n h^n + rho^n K^n - p^{n-1})/dt, or with K^{n-1} in place
+         * of K^n in the literal reading ---- */
         for (int k = 0; k < nz; ++k)
             for (int i = 0; i < nx; ++i) {
                 int q = k * nx + i;
-                double Kn = 0.5 * (s->u[q] * s->u[q] + s->w[q] * s->w[q]);
+                double Kn = (c->reading_flags & ORC_READING_K_LAGGED)
+                                ? s->Kold[q]
+                                : 0.5 * (s->u[q] * s->u[q] + s->w[q] * s->w[q]);
                 double be = (s->rho[q] * s->h[q] + s->rho[q] * Kn - s->pold[q]) / dt;
                 bh[q] = be - rho1[q] * K1[q] / dt
                       - orc_convection_cell(c, s->phix, s->phiz, K1, BC_EVEN, i, k)
@@ -710,9 +722,11 @@ int orc_step(const orc_cfg *c, orc_state *s, int32_t nsteps, orc_stats *st, orc_
             if (dump->b) memcpy(dump->b, b, n * sizeof(double));
             if (dump->Dx) memcpy(dump->Dx, Dx, nfx * sizeof(double));
             if (dump->Dz) memcpy(dump->Dz, Dz, nfz * sizeof(double));
+            if (dump->bh) memcpy(dump->bh, bh, n * sizeof(double));
         }
 
-        /* ---- end of step: the new state; p^{n-1} <- p^n ---- */
+        /* ---- end of step: the new state; p^{n-1} <- p^n, K^{n-1} <- K^n ---- */
+        for (size_t q = 0; q < n; ++q) s->Kold[q] = 0.5 * (s->u[q] * s->u[q] + s->w[q] * s->w[q]);
         memcpy(s->pold, s->p, n * sizeof(double));
         memcpy(s->p, pnext, n * sizeof(double));
         memcpy(s->pp, pnew, n * sizeof(double));

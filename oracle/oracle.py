@@ -43,14 +43,15 @@ class _Cfg(C.Structure):
                 ("R", C.c_double), ("cp", C.c_double), ("g", C.c_double), ("p0", C.c_double),
                 ("mu", C.c_double), ("Pr", C.c_double), ("dt", C.c_double),
                 ("n_corr", C.c_int32), ("jac_rtol", C.c_double), ("jac_maxit", C.c_int32),
-                ("cg_rtol", C.c_double), ("cg_maxit", C.c_int32), ("cs", C.c_double)]
+                ("cg_rtol", C.c_double), ("cg_maxit", C.c_int32), ("cs", C.c_double),
+                ("reading_flags", C.c_uint32)]
 
 
 _P = C.POINTER(C.c_double)
 
 
 class _State(C.Structure):
-    _fields_ = [(n, _P) for n in ("rho", "u", "w", "T", "h", "p", "pp", "pold", "phix", "phiz")]
+    _fields_ = [(n, _P) for n in ("rho", "u", "w", "T", "h", "p", "pp", "pold", "phix", "phiz", "Kold")]
 
 
 class _Stats(C.Structure):
@@ -61,7 +62,7 @@ class _Stats(C.Structure):
 
 class _Dump(C.Structure):
     _fields_ = [(n, _P) for n in ("rho1", "u1", "w1", "h1", "T1", "rho2", "psi",
-                                  "Hx", "Hz", "b", "Dx", "Dz")]
+                                  "Hx", "Hz", "b", "Dx", "Dz", "bh")]
 
 
 def _bind(path: str):
@@ -113,7 +114,9 @@ def _ptr(a: np.ndarray):
     return a.ctypes.data_as(_P)
 
 
-STATE_FIELDS = ("rho", "u", "w", "T", "h", "p", "pp", "pold", "phix", "phiz")
+STATE_FIELDS = ("rho", "u", "w", "T", "h", "p", "pp", "pold", "phix", "phiz", "Kold")
+# reading flags (Constants.reading_flags): the literal K^{n-1} of eq. step3_sd
+READING_K_LAGGED = 1
 
 
 class OracleState:
@@ -160,7 +163,7 @@ class Oracle:
         self.cfg = _Cfg(grid.nx, grid.nz, grid.lx, grid.lz, const.R, const.cp, const.g,
                         const.p0, const.mu, const.Pr, const.dt, const.n_corr,
                         const.jac_rtol, const.jac_maxit, const.cg_rtol, const.cg_maxit,
-                        getattr(const, "cs", 0.0))
+                        getattr(const, "cs", 0.0), getattr(const, "reading_flags", 0))
         self.lib = _lib_handle() if lib_path is None else _bind(lib_path)
         self.last_stats = None
 
@@ -185,11 +188,11 @@ class Oracle:
         if dump:
             nx, nz = self.grid.nx, self.grid.nz
             d = {k: np.zeros((nz, nx)) for k in ("rho1", "u1", "w1", "h1", "T1", "rho2",
-                                                 "psi", "Hx", "Hz", "b")}
+                                                 "psi", "Hx", "Hz", "b", "bh")}
             d["Dx"] = np.zeros((nz, nx + 1))
             d["Dz"] = np.zeros((nz + 1, nx))
             dptr = _Dump(*[_ptr(d[k]) for k in ("rho1", "u1", "w1", "h1", "T1", "rho2", "psi",
-                                                  "Hx", "Hz", "b", "Dx", "Dz")])
+                                                  "Hx", "Hz", "b", "Dx", "Dz", "bh")])
         cs = s.cstruct()
         self.lib.orc_step(C.byref(self.cfg), C.byref(cs), int(n), C.byref(st),
                           C.byref(dptr) if dptr is not None else None)

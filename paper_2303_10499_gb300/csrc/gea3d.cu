@@ -1865,6 +1865,7 @@ int gea3d_create(const gea3d_grid *grid, const gea_constants *c, gea3d_ctx **out
     if (!(c->R > 0) || !(c->cp > c->R) || !(c->g >= 0) || !(c->p0 > 0) || !(c->mu >= 0) || !(c->Pr > 0) ||
         !(c->dt > 0) || c->n_corr < 1 || c->n_corr > 4 || !(c->jac_rtol > 0) || c->jac_maxit < 1 ||
         !(c->cg_rtol > 0) || c->cg_maxit < 1 || c->mg_min_cells < 0 || (c->flags & ~GEA_FLAG_MIXED) != 0 ||
+        c->reading_flags != 0 ||
         (!(c->flags & GEA_FLAG_MIXED) && c->mp_rtol != 0.0) ||
         ((c->flags & GEA_FLAG_MIXED) && c->mp_rtol != 0.0 && !(c->mp_rtol >= 1e-7 && c->mp_rtol < 1.0)) ||
         !(c->cs >= 0.0) || (c->cs > 0.0 && c->Pr != 1.0))

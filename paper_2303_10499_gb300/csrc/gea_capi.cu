@@ -504,6 +504,7 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
         !(c->Pr > 0) || !(c->dt > 0) || c->n_corr < 1 || c->n_corr > 4 || !(c->jac_rtol > 0) ||
         c->jac_maxit < 1 || !(c->cg_rtol > 0) || c->cg_maxit < 1 || c->mg_min_cells < 0 ||
         (c->flags & ~(GEA_FLAG_GRAPH | GEA_FLAG_MIXED | GEA_FLAG_KEEP_R0)) ||
+        (c->reading_flags & ~(uint32_t)GEA_READING_K_LAGGED) ||
         ((c->flags & GEA_FLAG_KEEP_R0) && (c->flags & GEA_FLAG_MIXED)))
         return GEA_ERR_INVAL;
     if ((c->flags & GEA_FLAG_MIXED) && c->mp_rtol != 0.0 && !(c->mp_rtol >= 1e-7 && c->mp_rtol < 1.0))
@@ -518,6 +519,7 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
     ctx->F.R = c->R; ctx->F.cp = c->cp; ctx->F.g = c->g; ctx->F.p0 = c->p0;
     ctx->F.mu = c->mu; ctx->F.nuh = c->mu / c->Pr; ctx->F.dt = c->dt; ctx->F.idt = 1.0 / c->dt;
     ctx->F.omega = kOmega;
+    ctx->F.k_lagged = (c->reading_flags & GEA_READING_K_LAGGED) ? 1 : 0;
     ctx->mixed = (c->flags & GEA_FLAG_MIXED) != 0;
     if (cudaGetDevice(&ctx->device) != cudaSuccess) {
         delete ctx;
@@ -544,7 +546,7 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
     const Geom &G = ctx->G;
     const size_t cell = arr_bytes(G, G.nz), fz = arr_bytes(G, G.nz + 1);
     size_t total = 0;
-    total += 2 * (9 * cell + fz);                  // two states (phiz has nz+1 rows)
+    total += 2 * (10 * cell + fz);                 // two states (phiz has nz+1 rows)
     total += 33 * cell + 2 * fz;                   // scratch (Dz has nz+1 rows)
     total += 4 * cell;                             // staging for conservative fields
     total += 2 * cell + round_up(G.nz * sizeof(double), 256);   // theta_bar, theta'
@@ -582,6 +584,7 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
         State &S = ctx->S[s];
         S.rho = take(cell); S.u = take(cell); S.w = take(cell); S.T = take(cell); S.h = take(cell);
         S.p = take(cell); S.pp = take(cell); S.pold = take(cell); S.phix = take(cell); S.phiz = take(fz);
+        S.Kold = take(cell);
     }
     Stencil9 &T = ctx->T;
     T.cC = take(cell); T.cE1 = take(cell); T.cE2 = take(cell); T.cW1 = take(cell); T.cW2 = take(cell);
@@ -688,10 +691,14 @@ int gea_set_state(gea_ctx *ctx, const gea_state_view *v)
         launch_derive(G, ctx->F, st, st + cellw, st + 2 * cellw, st + 3 * cellw, S, ctx->sc, ctx->stream);
         CK(cudaGetLastError());
     } else if (v->kind == GEA_STATE_FULL) {
-        const double *src[10] = {v->rho, v->u, v->w, v->T, v->h, v->p, v->pp, v->pold, v->phix, v->phiz};
-        double *dst[10] = {S.rho, S.u, S.w, S.T, S.h, S.p, S.pp, S.pold, S.phix, S.phiz};
-        for (int f = 0; f < 10; ++f) {
+        const double *src[11] = {v->rho, v->u, v->w, v->T, v->h, v->p, v->pp, v->pold, v->phix, v->phiz,
+                                 v->Kold};
+        double *dst[11] = {S.rho, S.u, S.w, S.T, S.h, S.p, S.pp, S.pold, S.phix, S.phiz, S.Kold};
+        // K^{n-1} belongs to the state only in the literal reading of eq. step3_sd
+        const int nf = ctx->F.k_lagged ? 11 : 10;
+        for (int f = 0; f < nf; ++f)
             if (!src[f]) return fail(ctx, GEA_ERR_INVAL, "null field %d", f);
+        for (int f = 0; f < nf; ++f) {
             const int cols = f == 8 ? nx + 1 : nx, rows = f == 9 ? nz + 1 : nz;
             int rc = copy_in(ctx, dst[f], src[f], cols, rows);
             if (rc) return rc;
@@ -785,9 +792,10 @@ int gea_get_state(gea_ctx *ctx, gea_state_view *v)
     const int nx = G.nx, nz = G.nz;
     const State &S = ctx->S[current_slot(ctx, h)];
     if (v->kind == GEA_STATE_FULL) {
-        double *dst[10] = {v->rho, v->u, v->w, v->T, v->h, v->p, v->pp, v->pold, v->phix, v->phiz};
-        const double *src[10] = {S.rho, S.u, S.w, S.T, S.h, S.p, S.pp, S.pold, S.phix, S.phiz};
-        for (int f = 0; f < 10; ++f) {
+        double *dst[11] = {v->rho, v->u, v->w, v->T, v->h, v->p, v->pp, v->pold, v->phix, v->phiz, v->Kold};
+        const double *src[11] = {S.rho, S.u, S.w, S.T, S.h, S.p, S.pp, S.pold, S.phix, S.phiz, S.Kold};
+        const int nf = ctx->F.k_lagged ? 11 : 10;
+        for (int f = 0; f < nf; ++f) {
             if (!dst[f]) continue;
             const int cols = f == 8 ? nx + 1 : nx, rows = f == 9 ? nz + 1 : nz;
             if ((rc = copy_out(ctx, dst[f], src[f], cols, rows))) return rc;

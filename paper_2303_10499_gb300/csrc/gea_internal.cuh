@@ -41,12 +41,14 @@ struct Phys {
     double R, cp, g, p0, mu, nuh, dt, idt;   // nuh = mu / Pr
     double omega;                            // damped-Jacobi weight of the smoother
     double les_d2;                           // Smagorinsky (cs Delta)^2; 0: constant viscosity
+    int k_lagged;                            // GEA_READING_K_LAGGED: K^{n-1} in eq. step3_sd
 };
 
 // Persistent state of one time level (Section 3's solution tuple plus the
-// face mass fluxes phi and p^{n-1}).
+// face mass fluxes phi, p^{n-1} and, for the literal reading of eq.
+// step3_sd, K^{n-1}).
 struct State {
-    double *rho, *u, *w, *T, *h, *p, *pp, *pold, *phix, *phiz;
+    double *rho, *u, *w, *T, *h, *p, *pp, *pold, *phix, *phiz, *Kold;
 };
 
 // One multigrid level of the Helmholtz operator

@@ -47,6 +47,7 @@ __global__ void k_derive(Geom G, Phys F, const double *__restrict__ rho,
     S.p[q] = p;
     S.pp[q] = p + r * F.g * z;
     S.pold[q] = p;
+    S.Kold[q] = K;   // K^{-1} := K^0
     S.phix[k * G.P + i] = i > 0 ? 0.5 * (rhou[q - 1] + rhou[q]) * G.dz : 0.0;
     if (i == G.nx - 1) S.phix[k * G.P + G.nx] = 0.0;
     S.phiz[k * G.P + i] = k > 0 ? 0.5 * (rhow[q - G.P] + rhow[q]) * G.dx : 0.0;

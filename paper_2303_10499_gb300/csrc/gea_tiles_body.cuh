@@ -494,7 +494,8 @@ __device__ __forceinline__ void ph_enth_rhs_t(const StepArgs &a, const MixedArgs
         c -= ld(&S.phiz[q]) * (7.0 * (K[y - 1][x] + K[y][x]) - (K[y - 2][x] + K[y + 1][x]));
         c *= G.iV * (1.0 / 12.0);
         const double rq = ld(&S.rho[q]), u = ld(&S.u[q]), w = ld(&S.w[q]), h = ld(&S.h[q]);
-        const double Kn = 0.5 * (u * u + w * w);
+        // b~_e carries rho^n K^n, or rho^n K^{n-1} in the literal reading
+        const double Kn = F.k_lagged ? ld(&S.Kold[q]) : 0.5 * (u * u + w * w);
         const double rho1 = ld(&a.rho1[q]);
         const double be = (rq * h + rq * Kn - ld(&S.pold[q])) * F.idt;
         const double bh = be - rho1 * K[y][x] * F.idt - c + ld(&S.p[q]) * F.idt - rho1 * F.g * w1c;
@@ -1028,7 +1029,8 @@ __device__ __forceinline__ void ph_guess_apply(const LevelT<R> &L, const float *
 
 // Flux and velocity correction: F_f = D_f (H_f - G_f) with
 // G_f = (p'_b - p'_a)/Delta - g z_f (rho2_b - rho2_a)/Delta; u = (dt/rho1)(H - G_cell);
-// p = p' - rho2 g z; rho = p / (R T^{n+1}) = p psi; phi = F |A|; p^{n-1} <- p^n.
+// p = p' - rho2 g z; rho = p / (R T^{n+1}) = p psi; phi = F |A|; p^{n-1} <- p^n
+// (and K^{n-1} <- K^n in the literal reading of eq. step3_sd).
 __device__ __forceinline__ void ph_correct(const StepArgs &a, double *sm, int bx, int bz)
 {
     const Geom &G = a.G;
@@ -1075,6 +1077,10 @@ __device__ __forceinline__ void ph_correct(const StepArgs &a, double *sm, int bx
         N.p[q] = pn;
         N.rho[q] = pn * ld(&a.psi[q]);
         N.pold[q] = ld(&a.S.p[q]);
+        if (F.k_lagged) {
+            const double un = ld(&a.S.u[q]), wn = ld(&a.S.w[q]);
+            N.Kold[q] = 0.5 * (un * un + wn * wn);   // K^{n-1} of the next step
+        }
     }
     __syncthreads();
 }

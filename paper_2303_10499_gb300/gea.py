@@ -25,7 +25,8 @@ FLAG_GRAPH, FLAG_MIXED, FLAG_KEEP_R0 = 1, 2, 4
 MEM_HOST, MEM_DEVICE = 0, 1
 FIELDS = {"rho1": 0, "u1": 1, "w1": 2, "h1": 3, "rho2": 4, "Hx": 5, "Hz": 6, "b": 7,
           "Dx": 8, "Dz": 9, "hc": 10, "hax": 11, "haz": 12, "r0": 13}
-FULL_FIELDS = ("rho", "u", "w", "T", "h", "p", "pp", "pold", "phix", "phiz")
+FULL_FIELDS = ("rho", "u", "w", "T", "h", "p", "pp", "pold", "phix", "phiz", "Kold")
+READING_K_LAGGED = 1   # gea_constants.reading_flags: the literal K^{n-1} of eq. step3_sd
 # tile shapes of the persistent kernels (gea_set_tile_shape): cells in x by z
 TILE_SHAPES = {0: "32x8", 1: "16x16", 2: "64x4"}
 
@@ -45,13 +46,14 @@ class _Const(C.Structure):
                 ("mu", C.c_double), ("Pr", C.c_double), ("dt", C.c_double),
                 ("n_corr", C.c_int32), ("jac_rtol", C.c_double), ("jac_maxit", C.c_int32),
                 ("cg_rtol", C.c_double), ("cg_maxit", C.c_int32),
-                ("mg_min_cells", C.c_int32), ("flags", C.c_int32), ("mp_rtol", C.c_double), ("cs", C.c_double)]
+                ("mg_min_cells", C.c_int32), ("flags", C.c_int32), ("mp_rtol", C.c_double), ("cs", C.c_double),
+                ("reading_flags", C.c_uint32)]
 
 
 class _View(C.Structure):
     _fields_ = [("kind", C.c_int32), ("mem", C.c_int32)] + [
         (n, C.c_void_p) for n in ("rho", "rhou", "rhow", "rhoe", "u", "w", "T", "h", "p", "pp",
-                                  "pold", "phix", "phiz")]
+                                  "pold", "phix", "phiz", "Kold")]
 
 
 class _Grid3(C.Structure):
@@ -174,7 +176,8 @@ class Solver:
             (FLAG_KEEP_R0 if keep_r0 else 0)
         c = _Const(const.R, const.cp, const.g, const.p0, const.mu, const.Pr, const.dt,
                    const.n_corr, const.jac_rtol, const.jac_maxit, const.cg_rtol, const.cg_maxit,
-                   mg_min_cells, flags, mp_rtol, getattr(const, "cs", 0.0))
+                   mg_min_cells, flags, mp_rtol, getattr(const, "cs", 0.0),
+                   getattr(const, "reading_flags", 0))
         h = C.c_void_p()
         rc = self.lib.gea_create(C.byref(g), C.byref(c), C.byref(h))
         if rc != GEA_OK:
@@ -219,7 +222,8 @@ class Solver:
         v.kind = STATE_FULL
         v.mem = MEM_DEVICE if _is_device(state["rho"]) else MEM_HOST
         for k in FULL_FIELDS:
-            setattr(v, k, _addr(state[k]))
+            # Kold (K^{n-1}) is part of the state only with READING_K_LAGGED
+            setattr(v, k, _addr(state[k]) if k in state else None)
         self._check(self.lib.gea_set_state(self.h, C.byref(v)))
 
     def get_full(self, out: Optional[Dict] = None) -> Dict[str, np.ndarray]:
@@ -566,7 +570,8 @@ class Solver3D:
         g = _Grid3(grid.nx, grid.ny, grid.nz, grid.lx, grid.ly, grid.lz)
         c = _Const(const.R, const.cp, const.g, const.p0, const.mu, const.Pr, const.dt,
                    const.n_corr, const.jac_rtol, const.jac_maxit, const.cg_rtol, const.cg_maxit,
-                   mg_min_cells, FLAG_MIXED if mixed else 0, mp_rtol, getattr(const, "cs", 0.0))
+                   mg_min_cells, FLAG_MIXED if mixed else 0, mp_rtol, getattr(const, "cs", 0.0),
+                   getattr(const, "reading_flags", 0))
         h = C.c_void_p()
         rc = self.lib.gea3d_create(C.byref(g), C.byref(c), C.byref(h))
         if rc != GEA_OK:

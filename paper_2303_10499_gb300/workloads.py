@@ -82,6 +82,7 @@ class Constants:
     cg_rtol: float = 1e-17
     cg_maxit: int = 400
     cs: float = 0.0        # Smagorinsky constant (0: constant viscosity only)
+    reading_flags: int = 0  # 1: the literal K^{n-1} of eq. step3_sd (default K^n)
 
     @property
     def cv(self) -> float:

@@ -425,3 +425,44 @@ def test_theta_prime_of_the_bubble(oracle_mod):
     th0 = W.bubble_perturbation(wl.grid, "cosine", 2.0, 2000.0, 10000.0, 2000.0)
     np.testing.assert_allclose(th, wl.theta_bar[:, None] * th0 / 300.0, atol=1e-10)
     assert 1.98 < th.max() < 2.0
+
+
+def test_lagged_kinetic_energy_reading(oracle_mod):
+    """The literal reading of eq. step3_sd (reading flag 1): b~_e carries
+    rho^n K^{n-1} instead of rho^n K^n, with K^{-1} := K^0.
+    (a) The first step is the default reading's, bit for bit.
+    (b) On a later step the enthalpy right-hand side differs from the
+        default's by exactly rho^n (K^{n-1} - K^n) / dt (sign and factor of
+        the one changed term), all else equal.
+    (c) The reading keeps mass conservation and the rest atmosphere."""
+    import dataclasses
+    grid = W.Grid(24, 16, 24 * 40.0, 16 * 30.0)
+    c0 = W.Constants(dt=0.2, mu=1.5)
+    c1 = dataclasses.replace(c0, reading_flags=oracle_mod.READING_K_LAGGED)
+    wl = W.random_flow(grid, c0, seed=12, uamp=4.0, thamp=2.0)
+    o0, o1 = oracle_mod.Oracle(grid, c0), oracle_mod.Oracle(grid, c1)
+    a, b = o0.derive(wl.fields), o1.derive(wl.fields)
+    assert np.array_equal(a["Kold"], 0.5 * (a["u"] ** 2 + a["w"] ** 2))
+    o0.step(a, 1)
+    o1.step(b, 1)
+    for k in oracle_mod.oracle.STATE_FIELDS:
+        assert np.array_equal(a[k], b[k]), k
+    # (b): from the same state after one step, K^{n-1} != K^n
+    s1, s0 = b.copy(), b.copy()
+    Kn = 0.5 * (b["u"] ** 2 + b["w"] ** 2)
+    assert np.abs(b["Kold"] - Kn).max() > 1e-3
+    _, d1 = o1.step(s1, 1, dump=True)
+    _, d0 = o0.step(s0, 1, dump=True)
+    expect = b["rho"] * (b["Kold"] - Kn) / c0.dt
+    assert np.abs((d1["bh"] - d0["bh"]) - expect).max() <= 1e-14 * np.abs(d0["bh"]).max()
+    assert np.abs(s1["u"] - s0["u"]).max() > 0.0   # the reading changes the flow
+    # (c)
+    _, m0, _ = o1.diagnostics(b, np.full(grid.nz, 300.0))
+    o1.step(b, 10)
+    _, m1, _ = o1.diagnostics(b, np.full(grid.nz, 300.0))
+    assert abs(m1 - m0) / m0 < 1e-13
+    rest = W.rest_atmosphere(W.Grid(32, 16, 3200.0, 1600.0), c1)
+    orr = oracle_mod.Oracle(rest.grid, c1)
+    sr = orr.derive(rest.fields)
+    orr.step(sr, 20)
+    assert np.abs(sr["u"]).max() < 1e-10 and np.abs(sr["w"]).max() < 1e-10
