@@ -102,6 +102,8 @@ def parse():
     ap.add_argument("--three-d", default=None, metavar="WORKLOAD",
                     help="the three-dimensional step on a 3D workload (bubble3d_512x512x256: the "
                          "10 km cube bubble, 67M cells)")
+    ap.add_argument("--dts", type=lambda t: [float(x) for x in t.split(",")], default=[0.05, 0.2, 0.5],
+                    help="--learned: time steps of the 4096 x 2048 runs (comma separated)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle baseline sample")
     return ap.parse_args()
@@ -419,12 +421,28 @@ def matched_error(gea, wl, steps):
             "rel_l2": rel, "against": "FP64 GPU step (equal to the FP64 oracle to <= 1e-10 rel. L2)"}
 
 
+def learned_training_set(W, learned, steps=8, every=2):
+    """Pressure systems (the first corrector's r0 and operator, every `every`
+    steps of `steps`) of the configurations the learned stage is trained on:
+    the 160 x 80 and 640 x 320 bubbles and LES members on 100^2, 200^2 and
+    400^2 cells -- none of them the 4096 x 2048 grid it is evaluated on."""
+    wls = [W.get("bubble160x80"), W.get("bubble640x320")] + [W.les_member(n) for n in (100, 200, 400)]
+    samples = []
+    for wl in wls:
+        samples += learned.collect(wl, steps, every=every, const=wl.const)
+    return samples, [wl.name for wl in wls]
+
+
 def run_learned(args):
-    """Plain MG-CG against the learned initial guess, and against flexible CG
-    with the network as the preconditioner, on the 4096 x 2048 bubble with
-    pressure solves to 1e-8 (relative to ||b||): all timed like the main line,
-    after the network is trained on the FP64 solver's own pressure systems of
-    the first 8 steps (training time reported separately)."""
+    """The learned pressure stage on the 4096 x 2048 bubble, pressure solves to
+    1e-8 of ||b||, for each time step in --dts (the configuration leaves dt
+    open; the Helmholtz operator's Laplacian part grows with dt^2, which is
+    what gives a learned start something to do). Per dt, timed like the main
+    line: plain FP64 MG-CG, the learned initial guess, flexible CG with the
+    network stage, the mixed-precision step alone and with the learned
+    guess. Two networks: one trained on held-out configurations (the smaller
+    bubbles and the LES members, none on this grid) and one trained on the
+    first steps of this run itself (in distribution), for reference."""
     import copy
     import numpy as np
     import torch
@@ -435,63 +453,96 @@ def run_learned(args):
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
     B.build()
-    wl = W.get("bubble4096x2048")
-    const = copy.copy(wl.const)
-    const.cg_rtol = 1e-8
-    t0 = time.perf_counter()
-    samples = learned.collect(wl, 8, every=2, const=wl.const)
-    t_collect = time.perf_counter() - t0
-    net = gea.Net(8, 1024, 1024, relu=False)
-    net.set_params(learned.initial_params(1) * 0.5)
-    tr = learned.train(net, samples, 400, n=8, h=256, w=256, lr=2e-3)
+    base = W.get("bubble4096x2048")
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-    arms = {}
-    for use in (0, 1, 2):
-        s = gea.Solver(wl.grid, const, stream=stream, graph=True)
-        s.set_conservative(wl.fields)
-        if use:
-            s.attach_net(net, use)
+
+    def train_net(samples, crop, batch, iters):
+        net = gea.Net(8, 1024, 1024, relu=False)
+        net.set_params(learned.initial_params(1) * 0.5)
+        tr = learned.train(net, samples, iters, n=batch, h=crop, w=crop, lr=2e-3)
+        return net, {"samples": len(samples), "iterations": iters, "batch": f"{batch} x {crop} x {crop} crops",
+                     "seconds": tr["seconds"], "loss_first": tr["losses"][0],
+                     "loss_last20": float(np.mean(tr["losses"][-20:]))}
+
+    t0 = time.perf_counter()
+    held_samples, held_names = learned_training_set(W, learned)
+    t_collect = time.perf_counter() - t0
+    net_held, tr_held = train_net(held_samples, 64, 8, 400)
+    tr_held.update({"collect_s": t_collect, "workloads": held_names})
+    del held_samples
+
+    def arm(const, mixed, net, mode):
+        s = gea.Solver(base.grid, const, stream=stream, graph=True, mixed=mixed)
+        s.set_conservative(base.fields)
+        if net is not None:
+            s.attach_net(net, mode)
         ms, launches, clocks = timed_steps(s, stream, flush, args.steps, args.warmup, world, local)
         its = []
-        for _ in range(5):
+        for _ in range(3):
             s.step(1)
             its.append(s.stats()["cg_iters"])
         pms = pressure_ms(s)
-        prof = s.profile_step()
-        th, _, _ = s.diagnostics(wl.theta_bar)
-        arms[use] = {"value": wl.grid.cells * args.steps / (sum(ms) / 1e3), "unit": UNIT,
-                     "ms_per_step": statistics.mean(ms), "pressure_solve_ms_per_step": pms,
-                     "cg_iters_per_step": its, "gpu_launches": int(launches), "clocks": clocks,
-                     "kernel_ms_eager_step": {k: round(v["ms"], 4) for k, v in prof.items()
-                                              if k in ("net_forward", "guess_in", "guess_dots",
-                                                       "guess_apply", "cg_pspmv", "cg_update_down",
-                                                       "mg_up", "mg_down", "helm_rhs", "fcg_stage_in",
-                                                       "fcg_stage_out", "fcg_pspmv", "fcg_update")},
-                     "_theta": th}
+        th, _, _ = s.diagnostics(base.theta_bar)
+        n_steps = args.warmup + args.steps + 3 + 5
         s.close()
-    th0 = arms[0].pop("_theta")
-    dth = float(np.abs(arms[1].pop("_theta") - th0).max())
-    dth2 = float(np.abs(arms[2].pop("_theta") - th0).max())
+        return {"value": base.grid.cells * args.steps / (sum(ms) / 1e3), "unit": UNIT,
+                "ms_per_step": statistics.mean(ms), "pressure_solve_ms_per_step": pms,
+                "cg_iters_per_step": its, "gpu_launches": int(launches), "clocks": clocks,
+                "steps_before_theta": n_steps, "_theta": th}
+
+    per_dt = {}
+    for dt in args.dts:
+        const = copy.copy(base.const)
+        const.dt = dt
+        const.cg_rtol = 1e-8
+        # the in-distribution reference network: trained on this run's own
+        # first steps (FP64 solver, parity tolerance) at this dt
+        own_const = copy.copy(base.const)
+        own_const.dt = dt
+        own_const.cg_rtol = 1e-10   # the first corrector's r0 hardly depends on it
+        own = learned.collect(base, 8, every=2, const=own_const)
+        net_own, tr_own = train_net(own, 256, 8, 400)
+        del own
+        arms = {
+            "plain_fp64": arm(const, False, None, 0),
+            "learned_guess_fp64": arm(const, False, net_held, 1),
+            "network_fcg_fp64": arm(const, False, net_held, 2),
+            "mixed": arm(const, True, None, 0),
+            "mixed_learned_guess": arm(const, True, net_held, 1),
+            "learned_guess_fp64_own_net": arm(const, False, net_own, 1),
+            "mixed_learned_guess_own_net": arm(const, True, net_own, 1),
+        }
+        net_own.close()
+        th0 = arms["plain_fp64"]["_theta"]
+        v0 = arms["plain_fp64"]["value"]
+        for k, a in arms.items():
+            a["max_abs_dtheta_K_vs_plain_fp64"] = float(np.abs(a["_theta"] - th0).max())
+            a["speedup_vs_plain_fp64"] = a["value"] / v0
+        for a in arms.values():
+            a.pop("_theta")
+        ratio = 2 * dt * dt * base.const.R * 300.0 * (1 / base.grid.dx ** 2 + 1 / base.grid.dz ** 2)
+        per_dt[f"{dt:g}"] = {"dt": dt, "laplacian_to_diagonal_ratio": ratio, "arms": arms,
+                             "own_net_training": tr_own}
+    best = max(((d, k, a) for d, v in per_dt.items() for k, a in v["arms"].items()
+                if "learned" in k or "fcg" in k), key=lambda t: t[2]["speedup_vs_plain_fp64"])
+    first = per_dt[f"{args.dts[0]:g}"]["arms"]
     res = {
-        "metric": METRIC, "value": arms[1]["value"], "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": arms[1]["ms_per_step"],
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+bf16",
+        "metric": METRIC, "value": first["mixed_learned_guess"]["value"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": first["mixed_learned_guess"]["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32+bf16",
         "data": "synthetic",
-        "config": {"workload": wl.name + " learned initial guess", "grid": [wl.grid.nx, wl.grid.nz],
-                   "cg_rtol": const.cg_rtol, "network": "4-level U-Net, 16 base channels, linear, "
+        "config": {"workload": base.name + " learned pressure stage", "grid": [base.grid.nx, base.grid.nz],
+                   "dts": list(args.dts), "cg_rtol": 1e-8, "value_arm": f"mixed_learned_guess at dt {args.dts[0]:g}",
+                   "network": "4-level U-Net, 16 base channels, linear, "
                    f"{gea.net_param_count()} parameters, bfloat16 tensor-core layers",
                    "l2": "flushed between timed steps (256 MB write, untimed)"},
-        "plain_mg_cg": arms[0], "learned_guess": arms[1],
-        "speedup_vs_plain": arms[1]["value"] / arms[0]["value"],
-        "max_abs_dtheta_K_learned_vs_plain": dth,
-        "network_preconditioner_fcg": arms[2],
-        "fcg_speedup_vs_plain": arms[2]["value"] / arms[0]["value"],
-        "max_abs_dtheta_K_fcg_vs_plain": dth2,
-        "training": {"samples": len(samples), "collect_s": t_collect, "iterations": 400,
-                     "batch": "8 x 256 x 256 crops", "seconds": tr["seconds"],
-                     "loss_first": tr["losses"][0], "loss_last20": float(np.mean(tr["losses"][-20:]))},
+        "per_dt": per_dt,
+        "held_out_training": tr_held,
+        "best_learned_arm": {"dt": best[0], "arm": best[1], "speedup_vs_plain_fp64": best[2]["speedup_vs_plain_fp64"],
+                             "max_abs_dtheta_K_vs_plain_fp64": best[2]["max_abs_dtheta_K_vs_plain_fp64"]},
     }
+    net_held.close()
     if rank == 0:
         print(json.dumps(res), flush=True)
 
