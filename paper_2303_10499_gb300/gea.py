@@ -226,16 +226,23 @@ class Solver:
             setattr(v, k, _addr(state[k]) if k in state else None)
         self._check(self.lib.gea_set_state(self.h, C.byref(v)))
 
+    def full_fields(self):
+        """The fields of this context's FULL state: K^{n-1} (Kold) belongs to it
+        only with READING_K_LAGGED."""
+        lagged = getattr(self.const, "reading_flags", 0) & READING_K_LAGGED
+        return FULL_FIELDS if lagged else FULL_FIELDS[:-1]
+
     def get_full(self, out: Optional[Dict] = None) -> Dict[str, np.ndarray]:
         nx, nz = self.grid.nx, self.grid.nz
+        fields = self.full_fields()
         if out is None:
-            out = {k: np.empty((nz, nx)) for k in FULL_FIELDS}
+            out = {k: np.empty((nz, nx)) for k in fields}
             out["phix"] = np.empty((nz, nx + 1))
             out["phiz"] = np.empty((nz + 1, nx))
         v = _View()
         v.kind = STATE_FULL
         v.mem = MEM_DEVICE if _is_device(out["rho"]) else MEM_HOST
-        for k in FULL_FIELDS:
+        for k in fields:
             setattr(v, k, _addr(out[k]))
         self._check(self.lib.gea_get_state(self.h, C.byref(v)))
         return out
