@@ -128,7 +128,10 @@ def test_weights_and_autotune(gea):
     assert nb[2] == max(nb) and nb[2] > 10 * max(nb[:2])
     E.close()
     E, rep = ensemble.autotune(ss, stream=torch.cuda.current_stream(), betas=(0.0, 1.0), trial_steps=1)
-    assert set(rep["ms_per_step_by_beta"]) == {"0.0", "1.0"}
+    by = rep["ms_per_step_by_shape_and_beta"]
+    assert set(by) == {"32x8", "16x16", "64x4"} and all(set(v) == {"0.0", "1.0"} for v in by.values())
+    assert rep["tile_shape"] in by
     E.step(1)
     steps = ss[0].stats()["steps_done"]
-    assert steps == 1 + 2 + 1 and all(s.stats()["status"] == 0 for s in ss)
+    # one step to measure the iterations, one per shape and weight, one more
+    assert steps == 1 + 3 * 2 + 1 and all(s.stats()["status"] == 0 for s in ss)
