@@ -104,8 +104,6 @@ def parse():
                          "10 km cube bubble, 67M cells)")
     ap.add_argument("--dts", type=lambda t: [float(x) for x in t.split(",")], default=[0.05, 0.2, 0.5],
                     help="--learned: time steps of the 4096 x 2048 runs (comma separated)")
-    ap.add_argument("--train-iters", type=int, default=400,
-                    help="--learned: Adam iterations of each network's training")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle baseline sample")
     return ap.parse_args()
@@ -470,7 +468,7 @@ def run_learned(args):
     t0 = time.perf_counter()
     held_samples, held_names = learned_training_set(W, learned)
     t_collect = time.perf_counter() - t0
-    net_held, tr_held = train_net(held_samples, 64, 8, args.train_iters)
+    net_held, tr_held = train_net(held_samples, 64, 8, 400)
     tr_held.update({"collect_s": t_collect, "workloads": held_names})
     del held_samples
 
@@ -504,7 +502,7 @@ def run_learned(args):
         own_const.dt = dt
         own_const.cg_rtol = 1e-10   # the first corrector's r0 hardly depends on it
         own = learned.collect(base, 8, every=2, const=own_const)
-        net_own, tr_own = train_net(own, 256, 8, args.train_iters)
+        net_own, tr_own = train_net(own, 256, 8, 400)
         del own
         arms = {
             "plain_fp64": arm(const, False, None, 0),

@@ -349,35 +349,16 @@ __device__ bool run_step(const PersistArgs &P, const StepArgs &a, const Grp &g, 
                 else rbar<1>(g, acc, red, a.partials, [&](const double (&t)[1]) { fin_rz(sc, t); });
             }
         };
-        auto cap = [&] {
-            if (!sc->done[LOOP_CG] && !sc->status && sc->cg_it >= P.cg_maxit) sc->status = GEA_ERR_NOCONV;
-        };
-        if (nlev == 1) {
-            // single-level preconditioner: CG in the single-reduction form of
-            // Chronopoulos and Gear, one phase and one reduction per
-            // iteration (ph_cg_fused). Its two-buffer vectors borrow arrays
-            // that are idle during the pressure solve: w in e and q, s in
-            // the momentum right-hand sides b_u, b_w (rebuilt every step).
-            double *Wb[2] = {L[0].e, a.q};
-            double *Sb[2] = {a.bu, a.bw};
-            for (int j = 0; !stop(sc) && !sc->done[LOOP_CG]; ++j) {
-                const bool first = j == 0;
-                const double alpha = sc->alpha, beta = sc->beta;
-                double acc[3] = {0.0, 0.0, 0.0};
-                for_tiles(g, G, [&](int bx, int bz) {
-                    ph_cg_fused<double>(L[0], res_of(L[0], j), res_of(L[0], j + 1), Wb[j & 1], Wb[(j + 1) & 1],
-                                        Sb[j & 1], Sb[(j + 1) & 1], L[0].e2, a.p0, a.N.pp, alpha, beta, first,
-                                        sm, bx, bz, acc);
-                });
-                rbar<3>(g, acc, red, a.partials, [&](const double (&t)[3]) {
-                    fin_cg_fused(sc, t, a.cg_rtol2, first);
-                    if (!first) cap();
-                });
+        if (!stop(sc) && !sc->done[LOOP_CG]) {
+            if (nlev == 1) {
+                double acc[1] = {0.0};
+                for_tiles(g, G, [&](int bx, int bz) { ph_mg_single(L[0], L[0].e2, sm, bx, bz, acc); });
+                rbar<1>(g, acc, red, a.partials, [&](const double (&t)[1]) { fin_rz(sc, t); });
+            } else {
+                vcycle_levels(0);
             }
-        } else if (!stop(sc) && !sc->done[LOOP_CG]) {
-            vcycle_levels(0);
         }
-        while (nlev > 1 && !stop(sc) && !sc->done[LOOP_CG]) {
+        while (!stop(sc) && !sc->done[LOOP_CG]) {
             // p = z + beta p, q = A p
             const int it = sc->cg_it;
             const double *pold = (it & 1) ? a.p1 : a.p0;
@@ -390,16 +371,33 @@ __device__ bool run_step(const PersistArgs &P, const StepArgs &a, const Grp &g, 
             }
             // x += alpha p, r -= alpha q, with the first step of the next V-cycle
             const double alpha = sc->alpha;
-            double acc[1] = {0.0};
-            for_tiles(g, G, [&](int bx, int bz) {
-                ph_update_down<double>(L[0], L[1], a.q, res_of(L[0], it), res_of(L[0], it + 1), a.N.pp, pnew,
-                                       alpha, a.F.omega, sm, bx, bz, acc);
-            });
-            rbar<1>(g, acc, red, a.partials, [&](const double (&t)[1]) {
-                fin_update(sc, t, a.cg_rtol2);
-                cap();
-            });
-            if (!stop(sc) && !sc->done[LOOP_CG]) vcycle_levels(1);
+            auto cap = [&] {
+                if (!sc->done[LOOP_CG] && !sc->status && sc->cg_it >= P.cg_maxit) sc->status = GEA_ERR_NOCONV;
+            };
+            if (nlev == 1) {
+                double acc[2] = {0.0, 0.0};
+                for_tiles(g, G, [&](int bx, int bz) {
+                    ph_update_single<double>(L[0], a.q, res_of(L[0], it), res_of(L[0], it + 1), a.N.pp,
+                                             pnew, alpha, sm, bx, bz, acc);
+                });
+                rbar<2>(g, acc, red, a.partials, [&](const double (&t)[2]) {
+                    const double t0[1] = {t[0]}, t1[1] = {t[1]};
+                    fin_update(sc, t0, a.cg_rtol2);
+                    fin_rz(sc, t1);
+                    cap();
+                });
+            } else {
+                double acc[1] = {0.0};
+                for_tiles(g, G, [&](int bx, int bz) {
+                    ph_update_down<double>(L[0], L[1], a.q, res_of(L[0], it), res_of(L[0], it + 1), a.N.pp,
+                                           pnew, alpha, a.F.omega, sm, bx, bz, acc);
+                });
+                rbar<1>(g, acc, red, a.partials, [&](const double (&t)[1]) {
+                    fin_update(sc, t, a.cg_rtol2);
+                    cap();
+                });
+                if (!stop(sc) && !sc->done[LOOP_CG]) vcycle_levels(1);
+            }
         }
         if (stop(sc)) return false;
         if (g.rank == 0 && tid_of() == 0) sc->press_ns += globaltimer() - t0;
@@ -554,32 +552,16 @@ __device__ bool run_step_mixed(const PersistArgs &P, const MixedPersist &X, cons
                 else rbar<1>(g, acc, red, a.partials, [&](const double (&t)[1]) { fin_rz(sc, t); });
             }
         };
-        auto cap = [&] {
-            if (!sc->done[LOOP_CG] && !sc->status && sc->cg_it >= P.cg_maxit) sc->status = GEA_ERR_NOCONV;
-        };
-        if (nlev == 1) {
-            // single-reduction CG as in the FP64 step; w in e and q, s in
-            // the momentum increments (consumed by Step 2)
-            float *Wb[2] = {L[0].e, m.q};
-            float *Sb[2] = {m.du[0], m.du[1]};
-            for (int j = 0; !stop(sc) && !sc->done[LOOP_CG]; ++j) {
-                const bool first = j == 0;
-                const double alpha = sc->alpha, beta = sc->beta;
-                float acc[3] = {0.0f, 0.0f, 0.0f};
-                for_tiles(g, G, [&](int bx, int bz) {
-                    ph_cg_fused<float>(L[0], res_of(L[0], j), res_of(L[0], j + 1), Wb[j & 1], Wb[(j + 1) & 1],
-                                       Sb[j & 1], Sb[(j + 1) & 1], L[0].e2, m.p0, m.x, alpha, beta, first, sm,
-                                       bx, bz, acc);
-                });
-                rbar<3>(g, acc, red, a.partials, [&](const double (&t)[3]) {
-                    fin_cg_fused(sc, t, m.tol2, first);
-                    if (!first) cap();
-                });
+        if (!stop(sc) && !sc->done[LOOP_CG]) {
+            if (nlev == 1) {
+                float acc[1] = {0.0f};
+                for_tiles(g, G, [&](int bx, int bz) { ph_mg_single<float>(L[0], L[0].e2, sm, bx, bz, acc); });
+                rbar<1>(g, acc, red, a.partials, [&](const double (&t)[1]) { fin_rz(sc, t); });
+            } else {
+                vcycle_levels(0);
             }
-        } else if (!stop(sc) && !sc->done[LOOP_CG]) {
-            vcycle_levels(0);
         }
-        while (nlev > 1 && !stop(sc) && !sc->done[LOOP_CG]) {
+        while (!stop(sc) && !sc->done[LOOP_CG]) {
             const int it = sc->cg_it;
             const float *pold = (it & 1) ? m.p1 : m.p0;
             float *pnew = (it & 1) ? m.p0 : m.p1;
@@ -592,16 +574,33 @@ __device__ bool run_step_mixed(const PersistArgs &P, const MixedPersist &X, cons
                 rbar<1>(g, acc, red, a.partials, [&](const double (&t)[1]) { fin_pq(sc, t); });
             }
             const double alpha = sc->alpha;
-            float acc[1] = {0.0f};
-            for_tiles(g, G, [&](int bx, int bz) {
-                ph_update_down<float>(L[0], L[1], m.q, res_of(L[0], it), res_of(L[0], it + 1), m.x, pnew, alpha,
-                                      a.F.omega, sm, bx, bz, acc);
-            });
-            rbar<1>(g, acc, red, a.partials, [&](const double (&t)[1]) {
-                fin_update(sc, t, m.tol2);
-                cap();
-            });
-            if (!stop(sc) && !sc->done[LOOP_CG]) vcycle_levels(1);
+            auto cap = [&] {
+                if (!sc->done[LOOP_CG] && !sc->status && sc->cg_it >= P.cg_maxit) sc->status = GEA_ERR_NOCONV;
+            };
+            if (nlev == 1) {
+                float acc[2] = {0.0f, 0.0f};
+                for_tiles(g, G, [&](int bx, int bz) {
+                    ph_update_single<float>(L[0], m.q, res_of(L[0], it), res_of(L[0], it + 1), m.x, pnew, alpha,
+                                            sm, bx, bz, acc);
+                });
+                rbar<2>(g, acc, red, a.partials, [&](const double (&t)[2]) {
+                    const double t0[1] = {t[0]}, t1[1] = {t[1]};
+                    fin_update(sc, t0, m.tol2);
+                    fin_rz(sc, t1);
+                    cap();
+                });
+            } else {
+                float acc[1] = {0.0f};
+                for_tiles(g, G, [&](int bx, int bz) {
+                    ph_update_down<float>(L[0], L[1], m.q, res_of(L[0], it), res_of(L[0], it + 1), m.x, pnew,
+                                          alpha, a.F.omega, sm, bx, bz, acc);
+                });
+                rbar<1>(g, acc, red, a.partials, [&](const double (&t)[1]) {
+                    fin_update(sc, t, m.tol2);
+                    cap();
+                });
+                if (!stop(sc) && !sc->done[LOOP_CG]) vcycle_levels(1);
+            }
         }
         if (stop(sc)) return false;
         // p' += dp, then the FP64 correction

@@ -42,11 +42,10 @@ constexpr int kT1 = (BZ + 2) * (BX + 2);   // doubles of a halo-1 tile
 constexpr int kT2 = (BZ + 4) * (BX + 4);   // doubles of a halo-2 tile
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
 // the largest phase footprint: four halo-1 tiles (pressure right-hand
-// side), three halo-2 tiles (enthalpy right-hand side), two halo-2 tiles and
-// a halo-1 tile (single-reduction CG), two halo-1 tiles and the x- and
-// z-face rows (EOS, correction) or a tile of residuals (restriction)
-constexpr int kTileSmem = cmax(cmax(cmax(4 * kT1, 3 * kT2), 2 * kT2 + kT1),
-                               2 * kT1 + cmax(BZ * (BX + 1) + (BZ + 1) * BX, BZ * BX));
+// side), three halo-2 tiles (enthalpy right-hand side), two halo-1 tiles and
+// the x- and z-face rows (EOS, correction) or a tile of residuals (restriction)
+constexpr int kTileSmem =
+    cmax(cmax(4 * kT1, 3 * kT2), 2 * kT1 + cmax(BZ * (BX + 1) + (BZ + 1) * BX, BZ * BX));
 
 template <int H, class R = double>
 __device__ __forceinline__ Tile<H, R> &tile_at(double *sm, int slot)
@@ -868,93 +867,6 @@ __device__ __forceinline__ void ph_mg_single(const LevelT<R> &f, R *out, double 
 
 // ---- CG vector steps ----
 
-// One iteration of preconditioned conjugate gradients in the
-// single-reduction form of Chronopoulos and Gear, for the single-level
-// preconditioner M (two damped Jacobi sweeps from zero, z = e + W(r - A e)
-// with e = W r, W = omega/d): both dot products of an iteration come from one
-// grid-wide reduction, so an iteration is one phase instead of two. With the
-// step length alpha_i and beta_i of the previous phase's dots:
-//   s_i = w_i + beta_i s_{i-1}          (s = A p, by recurrence)
-//   r_{i+1} = r_i - alpha_i s_i         on the tile and a halo of 2,
-//   u_{i+1} = M r_{i+1}                 on the tile and a halo of 1,
-//   w_{i+1} = A u_{i+1}                 on the tile,
-//   p_i = u_i + beta_i p_{i-1},  x_{i+1} = x_i + alpha_i p_i;
-// acc += (r_{i+1}.u_{i+1}, w_{i+1}.u_{i+1}, r_{i+1}.r_{i+1}). first: the start
-// of a solve (r_0 from the right-hand side phase): u_0 = M r_0, w_0 = A u_0,
-// s_{-1} = p_{-1} = 0 and the dots. r, w and s are read on the halo and
-// written on the tile, so each alternates between two buffers (in/out); u,
-// p and x are read and written at the thread's own cell only.
-template <class R>
-__device__ __forceinline__ void ph_cg_fused(const LevelT<R> &L, const R *rin, R *rout, const R *win, R *wout,
-                                            const R *sin, R *sout, R *u, R *p, R *x, double alpha_d,
-                                            double beta_d, bool first, double *sm, int bx, int bz,
-                                            R (&acc)[3])
-{
-    const Geom &G = L.G;
-    const R alpha = (R)alpha_d, beta = (R)beta_d;
-    Tile<2, R> &sr = tile_at<2, R>(sm, 0);   // r_{i+1}
-    Tile<2, R> &se = tile_at<2, R>(sm, 1);   // e = W r_{i+1}
-    Tile<1, R> &su = *reinterpret_cast<Tile<1, R> *>(reinterpret_cast<R *>(sm) + 2 * kT2);   // u_{i+1}
-    const int tid = threadIdx.x + threadIdx.y * BX;
-    {
-        const int i0 = bx * BX - 2, k0 = bz * BZ - 2;
-        constexpr int W2 = BX + 4, NE2 = (BZ + 4) * (BX + 4);
-        for (int e = tid; e < NE2; e += NTHREADS) {
-            const int tk = e / W2, ti = e - tk * W2;
-            const int i = i0 + ti, k = k0 + tk;
-            R rn = 0, ev = 0;
-            if (i >= 0 && i < G.nx && k >= 0 && k < G.nz) {
-                const int q = k * G.P + i;
-                rn = ld(&rin[q]);
-                if (!first) rn = fma(-alpha, fma(beta, ld(&sin[q]), ld(&win[q])), rn);
-                ev = ld(&L.wd[q]) * rn;
-            }
-            sr[tk][ti] = rn;
-            se[tk][ti] = ev;
-        }
-    }
-    __syncthreads();
-    {
-        const int i0 = bx * BX - 1, k0 = bz * BZ - 1;
-        constexpr int W1 = BX + 2, NE1 = (BZ + 2) * (BX + 2);
-        for (int e = tid; e < NE1; e += NTHREADS) {
-            const int tk = e / W1, ti = e - tk * W1;
-            const int i = i0 + ti, k = k0 + tk;
-            R uv = 0;
-            if (i >= 0 && i < G.nx && k >= 0 && k < G.nz) {
-                const int q = k * G.P + i;
-                const int y = tk + 1, xx = ti + 1;   // the cell in the halo-2 tiles
-                uv = fma(ld(&L.wd[q]), sr[y][xx] - helm_tile<2, R>(L, q, i, k, se, y, xx), se[y][xx]);
-            }
-            su[tk][ti] = uv;
-        }
-    }
-    __syncthreads();
-    int i, k;
-    if (cell_of(G, bx, bz, i, k)) {
-        const int q = cidx(G, i, k);
-        const int y = threadIdx.y + 1, xx = threadIdx.x + 1;
-        const R un = su[y][xx];
-        const R wn = helm_tile<1, R>(L, q, i, k, su, y, xx);
-        const R rn = sr[y + 1][xx + 1];
-        R sv = 0, pv = 0;
-        if (!first) {
-            sv = fma(beta, ld(&sin[q]), ld(&win[q]));
-            pv = fma(beta, ld(&p[q]), ld(&u[q]));
-            x[q] = fma(alpha, pv, ld(&x[q]));
-        }
-        sout[q] = sv;
-        p[q] = pv;
-        u[q] = un;
-        rout[q] = rn;
-        wout[q] = wn;
-        acc[0] = fma(rn, un, acc[0]);
-        acc[1] = fma(wn, un, acc[1]);
-        acc[2] = fma(rn, rn, acc[2]);
-    }
-    __syncthreads();
-}
-
 // p_new = z + beta p_old (computed once per tile cell) and q = A p_new;
 // acc += p.q.
 template <class R>
@@ -1262,35 +1174,6 @@ __device__ __forceinline__ void fin_update(Scal *sc, const double (&t)[1], doubl
     sc->cg_relres[c] = sc->b2 > 0.0 ? sqrt(t[0] / sc->b2) : 0.0;
     if (!isfinite(t[0])) sc->status = 5;
     else if (t[0] <= tol2 * sc->b2) sc->done[LOOP_CG] = 1;
-}
-
-// After a phase of ph_cg_fused, t = (gamma, delta, r.r) of the new residual:
-// the convergence test (not at the start, which the right-hand side phase
-// already tested), then the next step lengths of Chronopoulos and Gear,
-// beta = gamma / gamma_old, alpha = gamma / (delta - beta gamma / alpha_old)
-// (at the start beta = 0, alpha = gamma / delta). rz keeps gamma.
-__device__ __forceinline__ void fin_cg_fused(Scal *sc, const double (&t)[3], double tol2, bool first)
-{
-    const double g = t[0], dl = t[1];
-    if (!first) {
-        const double one[1] = {t[2]};
-        fin_update(sc, one, tol2);
-    }
-    if (!isfinite(g) || !isfinite(dl)) {
-        sc->status = GEA_ERR_NONFINITE;
-        return;
-    }
-    if (sc->done[LOOP_CG]) return;
-    if (first || sc->rz == 0.0 || sc->alpha == 0.0) {
-        sc->beta = 0.0;
-        sc->alpha = dl != 0.0 ? g / dl : 0.0;
-    } else {
-        const double b = g / sc->rz;
-        const double den = dl - b * g / sc->alpha;
-        sc->beta = b;
-        sc->alpha = den != 0.0 ? g / den : 0.0;
-    }
-    sc->rz = g;
 }
 
 // the step length minimising the A-norm error along e: alpha = r.e / e.Ae
