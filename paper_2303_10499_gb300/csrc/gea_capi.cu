@@ -35,7 +35,8 @@ struct gea_ctx {
     State S[2];
     Stencil9 T;
     double *rho1, *dinvu, *dinvh, *bu, *bw, *ua, *wa, *ub, *wb, *bh, *ha, *hb, *rho2, *psi, *Dx,
-        *Dz, *Hx, *Hz, *b, *p0, *p1, *q;
+        *Dz, *Hx, *Hz, *b, *p0, *p1, *q, *dtr1;
+    double *gzc, *gzf;                     // g z of cell-centre rows (nz) and z-face rows (nz + 1)
     double *stage;                         // staging for conservative set/get (4 fields)
     double *thbar;                         // nz values
     double *thout;                         // theta' output
@@ -120,6 +121,9 @@ StepArgs step_args(gea_ctx *c, int from)
     a.bh = c->bh; a.ha = c->ha; a.hb = c->hb;
     a.rho2 = c->rho2; a.psi = c->psi; a.Dx = c->Dx; a.Dz = c->Dz; a.Hx = c->Hx; a.Hz = c->Hz;
     a.b = c->b; a.p0 = c->p0; a.p1 = c->p1; a.q = c->q;
+    a.dtr1 = c->dtr1;
+    a.gzc = c->gzc;
+    a.gzf = c->gzf;
     a.sc = c->sc;
     a.partials = c->partials;
     a.jac_rtol2 = c->C.jac_rtol * c->C.jac_rtol;
@@ -520,6 +524,8 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
     ctx->F.mu = c->mu; ctx->F.nuh = c->mu / c->Pr; ctx->F.dt = c->dt; ctx->F.idt = 1.0 / c->dt;
     ctx->F.omega = kOmega;
     ctx->F.k_lagged = (c->reading_flags & GEA_READING_K_LAGGED) ? 1 : 0;
+    ctx->F.les = ctx->F.les_d2 > 0.0 ? 1 : 0;
+    ctx->F.pr_ne1 = ctx->F.nuh != ctx->F.mu ? 1 : 0;
     ctx->mixed = (c->flags & GEA_FLAG_MIXED) != 0;
     if (cudaGetDevice(&ctx->device) != cudaSuccess) {
         delete ctx;
@@ -547,7 +553,8 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
     const size_t cell = arr_bytes(G, G.nz), fz = arr_bytes(G, G.nz + 1);
     size_t total = 0;
     total += 2 * (10 * cell + fz);                 // two states (phiz has nz+1 rows)
-    total += 33 * cell + 2 * fz;                   // scratch (Dz has nz+1 rows)
+    total += 34 * cell + 2 * fz;                   // scratch (Dz has nz+1 rows)
+    total += round_up((2 * (size_t)G.nz + 1) * sizeof(double), 256);   // height tables
     total += 4 * cell;                             // staging for conservative fields
     total += 2 * cell + round_up(G.nz * sizeof(double), 256);   // theta_bar, theta'
     if (c->flags & GEA_FLAG_KEEP_R0) total += cell;
@@ -596,6 +603,9 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
     ctx->psi = take(cell); ctx->Dx = take(cell); ctx->Dz = take(fz); ctx->Hx = take(cell);
     ctx->Hz = take(cell); ctx->b = take(cell); ctx->p0 = take(cell); ctx->p1 = take(cell);
     ctx->q = take(cell);
+    ctx->dtr1 = take(cell);
+    ctx->gzc = take(round_up((2 * (size_t)G.nz + 1) * sizeof(double), 256));
+    ctx->gzf = ctx->gzc + G.nz;
     ctx->stage = take(4 * cell);
     ctx->thout = take(cell);
     ctx->thbar = take(round_up(G.nz * sizeof(double), 256));
@@ -640,6 +650,16 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
     if ((size_t)(ptr - ctx->mem) > total) {
         gea_destroy(ctx);
         return GEA_ERR_NOMEM;
+    }
+    {
+        // g z of the cell centres z_k = (k + 1/2) dz and of the z-faces k dz
+        std::vector<double> h(2 * (size_t)G.nz + 1);
+        for (int k = 0; k < G.nz; ++k) h[k] = ctx->F.g * ((k + 0.5) * G.dz);
+        for (int k = 0; k <= G.nz; ++k) h[G.nz + k] = ctx->F.g * (k * G.dz);
+        if (cudaMemcpy(ctx->gzc, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+            gea_destroy(ctx);
+            return GEA_ERR_CUDA;
+        }
     }
     for (int e = 0; e < 8; ++e) cudaEventCreate(&ctx->ev[e]);
     ctx->nev = 8;

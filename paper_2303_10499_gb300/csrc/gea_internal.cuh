@@ -42,6 +42,9 @@ struct Phys {
     double omega;                            // damped-Jacobi weight of the smoother
     double les_d2;                           // Smagorinsky (cs Delta)^2; 0: constant viscosity
     int k_lagged;                            // GEA_READING_K_LAGGED: K^{n-1} in eq. step3_sd
+    // uniform branch flags as integers (an FP64 compare issues on the FP64 pipe)
+    int les;                                 // les_d2 > 0
+    int pr_ne1;                              // nuh != mu (Pr != 1): the enthalpy stencil differs
 };
 
 // Persistent state of one time level (Section 3's solution tuple plus the
@@ -157,6 +160,8 @@ struct StepArgs {
     double *rho1, *dinvu, *dinvh, *bu, *bw, *ua, *wa, *ub, *wb;   // Step 1
     double *bh, *ha, *hb;                                // Step 2
     double *rho2, *psi, *Dx, *Dz, *Hx, *Hz, *b;          // Step 3
+    double *dtr1;                                        // dt / rho^{n+1/3} (Step 1, used by Step 3)
+    const double *gzc, *gzf;   // g z of the cell centres of row k (nz values) and of z-face k (nz + 1)
     double *p0, *p1, *q;                                 // CG directions (ping-pong) and A p
     Scal *sc;
     double *partials;

@@ -226,7 +226,7 @@ __device__ bool run_step(const PersistArgs &P, const StepArgs &a, const Grp &g, 
     const int nlev = P.nlev;
 
     // ---- Smagorinsky eddy viscosity of the step (LES) ----
-    if (a.F.les_d2 > 0.0) {
+    if (a.F.les) {
         for_tiles(g, G, [&](int bx, int bz) { ph_les(a, sm, bx, bz); });
         gbar(g);
         if (stop(sc)) return false;
@@ -431,7 +431,7 @@ __device__ bool run_step_mixed(const PersistArgs &P, const MixedPersist &X, cons
     const Level &L0 = P.L[0];
     if (g.rank == 0 && tid_of() == 0) g.gs->u1_slot = g.gs->h1_slot = 0;
 
-    if (a.F.les_d2 > 0.0) {
+    if (a.F.les) {
         for_tiles(g, G, [&](int bx, int bz) { ph_les(a, sm, bx, bz); });
         gbar(g);
         if (stop(sc)) return false;

@@ -269,7 +269,7 @@ __device__ __forceinline__ void ph_pred_t(const StepArgs &a, const MixedArgs &m,
         // diffusion: mu/dx^2 per face, or with LES the face mean of mu_eff
         // (a wall face takes the cell's own)
         double me, mw, mn, ms;
-        if (F.les_d2 > 0.0) {
+        if (F.les) {
             const double mc = ld(&a.mueff[q]);
             const double ix2 = 0.5 * G.idx * G.idx, iz2 = 0.5 * G.idz * G.idz;
             me = (mc + (i + 1 < G.nx ? ld(&a.mueff[q + 1]) : mc)) * ix2;
@@ -294,24 +294,27 @@ __device__ __forceinline__ void ph_pred_t(const StepArgs &a, const MixedArgs &m,
         a.T.cN2[q] = cN2;
         a.T.cS2[q] = cS2;
         const double diu = 1.0 / cC;
-        const double dih = 1.0 / (cC + 2.0 * (F.nuh - F.mu) * (G.idx * G.idx + G.idz * G.idz));
+        const double dih =
+            F.pr_ne1 ? 1.0 / (cC + 2.0 * (F.nuh - F.mu) * (G.idx * G.idx + G.idz * G.idz)) : diu;
         if (!MX) {
             a.dinvu[q] = diu;
             a.dinvh[q] = dih;
         }
-        const double z = (k + 0.5) * G.dz;
+        // face forces (p'_b - p'_a - g z_f (rho_b - rho_a)) / Delta; the cell
+        // and face heights g z come from per-row tables
+        const double gz = ld(&a.gzc[k]);
         const double pq = ld(&S.pp[q]);
         double gxw = 0.0, gxe = 0.0, gzs = 0.0, gzn = 0.0;
-        if (i > 0) gxw = (pq - ld(&S.pp[q - 1])) * G.idx - F.g * z * (rq - ld(&S.rho[q - 1])) * G.idx;
-        if (i + 1 < G.nx) gxe = (ld(&S.pp[q + 1]) - pq) * G.idx - F.g * z * (ld(&S.rho[q + 1]) - rq) * G.idx;
-        if (k > 0)
-            gzs = (pq - ld(&S.pp[q - G.P])) * G.idz - F.g * (k * G.dz) * (rq - ld(&S.rho[q - G.P])) * G.idz;
+        if (i > 0) gxw = fma(-gz, rq - ld(&S.rho[q - 1]), pq - ld(&S.pp[q - 1])) * G.idx;
+        if (i + 1 < G.nx) gxe = fma(-gz, ld(&S.rho[q + 1]) - rq, ld(&S.pp[q + 1]) - pq) * G.idx;
+        if (k > 0) gzs = fma(-ld(&a.gzf[k]), rq - ld(&S.rho[q - G.P]), pq - ld(&S.pp[q - G.P])) * G.idz;
         if (k + 1 < G.nz)
-            gzn = (ld(&S.pp[q + G.P]) - pq) * G.idz - F.g * ((k + 1) * G.dz) * (ld(&S.rho[q + G.P]) - rq) * G.idz;
+            gzn = fma(-ld(&a.gzf[k + 1]), ld(&S.rho[q + G.P]) - rq, ld(&S.pp[q + G.P]) - pq) * G.idz;
         const double u = ld(&S.u[q]), w = ld(&S.w[q]);
         const double bu = rq * u * F.idt - 0.5 * (gxw + gxe);
         const double bw = rq * w * F.idt - 0.5 * (gzs + gzn);
         a.rho1[q] = rho1;
+        a.dtr1[q] = F.dt / rho1;
         const int y = threadIdx.y + 2, x = threadIdx.x + 2;
         // T(X) at the cell from a halo-2 tile, in apply9's order
         auto t9 = [&](const Tile<2> &t) {
@@ -411,6 +414,7 @@ template <class R, int BC>
 __device__ __forceinline__ void ph_sweep1(const Geom &G, const Phys &F, const Stencil9T<R> &T,
                                           const R *dinv, const R *bv, R lc, const R *xin, R *xout,
                                           double *sm, int bx, int bz, R (&acc)[1])
+// (lc is used when F.pr_ne1, i.e. mu/Pr != mu)
 {
     Tile<2, R> &sh = tile_at<2, R>(sm, 0);
     load_tile<BC, 2, R>(sh, G, F, xin, bx, bz);
@@ -420,7 +424,7 @@ __device__ __forceinline__ void ph_sweep1(const Geom &G, const Phys &F, const St
         const int q = cidx(G, i, k);
         const int y = threadIdx.y + 2, x = threadIdx.x + 2;
         R t = apply9<2, R>(T, q, sh, y, x);
-        if (lc != (R)0) t = fma(lc, lap5<2, R>(G, sh, y, x), t);
+        if (F.pr_ne1) t = fma(lc, lap5<2, R>(G, sh, y, x), t);
         const R r = ld(&bv[q]) - t;
         xout[q] = fma(r, ld(&dinv[q]), sh[y][x]);
         acc[0] = fma(r, r, acc[0]);
@@ -505,7 +509,7 @@ __device__ __forceinline__ void ph_enth_rhs_t(const StepArgs &a, const MixedArgs
             if (SW1) {
                 const Tile<2> &sh = tile_at<2>(sm, 2);
                 double t = apply9<2>(a.T, q, sh, y, x);
-                if (F.nuh != F.mu) t = fma(F.mu - F.nuh, lap5<2>(G, sh, y, x), t);
+                if (F.pr_ne1) t = fma(F.mu - F.nuh, lap5<2>(G, sh, y, x), t);
                 const double r0 = bh - t;
                 h0[q] = fma(r0, ld(&a.dinvh[q]), sh[y][x]);
                 acc[SW1 ? 1 : 0] = fma(r0, r0, acc[SW1 ? 1 : 0]);
@@ -517,7 +521,7 @@ __device__ __forceinline__ void ph_enth_rhs_t(const StepArgs &a, const MixedArgs
             a.wa[q] = w1c;
             const Tile<2> &sh = tile_at<2>(sm, 2);
             double t = apply9<2>(a.T, q, sh, y, x);
-            if (F.nuh != F.mu) t = fma(F.mu - F.nuh, lap5<2>(G, sh, y, x), t);
+            if (F.pr_ne1) t = fma(F.mu - F.nuh, lap5<2>(G, sh, y, x), t);
             const double r0 = bh - t;
             const float fr = (float)r0;
             m.r0h[q] = fr;
@@ -577,8 +581,10 @@ __device__ __forceinline__ void ph_eos_t(const StepArgs &a, const Level &L, cons
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int y = ty + 1, x = tx + 1;
     const double ix2 = G.idx * G.idx, iz2 = G.idz * G.idz;
+    // dt rho2_f / rho1_f with linear face averages (the two halves cancel
+    // exactly in binary)
     auto dface = [&](int ya, int xa, int yb, int xb) {
-        return F.dt * (0.5 * (s2[ya][xa] + s2[yb][xb])) / (0.5 * (s1[ya][xa] + s1[yb][xb]));
+        return F.dt * (s2[ya][xa] + s2[yb][xb]) / (s1[ya][xa] + s1[yb][xb]);
     };
     if (in) {
         fx[ty][tx] = i > 0 ? dface(y, x - 1, y, x) : 0.0;
@@ -708,18 +714,17 @@ __device__ __forceinline__ void ph_helm_rhs_t(const StepArgs &a, const Level &L,
     if (cell_of(G, bx, bz, i, k)) {
         const int q = cidx(G, i, k);
         const int y = threadIdx.y + 1, x = threadIdx.x + 1;
-        const double z = (k + 0.5) * G.dz;
+        const double gz = ld(&a.gzc[k]);
+        const double gzx = gz * G.idx, gzs = ld(&a.gzf[k]) * G.idz, gzn = ld(&a.gzf[k + 1]) * G.idz;
         const double r2q = s2[y][x];
         const double Dw = ld(&a.Dx[k * G.P + i]), De = ld(&a.Dx[k * G.P + i + 1]);
         const double Ds = ld(&a.Dz[k * G.P + i]), Dn = ld(&a.Dz[(k + 1) * G.P + i]);
         // wall faces have D = 0 and zero tile entries beyond the box
-        double flux = De * G.dz * (0.5 * (shx[y][x] + shx[y][x + 1]) + F.g * z * (s2[y][x + 1] - r2q) * G.idx);
-        flux += Dw * G.dz * (-0.5 * (shx[y][x] + shx[y][x - 1]) + F.g * z * (s2[y][x - 1] - r2q) * G.idx);
-        flux += Dn * G.dx *
-                (0.5 * (shz[y][x] + shz[y + 1][x]) + F.g * ((k + 1) * G.dz) * (s2[y + 1][x] - r2q) * G.idz);
-        flux += Ds * G.dx *
-                (-0.5 * (shz[y][x] + shz[y - 1][x]) + F.g * (k * G.dz) * (s2[y - 1][x] - r2q) * G.idz);
-        const double b = (ld(&a.S.rho[q]) + ld(&a.psi[q]) * r2q * F.g * z) * F.idt - flux * G.iV;
+        double flux = De * G.dz * fma(0.5, shx[y][x] + shx[y][x + 1], gzx * (s2[y][x + 1] - r2q));
+        flux += Dw * G.dz * fma(-0.5, shx[y][x] + shx[y][x - 1], gzx * (s2[y][x - 1] - r2q));
+        flux += Dn * G.dx * fma(0.5, shz[y][x] + shz[y + 1][x], gzn * (s2[y + 1][x] - r2q));
+        flux += Ds * G.dx * fma(-0.5, shz[y][x] + shz[y - 1][x], gzs * (s2[y - 1][x] - r2q));
+        const double b = fma(ld(&a.psi[q]) * r2q, gz, ld(&a.S.rho[q])) * F.idt - flux * G.iV;
         const double r = b - helm_tile<1>(L, q, i, k, sx, y, x);
         a.b[q] = b;
         xout[q] = sx[y][x];
@@ -1046,12 +1051,12 @@ __device__ __forceinline__ void ph_correct(const StepArgs &a, double *sm, int bx
     const bool in = cell_of(G, bx, bz, i, k);
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int y = ty + 1, x = tx + 1;
-    const double z = (k + 0.5) * G.dz;
+    const double gzk = in ? ld(&a.gzc[k]) : 0.0;
     auto gxf = [&](int xa) {   // x-face between tile columns xa and xa+1 of row y
-        return (sx[y][xa + 1] - sx[y][xa]) * G.idx - F.g * z * (s2[y][xa + 1] - s2[y][xa]) * G.idx;
+        return fma(-gzk, s2[y][xa + 1] - s2[y][xa], sx[y][xa + 1] - sx[y][xa]) * G.idx;
     };
     auto gzf = [&](int ya, int kf) {   // z-face between tile rows ya and ya+1, face index kf
-        return (sx[ya + 1][x] - sx[ya][x]) * G.idz - F.g * (kf * G.dz) * (s2[ya + 1][x] - s2[ya][x]) * G.idz;
+        return fma(-ld(&a.gzf[kf]), s2[ya + 1][x] - s2[ya][x], sx[ya + 1][x] - sx[ya][x]) * G.idz;
     };
     if (in) {
         gx[ty][tx] = i > 0 ? gxf(x - 1) : 0.0;
@@ -1070,10 +1075,10 @@ __device__ __forceinline__ void ph_correct(const StepArgs &a, double *sm, int bx
         N.phiz[k * G.P + i] = Fs * G.dx;
         if (i == G.nx - 1) N.phix[k * G.P + G.nx] = 0.0;
         if (k == G.nz - 1) N.phiz[G.nz * G.P + i] = 0.0;
-        const double dtr1 = F.dt / ld(&a.rho1[q]);
+        const double dtr1 = ld(&a.dtr1[q]);
         N.u[q] = dtr1 * (hxq - 0.5 * (gxw + gxe));
         N.w[q] = dtr1 * (hzq - 0.5 * (gzs + gzn));
-        const double pn = fma(-s2[y][x] * F.g, z, sx[y][x]);
+        const double pn = fma(-s2[y][x], gzk, sx[y][x]);
         N.p[q] = pn;
         N.rho[q] = pn * ld(&a.psi[q]);
         N.pold[q] = ld(&a.S.p[q]);
