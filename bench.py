@@ -353,6 +353,27 @@ def whole_step(prof, pk, ms_per_step):
             "ms_at_binding_roofline": max(t_alu, t_hbm) * 1e3}
 
 
+def per_kernel_account(prof, pk):
+    """Every kernel of one eager profiled step against its binding roofline:
+    model flops (FP64 or FP32) and algorithmic bytes of its launches over
+    their summed CUDA-event time, with its share of the step."""
+    total = sum(v["ms"] for v in prof.values())
+    out = {}
+    for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"]):
+        if k not in KERNEL_MODEL or v["ms"] <= 0:
+            continue
+        words, flops, prec = KERNEL_MODEL[k]
+        t = v["ms"] * 1e-3
+        tfl = flops * v["cells"] / t / 1e12
+        gbs = words * 8 * v["cells"] / t / 1e9
+        alu = pk["fp64_tflops"] if prec == "f64" else pk["fp32_tflops"]
+        out[k] = {"share": round(v["ms"] / total, 4), "launches": v["launches"],
+                  "ms": round(v["ms"], 4), "tflops": round(tfl, 4), "frac_alu": round(tfl / alu, 3),
+                  "gbs": round(gbs, 1), "frac_hbm": round(gbs / pk["hbm_gbs"], 3),
+                  "avg_cells_per_launch": v["cells"] // max(1, v["launches"])}
+    return out
+
+
 def w3_record(gea, W, stream, flush, pk, local, steps=10, warmup=3):
     """The 4096 x 2048 smooth bubble (larger than L2: the HBM/FP64-roofline
     workload), FP64, CUDA-graph driver: pressure solves to 1e-8 of ||b|| (the
@@ -384,6 +405,7 @@ def w3_record(gea, W, stream, flush, pk, local, steps=10, warmup=3):
             "gpu_launches": int(launches), "clocks": clocks,
             "whole_step": whole_step(prof, pk, mean),
             "dominant_kernel": roofline(prof, pk, mean, False, wl.name),
+            "per_kernel": per_kernel_account(prof, pk),
         }
         s.close()
     del dev

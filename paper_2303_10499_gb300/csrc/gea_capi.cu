@@ -13,6 +13,7 @@
 #include "../../include/gea.h"
 #include "../../include/gea_net.h"
 
+#include <nvtx3/nvToolsExt.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -438,7 +439,8 @@ int ensure_graphs(gea_ctx *ctx)
     return GEA_OK;
 }
 
-// Records an event pair around every launch of an eager step.
+// Records an event pair around every launch of an eager step, inside an
+// NVTX range named after the kernel (visible to a timeline profiler).
 struct EventTracer : Tracer {
     struct Rec {
         const char *name;
@@ -449,12 +451,17 @@ struct EventTracer : Tracer {
     void begin(const char *name, long long cells, cudaStream_t st) override
     {
         Rec r{name, cells, nullptr, nullptr};
+        nvtxRangePushA(name);
         cudaEventCreate(&r.e0);
         cudaEventCreate(&r.e1);
         cudaEventRecord(r.e0, st);
         recs.push_back(r);
     }
-    void end(cudaStream_t st) override { cudaEventRecord(recs.back().e1, st); }
+    void end(cudaStream_t st) override
+    {
+        cudaEventRecord(recs.back().e1, st);
+        nvtxRangePop();
+    }
     ~EventTracer() override
     {
         for (auto &r : recs) {
@@ -747,9 +754,18 @@ int gea_set_state(gea_ctx *ctx, const gea_state_view *v)
     return GEA_OK;
 }
 
+namespace {
+// NVTX range around the enqueueing of steps (the host side of gea_step)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+}  // namespace
+
 int gea_step_async(gea_ctx *ctx, int32_t n)
 {
     if (!ctx || n < 0) return GEA_ERR_INVAL;
+    NvtxRange range(ctx->pers_blocks > 0 && !ctx->net ? "gea_step persistent" : "gea_step graph");
     if (!ctx->have_state) return fail(ctx, GEA_ERR_STATE, "no state set");
     if (n == 0) return GEA_OK;
     if (ctx->pers_blocks > 0 && !ctx->net) {
