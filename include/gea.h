@@ -372,20 +372,23 @@ int gea_probe_fma(int32_t bits, int32_t blocks, int32_t iters, void *out, void *
 
 /* ---- ensembles: many independent contexts advanced by one launch ----
  *
- * An ensemble runs the steps of n FP64 contexts (members, each with its own
+ * An ensemble runs the steps of n contexts (members, each with its own
  * grid, constants and state) in one cooperative launch: every member gets a
  * contiguous share of the GPU's co-resident thread blocks, in proportion to
- * its weight (default: its number of 32 x 8 tiles; at least one block, at
- * most one per tile), and steps on those blocks with
+ * its weight (default: its number of tiles of the members' tile shape; at
+ * least one block, at most one per tile), and steps on those blocks with
  * its own grid barrier and its own reductions, so members never wait for
- * one another. The results of a member are those of its own persistent
- * driver up to the order of the reduction sums. The ensemble takes over the
- * members' streams (gea_ensemble_set_stream sets all of them); while it
- * exists, step members only through it. Members must not use GEA_FLAG_MIXED
- * or GEA_FLAG_KEEP_R0 or an attached network.
- * Errors: GEA_ERR_INVAL (null or unsuitable members, more members than
- * co-resident blocks), GEA_ERR_STATE (a member without state, on step),
- * GEA_ERR_NOMEM, GEA_ERR_CUDA. */
+ * one another. The members are all FP64 or all mixed precision
+ * (GEA_FLAG_MIXED: the mixed-precision step, one launch for all of them),
+ * and share one tile shape (gea_set_tile_shape). The results of a member are
+ * those of its own persistent driver up to the order of the reduction sums.
+ * The ensemble takes over the members' streams (gea_ensemble_set_stream
+ * sets all of them); while it exists, step members only through it. Members
+ * must not use GEA_FLAG_KEEP_R0 or an attached network.
+ * Errors: GEA_ERR_INVAL (null or unsuitable members, FP64 and mixed members
+ * together, different tile shapes, more members than co-resident blocks),
+ * GEA_ERR_STATE (a member without state, on step), GEA_ERR_NOMEM,
+ * GEA_ERR_CUDA. */
 typedef struct gea_ensemble gea_ensemble;
 /* weights (optional, n positive values): blocks in proportion to weights[m]
  * instead of the member's tile count. */
@@ -394,8 +397,17 @@ int gea_ensemble_set_stream(gea_ensemble *e, void *stream);
 /* Blocks given to member m (0 <= m < n), or -1. */
 int gea_ensemble_blocks(const gea_ensemble *e, int32_t m);
 /* Enqueue n steps of every member (one launch); gea_sync on a member, or
- * gea_ensemble_sync, waits and reports. */
+ * gea_ensemble_sync, waits and reports. While every member's state is in
+ * the same slot parity (always, unless members were stepped apart), the
+ * launch is one CUDA graph launch: a graph holding the cooperative kernel
+ * node is captured on the first call for each parity and n, with its own
+ * device copy of the members' arguments, and replayed (no host staging, no
+ * synchronisation). Otherwise, or after gea_ensemble_set_graph(e, 0), the
+ * arguments are staged and the kernel launched directly. Both run the same
+ * kernel on the same arguments. */
 int gea_ensemble_step(gea_ensemble *e, int32_t n);
+/* on = 0: launch directly instead of through the captured graphs. */
+int gea_ensemble_set_graph(gea_ensemble *e, int32_t on);
 /* Wait for the launches; the first member error code, or GEA_OK. */
 int gea_ensemble_sync(gea_ensemble *e);
 void gea_ensemble_destroy(gea_ensemble *e);

@@ -1118,7 +1118,70 @@ struct gea_ensemble {
     void *dargs = nullptr;
     int *dfirst = nullptr;
     int shape = SHAPE_32x8;          // the members' tile shape
+    bool mixed = false;              // mixed-precision members (GEA_FLAG_MIXED)
+    // the launch as a CUDA graph: one instantiated graph (a cooperative kernel
+    // node reading its own device copy of the argument blocks) per state slot
+    // parity and step count, used while every member is at the same parity
+    bool use_graph = true;
+    cudaStream_t cap = nullptr;      // private stream for the capture
+    struct Graph {
+        int parity, n;
+        long long sig;               // the members' barrier poll limits when built
+        void *dargs;
+        cudaGraph_t g;
+        cudaGraphExec_t x;
+    };
+    std::vector<Graph> graphs;
 };
+
+namespace {
+
+// fill the host staging with every member's argument block
+void ensemble_fill(gea_ensemble *e, int n, int parity)
+{
+    for (size_t i = 0; i < e->m.size(); ++i) {
+        gea_ctx *c = e->m[i];
+        StepArgs a[2] = {step_args(c, 0), step_args(c, 1)};
+        const int first = parity >= 0 ? parity : (int)((c->base + c->steps_at_sync) & 1);
+        if (e->mixed)
+            persist_args_fill_mixed(e->hargs + i * e->argb, a, c->L[0], c->mx, c->Lf.data(), (int)c->Lf.size(),
+                                    kCoarseSweeps, c->C.n_corr, c->C.jac_maxit, c->C.cg_maxit, first, n,
+                                    c->wait_polls);
+        else
+            persist_args_fill(e->hargs + i * e->argb, a, c->L.data(), (int)c->L.size(), kCoarseSweeps,
+                              c->C.n_corr, c->C.jac_maxit, c->C.cg_maxit, first, n, c->wait_polls);
+    }
+}
+
+// the graph of n steps from state slot `parity`, built on first use
+gea_ensemble::Graph *ensemble_graph(gea_ensemble *e, int n, int parity, long long sig)
+{
+    for (auto &g : e->graphs)
+        if (g.parity == parity && g.n == n && g.sig == sig) return &g;
+    gea_ensemble::Graph g{parity, n, sig, nullptr, nullptr, nullptr};
+    const size_t bytes = e->argb * e->m.size();
+    if (cudaStreamSynchronize(e->st) != cudaSuccess || cudaMalloc(&g.dargs, bytes) != cudaSuccess) return nullptr;
+    ensemble_fill(e, n, parity);
+    bool ok = cudaMemcpy(g.dargs, e->hargs, bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaStreamBeginCapture(e->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        const cudaError_t le = persist_ops(e->shape).launch_ensemble(g.dargs, e->mixed ? 1 : 0, e->dfirst,
+                                                                    (int)e->m.size(), e->blocks, e->cap);
+        const cudaError_t ce = cudaStreamEndCapture(e->cap, &g.g);
+        ok = le == cudaSuccess && ce == cudaSuccess && g.g &&
+             cudaGraphInstantiate(&g.x, g.g, 0) == cudaSuccess;
+    }
+    if (!ok) {
+        cudaGetLastError();
+        if (g.g) cudaGraphDestroy(g.g);
+        cudaFree(g.dargs);
+        return nullptr;
+    }
+    e->graphs.push_back(g);
+    return &e->graphs.back();
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -1128,7 +1191,8 @@ int gea_ensemble_create(gea_ctx **members, int32_t n, const double *weights, gea
     *out = nullptr;
     for (int i = 0; i < n; ++i) {
         gea_ctx *c = members[i];
-        if (!c || c->mixed || c->net || c->r0keep) return GEA_ERR_INVAL;
+        // all members FP64 or all mixed precision: one kernel per launch
+        if (!c || c->net || c->r0keep || c->mixed != members[0]->mixed) return GEA_ERR_INVAL;
         for (int j = 0; j < i; ++j)
             if (members[j] == c) return GEA_ERR_INVAL;
     }
@@ -1137,7 +1201,7 @@ int gea_ensemble_create(gea_ctx **members, int32_t n, const double *weights, gea
     for (int i = 1; i < n; ++i)
         if (members[i]->shape != shape) return GEA_ERR_INVAL;
     const PersistOps &ops = persist_ops(shape);
-    const int B = ops.ensemble_max_blocks();
+    const int B = ops.ensemble_max_blocks(members[0]->mixed ? 1 : 0);
     cudaGetLastError();
     if (B < n) return GEA_ERR_INVAL;
     // blocks in proportion to the members' tiles, at least one each and at
@@ -1179,9 +1243,11 @@ int gea_ensemble_create(gea_ctx **members, int32_t n, const double *weights, gea
     for (int i = 0; i < n; ++i) e->first[i + 1] = e->first[i] + nb[i];
     e->blocks = e->first[n];
     e->shape = shape;
-    e->argb = persist_args_bytes();   // the kernel indexes an array of argument blocks
+    e->mixed = members[0]->mixed;
+    e->argb = persist_args_bytes(e->mixed ? 1 : 0);   // the kernel indexes an array of argument blocks
     e->st = members[0]->stream;
-    if (cudaMallocHost(&e->hargs, e->argb * n) != cudaSuccess ||
+    if (cudaStreamCreateWithFlags(&e->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMallocHost(&e->hargs, e->argb * n) != cudaSuccess ||
         cudaMalloc(&e->dargs, e->argb * n) != cudaSuccess ||
         cudaMalloc(&e->dfirst, sizeof(int) * (n + 1)) != cudaSuccess ||
         cudaMemcpy(e->dfirst, e->first.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -1191,6 +1257,13 @@ int gea_ensemble_create(gea_ctx **members, int32_t n, const double *weights, gea
     }
     for (gea_ctx *c : e->m) c->stream = e->st;
     *out = e;
+    return GEA_OK;
+}
+
+int gea_ensemble_set_graph(gea_ensemble *e, int32_t on)
+{
+    if (!e) return GEA_ERR_INVAL;
+    e->use_graph = on != 0;
     return GEA_OK;
 }
 
@@ -1215,19 +1288,32 @@ int gea_ensemble_step(gea_ensemble *e, int32_t n)
     if (n == 0) return GEA_OK;
     for (gea_ctx *c : e->m)
         if (!c->have_state) return GEA_ERR_STATE;
+    int parity = -1;
+    bool same = true;
+    long long sig = 0;
+    for (gea_ctx *c : e->m) {
+        const int p = (int)((c->base + c->steps_at_sync) & 1);
+        if (parity < 0) parity = p;
+        else if (p != parity) same = false;
+        sig = sig * 31 + c->wait_polls + 2;
+    }
+    if (e->use_graph && same) {
+        gea_ensemble::Graph *g = ensemble_graph(e, n, parity, sig);
+        if (g && cudaGraphLaunch(g->x, e->st) == cudaSuccess) {
+            for (gea_ctx *c : e->m) c->steps_at_sync += n;
+            return GEA_OK;
+        }
+        // no graph on this platform: launch directly from now on
+        cudaGetLastError();
+        e->use_graph = false;
+    }
     // the staging buffer may still feed the previous launch's copy
     if (cudaStreamSynchronize(e->st) != cudaSuccess) return GEA_ERR_CUDA;
-    for (size_t i = 0; i < e->m.size(); ++i) {
-        gea_ctx *c = e->m[i];
-        StepArgs a[2] = {step_args(c, 0), step_args(c, 1)};
-        const int first = (int)((c->base + c->steps_at_sync) & 1);
-        persist_args_fill(e->hargs + i * e->argb, a, c->L.data(), (int)c->L.size(), kCoarseSweeps, c->C.n_corr,
-                          c->C.jac_maxit, c->C.cg_maxit, first, n, c->wait_polls);
-    }
+    ensemble_fill(e, n, -1);
     if (cudaMemcpyAsync(e->dargs, e->hargs, e->argb * e->m.size(), cudaMemcpyHostToDevice, e->st) !=
             cudaSuccess ||
-        persist_ops(e->shape).launch_ensemble(e->dargs, e->dfirst, (int)e->m.size(), e->blocks, e->st) !=
-            cudaSuccess) {
+        persist_ops(e->shape).launch_ensemble(e->dargs, e->mixed ? 1 : 0, e->dfirst, (int)e->m.size(), e->blocks,
+                                              e->st) != cudaSuccess) {
         cudaGetLastError();
         return GEA_ERR_CUDA;
     }
@@ -1251,6 +1337,12 @@ void gea_ensemble_destroy(gea_ensemble *e)
     if (!e) return;
     if (e->st) cudaStreamSynchronize(e->st);
     else cudaDeviceSynchronize();
+    for (auto &g : e->graphs) {
+        cudaGraphExecDestroy(g.x);
+        cudaGraphDestroy(g.g);
+        cudaFree(g.dargs);
+    }
+    if (e->cap) cudaStreamDestroy(e->cap);
     if (e->hargs) cudaFreeHost(e->hargs);
     if (e->dargs) cudaFree(e->dargs);
     if (e->dfirst) cudaFree(e->dfirst);

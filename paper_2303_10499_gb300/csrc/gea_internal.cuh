@@ -423,6 +423,15 @@ struct PersistArgs {
     unsigned long long spin_limit;   // polls of a grid barrier before giving up
 };
 
+// FP32 data of the mixed-precision step for the persistent kernels: the
+// increments' operator, vectors and CG buffers, and the FP32 multigrid
+// hierarchy (nlev levels).
+struct MixedPersist {
+    MixedArgs m;
+    LevelF Lf[kMaxLevels];
+    int nlev;
+};
+
 // Grid-barrier polls before a block gives up (GEA_ERR_TIMEOUT): a few
 // seconds of ~0.7 us polls by default (wait_polls < 0); 0 makes every block
 // that is not the last to arrive give up at once.
@@ -440,20 +449,23 @@ inline unsigned long long spin_limit_of(long long wait_polls)
 //  launch / launch_mixed: n steps of one context (the FP64 finest-to-coarsest
 //      hierarchy L, or the FP64 finest level L0 with the FP32 operator m and
 //      hierarchy Lf), wait_polls as in spin_limit_of;
-//  launch_ensemble: one argument block per member (persist_args_fill) in
-//      device memory, first[m] the member's first block (nmem + 1 entries).
+//  launch_ensemble: one argument block per member in device memory
+//      (persist_args_fill, or persist_args_fill_mixed for mixed-precision
+//      members: mixed != 0), first[m] the member's first block (nmem + 1
+//      entries).
 struct PersistOps {
     int bx, bz;
     int (*max_blocks)();
     int (*mixed_max_blocks)();
-    int (*ensemble_max_blocks)();
+    int (*ensemble_max_blocks)(int mixed);
     cudaError_t (*launch)(const StepArgs a[2], const Level *L, int nlev, int ncoarse, int n_corr, int jac_maxit,
                           int cg_maxit, int first_slot, int nsteps, int blocks, long long wait_polls,
                           cudaStream_t st);
     cudaError_t (*launch_mixed)(const StepArgs a[2], const Level &L0, const MixedArgs &m, const LevelF *Lf,
                                 int nlev, int ncoarse, int n_corr, int jac_maxit, int cg_maxit, int first_slot,
                                 int nsteps, int blocks, long long wait_polls, cudaStream_t st);
-    cudaError_t (*launch_ensemble)(const void *Pm, const int *first, int nmem, int blocks, cudaStream_t st);
+    cudaError_t (*launch_ensemble)(const void *Pm, int mixed, const int *first, int nmem, int blocks,
+                                   cudaStream_t st);
 };
 enum { SHAPE_32x8 = 0, SHAPE_16x16 = 1, SHAPE_64x4 = 2, NSHAPES = 3 };
 const PersistOps &persist_ops(int shape);
@@ -462,8 +474,14 @@ inline long long shape_tiles(const Geom &G, int bx, int bz)
 {
     return (long long)((G.nx + bx - 1) / bx) * ((G.nz + bz - 1) / bz);
 }
-size_t persist_args_bytes();
+// bytes of one member's argument block of an ensemble launch
+size_t persist_args_bytes(int mixed);
 void persist_args_fill(void *dst, const StepArgs a[2], const Level *L, int nlev, int ncoarse, int n_corr,
                        int jac_maxit, int cg_maxit, int first_slot, int nsteps, long long wait_polls);
+// the mixed-precision member's block: PersistArgs (the FP64 finest level
+// L0) followed by MixedPersist (m, the FP32 hierarchy Lf[0 .. nlev-1])
+void persist_args_fill_mixed(void *dst, const StepArgs a[2], const Level &L0, const MixedArgs &m,
+                             const LevelF *Lf, int nlev, int ncoarse, int n_corr, int jac_maxit, int cg_maxit,
+                             int first_slot, int nsteps, long long wait_polls);
 
 }  // namespace gea

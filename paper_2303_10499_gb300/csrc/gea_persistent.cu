@@ -27,7 +27,20 @@ const PersistOps &persist_ops(int shape)
     }
 }
 
-size_t persist_args_bytes() { return sizeof(PersistArgs); }
+size_t persist_args_bytes(int mixed) { return mixed ? sizeof(PersistArgs) + sizeof(MixedPersist) : sizeof(PersistArgs); }
+
+void persist_args_fill_mixed(void *dst, const StepArgs a[2], const Level &L0, const MixedArgs &m,
+                             const LevelF *Lf, int nlev, int ncoarse, int n_corr, int jac_maxit, int cg_maxit,
+                             int first_slot, int nsteps, long long wait_polls)
+{
+    persist_args_fill(dst, a, &L0, 1, ncoarse, n_corr, jac_maxit, cg_maxit, first_slot, nsteps, wait_polls);
+    MixedPersist X;
+    memset(&X, 0, sizeof(X));
+    X.m = m;
+    for (int l = 0; l < nlev && l < kMaxLevels; ++l) X.Lf[l] = Lf[l];
+    X.nlev = nlev;
+    memcpy(static_cast<char *>(dst) + sizeof(PersistArgs), &X, sizeof(X));
+}
 
 void persist_args_fill(void *dst, const StepArgs a[2], const Level *L, int nlev, int ncoarse, int n_corr,
                        int jac_maxit, int cg_maxit, int first_slot, int nsteps, long long wait_polls)

@@ -408,15 +408,6 @@ __device__ bool run_step(const PersistArgs &P, const StepArgs &a, const Grp &g, 
     return !stop(sc);
 }
 
-// FP32 data of the mixed-precision step for the persistent kernel: the
-// increments' operator, vectors and CG buffers, and the FP32 multigrid
-// hierarchy (nlev levels).
-struct MixedPersist {
-    MixedArgs m;
-    LevelF Lf[kMaxLevels];
-    int nlev;
-};
-
 // One mixed-precision time step (the phases of the graph's mixed step, in
 // its order): FP64 residuals, FP32 Jacobi and MG-CG solves of the
 // increments, FP64 updates. Returns false if the step did not complete.
@@ -672,8 +663,11 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_persistent_mixed(PersistArgs P,
 // runs its steps on blocks first[m] .. first[m+1]-1 with its own grid
 // barrier and reductions over those blocks only, so members whose solves
 // take different iteration counts never wait for one another. Each block
-// keeps its member's arguments in shared memory.
-__global__ void __launch_bounds__(NTHREADS, 3) k_ensemble(const PersistArgs *Pm, const int *first, int nmem)
+// keeps its member's arguments in shared memory: a PersistArgs block of
+// `stride` bytes per member, for the mixed-precision step (MX) followed by
+// the member's MixedPersist.
+template <bool MX>
+__global__ void __launch_bounds__(NTHREADS, 3) k_ensemble(const char *Pm, int stride, const int *first, int nmem)
 {
     extern __shared__ double dsm[];
     double *sm = dsm;
@@ -688,12 +682,14 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_ensemble(const PersistArgs *Pm,
     }
     const int m = lo;
     {
-        const uint32_t *src = reinterpret_cast<const uint32_t *>(&Pm[m]);
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(Pm + (size_t)m * stride);
         uint32_t *dst = reinterpret_cast<uint32_t *>(Ps);
-        for (int i = tid; i < (int)(sizeof(PersistArgs) / 4); i += NTHREADS) dst[i] = __ldg(&src[i]);
+        for (int i = tid; i < stride / 4; i += NTHREADS) dst[i] = __ldg(&src[i]);
     }
     __syncthreads();
     const PersistArgs &P = *Ps;
+    const MixedPersist &X = *reinterpret_cast<const MixedPersist *>(reinterpret_cast<const char *>(Ps) +
+                                                                    sizeof(PersistArgs));
     Scal *sc = P.a[0].sc;
     __shared__ unsigned gen;
     if (tid == 0) {
@@ -708,35 +704,40 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_ensemble(const PersistArgs *Pm,
         if (g.rank == 0 && tid == 0) sc->launches += 1;
         for (int s = 0; s < P.nsteps; ++s) {
             const int slot = (P.first_slot + s) & 1;
-            if (!run_step(P, P.a[slot], g, sm, red)) break;
+            const bool ok = MX ? run_step_mixed(P, X, P.a[slot], g, sm, red) : run_step(P, P.a[slot], g, sm, red);
+            if (!ok) break;
         }
         if (g.rank == 0 && tid == 0 && rdi(&sc->status)) sc->last_status = rdi(&sc->status);
     }
     leave(g);
 }
 
-constexpr size_t kEnsembleSmem = kPersistSmem + (sizeof(PersistArgs) + 15) / 16 * 16;
+// bytes of one member's argument block and the ensemble kernels' shared memory
+constexpr size_t kArgsFp64 = sizeof(PersistArgs);
+constexpr size_t kArgsMixed = sizeof(PersistArgs) + sizeof(MixedPersist);
+constexpr size_t kEnsembleSmem = kPersistSmem + (kArgsFp64 + 15) / 16 * 16;
+constexpr size_t kEnsembleSmemMixed = kPersistSmem + (kArgsMixed + 15) / 16 * 16;
 
-int ensemble_max_blocks()
+int ensemble_max_blocks(int mixed)
 {
     int dev = 0, sms = 0, per_sm = 0;
+    const void *k = mixed ? (const void *)k_ensemble<true> : (const void *)k_ensemble<false>;
+    const size_t smem = mixed ? kEnsembleSmemMixed : kEnsembleSmem;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    if (cudaFuncSetAttribute(k_ensemble, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEnsembleSmem) !=
-        cudaSuccess)
-        return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ensemble, NTHREADS, kEnsembleSmem) !=
-        cudaSuccess)
-        return 0;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NTHREADS, smem) != cudaSuccess) return 0;
     return per_sm * sms;
 }
 
-cudaError_t launch_ensemble(const void *Pm, const int *first, int nmem, int blocks, cudaStream_t st)
+cudaError_t launch_ensemble(const void *Pm, int mixed, const int *first, int nmem, int blocks, cudaStream_t st)
 {
-    const PersistArgs *P = static_cast<const PersistArgs *>(Pm);
-    void *args[] = {&P, &first, &nmem};
-    return cudaLaunchCooperativeKernel((const void *)k_ensemble, dim3(blocks), dim3(BX, BZ), args, kEnsembleSmem,
-                                       st);
+    const char *P = static_cast<const char *>(Pm);
+    int stride = (int)(mixed ? kArgsMixed : kArgsFp64);
+    void *args[] = {&P, &stride, &first, &nmem};
+    const void *k = mixed ? (const void *)k_ensemble<true> : (const void *)k_ensemble<false>;
+    return cudaLaunchCooperativeKernel(k, dim3(blocks), dim3(BX, BZ), args,
+                                       mixed ? kEnsembleSmemMixed : kEnsembleSmem, st);
 }
 
 int persistent_max_blocks()

@@ -114,6 +114,7 @@ def library() -> C.CDLL:
         lib.gea_ensemble_set_stream.argtypes = [P, P]
         lib.gea_ensemble_blocks.argtypes = [P, I]
         lib.gea_ensemble_step.argtypes = [P, I]
+        lib.gea_ensemble_set_graph.argtypes = [P, I]
         lib.gea_ensemble_sync.argtypes = [P]
         lib.gea_ensemble_destroy.argtypes = [P]
         lib.gea_ensemble_destroy.restype = None
@@ -538,6 +539,10 @@ class Ensemble:
 
     def blocks(self):
         return [int(self.lib.gea_ensemble_blocks(self.h, m)) for m in range(len(self.solvers))]
+
+    def set_graph(self, on: bool):
+        """Launch through captured CUDA graphs (default) or directly."""
+        _chk(self.lib.gea_ensemble_set_graph(self.h, 1 if on else 0), "gea_ensemble_set_graph")
 
     def step_async(self, n: int = 1):
         _chk(self.lib.gea_ensemble_step(self.h, int(n)), "gea_ensemble_step")

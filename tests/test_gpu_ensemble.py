@@ -135,3 +135,76 @@ def test_weights_and_autotune(gea):
     steps = ss[0].stats()["steps_done"]
     # one step to measure the iterations, one per shape and weight, one more
     assert steps == 1 + 3 * 2 + 1 and all(s.stats()["status"] == 0 for s in ss)
+
+
+def test_ensemble_graph_launch_equals_direct_launch(gea):
+    """The ensemble step as a replayed CUDA graph (one cooperative kernel node
+    with its own device copy of the arguments) gives the direct launch's
+    states bit for bit, over 1-step and 2-step calls and both slot parities;
+    members at different parities fall back to the direct launch."""
+    wls = W.les_ensemble(5, seed=4)
+
+    def members():
+        ss = [gea.Solver(wl.grid, wl.const) for wl in wls]
+        for s, wl in zip(ss, wls):
+            s.set_conservative(wl.fields)
+        return ss
+
+    out = []
+    for graph in (True, False):
+        ss = members()
+        E = gea.Ensemble(ss)
+        E.set_graph(graph)
+        for n in (1, 1, 2, 1, 2):
+            E.step(n)
+        E.close()
+        out.append([s.get_full() for s in ss])
+        assert all(s.stats()["steps_done"] == 7 and s.stats()["status"] == 0 for s in ss)
+    for a, b in zip(*out):
+        for k in a:
+            assert np.array_equal(a[k], b[k]), k
+    # parities apart: member 0 one step ahead
+    ss = members()
+    ss[0].step(1)
+    E = gea.Ensemble(ss)
+    E.step(2)
+    E.close()
+    assert ss[0].stats()["steps_done"] == 3 and ss[1].stats()["steps_done"] == 2
+    ref = gea.Solver(wls[0].grid, wls[0].const)
+    ref.set_conservative(wls[0].fields)
+    ref.step(3)
+    a, b = ss[0].get_full(), ref.get_full()
+    for k in ("rho", "T", "pp"):
+        assert np.abs(a[k] - b[k]).max() <= 1e-13 * np.abs(b[k]).max(), k
+
+
+def test_mixed_precision_ensemble(gea):
+    """Mixed-precision members (FP64 state, FP32 inner solves) in one launch:
+    each member's result is its own mixed persistent run's up to the order of
+    the sums (the FP32 solves' rounding; the bars of the mixed drivers'
+    agreement test), and FP64 and mixed members cannot share a launch."""
+    wls = W.les_ensemble(4, seed=5)
+    ss = []
+    for wl in wls:
+        s = gea.Solver(wl.grid, wl.const, mixed=True)
+        s.set_conservative(wl.fields)
+        ss.append(s)
+    E = gea.Ensemble(ss)
+    E.step(4)
+    E.close()
+    for s, wl in zip(ss, wls):
+        assert s.stats()["status"] == 0 and s.stats()["steps_done"] == 4
+        ref = gea.Solver(wl.grid, wl.const, mixed=True)
+        ref.set_conservative(wl.fields)
+        ref.step(4)
+        a, b = s.get_full(), ref.get_full()
+        for k in ("rho", "T", "pp"):
+            assert np.abs(a[k] - b[k]).max() <= 1e-11 * np.abs(b[k]).max(), k
+        vmax = max(np.abs(b["u"]).max(), np.abs(b["w"]).max())
+        for k in ("u", "w"):
+            assert np.abs(a[k] - b[k]).max() <= 1e-8 * vmax, k
+    f = gea.Solver(wls[0].grid, wls[0].const)
+    f.set_conservative(wls[0].fields)
+    with pytest.raises(gea.GeaError) as ei:
+        gea.Ensemble([f, ss[1]])
+    assert ei.value.code == gea.GEA_ERR_INVAL
