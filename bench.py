@@ -571,7 +571,9 @@ def run_learned(args):
 
 def run_ensemble(args):
     """The LES ensemble: one cooperative launch per step for all members
-    against one launch per member per step, same states, same step counts."""
+    against one launch per member per step, same states, same step counts;
+    then the same members in mixed precision, in one launch."""
+    import numpy as np
     import torch
     from paper_2303_10499_gb300 import build as B
     from paper_2303_10499_gb300 import gea
@@ -626,6 +628,33 @@ def run_ensemble(args):
     iters = [sv.stats()["cg_iters"] for sv in solvers[:3]]
     nb = E.blocks()
     E.close()
+    # the mixed-precision members (FP64 state, FP32 inner solves) in one
+    # launch, with the tuned shape, against the FP64 ensemble: time per step
+    # and max |theta'| difference after the same steps from the same states
+    shape = [k for k, v in gea.TILE_SHAPES.items() if v == tune["tile_shape"]][0]
+    mixed = [gea.Solver(wl.grid, wl.const, stream=stream, mixed=True) for wl in wls]
+    for sv in mixed:
+        sv.set_tile_shape(shape)
+
+    def reset_mixed():
+        for sv, wl in zip(mixed, wls):
+            sv.set_conservative(wl.fields)
+
+    EM = gea.Ensemble(mixed, stream=stream)
+    ms_mix, clocks_mix = timed(lambda: EM.step_async(1), reset_mixed)
+    EM.sync()
+    EM.close()
+    n_check = 20
+    reset()
+    reset_mixed()
+    E1 = gea.Ensemble(solvers, stream=stream)
+    E1.step(n_check)
+    E1.close()
+    EM = gea.Ensemble(mixed, stream=stream)
+    EM.step(n_check)
+    EM.close()
+    dth = max(float(np.abs(m.diagnostics(wl.theta_bar)[0] - f.diagnostics(wl.theta_bar)[0]).max())
+              for m, f, wl in zip(mixed, solvers, wls))
     value = cells * args.steps / (sum(ms_ens) / 1e3)
     seq = cells * args.steps / (sum(ms_seq) / 1e3)
     sizes = sorted({wl.grid.nx for wl in wls})
@@ -649,6 +678,11 @@ def run_ensemble(args):
                        "gain_vs_32x8": min(tune["ms_per_step_by_shape_and_beta"]["32x8"].values()) /
                        min(tune["ms_per_step_by_shape_and_beta"][tune["tile_shape"]].values())},
         "speedup_vs_one_launch_per_member": value / seq,
+        "mixed_precision_ensemble": {
+            "value": cells * args.steps / (sum(ms_mix) / 1e3), "unit": UNIT,
+            "ms_per_step": statistics.mean(ms_mix), "speedup_vs_fp64_ensemble": statistics.mean(ms_ens) /
+            statistics.mean(ms_mix), "tile_shape": tune["tile_shape"], "clocks": clocks_mix,
+            "max_abs_dtheta_K_vs_fp64_ensemble": dth, "steps_compared": n_check},
         "cg_iters_last_step_first_members": iters,
         "gpu_launches": 1, "clocks": clocks,
     }
