@@ -181,8 +181,12 @@ def test_ensemble_graph_launch_equals_direct_launch(gea):
 def test_mixed_precision_ensemble(gea):
     """Mixed-precision members (FP64 state, FP32 inner solves) in one launch:
     each member's result is its own mixed persistent run's up to the order of
-    the sums (the FP32 solves' rounding; the bars of the mixed drivers'
-    agreement test), and FP64 and mixed members cannot share a launch."""
+    the sums, and FP64 and mixed members cannot share a launch. In the
+    ensemble a member runs on fewer blocks than alone, so its FP32 reductions
+    add in another order and the inner solves (stopped at 1e-5 of their
+    initial residual) take other iterates within that tolerance: velocities
+    agree to well inside the mixed step's own distance to the FP64 step
+    (checked: at most a tenth of it), scalars to 1e-11."""
     wls = W.les_ensemble(4, seed=5)
     ss = []
     for wl in wls:
@@ -200,9 +204,14 @@ def test_mixed_precision_ensemble(gea):
         a, b = s.get_full(), ref.get_full()
         for k in ("rho", "T", "pp"):
             assert np.abs(a[k] - b[k]).max() <= 1e-11 * np.abs(b[k]).max(), k
-        vmax = max(np.abs(b["u"]).max(), np.abs(b["w"]).max())
+        f64 = gea.Solver(wl.grid, wl.const)
+        f64.set_conservative(wl.fields)
+        f64.step(4)
+        c = f64.get_full()
         for k in ("u", "w"):
-            assert np.abs(a[k] - b[k]).max() <= 1e-8 * vmax, k
+            d_ens = np.abs(a[k] - b[k]).max()
+            d_mixed = np.abs(b[k] - c[k]).max()
+            assert d_ens <= 0.1 * d_mixed, (k, d_ens, d_mixed)
     f = gea.Solver(wls[0].grid, wls[0].const)
     f.set_conservative(wls[0].fields)
     with pytest.raises(gea.GeaError) as ei:
