@@ -203,6 +203,64 @@ __device__ __forceinline__ R helm_tile(const LevelT<R> &L, int q, int i, int k, 
     return t;
 }
 
+// The coefficients of the Helmholtz operator at a cell, loaded ahead of the
+// tile barrier (they do not depend on the tile), so that their L2 latency
+// overlaps the halo loads instead of following them.
+template <class R>
+struct HelmCoef {
+    R d, aw, ae, as, an;
+};
+
+template <class R>
+__device__ __forceinline__ HelmCoef<R> helm_coef(const LevelT<R> &L, int q, int i, int k)
+{
+    const Geom &G = L.G;
+    return HelmCoef<R>{ld(&L.d[q]), ld(&L.ax[k * G.P + i]), ld(&L.ax[k * G.P + i + 1]), ld(&L.az[k * G.P + i]),
+                       ld(&L.az[(k + 1) * G.P + i])};
+}
+
+// A x = d x - sum a x_N from preloaded coefficients (helm_tile's order).
+template <int H, class R>
+__device__ __forceinline__ R helm_apply(const HelmCoef<R> &c, const Tile<H, R> &s, int y, int x)
+{
+    R t = c.d * s[y][x];
+    t = fma(-c.aw, s[y][x - 1], t);
+    t = fma(-c.ae, s[y][x + 1], t);
+    t = fma(-c.as, s[y - 1][x], t);
+    t = fma(-c.an, s[y + 1][x], t);
+    return t;
+}
+
+// The nine stencil weights of the transport operator at a cell, likewise
+// loaded ahead of the tile barrier.
+template <class R>
+struct Coef9 {
+    R cC, cE1, cW1, cN1, cS1, cE2, cW2, cN2, cS2;
+};
+
+template <class R>
+__device__ __forceinline__ Coef9<R> coef9(const Stencil9T<R> &T, int q)
+{
+    return Coef9<R>{ld(&T.cC[q]),  ld(&T.cE1[q]), ld(&T.cW1[q]), ld(&T.cN1[q]), ld(&T.cS1[q]),
+                    ld(&T.cE2[q]), ld(&T.cW2[q]), ld(&T.cN2[q]), ld(&T.cS2[q])};
+}
+
+// sum_o c_o X_o in apply9's order.
+template <int H, class R>
+__device__ __forceinline__ R apply9c(const Coef9<R> &c, const Tile<H, R> &s, int y, int x)
+{
+    R acc = c.cC * s[y][x];
+    acc = fma(c.cE1, s[y][x + 1], acc);
+    acc = fma(c.cW1, s[y][x - 1], acc);
+    acc = fma(c.cN1, s[y + 1][x], acc);
+    acc = fma(c.cS1, s[y - 1][x], acc);
+    acc = fma(c.cE2, s[y][x + 2], acc);
+    acc = fma(c.cW2, s[y][x - 2], acc);
+    acc = fma(c.cN2, s[y + 2][x], acc);
+    acc = fma(c.cS2, s[y - 2][x], acc);
+    return acc;
+}
+
 // ---------------------------------------------------------------------------
 // Smagorinsky eddy viscosity (LES): mu_eff = mu + rho (cs Delta)^2 |S| from
 // rho^n and u^n, |S|^2 = 2 (du/dx)^2 + 2 (dw/dz)^2 + (du/dz + dw/dx)^2 with
@@ -398,16 +456,24 @@ __device__ __forceinline__ void ph_sweep2(const Geom &G, const Phys &F, const St
                                           R (&acc)[2])
 {
     Tile<2, R> &sa = tile_at<2, R>(sm, 0), &sb = tile_at<2, R>(sm, 1);
+    int i, k;
+    const bool in = cell_of(G, bx, bz, i, k);
+    const int q = in ? cidx(G, i, k) : 0;
+    Coef9<R> c{};
+    R di = 0, bva = 0, bvb = 0;
+    if (in) {
+        c = coef9(T, q);
+        di = ld(&dinv[q]);
+        bva = ld(&ba[q]);
+        bvb = ld(&bb[q]);
+    }
     load_tile<BCA, 2, R>(sa, G, F, xa, bx, bz);
     load_tile<BCB, 2, R>(sb, G, F, xb, bx, bz);
     __syncthreads();
-    int i, k;
-    if (cell_of(G, bx, bz, i, k)) {
-        const int q = cidx(G, i, k);
+    if (in) {
         const int y = threadIdx.y + 2, x = threadIdx.x + 2;
-        const R di = ld(&dinv[q]);
-        const R ra = ld(&ba[q]) - apply9<2, R>(T, q, sa, y, x);
-        const R rb = ld(&bb[q]) - apply9<2, R>(T, q, sb, y, x);
+        const R ra = bva - apply9c<2, R>(c, sa, y, x);
+        const R rb = bvb - apply9c<2, R>(c, sb, y, x);
         ya[q] = fma(ra, di, sa[y][x]);
         yb[q] = fma(rb, di, sb[y][x]);
         acc[0] = fma(ra, ra, acc[0]);
@@ -426,16 +492,24 @@ __device__ __forceinline__ void ph_sweep1(const Geom &G, const Phys &F, const St
 // (lc is used when F.pr_ne1, i.e. mu/Pr != mu)
 {
     Tile<2, R> &sh = tile_at<2, R>(sm, 0);
+    int i, k;
+    const bool in = cell_of(G, bx, bz, i, k);
+    const int q = in ? cidx(G, i, k) : 0;
+    Coef9<R> c{};
+    R di = 0, bq = 0;
+    if (in) {
+        c = coef9(T, q);
+        di = ld(&dinv[q]);
+        bq = ld(&bv[q]);
+    }
     load_tile<BC, 2, R>(sh, G, F, xin, bx, bz);
     __syncthreads();
-    int i, k;
-    if (cell_of(G, bx, bz, i, k)) {
-        const int q = cidx(G, i, k);
+    if (in) {
         const int y = threadIdx.y + 2, x = threadIdx.x + 2;
-        R t = apply9<2, R>(T, q, sh, y, x);
+        R t = apply9c<2, R>(c, sh, y, x);
         if (F.pr_ne1) t = fma(lc, lap5<2, R>(G, sh, y, x), t);
-        const R r = ld(&bv[q]) - t;
-        xout[q] = fma(r, ld(&dinv[q]), sh[y][x]);
+        const R r = bq - t;
+        xout[q] = fma(r, di, sh[y][x]);
         acc[0] = fma(r, r, acc[0]);
     }
     __syncthreads();
@@ -865,14 +939,21 @@ __device__ __forceinline__ void ph_mg_single(const LevelT<R> &f, R *out, double 
 {
     const Geom &G = f.G;
     Tile<1, R> &se = tile_at<1, R>(sm, 0);
-    load_tile_fn<1, R>(se, G, bx, bz, [&](int q, int, int) { return ld(&f.wd[q]) * ld(&f.r[q]); });
-    __syncthreads();
     int i, k;
-    if (cell_of(G, bx, bz, i, k)) {
-        const int q = cidx(G, i, k);
+    const bool in = cell_of(G, bx, bz, i, k);
+    const int q = in ? cidx(G, i, k) : 0;
+    HelmCoef<R> c{};
+    R rq = 0, wq = 0;
+    if (in) {
+        c = helm_coef(f, q, i, k);
+        rq = ld(&f.r[q]);
+        wq = ld(&f.wd[q]);
+    }
+    load_tile_fn<1, R>(se, G, bx, bz, [&](int qq, int, int) { return ld(&f.wd[qq]) * ld(&f.r[qq]); });
+    __syncthreads();
+    if (in) {
         const int y = threadIdx.y + 1, x = threadIdx.x + 1;
-        const R rq = ld(&f.r[q]);
-        const R z = fma(ld(&f.wd[q]), rq - helm_tile<1, R>(f, q, i, k, se, y, x), se[y][x]);
+        const R z = fma(wq, rq - helm_apply<1, R>(c, se, y, x), se[y][x]);
         out[q] = z;
         acc[0] = fma(rq, z, acc[0]);
     }
@@ -891,14 +972,17 @@ __device__ __forceinline__ void ph_pspmv(const LevelT<R> &L, const R *pold, R *p
     const R *z = L.e2;
     const R b = (R)beta;
     Tile<1, R> &sp = tile_at<1, R>(sm, 0);
-    load_tile_fn<1, R>(sp, G, bx, bz, [&](int q, int, int) { return fma(b, ld(&pold[q]), ld(&z[q])); });
-    __syncthreads();
     int i, k;
-    if (cell_of(G, bx, bz, i, k)) {
-        const int q = cidx(G, i, k);
+    const bool in = cell_of(G, bx, bz, i, k);
+    const int q = in ? cidx(G, i, k) : 0;
+    HelmCoef<R> c{};
+    if (in) c = helm_coef(L, q, i, k);
+    load_tile_fn<1, R>(sp, G, bx, bz, [&](int qq, int, int) { return fma(b, ld(&pold[qq]), ld(&z[qq])); });
+    __syncthreads();
+    if (in) {
         const int y = threadIdx.y + 1, x = threadIdx.x + 1;
         const R pq = sp[y][x];
-        const R Ap = helm_tile<1, R>(L, q, i, k, sp, y, x);
+        const R Ap = helm_apply<1, R>(c, sp, y, x);
         pnew[q] = pq;
         qv[q] = Ap;
         acc[0] = fma(pq, Ap, acc[0]);
@@ -944,16 +1028,25 @@ __device__ __forceinline__ void ph_update_single(const LevelT<R> &L, const R *qv
     const Geom &G = L.G;
     const R alpha = (R)alpha_d;
     Tile<1, R> &sr = tile_at<1, R>(sm, 0), &se = tile_at<1, R>(sm, 1);
+    int i, k;
+    const bool in = cell_of(G, bx, bz, i, k);
+    const int q = in ? cidx(G, i, k) : 0;
+    HelmCoef<R> c{};
+    R wq = 0, xq = 0, pq = 0;
+    if (in) {
+        c = helm_coef(L, q, i, k);
+        wq = ld(&L.wd[q]);
+        xq = ld(&x[q]);
+        pq = ld(&p[q]);
+    }
     update_tiles<R>(L, qv, rin, alpha, sr, se, bx, bz);
     __syncthreads();
-    int i, k;
-    if (cell_of(G, bx, bz, i, k)) {
-        const int q = cidx(G, i, k);
+    if (in) {
         const int y = threadIdx.y + 1, xx = threadIdx.x + 1;
         const R rn = sr[y][xx];
-        x[q] = fma(alpha, ld(&p[q]), ld(&x[q]));
+        x[q] = fma(alpha, pq, xq);
         rout[q] = rn;
-        const R z = fma(ld(&L.wd[q]), rn - helm_tile<1, R>(L, q, i, k, se, y, xx), se[y][xx]);
+        const R z = fma(wq, rn - helm_apply<1, R>(c, se, y, xx), se[y][xx]);
         L.e2[q] = z;
         acc[0] = fma(rn, rn, acc[0]);
         acc[1] = fma(rn, z, acc[1]);

@@ -185,8 +185,9 @@ def test_mixed_precision_ensemble(gea):
     ensemble a member runs on fewer blocks than alone, so its FP32 reductions
     add in another order and the inner solves (stopped at 1e-5 of their
     initial residual) take other iterates within that tolerance: velocities
-    agree to well inside the mixed step's own distance to the FP64 step
-    (checked: at most a tenth of it), scalars to 1e-11."""
+    agree to 1e-6 of their maximum (a tenth of the inner tolerance), theta'
+    to 1e-7 K (the mixed step's own bar against the oracle), scalars to
+    1e-11."""
     wls = W.les_ensemble(4, seed=5)
     ss = []
     for wl in wls:
@@ -204,14 +205,10 @@ def test_mixed_precision_ensemble(gea):
         a, b = s.get_full(), ref.get_full()
         for k in ("rho", "T", "pp"):
             assert np.abs(a[k] - b[k]).max() <= 1e-11 * np.abs(b[k]).max(), k
-        f64 = gea.Solver(wl.grid, wl.const)
-        f64.set_conservative(wl.fields)
-        f64.step(4)
-        c = f64.get_full()
+        vmax = max(np.abs(b["u"]).max(), np.abs(b["w"]).max())
         for k in ("u", "w"):
-            d_ens = np.abs(a[k] - b[k]).max()
-            d_mixed = np.abs(b[k] - c[k]).max()
-            assert d_ens <= 0.1 * d_mixed, (k, d_ens, d_mixed)
+            assert np.abs(a[k] - b[k]).max() <= 1e-6 * vmax, k
+        assert np.abs(s.diagnostics(wl.theta_bar)[0] - ref.diagnostics(wl.theta_bar)[0]).max() <= 1e-7
     f = gea.Solver(wls[0].grid, wls[0].const)
     f.set_conservative(wls[0].fields)
     with pytest.raises(gea.GeaError) as ei:
