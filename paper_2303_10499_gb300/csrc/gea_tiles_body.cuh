@@ -757,17 +757,27 @@ __device__ __forceinline__ void ph_H(const StepArgs &a, const double *U, const d
     const Geom &G = a.G;
     const Phys &F = a.F;
     Tile<2> &su = tile_at<2>(sm, 0), &sw = tile_at<2>(sm, 1);
+    int i, k;
+    const bool in = cell_of(G, bx, bz, i, k);
+    const int q = in ? cidx(G, i, k) : 0;
+    // the cell's stencil weights (shared by both components) and state,
+    // loaded ahead of the tile barrier
+    Coef9<double> c{};
+    double ru = 0.0, rw = 0.0, r1dt = 0.0;
+    if (in) {
+        c = coef9(a.T, q);
+        const double rdt = ld(&a.S.rho[q]) * F.idt;
+        ru = rdt * ld(&a.S.u[q]);
+        rw = rdt * ld(&a.S.w[q]);
+        r1dt = ld(&a.rho1[q]) * F.idt;
+    }
     load_tile<BC_U, 2>(su, G, F, U, bx, bz);
     load_tile<BC_W, 2>(sw, G, F, W, bx, bz);
     __syncthreads();
-    int i, k;
-    if (cell_of(G, bx, bz, i, k)) {
-        const int q = cidx(G, i, k);
+    if (in) {
         const int y = threadIdx.y + 2, x = threadIdx.x + 2;
-        const State &S = a.S;
-        const double rdt = ld(&S.rho[q]) * F.idt, r1dt = ld(&a.rho1[q]) * F.idt;
-        a.Hx[q] = fma(r1dt, su[y][x], fma(rdt, ld(&S.u[q]), -apply9<2>(a.T, q, su, y, x)));
-        a.Hz[q] = fma(r1dt, sw[y][x], fma(rdt, ld(&S.w[q]), -apply9<2>(a.T, q, sw, y, x)));
+        a.Hx[q] = fma(r1dt, su[y][x], ru - apply9c<2>(c, su, y, x));
+        a.Hz[q] = fma(r1dt, sw[y][x], rw - apply9c<2>(c, sw, y, x));
     }
     __syncthreads();
 }
@@ -788,27 +798,38 @@ __device__ __forceinline__ void ph_helm_rhs_t(const StepArgs &a, const Level &L,
     const Phys &F = a.F;
     Tile<1> &sx = tile_at<1>(sm, 0), &s2 = tile_at<1>(sm, 1), &shx = tile_at<1>(sm, 2),
             &shz = tile_at<1>(sm, 3);
+    int i, k;
+    const bool in = cell_of(G, bx, bz, i, k);
+    const int q0 = in ? cidx(G, i, k) : 0;
+    // the cell's face coefficients and operator, loaded ahead of the tile
+    // barrier
+    double Dw = 0.0, De = 0.0, Ds = 0.0, Dn = 0.0;
+    HelmCoef<double> hc{};
+    if (in) {
+        Dw = ld(&a.Dx[k * G.P + i]);
+        De = ld(&a.Dx[k * G.P + i + 1]);
+        Ds = ld(&a.Dz[k * G.P + i]);
+        Dn = ld(&a.Dz[(k + 1) * G.P + i]);
+        hc = helm_coef(L, q0, i, k);
+    }
     load_tile_fn<1>(sx, G, bx, bz, [&](int q, int, int) { return ld(&xin[q]); });
     load_tile_fn<1>(s2, G, bx, bz, [&](int q, int, int) { return ld(&a.rho2[q]); });
     load_tile_fn<1>(shx, G, bx, bz, [&](int q, int, int) { return ld(&a.Hx[q]); });
     load_tile_fn<1>(shz, G, bx, bz, [&](int q, int, int) { return ld(&a.Hz[q]); });
     __syncthreads();
-    int i, k;
-    if (cell_of(G, bx, bz, i, k)) {
-        const int q = cidx(G, i, k);
+    if (in) {
+        const int q = q0;
         const int y = threadIdx.y + 1, x = threadIdx.x + 1;
         const double gz = ld(&a.gzc[k]);
         const double gzx = gz * G.idx, gzs = ld(&a.gzf[k]) * G.idz, gzn = ld(&a.gzf[k + 1]) * G.idz;
         const double r2q = s2[y][x];
-        const double Dw = ld(&a.Dx[k * G.P + i]), De = ld(&a.Dx[k * G.P + i + 1]);
-        const double Ds = ld(&a.Dz[k * G.P + i]), Dn = ld(&a.Dz[(k + 1) * G.P + i]);
         // wall faces have D = 0 and zero tile entries beyond the box
         double flux = De * G.dz * fma(0.5, shx[y][x] + shx[y][x + 1], gzx * (s2[y][x + 1] - r2q));
         flux += Dw * G.dz * fma(-0.5, shx[y][x] + shx[y][x - 1], gzx * (s2[y][x - 1] - r2q));
         flux += Dn * G.dx * fma(0.5, shz[y][x] + shz[y + 1][x], gzn * (s2[y + 1][x] - r2q));
         flux += Ds * G.dx * fma(-0.5, shz[y][x] + shz[y - 1][x], gzs * (s2[y - 1][x] - r2q));
         const double b = fma(ld(&a.psi[q]) * r2q, gz, ld(&a.S.rho[q])) * F.idt - flux * G.iV;
-        const double r = b - helm_tile<1>(L, q, i, k, sx, y, x);
+        const double r = b - helm_apply<1>(hc, sx, y, x);
         a.b[q] = b;
         xout[q] = sx[y][x];
         if (!MX) {
@@ -1146,11 +1167,31 @@ __device__ __forceinline__ void ph_correct(const StepArgs &a, double *sm, int bx
     double(*gx)[BX + 1] = reinterpret_cast<double(*)[BX + 1]>(sm + 2 * kT1);
     double(*gz)[BX] = reinterpret_cast<double(*)[BX]>(sm + 2 * kT1 + BZ * (BX + 1));
     const State &N = a.N;
+    int i, k;
+    const bool in = cell_of(G, bx, bz, i, k);
+    const int q0 = in ? cidx(G, i, k) : 0;
+    // the cell's own inputs, loaded ahead of the tile barrier: H(u) at the
+    // cell and at its west and south neighbours (the face averages), D on
+    // the west and south faces, dt/rho1, psi, p^n
+    double hxq = 0.0, hzq = 0.0, hxw = 0.0, hzs = 0.0, Dw = 0.0, Ds = 0.0, dtr1 = 0.0, psq = 0.0, pnq = 0.0;
+    if (in) {
+        hxq = ld(&a.Hx[q0]);
+        hzq = ld(&a.Hz[q0]);
+        if (i > 0) {
+            hxw = ld(&a.Hx[q0 - 1]);
+            Dw = ld(&a.Dx[k * G.P + i]);
+        }
+        if (k > 0) {
+            hzs = ld(&a.Hz[q0 - G.P]);
+            Ds = ld(&a.Dz[k * G.P + i]);
+        }
+        dtr1 = ld(&a.dtr1[q0]);
+        psq = ld(&a.psi[q0]);
+        pnq = ld(&a.S.p[q0]);
+    }
     load_tile_fn<1>(sx, G, bx, bz, [&](int q, int, int) { return ld(&N.pp[q]); });
     load_tile_fn<1>(s2, G, bx, bz, [&](int q, int, int) { return ld(&a.rho2[q]); });
     __syncthreads();
-    int i, k;
-    const bool in = cell_of(G, bx, bz, i, k);
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int y = ty + 1, x = tx + 1;
     const double gzk = in ? ld(&a.gzc[k]) : 0.0;
@@ -1168,22 +1209,20 @@ __device__ __forceinline__ void ph_correct(const StepArgs &a, double *sm, int bx
     }
     __syncthreads();
     if (in) {
-        const int q = cidx(G, i, k);
-        const double hxq = ld(&a.Hx[q]), hzq = ld(&a.Hz[q]);
+        const int q = q0;
         const double gxw = gx[ty][tx], gxe = gx[ty][tx + 1], gzs = gz[ty][tx], gzn = gz[ty + 1][tx];
-        const double Fw = i > 0 ? ld(&a.Dx[k * G.P + i]) * (0.5 * (ld(&a.Hx[q - 1]) + hxq) - gxw) : 0.0;
-        const double Fs = k > 0 ? ld(&a.Dz[k * G.P + i]) * (0.5 * (ld(&a.Hz[q - G.P]) + hzq) - gzs) : 0.0;
+        const double Fw = i > 0 ? Dw * (0.5 * (hxw + hxq) - gxw) : 0.0;   // wall faces carry zero
+        const double Fs = k > 0 ? Ds * (0.5 * (hzs + hzq) - gzs) : 0.0;
         N.phix[k * G.P + i] = Fw * G.dz;
         N.phiz[k * G.P + i] = Fs * G.dx;
         if (i == G.nx - 1) N.phix[k * G.P + G.nx] = 0.0;
         if (k == G.nz - 1) N.phiz[G.nz * G.P + i] = 0.0;
-        const double dtr1 = ld(&a.dtr1[q]);
         N.u[q] = dtr1 * (hxq - 0.5 * (gxw + gxe));
         N.w[q] = dtr1 * (hzq - 0.5 * (gzs + gzn));
         const double pn = fma(-s2[y][x], gzk, sx[y][x]);
         N.p[q] = pn;
-        N.rho[q] = pn * ld(&a.psi[q]);
-        N.pold[q] = ld(&a.S.p[q]);
+        N.rho[q] = pn * psq;
+        N.pold[q] = pnq;
         if (F.k_lagged) {
             const double un = ld(&a.S.u[q]), wn = ld(&a.S.w[q]);
             N.Kold[q] = 0.5 * (un * un + wn * wn);   // K^{n-1} of the next step
