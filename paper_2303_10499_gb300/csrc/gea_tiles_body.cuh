@@ -875,19 +875,26 @@ __device__ __forceinline__ void ph_mg_down(const LevelT<R> &f, const LevelT<R> &
     const Geom &G = f.G;
     Tile<1, R> &se = tile_at<1, R>(sm, 0);
     R(*sres)[BX] = reinterpret_cast<R(*)[BX]>(reinterpret_cast<R *>(sm) + kT1);
-    load_tile_fn<1, R>(se, G, bx, bz, [&](int q, int, int) { return ld(&f.wd[q]) * ld(&f.r[q]); });
-    __syncthreads();
     int i, k;
     const int tx = threadIdx.x, ty = threadIdx.y;
-    if (cell_of(G, bx, bz, i, k)) {
-        const int q = cidx(G, i, k);
+    const bool in = cell_of(G, bx, bz, i, k);
+    const int q0 = in ? cidx(G, i, k) : 0;
+    HelmCoef<R> hc{};
+    R rq = 0;
+    if (in) {   // ahead of the tile barrier
+        hc = helm_coef(f, q0, i, k);
+        rq = ld(&f.r[q0]);
+    }
+    load_tile_fn<1, R>(se, G, bx, bz, [&](int q, int, int) { return ld(&f.wd[q]) * ld(&f.r[q]); });
+    __syncthreads();
+    if (in) {
         const int y = ty + 1, x = tx + 1;
-        R t = (R)(1.0 - omega) * ld(&f.r[q]);
-        t = fma(ld(&f.ax[k * G.P + i]), se[y][x - 1], t);
-        t = fma(ld(&f.ax[k * G.P + i + 1]), se[y][x + 1], t);
-        t = fma(ld(&f.az[k * G.P + i]), se[y - 1][x], t);
-        t = fma(ld(&f.az[(k + 1) * G.P + i]), se[y + 1][x], t);
-        f.e[q] = se[y][x];
+        R t = (R)(1.0 - omega) * rq;
+        t = fma(hc.aw, se[y][x - 1], t);
+        t = fma(hc.ae, se[y][x + 1], t);
+        t = fma(hc.as, se[y - 1][x], t);
+        t = fma(hc.an, se[y + 1][x], t);
+        f.e[q0] = se[y][x];
         sres[ty][tx] = t;
     }
     __syncthreads();
@@ -936,17 +943,24 @@ __device__ __forceinline__ void ph_mg_up(const LevelT<R> &f, const R *res, const
 {
     const Geom &G = f.G;
     Tile<1, R> &se = tile_at<1, R>(sm, 0);
+    int i, k;
+    const bool in = cell_of(G, bx, bz, i, k);
+    const int q0 = in ? cidx(G, i, k) : 0;
+    HelmCoef<R> hc{};
+    R rq = 0, wq = 0;
+    if (in) {   // ahead of the tile barrier
+        hc = helm_coef(f, q0, i, k);
+        rq = ld(&res[q0]);
+        wq = ld(&f.wd[q0]);
+    }
     load_tile_fn<1, R>(se, G, bx, bz, [&](int q, int ii, int kk) {
         return ld(&f.e[q]) + ld(&ec[(kk >> 1) * Pc + (ii >> 1)]);
     });
     __syncthreads();
-    int i, k;
-    if (cell_of(G, bx, bz, i, k)) {
-        const int q = cidx(G, i, k);
+    if (in) {
         const int y = threadIdx.y + 1, x = threadIdx.x + 1;
-        const R rq = ld(&res[q]);
-        const R z = fma(ld(&f.wd[q]), rq - helm_tile<1, R>(f, q, i, k, se, y, x), se[y][x]);
-        out[q] = z;
+        const R z = fma(wq, rq - helm_apply<1, R>(hc, se, y, x), se[y][x]);
+        out[q0] = z;
         acc[0] = fma(rq, z, acc[0]);
     }
     __syncthreads();
@@ -1087,21 +1101,32 @@ __device__ __forceinline__ void ph_update_down(const LevelT<R> &f, const LevelT<
     const R alpha = (R)alpha_d;
     Tile<1, R> &sr = tile_at<1, R>(sm, 0), &se = tile_at<1, R>(sm, 1);
     R(*sres)[BX] = reinterpret_cast<R(*)[BX]>(reinterpret_cast<R *>(sm) + 2 * kT1);
-    update_tiles<R>(f, qv, rin, alpha, sr, se, bx, bz);
-    __syncthreads();
     int i, k;
     const int tx = threadIdx.x, ty = threadIdx.y;
-    if (cell_of(G, bx, bz, i, k)) {
-        const int q = cidx(G, i, k);
+    const bool in = cell_of(G, bx, bz, i, k);
+    const int q0 = in ? cidx(G, i, k) : 0;
+    R aw = 0, ae = 0, as = 0, an = 0, xq = 0, pq = 0;
+    if (in) {   // ahead of the tile barrier
+        aw = ld(&f.ax[k * G.P + i]);
+        ae = ld(&f.ax[k * G.P + i + 1]);
+        as = ld(&f.az[k * G.P + i]);
+        an = ld(&f.az[(k + 1) * G.P + i]);
+        xq = ld(&x[q0]);
+        pq = ld(&p[q0]);
+    }
+    update_tiles<R>(f, qv, rin, alpha, sr, se, bx, bz);
+    __syncthreads();
+    if (in) {
+        const int q = q0;
         const int y = ty + 1, xx = tx + 1;
         const R rn = sr[y][xx];
-        x[q] = fma(alpha, ld(&p[q]), ld(&x[q]));
+        x[q] = fma(alpha, pq, xq);
         rout[q] = rn;
         R t = (R)(1.0 - omega) * rn;
-        t = fma(ld(&f.ax[k * G.P + i]), se[y][xx - 1], t);
-        t = fma(ld(&f.ax[k * G.P + i + 1]), se[y][xx + 1], t);
-        t = fma(ld(&f.az[k * G.P + i]), se[y - 1][xx], t);
-        t = fma(ld(&f.az[(k + 1) * G.P + i]), se[y + 1][xx], t);
+        t = fma(aw, se[y][xx - 1], t);
+        t = fma(ae, se[y][xx + 1], t);
+        t = fma(as, se[y - 1][xx], t);
+        t = fma(an, se[y + 1][xx], t);
         f.e[q] = se[y][xx];
         sres[ty][tx] = t;
         acc[0] = fma(rn, rn, acc[0]);
