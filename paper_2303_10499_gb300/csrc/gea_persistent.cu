@@ -1,15 +1,18 @@
 // gea_persistent.cu -- the persistent step kernels for the 32 x 8 tile (the
-// tile of the per-phase kernels), the tile-shape table, and the argument
-// blocks of ensemble launches.
+// default shape, also the tile of the per-phase kernels), the tile-shape
+// table, and the argument blocks of ensemble launches.
 #include "gea_internal.cuh"
-#include "gea_tiles.cuh"
 
 #include <string.h>
 
 namespace gea {
-namespace tiles {
+namespace tiles_32x8 {
+constexpr int BX = 32;   // cells (threads) per tile row
+constexpr int BZ = 8;    // rows per tile
+constexpr bool kPrefetch = true;   // cell inputs loaded ahead of the tile barrier
+#include "gea_tiles_body.cuh"
 #include "gea_persistent_body.cuh"
-}  // namespace tiles
+}  // namespace tiles_32x8
 
 namespace tiles_16x16 {
 extern const PersistOps ops;
@@ -23,7 +26,7 @@ const PersistOps &persist_ops(int shape)
     switch (shape) {
     case SHAPE_16x16: return tiles_16x16::ops;
     case SHAPE_64x4: return tiles_64x4::ops;
-    default: return tiles::ops;
+    default: return tiles_32x8::ops;
     }
 }
 

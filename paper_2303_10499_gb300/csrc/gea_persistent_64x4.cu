@@ -9,6 +9,7 @@ namespace gea {
 namespace tiles_64x4 {
 constexpr int BX = 64;   // cells (threads) per tile row
 constexpr int BZ = 4;   // rows per tile
+constexpr bool kPrefetch = true;   // cell inputs loaded ahead of the tile barrier
 #include "gea_tiles_body.cuh"
 #include "gea_persistent_body.cuh"
 }  // namespace tiles_64x4

@@ -6,6 +6,7 @@
 
 namespace gea {
 namespace tiles {
+constexpr bool kPrefetch = false;   // per-phase kernels: occupancy first
 #include "gea_tiles_body.cuh"
 }  // namespace tiles
 }  // namespace gea

@@ -203,9 +203,13 @@ __device__ __forceinline__ R helm_tile(const LevelT<R> &L, int q, int i, int k, 
     return t;
 }
 
-// The coefficients of the Helmholtz operator at a cell, loaded ahead of the
-// tile barrier (they do not depend on the tile), so that their L2 latency
-// overlaps the halo loads instead of following them.
+// The coefficients of the Helmholtz operator at a cell. With kPrefetch (set
+// by the includer: the persistent kernels, whose occupancy the register
+// file already fixes at three blocks per SM) the phases load a cell's own
+// coefficients and inputs ahead of the tile barrier (they do not depend on
+// the tile), so that their L2 latency overlaps the halo loads; without it
+// (the per-phase kernels, where the extra live registers would cost
+// occupancy) after the barrier.
 template <class R>
 struct HelmCoef {
     R d, aw, ae, as, an;
@@ -461,16 +465,18 @@ __device__ __forceinline__ void ph_sweep2(const Geom &G, const Phys &F, const St
     const int q = in ? cidx(G, i, k) : 0;
     Coef9<R> c{};
     R di = 0, bva = 0, bvb = 0;
-    if (in) {
+    auto fetch = [&] {
         c = coef9(T, q);
         di = ld(&dinv[q]);
         bva = ld(&ba[q]);
         bvb = ld(&bb[q]);
-    }
+    };
+    if (kPrefetch && in) fetch();
     load_tile<BCA, 2, R>(sa, G, F, xa, bx, bz);
     load_tile<BCB, 2, R>(sb, G, F, xb, bx, bz);
     __syncthreads();
     if (in) {
+        if (!kPrefetch) fetch();
         const int y = threadIdx.y + 2, x = threadIdx.x + 2;
         const R ra = bva - apply9c<2, R>(c, sa, y, x);
         const R rb = bvb - apply9c<2, R>(c, sb, y, x);
@@ -497,14 +503,16 @@ __device__ __forceinline__ void ph_sweep1(const Geom &G, const Phys &F, const St
     const int q = in ? cidx(G, i, k) : 0;
     Coef9<R> c{};
     R di = 0, bq = 0;
-    if (in) {
+    auto fetch = [&] {
         c = coef9(T, q);
         di = ld(&dinv[q]);
         bq = ld(&bv[q]);
-    }
+    };
+    if (kPrefetch && in) fetch();
     load_tile<BC, 2, R>(sh, G, F, xin, bx, bz);
     __syncthreads();
     if (in) {
+        if (!kPrefetch) fetch();
         const int y = threadIdx.y + 2, x = threadIdx.x + 2;
         R t = apply9c<2, R>(c, sh, y, x);
         if (F.pr_ne1) t = fma(lc, lap5<2, R>(G, sh, y, x), t);
@@ -764,17 +772,19 @@ __device__ __forceinline__ void ph_H(const StepArgs &a, const double *U, const d
     // loaded ahead of the tile barrier
     Coef9<double> c{};
     double ru = 0.0, rw = 0.0, r1dt = 0.0;
-    if (in) {
+    auto fetch = [&] {
         c = coef9(a.T, q);
         const double rdt = ld(&a.S.rho[q]) * F.idt;
         ru = rdt * ld(&a.S.u[q]);
         rw = rdt * ld(&a.S.w[q]);
         r1dt = ld(&a.rho1[q]) * F.idt;
-    }
+    };
+    if (kPrefetch && in) fetch();
     load_tile<BC_U, 2>(su, G, F, U, bx, bz);
     load_tile<BC_W, 2>(sw, G, F, W, bx, bz);
     __syncthreads();
     if (in) {
+        if (!kPrefetch) fetch();
         const int y = threadIdx.y + 2, x = threadIdx.x + 2;
         a.Hx[q] = fma(r1dt, su[y][x], ru - apply9c<2>(c, su, y, x));
         a.Hz[q] = fma(r1dt, sw[y][x], rw - apply9c<2>(c, sw, y, x));
@@ -805,19 +815,21 @@ __device__ __forceinline__ void ph_helm_rhs_t(const StepArgs &a, const Level &L,
     // barrier
     double Dw = 0.0, De = 0.0, Ds = 0.0, Dn = 0.0;
     HelmCoef<double> hc{};
-    if (in) {
+    auto fetch = [&] {
         Dw = ld(&a.Dx[k * G.P + i]);
         De = ld(&a.Dx[k * G.P + i + 1]);
         Ds = ld(&a.Dz[k * G.P + i]);
         Dn = ld(&a.Dz[(k + 1) * G.P + i]);
         hc = helm_coef(L, q0, i, k);
-    }
+    };
+    if (kPrefetch && in) fetch();
     load_tile_fn<1>(sx, G, bx, bz, [&](int q, int, int) { return ld(&xin[q]); });
     load_tile_fn<1>(s2, G, bx, bz, [&](int q, int, int) { return ld(&a.rho2[q]); });
     load_tile_fn<1>(shx, G, bx, bz, [&](int q, int, int) { return ld(&a.Hx[q]); });
     load_tile_fn<1>(shz, G, bx, bz, [&](int q, int, int) { return ld(&a.Hz[q]); });
     __syncthreads();
     if (in) {
+        if (!kPrefetch) fetch();
         const int q = q0;
         const int y = threadIdx.y + 1, x = threadIdx.x + 1;
         const double gz = ld(&a.gzc[k]);
@@ -881,13 +893,15 @@ __device__ __forceinline__ void ph_mg_down(const LevelT<R> &f, const LevelT<R> &
     const int q0 = in ? cidx(G, i, k) : 0;
     HelmCoef<R> hc{};
     R rq = 0;
-    if (in) {   // ahead of the tile barrier
+    auto fetch = [&] {   // ahead of the tile barrier
         hc = helm_coef(f, q0, i, k);
         rq = ld(&f.r[q0]);
-    }
+    };
+    if (kPrefetch && in) fetch();
     load_tile_fn<1, R>(se, G, bx, bz, [&](int q, int, int) { return ld(&f.wd[q]) * ld(&f.r[q]); });
     __syncthreads();
     if (in) {
+        if (!kPrefetch) fetch();
         const int y = ty + 1, x = tx + 1;
         R t = (R)(1.0 - omega) * rq;
         t = fma(hc.aw, se[y][x - 1], t);
@@ -948,16 +962,18 @@ __device__ __forceinline__ void ph_mg_up(const LevelT<R> &f, const R *res, const
     const int q0 = in ? cidx(G, i, k) : 0;
     HelmCoef<R> hc{};
     R rq = 0, wq = 0;
-    if (in) {   // ahead of the tile barrier
+    auto fetch = [&] {   // ahead of the tile barrier
         hc = helm_coef(f, q0, i, k);
         rq = ld(&res[q0]);
         wq = ld(&f.wd[q0]);
-    }
+    };
+    if (kPrefetch && in) fetch();
     load_tile_fn<1, R>(se, G, bx, bz, [&](int q, int ii, int kk) {
         return ld(&f.e[q]) + ld(&ec[(kk >> 1) * Pc + (ii >> 1)]);
     });
     __syncthreads();
     if (in) {
+        if (!kPrefetch) fetch();
         const int y = threadIdx.y + 1, x = threadIdx.x + 1;
         const R z = fma(wq, rq - helm_apply<1, R>(hc, se, y, x), se[y][x]);
         out[q0] = z;
@@ -979,14 +995,16 @@ __device__ __forceinline__ void ph_mg_single(const LevelT<R> &f, R *out, double 
     const int q = in ? cidx(G, i, k) : 0;
     HelmCoef<R> c{};
     R rq = 0, wq = 0;
-    if (in) {
+    auto fetch = [&] {
         c = helm_coef(f, q, i, k);
         rq = ld(&f.r[q]);
         wq = ld(&f.wd[q]);
-    }
+    };
+    if (kPrefetch && in) fetch();
     load_tile_fn<1, R>(se, G, bx, bz, [&](int qq, int, int) { return ld(&f.wd[qq]) * ld(&f.r[qq]); });
     __syncthreads();
     if (in) {
+        if (!kPrefetch) fetch();
         const int y = threadIdx.y + 1, x = threadIdx.x + 1;
         const R z = fma(wq, rq - helm_apply<1, R>(c, se, y, x), se[y][x]);
         out[q] = z;
@@ -1011,10 +1029,11 @@ __device__ __forceinline__ void ph_pspmv(const LevelT<R> &L, const R *pold, R *p
     const bool in = cell_of(G, bx, bz, i, k);
     const int q = in ? cidx(G, i, k) : 0;
     HelmCoef<R> c{};
-    if (in) c = helm_coef(L, q, i, k);
+    if (kPrefetch && in) c = helm_coef(L, q, i, k);
     load_tile_fn<1, R>(sp, G, bx, bz, [&](int qq, int, int) { return fma(b, ld(&pold[qq]), ld(&z[qq])); });
     __syncthreads();
     if (in) {
+        if (!kPrefetch) c = helm_coef(L, q, i, k);
         const int y = threadIdx.y + 1, x = threadIdx.x + 1;
         const R pq = sp[y][x];
         const R Ap = helm_apply<1, R>(c, sp, y, x);
@@ -1068,15 +1087,17 @@ __device__ __forceinline__ void ph_update_single(const LevelT<R> &L, const R *qv
     const int q = in ? cidx(G, i, k) : 0;
     HelmCoef<R> c{};
     R wq = 0, xq = 0, pq = 0;
-    if (in) {
+    auto fetch = [&] {
         c = helm_coef(L, q, i, k);
         wq = ld(&L.wd[q]);
         xq = ld(&x[q]);
         pq = ld(&p[q]);
-    }
+    };
+    if (kPrefetch && in) fetch();
     update_tiles<R>(L, qv, rin, alpha, sr, se, bx, bz);
     __syncthreads();
     if (in) {
+        if (!kPrefetch) fetch();
         const int y = threadIdx.y + 1, xx = threadIdx.x + 1;
         const R rn = sr[y][xx];
         x[q] = fma(alpha, pq, xq);
@@ -1106,17 +1127,19 @@ __device__ __forceinline__ void ph_update_down(const LevelT<R> &f, const LevelT<
     const bool in = cell_of(G, bx, bz, i, k);
     const int q0 = in ? cidx(G, i, k) : 0;
     R aw = 0, ae = 0, as = 0, an = 0, xq = 0, pq = 0;
-    if (in) {   // ahead of the tile barrier
+    auto fetch = [&] {   // ahead of the tile barrier
         aw = ld(&f.ax[k * G.P + i]);
         ae = ld(&f.ax[k * G.P + i + 1]);
         as = ld(&f.az[k * G.P + i]);
         an = ld(&f.az[(k + 1) * G.P + i]);
         xq = ld(&x[q0]);
         pq = ld(&p[q0]);
-    }
+    };
+    if (kPrefetch && in) fetch();
     update_tiles<R>(f, qv, rin, alpha, sr, se, bx, bz);
     __syncthreads();
     if (in) {
+        if (!kPrefetch) fetch();
         const int q = q0;
         const int y = ty + 1, xx = tx + 1;
         const R rn = sr[y][xx];
@@ -1199,7 +1222,7 @@ __device__ __forceinline__ void ph_correct(const StepArgs &a, double *sm, int bx
     // cell and at its west and south neighbours (the face averages), D on
     // the west and south faces, dt/rho1, psi, p^n
     double hxq = 0.0, hzq = 0.0, hxw = 0.0, hzs = 0.0, Dw = 0.0, Ds = 0.0, dtr1 = 0.0, psq = 0.0, pnq = 0.0;
-    if (in) {
+    auto fetch = [&] {
         hxq = ld(&a.Hx[q0]);
         hzq = ld(&a.Hz[q0]);
         if (i > 0) {
@@ -1213,7 +1236,8 @@ __device__ __forceinline__ void ph_correct(const StepArgs &a, double *sm, int bx
         dtr1 = ld(&a.dtr1[q0]);
         psq = ld(&a.psi[q0]);
         pnq = ld(&a.S.p[q0]);
-    }
+    };
+    if (kPrefetch && in) fetch();
     load_tile_fn<1>(sx, G, bx, bz, [&](int q, int, int) { return ld(&N.pp[q]); });
     load_tile_fn<1>(s2, G, bx, bz, [&](int q, int, int) { return ld(&a.rho2[q]); });
     __syncthreads();
@@ -1234,6 +1258,7 @@ __device__ __forceinline__ void ph_correct(const StepArgs &a, double *sm, int bx
     }
     __syncthreads();
     if (in) {
+        if (!kPrefetch) fetch();
         const int q = q0;
         const double gxw = gx[ty][tx], gxe = gx[ty][tx + 1], gzs = gz[ty][tx], gzn = gz[ty + 1][tx];
         const double Fw = i > 0 ? Dw * (0.5 * (hxw + hxq) - gxw) : 0.0;   // wall faces carry zero
