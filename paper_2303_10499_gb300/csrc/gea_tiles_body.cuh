@@ -209,7 +209,14 @@ __device__ __forceinline__ R helm_tile(const LevelT<R> &L, int q, int i, int k, 
 // coefficients and inputs ahead of the tile barrier (they do not depend on
 // the tile), so that their L2 latency overlaps the halo loads; without it
 // (the per-phase kernels, where the extra live registers would cost
-// occupancy) after the barrier.
+// occupancy) after the barrier. Two phases load early in every instance:
+// the single-field Jacobi sweep and the CG direction update with A p, which
+// measured faster that way in the per-phase kernels too (the 4096 x 2048
+// enthalpy sweep went from 0.47 to 0.80 of the FP64 peak), while the
+// two-field sweep, the multigrid phases and the right-hand sides lost
+// occupancy and speed.
+constexpr bool kPrefetchSweep1 = true;
+constexpr bool kPrefetchSpmv = true;
 template <class R>
 struct HelmCoef {
     R d, aw, ae, as, an;
@@ -508,11 +515,11 @@ __device__ __forceinline__ void ph_sweep1(const Geom &G, const Phys &F, const St
         di = ld(&dinv[q]);
         bq = ld(&bv[q]);
     };
-    if (kPrefetch && in) fetch();
+    if (kPrefetchSweep1 && in) fetch();
     load_tile<BC, 2, R>(sh, G, F, xin, bx, bz);
     __syncthreads();
     if (in) {
-        if (!kPrefetch) fetch();
+        if (!kPrefetchSweep1) fetch();
         const int y = threadIdx.y + 2, x = threadIdx.x + 2;
         R t = apply9c<2, R>(c, sh, y, x);
         if (F.pr_ne1) t = fma(lc, lap5<2, R>(G, sh, y, x), t);
@@ -1029,11 +1036,11 @@ __device__ __forceinline__ void ph_pspmv(const LevelT<R> &L, const R *pold, R *p
     const bool in = cell_of(G, bx, bz, i, k);
     const int q = in ? cidx(G, i, k) : 0;
     HelmCoef<R> c{};
-    if (kPrefetch && in) c = helm_coef(L, q, i, k);
+    if (kPrefetchSpmv && in) c = helm_coef(L, q, i, k);
     load_tile_fn<1, R>(sp, G, bx, bz, [&](int qq, int, int) { return fma(b, ld(&pold[qq]), ld(&z[qq])); });
     __syncthreads();
     if (in) {
-        if (!kPrefetch) c = helm_coef(L, q, i, k);
+        if (!kPrefetchSpmv) c = helm_coef(L, q, i, k);
         const int y = threadIdx.y + 1, x = threadIdx.x + 1;
         const R pq = sp[y][x];
         const R Ap = helm_apply<1, R>(c, sp, y, x);
