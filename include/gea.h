@@ -319,7 +319,9 @@ double gea_last_pressure_ms(gea_ctx *ctx);
 typedef struct gea_kernel_time {
     char name[40];     /* kernel (stage) name */
     int32_t launches;  /* launches in the step */
-    int64_t cells;     /* grid cells covered, summed over the launches */
+    int64_t cells;     /* grid cells covered, summed over the launches that did
+                          their work (a solver-loop kernel launched after its
+                          loop finished returns at once and adds none) */
     double ms;         /* summed CUDA-event durations of the launches */
 } gea_kernel_time;
 

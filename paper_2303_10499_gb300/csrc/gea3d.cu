@@ -1596,7 +1596,10 @@ int capture_while3(gea3d_ctx *ctx, cudaStream_t s, Body body)
     return GEA_OK;
 }
 
-// Event pairs around the launches of an eager step (per-kernel timing).
+// Event pairs around the launches of an eager step (per-kernel timing). A
+// solver-loop kernel launched after its loop finished returns at once (a
+// converged solve, or the second Jacobi sweep of a pair that copies): it is
+// recorded with zero cells, the loop's flags read before the launch.
 struct Trace3 {
     struct Rec {
         const char *name;
@@ -1604,6 +1607,18 @@ struct Trace3 {
         cudaEvent_t e0, e1;
     };
     std::vector<Rec> recs;
+    const Sc *dsc = nullptr;
+    // the loop whose finished flag makes the kernel return, or -1
+    static int gate(const char *name)
+    {
+        static const char *cg[] = {"g3_mg_coarse", "g3_mg_down", "g3_mg_single", "g3_mg_up", "g3_pupd", "g3_spmv",
+                                   "g3_update", "g3_mx_pupd", "g3_mx_spmv", "g3_mx_update"};
+        for (const char *c : cg)
+            if (!strcmp(name, c)) return L_CG;
+        if (!strcmp(name, "g3_mom") || !strcmp(name, "g3_mx_mom")) return L_MOM;
+        if (!strcmp(name, "g3_enth") || !strcmp(name, "g3_mx_enth")) return L_ENTH;
+        return -1;
+    }
     ~Trace3()
     {
         for (auto &r : recs) {
@@ -1622,6 +1637,13 @@ void traced(Trace3 *tr, const char *name, const Geo &G, cudaStream_t st, Go go)
         return;
     }
     Trace3::Rec r{name, (long long)G.nx * G.ny * G.nz, nullptr, nullptr};
+    const int g = Trace3::gate(name);
+    if (g >= 0 && tr->dsc) {
+        Sc h;
+        if (cudaMemcpyAsync(&h, tr->dsc, sizeof(Sc), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+            cudaStreamSynchronize(st) == cudaSuccess && (h.status || h.done[g]))
+            r.cells = 0;
+    }
     cudaEventCreate(&r.e0);
     cudaEventCreate(&r.e1);
     cudaEventRecord(r.e0, st);
@@ -2115,6 +2137,7 @@ int gea3d_profile_step(gea3d_ctx *ctx, gea_kernel_time *out, int32_t max_entries
     if (h.status) return fail3(ctx, h.status, "device status %d", h.status);
     {
         Trace3 tr;
+        tr.dsc = ctx->sc;
         const int rc = record3(ctx, (int)(h.steps_done & 1), ctx->stream, false, &tr);
         if (rc) return rc;
         CK3(cudaStreamSynchronize(ctx->stream));

@@ -440,7 +440,13 @@ int ensure_graphs(gea_ctx *ctx)
 }
 
 // Records an event pair around every launch of an eager step, inside an
-// NVTX range named after the kernel (visible to a timeline profiler).
+// NVTX range named after the kernel (visible to a timeline profiler). A
+// kernel of a solver loop returns at once when its loop has already
+// finished (the solve converged inside the loop body, or the second Jacobi
+// sweep of a pair copies after the first met the tolerance): such a launch is
+// recorded with zero cells, so that the per-cell work models count only
+// launches that did the work (the loop's flags are read before the launch;
+// the profiled step synchronises anyway).
 struct EventTracer : Tracer {
     struct Rec {
         const char *name;
@@ -448,8 +454,29 @@ struct EventTracer : Tracer {
         cudaEvent_t e0, e1;
     };
     std::vector<Rec> recs;
+    const Scal *dsc;
+    explicit EventTracer(const Scal *sc) : dsc(sc) {}
+    // the loop whose finished flag makes the kernel return, or -1
+    static int gate(const char *name)
+    {
+        static const char *cg[] = {"mg_down", "mg_coarse", "mg_up", "mg_single", "cg_pspmv", "cg_update_single",
+                                   "cg_update_down", "mx_mg_down", "mx_mg_coarse", "mx_mg_up", "mx_mg_single",
+                                   "mx_pspmv", "mx_update_single", "mx_update_down"};
+        for (const char *c : cg)
+            if (!strcmp(name, c)) return LOOP_CG;
+        if (!strcmp(name, "mom_jacobi") || !strcmp(name, "mx_mom")) return LOOP_MOM;
+        if (!strcmp(name, "enth_jacobi") || !strcmp(name, "mx_enth")) return LOOP_ENTH;
+        return -1;
+    }
     void begin(const char *name, long long cells, cudaStream_t st) override
     {
+        const int g = gate(name);
+        if (g >= 0) {
+            Scal h;
+            if (cudaMemcpyAsync(&h, dsc, sizeof(Scal), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+                cudaStreamSynchronize(st) == cudaSuccess && (h.status || h.done[g]))
+                cells = 0;
+        }
         Rec r{name, cells, nullptr, nullptr};
         nvtxRangePushA(name);
         cudaEventCreate(&r.e0);
@@ -966,7 +993,7 @@ int gea_profile_step(gea_ctx *ctx, gea_kernel_time *out, int32_t max_entries, in
     if (rc) return rc;
     if (h.status) return fail(ctx, h.status, "device status %d", h.status);
     const int from = current_slot(ctx, h);
-    EventTracer tr;
+    EventTracer tr(ctx->sc);
     rc = record_any(ctx, from, ctx->stream, false, &tr);
     if (rc) return rc;
     CK(cudaStreamSynchronize(ctx->stream));
