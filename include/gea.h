@@ -54,7 +54,7 @@ enum {
 };
 
 enum { GEA_STATE_CONSERVATIVE = 0, GEA_STATE_FULL = 1 };
-enum { GEA_FLAG_GRAPH = 1, GEA_FLAG_MIXED = 2, GEA_FLAG_KEEP_R0 = 4 };
+enum { GEA_FLAG_GRAPH = 1, GEA_FLAG_MIXED = 2, GEA_FLAG_KEEP_R0 = 4, GEA_FLAG_DEBUG_PADS = 8 };
 enum { GEA_MEM_HOST = 0, GEA_MEM_DEVICE = 1 };
 
 /* Uniform Cartesian grid: nx * nz cells on [0, lx] x [0, lz] (metres).
@@ -102,6 +102,12 @@ typedef struct gea_grid {
  *            GEA_FLAG_KEEP_R0: keep the initial residual of the first
  *            corrector's pressure solve (GEA_FIELD_R0; CUDA-graph driver;
  *            not with GEA_FLAG_MIXED).
+ *            GEA_FLAG_DEBUG_PADS: a debugging layout in place of a device
+ *            memory checker (gea_debug_* below): every array gets a guard
+ *            band of GEA_PAD_GUARD_BYTES bytes behind it (one more before
+ *            the first), and the padding of every row, the unused tail of
+ *            every array and the guard bands are filled with a NaN pattern
+ *            at creation. The step results are the same as without it.
  *            Other bits must be 0.
  *  mp_rtol   relative tolerance of the FP32 solves (GEA_FLAG_MIXED only);
  *            0 selects 1e-5, otherwise 1e-7 <= mp_rtol < 1.
@@ -372,6 +378,20 @@ int gea_mass_energy_noalloc(int32_t nx, int32_t nz, double lx, double lz, double
  * GEA_ERR_CUDA. */
 int gea_probe_fma(int32_t bits, int32_t blocks, int32_t iters, void *out, void *stream);
 
+/* Grid-barrier latency probe (the paper has no counterpart): one cooperative
+ * launch of `blocks` blocks of 256 threads (all resident at once) that pass
+ * `iters` grid barriers of the protocol the persistent step kernels use
+ * (one acquire-release arrival per block on a monotone counter, acquire
+ * polls until it reaches the barrier's count), with nothing between them;
+ * read_status != 0 adds the read of a status word after each barrier, as
+ * those kernels do. scratch: caller-owned device memory of at least 16
+ * bytes, zeroed by the call; its third 32-bit word is nonzero afterwards if a
+ * bounded wait (2^22 polls) gave up. Enqueued on `stream`; the caller times
+ * it with CUDA events (time / iters = one barrier). Errors: GEA_ERR_INVAL
+ * (blocks < 1, iters < 1, null scratch, more blocks than fit at once),
+ * GEA_ERR_CUDA. */
+int gea_probe_barrier(int32_t blocks, int32_t iters, int32_t read_status, void *scratch, void *stream);
+
 /* ---- ensembles: many independent contexts advanced by one launch ----
  *
  * An ensemble runs the steps of n contexts (members, each with its own
@@ -413,6 +433,67 @@ int gea_ensemble_set_graph(gea_ensemble *e, int32_t on);
 /* Wait for the launches; the first member error code, or GEA_OK. */
 int gea_ensemble_sync(gea_ensemble *e);
 void gea_ensemble_destroy(gea_ensemble *e);
+
+/* ---- Pad checking (GEA_FLAG_DEBUG_PADS contexts) ----
+ * A stand-in for a device memory checker. Every array of a context lives in
+ * one device allocation as rows of a fixed pitch (the row pitch of a cell
+ * array is round_up(nx + 1, 32) elements), so an index off by one in x
+ * lands in a row's padding, and a row or array overrun lands in the array's
+ * unused tail or the guard band behind it. With the flag, all of these
+ * "pad" elements hold GEA_PAD_POISON64 (FP64 arrays) or GEA_PAD_POISON32
+ * (FP32 arrays), NaN bit patterns: a kernel that writes out of bounds
+ * changes a pad (found by the checks below), and one that reads out of
+ * bounds draws a NaN into its results (found by the residual norms,
+ * GEA_ERR_NONFINITE, and by comparison with a reference). The library's
+ * kernels neither read nor write pads. */
+#define GEA_PAD_GUARD_BYTES 512
+#define GEA_PAD_POISON64 0x7FF4BAD0DEAD0BADull
+#define GEA_PAD_POISON32 0x7FA0BAD0u
+
+/* One array of the context's allocation: cols x rows elements in use, each
+ * row `pitch` elements long, then unused elements up to `span` (the array's
+ * tail and its guard band). Element (row r, column c) is at
+ * ptr + (r * pitch + c) * elem_bytes. */
+typedef struct gea_pad_region {
+    char name[24];       /* e.g. "S0.phix", "L1.az", "F.T.cC" (F: FP32) */
+    void *ptr;           /* device pointer to element (0, 0) */
+    int32_t elem_bytes;  /* 8 (FP64) or 4 (FP32) */
+    int32_t pitch, rows, cols;
+    int64_t span;        /* elements from ptr to the next array */
+} gea_pad_region;
+
+/* Result of a pad check. */
+typedef struct gea_pad_report {
+    int64_t bad;          /* pad elements that no longer hold the poison */
+    int32_t launch;       /* gea_debug_step: index of the first launch after
+                             which a pad had changed, -1 if none */
+    char kernel[40];      /* its kernel (stage) name, "" if none */
+    char array[24];       /* array of the first changed pad element ("" if none):
+                             gea_debug_step: the lowest one changed by that
+                             launch; gea_debug_check_pads: the lowest one */
+    int32_t row, col;     /* its position (row >= rows or col >= cols of the array) */
+} gea_pad_report;
+
+/* The context's arrays (up to max entries into out; their number into *n).
+ * Errors: GEA_ERR_INVAL (null pointers, or a context without
+ * GEA_FLAG_DEBUG_PADS). */
+int gea_debug_pad_regions(gea_ctx *ctx, gea_pad_region *out, int32_t max, int32_t *n);
+
+/* Write the poison into every pad element again. Synchronises.
+ * Errors: GEA_ERR_INVAL (null ctx, no GEA_FLAG_DEBUG_PADS), GEA_ERR_CUDA. */
+int gea_debug_poison(gea_ctx *ctx);
+
+/* Count the pad elements that no longer hold the poison (a device kernel
+ * over every array; rep->launch = -1). Synchronises. Errors as
+ * gea_debug_poison. */
+int gea_debug_check_pads(gea_ctx *ctx, gea_pad_report *rep);
+
+/* Advance one step with the kernels of gea_profile_step, launched one by
+ * one, checking every pad after every launch; rep names the first launch
+ * that changed a pad, and rep->bad counts the changed pads after the step.
+ * Returns the step's own status (as gea_step) when the step fails.
+ * Synchronises. Errors as gea_profile_step, and as gea_debug_poison. */
+int gea_debug_step(gea_ctx *ctx, gea_pad_report *rep);
 
 const char *gea_last_error(const gea_ctx *ctx);
 void gea_destroy(gea_ctx *ctx);

@@ -15,8 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgea.so")
 SOURCES = ["gea_kernels.cu", "gea_persistent.cu", "gea_persistent_16x16.cu", "gea_persistent_64x4.cu", "gea_mixed.cu", "gea_capi.cu", "gea_noalloc.cu",
-           "gea_conv.cu", "gea_net.cu", "gea3d.cu", "gea_probe.cu"]
-HEADERS = ["gea_internal.cuh", "gea_tiles.cuh", "gea_tiles_body.cuh", "gea_persistent_body.cuh"]
+           "gea_conv.cu", "gea_net.cu", "gea3d.cu", "gea_probe.cu", "gea_debug.cu"]
+HEADERS = ["gea_internal.cuh", "gea_tiles.cuh", "gea_tiles_body.cuh", "gea_persistent_body.cuh", "gea_debug.cuh"]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]

@@ -10,10 +10,12 @@
 // round trip. Two graphs (state 0 -> 1 and state 1 -> 0) are built on the
 // first step.
 #include "gea_internal.cuh"
+#include "gea_debug.cuh"
 #include "../../include/gea.h"
 #include "../../include/gea_net.h"
 
 #include <nvtx3/nvToolsExt.h>
+#include <limits.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -39,6 +41,7 @@ struct gea_ctx {
         *Dz, *Hx, *Hz, *b, *p0, *p1, *q, *dtr1;
     double *gzc, *gzf;                     // g z of cell-centre rows (nz) and z-face rows (nz + 1)
     double *stage;                         // staging for conservative set/get (4 fields)
+    size_t stage_stride = 0;               // elements from one staging field to the next
     double *thbar;                         // nz values
     double *thout;                         // theta' output
     std::vector<Level> L;                 // FP64 hierarchy (mixed precision: the finest level only)
@@ -64,6 +67,11 @@ struct gea_ctx {
     long long wait_polls = -1;            // grid-barrier poll limit of the persistent kernels (< 0: default)
     int shape = SHAPE_32x8;               // tile shape of the persistent kernels (gea_set_tile_shape)
     long long steps_at_sync = 0;          // device steps_done at the last sync
+    // GEA_FLAG_DEBUG_PADS: the pitched arrays, on the host and the device,
+    // and the check results (two: per-launch tracking, final count)
+    std::vector<gea_pad_region> pads;
+    PadRegionDev *dpads = nullptr;
+    PadResult *dpres = nullptr;
     char err[256] = {0};
 };
 
@@ -498,6 +506,21 @@ struct EventTracer : Tracer {
     }
 };
 
+// Checks every pad of a GEA_FLAG_DEBUG_PADS context after every launch of
+// an eager step (check ordinal = the launch's index).
+struct PadTracer : Tracer {
+    gea_ctx *ctx;
+    std::vector<const char *> names;
+    cudaError_t err = cudaSuccess;
+    explicit PadTracer(gea_ctx *c) : ctx(c) {}
+    void begin(const char *name, long long, cudaStream_t) override { names.push_back(name); }
+    void end(cudaStream_t st) override
+    {
+        cudaError_t e = launch_pad_check(ctx->dpads, (int)ctx->pads.size(), ctx->dpres, (int)names.size() - 1, st);
+        if (err == cudaSuccess) err = e;
+    }
+};
+
 int read_scal(gea_ctx *ctx, Scal *h)
 {
     CK(cudaMemcpyAsync(h, ctx->sc, sizeof(Scal), cudaMemcpyDeviceToHost, ctx->stream));
@@ -541,7 +564,7 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
     if (!(c->R > 0) || !(c->cp > c->R) || !(c->g >= 0) || !(c->p0 > 0) || !(c->mu >= 0) ||
         !(c->Pr > 0) || !(c->dt > 0) || c->n_corr < 1 || c->n_corr > 4 || !(c->jac_rtol > 0) ||
         c->jac_maxit < 1 || !(c->cg_rtol > 0) || c->cg_maxit < 1 || c->mg_min_cells < 0 ||
-        (c->flags & ~(GEA_FLAG_GRAPH | GEA_FLAG_MIXED | GEA_FLAG_KEEP_R0)) ||
+        (c->flags & ~(GEA_FLAG_GRAPH | GEA_FLAG_MIXED | GEA_FLAG_KEEP_R0 | GEA_FLAG_DEBUG_PADS)) ||
         (c->reading_flags & ~(uint32_t)GEA_READING_K_LAGGED) ||
         ((c->flags & GEA_FLAG_KEEP_R0) && (c->flags & GEA_FLAG_MIXED)))
         return GEA_ERR_INVAL;
@@ -612,6 +635,9 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
     }
     total += round_up((kGcntDoubles + 8 * nb_all) * sizeof(double), 256);   // group counters, reduction partials
     total += round_up(sizeof(Scal), 256);
+    const bool dbg = (c->flags & GEA_FLAG_DEBUG_PADS) != 0;
+    const size_t guard = dbg ? GEA_PAD_GUARD_BYTES : 0;
+    if (dbg) total += guard * (kMaxPadRegions + 1);
     ctx->mem_bytes = total;
     if (cudaMalloc(&ctx->mem, total) != cudaSuccess) {
         cudaGetLastError();
@@ -619,60 +645,105 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
         return GEA_ERR_NOMEM;
     }
     cudaMemset(ctx->mem, 0, total);
-    char *ptr = ctx->mem;
+    char *ptr = ctx->mem + guard;
     auto take = [&](size_t bytes) { double *r = (double *)ptr; ptr += bytes; return r; };
+    // one pitched array (rows x cols in use, the level's pitch), recorded
+    // for pad checking, with the guard band behind it
+    auto arr = [&](const Geom &g, int rows, int cols, int esize, const char *fmt, int i) -> char * {
+        const size_t bytes = round_up((size_t)g.P * rows * esize, 256);
+        char *r = ptr;
+        ptr += bytes + guard;
+        if (dbg && ctx->pads.size() < (size_t)kMaxPadRegions) {
+            gea_pad_region pr;
+            memset(&pr, 0, sizeof(pr));
+            snprintf(pr.name, sizeof(pr.name), fmt, i);
+            pr.ptr = r;
+            pr.elem_bytes = esize;
+            pr.pitch = g.P;
+            pr.rows = rows;
+            pr.cols = cols;
+            pr.span = (int64_t)((bytes + guard) / esize);
+            ctx->pads.push_back(pr);
+        }
+        return r;
+    };
+    // a vector of n doubles (one row of n)
+    auto vec = [&](size_t n, const char *name) -> double * {
+        Geom g1 = G;
+        g1.P = (int)n;
+        return (double *)arr(g1, 1, (int)n, 8, name, 0);
+    };
+    const int nx = G.nx, nz = G.nz;
+    auto cellA = [&](const char *fmt, int i) { return (double *)arr(G, nz, nx, 8, fmt, i); };
     for (int s = 0; s < 2; ++s) {
         State &S = ctx->S[s];
-        S.rho = take(cell); S.u = take(cell); S.w = take(cell); S.T = take(cell); S.h = take(cell);
-        S.p = take(cell); S.pp = take(cell); S.pold = take(cell); S.phix = take(cell); S.phiz = take(fz);
-        S.Kold = take(cell);
+        S.rho = cellA("S%d.rho", s); S.u = cellA("S%d.u", s); S.w = cellA("S%d.w", s);
+        S.T = cellA("S%d.T", s); S.h = cellA("S%d.h", s); S.p = cellA("S%d.p", s);
+        S.pp = cellA("S%d.pp", s); S.pold = cellA("S%d.pold", s);
+        S.phix = (double *)arr(G, nz, nx + 1, 8, "S%d.phix", s);
+        S.phiz = (double *)arr(G, nz + 1, nx, 8, "S%d.phiz", s);
+        S.Kold = cellA("S%d.Kold", s);
     }
     Stencil9 &T = ctx->T;
-    T.cC = take(cell); T.cE1 = take(cell); T.cE2 = take(cell); T.cW1 = take(cell); T.cW2 = take(cell);
-    T.cN1 = take(cell); T.cN2 = take(cell); T.cS1 = take(cell); T.cS2 = take(cell);
-    ctx->rho1 = take(cell); ctx->dinvu = take(cell); ctx->dinvh = take(cell);
-    ctx->bu = take(cell); ctx->bw = take(cell);
-    ctx->ua = take(cell); ctx->wa = take(cell); ctx->ub = take(cell); ctx->wb = take(cell);
-    ctx->bh = take(cell); ctx->ha = take(cell); ctx->hb = take(cell); ctx->rho2 = take(cell);
-    ctx->psi = take(cell); ctx->Dx = take(cell); ctx->Dz = take(fz); ctx->Hx = take(cell);
-    ctx->Hz = take(cell); ctx->b = take(cell); ctx->p0 = take(cell); ctx->p1 = take(cell);
-    ctx->q = take(cell);
-    ctx->dtr1 = take(cell);
-    ctx->gzc = take(round_up((2 * (size_t)G.nz + 1) * sizeof(double), 256));
-    ctx->gzf = ctx->gzc + G.nz;
-    ctx->stage = take(4 * cell);
-    ctx->thout = take(cell);
-    ctx->thbar = take(round_up(G.nz * sizeof(double), 256));
-    if (c->flags & GEA_FLAG_KEEP_R0) ctx->r0keep = take(cell);
-    if (c->cs > 0.0) ctx->mueff = take(cell);
+    T.cC = cellA("T.cC", 0); T.cE1 = cellA("T.cE1", 0); T.cE2 = cellA("T.cE2", 0); T.cW1 = cellA("T.cW1", 0);
+    T.cW2 = cellA("T.cW2", 0); T.cN1 = cellA("T.cN1", 0); T.cN2 = cellA("T.cN2", 0); T.cS1 = cellA("T.cS1", 0);
+    T.cS2 = cellA("T.cS2", 0);
+    ctx->rho1 = cellA("rho1", 0); ctx->dinvu = cellA("dinvu", 0); ctx->dinvh = cellA("dinvh", 0);
+    ctx->bu = cellA("bu", 0); ctx->bw = cellA("bw", 0);
+    ctx->ua = cellA("ua", 0); ctx->wa = cellA("wa", 0); ctx->ub = cellA("ub", 0); ctx->wb = cellA("wb", 0);
+    ctx->bh = cellA("bh", 0); ctx->ha = cellA("ha", 0); ctx->hb = cellA("hb", 0); ctx->rho2 = cellA("rho2", 0);
+    ctx->psi = cellA("psi", 0);
+    ctx->Dx = (double *)arr(G, nz, nx + 1, 8, "Dx", 0);
+    ctx->Dz = (double *)arr(G, nz + 1, nx, 8, "Dz", 0);
+    ctx->Hx = cellA("Hx", 0); ctx->Hz = cellA("Hz", 0); ctx->b = cellA("b", 0);
+    ctx->p0 = cellA("p0", 0); ctx->p1 = cellA("p1", 0); ctx->q = cellA("q", 0);
+    ctx->dtr1 = cellA("dtr1", 0);
+    ctx->gzc = vec(2 * (size_t)nz + 1, "gz");
+    ctx->gzf = ctx->gzc + nz;
+    ctx->stage = cellA("stage%d", 0);
+    for (int j = 1; j < 4; ++j) cellA("stage%d", j);
+    ctx->stage_stride = (arr_bytes(G, nz) + guard) / sizeof(double);
+    ctx->thout = cellA("thout", 0);
+    ctx->thbar = vec(nz, "thbar");
+    if (c->flags & GEA_FLAG_KEEP_R0) ctx->r0keep = cellA("r0keep", 0);
+    if (c->cs > 0.0) ctx->mueff = cellA("mueff", 0);
     for (size_t lv = 0; lv < nlev64; ++lv) {
         const Geom &g = lg[lv];
+        const int l_ = (int)lv;
         Level l;
         l.G = g;
-        const size_t lc = arr_bytes(g, g.nz), lf = arr_bytes(g, g.nz + 1);
-        l.c = take(lc); l.d = take(lc); l.wd = take(lc); l.ax = take(lc); l.az = take(lf);
-        l.r = take(lc); l.e = take(lc); l.e2 = take(lc); l.r_alt = take(lc);
+        auto la = [&](const char *fmt) { return (double *)arr(g, g.nz, g.nx, 8, fmt, l_); };
+        l.c = la("L%d.c"); l.d = la("L%d.d"); l.wd = la("L%d.wd");
+        l.ax = (double *)arr(g, g.nz, g.nx + 1, 8, "L%d.ax", l_);
+        l.az = (double *)arr(g, g.nz + 1, g.nx, 8, "L%d.az", l_);
+        l.r = la("L%d.r"); l.e = la("L%d.e"); l.e2 = la("L%d.e2"); l.r_alt = la("L%d.r_alt");
         ctx->L.push_back(l);
     }
     if (ctx->mixed) {
-        auto takef = [&](size_t bytes) { return (float *)take(bytes); };
+        auto cellF = [&](const char *fmt, int i) { return (float *)arr(G, nz, nx, 4, fmt, i); };
         MixedArgs &m = ctx->mx;
         Stencil9F &T32 = m.T;
-        T32.cC = takef(cellf); T32.cE1 = takef(cellf); T32.cE2 = takef(cellf); T32.cW1 = takef(cellf);
-        T32.cW2 = takef(cellf); T32.cN1 = takef(cellf); T32.cN2 = takef(cellf); T32.cS1 = takef(cellf);
-        T32.cS2 = takef(cellf);
-        m.dinvu = takef(cellf); m.dinvh = takef(cellf);
-        m.r0u = takef(cellf); m.r0w = takef(cellf); m.r0h = takef(cellf);
-        for (int j = 0; j < 2; ++j) { m.du[j] = takef(cellf); m.dw[j] = takef(cellf); m.dh[j] = takef(cellf); }
-        m.x = takef(cellf); m.p0 = takef(cellf); m.p1 = takef(cellf); m.q = takef(cellf);
+        T32.cC = cellF("F.T.cC", 0); T32.cE1 = cellF("F.T.cE1", 0); T32.cE2 = cellF("F.T.cE2", 0);
+        T32.cW1 = cellF("F.T.cW1", 0); T32.cW2 = cellF("F.T.cW2", 0); T32.cN1 = cellF("F.T.cN1", 0);
+        T32.cN2 = cellF("F.T.cN2", 0); T32.cS1 = cellF("F.T.cS1", 0); T32.cS2 = cellF("F.T.cS2", 0);
+        m.dinvu = cellF("F.dinvu", 0); m.dinvh = cellF("F.dinvh", 0);
+        m.r0u = cellF("F.r0u", 0); m.r0w = cellF("F.r0w", 0); m.r0h = cellF("F.r0h", 0);
+        for (int j = 0; j < 2; ++j) {
+            m.du[j] = cellF("F.du%d", j); m.dw[j] = cellF("F.dw%d", j); m.dh[j] = cellF("F.dh%d", j);
+        }
+        m.x = cellF("F.x", 0); m.p0 = cellF("F.p0", 0); m.p1 = cellF("F.p1", 0); m.q = cellF("F.q", 0);
         const double rt = c->mp_rtol != 0.0 ? c->mp_rtol : kMixedRtol;
         m.tol2 = rt * rt;
-        for (const Geom &g : lg) {
+        for (size_t lv = 0; lv < lg.size(); ++lv) {
+            const Geom &g = lg[lv];
+            const int l_ = (int)lv;
             LevelF l;
             l.G = g;
-            const size_t lc = arr_bytes_f(g, g.nz), lf = arr_bytes_f(g, g.nz + 1);
-            l.c = takef(lc); l.d = takef(lc); l.wd = takef(lc); l.ax = takef(lc); l.az = takef(lf);
-            l.r = takef(lc); l.e = takef(lc); l.e2 = takef(lc); l.r_alt = takef(lc);
+            auto la = [&](const char *fmt) { return (float *)arr(g, g.nz, g.nx, 4, fmt, l_); };
+            l.c = la("F.L%d.c"); l.d = la("F.L%d.d"); l.wd = la("F.L%d.wd");
+            l.ax = (float *)arr(g, g.nz, g.nx + 1, 4, "F.L%d.ax", l_);
+            l.az = (float *)arr(g, g.nz + 1, g.nx, 4, "F.L%d.az", l_);
+            l.r = la("F.L%d.r"); l.e = la("F.L%d.e"); l.e2 = la("F.L%d.e2"); l.r_alt = la("F.L%d.r_alt");
             ctx->Lf.push_back(l);
         }
     }
@@ -691,6 +762,24 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
         for (int k = 0; k < G.nz; ++k) h[k] = ctx->F.g * ((k + 0.5) * G.dz);
         for (int k = 0; k <= G.nz; ++k) h[G.nz + k] = ctx->F.g * (k * G.dz);
         if (cudaMemcpy(ctx->gzc, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+            gea_destroy(ctx);
+            return GEA_ERR_CUDA;
+        }
+    }
+    if (dbg) {
+        // the region table on the device, two check results, then the poison
+        std::vector<PadRegionDev> hr;
+        for (const gea_pad_region &pr : ctx->pads)
+            hr.push_back(PadRegionDev{(char *)pr.ptr, (long long)pr.span, pr.elem_bytes, pr.pitch, pr.rows, pr.cols});
+        if (cudaMalloc(&ctx->dpads, hr.size() * sizeof(PadRegionDev)) != cudaSuccess ||
+            cudaMalloc(&ctx->dpres, 2 * sizeof(PadResult)) != cudaSuccess) {
+            cudaGetLastError();
+            gea_destroy(ctx);
+            return GEA_ERR_NOMEM;
+        }
+        if (cudaMemcpy(ctx->dpads, hr.data(), hr.size() * sizeof(PadRegionDev), cudaMemcpyHostToDevice) !=
+                cudaSuccess ||
+            launch_pad_poison(ctx->dpads, (int)hr.size(), 0) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
             gea_destroy(ctx);
             return GEA_ERR_CUDA;
         }
@@ -735,7 +824,7 @@ int gea_set_state(gea_ctx *ctx, const gea_state_view *v)
     State &S = ctx->S[0];
     if (v->kind == GEA_STATE_CONSERVATIVE) {
         if (!v->rhou || !v->rhow || !v->rhoe) return fail(ctx, GEA_ERR_INVAL, "null conservative field");
-        const size_t cellw = arr_bytes(G, nz) / sizeof(double);
+        const size_t cellw = ctx->stage_stride;
         double *st = ctx->stage;
         int rc;
         if ((rc = copy_in(ctx, st, v->rho, nx, nz)) || (rc = copy_in(ctx, st + cellw, v->rhou, nx, nz)) ||
@@ -865,7 +954,7 @@ int gea_get_state(gea_ctx *ctx, gea_state_view *v)
         }
     } else if (v->kind == GEA_STATE_CONSERVATIVE) {
         // computed on the device into the staging area, then copied out
-        const size_t cellw = arr_bytes(G, nz) / sizeof(double);
+        const size_t cellw = ctx->stage_stride;
         double *st = ctx->stage;
         launch_conserve(G, ctx->F, S, st, st + cellw, st + 2 * cellw, st + 3 * cellw, ctx->stream);
         CK(cudaGetLastError());
@@ -1016,6 +1105,101 @@ int gea_profile_step(gea_ctx *ctx, gea_kernel_time *out, int32_t max_entries, in
     }
     *n_entries = (int32_t)agg.size();
     for (size_t j = 0; j < agg.size() && (int32_t)j < max_entries; ++j) out[j] = agg[j];
+    ctx->steps_at_sync += 1;
+    return gea_sync(ctx);
+}
+
+namespace {
+
+int pad_reset(gea_ctx *ctx)
+{
+    PadResult h[2];
+    for (PadResult &r : h) {
+        r.bad = 0;
+        r.key = ~0ull;
+        r.first = INT_MAX;
+        r.pad_ = 0;
+    }
+    CK(cudaMemcpyAsync(ctx->dpres, h, sizeof(h), cudaMemcpyHostToDevice, ctx->stream));
+    return GEA_OK;
+}
+
+// rep from the per-launch tracking (slot 0, names: the launches) and the
+// final count (slot 1)
+int pad_report(gea_ctx *ctx, const std::vector<const char *> *names, gea_pad_report *rep)
+{
+    PadResult h[2];
+    CK(cudaMemcpyAsync(h, ctx->dpres, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    memset(rep, 0, sizeof(*rep));
+    rep->bad = (int64_t)h[1].bad;
+    rep->launch = -1;
+    const PadResult &f = names ? h[0] : h[1];
+    if (names && f.first != INT_MAX) {
+        rep->launch = f.first;
+        if (f.first >= 0 && (size_t)f.first < names->size())
+            snprintf(rep->kernel, sizeof(rep->kernel), "%s", (*names)[f.first]);
+    }
+    if (f.key != ~0ull) {
+        const size_t reg = (size_t)(f.key >> 40);
+        const long long e = (long long)(f.key & ((1ull << 40) - 1));
+        if (reg < ctx->pads.size()) {
+            const gea_pad_region &pr = ctx->pads[reg];
+            snprintf(rep->array, sizeof(rep->array), "%s", pr.name);
+            rep->row = (int32_t)(e / pr.pitch);
+            rep->col = (int32_t)(e % pr.pitch);
+        }
+    }
+    return GEA_OK;
+}
+
+}  // namespace
+
+int gea_debug_pad_regions(gea_ctx *ctx, gea_pad_region *out, int32_t max, int32_t *n)
+{
+    if (!ctx || !n || (!out && max > 0)) return GEA_ERR_INVAL;
+    if (!ctx->dpads) return fail(ctx, GEA_ERR_INVAL, "the context was created without GEA_FLAG_DEBUG_PADS");
+    *n = (int32_t)ctx->pads.size();
+    for (size_t j = 0; j < ctx->pads.size() && (int32_t)j < max; ++j) out[j] = ctx->pads[j];
+    return GEA_OK;
+}
+
+int gea_debug_poison(gea_ctx *ctx)
+{
+    if (!ctx) return GEA_ERR_INVAL;
+    if (!ctx->dpads) return fail(ctx, GEA_ERR_INVAL, "the context was created without GEA_FLAG_DEBUG_PADS");
+    CK(launch_pad_poison(ctx->dpads, (int)ctx->pads.size(), ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return GEA_OK;
+}
+
+int gea_debug_check_pads(gea_ctx *ctx, gea_pad_report *rep)
+{
+    if (!ctx || !rep) return GEA_ERR_INVAL;
+    if (!ctx->dpads) return fail(ctx, GEA_ERR_INVAL, "the context was created without GEA_FLAG_DEBUG_PADS");
+    int rc = pad_reset(ctx);
+    if (rc) return rc;
+    CK(launch_pad_check(ctx->dpads, (int)ctx->pads.size(), ctx->dpres + 1, 0, ctx->stream));
+    return pad_report(ctx, nullptr, rep);
+}
+
+int gea_debug_step(gea_ctx *ctx, gea_pad_report *rep)
+{
+    if (!ctx || !rep) return GEA_ERR_INVAL;
+    if (!ctx->dpads) return fail(ctx, GEA_ERR_INVAL, "the context was created without GEA_FLAG_DEBUG_PADS");
+    if (!ctx->have_state) return fail(ctx, GEA_ERR_STATE, "no state set");
+    Scal h;
+    int rc = read_scal(ctx, &h);
+    if (rc) return rc;
+    if (h.status) return fail(ctx, h.status, "device status %d", h.status);
+    if ((rc = pad_reset(ctx))) return rc;
+    const int from = current_slot(ctx, h);
+    PadTracer tr(ctx);
+    rc = record_any(ctx, from, ctx->stream, false, &tr);
+    if (rc) return rc;
+    CK(tr.err);
+    CK(launch_pad_check(ctx->dpads, (int)ctx->pads.size(), ctx->dpres + 1, INT_MAX, ctx->stream));
+    if ((rc = pad_report(ctx, &tr.names, rep))) return rc;
     ctx->steps_at_sync += 1;
     return gea_sync(ctx);
 }
@@ -1390,6 +1574,8 @@ void gea_destroy(gea_ctx *ctx)
     if (ctx->cap) cudaStreamDestroy(ctx->cap);
     if (ctx->cap2) cudaStreamDestroy(ctx->cap2);
     if (ctx->mem) cudaFree(ctx->mem);
+    if (ctx->dpads) cudaFree(ctx->dpads);
+    if (ctx->dpres) cudaFree(ctx->dpres);
     if (ctx->net_r) cudaFree(ctx->net_r);
     if (ctx->net_e) cudaFree(ctx->net_e);
     if (ctx->net_s) cudaFree(ctx->net_s);

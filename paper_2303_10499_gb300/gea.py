@@ -12,7 +12,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
-from typing import Dict, Optional
+from typing import Dict, List, Optional
 
 import numpy as np
 
@@ -21,7 +21,8 @@ from .build import LIB
 GEA_OK, GEA_ERR_INVAL, GEA_ERR_NOMEM, GEA_ERR_CUDA, GEA_ERR_NOCONV, GEA_ERR_NONFINITE, \
     GEA_ERR_STATE, GEA_ERR_TIMEOUT = range(8)
 STATE_CONSERVATIVE, STATE_FULL = 0, 1
-FLAG_GRAPH, FLAG_MIXED, FLAG_KEEP_R0 = 1, 2, 4
+FLAG_GRAPH, FLAG_MIXED, FLAG_KEEP_R0, FLAG_DEBUG_PADS = 1, 2, 4, 8
+PAD_POISON64, PAD_POISON32 = 0x7FF4BAD0DEAD0BAD, 0x7FA0BAD0
 MEM_HOST, MEM_DEVICE = 0, 1
 FIELDS = {"rho1": 0, "u1": 1, "w1": 2, "h1": 3, "rho2": 4, "Hx": 5, "Hz": 6, "b": 7,
           "Dx": 8, "Dz": 9, "hc": 10, "hax": 11, "haz": 12, "r0": 13}
@@ -73,6 +74,16 @@ class _KTime(C.Structure):
                 ("ms", C.c_double)]
 
 
+class _PadRegion(C.Structure):
+    _fields_ = [("name", C.c_char * 24), ("ptr", C.c_void_p), ("elem_bytes", C.c_int32),
+                ("pitch", C.c_int32), ("rows", C.c_int32), ("cols", C.c_int32), ("span", C.c_int64)]
+
+
+class _PadReport(C.Structure):
+    _fields_ = [("bad", C.c_int64), ("launch", C.c_int32), ("kernel", C.c_char * 40),
+                ("array", C.c_char * 24), ("row", C.c_int32), ("col", C.c_int32)]
+
+
 _lib = None
 
 
@@ -98,6 +109,10 @@ def library() -> C.CDLL:
         lib.gea_last_pressure_ms.argtypes = [P]
         lib.gea_last_pressure_ms.restype = C.c_double
         lib.gea_profile_step.argtypes = [P, C.POINTER(_KTime), C.c_int32, C.POINTER(C.c_int32)]
+        lib.gea_debug_pad_regions.argtypes = [P, C.POINTER(_PadRegion), C.c_int32, C.POINTER(C.c_int32)]
+        lib.gea_debug_poison.argtypes = [P]
+        lib.gea_debug_check_pads.argtypes = [P, C.POINTER(_PadReport)]
+        lib.gea_debug_step.argtypes = [P, C.POINTER(_PadReport)]
         lib.gea_last_error.argtypes = [P]
         lib.gea_last_error.restype = C.c_char_p
         lib.gea_destroy.argtypes = [P]
@@ -110,6 +125,7 @@ def library() -> C.CDLL:
         lib.gea_set_tile_shape.argtypes = [P, I]
         lib.gea_apply_precond.argtypes = [P, P, P]
         lib.gea_probe_fma.argtypes = [I, I, I, P, P]
+        lib.gea_probe_barrier.argtypes = [I, I, I, P, P]
         lib.gea_ensemble_create.argtypes = [C.POINTER(P), I, P, C.POINTER(P)]
         lib.gea_ensemble_set_stream.argtypes = [P, P]
         lib.gea_ensemble_blocks.argtypes = [P, I]
@@ -164,17 +180,19 @@ class Solver:
     """One context of the library: a grid, its constants and device state."""
 
     def __init__(self, grid, const, mg_min_cells: int = 0, stream=None, graph: bool = False,
-                 mixed: bool = False, mp_rtol: float = 0.0, keep_r0: bool = False):
+                 mixed: bool = False, mp_rtol: float = 0.0, keep_r0: bool = False,
+                 debug_pads: bool = False):
         """graph=True runs each step as a CUDA graph of per-phase kernels
         instead of the persistent cooperative kernel (GEA_FLAG_GRAPH).
         mixed=True selects the mixed-precision step (GEA_FLAG_MIXED): FP32
         inner solves for FP64 increments, to ||r|| <= mp_rtol ||r0|| (0: the
-        library default)."""
+        library default). debug_pads=True lays the arrays out with guard
+        bands and NaN-poisoned pads (GEA_FLAG_DEBUG_PADS; debug_* methods)."""
         self.lib = library()
         self.grid, self.const = grid, const
         g = _Grid(grid.nx, grid.nz, grid.lx, grid.lz)
         flags = (FLAG_GRAPH if graph else 0) | (FLAG_MIXED if mixed else 0) | \
-            (FLAG_KEEP_R0 if keep_r0 else 0)
+            (FLAG_KEEP_R0 if keep_r0 else 0) | (FLAG_DEBUG_PADS if debug_pads else 0)
         c = _Const(const.R, const.cp, const.g, const.p0, const.mu, const.Pr, const.dt,
                    const.n_corr, const.jac_rtol, const.jac_maxit, const.cg_rtol, const.cg_maxit,
                    mg_min_cells, flags, mp_rtol, getattr(const, "cs", 0.0),
@@ -383,6 +401,37 @@ class Solver:
         return {buf[i].name.decode(): {"launches": buf[i].launches, "cells": buf[i].cells,
                                        "ms": buf[i].ms} for i in range(min(n.value, 64))}
 
+    # ---- pad checking (debug_pads=True) ----
+    def debug_pad_regions(self) -> List[Dict]:
+        """The context's arrays: name, device pointer, element bytes, pitch,
+        rows and columns in use, span (elements up to the next array)."""
+        buf = (_PadRegion * 1024)()
+        n = C.c_int32()
+        self._check(self.lib.gea_debug_pad_regions(self.h, buf, 1024, C.byref(n)))
+        return [{"name": r.name.decode(), "ptr": r.ptr, "elem_bytes": r.elem_bytes, "pitch": r.pitch,
+                 "rows": r.rows, "cols": r.cols, "span": r.span} for r in buf[:min(n.value, 1024)]]
+
+    def debug_poison(self):
+        self._check(self.lib.gea_debug_poison(self.h))
+
+    @staticmethod
+    def _pad_report(r) -> Dict:
+        return {"bad": r.bad, "launch": r.launch, "kernel": r.kernel.decode(), "array": r.array.decode(),
+                "row": r.row, "col": r.col}
+
+    def debug_check_pads(self) -> Dict:
+        """Pad elements that no longer hold the poison, and the first one."""
+        r = _PadReport()
+        self._check(self.lib.gea_debug_check_pads(self.h, C.byref(r)))
+        return self._pad_report(r)
+
+    def debug_step(self) -> Dict:
+        """One eagerly launched step with every pad checked after every
+        launch; names the first launch that changed a pad."""
+        r = _PadReport()
+        self._check(self.lib.gea_debug_step(self.h, C.byref(r)))
+        return self._pad_report(r)
+
 
 def probe_fma(bits: int = 64, blocks: int = 608, iters: int = 16384, stream=None, repeats: int = 5) -> Dict:
     """Measured FMA rate (gea_probe_fma): the best of `repeats` CUDA-event
@@ -407,6 +456,34 @@ def probe_fma(bits: int = 64, blocks: int = 608, iters: int = 16384, stream=None
     assert torch.isfinite(out).all()
     return {"tflops": flops / (best * 1e-3) / 1e12, "ms": best, "blocks": blocks, "iters": iters,
             "flops": flops}
+
+
+def probe_barrier(blocks: int = 456, iters: int = 20000, read_status: bool = True, stream=None,
+                  repeats: int = 3) -> Dict:
+    """Measured cost of one grid barrier of the persistent kernels' protocol
+    (gea_probe_barrier): the best of `repeats` CUDA-event timed launches of
+    `iters` barriers on `blocks` co-resident blocks, in microseconds per
+    barrier."""
+    import torch
+    lib = library()
+    stream = stream or torch.cuda.current_stream()
+    scratch = torch.zeros(4, dtype=torch.int32, device="cuda")
+    _chk(lib.gea_probe_barrier(blocks, max(1, iters // 10), int(read_status), scratch.data_ptr(),
+                               stream.cuda_stream), "gea_probe_barrier")   # warm-up
+    best = None
+    for _ in range(repeats):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _chk(lib.gea_probe_barrier(blocks, iters, int(read_status), scratch.data_ptr(), stream.cuda_stream),
+             "gea_probe_barrier")
+        e1.record(stream)
+        e1.synchronize()
+        if int(scratch[2].item()) != 0:
+            raise GeaError(GEA_ERR_TIMEOUT, "gea_probe_barrier: a bounded wait gave up")
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    return {"us_per_barrier": best * 1e3 / iters, "ms": best, "blocks": blocks, "iters": iters,
+            "read_status": bool(read_status)}
 
 
 CONV_PLAIN, CONV_POOL, CONV_UPADD = 0, 1, 2

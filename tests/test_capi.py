@@ -44,8 +44,8 @@ def test_binding_struct_sizes_match_header():
 #include <stdio.h>
 #include <stddef.h>
 #include "gea.h"
-int main(void){printf("%zu %zu %zu %zu\n", sizeof(gea_grid), sizeof(gea_constants),
- sizeof(gea_state_view), sizeof(gea_stats)); return 0;}
+int main(void){printf("%zu %zu %zu %zu %zu %zu\n", sizeof(gea_grid), sizeof(gea_constants),
+ sizeof(gea_state_view), sizeof(gea_stats), sizeof(gea_pad_region), sizeof(gea_pad_report)); return 0;}
 '''
     with tempfile.TemporaryDirectory() as d:
         c = os.path.join(d, "s.c")
@@ -54,7 +54,8 @@ int main(void){printf("%zu %zu %zu %zu\n", sizeof(gea_grid), sizeof(gea_constant
         subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
         sizes = [int(x) for x in subprocess.check_output([exe]).split()]
     assert sizes == [ctypes.sizeof(gea._Grid), ctypes.sizeof(gea._Const),
-                     ctypes.sizeof(gea._View), ctypes.sizeof(gea._Stats)]
+                     ctypes.sizeof(gea._View), ctypes.sizeof(gea._Stats),
+                     ctypes.sizeof(gea._PadRegion), ctypes.sizeof(gea._PadReport)]
 
 
 def test_binding_fails_loudly_without_a_gpu():
