@@ -214,7 +214,8 @@ class ClockSampler:
 # sources; a change to any of them invalidates that figure alone)
 KERNEL_SOURCES = {
     "k_persistent": ("gea_internal.cuh", "gea_tiles_body.cuh", "gea_persistent_body.cuh"),
-    "mg_up": ("gea_internal.cuh", "gea_tiles_body.cuh", "gea_kernels.cu"),
+    "mg_up": ("gea_internal.cuh", "gea_tiles_body.cuh", "gea_tiles.cuh", "gea_kernels.cu"),
+    "mom_jacobi": ("gea_internal.cuh", "gea_tiles_body.cuh", "gea_tiles.cuh", "gea_kernels.cu"),
     "g3_": ("gea_internal.cuh", "gea3d.cu"),
 }
 
