@@ -88,6 +88,39 @@ def test_conv3x3_matches_oracle(env, oracle_mod, cin, cout, mode):
     assert int(status.item()) == 0
 
 
+@pytest.mark.parametrize("cin,cout,mode,n,h", [(16, 16, 0, 1, 1700), (16, 16, 1, 1, 1700),
+                                                (32, 64, 2, 1, 900), (64, 32, 0, 2, 300),
+                                                (64, 64, 0, 2, 300), (64, 64, 2, 2, 300)])
+def test_conv3x3_column_runs(env, oracle_mod, cin, cout, mode, n, h):
+    """Images tall enough that every CTA walks several tiles down a tile
+    column (the ring of staged rows, the row prefetched during the previous
+    tile's MMA batch, the two accumulator buffers), with ranges that cross
+    from one column or image into the next."""
+    torch, G = env
+    from oracle import unet
+    rng = np.random.default_rng(7 * cin + 3 * cout + mode + h)
+    w = 260                      # 2 x 128 + 4: a ragged last tile column
+    xs = rng.standard_normal((n, 2 * h, 2 * w, cin) if mode == 1 else (n, h, w, cin))
+    x1 = rng.standard_normal((n, h // 2, w // 2, cin)) if mode == 2 else None
+    wt = rng.standard_normal((cout, 3, 3, cin)) / np.sqrt(9 * cin)
+    b = rng.standard_normal(cout) * 0.1
+    xs, wt = unet.bf16_round(xs), unet.bf16_round(wt)
+    x1 = unet.bf16_round(x1) if x1 is not None else None
+    xin = xs if mode == 0 else (unet.bf16_round(unet.pool(xs)) if mode == 1 else unet.bf16_round(xs + unet.up(x1)))
+    ref = unet.conv(xin, wt, b)
+    acc = 9 * cin * 2.0 ** -24 * unet.conv(np.abs(xin), np.abs(wt), np.abs(b))
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    y = torch.zeros((n, h, w, cout), dtype=torch.float32, device="cuda")
+    G.conv3x3(bits(torch, to_bf16(torch, xs)), bits(torch, to_bf16(torch, wt)), y, n, h, w, cin, cout,
+              mode=mode, flags=2, x1=bits(torch, to_bf16(torch, x1)) if x1 is not None else None,
+              bias=torch.tensor(b, dtype=torch.float32).cuda(), status=status)
+    torch.cuda.synchronize()
+    got = y.cpu().numpy().astype(np.float64)
+    bad = np.abs(got - ref) > acc + 1e-30
+    assert not bad.any(), (int(bad.sum()), float(np.abs(got - ref).max()))
+    assert int(status.item()) == 0
+
+
 def test_conv3x3_rejects_bad_arguments(env):
     torch, G = env
     x = torch.zeros(16, dtype=torch.int16, device="cuda")
