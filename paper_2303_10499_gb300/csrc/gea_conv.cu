@@ -283,17 +283,21 @@ __host__ __device__ constexpr int smem_bytes()
 // A CTA takes a contiguous range of tiles in (image, tile column, row)
 // order, the row fastest, so that consecutive tiles of a column share two
 // of their three input rows: a tile needs one new row, copied kDist tiles
-// ahead. Two accumulator buffers in tensor memory let the bias, activation
-// and store of tile i - 1 run while tile i's MMA batch runs. Per tile:
-//   wait for and finish the new row of tile i | issue MMA(i) into buffer i&1
-//   | copy the row of tile i + kDist | wait MMA(i-1), store tile i-1 from
-//   buffer (i-1)&1.
+// ahead. The CTA's warps have two roles. One extra warp issues the MMA
+// batches (one thread); the other NT threads copy rows and, from the second
+// of two accumulator buffers in tensor memory, apply the bias and activation
+// and store the previous tile, while the batch runs:
+//   loaders: wait for and finish the new row of tile i | barrier | copy the
+//   row of tile i + kDist | wait for batch i-1 (mbarrier), store tile i-1
+//   MMA warp: barrier | issue batch i into buffer i&1, commit to its mbarrier
 // The first tile of a column run stages its three rows (and the next kDist
-// - 1 rows) after the batch of the tile before it has completed.
+// - 1 rows) once the batch of the tile before it has completed. A wait that
+// runs out (bounded polls) sets a flag that every thread reads after the
+// next barrier, and the CTA leaves the loop.
 template <int CIN, int COUT, int MODE>
-__global__ void __launch_bounds__(threads_of<CIN, COUT>()) k_conv3x3(ConvArgs a)
+__global__ void __launch_bounds__(threads_of<CIN, COUT>() + 32) k_conv3x3(ConvArgs a)
 {
-    constexpr int NT = threads_of<CIN, COUT>();
+    constexpr int NT = threads_of<CIN, COUT>();   // loaders (and epilogue)
     static_assert(CIN % 16 == 0 && COUT % 16 == 0 && COUT <= 256, "channel counts");
     constexpr int G = CIN / 8;
     constexpr int rowB = G * kGrpB;
@@ -306,20 +310,22 @@ __global__ void __launch_bounds__(threads_of<CIN, COUT>()) k_conv3x3(ConvArgs a)
     float *sBias = reinterpret_cast<float *>(sX + (MODE == GEA_CONV_UPADD ? kSide : 0) * rowB);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(sBias + COUT);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
-    int *okflag = reinterpret_cast<int *>(tslot + 1);
+    int *sfail = reinterpret_cast<int *>(tslot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool loader = tid < NT;
 
     // weights: element (o, k = tap * CIN + c) at
     // (k / 8) * lboB + (o / 8) * 128 + (o % 8) * 16 + (k % 8) * 2
-    for (int e = tid; e < COUT * 9 * G; e += NT) {
+    for (int e = tid; e < COUT * 9 * G; e += NT + 32) {
         const int kg = e % (9 * G), o = e / (9 * G);
         const uint4 v = ld16(a.wt + (size_t)o * 9 * CIN + kg * 8);
         *reinterpret_cast<uint4 *>(sW + kg * lboB + (o / 8) * 128 + (o % 8) * 16) = v;
     }
-    for (int o = tid; o < COUT; o += NT) sBias[o] = a.bias ? __ldg(&a.bias[o]) : 0.0f;
+    for (int o = tid; o < COUT; o += NT + 32) sBias[o] = a.bias ? __ldg(&a.bias[o]) : 0.0f;
     if (tid == 0) {
         mbar_init(smem_u32(&mbar[0]), 1);
         mbar_init(smem_u32(&mbar[1]), 1);
+        *sfail = 0;
     }
     if (warp == 0) tmem_alloc(smem_u32(tslot), 2 * bufC);
     fence_proxy_async();
@@ -331,44 +337,27 @@ __global__ void __launch_bounds__(threads_of<CIN, COUT>()) k_conv3x3(ConvArgs a)
     auto slot = [&](int yy) { return sR + ((yy + 1) % kRing) * rowB; };
     auto side = [&](int yy) { return sX + ((yy + 1) % kSide) * rowB; };
 
-    // phase bits and outstanding commits of the two buffers (thread 0's view
-    // is authoritative; every thread tracks the same values)
+    // phase bits and outstanding batches of the two buffers (the loaders
+    // track them; thread 0's copy drains the batches after a failed wait)
     uint32_t phase = 0, pending = 0;
-    // Wait until buffer j's batch has completed (bounded; all threads). On
-    // give-up, wait once more, bounded, for every batch still outstanding
-    // before the CTA frees its tensor memory and shared memory; if that also
-    // gives up nothing can contain the batches, and the status says so.
-    auto wait_buf = [&](int j) -> bool {
-        if (tid == 0) {
-            const uint32_t mb = smem_u32(&mbar[j]);
-            const uint32_t ph = (phase >> j) & 1u;
-            unsigned spins = 0;
-            bool ok = true;
-            while (!mbar_try_wait(mb, ph)) {
-                if (++spins > kWaitLimit) {
-                    ok = false;
-                    break;
-                }
-                __nanosleep(32);
+    // a loader's bounded wait for buffer j's batch
+    auto wait_batch = [&](int j) -> bool {
+        const uint32_t mb = smem_u32(&mbar[j]);
+        const uint32_t ph = (phase >> j) & 1u;
+        unsigned spins = 0;
+        while (!mbar_try_wait(mb, ph)) {
+            if (++spins > kWaitLimit) {
+                *sfail = 1;
+                return false;
             }
-            if (!ok) {
-                for (int q = 0; q < 2; ++q) {
-                    if (!((pending >> q) & 1u)) continue;
-                    unsigned drain = 0;
-                    while (!mbar_try_wait(smem_u32(&mbar[q]), (phase >> q) & 1u) && ++drain <= kWaitLimit)
-                        __nanosleep(32);
-                }
-                if (a.status) atomicExch(a.status, GEA_ERR_TIMEOUT);
-            }
-            *okflag = ok ? 1 : 0;
+            __nanosleep(32);
         }
-        __syncthreads();
         tc_fence_after();
-        return *okflag != 0;
+        return true;
     };
     // bias, activation and store of the tile (b, y, x0) held in buffer j:
     // warp w reads the lanes (pixels) of sub-partition w % 4; with 256
-    // threads warps w and w + 4 split the channels. A thread's columns (16
+    // loaders warps w and w + 4 split the channels. A thread's columns (16
     // or 32) are loaded before one wait
     auto epilogue = [&](int j, int b, int y, int x0) {
         constexpr int CH = (NT == 256 && COUT >= 32) ? COUT / 2 : COUT;   // channels per warp
@@ -423,87 +412,113 @@ __global__ void __launch_bounds__(threads_of<CIN, COUT>()) k_conv3x3(ConvArgs a)
         cp_async_commit();
     };
     auto in_run = [&](long long t, int y, int k) { return y + k < a.h && t + k < t1; };
-    bool ok = true;
+    // tile coordinates, advanced without divisions
+    int y = (int)(t0 % a.h);
+    int col = (int)(t0 / a.h);
     int pb = 0, py = 0, px0 = 0;   // the previous tile
     for (long long t = t0; t < t1; ++t) {
         const int i = (int)(t - t0);
-        const int y = (int)(t % a.h);
-        const long long col = t / a.h;
-        const int x0 = (int)(col % a.tiles_per_row) * kM, b = (int)(col / a.tiles_per_row);
-        if (i == 0 || y == 0) {
-            // first tile of a column run: its three rows, once the previous
-            // tile's batch no longer reads the ring, then the rows of the
-            // next kDist - 1 tiles
-            if (i > 0 && !wait_buf((i - 1) & 1)) {
-                ok = false;
-                break;
-            }
-            for (int r = 0; r < 3; ++r) issue(y - 1 + r, b, x0);
-            cp_async_wait(0);
-            for (int r = 0; r < 3; ++r) finish_row<CIN, MODE, NT>(slot(y - 1 + r), side(y - 1 + r));
-            for (int k = 1; k < kDist; ++k)
-                if (in_run(t, y, k)) issue(y + 1 + k, b, x0);
-        } else {
-            // row y + 1: the groups issued after it are those of the rows of
-            // tiles t + 1 .. t + kDist - 1 of the run (the row of tile
-            // t + kDist is issued below, after the barrier)
-            int newer = 0;
-            for (int k = 1; k < kDist; ++k) newer += in_run(t, y, k) ? 1 : 0;
-            cp_async_wait(newer);
-            finish_row<CIN, MODE, NT>(slot(y + 1), side(y + 1));
+        if (i > 0 && ++y == a.h) {
+            y = 0;
+            ++col;
         }
-        fence_proxy_async();
+        const int x0 = (col % a.tiles_per_row) * kM, b = col / a.tiles_per_row;
+        const int j = i & 1;
+        if (loader) {
+            if (i == 0 || y == 0) {
+                // first tile of a column run: its three rows, once the
+                // previous tile's batch no longer reads the ring, then the
+                // rows of the next kDist - 1 tiles
+                if (i == 0 || wait_batch(j ^ 1)) {
+                    for (int r = 0; r < 3; ++r) issue(y - 1 + r, b, x0);
+                    cp_async_wait(0);
+                    for (int r = 0; r < 3; ++r) finish_row<CIN, MODE, NT>(slot(y - 1 + r), side(y - 1 + r));
+                    for (int k = 1; k < kDist; ++k)
+                        if (in_run(t, y, k)) issue(y + 1 + k, b, x0);
+                }
+            } else {
+                // row y + 1: the groups issued after it are those of the
+                // rows of tiles t + 1 .. t + kDist - 1 of the run
+                int newer = 0;
+                for (int k = 1; k < kDist; ++k) newer += in_run(t, y, k) ? 1 : 0;
+                cp_async_wait(newer);
+                finish_row<CIN, MODE, NT>(slot(y + 1), side(y + 1));
+            }
+            fence_proxy_async();
+        }
         tc_fence_before();
         __syncthreads();
-        const int j = i & 1;
-        if (tid == 0) {
-            tc_fence_after();
-            // the descriptors differ only in their start address field
-            // (address / 16, below 2^14 in the shared window), so each is a
-            // base descriptor plus a constant
-            const uint64_t bD = smem_desc(smem_u32(sW), lboB, 128);
-            const uint64_t aD[3] = {smem_desc(smem_u32(slot(y - 1)), kGrpB, 128),
-                                    smem_desc(smem_u32(slot(y)), kGrpB, 128),
-                                    smem_desc(smem_u32(slot(y + 1)), kGrpB, 128)};
-            uint32_t acc = 0;
+        if (*sfail) break;
+        if (warp == NT / 32) {
+            if (lane == 0) {
+                tc_fence_after();
+                // the descriptors differ only in their start address field
+                // (address / 16, below 2^14 in the shared window), so each
+                // is a base descriptor plus a constant
+                const uint64_t bD = smem_desc(smem_u32(sW), lboB, 128);
+                const uint64_t aD[3] = {smem_desc(smem_u32(slot(y - 1)), kGrpB, 128),
+                                        smem_desc(smem_u32(slot(y)), kGrpB, 128),
+                                        smem_desc(smem_u32(slot(y + 1)), kGrpB, 128)};
+                uint32_t acc = 0;
 #pragma unroll
-            for (int tap = 0; tap < 9; ++tap) {
-                const int r = tap / 3, dx = tap % 3 - 1;
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int r = tap / 3, dx = tap % 3 - 1;
 #pragma unroll
-                for (int kc = 0; kc < CIN / 16; ++kc) {
-                    const uint64_t ad = aD[r] + (uint64_t)(((1 + dx) * 16 + 2 * kc * kGrpB) >> 4);
-                    const uint64_t bd = bD + (uint64_t)(((tap * G + 2 * kc) * lboB) >> 4);
-                    mma_bf16(tmem + (uint32_t)j * bufC, ad, bd, idesc, acc);
-                    acc = 1;
+                    for (int kc = 0; kc < CIN / 16; ++kc) {
+                        const uint64_t ad = aD[r] + (uint64_t)(((1 + dx) * 16 + 2 * kc * kGrpB) >> 4);
+                        const uint64_t bd = bD + (uint64_t)(((tap * G + 2 * kc) * lboB) >> 4);
+                        mma_bf16(tmem + (uint32_t)j * bufC, ad, bd, idesc, acc);
+                        acc = 1;
+                    }
+                }
+                mma_commit(smem_u32(&mbar[j]));
+            }
+            __syncwarp();
+        } else {
+            pending |= 1u << j;
+            // the row of tile t + kDist, into the slot of row y - 3 (read
+            // last by the batch of tile t - 2, which has completed), while
+            // the batch runs
+            if (in_run(t, y, kDist)) issue(y + 1 + kDist, b, x0);
+            if (i > 0) {
+                const int jp = j ^ 1;
+                if (wait_batch(jp)) {
+                    epilogue(jp, pb, py, px0);
+                    phase ^= 1u << jp;
+                    pending &= ~(1u << jp);
                 }
             }
-            mma_commit(smem_u32(&mbar[j]));
+            tc_fence_before();
         }
-        pending |= 1u << j;
-        // the row of tile t + kDist, into the slot of row y - 3 (read last by
-        // the batch of tile t - 2, which has completed), while the batch runs
-        if (in_run(t, y, kDist)) issue(y + 1 + kDist, b, x0);
-        if (i > 0) {
-            const int jp = j ^ 1;
-            if (!wait_buf(jp)) {
-                ok = false;
-                break;
-            }
-            epilogue(jp, pb, py, px0);
-            phase ^= 1u << jp;
-            pending &= ~(1u << jp);
-        }
-        tc_fence_before();
         pb = b;
         py = y;
         px0 = x0;
     }
-    if (ok && t1 > t0) {
+    // the last tile
+    if (loader && !*sfail && t1 > t0) {
         const int jl = (int)((t1 - 1 - t0) & 1);
-        if (wait_buf(jl)) epilogue(jl, pb, py, px0);
+        if (wait_batch(jl)) {
+            epilogue(jl, pb, py, px0);
+            phase ^= 1u << jl;
+            pending &= ~(1u << jl);
+        }
         tc_fence_before();
     }
-    cp_async_wait_all();
+    cp_async_wait(0);
+    __syncthreads();
+    if (*sfail && tid == 0) {
+        // a wait ran out: the committed batches may still be running and
+        // reading shared memory and writing tensor memory, so wait once more,
+        // bounded, for every batch still outstanding before the CTA frees
+        // them. If that also runs out nothing can contain the batches: the
+        // status says so, and the caller must treat the CUDA context as lost.
+        for (int q = 0; q < 2; ++q) {
+            if (!((pending >> q) & 1u)) continue;
+            unsigned drain = 0;
+            while (!mbar_try_wait(smem_u32(&mbar[q]), (phase >> q) & 1u) && ++drain <= kWaitLimit) __nanosleep(32);
+        }
+        if (a.status) atomicExch(a.status, GEA_ERR_TIMEOUT);
+    }
     __syncthreads();
     tc_fence_after();
     if (warp == 0) tmem_dealloc(tmem, 2 * bufC);
@@ -537,7 +552,7 @@ cudaError_t launch_one(const ConvArgs &a0, cudaStream_t st)
             attr_err = cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
         if (attr_err == cudaSuccess) attr_err = cudaFuncGetAttributes(&fa, kern);
         if (attr_err != cudaSuccess) return;
-        constexpr int NT = threads_of<CIN, COUT>();
+        constexpr int NT = threads_of<CIN, COUT>() + 32;
         per_sm = thr_sm / NT;
         const int by_smem = smem_sm / (smem + (int)fa.sharedSizeBytes + 1024);
         const int by_regs = regs_sm / (NT * (fa.numRegs > 0 ? fa.numRegs : 1));
@@ -553,7 +568,7 @@ cudaError_t launch_one(const ConvArgs &a0, cudaStream_t st)
     a.ntiles = a.n * a.h * a.tiles_per_row;
     int gx = sms * per_sm;
     if (gx > a.ntiles) gx = a.ntiles;
-    kern<<<gx, threads_of<CIN, COUT>(), smem, st>>>(a);
+    kern<<<gx, threads_of<CIN, COUT>() + 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
