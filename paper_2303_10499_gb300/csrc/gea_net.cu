@@ -70,18 +70,35 @@ __device__ __forceinline__ float round_bf(float f) { return bf2f(f2bf(f)); }
 // ---- per-sample sums (deterministic: block partials, then a fixed-order sum) ----
 
 // part[b * gridDim.x + blk] = sum over the block's share of sample b of v^2
-// (sq) or v.
-__global__ void k_sample_partials(const float *x, long long per, int sq, double *part)
+// (sq) or v. A thread takes four consecutive values at a time (per is a
+// multiple of 64) into four FP64 sums, which it adds in a fixed order, with
+// one 16-byte load when x is 16-byte aligned (vec); v^2 of an FP32 value is
+// exact in FP64, so fma(v, v, s) adds it with the one rounding of the sum.
+__global__ void k_sample_partials(const float *x, long long per, int sq, int vec, double *part)
 {
     __shared__ double red[kThreads];
     const int b = blockIdx.y;
     const float *xs = x + (size_t)b * per;
-    double s = 0.0;
-    for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < per; i += (long long)gridDim.x * kThreads) {
-        const double v = xs[i];
-        s += sq ? v * v : v;
+    const long long n4 = per / 4;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n4; i += (long long)gridDim.x * kThreads) {
+        float4 v;
+        if (vec) {
+            v = __ldg(reinterpret_cast<const float4 *>(xs) + i);
+        } else {
+            v.x = __ldg(&xs[4 * i]); v.y = __ldg(&xs[4 * i + 1]);
+            v.z = __ldg(&xs[4 * i + 2]); v.w = __ldg(&xs[4 * i + 3]);
+        }
+        if (sq) {
+            s0 = fma((double)v.x, (double)v.x, s0);
+            s1 = fma((double)v.y, (double)v.y, s1);
+            s2 = fma((double)v.z, (double)v.z, s2);
+            s3 = fma((double)v.w, (double)v.w, s3);
+        } else {
+            s0 += v.x; s1 += v.y; s2 += v.z; s3 += v.w;
+        }
     }
-    red[threadIdx.x] = s;
+    red[threadIdx.x] = (s0 + s1) + (s2 + s3);
     __syncthreads();
     for (int o = kThreads / 2; o > 0; o >>= 1) {
         if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
@@ -91,14 +108,21 @@ __global__ void k_sample_partials(const float *x, long long per, int sq, double 
 }
 
 // out[b] = scale(sum of the nblk partials of sample b); mode 0: sqrt(s / per)
-// (rms), 1: s / per (mean)
-__global__ void k_sample_finish(const double *part, int nblk, long long per, int mode, float *out, int n)
+// (rms), 1: s / per (mean). One block per sample: thread t adds partials
+// t, t + kThreads, ..., then a fixed-order tree.
+__global__ void k_sample_finish(const double *part, int nblk, long long per, int mode, float *out)
 {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= n) return;
+    __shared__ double red[kThreads];
+    const int b = blockIdx.x;
     double s = 0.0;
-    for (int i = 0; i < nblk; ++i) s += part[(size_t)b * nblk + i];
-    out[b] = mode == 0 ? (float)sqrt(s / (double)per) : (float)(s / (double)per);
+    for (int i = threadIdx.x; i < nblk; i += kThreads) s += part[(size_t)b * nblk + i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = kThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[b] = mode == 0 ? (float)sqrt(red[0] / (double)per) : (float)(red[0] / (double)per);
 }
 
 // x = r / rms per sample (0 if rms = 0), FP32 and bfloat16
@@ -114,34 +138,62 @@ __global__ void k_prep(const float *r, const float *rms, long long per, long lon
 
 // ---- first layer (1 input channel) and output layer (1x1) on the CUDA cores ----
 
-__global__ void k_conv_first(int n, int h, int w, const uint16_t *x, const float *wt, const float *bias, int relu,
-                             uint16_t *y)
+// Pixels of one row per thread in the first layer (w is a multiple of 8):
+// each weight read from shared memory serves kFirstPix multiply-adds.
+constexpr int kFirstPix = 4;
+
+__global__ void __launch_bounds__(kThreads) k_conv_first(int n, int h, int w, const uint16_t *x, const float *wt,
+                                                         const float *bias, int relu, uint16_t *y)
 {
-    const long long p = blockIdx.x * (long long)kThreads + threadIdx.x;
-    if (p >= (long long)n * h * w) return;
-    const int j = (int)(p % w);
-    const int i = (int)((p / w) % h);
-    const long long base = p - ((long long)i * w + j);
-    float xv[9];
+    __shared__ float sw[16 * 9], sb[16];
+    for (int e = threadIdx.x; e < 16 * 9; e += kThreads) sw[e] = round_bf(wt[e]);
+    if (threadIdx.x < 16) sb[threadIdx.x] = bias[threadIdx.x];
+    __syncthreads();
+    const long long p0 = (blockIdx.x * (long long)kThreads + threadIdx.x) * kFirstPix;
+    if (p0 >= (long long)n * h * w) return;
+    const int j0 = (int)(p0 % w);
+    const int i = (int)((p0 / w) % h);
+    const long long base = p0 - ((long long)i * w + j0);
+    // input rows i-1..i+1, columns j0-1..j0+kFirstPix (zero outside the image)
+    float xv[3][kFirstPix + 2];
 #pragma unroll
-    for (int t = 0; t < 9; ++t) {
-        const int ii = i + t / 3 - 1, jj = j + t % 3 - 1;
-        xv[t] = (ii >= 0 && ii < h && jj >= 0 && jj < w) ? bf2f(x[base + (long long)ii * w + jj]) : 0.0f;
+    for (int r = 0; r < 3; ++r) {
+        const int ii = i + r - 1;
+#pragma unroll
+        for (int c = 0; c < kFirstPix + 2; ++c) {
+            const int jj = j0 + c - 1;
+            xv[r][c] = (ii >= 0 && ii < h && jj >= 0 && jj < w) ? bf2f(x[base + (long long)ii * w + jj]) : 0.0f;
+        }
     }
-    float o[16];
+    // per output: the bias, then the taps in row-major order, one FMA each
+    uint32_t u[kFirstPix][8];
 #pragma unroll
-    for (int c = 0; c < 16; ++c) {
-        float s = bias[c];
+    for (int c = 0; c < 16; c += 2) {
+        float o[2][kFirstPix];
 #pragma unroll
-        for (int t = 0; t < 9; ++t) s = fmaf(round_bf(wt[c * 9 + t]), xv[t], s);
-        o[c] = relu ? fmaxf(s, 0.0f) : s;
+        for (int k = 0; k < 2; ++k) {
+#pragma unroll
+            for (int px = 0; px < kFirstPix; ++px) o[k][px] = sb[c + k];
+#pragma unroll
+            for (int t = 0; t < 9; ++t) {
+                const float wv = sw[(c + k) * 9 + t];
+#pragma unroll
+                for (int px = 0; px < kFirstPix; ++px) o[k][px] = fmaf(wv, xv[t / 3][px + t % 3], o[k][px]);
+            }
+#pragma unroll
+            for (int px = 0; px < kFirstPix; ++px)
+                if (relu) o[k][px] = fmaxf(o[k][px], 0.0f);
+        }
+#pragma unroll
+        for (int px = 0; px < kFirstPix; ++px)
+            u[px][c / 2] = (uint32_t)f2bf(o[0][px]) | ((uint32_t)f2bf(o[1][px]) << 16);
     }
-    uint4 *dst = reinterpret_cast<uint4 *>(y + p * 16);
-    uint32_t u[8];
+    uint4 *dst = reinterpret_cast<uint4 *>(y + p0 * 16);
 #pragma unroll
-    for (int c = 0; c < 8; ++c) u[c] = (uint32_t)f2bf(o[2 * c]) | ((uint32_t)f2bf(o[2 * c + 1]) << 16);
-    dst[0] = make_uint4(u[0], u[1], u[2], u[3]);
-    dst[1] = make_uint4(u[4], u[5], u[6], u[7]);
+    for (int px = 0; px < kFirstPix; ++px) {
+        dst[2 * px] = make_uint4(u[px][0], u[px][1], u[px][2], u[px][3]);
+        dst[2 * px + 1] = make_uint4(u[px][4], u[px][5], u[px][6], u[px][7]);
+    }
 }
 
 __global__ void k_conv_out(long long npix, const uint16_t *x, const float *wt, const float *bias, float *y)
@@ -487,6 +539,9 @@ struct gea_net {
 namespace {
 
 constexpr int kSampleBlocks = 64;
+// blocks per sample of the per-sample sums of the forward pass (a read of
+// the whole input, as wide as the GPU)
+constexpr int kStatBlocks = 608;
 
 long long count_params(long long *offw, long long *offb)
 {
@@ -529,9 +584,10 @@ int pack_all(gea_net *net)
 // per-sample reduction of x (n samples of `per` values) into out[b]
 void sample_stat(gea_net *net, const float *x, int n, long long per, int mode, float *out)
 {
-    dim3 g(kSampleBlocks, n);
-    k_sample_partials<<<g, kThreads, 0, net->st>>>(x, per, mode == 0 ? 1 : 0, net->dpart);
-    k_sample_finish<<<blocks(n), kThreads, 0, net->st>>>(net->dpart, kSampleBlocks, per, mode, out, n);
+    dim3 g(kStatBlocks, n);
+    const int vec = (reinterpret_cast<uintptr_t>(x) & 15u) == 0;
+    k_sample_partials<<<g, kThreads, 0, net->st>>>(x, per, mode == 0 ? 1 : 0, vec, net->dpart);
+    k_sample_finish<<<n, kThreads, 0, net->st>>>(net->dpart, kStatBlocks, per, mode, out);
 }
 
 int forward(gea_net *net, int n, int h, int w, const float *r, float *y)
@@ -540,7 +596,7 @@ int forward(gea_net *net, int n, int h, int w, const float *r, float *y)
     const long long per = (long long)h * w, tot = per * n;
     sample_stat(net, r, n, per, 0, net->rms);
     k_prep<<<blocks(tot), kThreads, 0, st>>>(r, net->rms, per, tot, net->xh, net->xbf);
-    k_conv_first<<<blocks(tot), kThreads, 0, st>>>(n, h, w, net->xbf, net->theta + net->offw[0],
+    k_conv_first<<<blocks(tot / kFirstPix), kThreads, 0, st>>>(n, h, w, net->xbf, net->theta + net->offw[0],
                                                    net->theta + net->offb[0], net->relu && kL[0].act, net->act[0]);
     for (int l = 1; l < kOut; ++l) {
         const LayerDef &d = kL[l];
@@ -735,7 +791,7 @@ int gea_net_create(int32_t n_max, int32_t h_max, int32_t w_max, int32_t flags, g
     if (17 * ((pix + kThreads - 1) / kThreads) > pcount) pcount = 17 * ((pix + kThreads - 1) / kThreads);
     net->part = take<float>(net, pcount, ok);
     net->partb = take<float>(net, ns * 64, ok);
-    net->dpart = take<double>(net, (size_t)n_max * kSampleBlocks, ok);
+    net->dpart = take<double>(net, (size_t)n_max * (kStatBlocks > kSampleBlocks ? kStatBlocks : kSampleBlocks), ok);
     net->loss = take<double>(net, 1, ok);
     net->status = take<int>(net, 1, ok);
     if (!ok) {
