@@ -102,6 +102,13 @@ def parse():
     ap.add_argument("--three-d", default=None, metavar="WORKLOAD",
                     help="the three-dimensional step on a 3D workload (bubble3d_512x512x256: the "
                          "10 km cube bubble, 67M cells)")
+    ap.add_argument("--sweep", action="store_true",
+                    help="the size sweep of the smooth bubble, 256 x 128 to 8192 x 4096 cells (FP64, "
+                         "pressure solves to 1e-8 of ||b||): ms per step, cell-steps/s and the whole "
+                         "step against the FP64 and HBM ceilings per size")
+    ap.add_argument("--full-run", action="store_true",
+                    help="the 640 x 320 bubble run to t = 1020 s (20,400 steps at dt = 0.05 s), FP64 "
+                         "and mixed precision, with the per-field error of the mixed run at the end")
     ap.add_argument("--dts", type=lambda t: [float(x) for x in t.split(",")], default=[0.05, 0.2, 0.5],
                     help="--learned: time steps of the 4096 x 2048 runs (comma separated)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
@@ -960,6 +967,137 @@ def run_ours(args):
         print(json.dumps(res), flush=True)
 
 
+SWEEP_SIZES = [(256, 128), (512, 256), (640, 320), (1024, 512), (2048, 1024), (4096, 2048), (8192, 4096)]
+
+
+def run_sweep(args):
+    """Throughput against grid size: the smooth bubble (20 km x 10 km,
+    dt = 0.05 s) from 256 x 128 to 8192 x 4096 cells, FP64, pressure solves
+    to 1e-8 of ||b||, the library's own choice of driver (the persistent
+    kernel while a grid's tiles fit the co-resident blocks a few times, the
+    CUDA graph above). Each size is timed like the main line (L2 flushed
+    before every timed step) and its whole step is set against the FP64 and
+    HBM ceilings on the flop and byte model of one profiled step. The
+    working set moves from L2 (129 MB) into HBM between 640 x 320 and
+    2048 x 1024."""
+    import copy
+    import torch
+    from paper_2303_10499_gb300 import build as B
+    from paper_2303_10499_gb300 import gea
+    from paper_2303_10499_gb300 import workloads as W
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    B.build()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    pk = peaks(measure=True)
+    rows = []
+    for nx, nz in SWEEP_SIZES:
+        wl = W.smooth_bubble_20km(nx, nz, dt=0.05)
+        const = copy.copy(wl.const)
+        const.cg_rtol = 1e-8
+        s = gea.Solver(wl.grid, const, stream=stream)
+        s.set_conservative({k: torch.from_numpy(v).cuda() for k, v in wl.fields.items()})
+        ms, launches, clocks = timed_steps(s, stream, flush, args.steps, args.warmup, 1, local)
+        st = s.stats()
+        prof = s.profile_step()
+        mean = statistics.mean(ms)
+        ws = whole_step(prof, pk, mean)
+        rows.append({"grid": [nx, nz], "cells": wl.grid.cells, "driver": st["driver"],
+                     "mg_levels": st["mg_levels"], "ms_per_step": mean, "ms_per_step_min": min(ms),
+                     "value": wl.grid.cells * args.steps / (sum(ms) / 1e3), "unit": UNIT,
+                     "cg_iters_last_step": st["cg_iters"],
+                     "jacobi_sweeps_last_step": [st["jac_u"], st["jac_h"]],
+                     "gpu_launches": int(launches), "clocks": clocks,
+                     "bytes_per_step": ws["bytes_per_step"], "hbm_gbs": ws["hbm_gbs"],
+                     "frac_hbm": ws["frac_hbm"], "fp64_tflops": ws["fp64_tflops"],
+                     "frac_fp64": ws["frac_fp64"], "bound": ws["bound"],
+                     "frac_binding": ws["frac_binding"]})
+        s.close()
+        torch.cuda.empty_cache()
+    top = rows[-1]
+    res = {"metric": METRIC, "value": top["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": top["ms_per_step"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "smooth_bubble size sweep", "dt": 0.05, "cg_rtol": 1e-8,
+                      "value_at": f"{top['grid'][0]}x{top['grid'][1]}",
+                      "l2": "flushed between timed steps (256 MB write, untimed)"},
+           "sweep": rows, "peaks": pk}
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+
+
+def run_full(args):
+    """The 640 x 320 smooth bubble run to t = 1020 s (20,400 steps of
+    0.05 s) by the FP64 step and by the mixed-precision step, each from the
+    initial state, timed over the whole run (CUDA events around chunks of
+    steps, no L2 flush: this is a production run); then the mixed run's
+    per-field error against the FP64 run at t = 1020 s: max |theta'|
+    difference (K), relative L2 of rho and rho e, of rho u and rho w
+    against the momentum vector. The FP64 step itself equals the FP64 oracle
+    to <= 1e-10 relative L2 over the first 100 steps (the parity tests); a
+    20,400-step oracle run would take about 50 minutes of one host core."""
+    import numpy as np
+    import torch
+    from paper_2303_10499_gb300 import build as B
+    from paper_2303_10499_gb300 import gea
+    from paper_2303_10499_gb300 import workloads as W
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    B.build()
+    wl = W.get("bubble640x320")
+    t_end, chunk = 1020.0, 1000
+    nsteps = int(round(t_end / wl.const.dt))
+    stream = torch.cuda.current_stream()
+    dev = {k: torch.from_numpy(v).cuda() for k, v in wl.fields.items()}
+    arms = {}
+    for mixed in (False, True):
+        s = gea.Solver(wl.grid, wl.const, stream=stream, mixed=mixed)
+        s.set_conservative(dev)
+        clk = ClockSampler(local)
+        clk.start()
+        ms, done, iters = 0.0, 0, []
+        while done < nsteps:
+            n = min(chunk, nsteps - done)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.step_async(n)
+            e1.record(stream)
+            s.sync()
+            ms += e0.elapsed_time(e1)
+            done += n
+            iters.append(s.stats()["cg_iters"])
+        clocks = clk.stop()
+        st = s.stats()
+        th, _, _ = s.diagnostics(wl.theta_bar)
+        arms["mixed" if mixed else "fp64"] = {
+            "steps": done, "t_end_s": done * wl.const.dt, "seconds": ms / 1e3,
+            "ms_per_step": ms / done, "value": wl.grid.cells * done / (ms / 1e3), "unit": UNIT,
+            "driver": st["driver"], "status": st["status"], "cg_iters_every_1000_steps": iters,
+            "theta_prime_K": {"min": float(th.min()), "max": float(th.max())}, "clocks": clocks,
+            "_cons": s.get_conservative(), "_theta": th}
+        s.close()
+    a64, a32 = arms["fp64"], arms["mixed"]
+    c64, c32 = a64.pop("_cons"), a32.pop("_cons")
+    th64, th32 = a64.pop("_theta"), a32.pop("_theta")
+    m = np.hypot(np.linalg.norm(c64["rhou"]), np.linalg.norm(c64["rhow"]))
+    rel = {k: float(np.linalg.norm(c32[k] - c64[k]) / np.linalg.norm(c64[k])) for k in ("rho", "rhoe")}
+    rel.update({k: float(np.linalg.norm(c32[k] - c64[k]) / m) for k in ("rhou", "rhow")})
+    res = {"metric": METRIC, "value": a32["value"], "unit": UNIT, "n_gpus": 1, "steps": nsteps,
+           "warmup": 0, "ms_per_step": a32["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+           "config": {"workload": wl.name + " to t = 1020 s", "grid": [wl.grid.nx, wl.grid.nz],
+                      "dt": wl.const.dt, "cg_rtol": wl.const.cg_rtol, "value_arm": "mixed",
+                      "l2": "not flushed (whole-run timing, steps in chunks of 1000)"},
+           "fp64": a64, "mixed": a32, "speedup_vs_fp64": a32["value"] / a64["value"],
+           "error_vs_fp64_at_t_end": {"max_abs_dtheta_K": float(np.abs(th32 - th64).max()),
+                                      "rel_l2": rel}}
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+
+
 def _oracle_replica(job):
     """One host process of the all-cores baseline: `n` oracle steps of the
     named workload after one untimed step; returns (cell-steps, seconds)."""
@@ -1053,6 +1191,10 @@ def main():
         run_ensemble(args)
     elif args.three_d:
         run_3d(args)
+    elif args.sweep:
+        run_sweep(args)
+    elif args.full_run:
+        run_full(args)
     else:
         run_ours(args)
 
