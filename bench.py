@@ -109,6 +109,10 @@ def parse():
     ap.add_argument("--full-run", action="store_true",
                     help="the 640 x 320 bubble run to t = 1020 s (20,400 steps at dt = 0.05 s), FP64 "
                          "and mixed precision, with the per-field error of the mixed run at the end")
+    ap.add_argument("--oracle-table", action="store_true",
+                    help="the FP64 CPU oracle, single-threaded, on W0 (160 x 80, 100 steps), W1 "
+                         "(640 x 320, 100 steps) and W3 (4096 x 2048, 3 steps) from t = 0, beside the "
+                         "FP64 GPU step on the same steps")
     ap.add_argument("--dts", type=lambda t: [float(x) for x in t.split(",")], default=[0.05, 0.2, 0.5],
                     help="--learned: time steps of the 4096 x 2048 runs (comma separated)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
@@ -1098,6 +1102,67 @@ def run_full(args):
         print(json.dumps(res), flush=True)
 
 
+def run_oracle_table(args):
+    """The oracle timings of the measurement plan: the FP64 CPU oracle as it
+    stands, single-threaded, on W0 (the 160 x 80 bubble, 100 steps), W1 (640
+    x 320, 100 steps) and W3 (4096 x 2048, 3 steps), every run from t = 0,
+    and the FP64 GPU step on the same steps from the same state (CUDA events
+    around the whole run on the solver stream, no L2 flush), with the
+    largest relative L2 difference of the state fields between the two at
+    the end."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_2303_10499_gb300 import build as B
+    from paper_2303_10499_gb300 import gea
+    from paper_2303_10499_gb300 import workloads as W
+
+    world, rank, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    B.build()
+    oracle.build_oracle()
+    stream = torch.cuda.current_stream()
+    rows = []
+    for name, n in (("bubble160x80", 100), ("bubble640x320", 100), ("bubble4096x2048", 3)):
+        wl = W.get(name)
+        o = oracle.Oracle(wl.grid, wl.const)
+        so = o.derive(wl.fields)
+        t0 = time.perf_counter()
+        o.step(so, n)
+        t_cpu = time.perf_counter() - t0
+        s = gea.Solver(wl.grid, wl.const, stream=stream)
+        s.set_conservative(wl.fields)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s.step_async(n)
+        e1.record(stream)
+        s.sync()
+        t_gpu = e0.elapsed_time(e1) / 1e3
+        g = s.get_full()
+        st = s.stats()
+        s.close()
+        diff = max(float(np.linalg.norm(g[k] - so[k]) / np.linalg.norm(so[k])) for k in ("rho", "T", "pp"))
+        rows.append({"workload": name, "grid": [wl.grid.nx, wl.grid.nz], "steps": n,
+                     "oracle": {"seconds": t_cpu, "value": wl.grid.cells * n / t_cpu, "unit": UNIT,
+                                "cores": 1, "kind": "oracle"},
+                     "gpu_fp64": {"seconds": t_gpu, "value": wl.grid.cells * n / t_gpu, "unit": UNIT,
+                                  "driver": st["driver"]},
+                     "gpu_over_oracle": t_cpu / t_gpu,
+                     "max_rel_l2_rho_T_pp_gpu_vs_oracle": diff})
+    w1 = rows[1]
+    res = {"metric": METRIC, "value": w1["gpu_fp64"]["value"], "unit": UNIT, "n_gpus": 1,
+           "steps": w1["steps"], "warmup": 0, "ms_per_step": w1["gpu_fp64"]["seconds"] * 1e3 / w1["steps"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": "oracle table W0, W1, W3 from t = 0", "value_at": "bubble640x320",
+                      "l2": "not flushed (whole-run timing)"},
+           "oracle_table": rows}
+    print(json.dumps(res), flush=True)
+
+
 def _oracle_replica(job):
     """One host process of the all-cores baseline: `n` oracle steps of the
     named workload after one untimed step; returns (cell-steps, seconds)."""
@@ -1195,6 +1260,8 @@ def main():
         run_sweep(args)
     elif args.full_run:
         run_full(args)
+    elif args.oracle_table:
+        run_oracle_table(args)
     else:
         run_ours(args)
 
