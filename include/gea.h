@@ -305,6 +305,26 @@ int gea_set_tile_shape(gea_ctx *ctx, int32_t shape);
  * failure path without a hang. The CUDA-graph driver has no such waits.
  * Errors: GEA_ERR_INVAL (null ctx). */
 int gea_set_wait_limit(gea_ctx *ctx, int64_t polls);
+
+/* Phase trace of the persistent step kernels (tracing; the paper has no
+ * counterpart: it measures the phases of Section 3's step, Steps 1-3 and the
+ * PISO correctors, as the device runs them). trace: a caller-owned device
+ * buffer of `capacity` uint64 values, 8-byte aligned, written by every step
+ * launched while it is set; the library keeps the pointer, not the data.
+ * With B the blocks of the persistent grid (returned in *blocks, which may
+ * be null; 0 when the context steps through the CUDA graph), row 0 holds,
+ * per block b, its kernel entry time at [2b] and its SM at [2b + 1]; row k
+ * (1 <= k <= max_barriers) holds block b's arrival at [2(kB + b)] and its
+ * release from [2(kB + b) + 1] the k-th grid barrier of the launch, in
+ * ns of the GPU's global timer. Barriers past max_barriers are not
+ * recorded. The grid barriers of a step separate its phases: the Jacobi
+ * sweeps, the right-hand sides, the EOS update, the two phases of each CG
+ * iteration, the corrections. capacity must be at least
+ * 2 (max_barriers + 1) B. trace null turns the trace off (as does
+ * gea_set_tile_shape). Errors: GEA_ERR_INVAL (null ctx, max_barriers < 1
+ * with a buffer, a capacity too small, a misaligned buffer, a context
+ * without the persistent driver). */
+int gea_set_trace(gea_ctx *ctx, uint64_t *trace, int32_t max_barriers, int64_t capacity, int32_t *blocks);
 int gea_get_field(gea_ctx *ctx, int32_t which, double *host);
 
 /* Apply the pressure solve's preconditioner to r: z = M r with M one

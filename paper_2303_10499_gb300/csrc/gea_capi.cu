@@ -65,6 +65,8 @@ struct gea_ctx {
     int base = 0;                         // state slot loaded by the last set_state
     int pers_blocks = 0;                  // persistent-kernel grid (0: graph path only)
     long long wait_polls = -1;            // grid-barrier poll limit of the persistent kernels (< 0: default)
+    unsigned long long *trace = nullptr;  // phase trace of the persistent kernels (gea_set_trace; not owned)
+    int trace_bars = 0;
     int shape = SHAPE_32x8;               // tile shape of the persistent kernels (gea_set_tile_shape)
     long long steps_at_sync = 0;          // device steps_done at the last sync
     // GEA_FLAG_DEBUG_PADS: the pitched arrays, on the host and the device,
@@ -138,6 +140,8 @@ StepArgs step_args(gea_ctx *c, int from)
     a.jac_rtol2 = c->C.jac_rtol * c->C.jac_rtol;
     a.cg_rtol2 = c->C.cg_rtol * c->C.cg_rtol;
     a.tiles_per_block = c->tiles_per_block;
+    a.trace = c->trace;
+    a.trace_bars = c->trace_bars;
     return a;
 }
 
@@ -1261,6 +1265,9 @@ int gea_set_tile_shape(gea_ctx *ctx, int32_t shape)
         ctx->pers_blocks = (long long)pmax < nt ? pmax : (int)nt;
     }
     ctx->shape = shape;
+    // a phase trace was sized for the previous grid of blocks
+    ctx->trace = nullptr;
+    ctx->trace_bars = 0;
     return GEA_OK;
 }
 
@@ -1268,6 +1275,26 @@ int gea_set_wait_limit(gea_ctx *ctx, int64_t polls)
 {
     if (!ctx) return GEA_ERR_INVAL;
     ctx->wait_polls = polls < 0 ? -1 : polls;
+    return GEA_OK;
+}
+
+int gea_set_trace(gea_ctx *ctx, uint64_t *trace, int32_t max_barriers, int64_t capacity, int32_t *blocks)
+{
+    if (!ctx || max_barriers < 0 || (trace && max_barriers == 0)) return GEA_ERR_INVAL;
+    if (blocks) *blocks = ctx->pers_blocks;
+    if (!trace) {
+        ctx->trace = nullptr;
+        ctx->trace_bars = 0;
+        return GEA_OK;
+    }
+    if (ctx->pers_blocks <= 0)
+        return fail(ctx, GEA_ERR_INVAL, "the phase trace needs the persistent driver");
+    if (capacity < 2LL * (max_barriers + 1) * ctx->pers_blocks)
+        return fail(ctx, GEA_ERR_INVAL, "trace buffer of %lld values holds fewer than 2 x %d x %d",
+                    (long long)capacity, max_barriers + 1, ctx->pers_blocks);
+    if (reinterpret_cast<uintptr_t>(trace) % 8) return fail(ctx, GEA_ERR_INVAL, "trace buffer not 8-byte aligned");
+    ctx->trace = reinterpret_cast<unsigned long long *>(trace);
+    ctx->trace_bars = max_barriers;
     return GEA_OK;
 }
 

@@ -167,6 +167,11 @@ struct StepArgs {
     double *partials;
     double jac_rtol2, cg_rtol2;
     int tiles_per_block;   // per-phase kernels with a reduction: tiles a block walks (0: the size rule)
+    // phase trace of the persistent kernels (gea_set_trace; null: off):
+    // per block its entry time and SM, then per grid barrier its arrival
+    // and release times (%globaltimer), for at most trace_bars barriers
+    unsigned long long *trace;
+    int trace_bars;
 };
 
 __device__ __forceinline__ int cidx(const Geom &G, int i, int k) { return k * G.P + i; }

@@ -69,7 +69,22 @@ struct Grp {
     unsigned *gen;   // barriers this block has passed in this launch
     Scal *gs;        // the context's scalars in global memory (barrier words, status, results)
     unsigned long long spin_limit;   // polls of a barrier before the block gives up
+    unsigned long long *trace;       // phase trace (null: off), see trace_entry
+    int trace_bars;                  // barriers the trace holds
 };
+
+// Phase trace layout: 2 x nb values per row; row 0 holds each block's
+// kernel entry time and SM, row k >= 1 each block's arrival at and release
+// from the k-th grid barrier of the launch (%globaltimer, ns).
+__device__ __forceinline__ void trace_entry(const Grp &g)
+{
+    if (g.trace && tid_of() == 0) {
+        unsigned smid;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+        g.trace[2 * (size_t)g.rank] = globaltimer();
+        g.trace[2 * (size_t)g.rank + 1] = smid;
+    }
+}
 
 // The block's own copy of the context's scalars. Every block finishes every
 // grid reduction itself (the same partials added in the same order give
@@ -110,6 +125,9 @@ __device__ __forceinline__ void gbar(const Grp &g)
     if (tid_of() == 0) {
         const unsigned k = *g.gen + 1u;
         const unsigned target = k * (unsigned)g.nb;
+        unsigned long long *tr =
+            (g.trace && k <= (unsigned)g.trace_bars) ? g.trace + 2 * ((size_t)k * g.nb + g.rank) : nullptr;
+        if (tr) tr[0] = globaltimer();
         unsigned c = atom_add_acq_rel(&gs->bar_count, 1u) + 1u;
         unsigned long long spins = 0;
         while ((int)(c - target) < 0) {
@@ -119,6 +137,7 @@ __device__ __forceinline__ void gbar(const Grp &g)
             }
             c = ld_acquire(&gs->bar_count);
         }
+        if (tr) tr[1] = globaltimer();
         *g.gen = k;
         s_stop = rdi(&gs->status) != 0 || s_ctl.status != 0;
     }
@@ -619,7 +638,8 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_persistent(PersistArgs P)
     }
     load_ctl(gs);
     __syncthreads();
-    const Grp g{(int)blockIdx.x, (int)gridDim.x, &gen, gs, P.spin_limit};
+    const Grp g{(int)blockIdx.x, (int)gridDim.x, &gen, gs, P.spin_limit, P.a[0].trace, P.a[0].trace_bars};
+    trace_entry(g);
     if (!s_stop) {
         if (blockIdx.x == 0 && tid_of() == 0) gs->launches += 1;
         for (int s = 0; s < P.nsteps; ++s) {
@@ -647,7 +667,8 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_persistent_mixed(PersistArgs P,
     }
     load_ctl(gs);
     __syncthreads();
-    const Grp g{(int)blockIdx.x, (int)gridDim.x, &gen, gs, P.spin_limit};
+    const Grp g{(int)blockIdx.x, (int)gridDim.x, &gen, gs, P.spin_limit, P.a[0].trace, P.a[0].trace_bars};
+    trace_entry(g);
     if (!s_stop) {
         if (blockIdx.x == 0 && tid_of() == 0) gs->launches += 1;
         for (int s = 0; s < P.nsteps; ++s) {
@@ -699,7 +720,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_ensemble(const char *Pm, int st
     load_ctl(sc);
     __syncthreads();
     const Grp g{(int)blockIdx.x - __ldg(&first[m]), __ldg(&first[m + 1]) - __ldg(&first[m]), &gen, sc,
-                P.spin_limit};
+                P.spin_limit, nullptr, 0};
     if (!s_stop) {
         if (g.rank == 0 && tid == 0) sc->launches += 1;
         for (int s = 0; s < P.nsteps; ++s) {

@@ -122,6 +122,7 @@ def library() -> C.CDLL:
         lib.gea_attach_net.argtypes = [P, P, I]
         lib.gea_set_tiles_per_block.argtypes = [P, I]
         lib.gea_set_wait_limit.argtypes = [P, C.c_int64]
+        lib.gea_set_trace.argtypes = [P, P, I, C.c_int64, C.POINTER(I)]
         lib.gea_set_tile_shape.argtypes = [P, I]
         lib.gea_apply_precond.argtypes = [P, P, P]
         lib.gea_probe_fma.argtypes = [I, I, I, P, P]
@@ -329,6 +330,35 @@ class Solver:
         """Grid-barrier poll limit of the persistent kernels (gea_set_wait_limit;
         < 0: the default)."""
         self._check(self.lib.gea_set_wait_limit(self.h, int(polls)))
+
+    def trace_step(self, max_barriers: int = 512) -> Dict:
+        """One step of the persistent driver with its phase trace
+        (gea_set_trace). Returns the grid's blocks, each block's SM and entry
+        time, and per grid barrier of the step (rows) every block's arrival
+        and release (columns), in ns after the earliest block entry; only the
+        barriers the step passed are kept."""
+        import torch
+        nb = C.c_int32(0)
+        self._check(self.lib.gea_set_trace(self.h, None, 0, 0, C.byref(nb)))
+        if nb.value <= 0:
+            raise GeaError(GEA_ERR_INVAL, "the phase trace needs the persistent driver")
+        cap = 2 * (max_barriers + 1) * nb.value
+        buf = torch.zeros(cap, dtype=torch.int64, device="cuda")
+        torch.cuda.synchronize()
+        self._check(self.lib.gea_set_trace(self.h, C.c_void_p(buf.data_ptr()), int(max_barriers), cap,
+                                           C.byref(nb)))
+        try:
+            self.step(1)
+        finally:
+            self.lib.gea_set_trace(self.h, None, 0, 0, None)
+        t = buf.cpu().numpy().view(np.uint64).reshape(max_barriers + 1, nb.value, 2)
+        entry = t[0, :, 0].astype(np.int64)
+        used = int(np.count_nonzero(t[1:, 0, 0]))
+        t0 = entry.min()
+        arrive = t[1:1 + used, :, 0].astype(np.int64) - t0
+        release = t[1:1 + used, :, 1].astype(np.int64) - t0
+        return {"blocks": nb.value, "sm": t[0, :, 1].astype(np.int64), "entry": entry - t0,
+                "arrive": arrive, "release": release, "barriers": used}
 
     def pressure_ms(self) -> float:
         return float(self.lib.gea_last_pressure_ms(self.h))

@@ -7,11 +7,18 @@ per-kernel times of each step.
     python -m paper_2303_10499_gb300.run --ensemble 12 --steps 2
     python -m paper_2303_10499_gb300.run --conv 16,16,0 --h 2048 --w 4096 --steps 5
     python -m paper_2303_10499_gb300.run --workload bubble3d_192x192x96 --steps 3 [--eager]
+    python -m paper_2303_10499_gb300.run --workload bubble640x320 --steps 5 --trace
 
 --eager advances every step with gea_profile_step: the kernels of the CUDA
 graph launched one by one from the host, each bracketed by CUDA events (the
 form a kernel profiler can attach to; kernels inside a graph with conditional
 nodes cannot be profiled individually).
+
+--trace advances --steps steps, then traces one more step of the persistent
+driver (gea_set_trace) and prints one line per phase: the grid barrier that
+ends it, the mean and largest time a block spent in the phase (from its
+release from the previous barrier, or its entry, to its arrival), and the
+time from the last arrival to the releases.
 """
 import argparse
 import json
@@ -27,6 +34,7 @@ def main(argv=None):
     ap.add_argument("--eager", action="store_true", help="per-kernel launches (profiled step)")
     ap.add_argument("--ensemble", type=int, default=0,
                     help="step this many LES bubbles of the ensemble workload in one launch per step")
+    ap.add_argument("--trace", action="store_true", help="phase trace of one persistent step")
     ap.add_argument("--conv", default="", help="cin,cout,mode: time gea_conv3x3 on an h x w image")
     ap.add_argument("--h", type=int, default=2048)
     ap.add_argument("--w", type=int, default=4096)
@@ -50,6 +58,8 @@ def main(argv=None):
     else:
         s = gea.Solver(wl.grid, wl.const, graph=args.graph, mixed=args.mixed)
     s.set_conservative(wl.fields)
+    if args.trace:
+        return run_trace(args, s, wl)
     per_kernel = {}
     t0 = time.perf_counter()
     for _ in range(args.steps):
@@ -66,6 +76,60 @@ def main(argv=None):
     if per_kernel:
         out["per_kernel"] = per_kernel
     print(json.dumps(out))
+    s.close()
+
+
+def phase_labels(st, n_corr, les):
+    """Names of the phases of one FP64 persistent step with a one-level
+    preconditioner, in the order of their grid barriers (the structure of
+    the step kernel), from the step's sweep and iteration counts."""
+    lab = ["LES eddy viscosity"] if les else []
+    lab.append("Step 1: predictor set-up + momentum sweep 1")
+    lab += [f"momentum sweep {j}" for j in range(2, st["jac_u"] + 1)]
+    lab.append("Step 2: enthalpy right-hand side + sweep 1")
+    lab += [f"enthalpy sweep {j}" for j in range(2, st["jac_h"] + 1)]
+    lab.append("EOS update + H(u)")
+    for c in range(n_corr):
+        if c > 0:
+            lab.append("H(u)")
+        lab.append(f"corrector {c + 1}: pressure right-hand side")
+        its = st["cg_iters"][c]
+        if its > 0:
+            lab.append(f"corrector {c + 1}: first preconditioning")
+        for i in range(1, its + 1):
+            lab += [f"corrector {c + 1}: CG {i} p, A p", f"corrector {c + 1}: CG {i} update + preconditioning"]
+        if c + 1 < n_corr:
+            lab.append(f"corrector {c + 1}: correction")
+    lab.append(f"corrector {n_corr}: correction + step end")
+    return lab
+
+
+def run_trace(args, s, wl):
+    import numpy as np
+    for _ in range(args.steps):
+        s.step(1)
+    tr = s.trace_step()
+    st = s.stats()
+    a, r = tr["arrive"], tr["release"]
+    prev = np.vstack([tr["entry"][None, :], r[:-1]])
+    work = (a - prev) / 1e3
+    lab = None
+    if st["driver"] == "persistent" and st["mg_levels"] == 1:
+        lab = phase_labels(st, wl.const.n_corr, wl.const.cs > 0)
+        if len(lab) != tr["barriers"]:
+            lab = None
+    for k in range(tr["barriers"]):
+        print(json.dumps({"barrier": k + 1, "phase": lab[k] if lab else None,
+                          "block_us_mean": round(float(work[k].mean()), 2),
+                          "block_us_max": round(float(work[k].max()), 2),
+                          "release_after_last_arrival_us": round(float((r[k] - a[k].max()).mean() / 1e3), 2)}))
+    step_us = float(r[-1].max()) / 1e3
+    print(json.dumps({"workload": wl.name, "driver": st["driver"], "blocks": tr["blocks"],
+                      "barriers": tr["barriers"], "step_us": round(step_us, 1),
+                      "sum_block_us_max": round(float(work.max(axis=1).sum()), 1),
+                      "sum_block_us_mean": round(float(work.mean(axis=1).sum()), 1),
+                      "sum_release_us": round(float(sum((r[k] - a[k].max()).mean() for k in range(tr["barriers"])) / 1e3), 1),
+                      "stats": st}))
     s.close()
 
 
