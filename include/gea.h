@@ -415,12 +415,16 @@ int gea_probe_barrier(int32_t blocks, int32_t iters, int32_t read_status, void *
 /* ---- ensembles: many independent contexts advanced by one launch ----
  *
  * An ensemble runs the steps of n contexts (members, each with its own
- * grid, constants and state) in one cooperative launch: every member gets a
- * contiguous share of the GPU's co-resident thread blocks, in proportion to
- * its weight (default: its number of tiles of the members' tile shape; at
- * least one block, at most one per tile), and steps on those blocks with
- * its own grid barrier and its own reductions, so members never wait for
- * one another. The members are all FP64 or all mixed precision
+ * grid, constants and state) in one cooperative launch. The GPU's
+ * co-resident thread blocks are shared out in proportion to the members'
+ * weights (default: a member's number of tiles of the members' tile shape).
+ * A member whose share is one block or more runs on blocks of its own (at
+ * most one per tile) with its own grid barrier and its own reductions, so
+ * members never wait for one another; members whose shares are below one
+ * block are packed, in member order and up to one block's worth of weight,
+ * onto a block they share and on which they run one after another, each as
+ * a grid of one block (if that left a larger member without a block, every
+ * member gets one of its own instead). The members are all FP64 or all mixed precision
  * (GEA_FLAG_MIXED: the mixed-precision step, one launch for all of them),
  * and share one tile shape (gea_set_tile_shape). The results of a member are
  * those of its own persistent driver up to the order of the reduction sums.
@@ -428,15 +432,17 @@ int gea_probe_barrier(int32_t blocks, int32_t iters, int32_t read_status, void *
  * sets all of them); while it exists, step members only through it. Members
  * must not use GEA_FLAG_KEEP_R0 or an attached network.
  * Errors: GEA_ERR_INVAL (null or unsuitable members, FP64 and mixed members
- * together, different tile shapes, more members than co-resident blocks),
+ * together, different tile shapes, no partition of the blocks that fits),
  * GEA_ERR_STATE (a member without state, on step), GEA_ERR_NOMEM,
  * GEA_ERR_CUDA. */
 typedef struct gea_ensemble gea_ensemble;
 /* weights (optional, n positive values): blocks in proportion to weights[m]
- * instead of the member's tile count. */
+ * (a member's work: tiles times the phases of its step) instead of the
+ * member's tile count. */
 int gea_ensemble_create(gea_ctx **members, int32_t n, const double *weights, gea_ensemble **out);
 int gea_ensemble_set_stream(gea_ensemble *e, void *stream);
-/* Blocks given to member m (0 <= m < n), or -1. */
+/* Blocks member m (0 <= m < n) runs on (1 for a member on a shared block),
+ * or -1. */
 int gea_ensemble_blocks(const gea_ensemble *e, int32_t m);
 /* Enqueue n steps of every member (one launch); gea_sync on a member, or
  * gea_ensemble_sync, waits and reports. While every member's state is in

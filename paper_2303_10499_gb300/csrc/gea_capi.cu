@@ -1348,13 +1348,15 @@ int gea_attach_net(gea_ctx *ctx, gea_net *net, int32_t mode)
 
 struct gea_ensemble {
     std::vector<gea_ctx *> m;
-    std::vector<int> first;          // first block of each member, n + 1 entries
+    std::vector<int> groups;         // group table of the launch (PersistOps::launch_ensemble)
+    int ngroups = 0;
+    std::vector<int> nbm;            // blocks each member runs on (1: a block it may share)
     int blocks = 0;
     cudaStream_t st = nullptr;
     size_t argb = 0;                 // bytes of one member's argument block
     char *hargs = nullptr;           // pinned host staging of the argument blocks
     void *dargs = nullptr;
-    int *dfirst = nullptr;
+    int *dgroups = nullptr;
     int shape = SHAPE_32x8;          // the members' tile shape
     bool mixed = false;              // mixed-precision members (GEA_FLAG_MIXED)
     // the launch as a CUDA graph: one instantiated graph (a cooperative kernel
@@ -1403,8 +1405,8 @@ gea_ensemble::Graph *ensemble_graph(gea_ensemble *e, int n, int parity, long lon
     bool ok = cudaMemcpy(g.dargs, e->hargs, bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaStreamBeginCapture(e->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     if (ok) {
-        const cudaError_t le = persist_ops(e->shape).launch_ensemble(g.dargs, e->mixed ? 1 : 0, e->dfirst,
-                                                                    (int)e->m.size(), e->blocks, e->cap);
+        const cudaError_t le = persist_ops(e->shape).launch_ensemble(g.dargs, e->mixed ? 1 : 0, e->dgroups,
+                                                                    e->ngroups, e->blocks, e->cap);
         const cudaError_t ce = cudaStreamEndCapture(e->cap, &g.g);
         ok = le == cudaSuccess && ce == cudaSuccess && g.g &&
              cudaGraphInstantiate(&g.x, g.g, 0) == cudaSuccess;
@@ -1417,6 +1419,102 @@ gea_ensemble::Graph *ensemble_graph(gea_ensemble *e, int n, int parity, long lon
     }
     e->graphs.push_back(g);
     return &e->graphs.back();
+}
+
+// Blocks of an ensemble launch for members of weights wt (tiles[i] tiles
+// each) on B co-resident blocks, as a group table (PersistOps::
+// launch_ensemble) and the blocks each member runs on. A member whose share
+// B wt / sum(wt) is below one block runs on a block it shares with other
+// such members, packed in member order while their shares add up to at most
+// one block (they run in turn); the others split the remaining blocks in
+// proportion to their weights (at least one each, at most one per tile, the
+// remainder by largest fractional share). If that would leave a member
+// without a block, every member gets a block of its own (n <= B) and the
+// rest in proportion. Returns false if no partition fits.
+bool ensemble_partition(const std::vector<double> &wt, const std::vector<long long> &tiles, int B,
+                        std::vector<int> &groups, int &ngroups, std::vector<int> &nbm, int &blocks)
+{
+    const int n = (int)wt.size();
+    auto split = [&](const std::vector<int> &who, int avail, std::vector<int> &nb) -> bool {
+        nb.assign(who.size(), 1);
+        if ((int)who.size() > avail) return false;
+        double tot = 0.0;
+        for (int i : who) tot += wt[i];
+        const int extra = avail - (int)who.size();
+        std::vector<double> frac(who.size(), 0.0);
+        int used = (int)who.size();
+        for (size_t k = 0; k < who.size(); ++k) {
+            const double share = (double)extra * wt[who[k]] / tot;
+            int e = (int)share;
+            if (e > tiles[who[k]] - 1) e = (int)tiles[who[k]] - 1;
+            nb[k] += e;
+            used += e;
+            frac[k] = share - e;
+        }
+        while (used < avail) {
+            int best = -1;
+            for (size_t k = 0; k < who.size(); ++k)
+                if (nb[k] < tiles[who[k]] && (best < 0 || frac[k] > frac[best])) best = (int)k;
+            if (best < 0) break;
+            nb[best] += 1;
+            frac[best] = -1.0;
+            used += 1;
+        }
+        return true;
+    };
+    double tot = 0.0;
+    for (double w : wt) tot += w;
+    std::vector<int> big;
+    std::vector<std::vector<int>> bins;
+    double load = 2.0;
+    for (int i = 0; i < n; ++i) {
+        const double share = (double)B * wt[i] / tot;
+        if (share >= 1.0) {
+            big.push_back(i);
+            continue;
+        }
+        if (load + share > 1.0) {
+            bins.emplace_back();
+            load = 0.0;
+        }
+        bins.back().push_back(i);
+        load += share;
+    }
+    std::vector<int> nb;
+    std::vector<int> gb{0}, gm{0}, order;
+    nbm.assign(n, 1);
+    if (split(big, B - (int)bins.size(), nb)) {
+        for (size_t k = 0; k < big.size(); ++k) {
+            gb.push_back(gb.back() + nb[k]);
+            gm.push_back(gm.back() + 1);
+            order.push_back(big[k]);
+            nbm[big[k]] = nb[k];
+        }
+        for (const auto &bin : bins) {
+            gb.push_back(gb.back() + 1);
+            gm.push_back(gm.back() + (int)bin.size());
+            order.insert(order.end(), bin.begin(), bin.end());
+        }
+    } else {
+        std::vector<int> all(n);
+        for (int i = 0; i < n; ++i) all[i] = i;
+        if (!split(all, B, nb)) return false;
+        gb.assign(1, 0);
+        gm.assign(1, 0);
+        order.clear();
+        for (int i = 0; i < n; ++i) {
+            gb.push_back(gb.back() + nb[i]);
+            gm.push_back(gm.back() + 1);
+            order.push_back(i);
+            nbm[i] = nb[i];
+        }
+    }
+    ngroups = (int)gb.size() - 1;
+    blocks = gb.back();
+    groups = gb;
+    groups.insert(groups.end(), gm.begin(), gm.end());
+    groups.insert(groups.end(), order.begin(), order.end());
+    return true;
 }
 
 }  // namespace
@@ -1441,45 +1539,23 @@ int gea_ensemble_create(gea_ctx **members, int32_t n, const double *weights, gea
     const PersistOps &ops = persist_ops(shape);
     const int B = ops.ensemble_max_blocks(members[0]->mixed ? 1 : 0);
     cudaGetLastError();
-    if (B < n) return GEA_ERR_INVAL;
-    // blocks in proportion to the members' tiles, at least one each and at
-    // most one per tile; the remainder by largest fractional share
+    if (B < 1) return GEA_ERR_INVAL;
     std::vector<long long> tiles(n);
     std::vector<double> wt(n);
-    double tot = 0.0;
     for (int i = 0; i < n; ++i) {
         tiles[i] = shape_tiles(members[i]->G, ops.bx, ops.bz);
         wt[i] = weights ? weights[i] : (double)tiles[i];
         if (!(wt[i] > 0.0) || !(wt[i] < 1e300)) return GEA_ERR_INVAL;
-        tot += wt[i];
     }
-    std::vector<int> nb(n, 1);
-    int left = B - n;
-    std::vector<double> frac(n, 0.0);
-    for (int i = 0; i < n; ++i) {
-        const double share = (double)left * wt[i] / tot;
-        int extra = (int)share;
-        if (extra > tiles[i] - 1) extra = (int)tiles[i] - 1;
-        nb[i] += extra;
-        frac[i] = share - extra;
-    }
-    int used = 0;
-    for (int i = 0; i < n; ++i) used += nb[i];
-    while (used < B) {
-        int best = -1;
-        for (int i = 0; i < n; ++i)
-            if (nb[i] < tiles[i] && (best < 0 || frac[i] > frac[best])) best = i;
-        if (best < 0) break;
-        nb[best] += 1;
-        frac[best] = -1.0;
-        used += 1;
-    }
+    std::vector<int> groups, nbm;
+    int ngroups = 0, blocks = 0;
+    if (!ensemble_partition(wt, tiles, B, groups, ngroups, nbm, blocks)) return GEA_ERR_INVAL;
     gea_ensemble *e = new gea_ensemble();
     e->m.assign(members, members + n);
-    e->first.resize(n + 1);
-    e->first[0] = 0;
-    for (int i = 0; i < n; ++i) e->first[i + 1] = e->first[i] + nb[i];
-    e->blocks = e->first[n];
+    e->groups = groups;
+    e->ngroups = ngroups;
+    e->nbm = nbm;
+    e->blocks = blocks;
     e->shape = shape;
     e->mixed = members[0]->mixed;
     e->argb = persist_args_bytes(e->mixed ? 1 : 0);   // the kernel indexes an array of argument blocks
@@ -1487,8 +1563,8 @@ int gea_ensemble_create(gea_ctx **members, int32_t n, const double *weights, gea
     if (cudaStreamCreateWithFlags(&e->cap, cudaStreamNonBlocking) != cudaSuccess ||
         cudaMallocHost(&e->hargs, e->argb * n) != cudaSuccess ||
         cudaMalloc(&e->dargs, e->argb * n) != cudaSuccess ||
-        cudaMalloc(&e->dfirst, sizeof(int) * (n + 1)) != cudaSuccess ||
-        cudaMemcpy(e->dfirst, e->first.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaMalloc(&e->dgroups, sizeof(int) * groups.size()) != cudaSuccess ||
+        cudaMemcpy(e->dgroups, groups.data(), sizeof(int) * groups.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaGetLastError();
         gea_ensemble_destroy(e);
         return GEA_ERR_NOMEM;
@@ -1517,7 +1593,7 @@ int gea_ensemble_set_stream(gea_ensemble *e, void *stream)
 int gea_ensemble_blocks(const gea_ensemble *e, int32_t m)
 {
     if (!e || m < 0 || m >= (int)e->m.size()) return -1;
-    return e->first[m + 1] - e->first[m];
+    return e->nbm[m];
 }
 
 int gea_ensemble_step(gea_ensemble *e, int32_t n)
@@ -1550,7 +1626,7 @@ int gea_ensemble_step(gea_ensemble *e, int32_t n)
     ensemble_fill(e, n, -1);
     if (cudaMemcpyAsync(e->dargs, e->hargs, e->argb * e->m.size(), cudaMemcpyHostToDevice, e->st) !=
             cudaSuccess ||
-        persist_ops(e->shape).launch_ensemble(e->dargs, e->mixed ? 1 : 0, e->dfirst, (int)e->m.size(), e->blocks,
+        persist_ops(e->shape).launch_ensemble(e->dargs, e->mixed ? 1 : 0, e->dgroups, e->ngroups, e->blocks,
                                               e->st) != cudaSuccess) {
         cudaGetLastError();
         return GEA_ERR_CUDA;
@@ -1583,7 +1659,7 @@ void gea_ensemble_destroy(gea_ensemble *e)
     if (e->cap) cudaStreamDestroy(e->cap);
     if (e->hargs) cudaFreeHost(e->hargs);
     if (e->dargs) cudaFree(e->dargs);
-    if (e->dfirst) cudaFree(e->dfirst);
+    if (e->dgroups) cudaFree(e->dgroups);
     delete e;
 }
 

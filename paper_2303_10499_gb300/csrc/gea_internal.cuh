@@ -456,8 +456,10 @@ inline unsigned long long spin_limit_of(long long wait_polls)
 //      hierarchy Lf), wait_polls as in spin_limit_of;
 //  launch_ensemble: one argument block per member in device memory
 //      (persist_args_fill, or persist_args_fill_mixed for mixed-precision
-//      members: mixed != 0), first[m] the member's first block (nmem + 1
-//      entries).
+//      members: mixed != 0) and the group table of the blocks: ngroups + 1
+//      first blocks, ngroups + 1 first entries of the member list, then the
+//      member list (a group of several blocks runs one member, a group of one
+//      block one or more members in turn).
 struct PersistOps {
     int bx, bz;
     int (*max_blocks)();
@@ -469,7 +471,7 @@ struct PersistOps {
     cudaError_t (*launch_mixed)(const StepArgs a[2], const Level &L0, const MixedArgs &m, const LevelF *Lf,
                                 int nlev, int ncoarse, int n_corr, int jac_maxit, int cg_maxit, int first_slot,
                                 int nsteps, int blocks, long long wait_polls, cudaStream_t st);
-    cudaError_t (*launch_ensemble)(const void *Pm, int mixed, const int *first, int nmem, int blocks,
+    cudaError_t (*launch_ensemble)(const void *Pm, int mixed, const int *groups, int ngroups, int blocks,
                                    cudaStream_t st);
 };
 enum { SHAPE_32x8 = 0, SHAPE_16x16 = 1, SHAPE_64x4 = 2, NSHAPES = 3 };

@@ -680,57 +680,66 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_persistent_mixed(PersistArgs P,
     leave(g);
 }
 
-// An ensemble of independent contexts in one cooperative launch: member m
-// runs its steps on blocks first[m] .. first[m+1]-1 with its own grid
-// barrier and reductions over those blocks only, so members whose solves
-// take different iteration counts never wait for one another. Each block
-// keeps its member's arguments in shared memory: a PersistArgs block of
+// An ensemble of independent contexts in one cooperative launch. The blocks
+// form groups (table `groups`: ngroups + 1 first blocks, ngroups + 1 first
+// entries of the member list, then the member list): a group of several
+// blocks runs one member, with its own barrier and reductions over those
+// blocks only, so members whose solves take different iteration counts never
+// wait for one another; a group of one block may run several small members,
+// one after another, each as a one-block grid. Each block keeps the argument
+// block of the member it runs in shared memory: a PersistArgs block of
 // `stride` bytes per member, for the mixed-precision step (MX) followed by
 // the member's MixedPersist.
 template <bool MX>
-__global__ void __launch_bounds__(NTHREADS, 3) k_ensemble(const char *Pm, int stride, const int *first, int nmem)
+__global__ void __launch_bounds__(NTHREADS, 3) k_ensemble(const char *Pm, int stride, const int *groups, int ngroups)
 {
     extern __shared__ double dsm[];
     double *sm = dsm;
     double *red = dsm + kTileSmem;
     PersistArgs *Ps = reinterpret_cast<PersistArgs *>(dsm + kTileSmem + kRedVals * NTHREADS);
     const int tid = tid_of();
-    int lo = 0, hi = nmem - 1;
+    const int *gb = groups, *gm = groups + ngroups + 1, *order = gm + ngroups + 1;
+    int lo = 0, hi = ngroups - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) / 2;
-        if (__ldg(&first[mid]) <= (int)blockIdx.x) lo = mid;
+        if (__ldg(&gb[mid]) <= (int)blockIdx.x) lo = mid;
         else hi = mid - 1;
     }
-    const int m = lo;
-    {
-        const uint32_t *src = reinterpret_cast<const uint32_t *>(Pm + (size_t)m * stride);
-        uint32_t *dst = reinterpret_cast<uint32_t *>(Ps);
-        for (int i = tid; i < stride / 4; i += NTHREADS) dst[i] = __ldg(&src[i]);
-    }
-    __syncthreads();
-    const PersistArgs &P = *Ps;
-    const MixedPersist &X = *reinterpret_cast<const MixedPersist *>(reinterpret_cast<const char *>(Ps) +
-                                                                    sizeof(PersistArgs));
-    Scal *sc = P.a[0].sc;
+    const int b0 = __ldg(&gb[lo]), nbk = __ldg(&gb[lo + 1]) - b0;
+    const int i1 = __ldg(&gm[lo + 1]);
     __shared__ unsigned gen;
-    if (tid == 0) {
-        s_stop = rdi(&sc->status) != 0;
-        gen = 0u;
-    }
-    load_ctl(sc);
-    __syncthreads();
-    const Grp g{(int)blockIdx.x - __ldg(&first[m]), __ldg(&first[m + 1]) - __ldg(&first[m]), &gen, sc,
-                P.spin_limit, nullptr, 0};
-    if (!s_stop) {
-        if (g.rank == 0 && tid == 0) sc->launches += 1;
-        for (int s = 0; s < P.nsteps; ++s) {
-            const int slot = (P.first_slot + s) & 1;
-            const bool ok = MX ? run_step_mixed(P, X, P.a[slot], g, sm, red) : run_step(P, P.a[slot], g, sm, red);
-            if (!ok) break;
+    for (int i = __ldg(&gm[lo]); i < i1; ++i) {
+        const int m = __ldg(&order[i]);
+        __syncthreads();   // nothing reads the previous member's arguments any more
+        {
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(Pm + (size_t)m * stride);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(Ps);
+            for (int w = tid; w < stride / 4; w += NTHREADS) dst[w] = __ldg(&src[w]);
         }
-        if (g.rank == 0 && tid == 0 && rdi(&sc->status)) sc->last_status = rdi(&sc->status);
+        __syncthreads();
+        const PersistArgs &P = *Ps;
+        const MixedPersist &X = *reinterpret_cast<const MixedPersist *>(reinterpret_cast<const char *>(Ps) +
+                                                                        sizeof(PersistArgs));
+        Scal *sc = P.a[0].sc;
+        if (tid == 0) {
+            s_stop = rdi(&sc->status) != 0;
+            gen = 0u;
+        }
+        load_ctl(sc);
+        __syncthreads();
+        const Grp g{(int)blockIdx.x - b0, nbk, &gen, sc, P.spin_limit, nullptr, 0};
+        if (!s_stop) {
+            if (g.rank == 0 && tid == 0) sc->launches += 1;
+            for (int s = 0; s < P.nsteps; ++s) {
+                const int slot = (P.first_slot + s) & 1;
+                const bool ok =
+                    MX ? run_step_mixed(P, X, P.a[slot], g, sm, red) : run_step(P, P.a[slot], g, sm, red);
+                if (!ok) break;
+            }
+            if (g.rank == 0 && tid == 0 && rdi(&sc->status)) sc->last_status = rdi(&sc->status);
+        }
+        leave(g);
     }
-    leave(g);
 }
 
 // bytes of one member's argument block and the ensemble kernels' shared memory
@@ -751,11 +760,11 @@ int ensemble_max_blocks(int mixed)
     return per_sm * sms;
 }
 
-cudaError_t launch_ensemble(const void *Pm, int mixed, const int *first, int nmem, int blocks, cudaStream_t st)
+cudaError_t launch_ensemble(const void *Pm, int mixed, const int *groups, int ngroups, int blocks, cudaStream_t st)
 {
     const char *P = static_cast<const char *>(Pm);
     int stride = (int)(mixed ? kArgsMixed : kArgsFp64);
-    void *args[] = {&P, &stride, &first, &nmem};
+    void *args[] = {&P, &stride, &groups, &ngroups};
     const void *k = mixed ? (const void *)k_ensemble<true> : (const void *)k_ensemble<false>;
     return cudaLaunchCooperativeKernel(k, dim3(blocks), dim3(BX, BZ), args,
                                        mixed ? kEnsembleSmemMixed : kEnsembleSmem, st);

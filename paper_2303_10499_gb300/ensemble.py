@@ -9,7 +9,10 @@ the thread blocks. The tuner weights member m by
     w_m = tiles_m * (1 + iterations_m) ** beta
 
 with iterations_m the Jacobi sweeps and CG iterations of its last step
-(beta = 0: tiles only), times a few real steps of the run with each beta,
+(beta = 0: tiles only; members whose weight is worth less than a block are
+packed onto shared blocks by the library, so a heavy weight on the large
+members is not capped by one block for every small one), times a few real
+steps of the run with each beta,
 and keeps the fastest partition. It does so for each tile shape of the
 persistent kernels (one thread per cell of a 32 x 8, 16 x 16 or 64 x 4
 tile; squarer tiles load smaller halos, wider ones longer rows, and the

@@ -214,3 +214,36 @@ def test_mixed_precision_ensemble(gea):
     with pytest.raises(gea.GeaError) as ei:
         gea.Ensemble([f, ss[1]])
     assert ei.value.code == gea.GEA_ERR_INVAL
+
+
+def test_small_members_share_blocks(gea):
+    """Members whose weight share is below one block are packed onto blocks
+    they share and run in turn, each as a one-block grid: an ensemble may
+    then hold more members than there are co-resident blocks, and every
+    member still matches its own persistent driver to rounding."""
+    wls = [W.random_flow(W.Grid(24, 16, 240.0, 160.0), W.Constants(dt=0.2, mu=1.5), seed=s, uamp=2.0,
+                         thamp=1.0) for s in range(600)]
+    wls.append(W.get("les400"))      # one large member beside them
+    steps = 4
+    ss = [gea.Solver(wl.grid, wl.const) for wl in wls]
+    for s, wl in zip(ss, wls):
+        s.set_conservative(wl.fields)
+    E = gea.Ensemble(ss)
+    nb = E.blocks()
+    assert len(nb) == len(wls) > 456 and all(b == 1 for b in nb[:-1]) and nb[-1] > 1
+    E.step(steps)
+    E.sync()
+    for k in list(range(0, 600, 37)) + [599, 600]:
+        st = ss[k].stats()
+        assert st["status"] == 0 and st["steps_done"] == steps, (k, st)
+        ref = gea.Solver(wls[k].grid, wls[k].const)
+        ref.set_conservative(wls[k].fields)
+        ref.step(steps)
+        a, b = ss[k].get_full(), ref.get_full()
+        vel = np.hypot(np.linalg.norm(b["u"]), np.linalg.norm(b["w"]))
+        for f in ("rho", "T", "pp"):
+            assert rel(a[f], b[f]) < 1e-12, (k, f)
+        for f in ("u", "w"):
+            assert np.linalg.norm(a[f] - b[f]) / vel < 1e-9, (k, f)
+        ref.close()
+    E.close()
