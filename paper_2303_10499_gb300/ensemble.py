@@ -45,7 +45,7 @@ def member_work(solvers, shape: int = 0) -> Tuple[np.ndarray, np.ndarray]:
     return tiles, np.array(its, dtype=np.float64)
 
 
-def autotune(solvers, stream=None, betas: Sequence[float] = (0.0, 0.5, 1.0, 1.5),
+def autotune(solvers, stream=None, betas: Sequence[float] = (0.0, 0.5, 1.0, 1.5, 2.0, 2.5),
              trial_steps: int = 2, shapes: Sequence[int] = (0, 1, 2)) -> Tuple["gea.Ensemble", Dict]:
     """Return the ensemble with the fastest tile shape and block partition
     and a report of the trials (ms per step for each shape and beta). The
