@@ -177,6 +177,46 @@ def _is_device(a) -> bool:
     return not isinstance(a, np.ndarray) and getattr(a, "is_cuda", False)
 
 
+CHECKPOINT_VERSION = 1
+
+
+def write_checkpoint(path: str, grid, const, state: Dict[str, np.ndarray], steps_done: int = 0) -> None:
+    """Write a FULL state (Solver.get_full) to `path` as an .npz file: the
+    state arrays, and as JSON the grid (nx, nz, lx, lz), the constants' fields
+    and the number of steps done. Reading it back and setting it continues
+    the run bit for bit (gea_set_state with the FULL view)."""
+    import dataclasses
+    import json
+    meta = {"version": CHECKPOINT_VERSION, "grid": [int(grid.nx), int(grid.nz), float(grid.lx), float(grid.lz)],
+            "constants": dataclasses.asdict(const) if dataclasses.is_dataclass(const) else dict(vars(const)),
+            "steps_done": int(steps_done), "fields": sorted(state)}
+    arrays = {k: np.ascontiguousarray(v, dtype=np.float64) for k, v in state.items()}
+    with open(path, "wb") as f:
+        np.savez(f, meta=np.array(json.dumps(meta)), **arrays)
+
+
+def read_checkpoint(path: str, grid=None) -> Dict:
+    """Read a checkpoint written by write_checkpoint: {"state", "grid",
+    "constants", "steps_done"}. With `grid`, the checkpoint must be of that
+    grid (GeaError GEA_ERR_INVAL otherwise); the arrays' shapes are checked
+    against the grid either way."""
+    import json
+    with np.load(path, allow_pickle=False) as z:
+        meta = json.loads(str(z["meta"]))
+        if meta.get("version") != CHECKPOINT_VERSION:
+            raise GeaError(GEA_ERR_INVAL, f"checkpoint version {meta.get('version')} is not {CHECKPOINT_VERSION}")
+        state = {k: np.array(z[k]) for k in meta["fields"]}
+    nx, nz, lx, lz = meta["grid"]
+    if grid is not None and (nx, nz) != (grid.nx, grid.nz):
+        raise GeaError(GEA_ERR_INVAL, f"checkpoint of a {nx} x {nz} grid, not {grid.nx} x {grid.nz}")
+    shapes = {"phix": (nz, nx + 1), "phiz": (nz + 1, nx)}
+    for k, v in state.items():
+        if v.shape != shapes.get(k, (nz, nx)):
+            raise GeaError(GEA_ERR_INVAL, f"checkpoint field {k} has shape {v.shape}")
+    return {"state": state, "grid": meta["grid"], "constants": meta["constants"],
+            "steps_done": meta["steps_done"]}
+
+
 class Solver:
     """One context of the library: a grid, its constants and device state."""
 
@@ -251,6 +291,19 @@ class Solver:
         only with READING_K_LAGGED."""
         lagged = getattr(self.const, "reading_flags", 0) & READING_K_LAGGED
         return FULL_FIELDS if lagged else FULL_FIELDS[:-1]
+
+    def save_checkpoint(self, path: str) -> None:
+        """The full state (get_full) with the grid, constants and steps done,
+        as an .npz file (write_checkpoint)."""
+        write_checkpoint(path, self.grid, self.const, self.get_full(), self.stats()["steps_done"])
+
+    def load_checkpoint(self, path: str) -> Dict:
+        """Set the full state from a checkpoint of this grid (read_checkpoint);
+        the steps that follow continue the checkpointed run bit for bit.
+        Returns the checkpoint's metadata."""
+        ck = read_checkpoint(path, self.grid)
+        self.set_full(ck["state"])
+        return ck
 
     def get_full(self, out: Optional[Dict] = None) -> Dict[str, np.ndarray]:
         nx, nz = self.grid.nx, self.grid.nz

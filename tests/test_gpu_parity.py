@@ -166,6 +166,26 @@ def test_checkpoint_roundtrip_bitwise(gea):
         assert np.array_equal(got[k], ref[k]), k
 
 
+def test_checkpoint_file_resumes_bitwise(gea, tmp_path):
+    """A checkpoint file of the full state (Solver.save_checkpoint) loaded
+    into a new context continues bit for bit."""
+    wl = W.get("bubble160x80")
+    a = gea.Solver(wl.grid, wl.const)
+    a.set_conservative(wl.fields)
+    a.step(6)
+    path = str(tmp_path / "bubble.npz")
+    a.save_checkpoint(path)
+    a.step(4)
+    ref = a.get_full()
+    b = gea.Solver(wl.grid, wl.const)
+    ck = b.load_checkpoint(path)
+    assert ck["steps_done"] == 6
+    b.step(4)
+    got = b.get_full()
+    for k in ref:
+        assert np.array_equal(got[k], ref[k]), k
+
+
 def test_deterministic(gea):
     wl = W.get("bubble160x80")
     out = []
