@@ -70,6 +70,15 @@ int gea3d_step(gea3d_ctx *ctx, int32_t n);
 int gea3d_get_state(gea3d_ctx *ctx, double *rho, double *u, double *v, double *w, double *T, double *p,
                     double *pp, int32_t mem);
 
+/* Diagnostics of the current state (Remark 2), computed on the device:
+ * theta' = T (p0/p)^(R/cp) - theta_bar(z) per cell into theta_prime (host or
+ * device, nz*ny*nx, x fastest; may be NULL) given the background theta_bar
+ * (host or device, nz values); mass = sum rho V and energy = sum rho e V with
+ * e = cv T + |u|^2/2 + g z (Section 2.1) (each may be NULL). Synchronises.
+ * Errors: GEA_ERR_INVAL (null ctx, theta_prime without theta_bar),
+ * GEA_ERR_STATE (no state), GEA_ERR_CUDA. */
+int gea3d_get_diag(gea3d_ctx *ctx, const double *theta_bar, double *theta_prime, double *mass, double *energy);
+
 /* Counters of the last completed step (driver 0: CUDA graph). */
 int gea3d_get_stats(gea3d_ctx *ctx, gea_stats *s);
 

@@ -38,7 +38,7 @@ constexpr double kCoarsestRatio = 1.0;
 constexpr double kRefT = 300.0;
 enum { E3 = 0, U3 = 1, V3 = 2, W3 = 3, H3 = 4 };
 enum { L_MOM = 0, L_ENTH = 1, L_CG = 2 };
-enum { C_PRED = 0, C_MOM, C_ERHS, C_ENTH, C_HELM, C_RZ, C_PQ, C_UPD, C_DER };
+enum { C_PRED = 0, C_MOM, C_ERHS, C_ENTH, C_HELM, C_RZ, C_PQ, C_UPD, C_DER, C_DIAG };
 
 struct Geo {
     int nx, ny, nz, P;
@@ -98,6 +98,7 @@ struct Sc {
     int last_status;
     long long launches;
     unsigned counters[16];
+    double mass, energy;   // diagnostics (k_diag3)
 };
 
 struct Args {
@@ -1535,6 +1536,33 @@ Geo make_geo(int nx, int ny, int nz, double lx, double ly, double lz)
 // elements of one array (cells or faces) of a level
 size_t elems(const Geo &G) { return (size_t)(G.nz + 1) * (G.ny + 1) * G.P; }
 
+// Diagnostics (Remark 2) in three dimensions: theta' = T (p0/p)^(R/cp) -
+// theta_bar(z) per cell into th (dense nz x ny x nx, x fastest; optional),
+// mass = sum rho V and energy = sum rho (cv T + |u|^2/2 + g z) V (Section
+// 2.1's total energy) into the scalars.
+__global__ void k_diag3(Geo G, Phy F, double p0, St S, const double *thbar, const double *gzc, double *th, Sc *sc,
+                        double *part)
+{
+    __shared__ double red[2 * NT];
+    int i, j, k;
+    double v[2] = {0.0, 0.0};
+    if (cell(G, i, j, k)) {
+        const int q = id3(G, i, j, k);
+        const double T = ld(&S.T[q]), rho = ld(&S.rho[q]);
+        if (th) th[((size_t)k * G.ny + j) * G.nx + i] = T / pow(ld(&S.p[q]) / p0, F.R / F.cp) - ld(&thbar[k]);
+        const double u = ld(&S.u[q]), vv = ld(&S.v[q]), w = ld(&S.w[q]);
+        const double V = G.dx * G.dy * G.dz;
+        const double K = 0.5 * (u * u + vv * vv + w * w);
+        v[0] = rho * V;
+        v[1] = rho * ((F.cp - F.R) * T + K + ld(&gzc[k])) * V;
+    }
+    double tot[2];
+    if (gsum<2>(v, red, part, &sc->counters[C_DIAG], tot)) {
+        sc->mass = tot[0];
+        sc->energy = tot[1];
+    }
+}
+
 dim3 grid_of(const Geo &G) { return dim3((G.nx + TX - 1) / TX, (G.ny + TY - 1) / TY, G.nz); }
 // the grid of the column kernels (kLayers cell layers per block)
 dim3 gridc_of(const Geo &G) { return dim3((G.nx + TX - 1) / TX, (G.ny + TY - 1) / TY, (G.nz + kLayers - 1) / kLayers); }
@@ -2106,6 +2134,32 @@ int gea3d_get_state(gea3d_ctx *ctx, double *rho, double *u, double *v, double *w
         CK3(cudaMemcpy3DAsync(&c, ctx->stream));
     }
     CK3(cudaStreamSynchronize(ctx->stream));
+    return GEA_OK;
+}
+
+int gea3d_get_diag(gea3d_ctx *ctx, const double *theta_bar, double *theta_prime, double *mass, double *energy)
+{
+    if (!ctx) return GEA_ERR_INVAL;
+    if (!ctx->have_state) return fail3(ctx, GEA_ERR_STATE, "no state set");
+    if (theta_prime && !theta_bar) return fail3(ctx, GEA_ERR_INVAL, "theta_prime needs theta_bar");
+    Sc h;
+    CK3(cudaMemcpyAsync(&h, ctx->sc, sizeof(Sc), cudaMemcpyDeviceToHost, ctx->stream));
+    CK3(cudaStreamSynchronize(ctx->stream));
+    const St &S = ctx->S[h.steps_done & 1];
+    const Geo &G = ctx->G;
+    const size_t cells = (size_t)G.nx * G.ny * G.nz;
+    // the staging area (5 dense fields) holds theta_bar, then theta'
+    double *thb = ctx->stage, *tho = ctx->stage + cells;
+    if (theta_bar) CK3(cudaMemcpyAsync(thb, theta_bar, G.nz * sizeof(double), cudaMemcpyDefault, ctx->stream));
+    k_diag3<<<grid_of(G), kBlk, 0, ctx->stream>>>(G, ctx->F, ctx->C.p0, S, thb, ctx->gz,
+                                                  theta_prime ? tho : nullptr, ctx->sc, ctx->part);
+    CK3(cudaGetLastError());
+    if (theta_prime)
+        CK3(cudaMemcpyAsync(theta_prime, tho, cells * sizeof(double), cudaMemcpyDefault, ctx->stream));
+    CK3(cudaMemcpyAsync(&h, ctx->sc, sizeof(Sc), cudaMemcpyDeviceToHost, ctx->stream));
+    CK3(cudaStreamSynchronize(ctx->stream));
+    if (mass) *mass = h.mass;
+    if (energy) *energy = h.energy;
     return GEA_OK;
 }
 

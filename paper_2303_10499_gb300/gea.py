@@ -155,6 +155,7 @@ def library() -> C.CDLL:
         lib.gea3d_step.argtypes = [P, I]
         lib.gea3d_get_state.argtypes = [P, P, P, P, P, P, P, P, I]
         lib.gea3d_get_stats.argtypes = [P, C.POINTER(_Stats)]
+        lib.gea3d_get_diag.argtypes = [P, P, P, P, P]
         lib.gea3d_profile_step.argtypes = [P, C.POINTER(_KTime), I, C.POINTER(I)]
         lib.gea3d_last_error.argtypes = [P]
         lib.gea3d_last_error.restype = C.c_char_p
@@ -785,6 +786,18 @@ class Solver3D:
         ptrs = [_addr(out[k]) if k in out else None for k in STATE3_FIELDS]
         self._check(self.lib.gea3d_get_state(self.h, *ptrs, mem))
         return out
+
+    def diagnostics(self, theta_bar: np.ndarray):
+        """theta' (nz, ny, nx), mass and total energy of the current state,
+        computed on the device (gea3d_get_diag)."""
+        tb = np.ascontiguousarray(theta_bar, dtype=np.float64)
+        g = self.grid
+        th = np.empty((g.nz, g.ny, g.nx))
+        m = C.c_double()
+        e = C.c_double()
+        self._check(self.lib.gea3d_get_diag(self.h, tb.ctypes.data, th.ctypes.data, C.addressof(m),
+                                            C.addressof(e)))
+        return th, m.value, e.value
 
     def step(self, n: int = 1):
         self._check(self.lib.gea3d_step(self.h, int(n)))

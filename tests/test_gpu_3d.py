@@ -273,3 +273,28 @@ def test_full_size_les_bubble_properties(gea):
     assert np.abs(u - v.transpose(0, 2, 1)).max() < 1e-8 * sc
     m0 = wl.fields["rho"].sum()
     assert abs(f["rho"].sum() - m0) < 1e-12 * m0
+
+
+def test_diagnostics_on_the_device(gea):
+    """theta', mass and total energy of gea3d_get_diag against their
+    definitions (Remark 2; Section 2.1's e = cv T + |u|^2/2 + g z) evaluated
+    on the state gea3d_get_state returns, after a few steps of the bubble."""
+    wl = W.get("bubble3d_64x64x32")
+    s = gea.Solver3D(wl.grid, wl.const)
+    s.set_conservative(wl.fields)
+    s.step(3)
+    th, m, e = s.diagnostics(wl.theta_bar)
+    st = s.get_state()
+    c, g = wl.const, wl.grid
+    th_ref = st["T"] * (c.p0 / st["p"]) ** (c.R / c.cp) - wl.theta_bar[:, None, None]
+    assert np.abs(th - th_ref).max() < 1e-11
+    assert th.max() > 0.5                     # the bubble's warm anomaly is there
+    V = g.dx * g.dy * g.dz
+    z = (np.arange(g.nz) + 0.5) * g.dz
+    assert abs(m - st["rho"].sum() * V) / m < 1e-13
+    K = 0.5 * (st["u"] ** 2 + st["v"] ** 2 + st["w"] ** 2)
+    e_ref = (st["rho"] * ((c.cp - c.R) * st["T"] + K + c.g * z[:, None, None])).sum() * V
+    assert abs(e - e_ref) / abs(e_ref) < 1e-12
+    # theta' needs the background
+    assert s.lib.gea3d_get_diag(s.h, None, th.ctypes.data, None, None) == gea.GEA_ERR_INVAL
+    s.close()
