@@ -330,8 +330,7 @@ int gea_get_field(gea_ctx *ctx, int32_t which, double *host);
 /* Apply the pressure solve's preconditioner to r: z = M r with M one
  * V(1,1)-cycle of the Galerkin multigrid hierarchy of the last completed step
  * (the operator of eq. p_prime_sd in its Helmholtz form, as the CG of Step 3
- * uses it; two Jacobi sweeps with the step's Chebyshev weights when the
- * hierarchy has one level). r, z:
+ * uses it; two undamped Jacobi sweeps when the hierarchy has one level). r, z:
  * nz*nx doubles, host or device. Lets a caller check what CG needs of M: it
  * is linear, symmetric and positive definite. FP64 contexts only.
  * Synchronises. Errors: GEA_ERR_INVAL (null pointers, a mixed-precision

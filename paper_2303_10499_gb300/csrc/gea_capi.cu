@@ -583,7 +583,6 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
     ctx->F.les_d2 = c->cs * c->cs * ctx->G.dx * ctx->G.dz;
     ctx->F.R = c->R; ctx->F.cp = c->cp; ctx->F.g = c->g; ctx->F.p0 = c->p0;
     ctx->F.mu = c->mu; ctx->F.nuh = c->mu / c->Pr; ctx->F.dt = c->dt; ctx->F.idt = 1.0 / c->dt;
-    ctx->F.omega = kOmega;
     ctx->F.k_lagged = (c->reading_flags & GEA_READING_K_LAGGED) ? 1 : 0;
     ctx->F.les = ctx->F.les_d2 > 0.0 ? 1 : 0;
     ctx->F.pr_ne1 = ctx->F.nuh != ctx->F.mu ? 1 : 0;
@@ -608,6 +607,15 @@ int gea_create(const gea_grid *grid, const gea_constants *c, gea_ctx **out)
         lg.push_back(make_geom(f.nx / 2, f.nz / 2, f.nx * f.dx, f.nz * f.dz));
         ratio *= 0.25;
     }
+    // Jacobi weight: omega damps the smoother of a multigrid hierarchy; a
+    // one-level preconditioner is two undamped sweeps (omega = 1), whose
+    // preconditioned operator lambda (2 - lambda) on the spectrum of D^-1 A
+    // (inside its Gershgorin interval [1 - rho, 1 + rho], rho < 1) is the
+    // degree-2 Chebyshev polynomial of that interval up to a factor, which
+    // CG does not see: condition number 1 / (1 - rho^2) for any rho, against
+    // (1 - (1 - omega (1 + rho))^2) / (1 - (1 - omega (1 - rho))^2) for two
+    // damped sweeps (1.28 against 1.50 at rho = 0.47, omega = 0.8)
+    ctx->F.omega = lg.size() == 1 ? 1.0 : kOmega;
 
     // one allocation for everything
     const Geom &G = ctx->G;

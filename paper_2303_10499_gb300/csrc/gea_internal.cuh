@@ -134,31 +134,7 @@ struct Scal {
     int h1_slot;
     unsigned long long press_ns; // globaltimer nanoseconds of the pressure solves, last step
     double galpha;              // step length of the learned initial guess
-    // single-level preconditioner: the largest omega (d_i - c_i) / d_i of the
-    // step's Helmholtz operator (omega times the Gershgorin radius of D^-1 A;
-    // FP64 bits, non-negative, so a max over them is an integer max), and
-    // the Chebyshev weights of its two sweeps relative to omega
-    unsigned long long gersh_bits;
-    double pk1, pk2;
 };
-
-// Weights of the two sweeps of the single-level preconditioner,
-// z = e + w2 D^-1 (r - A e) with e = w1 D^-1 r: the roots of the degree-2
-// Chebyshev polynomial of [1 - rho, 1 + rho], the Gershgorin interval of
-// the spectrum of D^-1 A (unit diagonal, off-diagonal row sum rho_i < 1),
-// w = 1 / (1 -+ rho / sqrt 2). The error propagator (1 - w1 l)(1 - w2 l) is
-// then at most rho^2 / (2 - rho^2) on the interval (against
-// max (1 - omega l)^2 for two damped sweeps of weight omega), and
-// M = (w1 + w2) D^-1 - w1 w2 D^-1 A D^-1 is symmetric and positive definite,
-// as CG needs. Stored relative to omega (the stored omega / d is scaled).
-__host__ __device__ inline void cheb_weights(double wrho_max, double omega, double &k1, double &k2)
-{
-    double rho = wrho_max / omega;
-    rho = rho > 0.0 ? (rho < 0.999 ? rho : 0.999) : 0.0;
-    const double h = rho * 0.70710678118654752;
-    k1 = 1.0 / ((1.0 + h) * omega);
-    k2 = 1.0 / ((1.0 - h) * omega);
-}
 
 // Optional per-launch hook (profiled eager steps only; never during graph
 // capture): begin/end bracket every kernel launch on stream st.
@@ -262,26 +238,6 @@ __device__ __forceinline__ void block_sum(const T (&v)[NV], T *red, T (&out)[NV]
         }
     }
     __syncthreads();
-}
-
-// Largest of one value per thread, valid in thread 0 (red: NTHREADS doubles;
-// every thread calls it). A maximum does not depend on the order it is taken
-// in, so it is deterministic however the blocks combine theirs.
-__device__ __forceinline__ double block_max(double v, double *red)
-{
-    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    red[tid] = v;
-    __syncthreads();
-    double m = 0.0;
-    if (tid < 32) {
-        m = red[tid];
-#pragma unroll
-        for (int q = 1; q < NTHREADS / 32; ++q) m = fmax(m, red[tid + 32 * q]);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
-    }
-    __syncthreads();
-    return m;
 }
 
 // The partials buffer of a context: kGcntDoubles doubles of group counters

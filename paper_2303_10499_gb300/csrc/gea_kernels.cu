@@ -140,11 +140,7 @@ __global__ void k_eos_coef(StepArgs a, Level L)
 {
     if (a.sc->status) return;
     __shared__ double sm[2 * kT1 + BZ * (BX + 1) + (BZ + 1) * BX];
-    double wrho = 0.0;
-    ph_eos(a, L, a.ha, sm, blockIdx.x, blockIdx.y, wrho);
-    const double bm = block_max(wrho, sm);
-    if (threadIdx.x == 0 && threadIdx.y == 0)
-        atomicMax(&a.sc->gersh_bits, (unsigned long long)__double_as_longlong(bm));
+    ph_eos(a, L, a.ha, sm, blockIdx.x, blockIdx.y);
 }
 
 __global__ void k_mg_coarsen(Level f, Level c, double omega)
@@ -168,10 +164,8 @@ __global__ void k_helm_rhs(StepArgs a, Level L, const double *xin, double *xout,
     __shared__ double red[2 * NTHREADS];
     double acc[2] = {0.0, 0.0}, tot[2];
     ph_helm_rhs(a, L, xin, xout, sm, blockIdx.x, blockIdx.y, acc);
-    if (grid_sum<2>(acc, red, a.partials, &a.sc->counters[CNT_HELM], tot)) {
+    if (grid_sum<2>(acc, red, a.partials, &a.sc->counters[CNT_HELM], tot))
         fin_helm(a.sc, tot, a.cg_rtol2, corr);
-        cheb_weights(__longlong_as_double((long long)a.sc->gersh_bits), a.F.omega, a.sc->pk1, a.sc->pk2);
-    }
 }
 
 __global__ void k_mg_down(Level f, Level c, double omega, Scal *sc)
@@ -207,8 +201,7 @@ __global__ void k_mg_single(Level f, double *out, StepArgs a)
     __shared__ double sm[kT1];
     __shared__ double red[NTHREADS];
     double acc[1] = {0.0}, tot[1];
-    const double k1 = a.sc->pk1, k2 = a.sc->pk2;
-    block_tiles(f.G, [&](int bx, int bz) { ph_mg_single(f, out, k1, k2, sm, bx, bz, acc); });
+    block_tiles(f.G, [&](int bx, int bz) { ph_mg_single(f, out, sm, bx, bz, acc); });
     if (grid_sum<1>(acc, red, a.partials, &a.sc->counters[CNT_RZ], tot)) fin_rz(a.sc, tot);
 }
 
@@ -238,8 +231,7 @@ __global__ void k_cg_update_single(StepArgs a, Level L, double *x)
     const double *p = (it & 1) ? a.p0 : a.p1;
     double acc[2] = {0.0, 0.0}, tot[2];
     block_tiles(L.G, [&](int bx, int bz) {
-        ph_update_single<double>(L, a.q, res_of(L, it), res_of(L, it + 1), x, p, sc->alpha, sc->pk1, sc->pk2, sm,
-                                 bx, bz, acc);
+        ph_update_single<double>(L, a.q, res_of(L, it), res_of(L, it + 1), x, p, sc->alpha, sm, bx, bz, acc);
     });
     if (grid_sum<2>(acc, red, a.partials, &sc->counters[CNT_UPD], tot)) {
         const double t0[1] = {tot[0]}, t1[1] = {tot[1]};
@@ -294,7 +286,6 @@ __global__ void k_step_begin(Scal *sc)
     sc->u1_slot = sc->h1_slot = 0;
     for (int c = 0; c < 4; ++c) { sc->cg_iters[c] = 0; sc->cg_relres[c] = 0.0; }
     sc->sweeps[0] = sc->sweeps[1] = 0;
-    sc->gersh_bits = 0ull;
 }
 
 __global__ void k_step_end(Scal *sc, int fixed_launches)

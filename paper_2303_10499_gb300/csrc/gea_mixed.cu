@@ -92,11 +92,7 @@ __global__ void k_mx_eos(StepArgs a, Level L, LevelF L32, const float *dh)
 {
     if (a.sc->status) return;
     __shared__ double sm[2 * kT1 + BZ * (BX + 1) + (BZ + 1) * BX];
-    double wrho = 0.0;
-    ph_eos_t<true>(a, L, L32, nullptr, dh, sm, blockIdx.x, blockIdx.y, wrho);
-    const double bm = block_max(wrho, sm);
-    if (threadIdx.x == 0 && threadIdx.y == 0)
-        atomicMax(&a.sc->gersh_bits, (unsigned long long)__double_as_longlong(bm));
+    ph_eos_t<true>(a, L, L32, nullptr, dh, sm, blockIdx.x, blockIdx.y);
 }
 
 __global__ void k_mx_coarsen(LevelF f, LevelF c, double omega)
@@ -112,10 +108,8 @@ __global__ void k_mx_helm_rhs(StepArgs a, Level L, LevelF L32, MixedArgs m, cons
     __shared__ double red[2 * NTHREADS];
     double acc[2] = {0.0, 0.0}, tot[2];
     ph_helm_rhs_t<true>(a, L, L32, m, xin, xout, sm, blockIdx.x, blockIdx.y, acc);
-    if (grid_sum<2>(acc, red, a.partials, &a.sc->counters[CNT_HELM], tot)) {
+    if (grid_sum<2>(acc, red, a.partials, &a.sc->counters[CNT_HELM], tot))
         fin_helm_mixed(a.sc, tot, a.cg_rtol2, corr);
-        cheb_weights(__longlong_as_double((long long)a.sc->gersh_bits), a.F.omega, a.sc->pk1, a.sc->pk2);
-    }
 }
 
 // ---- FP32 V-cycle and CG steps ----
@@ -154,8 +148,7 @@ __global__ void k_mx_mg_single(LevelF f, float *out, StepArgs a)
     __shared__ double red[NTHREADS];
     float acc[1] = {0.0f};
     double tot[1];
-    const double k1 = a.sc->pk1, k2 = a.sc->pk2;
-    block_tiles(f.G, [&](int bx, int bz) { ph_mg_single<float>(f, out, k1, k2, sm, bx, bz, acc); });
+    block_tiles(f.G, [&](int bx, int bz) { ph_mg_single<float>(f, out, sm, bx, bz, acc); });
     if (grid_sum<1, float>(acc, red, a.partials, &a.sc->counters[CNT_RZ], tot)) fin_rz(a.sc, tot);
 }
 
@@ -185,8 +178,7 @@ __global__ void k_mx_update_single(StepArgs a, LevelF L, MixedArgs m)
     float acc[2] = {0.0f, 0.0f};
     double tot[2];
     block_tiles(L.G, [&](int bx, int bz) {
-        ph_update_single<float>(L, m.q, res_of(L, it), res_of(L, it + 1), m.x, p, sc->alpha, sc->pk1, sc->pk2, sm,
-                                bx, bz, acc);
+        ph_update_single<float>(L, m.q, res_of(L, it), res_of(L, it + 1), m.x, p, sc->alpha, sm, bx, bz, acc);
     });
     if (grid_sum<2, float>(acc, red, a.partials, &sc->counters[CNT_UPD], tot)) {
         const double t0[1] = {tot[0]}, t1[1] = {tot[1]};

@@ -195,41 +195,6 @@ __device__ __forceinline__ void rbar(const Grp &g, const T (&v)[NV], double *red
     __syncthreads();
 }
 
-// Barrier with the grid-wide maximum of one per-thread value, which every
-// block completes from the block maxima (the partials buffers as in rbar);
-// thread 0 runs fin(max) on the block's copy of the scalars. A maximum
-// does not depend on the order it is taken in.
-template <class Fin>
-__device__ __forceinline__ void rbar_max(const Grp &g, double v, double *red, double *partials, Fin fin)
-{
-    const int tid = tid_of();
-    const int nb = g.nb;
-    double *pb = partials + kGcntDoubles + (size_t)(*g.gen & 1u) * kRedVals * nb;
-    const double bm = block_max(v, red);
-    if (tid == 0) pb[g.rank] = bm;
-    gbar(g);
-    double m = 0.0;
-    for (int b = tid; b < nb; b += NTHREADS) m = fmax(m, __ldcg(&pb[b]));
-    const double tot = block_max(m, red);
-    if (tid == 0) fin(tot);
-    __syncthreads();
-}
-
-// The Gershgorin maximum of the step's operator and the single-level
-// preconditioner's weights from it, into the block's copy of the scalars
-// and, from block rank 0, the context's (what a host-side application of
-// the preconditioner uses).
-__device__ __forceinline__ void fin_gersh(const Grp &g, Scal *sc, double wrho_max, double omega)
-{
-    sc->gersh_bits = (unsigned long long)__double_as_longlong(wrho_max);
-    cheb_weights(wrho_max, omega, sc->pk1, sc->pk2);
-    if (g.rank == 0) {
-        g.gs->gersh_bits = sc->gersh_bits;
-        g.gs->pk1 = sc->pk1;
-        g.gs->pk2 = sc->pk2;
-    }
-}
-
 template <class F>
 __device__ __forceinline__ void for_tiles(const Grp &g, const Geom &G, F f)
 {
@@ -352,12 +317,9 @@ __device__ bool run_step(const PersistArgs &P, const StepArgs &a, const Grp &g, 
     const double *h1 = hin;
     // the EOS update, and H(u^{n+1/3}) of the first corrector, which reads
     // nothing the EOS phase writes
-    {
-        double wrho = 0.0;
-        for_tiles(g, G, [&](int bx, int bz) { ph_eos(a, L[0], h1, sm, bx, bz, wrho); });
-        for_tiles(g, G, [&](int bx, int bz) { ph_H(a, u1, w1, sm, bx, bz); });
-        rbar_max(g, wrho, red, a.partials, [&](double m) { fin_gersh(g, sc, m, a.F.omega); });
-    }
+    for_tiles(g, G, [&](int bx, int bz) { ph_eos(a, L[0], h1, sm, bx, bz); });
+    for_tiles(g, G, [&](int bx, int bz) { ph_H(a, u1, w1, sm, bx, bz); });
+    gbar(g);
     for (int l = 0; l + 1 < nlev; ++l) {
         for_tiles(g, L[l + 1].G, [&](int bx, int bz) { ph_coarsen(L[l], L[l + 1], a.F.omega, bx, bz); });
         gbar(g);
@@ -409,9 +371,7 @@ __device__ bool run_step(const PersistArgs &P, const StepArgs &a, const Grp &g, 
         if (!stop(sc) && !sc->done[LOOP_CG]) {
             if (nlev == 1) {
                 double acc[1] = {0.0};
-                for_tiles(g, G, [&](int bx, int bz) {
-                    ph_mg_single(L[0], L[0].e2, sc->pk1, sc->pk2, sm, bx, bz, acc);
-                });
+                for_tiles(g, G, [&](int bx, int bz) { ph_mg_single(L[0], L[0].e2, sm, bx, bz, acc); });
                 rbar<1>(g, acc, red, a.partials, [&](const double (&t)[1]) { fin_rz(sc, t); });
             } else {
                 vcycle_levels(0);
@@ -437,7 +397,7 @@ __device__ bool run_step(const PersistArgs &P, const StepArgs &a, const Grp &g, 
                 double acc[2] = {0.0, 0.0};
                 for_tiles(g, G, [&](int bx, int bz) {
                     ph_update_single<double>(L[0], a.q, res_of(L[0], it), res_of(L[0], it + 1), a.N.pp,
-                                             pnew, alpha, sc->pk1, sc->pk2, sm, bx, bz, acc);
+                                             pnew, alpha, sm, bx, bz, acc);
                 });
                 rbar<2>(g, acc, red, a.partials, [&](const double (&t)[2]) {
                     const double t0[1] = {t[0]}, t1[1] = {t[1]};
@@ -550,12 +510,9 @@ __device__ bool run_step_mixed(const PersistArgs &P, const MixedPersist &X, cons
     if (stop(sc)) return false;
     // h^{n+1} = h^n + dh, the EOS update, the FP64 finest Helmholtz level and
     // its FP32 copy; H(u^{n+1/3}) of the first corrector reads nothing of it
-    {
-        double wrho = 0.0;
-        for_tiles(g, G, [&](int bx, int bz) { ph_eos_t<true>(a, L0, L[0], nullptr, hi, sm, bx, bz, wrho); });
-        for_tiles(g, G, [&](int bx, int bz) { ph_H(a, a.ua, a.wa, sm, bx, bz); });
-        rbar_max(g, wrho, red, a.partials, [&](double mx) { fin_gersh(g, sc, mx, a.F.omega); });
-    }
+    for_tiles(g, G, [&](int bx, int bz) { ph_eos_t<true>(a, L0, L[0], nullptr, hi, sm, bx, bz); });
+    for_tiles(g, G, [&](int bx, int bz) { ph_H(a, a.ua, a.wa, sm, bx, bz); });
+    gbar(g);
     for (int l = 0; l + 1 < nlev; ++l) {
         for_tiles(g, L[l + 1].G, [&](int bx, int bz) { ph_coarsen<float>(L[l], L[l + 1], a.F.omega, bx, bz); });
         gbar(g);
@@ -608,9 +565,7 @@ __device__ bool run_step_mixed(const PersistArgs &P, const MixedPersist &X, cons
         if (!stop(sc) && !sc->done[LOOP_CG]) {
             if (nlev == 1) {
                 float acc[1] = {0.0f};
-                for_tiles(g, G, [&](int bx, int bz) {
-                    ph_mg_single<float>(L[0], L[0].e2, sc->pk1, sc->pk2, sm, bx, bz, acc);
-                });
+                for_tiles(g, G, [&](int bx, int bz) { ph_mg_single<float>(L[0], L[0].e2, sm, bx, bz, acc); });
                 rbar<1>(g, acc, red, a.partials, [&](const double (&t)[1]) { fin_rz(sc, t); });
             } else {
                 vcycle_levels(0);
@@ -636,7 +591,7 @@ __device__ bool run_step_mixed(const PersistArgs &P, const MixedPersist &X, cons
                 float acc[2] = {0.0f, 0.0f};
                 for_tiles(g, G, [&](int bx, int bz) {
                     ph_update_single<float>(L[0], m.q, res_of(L[0], it), res_of(L[0], it + 1), m.x, pnew, alpha,
-                                            sc->pk1, sc->pk2, sm, bx, bz, acc);
+                                            sm, bx, bz, acc);
                 });
                 rbar<2>(g, acc, red, a.partials, [&](const double (&t)[2]) {
                     const double t0[1] = {t[0]}, t1[1] = {t[1]};

@@ -658,8 +658,7 @@ __device__ __forceinline__ void ph_enth(const StepArgs &a, const double *hin, do
 // MX: h^{n+1} = h^n + dh, and FP32 copies of the fine operator into L32.
 template <bool MX>
 __device__ __forceinline__ void ph_eos_t(const StepArgs &a, const Level &L, const LevelF &L32,
-                                         const double *h1, const float *dh, double *sm, int bx, int bz,
-                                         double &wrho)
+                                         const double *h1, const float *dh, double *sm, int bx, int bz)
 {
     const Geom &G = a.G;
     const Phys &F = a.F;
@@ -709,14 +708,10 @@ __device__ __forceinline__ void ph_eos_t(const StepArgs &a, const Level &L, cons
         if (i == G.nx - 1) { a.Dx[k * G.P + G.nx] = 0.0; L.ax[k * G.P + G.nx] = 0.0; }
         if (k == G.nz - 1) { a.Dz[G.nz * G.P + i] = 0.0; L.az[G.nz * G.P + i] = 0.0; }
         const double c = psi * F.idt;
-        const double lap = (Dw + De) * ix2 + (Ds + Dn) * iz2;
-        const double d = c + lap;
-        const double wdq = F.omega / d;
+        const double d = c + (Dw + De) * ix2 + (Ds + Dn) * iz2;
         L.c[q] = c;
         L.d[q] = d;
-        L.wd[q] = wdq;
-        // omega times this row's Gershgorin radius of D^-1 A
-        wrho = fmax(wrho, lap * wdq);
+        L.wd[q] = F.omega / d;
         if (MX) {
             L32.c[q] = (float)c;
             L32.d[q] = (float)d;
@@ -731,9 +726,9 @@ __device__ __forceinline__ void ph_eos_t(const StepArgs &a, const Level &L, cons
 }
 
 __device__ __forceinline__ void ph_eos(const StepArgs &a, const Level &L, const double *h1,
-                                       double *sm, int bx, int bz, double &wrho)
+                                       double *sm, int bx, int bz)
 {
-    ph_eos_t<false>(a, L, LevelF{}, h1, nullptr, sm, bx, bz, wrho);
+    ph_eos_t<false>(a, L, LevelF{}, h1, nullptr, sm, bx, bz);
 }
 
 // Galerkin coarsening with piecewise-constant transfer: the coarse reaction
@@ -994,15 +989,12 @@ __device__ __forceinline__ void ph_mg_up(const LevelT<R> &f, const R *res, const
     __syncthreads();
 }
 
-// Single-level preconditioner: two weighted Jacobi sweeps from zero,
-// z = e + k2 (omega/d)(r - A e) with e = k1 (omega/d) r, k1 and k2 the
-// Chebyshev weights of the step's operator relative to omega
-// (cheb_weights); acc += r.z.
+// Single-level preconditioner: two damped Jacobi sweeps from zero,
+// z = e + (omega/d)(r - A e) with e = (omega/d) r; acc += r.z.
 template <class R>
-__device__ __forceinline__ void ph_mg_single(const LevelT<R> &f, R *out, double k1d, double k2d, double *sm,
-                                             int bx, int bz, R (&acc)[1])
+__device__ __forceinline__ void ph_mg_single(const LevelT<R> &f, R *out, double *sm, int bx, int bz,
+                                             R (&acc)[1])
 {
-    const R k1 = (R)k1d, k2 = (R)k2d;
     const Geom &G = f.G;
     Tile<1, R> &se = tile_at<1, R>(sm, 0);
     int i, k;
@@ -1016,12 +1008,12 @@ __device__ __forceinline__ void ph_mg_single(const LevelT<R> &f, R *out, double 
         wq = ld(&f.wd[q]);
     };
     if (kPrefetch && in) fetch();
-    load_tile_fn<1, R>(se, G, bx, bz, [&](int qq, int, int) { return k1 * ld(&f.wd[qq]) * ld(&f.r[qq]); });
+    load_tile_fn<1, R>(se, G, bx, bz, [&](int qq, int, int) { return ld(&f.wd[qq]) * ld(&f.r[qq]); });
     __syncthreads();
     if (in) {
         if (!kPrefetch) fetch();
         const int y = threadIdx.y + 1, x = threadIdx.x + 1;
-        const R z = fma(k2 * wq, rq - helm_apply<1, R>(c, se, y, x), se[y][x]);
+        const R z = fma(wq, rq - helm_apply<1, R>(c, se, y, x), se[y][x]);
         out[q] = z;
         acc[0] = fma(rq, z, acc[0]);
     }
@@ -1063,8 +1055,8 @@ __device__ __forceinline__ void ph_pspmv(const LevelT<R> &L, const R *pold, R *p
 // V-cycle on the new residual (a CG iteration then needs one grid-wide
 // synchronisation less): the new residual and e = (omega/d) r_new are formed
 // on the tile and its halo from the old r and q in one pass.
-template <class R, bool SCALE>
-__device__ __forceinline__ void update_tiles(const LevelT<R> &L, const R *qv, const R *rin, R alpha, R k1,
+template <class R>
+__device__ __forceinline__ void update_tiles(const LevelT<R> &L, const R *qv, const R *rin, R alpha,
                                              Tile<1, R> &sr, Tile<1, R> &se, int bx, int bz)
 {
     const Geom &G = L.G;
@@ -1078,7 +1070,7 @@ __device__ __forceinline__ void update_tiles(const LevelT<R> &L, const R *qv, co
         if (i >= 0 && i < G.nx && k >= 0 && k < G.nz) {
             const int q = k * G.P + i;
             rn = fma(-alpha, ld(&qv[q]), ld(&rin[q]));
-            ev = SCALE ? k1 * ld(&L.wd[q]) * rn : ld(&L.wd[q]) * rn;
+            ev = ld(&L.wd[q]) * rn;
         }
         sr[tk][ti] = rn;
         se[tk][ti] = ev;
@@ -1087,16 +1079,15 @@ __device__ __forceinline__ void update_tiles(const LevelT<R> &L, const R *qv, co
 
 // The residual is read from rin (halo included) and written to rout: other
 // blocks still read the old residual while this one writes the new.
-// Single-level preconditioner (ph_mg_single's weighted sweeps): then
-// z = e + k2 (omega/d)(r_new - A e) with e = k1 (omega/d) r_new;
+// Single-level preconditioner: then z = e + (omega/d)(r_new - A e);
 // acc += (r_new^2, r_new . z).
 template <class R>
 __device__ __forceinline__ void ph_update_single(const LevelT<R> &L, const R *qv, const R *rin, R *rout,
-                                                 R *x, const R *p, double alpha_d, double k1d, double k2d,
-                                                 double *sm, int bx, int bz, R (&acc)[2])
+                                                 R *x, const R *p, double alpha_d, double *sm, int bx,
+                                                 int bz, R (&acc)[2])
 {
     const Geom &G = L.G;
-    const R alpha = (R)alpha_d, k1 = (R)k1d, k2 = (R)k2d;
+    const R alpha = (R)alpha_d;
     Tile<1, R> &sr = tile_at<1, R>(sm, 0), &se = tile_at<1, R>(sm, 1);
     int i, k;
     const bool in = cell_of(G, bx, bz, i, k);
@@ -1110,7 +1101,7 @@ __device__ __forceinline__ void ph_update_single(const LevelT<R> &L, const R *qv
         pq = ld(&p[q]);
     };
     if (kPrefetch && in) fetch();
-    update_tiles<R, true>(L, qv, rin, alpha, k1, sr, se, bx, bz);
+    update_tiles<R>(L, qv, rin, alpha, sr, se, bx, bz);
     __syncthreads();
     if (in) {
         if (!kPrefetch) fetch();
@@ -1118,7 +1109,7 @@ __device__ __forceinline__ void ph_update_single(const LevelT<R> &L, const R *qv
         const R rn = sr[y][xx];
         x[q] = fma(alpha, pq, xq);
         rout[q] = rn;
-        const R z = fma(k2 * wq, rn - helm_apply<1, R>(c, se, y, xx), se[y][xx]);
+        const R z = fma(wq, rn - helm_apply<1, R>(c, se, y, xx), se[y][xx]);
         L.e2[q] = z;
         acc[0] = fma(rn, rn, acc[0]);
         acc[1] = fma(rn, z, acc[1]);
@@ -1152,7 +1143,7 @@ __device__ __forceinline__ void ph_update_down(const LevelT<R> &f, const LevelT<
         pq = ld(&p[q0]);
     };
     if (kPrefetch && in) fetch();
-    update_tiles<R, false>(f, qv, rin, alpha, (R)1, sr, se, bx, bz);
+    update_tiles<R>(f, qv, rin, alpha, sr, se, bx, bz);
     __syncthreads();
     if (in) {
         if (!kPrefetch) fetch();
