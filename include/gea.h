@@ -280,6 +280,15 @@ int gea_attach_net(gea_ctx *ctx, struct gea_net *net, int32_t mode);
  * outside 0..16). */
 int gea_set_tiles_per_block(gea_ctx *ctx, int32_t n);
 
+/* Weight omega of the Jacobi sweeps of the pressure solve's preconditioner:
+ * the smoother of the multigrid V-cycle (default 0.8), or the two sweeps of
+ * a one-level preconditioner (default 1, undamped). Takes effect from the
+ * next step (the operator's omega/d is formed in every step's EOS phase);
+ * the converged pressure does not depend on it, the CG iterations do.
+ * Synchronises the stream; the step graphs are recorded anew. Errors:
+ * GEA_ERR_INVAL (omega outside (0, 2)). */
+int gea_set_smoother_weight(gea_ctx *ctx, double omega);
+
 /* Tile shape of the persistent step kernels (FP64, mixed precision and the
  * ensemble launch): 0 = 32 x 8 cells (the default, and the tile of the
  * per-phase kernels of the CUDA-graph driver), 1 = 16 x 16, 2 = 64 x 4; one

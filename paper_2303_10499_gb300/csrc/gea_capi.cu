@@ -300,7 +300,7 @@ int record_step(gea_ctx *ctx, int from, cudaStream_t s, bool graph, Tracer *tr)
     });
     if (rc) return rc;
     launch_eos_coef(a, L[0], s, tr); ++fixed;
-    for (int l = 0; l + 1 < nlev; ++l) { launch_mg_coarsen(L[l], L[l + 1], kOmega, s, tr); ++fixed; }
+    for (int l = 0; l + 1 < nlev; ++l) { launch_mg_coarsen(L[l], L[l + 1], ctx->F.omega, s, tr); ++fixed; }
     // Step 3: PISO correctors
     const int body_cg = (nlev == 1 ? 2 : 2 + (nlev - 2) + kCoarseSweeps + (nlev - 1)) + 1;
     for (int c = 0; c < ctx->C.n_corr; ++c) {
@@ -389,7 +389,7 @@ int record_step_mixed(gea_ctx *ctx, int from, cudaStream_t s, bool graph, Tracer
     });
     if (rc) return rc;
     launch_mx_eos(a, L0, Lf[0], m.dh[0], s, tr); ++fixed;
-    for (int l = 0; l + 1 < nlev; ++l) { launch_mx_coarsen(Lf[l], Lf[l + 1], kOmega, s, tr); ++fixed; }
+    for (int l = 0; l + 1 < nlev; ++l) { launch_mx_coarsen(Lf[l], Lf[l + 1], ctx->F.omega, s, tr); ++fixed; }
     const int body_cg = (nlev == 1 ? 2 : 2 + (nlev - 2) + kCoarseSweeps + (nlev - 1)) + 1;
     for (int c = 0; c < ctx->C.n_corr; ++c) {
         const double *U = c == 0 ? a.ua : a.N.u;
@@ -1228,6 +1228,21 @@ int gea_set_tiles_per_block(gea_ctx *ctx, int32_t n)
         ctx->graph[f] = nullptr;
     }
     ctx->tiles_per_block = n;
+    return GEA_OK;
+}
+
+int gea_set_smoother_weight(gea_ctx *ctx, double omega)
+{
+    if (!ctx || !(omega > 0.0) || !(omega < 2.0)) return GEA_ERR_INVAL;
+    if (ctx->stream) CK(cudaStreamSynchronize(ctx->stream));
+    // the step graphs hold the physical constants of their kernels
+    for (int f = 0; f < 2; ++f) {
+        if (ctx->exec[f]) cudaGraphExecDestroy(ctx->exec[f]);
+        if (ctx->graph[f]) cudaGraphDestroy(ctx->graph[f]);
+        ctx->exec[f] = nullptr;
+        ctx->graph[f] = nullptr;
+    }
+    ctx->F.omega = omega;
     return GEA_OK;
 }
 

@@ -124,6 +124,7 @@ def library() -> C.CDLL:
         lib.gea_set_wait_limit.argtypes = [P, C.c_int64]
         lib.gea_set_trace.argtypes = [P, P, I, C.c_int64, C.POINTER(I)]
         lib.gea_set_tile_shape.argtypes = [P, I]
+        lib.gea_set_smoother_weight.argtypes = [P, C.c_double]
         lib.gea_apply_precond.argtypes = [P, P, P]
         lib.gea_probe_fma.argtypes = [I, I, I, P, P]
         lib.gea_probe_barrier.argtypes = [I, I, I, P, P]
@@ -424,6 +425,10 @@ class Solver:
         (net None) detaches it."""
         self._check(self.lib.gea_attach_net(self.h, net.h if net is not None else None, mode))
         self._net = net if mode else None   # keep it alive while attached
+
+    def set_smoother_weight(self, omega: float):
+        """Weight of the preconditioner's Jacobi sweeps (gea_set_smoother_weight)."""
+        self._check(self.lib.gea_set_smoother_weight(self.h, float(omega)))
 
     def set_tiles_per_block(self, n: int):
         """Tiles a block walks in the per-phase kernels with a grid reduction

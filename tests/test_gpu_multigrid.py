@@ -145,3 +145,34 @@ def test_vcycle_linear_symmetric_positive(gea, name, nx, nz, mgmin, levels):
     a, b = s.get_full(), ref.get_full()
     for k in a:
         assert np.array_equal(a[k], b[k]), k
+
+
+def test_smoother_weight_changes_iterations_not_the_solution(gea):
+    """gea_set_smoother_weight: the weight of the preconditioner's Jacobi
+    sweeps changes how fast CG converges, not what it converges to (the
+    pressure solve runs to the same relative residual), on a one-level and a
+    three-level hierarchy; weights outside (0, 2) are refused."""
+    for name, mgmin in (("bubble160x80", 0), ("bubble160x80", 400)):
+        wl = W.get(name)
+        out = []
+        for om in (None, 0.7, 0.95):
+            s = gea.Solver(wl.grid, wl.const, mg_min_cells=mgmin)
+            s.set_conservative(wl.fields)
+            if om is not None:
+                s.set_smoother_weight(om)
+            s.step(5)
+            assert s.stats()["status"] == 0
+            out.append(s.get_full())
+            s.close()
+        ref = out[0]
+        vel = np.hypot(np.linalg.norm(ref["u"]), np.linalg.norm(ref["w"]))
+        for g in out[1:]:
+            for f in ("rho", "T", "pp"):
+                assert np.linalg.norm(g[f] - ref[f]) / np.linalg.norm(ref[f]) < 1e-12, (name, mgmin, f)
+            for f in ("u", "w"):
+                assert np.linalg.norm(g[f] - ref[f]) / vel < 1e-9, (name, mgmin, f)
+    s = gea.Solver(wl.grid, wl.const)
+    for bad in (0.0, -0.5, 2.0):
+        with pytest.raises(gea.GeaError):
+            s.set_smoother_weight(bad)
+    s.close()
