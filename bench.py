@@ -109,6 +109,10 @@ def parse():
     ap.add_argument("--full-run", action="store_true",
                     help="the 640 x 320 bubble run to t = 1020 s (20,400 steps at dt = 0.05 s), FP64 "
                          "and mixed precision, with the per-field error of the mixed run at the end")
+    ap.add_argument("--mixed-tolerance", action="store_true",
+                    help="the mixed-precision step at several inner tolerances on the 640 x 320 bubble: "
+                         "ms per step against max |theta'| from the FP64 step after 100 steps and at "
+                         "t = 1020 s")
     ap.add_argument("--oracle-table", action="store_true",
                     help="the FP64 CPU oracle, single-threaded, on W0 (160 x 80, 100 steps), W1 "
                          "(640 x 320, 100 steps) and W3 (4096 x 2048, 3 steps) from t = 0, beside the "
@@ -1100,6 +1104,77 @@ def run_full(args):
         print(json.dumps(res), flush=True)
 
 
+def run_mixed_tolerance(args):
+    """Speed against accuracy of the mixed-precision step on the 640 x 320
+    bubble: for each inner tolerance mp_rtol of its FP32 solves, the step
+    timed like the main line (L2 flushed between timed steps) and its
+    max |theta'| distance from the FP64 step after 100 steps and at
+    t = 1020 s (20,400 steps, both runs from the initial state). The FP64
+    step is timed the same way; speedup = FP64 ms / mixed ms."""
+    import numpy as np
+    import torch
+    from paper_2303_10499_gb300 import build as B
+    from paper_2303_10499_gb300 import gea
+    from paper_2303_10499_gb300 import workloads as W
+
+    world, rank, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    B.build()
+    wl = W.get("bubble640x320")
+    nfull = int(round(1020.0 / wl.const.dt))
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    def theta_after(mixed, rtol, n):
+        s = gea.Solver(wl.grid, wl.const, stream=stream, mixed=mixed, mp_rtol=rtol)
+        s.set_conservative(wl.fields)
+        done = 0
+        while done < n:
+            k = min(2000, n - done)
+            s.step(k)
+            done += k
+        st = s.stats()["status"]
+        th, _, _ = s.diagnostics(wl.theta_bar)
+        s.close()
+        return th, st
+
+    def timed(mixed, rtol):
+        s = gea.Solver(wl.grid, wl.const, stream=stream, mixed=mixed, mp_rtol=rtol)
+        s.set_conservative(wl.fields)
+        ms, _, clocks = timed_steps(s, stream, flush, args.steps, args.warmup, 1, local)
+        its = s.stats()["cg_iters"]
+        s.close()
+        return statistics.mean(ms), its, clocks
+
+    ref100, _ = theta_after(False, 0.0, 100)
+    reffull, _ = theta_after(False, 0.0, nfull)
+    ms64, its64, _ = timed(False, 0.0)
+    rows = []
+    for rtol in (1e-6, 1e-5, 1e-4, 1e-3, 1e-2):
+        ms, its, clocks = timed(True, rtol)
+        t100, st100 = theta_after(True, rtol, 100)
+        tfull, stfull = theta_after(True, rtol, nfull)
+        rows.append({"mp_rtol": rtol, "ms_per_step": ms, "speedup_vs_fp64": ms64 / ms,
+                     "cg_iters_last_step": its, "clocks": clocks,
+                     "max_abs_dtheta_K_100_steps": float(np.abs(t100 - ref100).max()),
+                     "max_abs_dtheta_K_t1020": float(np.abs(tfull - reffull).max()),
+                     "status": [st100, stfull]})
+    ok = [r for r in rows if r["max_abs_dtheta_K_t1020"] <= 1e-3 and r["status"] == [0, 0]]
+    best = max(ok, key=lambda r: r["speedup_vs_fp64"]) if ok else None
+    res = {"metric": METRIC, "value": wl.grid.cells / (best["ms_per_step"] / 1e3) if best else None,
+           "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": best["ms_per_step"] if best else None, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+           "config": {"workload": wl.name + " mixed-precision inner tolerance sweep",
+                      "value_arm": "fastest mp_rtol with max |dtheta'| <= 1e-3 K at t = 1020 s",
+                      "l2": "flushed between timed steps (256 MB write, untimed)"},
+           "fp64": {"ms_per_step": ms64, "cg_iters_last_step": its64}, "sweep": rows,
+           "best": best}
+    print(json.dumps(res), flush=True)
+
+
 def run_oracle_table(args):
     """The oracle timings of the measurement plan: the FP64 CPU oracle as it
     stands, single-threaded, on W0 (the 160 x 80 bubble, 100 steps), W1 (640
@@ -1260,6 +1335,8 @@ def main():
         run_full(args)
     elif args.oracle_table:
         run_oracle_table(args)
+    elif args.mixed_tolerance:
+        run_mixed_tolerance(args)
     else:
         run_ours(args)
 
