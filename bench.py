@@ -656,7 +656,10 @@ def run_ensemble(args):
         for sv, wl in zip(mixed, wls):
             sv.set_conservative(wl.fields)
 
-    EM = gea.Ensemble(mixed, stream=stream)
+    # the tuned partition's work weights, from the FP64 members' iterations
+    tiles_m, its_m = ensemble_tuner.member_work(solvers, shape)
+    w_mix = tiles_m * (1.0 + its_m) ** float(tune["beta"])
+    EM = gea.Ensemble(mixed, stream=stream, weights=w_mix)
     ms_mix, clocks_mix = timed(lambda: EM.step_async(1), reset_mixed)
     EM.sync()
     EM.close()
@@ -666,7 +669,7 @@ def run_ensemble(args):
     E1 = gea.Ensemble(solvers, stream=stream)
     E1.step(n_check)
     E1.close()
-    EM = gea.Ensemble(mixed, stream=stream)
+    EM = gea.Ensemble(mixed, stream=stream, weights=w_mix)
     EM.step(n_check)
     EM.close()
     dth = max(float(np.abs(m.diagnostics(wl.theta_bar)[0] - f.diagnostics(wl.theta_bar)[0]).max())
