@@ -964,6 +964,27 @@ def run_ours(args):
             "gpu_launches": int(launches_m) * world, "clocks": clocks_m, "driver": st_m["driver"],
             "error_vs_fp64": matched_error(gea, wl, 100) if rank == 0 else None,
         }
+    if rank == 0 and world == 1 and not args.mixed and wl.name == "smooth_bubble_640x320":
+        # the mixed step at matched error: inner tolerance 1e-3, timed the same
+        # way, with its max |theta'| distance from the FP64 run over the
+        # configuration's whole horizon (t = 1020 s); the bar is 1e-3 K
+        import numpy as np
+        rt = 1e-3
+        sq = gea.Solver(wl.grid, wl.const, stream=stream, mixed=True, mp_rtol=rt)
+        sq.set_conservative(dev)
+        ms_q, _, clocks_q = timed_steps(sq, stream, flush, args.steps, args.warmup, world, local)
+        its_q = sq.stats()["cg_iters"]
+        sq.close()
+        nfull = int(round(1020.0 / wl.const.dt))
+        th64, _ = theta_after(gea, wl, stream, False, 0.0, nfull)
+        thq, stq = theta_after(gea, wl, stream, True, rt, nfull)
+        err = float(np.abs(thq - th64).max())
+        res["mixed_precision_matched_error"] = {
+            "mp_rtol": rt, "value": cells * args.steps / (sum(ms_q) / 1e3), "unit": UNIT,
+            "ms_per_step": statistics.mean(ms_q), "speedup_vs_fp64": statistics.mean(ms) / statistics.mean(ms_q),
+            "cg_iters_last_step": its_q, "clocks": clocks_q,
+            "max_abs_dtheta_K_vs_fp64_t1020": err, "bar_K": 1e-3, "within_bar": bool(err <= 1e-3 and stq == 0),
+            "steps_compared": nfull}
     if rank == 0 and not args.no_w3 and wl.name != "bubble4096x2048":
         res["w3"] = w3_record(gea, W, stream, flush, pk, local)
     res["peaks"] = {k: v for k, v in pk.items()}
@@ -1107,6 +1128,23 @@ def run_full(args):
         print(json.dumps(res), flush=True)
 
 
+def theta_after(gea, wl, stream, mixed, rtol, n):
+    """theta' (device diagnostics) and status after n steps of the FP64 or
+    mixed step (inner tolerance rtol; 0: the library default) from the
+    workload's initial state."""
+    s = gea.Solver(wl.grid, wl.const, stream=stream, mixed=mixed, mp_rtol=rtol)
+    s.set_conservative(wl.fields)
+    done = 0
+    while done < n:
+        k = min(2000, n - done)
+        s.step(k)
+        done += k
+    st = s.stats()["status"]
+    th, _, _ = s.diagnostics(wl.theta_bar)
+    s.close()
+    return th, st
+
+
 def run_mixed_tolerance(args):
     """Speed against accuracy of the mixed-precision step on the 640 x 320
     bubble: for each inner tolerance mp_rtol of its FP32 solves, the step
@@ -1130,19 +1168,6 @@ def run_mixed_tolerance(args):
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
 
-    def theta_after(mixed, rtol, n):
-        s = gea.Solver(wl.grid, wl.const, stream=stream, mixed=mixed, mp_rtol=rtol)
-        s.set_conservative(wl.fields)
-        done = 0
-        while done < n:
-            k = min(2000, n - done)
-            s.step(k)
-            done += k
-        st = s.stats()["status"]
-        th, _, _ = s.diagnostics(wl.theta_bar)
-        s.close()
-        return th, st
-
     def timed(mixed, rtol):
         s = gea.Solver(wl.grid, wl.const, stream=stream, mixed=mixed, mp_rtol=rtol)
         s.set_conservative(wl.fields)
@@ -1151,14 +1176,14 @@ def run_mixed_tolerance(args):
         s.close()
         return statistics.mean(ms), its, clocks
 
-    ref100, _ = theta_after(False, 0.0, 100)
-    reffull, _ = theta_after(False, 0.0, nfull)
+    ref100, _ = theta_after(gea, wl, stream, False, 0.0, 100)
+    reffull, _ = theta_after(gea, wl, stream, False, 0.0, nfull)
     ms64, its64, _ = timed(False, 0.0)
     rows = []
     for rtol in (1e-6, 1e-5, 1e-4, 1e-3, 1e-2):
         ms, its, clocks = timed(True, rtol)
-        t100, st100 = theta_after(True, rtol, 100)
-        tfull, stfull = theta_after(True, rtol, nfull)
+        t100, st100 = theta_after(gea, wl, stream, True, rtol, 100)
+        tfull, stfull = theta_after(gea, wl, stream, True, rtol, nfull)
         rows.append({"mp_rtol": rtol, "ms_per_step": ms, "speedup_vs_fp64": ms64 / ms,
                      "cg_iters_last_step": its, "clocks": clocks,
                      "max_abs_dtheta_K_100_steps": float(np.abs(t100 - ref100).max()),
