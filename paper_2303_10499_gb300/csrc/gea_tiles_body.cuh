@@ -989,8 +989,10 @@ __device__ __forceinline__ void ph_mg_up(const LevelT<R> &f, const R *res, const
     __syncthreads();
 }
 
-// Single-level preconditioner: two damped Jacobi sweeps from zero,
-// z = e + (omega/d)(r - A e) with e = (omega/d) r; acc += r.z.
+// Single-level preconditioner: two Jacobi sweeps from zero,
+// z = e + (omega/d)(r - A e) with e = (omega/d) r (omega = 1 unless the
+// caller set another weight: then M^-1 A has the eigenvalues l (2 - l) of
+// the Chebyshev-optimal degree-2 form); acc += r.z.
 template <class R>
 __device__ __forceinline__ void ph_mg_single(const LevelT<R> &f, R *out, double *sm, int bx, int bz,
                                              R (&acc)[1])
