@@ -450,6 +450,16 @@ typedef struct gea_ensemble gea_ensemble;
  * member's tile count. */
 int gea_ensemble_create(gea_ctx **members, int32_t n, const double *weights, gea_ensemble **out);
 int gea_ensemble_set_stream(gea_ensemble *e, void *stream);
+/* The partition gea_ensemble_create makes, computed on the host alone (no
+ * device or context needed): n members of weights[m] > 0 and tiles[m] >= 1
+ * tiles on `blocks` co-resident blocks. member_blocks[m] receives the blocks
+ * member m runs on (1 on a shared block), member_group[m] its group (a
+ * group of several members shares one block and runs them in turn; a
+ * group of one member owns its blocks); *ngroups and *used_blocks (each
+ * may be NULL) the number of groups and of blocks used (<= blocks).
+ * Errors: GEA_ERR_INVAL (bad arguments, no partition that fits). */
+int gea_ensemble_plan(const double *weights, const int64_t *tiles, int32_t n, int32_t blocks,
+                      int32_t *member_blocks, int32_t *member_group, int32_t *ngroups, int32_t *used_blocks);
 /* Blocks member m (0 <= m < n) runs on (1 for a member on a shared block),
  * or -1. */
 int gea_ensemble_blocks(const gea_ensemble *e, int32_t m);

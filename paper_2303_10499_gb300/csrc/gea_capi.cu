@@ -1597,6 +1597,26 @@ int gea_ensemble_create(gea_ctx **members, int32_t n, const double *weights, gea
     return GEA_OK;
 }
 
+int gea_ensemble_plan(const double *weights, const int64_t *tiles, int32_t n, int32_t blocks,
+                      int32_t *member_blocks, int32_t *member_group, int32_t *ngroups, int32_t *used_blocks)
+{
+    if (!weights || !tiles || n < 1 || blocks < 1 || !member_blocks || !member_group) return GEA_ERR_INVAL;
+    std::vector<double> wt(weights, weights + n);
+    std::vector<long long> tl(tiles, tiles + n);
+    for (int i = 0; i < n; ++i)
+        if (!(wt[i] > 0.0) || !(wt[i] < 1e300) || tl[i] < 1) return GEA_ERR_INVAL;
+    std::vector<int> groups, nbm;
+    int ng = 0, used = 0;
+    if (!ensemble_partition(wt, tl, blocks, groups, ng, nbm, used)) return GEA_ERR_INVAL;
+    const int *gm = groups.data() + ng + 1, *order = gm + ng + 1;
+    for (int gi = 0; gi < ng; ++gi)
+        for (int k = gm[gi]; k < gm[gi + 1]; ++k) member_group[order[k]] = gi;
+    for (int i = 0; i < n; ++i) member_blocks[i] = nbm[i];
+    if (ngroups) *ngroups = ng;
+    if (used_blocks) *used_blocks = used;
+    return GEA_OK;
+}
+
 int gea_ensemble_set_graph(gea_ensemble *e, int32_t on)
 {
     if (!e) return GEA_ERR_INVAL;

@@ -131,6 +131,7 @@ def library() -> C.CDLL:
         lib.gea_ensemble_create.argtypes = [C.POINTER(P), I, P, C.POINTER(P)]
         lib.gea_ensemble_set_stream.argtypes = [P, P]
         lib.gea_ensemble_blocks.argtypes = [P, I]
+        lib.gea_ensemble_plan.argtypes = [P, P, I, I, P, P, C.POINTER(I), C.POINTER(I)]
         lib.gea_ensemble_step.argtypes = [P, I]
         lib.gea_ensemble_set_graph.argtypes = [P, I]
         lib.gea_ensemble_sync.argtypes = [P]
@@ -177,6 +178,24 @@ def _addr(a) -> int:
 
 def _is_device(a) -> bool:
     return not isinstance(a, np.ndarray) and getattr(a, "is_cuda", False)
+
+
+def ensemble_plan(weights, tiles, blocks: int) -> Dict:
+    """The block partition of an ensemble launch (gea_ensemble_plan),
+    computed on the host: per member its blocks and group, the number of
+    groups and of blocks used."""
+    lib = library()
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    t = np.ascontiguousarray(tiles, dtype=np.int64)
+    n = len(w)
+    nb = np.zeros(n, dtype=np.int32)
+    grp = np.zeros(n, dtype=np.int32)
+    ng, used = C.c_int32(0), C.c_int32(0)
+    rc = lib.gea_ensemble_plan(w.ctypes.data, t.ctypes.data, n, int(blocks), nb.ctypes.data, grp.ctypes.data,
+                               C.byref(ng), C.byref(used))
+    if rc != GEA_OK:
+        raise GeaError(rc, "gea_ensemble_plan failed")
+    return {"blocks": nb, "group": grp, "groups": ng.value, "used_blocks": used.value}
 
 
 CHECKPOINT_VERSION = 1
