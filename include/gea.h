@@ -201,8 +201,10 @@ int gea_set_stream(gea_ctx *ctx, void *stream);
  * rho and T (one synchronisation). FULL copies the fields as given (no
  * check; enqueued on the stream without waiting; host buffers must stay
  * unchanged until the stream reaches the copies).
- * Errors: GEA_ERR_INVAL (null pointers; CONSERVATIVE: rho <= 0 or T <= 0
- * anywhere). */
+ * Errors: GEA_ERR_INVAL (null pointers, unknown kind: the context is left
+ * as it was; CONSERVATIVE: rho <= 0 or T <= 0 anywhere), GEA_ERR_CUDA. After
+ * an error other than a rejected argument the context holds no state
+ * (gea_step: GEA_ERR_STATE) until a later set_state succeeds. */
 int gea_set_state(gea_ctx *ctx, const gea_state_view *v);
 
 /* Advance n >= 0 steps (Section 3, Steps 1-3). Returns after the launches
@@ -343,7 +345,8 @@ int gea_get_field(gea_ctx *ctx, int32_t which, double *host);
  * nz*nx doubles, host or device. Lets a caller check what CG needs of M: it
  * is linear, symmetric and positive definite. FP64 contexts only.
  * Synchronises. Errors: GEA_ERR_INVAL (null pointers, a mixed-precision
- * context), GEA_ERR_STATE (no completed step since the last set_state). */
+ * context), GEA_ERR_STATE (no completed step since the last set_state),
+ * GEA_ERR_CUDA; the step's solver counters are kept in every case. */
 int gea_apply_precond(gea_ctx *ctx, const double *r, double *z);
 
 /* Event-timed duration (ms) of the pressure solves (all correctors) of the
@@ -467,9 +470,10 @@ int gea_ensemble_blocks(const gea_ensemble *e, int32_t m);
  * gea_ensemble_sync, waits and reports. While every member's state is in
  * the same slot parity (always, unless members were stepped apart), the
  * launch is one CUDA graph launch: a graph holding the cooperative kernel
- * node is captured on the first call for each parity and n, with its own
- * device copy of the members' arguments, and replayed (no host staging, no
- * synchronisation). Otherwise, or after gea_ensemble_set_graph(e, 0), the
+ * node is captured on the first call for each parity, n and set of member
+ * settings the arguments carry (barrier poll limits, smoother weights), with
+ * its own device copy of the members' arguments, and replayed (no host
+ * staging, no synchronisation). Otherwise, or after gea_ensemble_set_graph(e, 0), the
  * arguments are staged and the kernel launched directly. Both run the same
  * kernel on the same arguments. */
 int gea_ensemble_step(gea_ensemble *e, int32_t n);

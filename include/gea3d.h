@@ -58,7 +58,9 @@ int gea3d_set_stream(gea3d_ctx *ctx, void *stream);
  * rho e with e = cv T + |u|^2/2 + g z; host or device per mem): u, T,
  * p = rho R T, h = cp T, p' = p + rho g z, p^{n-1} = p, and the face mass
  * fluxes from the mean of the two cells' momenta. GEA_ERR_INVAL if some
- * cell has rho <= 0 or T <= 0. */
+ * cell has rho <= 0 or T <= 0. After an error other than a rejected argument
+ * the context holds no state (gea3d_step: GEA_ERR_STATE) until a later call
+ * succeeds. */
 int gea3d_set_conservative(gea3d_ctx *ctx, const double *rho, const double *rhou, const double *rhov,
                            const double *rhow, const double *rhoe, int32_t mem);
 

@@ -2055,6 +2055,9 @@ int gea3d_set_conservative(gea3d_ctx *ctx, const double *rho, const double *rhou
         return GEA_ERR_INVAL;
     const Geo &G = ctx->G;
     const size_t n = (size_t)G.nx * G.ny * G.nz;
+    // the old state is being replaced: until this call succeeds the context
+    // holds none
+    ctx->have_state = false;
     CK3(cudaMemsetAsync(ctx->sc, 0, sizeof(Sc), ctx->stream));
     const double *src[5] = {rho, rhou, rhov, rhow, rhoe};
     for (int f = 0; f < 5; ++f)

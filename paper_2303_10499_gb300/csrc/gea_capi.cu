@@ -21,6 +21,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <utility>
 #include <vector>
 
 using namespace gea;
@@ -831,11 +832,27 @@ int gea_set_state(gea_ctx *ctx, const gea_state_view *v)
     const Geom &G = ctx->G;
     const int nx = G.nx, nz = G.nz;
     if (!v->rho) return fail(ctx, GEA_ERR_INVAL, "rho is null");
-    // reset the device scalars: status, counters, step count
-    CK(cudaMemsetAsync(ctx->sc, 0, sizeof(Scal), ctx->stream));
     State &S = ctx->S[0];
+    const double *src[11] = {v->rho, v->u, v->w, v->T, v->h, v->p, v->pp, v->pold, v->phix, v->phiz,
+                             v->Kold};
+    double *dst[11] = {S.rho, S.u, S.w, S.T, S.h, S.p, S.pp, S.pold, S.phix, S.phiz, S.Kold};
+    // K^{n-1} belongs to the state only in the literal reading of eq. step3_sd
+    const int nf = ctx->F.k_lagged ? 11 : 10;
+    // arguments are checked before the context is touched
     if (v->kind == GEA_STATE_CONSERVATIVE) {
         if (!v->rhou || !v->rhow || !v->rhoe) return fail(ctx, GEA_ERR_INVAL, "null conservative field");
+    } else if (v->kind == GEA_STATE_FULL) {
+        for (int f = 0; f < nf; ++f)
+            if (!src[f]) return fail(ctx, GEA_ERR_INVAL, "null field %d", f);
+    } else {
+        return fail(ctx, GEA_ERR_INVAL, "unknown state kind %d", v->kind);
+    }
+    // from here the old state is being replaced: until this call succeeds
+    // the context holds none
+    ctx->have_state = false;
+    // reset the device scalars: status, counters, step count
+    CK(cudaMemsetAsync(ctx->sc, 0, sizeof(Scal), ctx->stream));
+    if (v->kind == GEA_STATE_CONSERVATIVE) {
         const size_t cellw = ctx->stage_stride;
         double *st = ctx->stage;
         int rc;
@@ -845,21 +862,12 @@ int gea_set_state(gea_ctx *ctx, const gea_state_view *v)
             return rc;
         launch_derive(G, ctx->F, st, st + cellw, st + 2 * cellw, st + 3 * cellw, S, ctx->sc, ctx->stream);
         CK(cudaGetLastError());
-    } else if (v->kind == GEA_STATE_FULL) {
-        const double *src[11] = {v->rho, v->u, v->w, v->T, v->h, v->p, v->pp, v->pold, v->phix, v->phiz,
-                                 v->Kold};
-        double *dst[11] = {S.rho, S.u, S.w, S.T, S.h, S.p, S.pp, S.pold, S.phix, S.phiz, S.Kold};
-        // K^{n-1} belongs to the state only in the literal reading of eq. step3_sd
-        const int nf = ctx->F.k_lagged ? 11 : 10;
-        for (int f = 0; f < nf; ++f)
-            if (!src[f]) return fail(ctx, GEA_ERR_INVAL, "null field %d", f);
+    } else {
         for (int f = 0; f < nf; ++f) {
             const int cols = f == 8 ? nx + 1 : nx, rows = f == 9 ? nz + 1 : nz;
             int rc = copy_in(ctx, dst[f], src[f], cols, rows);
             if (rc) return rc;
         }
-    } else {
-        return fail(ctx, GEA_ERR_INVAL, "unknown state kind %d", v->kind);
     }
     if (v->kind == GEA_STATE_FULL) {
         // a full state is taken as given (only the derivation from the
@@ -1263,14 +1271,18 @@ int gea_apply_precond(gea_ctx *ctx, const double *r, double *z)
     run.cg_it = 0;
     CK(cudaMemcpyAsync(ctx->sc, &run, sizeof(Scal), cudaMemcpyHostToDevice, ctx->stream));
     Level *L = ctx->L.data();
-    if ((rc = copy_in(ctx, L[0].r, r, ctx->G.nx, ctx->G.nz))) return rc;
-    StepArgs a = step_args(ctx, 0);
-    launch_vcycle(a, L, (int)ctx->L.size(), kCoarseSweeps, ctx->stream, nullptr);
-    CK(cudaGetLastError());
-    if ((rc = copy_out(ctx, z, L[0].e2, ctx->G.nx, ctx->G.nz))) return rc;
+    rc = copy_in(ctx, L[0].r, r, ctx->G.nx, ctx->G.nz);
+    if (!rc) {
+        StepArgs a = step_args(ctx, 0);
+        launch_vcycle(a, L, (int)ctx->L.size(), kCoarseSweeps, ctx->stream, nullptr);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) rc = fail(ctx, GEA_ERR_CUDA, "V-cycle launch: %s", cudaGetErrorString(e));
+    }
+    if (!rc) rc = copy_out(ctx, z, L[0].e2, ctx->G.nx, ctx->G.nz);
+    // the scalars of the last completed step go back, also after an error
     CK(cudaMemcpyAsync(ctx->sc, &h, sizeof(Scal), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    return GEA_OK;
+    return rc;
 }
 
 int gea_set_tile_shape(gea_ctx *ctx, int32_t shape)
@@ -1389,7 +1401,10 @@ struct gea_ensemble {
     cudaStream_t cap = nullptr;      // private stream for the capture
     struct Graph {
         int parity, n;
-        long long sig;               // the members' barrier poll limits when built
+        // the members' settings that the argument blocks carry, when built:
+        // barrier poll limits and smoother weights
+        std::vector<long long> polls;
+        std::vector<double> omegas;
         void *dargs;
         cudaGraph_t g;
         cudaGraphExec_t x;
@@ -1416,12 +1431,19 @@ void ensemble_fill(gea_ensemble *e, int n, int parity)
     }
 }
 
-// the graph of n steps from state slot `parity`, built on first use
-gea_ensemble::Graph *ensemble_graph(gea_ensemble *e, int n, int parity, long long sig)
+// the graph of n steps from state slot `parity` with the members' current
+// settings, built on first use
+gea_ensemble::Graph *ensemble_graph(gea_ensemble *e, int n, int parity)
 {
+    std::vector<long long> polls;
+    std::vector<double> omegas;
+    for (gea_ctx *c : e->m) {
+        polls.push_back(c->wait_polls);
+        omegas.push_back(c->F.omega);
+    }
     for (auto &g : e->graphs)
-        if (g.parity == parity && g.n == n && g.sig == sig) return &g;
-    gea_ensemble::Graph g{parity, n, sig, nullptr, nullptr, nullptr};
+        if (g.parity == parity && g.n == n && g.polls == polls && g.omegas == omegas) return &g;
+    gea_ensemble::Graph g{parity, n, polls, omegas, nullptr, nullptr, nullptr};
     const size_t bytes = e->argb * e->m.size();
     if (cudaStreamSynchronize(e->st) != cudaSuccess || cudaMalloc(&g.dargs, bytes) != cudaSuccess) return nullptr;
     ensemble_fill(e, n, parity);
@@ -1440,7 +1462,7 @@ gea_ensemble::Graph *ensemble_graph(gea_ensemble *e, int n, int parity, long lon
         cudaFree(g.dargs);
         return nullptr;
     }
-    e->graphs.push_back(g);
+    e->graphs.push_back(std::move(g));
     return &e->graphs.back();
 }
 
@@ -1647,15 +1669,13 @@ int gea_ensemble_step(gea_ensemble *e, int32_t n)
         if (!c->have_state) return GEA_ERR_STATE;
     int parity = -1;
     bool same = true;
-    long long sig = 0;
     for (gea_ctx *c : e->m) {
         const int p = (int)((c->base + c->steps_at_sync) & 1);
         if (parity < 0) parity = p;
         else if (p != parity) same = false;
-        sig = sig * 31 + c->wait_polls + 2;
     }
     if (e->use_graph && same) {
-        gea_ensemble::Graph *g = ensemble_graph(e, n, parity, sig);
+        gea_ensemble::Graph *g = ensemble_graph(e, n, parity);
         if (g && cudaGraphLaunch(g->x, e->st) == cudaSuccess) {
             for (gea_ctx *c : e->m) c->steps_at_sync += n;
             return GEA_OK;

@@ -178,6 +178,29 @@ def test_ensemble_graph_launch_equals_direct_launch(gea):
         assert np.abs(a[k] - b[k]).max() <= 1e-13 * np.abs(b[k]).max(), k
 
 
+def test_ensemble_graph_follows_member_settings(gea):
+    """A captured ensemble graph carries the members' argument blocks; when a
+    member's smoother weight changes between steps the next launch uses the
+    new weight, so graph and direct launches stay equal bit for bit."""
+    wls = W.les_ensemble(3, seed=6)
+    out = []
+    for graph in (True, False):
+        ss = [gea.Solver(wl.grid, wl.const) for wl in wls]
+        for s, wl in zip(ss, wls):
+            s.set_conservative(wl.fields)
+        E = gea.Ensemble(ss)
+        E.set_graph(graph)
+        E.step(1)
+        ss[1].set_smoother_weight(0.8)
+        E.step(1)
+        E.step(1)
+        E.close()
+        out.append([s.get_full() for s in ss])
+    for a, b in zip(*out):
+        for k in a:
+            assert np.array_equal(a[k], b[k]), k
+
+
 def test_mixed_precision_ensemble(gea):
     """Mixed-precision members (FP64 state, FP32 inner solves) in one launch:
     each member's result is its own mixed persistent run's up to the order of

@@ -100,3 +100,35 @@ def test_nan_in_state_reports_nonfinite_and_keeps_state(gea, graph, field):
     assert ei.value.code == gea.GEA_ERR_NONFINITE
     same_state(s.get_full(), st)
     assert s.stats()["status"] == gea.GEA_ERR_NONFINITE
+
+
+def test_rejected_set_state_keeps_context(gea):
+    """A set_state whose arguments are rejected (a missing FULL field) leaves
+    the context as it was: same state, and the following steps equal an
+    uninterrupted run. A conservative state that fails its check (rho <= 0
+    in a cell) leaves no state, so the next step is refused."""
+    wl = W.get("bubble160x80")
+    s = gea.Solver(wl.grid, wl.const)
+    s.set_conservative(wl.fields)
+    s.step(2)
+    before = s.get_full()
+    partial = {k: v for k, v in before.items() if k != "T"}
+    with pytest.raises(gea.GeaError) as ei:
+        s.set_full(partial)
+    assert ei.value.code == gea.GEA_ERR_INVAL
+    same_state(s.get_full(), before)
+    assert s.stats()["steps_done"] == 2
+    s.step(1)
+    ref = gea.Solver(wl.grid, wl.const)
+    ref.set_conservative(wl.fields)
+    ref.step(3)
+    same_state(s.get_full(), ref.get_full())
+
+    bad = {k: np.array(v, copy=True) for k, v in wl.fields.items()}
+    bad["rho"][10, 20] = -1.0
+    with pytest.raises(gea.GeaError) as ei:
+        s.set_conservative(bad)
+    assert ei.value.code == gea.GEA_ERR_INVAL
+    with pytest.raises(gea.GeaError) as ei:
+        s.step(1)
+    assert ei.value.code == gea.GEA_ERR_STATE
