@@ -167,13 +167,35 @@ def library() -> C.CDLL:
     return _lib
 
 
-def _addr(a) -> int:
-    """Data pointer of a float64 numpy array or torch tensor (contiguous)."""
+def _buf(a, count: int, what: str, dtype: str = "float64", device: Optional[bool] = None) -> int:
+    """Data pointer of `a`, a numpy array or a torch tensor, after checking
+    that it is C-contiguous, of element type `dtype` ("float64", "float32",
+    "int32"; "bf16" for bfloat16 bit patterns: torch.bfloat16 or 16-bit
+    integers), holds exactly `count` elements and, with device True/False,
+    lives on the GPU/the host. The library reads or writes that many elements
+    behind the pointer, so anything else raises GeaError(GEA_ERR_INVAL)."""
     if isinstance(a, np.ndarray):
-        assert a.dtype == np.float64 and a.flags.c_contiguous, "need C-contiguous float64"
+        ok = (dtype != "bf16" and a.dtype == np.dtype(dtype) and a.flags.c_contiguous and a.size == count
+              and device is not True)
+        if not ok:
+            raise GeaError(GEA_ERR_INVAL, f"{what}: need a C-contiguous {dtype} array of {count} elements"
+                           f"{' on the device' if device else ''}, got {a.dtype} {a.shape}")
         return a.ctypes.data
-    assert a.dtype.__str__() == "torch.float64" and a.is_contiguous(), "need contiguous float64"
+    kind = str(getattr(a, "dtype", type(a).__name__))
+    types = ("torch.bfloat16", "torch.int16", "torch.uint16") if dtype == "bf16" else ("torch." + dtype,)
+    ok = (kind in types and hasattr(a, "data_ptr") and a.is_contiguous() and a.numel() == count
+          and (device is None or bool(a.is_cuda) == device))
+    if not ok:
+        shape = tuple(getattr(a, "shape", ()))
+        where = {None: "", True: " on the device", False: " on the host"}[device]
+        raise GeaError(GEA_ERR_INVAL, f"{what}: need a contiguous {dtype} tensor of {count} elements{where}, "
+                       f"got {kind} {shape}")
     return a.data_ptr()
+
+
+def _addr(a, count: int, what: str) -> int:
+    """Data pointer of a float64 field (host or device) of `count` values."""
+    return _buf(a, count, what)
 
 
 def _is_device(a) -> bool:
@@ -187,12 +209,12 @@ def ensemble_plan(weights, tiles, blocks: int) -> Dict:
     lib = library()
     w = np.ascontiguousarray(weights, dtype=np.float64)
     t = np.ascontiguousarray(tiles, dtype=np.int64)
-    n = len(w)
+    n = w.size
     nb = np.zeros(n, dtype=np.int32)
     grp = np.zeros(n, dtype=np.int32)
     ng, used = C.c_int32(0), C.c_int32(0)
-    rc = lib.gea_ensemble_plan(w.ctypes.data, t.ctypes.data, n, int(blocks), nb.ctypes.data, grp.ctypes.data,
-                               C.byref(ng), C.byref(used))
+    rc = lib.gea_ensemble_plan(_buf(w, n, "weights"), _buf(t, n, "tiles", "int64"), n, int(blocks),
+                               nb.ctypes.data, grp.ctypes.data, C.byref(ng), C.byref(used))
     if rc != GEA_OK:
         raise GeaError(rc, "gea_ensemble_plan failed")
     return {"blocks": nb, "group": grp, "groups": ng.value, "used_blocks": used.value}
@@ -283,6 +305,12 @@ class Solver:
             msg = self.lib.gea_last_error(self.h)
             raise GeaError(rc, msg.decode() if msg else "")
 
+    def _count(self, field: str) -> int:
+        """Values of a state field: nz x (nx + 1) x-face fluxes, (nz + 1) x nx
+        z-face fluxes, nz x nx cell values otherwise."""
+        nx, nz = self.grid.nx, self.grid.nz
+        return {"phix": nz * (nx + 1), "phiz": (nz + 1) * nx}.get(field, nz * nx)
+
     def set_stream(self, stream):
         """stream: a torch.cuda.Stream, a raw cudaStream_t integer or None."""
         self._stream = stream if hasattr(stream, "cuda_stream") else None
@@ -295,7 +323,7 @@ class Solver:
         v.kind = STATE_CONSERVATIVE
         v.mem = MEM_DEVICE if _is_device(fields["rho"]) else MEM_HOST
         for k in ("rho", "rhou", "rhow", "rhoe"):
-            setattr(v, k, _addr(fields[k]))
+            setattr(v, k, _addr(fields[k], self._count(k), k))
         self._check(self.lib.gea_set_state(self.h, C.byref(v)))
 
     def set_full(self, state: Dict):
@@ -304,7 +332,7 @@ class Solver:
         v.mem = MEM_DEVICE if _is_device(state["rho"]) else MEM_HOST
         for k in FULL_FIELDS:
             # Kold (K^{n-1}) is part of the state only with READING_K_LAGGED
-            setattr(v, k, _addr(state[k]) if k in state else None)
+            setattr(v, k, _addr(state[k], self._count(k), k) if k in state else None)
         self._check(self.lib.gea_set_state(self.h, C.byref(v)))
 
     def full_fields(self):
@@ -337,7 +365,7 @@ class Solver:
         v.kind = STATE_FULL
         v.mem = MEM_DEVICE if _is_device(out["rho"]) else MEM_HOST
         for k in fields:
-            setattr(v, k, _addr(out[k]))
+            setattr(v, k, _addr(out[k], self._count(k), k))
         self._check(self.lib.gea_get_state(self.h, C.byref(v)))
         return out
 
@@ -351,7 +379,7 @@ class Solver:
         v.kind = STATE_CONSERVATIVE
         v.mem = MEM_DEVICE if _is_device(out["rho"]) else MEM_HOST
         for k in ("rho", "rhou", "rhow", "rhoe"):
-            setattr(v, k, _addr(out[k]))
+            setattr(v, k, _addr(out[k], self._count(k), k))
         self._check(self.lib.gea_get_state(self.h, C.byref(v)))
         return out
 
@@ -371,8 +399,8 @@ class Solver:
         th = np.empty((self.grid.nz, self.grid.nx))
         m = C.c_double()
         e = C.c_double()
-        self._check(self.lib.gea_get_diag(self.h, tb.ctypes.data, th.ctypes.data,
-                                          C.addressof(m), C.addressof(e)))
+        self._check(self.lib.gea_get_diag(self.h, _buf(tb, self.grid.nz, "theta_bar", device=False),
+                                          th.ctypes.data, C.addressof(m), C.addressof(e)))
         return th, m.value, e.value
 
     def stats(self) -> Dict:
@@ -397,7 +425,7 @@ class Solver:
         last completed step (gea_apply_precond)."""
         r = np.ascontiguousarray(r, dtype=np.float64)
         z = np.empty((self.grid.nz, self.grid.nx))
-        self._check(self.lib.gea_apply_precond(self.h, r.ctypes.data, z.ctypes.data))
+        self._check(self.lib.gea_apply_precond(self.h, _buf(r, z.size, "r", device=False), z.ctypes.data))
         return z
 
     def set_wait_limit(self, polls: int):
@@ -610,6 +638,20 @@ def conv3x3(x0, wt, y, n, h, w, cin, cout, mode=CONV_PLAIN, flags=0, x1=None, bi
     `stream` (a torch stream or None for the current one)."""
     import torch
     st = (stream or torch.cuda.current_stream()).cuda_stream
+    n, h, w, cin, cout = int(n), int(h), int(w), int(cin), int(cout)
+    # with arguments the library accepts, every tensor must hold exactly what
+    # it reads or writes (x0 at twice the size for POOL, x1 at half for UPADD)
+    if n >= 1 and h >= 1 and w >= 1 and cin in (16, 32, 64) and cout in (16, 32, 64) and mode in (0, 1, 2):
+        f = 4 if mode == CONV_POOL else 1
+        _buf(x0, n * h * w * cin * f, "x0", "bf16", device=True)
+        if mode == CONV_UPADD and x1 is not None:
+            _buf(x1, n * (h // 2) * (w // 2) * cin, "x1", "bf16", device=True)
+        _buf(wt, cout * 9 * cin, "wt", "bf16", device=True)
+        if bias is not None:
+            _buf(bias, cout, "bias", "float32", device=True)
+        _buf(y, n * h * w * cout, "y", "float32" if flags & CONV_OUT_F32 else "bf16", device=True)
+        if status is not None:
+            _buf(status, 1, "status", "int32", device=True)
     rc = library().gea_conv3x3(n, h, w, cin, cout, mode, flags, _ptr(x0), _ptr(x1), _ptr(wt),
                                _ptr(bias), _ptr(y), _ptr(status), st)
     if rc != GEA_OK:
@@ -665,38 +707,59 @@ class Net:
     def set_params(self, theta):
         if isinstance(theta, np.ndarray):
             t = np.ascontiguousarray(theta, dtype=np.float32)
-            assert t.size == self.np
-            _chk(self.lib.gea_net_set_params(self.h, t.ctypes.data, MEM_HOST), "gea_net_set_params")
+            _chk(self.lib.gea_net_set_params(self.h, _buf(t, self.np, "theta", "float32"), MEM_HOST),
+                 "gea_net_set_params")
         else:
-            assert theta.numel() == self.np and theta.is_contiguous()
-            _chk(self.lib.gea_net_set_params(self.h, theta.data_ptr(), MEM_DEVICE), "gea_net_set_params")
+            _chk(self.lib.gea_net_set_params(self.h, _buf(theta, self.np, "theta", "float32", device=True),
+                                             MEM_DEVICE), "gea_net_set_params")
 
     def get_params(self) -> np.ndarray:
         t = np.empty(self.np, dtype=np.float32)
         _chk(self.lib.gea_net_get_params(self.h, t.ctypes.data, MEM_HOST), "gea_net_get_params")
         return t
 
+    def _operators(self, n, hh, ww, c, ax, az):
+        """Pointers of the Helmholtz coefficients of n samples of hh x ww."""
+        return (_buf(c, n * hh * ww, "c", "float32", device=True),
+                _buf(ax, n * hh * (ww + 1), "ax", "float32", device=True),
+                _buf(az, n * (hh + 1) * ww, "az", "float32", device=True))
+
     def forward(self, r, y):
-        n, hh, ww = r.shape
-        _chk(self.lib.gea_net_forward(self.h, n, hh, ww, r.data_ptr(), y.data_ptr()), "gea_net_forward")
+        n, hh, ww = (int(d) for d in r.shape)
+        pr = _buf(r, n * hh * ww, "r", "float32", device=True)
+        py = _buf(y, n * hh * ww, "y", "float32", device=True)
+        _chk(self.lib.gea_net_forward(self.h, n, hh, ww, pr, py), "gea_net_forward")
+        self._last = (n, hh, ww)
 
     def energy(self, c, ax, az, dy) -> float:
+        """Energy loss of the last forward pass (its n, h, w size the arrays)."""
+        n, hh, ww = getattr(self, "_last", (0, 0, 0))
+        if not n:
+            raise GeaError(GEA_ERR_STATE, "gea_net_energy: no forward pass")
+        pc, pax, paz = self._operators(n, hh, ww, c, ax, az)
         loss = C.c_float()
-        _chk(self.lib.gea_net_energy(self.h, c.data_ptr(), ax.data_ptr(), az.data_ptr(), dy.data_ptr(),
+        _chk(self.lib.gea_net_energy(self.h, pc, pax, paz, _buf(dy, n * hh * ww, "dy", "float32", device=True),
                                      C.byref(loss)), "gea_net_energy")
         return float(loss.value)
 
     def backward(self, dy, grad):
-        _chk(self.lib.gea_net_backward(self.h, dy.data_ptr(), grad.data_ptr()), "gea_net_backward")
+        n, hh, ww = getattr(self, "_last", (0, 0, 0))
+        if not n:
+            raise GeaError(GEA_ERR_STATE, "gea_net_backward: no forward pass")
+        _chk(self.lib.gea_net_backward(self.h, _buf(dy, n * hh * ww, "dy", "float32", device=True),
+                                       _buf(grad, self.np, "grad", "float32", device=True)), "gea_net_backward")
 
     def adam(self, grad, lr: float):
-        _chk(self.lib.gea_net_adam(self.h, grad.data_ptr(), lr), "gea_net_adam")
+        _chk(self.lib.gea_net_adam(self.h, _buf(grad, self.np, "grad", "float32", device=True), lr), "gea_net_adam")
 
     def train_step(self, r, c, ax, az, lr: float) -> float:
-        n, hh, ww = r.shape
+        n, hh, ww = (int(d) for d in r.shape)
+        pr = _buf(r, n * hh * ww, "r", "float32", device=True)
+        pc, pax, paz = self._operators(n, hh, ww, c, ax, az)
         loss = C.c_float()
-        _chk(self.lib.gea_net_train_step(self.h, n, hh, ww, r.data_ptr(), c.data_ptr(), ax.data_ptr(),
-                                         az.data_ptr(), lr, C.byref(loss)), "gea_net_train_step")
+        _chk(self.lib.gea_net_train_step(self.h, n, hh, ww, pr, pc, pax, paz, lr, C.byref(loss)),
+             "gea_net_train_step")
+        self._last = (n, hh, ww)
         return float(loss.value)
 
 
@@ -714,8 +777,7 @@ class Ensemble:
         w = None
         if weights is not None:
             self._w = np.ascontiguousarray(weights, dtype=np.float64)
-            assert self._w.size == len(self.solvers)
-            w = self._w.ctypes.data
+            w = _buf(self._w, len(self.solvers), "weights", device=False)
         h = C.c_void_p()
         _chk(self.lib.gea_ensemble_create(arr, len(self.solvers), w, C.byref(h)), "gea_ensemble_create")
         self.h = h
@@ -799,7 +861,8 @@ class Solver3D:
 
     def set_conservative(self, fields: Dict):
         mem = MEM_DEVICE if _is_device(fields["rho"]) else MEM_HOST
-        ptrs = [_addr(fields[k]) for k in ("rho", "rhou", "rhov", "rhow", "rhoe")]
+        n = self.grid.nx * self.grid.ny * self.grid.nz
+        ptrs = [_buf(fields[k], n, k, device=mem == MEM_DEVICE) for k in ("rho", "rhou", "rhov", "rhow", "rhoe")]
         self._check(self.lib.gea3d_set_conservative(self.h, *ptrs, mem))
 
     def get_state(self, out: Optional[Dict] = None) -> Dict:
@@ -807,7 +870,8 @@ class Solver3D:
         if out is None:
             out = {k: np.empty((g.nz, g.ny, g.nx)) for k in STATE3_FIELDS}
         mem = MEM_DEVICE if _is_device(next(iter(out.values()))) else MEM_HOST
-        ptrs = [_addr(out[k]) if k in out else None for k in STATE3_FIELDS]
+        n = g.nx * g.ny * g.nz
+        ptrs = [_buf(out[k], n, k, device=mem == MEM_DEVICE) if k in out else None for k in STATE3_FIELDS]
         self._check(self.lib.gea3d_get_state(self.h, *ptrs, mem))
         return out
 
@@ -819,8 +883,8 @@ class Solver3D:
         th = np.empty((g.nz, g.ny, g.nx))
         m = C.c_double()
         e = C.c_double()
-        self._check(self.lib.gea3d_get_diag(self.h, tb.ctypes.data, th.ctypes.data, C.addressof(m),
-                                            C.addressof(e)))
+        self._check(self.lib.gea3d_get_diag(self.h, _buf(tb, g.nz, "theta_bar", device=False), th.ctypes.data,
+                                            C.addressof(m), C.addressof(e)))
         return th, m.value, e.value
 
     def step(self, n: int = 1):
