@@ -311,9 +311,10 @@ int gea_set_tile_shape(gea_ctx *ctx, int32_t shape);
  * GEA_ERR_TIMEOUT and leaves the step at the next phase boundary, as does
  * every other block, so the launch always ends; the state stays at the last
  * completed step, and the error is sticky until the next gea_set_state.
- * polls < 0 restores the default (2^23 polls, a few seconds); 0 makes every
- * block that is not the last to arrive give up at once, which tests the
- * failure path without a hang. The CUDA-graph driver has no such waits.
+ * polls < 0 restores the default (2^23 polls, a few seconds), which is also
+ * the largest limit (larger values are taken as the default, so a wait stays
+ * bounded); 0 makes every block that is not the last to arrive give up at
+ * once, which tests the failure path without a hang. The CUDA-graph driver has no such waits.
  * Errors: GEA_ERR_INVAL (null ctx). */
 int gea_set_wait_limit(gea_ctx *ctx, int64_t polls);
 

@@ -1309,7 +1309,9 @@ int gea_set_tile_shape(gea_ctx *ctx, int32_t shape)
 int gea_set_wait_limit(gea_ctx *ctx, int64_t polls)
 {
     if (!ctx) return GEA_ERR_INVAL;
-    ctx->wait_polls = polls < 0 ? -1 : polls;
+    // a limit can only be lowered: above the default the wait stays bounded
+    // by the default
+    ctx->wait_polls = polls < 0 ? -1 : polls > (int64_t)kSpinLimit ? (int64_t)kSpinLimit : polls;
     return GEA_OK;
 }
 
